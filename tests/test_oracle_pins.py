@@ -1,0 +1,532 @@
+"""Pins of the FP64 CPU oracle against facts fixed by mathematics and physics,
+independent of the oracle's own code (closed forms, invariants, library
+routines, brute force).  No GPU needed."""
+import itertools
+import math
+import os
+import subprocess
+import sys
+import textwrap
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2105_10529_gb300 import inputs as IN
+
+MT = 173.0
+GS = math.sqrt(4 * math.pi * 0.118)
+
+
+def lin_pol(p, l):
+    """Linear polarisation basis built here (not the oracle's helper)."""
+    v = np.asarray(p[1:], float)
+    n = v / np.linalg.norm(v)
+    a = np.array([0.0, 0.0, 1.0]) if abs(n[2]) < 0.9 else np.array([1.0, 0.0, 0.0])
+    e1 = np.cross(a, n); e1 /= np.linalg.norm(e1)
+    e2 = np.cross(n, e1)
+    return np.concatenate([[0.0], e1 if l == 0 else e2])
+
+
+def boost(p, b):
+    bx, by, bz = b
+    b2 = bx * bx + by * by + bz * bz
+    g = 1 / math.sqrt(1 - b2)
+    out = []
+    for E, x, y, z in p:
+        bp = bx * x + by * y + bz * z
+        g2 = (g - 1) / b2
+        out.append([g * (E + bp), x + g2 * bp * bx + g * bx * E, y + g2 * bp * by + g * by * E,
+                    z + g2 * bp * bz + g * bz * E])
+    return np.array(out)
+
+
+def rotate(p, axis, ang):
+    axis = np.asarray(axis, float) / np.linalg.norm(axis)
+    K = np.array([[0, -axis[2], axis[1]], [axis[2], 0, -axis[0]], [-axis[1], axis[0], 0]])
+    R = np.eye(3) + math.sin(ang) * K + (1 - math.cos(ang)) * K @ K
+    q = p.copy()
+    q[:, 1:] = p[:, 1:] @ R.T
+    return q
+
+
+def event_momenta(rng, masses, rs):
+    nf = len(masses)
+    p, _ = O.rambo(nf, rs, masses, rng.random(4 * nf))
+    pin = np.array([[rs / 2, 0, 0, rs / 2], [rs / 2, 0, 0, -rs / 2]])
+    return np.vstack([pin, p])
+
+
+def mdot(a, b):
+    return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3]
+
+
+# ------------------------------------------------------------------ a1 Philox
+
+TRITON_PHILOX = textwrap.dedent("""
+    import os, sys, json
+    os.environ["TRITON_INTERPRET"] = "1"
+    import torch, triton, triton.language as tl
+    @triton.jit
+    def k(c0, c1, c2, c3, k0, k1, out, N: tl.constexpr):
+        i = tl.arange(0, N)
+        a = tl.load(c0 + i); b = tl.load(c1 + i); c = tl.load(c2 + i); d = tl.load(c3 + i)
+        ka = tl.load(k0 + i); kb = tl.load(k1 + i)
+        o0, o1, o2, o3 = tl.philox_impl(a, b, c, d, ka, kb, 10)
+        tl.store(out + i, o0); tl.store(out + N + i, o1)
+        tl.store(out + 2 * N + i, o2); tl.store(out + 3 * N + i, o3)
+    rows = json.loads(sys.stdin.read())
+    cols = [torch.tensor([r[j] for r in rows], dtype=torch.int64).to(torch.uint32) for j in range(6)]
+    out = torch.zeros(4 * len(rows), dtype=torch.uint32)
+    k[(1,)](*cols, out, N=len(rows))
+    o = out.to(torch.int64).tolist(); n = len(rows)
+    print(json.dumps([[o[j * n + i] & 0xFFFFFFFF for j in range(4)] for i in range(n)]))
+""")
+
+
+def test_philox_matches_independent_library_implementation():
+    """Philox4x32-10 (Salmon et al. 2011) against triton's philox, run by its
+    CPU interpreter in a child process: bit-exact on 32 counters/keys."""
+    pytest.importorskip("triton")
+    import json
+    rng = np.random.default_rng(11)
+    rows = [[0, 0, 0, 0, 0, 0], [0xFFFFFFFF] * 6]
+    rows += rng.integers(0, 2 ** 32, size=(30, 6), dtype=np.uint64).tolist()
+    env = dict(os.environ, TRITON_INTERPRET="1")
+    r = subprocess.run([sys.executable, "-c", TRITON_PHILOX], input=json.dumps(rows),
+                       capture_output=True, text=True, env=env, timeout=300)
+    if r.returncode != 0:
+        pytest.skip("triton interpreter unavailable: " + r.stderr[-300:])
+    ref = json.loads(r.stdout.strip().splitlines()[-1])
+    for row, exp in zip(rows, ref):
+        got = O.philox(row[:4], row[4:])
+        assert list(got) == exp, (row, got, exp)
+
+
+def test_uniform_conversion_is_exact_and_open():
+    assert O.u01(0, 0) == 0.5 * 2.0 ** -52
+    assert O.u01(0xFFFFFFFF, 0xFFFFFFFF) == 1.0 - 0.5 * 2.0 ** -52
+    # top 26 bits of each word only
+    assert O.u01(0x3F, 0x3F) == O.u01(0, 0)
+    assert O.u01(1 << 6, 0) == ((1 << 26) + 0.5) * 2.0 ** -52
+    u = O.uniforms(0, 12345, 3, 0, 18)
+    assert np.all((u > 0) & (u < 1))
+    # different iteration / channel / event give different streams
+    assert not np.array_equal(u, O.uniforms(0, 12345, 4, 0, 18))
+    assert not np.array_equal(u, O.uniforms(0, 12345, 3, 1, 18))
+    assert not np.array_equal(u, O.uniforms(0, 12346, 3, 0, 18))
+    # dims 2b, 2b+1 come from Philox block b
+    w = O.philox([12345, 0, 3, 2], [0, 0])
+    assert u[4] == O.u01(w[0], w[1]) and u[5] == O.u01(w[2], w[3])
+
+
+# ------------------------------------------------------------------ a2 VEGAS
+
+def test_vegas_uniform_grid_is_identity():
+    g = O.vegas_init(5, 50)
+    rng = np.random.default_rng(3)
+    for _ in range(200):
+        u = rng.random(5)
+        x, bins, j = O.vegas_map(g, u)
+        assert np.allclose(x, u, rtol=0, atol=2e-16)
+        assert np.array_equal(bins, np.floor(u * 50).astype(np.uint8))
+        assert abs(j - 1.0) < 1e-14
+
+
+def test_vegas_map_inside_bins_and_jacobian():
+    rng = np.random.default_rng(4)
+    e = np.sort(rng.random(49))
+    g = np.concatenate([[0.0], e, [1.0]])[None, :]
+    for _ in range(200):
+        u = rng.random(1)
+        x, b, j = O.vegas_map(g, u)
+        bb = int(b[0])
+        assert g[0, bb] <= x[0] <= g[0, bb + 1]
+        assert abs(j - 50 * (g[0, bb + 1] - g[0, bb])) <= 1e-15 * j
+
+
+def test_vegas_refine_constant_histogram_keeps_grid():
+    g = O.vegas_init(3, 50)
+    g2 = O.vegas_refine(np.ones((3, 50)), g)
+    assert np.allclose(g2, g, atol=1e-15)
+    # all-zero histogram: grid unchanged
+    assert np.array_equal(O.vegas_refine(np.zeros((3, 50)), g), g)
+
+
+def test_vegas_refine_equal_share_rebinning_closed_form():
+    """With alpha = 0 every bin with nonzero smoothed weight gets damped weight
+    1, so the new edges split the support of the smoothed histogram into 50
+    equal parts: a single filled bin 10 spreads (by smoothing) over bins 9-11,
+    i.e. [0.18, 0.24]."""
+    g = O.vegas_init(1, 50)
+    h = np.zeros((1, 50)); h[0, 10] = 3.0
+    g2 = O.vegas_refine(h, g, alpha=0.0)
+    k = np.arange(1, 50)
+    assert g2[0, 0] == 0.0 and g2[0, 50] == 1.0
+    assert np.allclose(g2[0, 1:50], 0.18 + 0.06 * k / 50, atol=1e-14)
+
+
+def test_vegas_integrates_peaked_function():
+    """VEGAS map + refine + combine on a separable Gaussian peak in 3-D with a
+    known integral; the result must lie within 4 sigma and the error must
+    drop below 1/5 of the uniform-grid error."""
+    rng = np.random.default_rng(7)
+    D, c, s = 3, 0.3, 0.05
+    one = math.sqrt(2 * math.pi) * s * 0.5 * (math.erf((1 - c) / (s * math.sqrt(2))) + math.erf(c / (s * math.sqrt(2))))
+    exact = one ** D
+    g = O.vegas_init(D, 50)
+    I, V = [], []
+    N = 4000
+    for it in range(6):
+        hist = np.zeros((D, 50)); sw = sw2 = 0.0
+        for _ in range(N):
+            x, b, j = O.vegas_map(g, rng.random(D))
+            f = np.exp(-0.5 * np.sum((x - c) ** 2) / s ** 2) * j / N
+            sw += f; sw2 += f * f
+            hist[np.arange(D), b.astype(int)] += f * f
+        I.append(sw); V.append((N * sw2 - sw * sw) / (N - 1))
+        g = O.vegas_refine(hist, g)
+    m, err, chi2 = O.vegas_combine(I, V)
+    assert abs(m - exact) < 4 * err
+    assert math.sqrt(V[-1]) < 0.2 * math.sqrt(V[0])
+
+
+# ------------------------------------------------------------------ a3 parton map
+
+def test_parton_map_jacobian_gives_luminosity_area():
+    """Integral of the Jacobian over the unit square = area of
+    {x1 x2 > tau0} in the unit square = 1 - tau0 + tau0 ln tau0."""
+    tau0 = 4 * MT ** 2 / 13000.0 ** 2
+    xg, wg = np.polynomial.legendre.leggauss(64)
+    xs, ws = 0.5 * (xg + 1), 0.5 * wg
+    tot = 0.0
+    for a, wa in zip(xs, ws):
+        for b, wb in zip(xs, ws):
+            x1, x2, j = O.parton_map(a, b, tau0)
+            tot += wa * wb * j
+            assert abs(x1 * x2 - tau0 ** a) < 1e-14 * tau0 ** a
+    assert abs(tot - (1 - tau0 + tau0 * math.log(tau0))) < 1e-12
+
+
+# ------------------------------------------------------------------ a4 RAMBO
+
+def test_rambo_massless_weight_is_textbook_volume():
+    rng = np.random.default_rng(1)
+    for n, ref in [(2, lambda s: 1 / (8 * math.pi)), (3, lambda s: s / (256 * math.pi ** 3))]:
+        p, w = O.rambo(n, 500.0, [0.0] * n, rng.random(4 * n))
+        assert abs(w - ref(500.0 ** 2)) < 1e-14 * ref(500.0 ** 2)
+
+
+@pytest.mark.parametrize("masses", [[MT, MT], [MT, MT, 0.0], [MT, MT, 0.0, 0.0], [0.0, 0.0, 0.0]])
+def test_rambo_conservation_and_mass_shell(masses):
+    rng = np.random.default_rng(2)
+    rs = 1500.0
+    for _ in range(50):
+        p, w = O.rambo(len(masses), rs, masses, rng.random(4 * len(masses)))
+        tot = p.sum(0)
+        assert abs(tot[0] - rs) < 1e-12 * rs
+        assert np.all(np.abs(tot[1:]) < 1e-11 * rs)
+        for pi, m in zip(p, masses):
+            assert abs(mdot(pi, pi) - m * m) < 1e-9 * rs * rs
+        assert w > 0
+
+
+def test_rambo_massive_two_body_weight_closed_form():
+    rng = np.random.default_rng(3)
+    for rs in [350.0, 400.0, 1000.0, 5000.0]:
+        p, w = O.rambo(2, rs, [MT, MT], rng.random(8))
+        beta = math.sqrt(1 - 4 * MT * MT / rs ** 2)
+        assert abs(w - beta / (8 * math.pi)) < 1e-13 * w
+
+
+def test_rambo_massive_three_body_volume_by_quadrature():
+    """<RAMBO weight> = Phi_3(s; m, m, 0) = int dm23^2/(2 pi) Phi_2(s; m, m23) Phi_2(m23^2; m, 0)."""
+    rs, m = 800.0, MT
+    s = rs * rs
+
+    def lam(a, b, c):
+        return a * a + b * b + c * c - 2 * a * b - 2 * a * c - 2 * b * c
+
+    def phi2(ss, ma, mb):
+        return math.sqrt(max(lam(ss, ma * ma, mb * mb), 0.0)) / (8 * math.pi * ss)
+
+    lo, hi = m * m, (rs - m) ** 2
+    xg, wg = np.polynomial.legendre.leggauss(200)
+    vol = sum(0.5 * (hi - lo) * w_ / (2 * math.pi) * phi2(s, m, math.sqrt(q)) * phi2(q, m, 0.0)
+              for q, w_ in zip(0.5 * (hi - lo) * (xg + 1) + lo, wg))
+    rng = np.random.default_rng(5)
+    ws = np.array([O.rambo(3, rs, [m, m, 0.0], rng.random(12))[1] for _ in range(40000)])
+    mc, err = ws.mean(), ws.std() / math.sqrt(len(ws))
+    assert abs(mc - vol) < 4 * err, (mc, vol, err)
+
+
+# ------------------------------------------------------------------ a5, a6
+
+def test_cuts_hand_built():
+    ph = IN.Physics()
+    sh = math.sinh(2.5)
+
+    def ev(glu):
+        p = np.zeros((6, 4))
+        p[:4, 0] = 1.0
+        for i, (pt, pz, phi) in enumerate(glu):
+            p[4 + i] = [math.hypot(pt, pz), pt * math.cos(phi), pt * math.sin(phi), pz]
+        return p
+
+    assert O.cuts(IN.GG_TTG, ph, ev([(31.0, 0.0, 0.0)])[:5]) == 1
+    assert O.cuts(IN.GG_TTG, ph, ev([(29.0, 0.0, 0.0)])[:5]) == 0
+    assert O.cuts(IN.GG_TTG, ph, ev([(40.0, 40.0 * math.sinh(2.49), 0.0)])[:5]) == 1
+    assert O.cuts(IN.GG_TTG, ph, ev([(40.0, -40.0 * math.sinh(2.51), 0.0)])[:5]) == 0
+    # Delta R: same eta, dphi 0.35 fails, 0.45 passes; wrap-around in phi
+    assert O.cuts(IN.GG_TTGG, ph, ev([(50, 10, 0.1), (60, 12, 0.45)])) == 0
+    assert O.cuts(IN.GG_TTGG, ph, ev([(50, 0, 0.0), (60, 0, 0.45)])) == 1
+    assert O.cuts(IN.GG_TTGG, ph, ev([(50, 0, 3.0), (60, 0, -3.0)])) == 0
+    assert O.cuts(IN.GG_TTGG, ph, ev([(50, 50 * math.sinh(0.3), 1.0), (60, 0, 1.0)])) == 0
+    assert O.cuts(IN.GG_TTGG, ph, ev([(50, 50 * math.sinh(0.5), 1.0), (60, 0, 1.0)])) == 1
+    assert O.cuts(IN.UG_TTU, ph, ev([(20.0, 0.0, 0.0)])[:5]) == 0
+    assert O.cuts(IN.GG_TT, ph, ev([])[:4]) == 1
+    assert abs(sh - 6.0502044810397875) < 1e-15
+
+
+def test_factorisation_scale():
+    ph = IN.Physics()
+    p = np.zeros((6, 4))
+    p[2, 1:] = [30.0, 40.0, 5.0]      # pT 50
+    p[3, 1:] = [0.0, 0.0, 100.0]      # pT 0
+    p[4, 1:] = [60.0, 80.0, 0.0]      # pT 100
+    p[5, 1:] = [0.0, 20.0, 7.0]       # pT 20
+    ht = math.sqrt(MT ** 2 + 2500) + MT + 100 + 20
+    assert abs(O.muf2(IN.GG_TTGG, ph, p) - ht * ht / 4) < 1e-10
+    ht3 = math.sqrt(MT ** 2 + 2500) + MT + 100
+    assert abs(O.muf2(IN.GG_TTG, ph, p[:5]) - ht3 * ht3 / 4) < 1e-10
+    assert O.muf2(IN.GG_TT, ph, p[:4]) == MT * MT
+
+
+# ------------------------------------------------------------------ a7 PDF
+
+def test_pdf_bicubic_exact_on_quadratics_and_nodes():
+    nx, nq = 100, 50
+    lx = np.linspace(math.log(1e-6), 0.0, nx)
+    lq = np.linspace(0.0, math.log(1e8), nq)
+    LX, LQ = np.meshgrid(lx, lq, indexing="ij")
+    f = lambda a, b: 3.0 + 0.2 * a - 0.1 * b + 0.05 * a * a + 0.02 * b * b - 0.03 * a * b
+    grid = np.stack([f(LX, LQ)] * 3)
+    pdf = O.Pdf(grid)
+    rng = np.random.default_rng(9)
+    for _ in range(300):
+        a = rng.uniform(lx[1], lx[nx - 3]); b = rng.uniform(lq[1], lq[nq - 3])
+        v = pdf.xf(0, math.exp(a), math.exp(b))
+        assert abs(v - f(a, b)) < 1e-11 * abs(f(a, b))
+    noisy = O.Pdf(IN.make_pdf_grid())
+    for i in [0, 5, 50, 98]:
+        for j in [0, 7, 30, 48]:
+            v = noisy.xf(0, math.exp(lx[i]), math.exp(lq[j]))
+            assert abs(v - noisy.grid[0, i, j]) < 1e-12 * abs(noisy.grid[0, i, j])
+    # Q^2 above the grid is clamped to its edge
+    x = 0.01
+    assert noisy.xf(0, x, 1e9) == noisy.xf(0, x, 1e8)
+
+
+def test_pdf_grid_momentum_sum():
+    """Without noise the gluon grid carries momentum fraction 1/2 at Q^2 = 1."""
+    g = IN.make_pdf_grid(noise=0.0)
+    pdf = O.Pdf(g)
+    xg, wg = np.polynomial.legendre.leggauss(200)
+    lx = 0.5 * (xg + 1) * math.log(1e-6)
+    # int_0^1 x g dx = int x g(x) x dlnx, tail below 1e-6 negligible (x^0.7)
+    tot = sum(w * 0.5 * (-math.log(1e-6)) * pdf.xf(0, math.exp(l), 1.0) * math.exp(l) for l, w in zip(lx, wg))
+    assert abs(tot - 0.5) < 2e-3
+
+
+# ------------------------------------------------------------------ matrix elements: closed forms
+
+def ee_momenta(rs, c, phi=0.3):
+    E = rs / 2
+    s = math.sqrt(1 - c * c)
+    return np.array([[E, 0, 0, E], [E, 0, 0, -E], [E, E * s * math.cos(phi), E * s * math.sin(phi), E * c],
+                     [E, -E * s * math.cos(phi), -E * s * math.sin(phi), -E * c]])
+
+
+def test_ee_mumu_qed_limit():
+    ph = IN.Physics(sqrt_s=1.0)
+    e2 = 4 * math.pi / ph.alpha_em_inv
+    for c in [-0.9, -0.2, 0.0, 0.5, 0.95]:
+        m2 = O.me2_ee_mumu_closed(ph, ee_momenta(1.0, c))
+        assert abs(m2 / (e2 * e2 * (1 + c * c)) - 1) < 3e-4
+
+
+def test_ee_mumu_z_peak_breit_wigner():
+    """At sqrt(s) = M_Z the gamma-Z interference vanishes and
+    sigma = 12 pi Gamma_ee Gamma_mumu / (M_Z^2 Gamma_Z^2) + 4 pi alpha^2 / (3 s),
+    with Gamma_ff = alpha M_Z (gL^2 + gR^2) / (6 sW^2 cW^2)."""
+    ph = IN.Physics(sqrt_s=91.188)
+    a = 1 / ph.alpha_em_inv
+    mz = ph.mz
+    mw2 = mz * mz / 2 + math.sqrt(mz ** 4 / 4 - math.pi * a * mz * mz / (math.sqrt(2) * ph.gf))
+    sw2 = 1 - mw2 / mz ** 2; cw2 = 1 - sw2
+    gL, gR = -0.5 + sw2, sw2
+    gam = a * mz * (gL ** 2 + gR ** 2) / (6 * sw2 * cw2)
+    s = mz * mz
+    ref = 12 * math.pi * gam * gam / (mz * mz * ph.wz ** 2) + 4 * math.pi * a * a / (3 * s)
+    xg, wg = np.polynomial.legendre.leggauss(40)
+    sig = sum(w * O.me2_ee_mumu_closed(ph, ee_momenta(mz, c)) / (32 * math.pi * s) for c, w in zip(xg, wg))
+    assert abs(sig / ref - 1) < 1e-12
+
+
+def test_gg_tt_recursion_equals_combridge():
+    rng = np.random.default_rng(21)
+    for rs in [360.0, 500.0, 2000.0, 8000.0]:
+        for _ in range(5):
+            p = event_momenta(rng, [MT, MT], rs)
+            bg = O.me2_bg(2, p, 2, MT, GS) / 256
+            cl = O.me2_gg_tt_closed(MT, GS, p)
+            assert abs(bg / cl - 1) < 1e-12
+
+
+def test_uu_tt_diagram_equals_closed_form():
+    rng = np.random.default_rng(22)
+    for rs in [360.0, 1000.0, 6000.0]:
+        for _ in range(5):
+            p = event_momenta(rng, [MT, MT], rs)
+            assert abs(O.me2_uu_tt_diagram(MT, GS, p) / O.me2_uu_tt_closed(MT, GS, p) - 1) < 1e-12
+
+
+@pytest.mark.parametrize("rs", [400.0, 1000.0, 3000.0])
+def test_sigma_hat_closed_forms(rs):
+    """int |M|^2 over the 2-body phase space = textbook sigma-hat (gg and q qbar)."""
+    s = rs * rs
+    rho = 4 * MT * MT / s
+    beta = math.sqrt(1 - rho)
+    a_s = GS ** 2 / (4 * math.pi)
+    gg = math.pi * a_s ** 2 / (3 * s) * ((1 + rho + rho * rho / 16) * math.log((1 + beta) / (1 - beta)) - beta * (7 / 4 + 31 * rho / 16))
+    qq = 8 * math.pi * a_s ** 2 / (27 * s) * beta * (1 + rho / 2)
+    xg, wg = np.polynomial.legendre.leggauss(600)
+    pa = beta * rs / 2
+    ig = iq = 0.0
+    for c, w in zip(xg, wg):
+        sn = math.sqrt(1 - c * c)
+        p = np.array([[rs / 2, 0, 0, rs / 2], [rs / 2, 0, 0, -rs / 2],
+                      [rs / 2, pa * sn, 0, pa * c], [rs / 2, -pa * sn, 0, -pa * c]])
+        # dPhi_2 = beta/(32 pi^2) dOmega -> beta/(16 pi) dcos
+        ig += w * O.me2_gg_tt_closed(MT, GS, p) * beta / (16 * math.pi) / (2 * s)
+        iq += w * O.me2_uu_tt_closed(MT, GS, p) * beta / (16 * math.pi) / (2 * s)
+    assert abs(ig / gg - 1) < 1e-12
+    assert abs(iq / qq - 1) < 1e-12
+
+
+# ------------------------------------------------------------------ matrix elements: invariants
+
+def gluon_setup(p, k):
+    gp = [p[0], p[1]] + [p[i] for i in range(4, 2 + k)]
+    kg = np.array([g if i < 2 else -g for i, g in enumerate(gp)])
+    return gp, kg
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_ward_identity_every_partial_amplitude(k):
+    rng = np.random.default_rng(30 + k)
+    masses = [MT, MT] + [0.0] * (k - 2)
+    p = event_momenta(rng, masses, 2500.0)
+    gp, kg = gluon_setup(p, k)
+    for pols in [(0,) * k, tuple(rng.integers(0, 2, k))]:
+        eps = np.array([lin_pol(gp[i], pols[i]) for i in range(k)], dtype=complex)
+        perms = list(itertools.permutations(range(k)))
+        spins = [(0, 0), (0, 1), (1, 0)]
+        scale = max(abs(O.bg_partial(kg, eps, p[2], p[3], MT, GS, s3, s4, perm))
+                    for perm in perms for s3, s4 in spins)
+        for perm in perms:
+            for j in range(k):
+                e2 = eps.copy(); e2[j] = gp[j]
+                for s3, s4 in spins:
+                    a = O.bg_partial(kg, e2, p[2], p[3], MT, GS, s3, s4, perm)
+                    assert abs(a) < 1e-13 * scale * gp[j][0]   # eps -> k scales A by ~E_j
+
+
+@pytest.mark.parametrize("k", [3, 4])
+def test_lorentz_invariance(k):
+    rng = np.random.default_rng(40 + k)
+    p = event_momenta(rng, [MT, MT] + [0.0] * (k - 2), 2000.0)
+    m0 = O.me2_bg(k, p, 2, MT, GS)
+    for b in [(0.3, -0.2, 0.5), (-0.6, 0.1, 0.1)]:
+        assert abs(O.me2_bg(k, boost(p, b), 2, MT, GS) / m0 - 1) < 1e-12
+    assert abs(O.me2_bg(k, rotate(p, (1, 2, 3), 0.7), 2, MT, GS) / m0 - 1) < 1e-12
+
+
+def test_bose_symmetry_gg_ttgg():
+    rng = np.random.default_rng(50)
+    p = event_momenta(rng, [MT, MT, 0.0, 0.0], 3000.0)
+    m0 = O.me2_bg(4, p, 2, MT, GS)
+    q = p.copy(); q[[4, 5]] = q[[5, 4]]
+    assert abs(O.me2_bg(4, q, 2, MT, GS) / m0 - 1) < 1e-12
+    q = p.copy(); q[[0, 1]] = q[[1, 0]]
+    assert abs(O.me2_bg(4, q, 2, MT, GS) / m0 - 1) < 1e-12
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_massless_partial_amplitudes_match_parke_taylor(k):
+    """Massless quark line: every nonzero helicity amplitude with <= 5 legs is
+    MHV or anti-MHV, |A|^2 = s_{qi}^3 s_{qbar i} / (cyclic product of s)
+    in the Tr(T^a T^b) = delta normalisation; with Tr = delta/2 and vertex
+    i g gamma^mu the partial amplitudes carry 2^(k/2) more (g = 1)."""
+    rng = np.random.default_rng(60 + k)
+    for _ in range(3):
+        rs = 1000.0
+        pf, _ = O.rambo(k, rs, [0.0] * k, rng.random(4 * k))
+        p = np.vstack([[[rs / 2, 0, 0, rs / 2], [rs / 2, 0, 0, -rs / 2]], pf])
+        t, tb = p[2], p[3]
+        gp, kg = gluon_setup(p, k)
+        gl_out = [-p[0], -p[1]] + [p[i] for i in range(4, 2 + k)]
+        s = lambda a, b: abs(mdot(a + b, a + b))
+        for perm in itertools.permutations(range(k)):
+            tot = 0.0
+            for pols in itertools.product((0, 1), repeat=k):
+                eps = np.array([lin_pol(gp[i], pols[i]) for i in range(k)], dtype=complex)
+                for s3 in (0, 1):
+                    for s4 in (0, 1):
+                        tot += abs(O.bg_partial(kg, eps, t, tb, 0.0, 1.0, s3, s4, perm)) ** 2
+            chain = [t] + [gl_out[i] for i in perm] + [tb]
+            den = np.prod([s(chain[i], chain[(i + 1) % len(chain)]) for i in range(len(chain))])
+            num = sum(s(t, g) ** 3 * s(tb, g) + s(t, g) * s(tb, g) ** 3 for g in gl_out)
+            n_conj = 1 if k == 2 else 2          # at 4 points MHV and anti-MHV coincide
+            assert abs(tot / (2 ** k * n_conj * num / den) - 1) < 1e-11
+
+
+def test_ug_ttu_ward_and_lorentz():
+    rng = np.random.default_rng(70)
+    for _ in range(3):
+        p = event_momenta(rng, [MT, MT, 0.0], 2000.0)
+        # reorder to u(p1) g(p2) -> t t~ u(p5)
+        m2 = O.me2_ug_ttu(MT, GS, p) * 96
+        assert O.amp2_ug_ttu_ward(MT, GS, p) < 1e-20 * m2
+        assert abs(O.me2_ug_ttu(MT, GS, boost(p, (0.2, 0.3, -0.4))) * 96 / m2 - 1) < 1e-12
+
+
+# ------------------------------------------------------------------ colour
+
+def test_gellmann_algebra():
+    T = [O.gellmann_T(a) for a in range(8)]
+    for a in range(8):
+        for b in range(8):
+            assert abs(np.trace(T[a] @ T[b]) - (0.5 if a == b else 0.0)) < 1e-15
+    cas = sum(t @ t for t in T)
+    assert np.allclose(cas, 4 / 3 * np.eye(3), atol=1e-15)
+    f = lambda a, b, c: (-2j * np.trace((T[a] @ T[b] - T[b] @ T[a]) @ T[c])).real
+    assert abs(f(0, 1, 2) - 1) < 1e-15
+    assert abs(f(0, 3, 6) - 0.5) < 1e-15
+    assert abs(f(3, 4, 7) - math.sqrt(3) / 2) < 1e-15
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_colour_matrix_casimir_and_symmetry(k):
+    Cm = O.colour_matrix(k)
+    CF, N = 4 / 3, 3
+    assert np.allclose(np.diag(Cm), CF ** k * N, atol=1e-12)
+    assert np.allclose(Cm, Cm.T, atol=1e-13)
+    rs = Cm.sum(1)
+    assert np.allclose(rs, rs[0], atol=1e-12)
+    if k == 2:
+        assert abs(Cm[0, 1] + CF / 2) < 1e-14
+    if k == 4:
+        vals = set(np.round(Cm.ravel() * 54).astype(int))
+        assert vals <= {512, 80, 71, 62, 8, -1, -10, -28, -64}
+        assert np.allclose(Cm * 54, np.round(Cm * 54), atol=1e-10)
