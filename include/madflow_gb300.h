@@ -1,0 +1,156 @@
+/*
+ * madflow_gb300 -- C ABI of the GB300 (sm_103a) leading-order Monte Carlo
+ * integrand of arXiv:2105.10529 ("Towards the automation of Monte Carlo
+ * simulation on GPU for particle physics processes", Carrazza, Cruz-Martinez,
+ * Rossi, Zaro).
+ *
+ * The paper (Sec. 1, Sec. 2.1) states the problem as: integrate a process
+ * over phase space with a VEGAS integrator that draws random numbers, builds
+ * the phase-space kinematics with fiducial cuts, interpolates PDFs, evaluates
+ * the squared matrix element of Sec. 2.2 and accumulates histograms, with
+ * every step on the GPU and results kept in GPU memory (Sec. 3.1).  The two
+ * user calls are therefore
+ *     integrate(process, sqrt_s, n_events, n_iter) -> sigma, error
+ *     evaluate(process, momenta)                   -> |M|^2
+ * plus the single-pass and inspection calls that the tests and the
+ * benchmark use.
+ *
+ * Conventions of every call:
+ *  - Return value: MF_OK (0) or an mf_status error code.  No C++ exception
+ *    crosses the ABI.  mf_last_error() gives a one-line reason.
+ *  - Pointers named *_dev are CUDA device pointers owned by the caller;
+ *    pointers named *_host are host pointers owned by the caller.  The
+ *    library owns only the buffers inside mf_ctx.
+ *  - All device work runs on the stream given to mf_create (NULL = legacy
+ *    default stream).  Calls that return host results synchronise that
+ *    stream before returning; calls that only write device buffers do not.
+ *  - Momenta are (E, px, py, pz) in GeV, float64, laid out [event][particle][4]
+ *    with the incoming particles first, in the process order listed below.
+ *  - Cross sections are in pb.
+ */
+#ifndef MADFLOW_GB300_H
+#define MADFLOW_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MF_ABI_VERSION 1
+
+/* Processes (particle order of the momenta):
+ *   MF_EE_MUMU  e-(1) e+(2) -> mu-(3) mu+(4), photon + Z, massless
+ *   MF_GG_TT    g(1) g(2) -> t(3) tbar(4)
+ *   MF_UU_TT    u(1) ubar(2) -> t(3) tbar(4)           (reserved, not built)
+ *   MF_GG_TTG   g(1) g(2) -> t(3) tbar(4) g(5)
+ *   MF_UG_TTU   u(1) g(2) -> t(3) tbar(4) u(5)         (reserved, not built)
+ *   MF_GG_TTGG  g(1) g(2) -> t(3) tbar(4) g(5) g(6)                          */
+enum mf_process { MF_EE_MUMU = 0, MF_GG_TT = 1, MF_UU_TT = 2, MF_GG_TTG = 3, MF_UG_TTU = 4, MF_GG_TTGG = 5 };
+
+/* Arithmetic of the matrix element: MF_FP64 everywhere in FP64; MF_MIXED
+ * evaluates wavefunctions, vertices and the colour sum in FP32 and keeps
+ * FP64 for phase space, Jacobians, propagator denominators, the heavy-quark
+ * spinor normalisation, PDFs, event weights and all accumulations. */
+enum mf_precision { MF_FP64 = 0, MF_MIXED = 1 };
+
+enum mf_status {
+    MF_OK = 0,
+    MF_ERR_ARG = 1,          /* invalid argument (null pointer, size out of range, unknown process) */
+    MF_ERR_CUDA = 2,         /* a CUDA runtime call failed; the reason is in mf_last_error           */
+    MF_ERR_TIMEOUT = 3,      /* a bounded device wait ran out                                        */
+    MF_ERR_NUMERIC = 4,      /* more non-finite event weights than allowed (they are zeroed)         */
+    MF_ERR_UNSUPPORTED = 5   /* process or option not built into this library                        */
+};
+
+/* Physics and integrator settings (GeV units).  mf_default_config fills the
+ * values of the synthetic workloads: m_t = 173, alpha_s = 0.118 (fixed),
+ * M_Z = 91.188, Gamma_Z = 2.441404, 1/alpha = 132.507, G_F = 1.16639e-5,
+ * pT > 30, |eta| < 2.5, Delta R > 0.4 on final light partons, 50 bins,
+ * alpha = 1.5, seed 0, channel 0, MF_MIXED. */
+typedef struct mf_config {
+    double mt;            /* top mass                                              */
+    double alpha_s;       /* strong coupling, fixed                                */
+    double mz, wz;        /* Z mass and width                                      */
+    double alpha_em_inv;  /* 1 / alpha_em                                          */
+    double gf;            /* Fermi constant (GeV^-2); sets M_W and sin^2(theta_W)  */
+    double pt_min;        /* light-parton pT cut (<= 0 disables)                   */
+    double eta_max;       /* light-parton |eta| cut (<= 0 disables)                */
+    double dr_min;        /* Delta R cut between final gluons (<= 0 disables)      */
+    unsigned long long seed;  /* Philox key                                        */
+    unsigned int channel;     /* channel id in the Philox counter (0..2^24-1)      */
+    int n_bins;           /* VEGAS bins per dimension, 2..64                        */
+    double alpha;         /* VEGAS damping exponent                                */
+    int precision;        /* mf_precision                                          */
+} mf_config;
+
+typedef struct mf_result {
+    double sigma_pb;          /* inverse-variance weighted mean over iterations     */
+    double error_pb;          /* its standard error                                 */
+    double chi2_dof;          /* chi^2 of the iteration estimates per d.o.f.        */
+    long long n_events_total; /* events evaluated                                   */
+    long long n_pass;         /* events passing the cuts                            */
+    long long n_nan;          /* non-finite weights set to zero                     */
+    int n_iter;
+} mf_result;
+
+/* Per-event outputs of mf_vegas_pass (device pointers, each nullable):
+ * u, x: [n][dim] uniforms and VEGAS-mapped points; bins: [n][dim] bin
+ * indices; w: [n] event weight f J in pb (before the 1/N of the estimator);
+ * mask: [n] cut mask; me2: [n] averaged |M|^2 (0 where the cuts fail);
+ * momenta: [n][n_ext][4] partonic-frame momenta. */
+typedef struct mf_event_arrays {
+    double *u, *x;
+    unsigned char *bins;
+    double *w;
+    unsigned char *mask;
+    double *me2;
+    double *momenta;
+} mf_event_arrays;
+
+int mf_default_config(mf_config *cfg);
+
+/* Number of external particles and the VEGAS dimension of a process
+ * (D = 2 for MF_EE_MUMU, 2 + 4 n_final otherwise).  MF_ERR_ARG for an
+ * unknown process. */
+int mf_process_info(int process, int *n_ext, int *dim);
+
+/* Create a context on the current CUDA device.  pdf_grid_host: x f(x,Q^2)
+ * on ln-uniform nodes, layout [flavour][ix][iq] with flavours 0 gluon,
+ * 1 u, 2 ubar (n_flav >= 1; the gluon processes read flavour 0), copied to
+ * the device.  stream: a cudaStream_t or NULL.  On success *out owns device
+ * buffers sized for every built process; release with mf_destroy. */
+int mf_create(struct mf_ctx **out, const mf_config *cfg, const double *pdf_grid_host, int n_flav, int nx, int nq,
+              double x_min, double q2_min, double q2_max, void *stream);
+void mf_destroy(struct mf_ctx *ctx);
+const char *mf_last_error(const struct mf_ctx *ctx);
+int mf_set_precision(struct mf_ctx *ctx, int precision);
+/* Replace the PDF grid (same shape as at creation) by a host copy. */
+int mf_set_pdf(struct mf_ctx *ctx, const double *pdf_grid_host);
+
+/* integrate (Sec. 2.1): n_iter VEGAS iterations of n_events each on a
+ * uniform starting grid, the grid refined after every iteration but the
+ * last; all iterations enter the weighted mean.  n_events >= 2,
+ * 1 <= n_iter <= 1000.  iter_host (nullable): [n_iter][2] estimate and
+ * variance per iteration; grid_host (nullable): [dim][n_bins+1] final grid.
+ * Synchronises the stream. */
+int mf_integrate(struct mf_ctx *ctx, int process, double sqrt_s, long long n_events, int n_iter,
+                 mf_result *out_host, double *iter_host, double *grid_host);
+
+/* One VEGAS pass over events [ev_offset, ev_offset + n_events) of Philox
+ * iteration `iteration` at a caller grid (grid_dev: [dim][n_bins+1]).
+ * sums_dev: [2 + dim n_bins] receives sum w, sum w^2 and the histogram
+ * of w^2 (w includes the 1/n_events of the estimator).  mask_in_dev
+ * (nullable, [n_events]) freezes the cut masks.  ev (nullable) requests the
+ * per-event outputs.  Does not synchronise. */
+int mf_vegas_pass(struct mf_ctx *ctx, int process, double sqrt_s, const double *grid_dev, long long n_events,
+                  long long ev_offset, unsigned int iteration, const unsigned char *mask_in_dev, double *sums_dev,
+                  const mf_event_arrays *ev);
+
+/* evaluate (Sec. 2.2): spin- and colour-averaged |M|^2 (identical-particle
+ * factor included) of n phase-space points.  momenta_dev: [n][n_ext][4];
+ * me2_dev: [n].  Does not synchronise. */
+int mf_evaluate(struct mf_ctx *ctx, int process, const double *momenta_dev, long long n, double *me2_dev);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

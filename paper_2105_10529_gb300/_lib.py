@@ -1,0 +1,79 @@
+"""ctypes declarations of the C ABI in include/madflow_gb300.h.
+
+Loading fails loudly when the CUDA library has not been built: there is no
+CPU fallback for any call.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmadflow_gb300.so")
+
+MF_EE_MUMU, MF_GG_TT, MF_UU_TT, MF_GG_TTG, MF_UG_TTU, MF_GG_TTGG = 0, 1, 2, 3, 4, 5
+MF_FP64, MF_MIXED = 0, 1
+STATUS = {0: "MF_OK", 1: "MF_ERR_ARG", 2: "MF_ERR_CUDA", 3: "MF_ERR_TIMEOUT", 4: "MF_ERR_NUMERIC",
+          5: "MF_ERR_UNSUPPORTED"}
+
+
+class MfConfig(C.Structure):
+    _fields_ = [("mt", C.c_double), ("alpha_s", C.c_double), ("mz", C.c_double), ("wz", C.c_double),
+                ("alpha_em_inv", C.c_double), ("gf", C.c_double), ("pt_min", C.c_double),
+                ("eta_max", C.c_double), ("dr_min", C.c_double), ("seed", C.c_ulonglong),
+                ("channel", C.c_uint), ("n_bins", C.c_int), ("alpha", C.c_double), ("precision", C.c_int)]
+
+
+class MfResult(C.Structure):
+    _fields_ = [("sigma_pb", C.c_double), ("error_pb", C.c_double), ("chi2_dof", C.c_double),
+                ("n_events_total", C.c_longlong), ("n_pass", C.c_longlong), ("n_nan", C.c_longlong),
+                ("n_iter", C.c_int)]
+
+
+class MfEventArrays(C.Structure):
+    _fields_ = [("u", C.c_void_p), ("x", C.c_void_p), ("bins", C.c_void_p), ("w", C.c_void_p),
+                ("mask", C.c_void_p), ("me2", C.c_void_p), ("momenta", C.c_void_p)]
+
+
+class MfError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"{STATUS.get(code, code)}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is not built; run __graft_entry__.build() "
+                               "(there is no CPU fallback)")
+        L = C.CDLL(LIB_PATH)
+        vp, dp, i64 = C.c_void_p, C.POINTER(C.c_double), C.c_longlong
+        sig = {
+            "mf_default_config": (C.c_int, [C.POINTER(MfConfig)]),
+            "mf_process_info": (C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+            "mf_create": (C.c_int, [C.POINTER(vp), C.POINTER(MfConfig), dp, C.c_int, C.c_int, C.c_int,
+                                    C.c_double, C.c_double, C.c_double, vp]),
+            "mf_destroy": (None, [vp]),
+            "mf_last_error": (C.c_char_p, [vp]),
+            "mf_set_precision": (C.c_int, [vp, C.c_int]),
+            "mf_set_pdf": (C.c_int, [vp, dp]),
+            "mf_integrate": (C.c_int, [vp, C.c_int, C.c_double, i64, C.c_int, C.POINTER(MfResult), dp, dp]),
+            "mf_vegas_pass": (C.c_int, [vp, C.c_int, C.c_double, vp, i64, i64, C.c_uint, vp, vp,
+                                        C.POINTER(MfEventArrays)]),
+            "mf_evaluate": (C.c_int, [vp, C.c_int, vp, i64, vp]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return ["mf_default_config", "mf_process_info", "mf_create", "mf_destroy", "mf_last_error",
+            "mf_set_precision", "mf_set_pdf", "mf_integrate", "mf_vegas_pass", "mf_evaluate"]

@@ -1,0 +1,149 @@
+"""Python front end of the C ABI (argument marshalling only; every step of
+the integrand runs in the library's CUDA kernels).  PyTorch provides device
+memory and the stream."""
+from __future__ import annotations
+
+import ctypes as C
+from typing import Optional
+
+import numpy as np
+
+from . import _lib
+from ._lib import MfConfig, MfError, MfEventArrays, MfResult
+from . import inputs as IN
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _check(ctx_ptr, rc: int):
+    if rc != 0:
+        msg = _lib.lib().mf_last_error(ctx_ptr)
+        raise MfError(rc, msg.decode() if msg else "")
+
+
+def process_info(process: int):
+    n_ext, dim = C.c_int(), C.c_int()
+    rc = _lib.lib().mf_process_info(process, C.byref(n_ext), C.byref(dim))
+    if rc:
+        raise MfError(rc, f"process {process}")
+    return n_ext.value, dim.value
+
+
+def make_config(physics: Optional[IN.Physics] = None, precision: int = _lib.MF_MIXED) -> MfConfig:
+    cfg = MfConfig()
+    _lib.lib().mf_default_config(C.byref(cfg))
+    if physics is not None:
+        for k in ("mt", "alpha_s", "mz", "wz", "alpha_em_inv", "gf", "pt_min", "eta_max", "dr_min",
+                  "seed", "channel", "n_bins", "alpha"):
+            setattr(cfg, k, getattr(physics, k))
+    cfg.precision = precision
+    return cfg
+
+
+class Context:
+    """Owns an mf_ctx bound to the current CUDA device and torch stream."""
+
+    def __init__(self, physics: Optional[IN.Physics] = None, pdf_grid: Optional[np.ndarray] = None,
+                 precision: int = _lib.MF_MIXED, stream=None):
+        torch = _torch()
+        if not torch.cuda.is_available():
+            raise RuntimeError("madflow_gb300 needs a CUDA device (no CPU fallback)")
+        self.physics = physics or IN.Physics()
+        grid = IN.make_pdf_grid() if pdf_grid is None else np.ascontiguousarray(pdf_grid, dtype=np.float64)
+        self._grid = grid
+        nf, nx, nq = grid.shape
+        s = stream if stream is not None else torch.cuda.current_stream()
+        self.stream = s
+        self.cfg = make_config(self.physics, precision)
+        ptr = C.c_void_p()
+        rc = _lib.lib().mf_create(C.byref(ptr), C.byref(self.cfg), grid.ctypes.data_as(C.POINTER(C.c_double)),
+                                  nf, nx, nq, IN.PDF_X_MIN, IN.PDF_Q2_MIN, IN.PDF_Q2_MAX,
+                                  C.c_void_p(s.cuda_stream))
+        if rc:
+            raise MfError(rc, "mf_create failed")
+        self.ptr = ptr
+
+    def close(self):
+        if getattr(self, "ptr", None):
+            _lib.lib().mf_destroy(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_precision(self, precision: int):
+        _check(self.ptr, _lib.lib().mf_set_precision(self.ptr, precision))
+
+    def set_pdf(self, grid_host: np.ndarray):
+        """Upload a host PDF grid (same shape as at creation); asynchronous on the stream."""
+        g = np.ascontiguousarray(grid_host, dtype=np.float64)
+        self._pending_pdf = g
+        _check(self.ptr, _lib.lib().mf_set_pdf(self.ptr, g.ctypes.data_as(C.POINTER(C.c_double))))
+
+    def integrate(self, process: int, sqrt_s: float, n_events: int, n_iter: int, want_grid: bool = False):
+        res = MfResult()
+        it = np.zeros((n_iter, 2))
+        _, dim = process_info(process)
+        grid = np.zeros((dim, self.cfg.n_bins + 1)) if want_grid else None
+        rc = _lib.lib().mf_integrate(self.ptr, process, sqrt_s, n_events, n_iter, C.byref(res),
+                                     it.ctypes.data_as(C.POINTER(C.c_double)),
+                                     grid.ctypes.data_as(C.POINTER(C.c_double)) if grid is not None else None)
+        out = dict(sigma=res.sigma_pb, error=res.error_pb, chi2dof=res.chi2_dof, n_events=res.n_events_total,
+                   n_pass=res.n_pass, n_nan=res.n_nan, per_iter=it, grid=grid, status=rc)
+        _check(self.ptr, rc)
+        return out
+
+    def vegas_pass(self, process: int, sqrt_s: float, grid, n_events: int, ev_offset: int = 0,
+                   iteration: int = 0, mask_in=None, want_events: bool = False, fields=None):
+        """One pass at a device grid; returns (sums tensor, events dict or None)."""
+        torch = _torch()
+        n_ext, dim = process_info(process)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        grid = grid.to(device=dev, dtype=torch.float64).contiguous()
+        sums = torch.empty(2 + dim * self.cfg.n_bins, dtype=torch.float64, device=dev)
+        ev = None
+        evs = None
+        if want_events:
+            fields = fields or ("u", "x", "bins", "w", "mask", "me2", "momenta")
+            shapes = dict(u=((n_events, dim), torch.float64), x=((n_events, dim), torch.float64),
+                          bins=((n_events, dim), torch.uint8), w=((n_events,), torch.float64),
+                          mask=((n_events,), torch.uint8), me2=((n_events,), torch.float64),
+                          momenta=((n_events, n_ext, 4), torch.float64))
+            evs = {f: torch.empty(*shapes[f][0], dtype=shapes[f][1], device=dev) for f in fields}
+            ev = MfEventArrays(**{f: C.c_void_p(evs[f].data_ptr()) if f in evs else None
+                                  for f, _ in MfEventArrays._fields_})
+        mptr = None
+        if mask_in is not None:
+            mask_in = mask_in.to(device=dev, dtype=torch.uint8).contiguous()
+            mptr = C.c_void_p(mask_in.data_ptr())
+        rc = _lib.lib().mf_vegas_pass(self.ptr, process, sqrt_s, C.c_void_p(grid.data_ptr()), n_events, ev_offset,
+                                      iteration, mptr, C.c_void_p(sums.data_ptr()),
+                                      C.byref(ev) if ev is not None else None)
+        _check(self.ptr, rc)
+        return sums, evs
+
+    def evaluate(self, process: int, momenta):
+        """Averaged |M|^2 of momenta [n, n_ext, 4] (float64, on the device)."""
+        torch = _torch()
+        mom = momenta.to(dtype=torch.float64).contiguous()
+        n = mom.shape[0]
+        out = torch.empty(n, dtype=torch.float64, device=mom.device)
+        rc = _lib.lib().mf_evaluate(self.ptr, process, C.c_void_p(mom.data_ptr()), n, C.c_void_p(out.data_ptr()))
+        _check(self.ptr, rc)
+        return out
+
+
+def integrate(process: int, sqrt_s: float, n_events: int, n_iter: int, physics: Optional[IN.Physics] = None,
+              precision: int = _lib.MF_MIXED):
+    """One-shot integrate(process, sqrt_s, n_events, n_iter) -> sigma, error (Sec. 2.1)."""
+    ctx = Context(physics, precision=precision)
+    try:
+        return ctx.integrate(process, sqrt_s, n_events, n_iter)
+    finally:
+        ctx.close()

@@ -1,0 +1,212 @@
+// Generated by paper_2105_10529_gb300/gen/qcd_diagrams.py -- do not edit.
+// gg_ttg: 16 Feynman diagrams (18 amplitudes with the four-gluon
+// colour structures counted apart), 6 colour flows, 32 helicities.
+// Wavefunction/vertex calls per helicity: {'vvv': 3, 'vvvv': 0, 'ffv_row': 3, 'ffv_col': 3, 'ffv_amp': 12, 'vvv_amp': 3, 'vvvv_amp': 1, 'ffv_cur': 1}
+#pragma once
+#include "mf_helas.cuh"
+namespace mf {
+struct Me_gg_ttg {
+  static constexpr int NEXT = 5;
+  static constexpr int NCOL = 6;
+  static constexpr int NHEL = 32;
+  static constexpr int NGLUON = 3;
+  static constexpr int NDIAG = 16;
+  static constexpr double COLOUR_DEN = 9.0;
+  static constexpr double AVG = 1.0 / 256.0;
+  static constexpr double SYM = 1.0;
+  // helicity-independent per-event pieces
+  template <typename R> struct Inv {
+    R kr[3][4]; R p3r[4]; R iG[4]; R iQ[6];
+    R e1[3][3]; R e2[3][3]; FermionBasis<R> fb3, fb4; R mt;
+  };
+  // averaged |M|^2 (spin/colour average and identical-particle factor included);
+  // p: momenta (E,px,py,pz) incoming first: g, g, t, tbar, g...
+  template <typename R>
+  __device__ static double me2(const double (&p)[NEXT][4], double mt, double gs);
+};
+
+// one helicity configuration: amplitudes, colour flows and the colour sum;
+// out of line so that its register allocation sees only one helicity
+template <typename R>
+__device__ __noinline__ R hel_gg_ttg(const Me_gg_ttg::Inv<R>& v, int ih)
+{
+    constexpr int NCOL = Me_gg_ttg::NCOL;
+#define HEL(i) ((ih >> (i)) & 1 ? 1 : -1)
+    cx<R> jamp[NCOL];
+    #pragma unroll
+    for (int c = 0; c < NCOL; ++c) jamp[c] = mkc(R(0), R(0));
+    const W4<R> g0 = ext_gluon(v.e1[0], v.e2[0], HEL(0), false);
+    const W4<R> g1 = ext_gluon(v.e1[1], v.e2[1], HEL(1), false);
+    const W4<R> g2 = ext_gluon(v.e1[2], v.e2[2], HEL(4), true);
+    const W4<R> ub3 = ext_ubar(v.fb3, HEL(2));
+    const W4<R> v4 = ext_v(v.fb4, HEL(3));
+    const R k1_1[4] = {v.kr[0][0], v.kr[0][1], v.kr[0][2], v.kr[0][3]};
+    const R k2_2[4] = {v.kr[1][0], v.kr[1][1], v.kr[1][2], v.kr[1][3]};
+    const W4<R> w3 = vvv_cur(g0, g1, k1_1, k2_2, v.iG[0]);
+    const R k1_4[4] = {v.kr[0][0], v.kr[0][1], v.kr[0][2], v.kr[0][3]};
+    const R k4_5[4] = {v.kr[2][0], v.kr[2][1], v.kr[2][2], v.kr[2][3]};
+    const W4<R> w6 = vvv_cur(g0, g2, k1_4, k4_5, v.iG[1]);
+    const R k2_7[4] = {v.kr[1][0], v.kr[1][1], v.kr[1][2], v.kr[1][3]};
+    const R k4_8[4] = {v.kr[2][0], v.kr[2][1], v.kr[2][2], v.kr[2][3]};
+    const W4<R> w9 = vvv_cur(g1, g2, k2_7, k4_8, v.iG[2]);
+    const R q1_10[4] = {v.p3r[0] - (v.kr[0][0]), v.p3r[1] - (v.kr[0][1]), v.p3r[2] - (v.kr[0][2]), v.p3r[3] - (v.kr[0][3])};
+    const W4<R> w11 = ffv_row(ub3, g0, q1_10, v.mt, v.iQ[0]);
+    const R q3_13[4] = {v.p3r[0] - (v.kr[0][0] + v.kr[1][0]), v.p3r[1] - (v.kr[0][1] + v.kr[1][1]), v.p3r[2] - (v.kr[0][2] + v.kr[1][2]), v.p3r[3] - (v.kr[0][3] + v.kr[1][3])};
+    const W4<R> w12 = ffv_col(g2, v4, q3_13, v.mt, v.iQ[2]);
+    const cx<R> a1 = ffv_amp(w11, w12, g1);
+    jamp[0].r -= a1.i; jamp[0].i += a1.r;
+    const R q5_15[4] = {v.p3r[0] - (v.kr[0][0] + v.kr[2][0]), v.p3r[1] - (v.kr[0][1] + v.kr[2][1]), v.p3r[2] - (v.kr[0][2] + v.kr[2][2]), v.p3r[3] - (v.kr[0][3] + v.kr[2][3])};
+    const W4<R> w14 = ffv_col(g1, v4, q5_15, v.mt, v.iQ[4]);
+    const cx<R> a2 = ffv_amp(w11, w14, g2);
+    jamp[1].r -= a2.i; jamp[1].i += a2.r;
+    const cx<R> a3 = ffv_amp(w11, v4, w9);
+    jamp[0].r -= a3.i; jamp[0].i += a3.r;
+    jamp[1].r += a3.i; jamp[1].i -= a3.r;
+    const R q2_16[4] = {v.p3r[0] - (v.kr[1][0]), v.p3r[1] - (v.kr[1][1]), v.p3r[2] - (v.kr[1][2]), v.p3r[3] - (v.kr[1][3])};
+    const W4<R> w17 = ffv_row(ub3, g1, q2_16, v.mt, v.iQ[1]);
+    const cx<R> a4 = ffv_amp(w17, w12, g0);
+    jamp[2].r -= a4.i; jamp[2].i += a4.r;
+    const R q6_19[4] = {v.p3r[0] - (v.kr[1][0] + v.kr[2][0]), v.p3r[1] - (v.kr[1][1] + v.kr[2][1]), v.p3r[2] - (v.kr[1][2] + v.kr[2][2]), v.p3r[3] - (v.kr[1][3] + v.kr[2][3])};
+    const W4<R> w18 = ffv_col(g0, v4, q6_19, v.mt, v.iQ[5]);
+    const cx<R> a5 = ffv_amp(w17, w18, g2);
+    jamp[3].r -= a5.i; jamp[3].i += a5.r;
+    const cx<R> a6 = ffv_amp(w17, v4, w6);
+    jamp[2].r -= a6.i; jamp[2].i += a6.r;
+    jamp[3].r += a6.i; jamp[3].i -= a6.r;
+    const R q4_20[4] = {v.p3r[0] - (v.kr[2][0]), v.p3r[1] - (v.kr[2][1]), v.p3r[2] - (v.kr[2][2]), v.p3r[3] - (v.kr[2][3])};
+    const W4<R> w21 = ffv_row(ub3, g2, q4_20, v.mt, v.iQ[3]);
+    const cx<R> a7 = ffv_amp(w21, w14, g0);
+    jamp[4].r -= a7.i; jamp[4].i += a7.r;
+    const cx<R> a8 = ffv_amp(w21, w18, g1);
+    jamp[5].r -= a8.i; jamp[5].i += a8.r;
+    const cx<R> a9 = ffv_amp(w21, v4, w3);
+    jamp[4].r -= a9.i; jamp[4].i += a9.r;
+    jamp[5].r += a9.i; jamp[5].i -= a9.r;
+    const cx<R> a10 = ffv_amp(ub3, w12, w3);
+    jamp[0].r -= a10.i; jamp[0].i += a10.r;
+    jamp[2].r += a10.i; jamp[2].i -= a10.r;
+    const cx<R> a11 = ffv_amp(ub3, w14, w6);
+    jamp[1].r -= a11.i; jamp[1].i += a11.r;
+    jamp[4].r += a11.i; jamp[4].i -= a11.r;
+    const cx<R> a12 = ffv_amp(ub3, w18, w9);
+    jamp[3].r -= a12.i; jamp[3].i += a12.r;
+    jamp[5].r += a12.i; jamp[5].i -= a12.r;
+    const W4<R> jq = ffv_cur(ub3, v4, v.iG[3]);
+    const R k1_22[4] = {v.kr[0][0], v.kr[0][1], v.kr[0][2], v.kr[0][3]};
+    const R k6_23[4] = {v.kr[1][0] + v.kr[2][0], v.kr[1][1] + v.kr[2][1], v.kr[1][2] + v.kr[2][2], v.kr[1][3] + v.kr[2][3]};
+    const R k7_24[4] = {v.kr[0][0] + v.kr[1][0] + v.kr[2][0], v.kr[0][1] + v.kr[1][1] + v.kr[2][1], v.kr[0][2] + v.kr[1][2] + v.kr[2][2], v.kr[0][3] + v.kr[1][3] + v.kr[2][3]};
+    const R nkk7_24[4] = {-k7_24[0], -k7_24[1], -k7_24[2], -k7_24[3]};
+    const cx<R> a13 = vvv_amp(g0, w9, jq, k1_22, k6_23, nkk7_24);
+    jamp[0].r -= a13.i; jamp[0].i += a13.r;
+    jamp[1].r += a13.i; jamp[1].i -= a13.r;
+    jamp[3].r += a13.i; jamp[3].i -= a13.r;
+    jamp[5].r -= a13.i; jamp[5].i += a13.r;
+    const R k3_25[4] = {v.kr[0][0] + v.kr[1][0], v.kr[0][1] + v.kr[1][1], v.kr[0][2] + v.kr[1][2], v.kr[0][3] + v.kr[1][3]};
+    const R k4_26[4] = {v.kr[2][0], v.kr[2][1], v.kr[2][2], v.kr[2][3]};
+    const R k7_27[4] = {v.kr[0][0] + v.kr[1][0] + v.kr[2][0], v.kr[0][1] + v.kr[1][1] + v.kr[2][1], v.kr[0][2] + v.kr[1][2] + v.kr[2][2], v.kr[0][3] + v.kr[1][3] + v.kr[2][3]};
+    const R nkk7_27[4] = {-k7_27[0], -k7_27[1], -k7_27[2], -k7_27[3]};
+    const cx<R> a14 = vvv_amp(w3, g2, jq, k3_25, k4_26, nkk7_27);
+    jamp[0].r -= a14.i; jamp[0].i += a14.r;
+    jamp[2].r += a14.i; jamp[2].i -= a14.r;
+    jamp[4].r += a14.i; jamp[4].i -= a14.r;
+    jamp[5].r -= a14.i; jamp[5].i += a14.r;
+    const R k5_28[4] = {v.kr[0][0] + v.kr[2][0], v.kr[0][1] + v.kr[2][1], v.kr[0][2] + v.kr[2][2], v.kr[0][3] + v.kr[2][3]};
+    const R k2_29[4] = {v.kr[1][0], v.kr[1][1], v.kr[1][2], v.kr[1][3]};
+    const R k7_30[4] = {v.kr[0][0] + v.kr[1][0] + v.kr[2][0], v.kr[0][1] + v.kr[1][1] + v.kr[2][1], v.kr[0][2] + v.kr[1][2] + v.kr[2][2], v.kr[0][3] + v.kr[1][3] + v.kr[2][3]};
+    const R nkk7_30[4] = {-k7_30[0], -k7_30[1], -k7_30[2], -k7_30[3]};
+    const cx<R> a15 = vvv_amp(w6, g1, jq, k5_28, k2_29, nkk7_30);
+    jamp[1].r -= a15.i; jamp[1].i += a15.r;
+    jamp[2].r += a15.i; jamp[2].i -= a15.r;
+    jamp[3].r -= a15.i; jamp[3].i += a15.r;
+    jamp[4].r += a15.i; jamp[4].i -= a15.r;
+    cx<R> a16, a17, a18;
+    vvvv_amp(g0, g1, g2, jq, a16, a17, a18);
+    jamp[0].r -= a16.i; jamp[0].i += a16.r;
+    jamp[2].r += a16.i; jamp[2].i -= a16.r;
+    jamp[4].r += a16.i; jamp[4].i -= a16.r;
+    jamp[5].r -= a16.i; jamp[5].i += a16.r;
+    jamp[1].r -= a17.i; jamp[1].i += a17.r;
+    jamp[2].r += a17.i; jamp[2].i -= a17.r;
+    jamp[3].r -= a17.i; jamp[3].i += a17.r;
+    jamp[4].r += a17.i; jamp[4].i -= a17.r;
+    jamp[0].r += a18.i; jamp[0].i -= a18.r;
+    jamp[1].r -= a18.i; jamp[1].i += a18.r;
+    jamp[3].r -= a18.i; jamp[3].i += a18.r;
+    jamp[5].r += a18.i; jamp[5].i -= a18.r;
+    R me = R(0);
+    { const R zr = R(64.0) * jamp[0].r + R(-16.0) * jamp[1].r + R(-16.0) * jamp[2].r + R(2.0) * jamp[3].r + R(2.0) * jamp[4].r + R(20.0) * jamp[5].r; const R zi = R(64.0) * jamp[0].i + R(-16.0) * jamp[1].i + R(-16.0) * jamp[2].i + R(2.0) * jamp[3].i + R(2.0) * jamp[4].i + R(20.0) * jamp[5].i;
+      me = fma(jamp[0].r, zr, fma(jamp[0].i, zi, me)); }
+    { const R zr = R(64.0) * jamp[1].r + R(2.0) * jamp[2].r + R(20.0) * jamp[3].r + R(-16.0) * jamp[4].r + R(2.0) * jamp[5].r; const R zi = R(64.0) * jamp[1].i + R(2.0) * jamp[2].i + R(20.0) * jamp[3].i + R(-16.0) * jamp[4].i + R(2.0) * jamp[5].i;
+      me = fma(jamp[1].r, zr, fma(jamp[1].i, zi, me)); }
+    { const R zr = R(64.0) * jamp[2].r + R(-16.0) * jamp[3].r + R(20.0) * jamp[4].r + R(2.0) * jamp[5].r; const R zi = R(64.0) * jamp[2].i + R(-16.0) * jamp[3].i + R(20.0) * jamp[4].i + R(2.0) * jamp[5].i;
+      me = fma(jamp[2].r, zr, fma(jamp[2].i, zi, me)); }
+    { const R zr = R(64.0) * jamp[3].r + R(2.0) * jamp[4].r + R(-16.0) * jamp[5].r; const R zi = R(64.0) * jamp[3].i + R(2.0) * jamp[4].i + R(-16.0) * jamp[5].i;
+      me = fma(jamp[3].r, zr, fma(jamp[3].i, zi, me)); }
+    { const R zr = R(64.0) * jamp[4].r + R(-16.0) * jamp[5].r; const R zi = R(64.0) * jamp[4].i + R(-16.0) * jamp[5].i;
+      me = fma(jamp[4].r, zr, fma(jamp[4].i, zi, me)); }
+    { const R zr = R(64.0) * jamp[5].r; const R zi = R(64.0) * jamp[5].i;
+      me = fma(jamp[5].r, zr, fma(jamp[5].i, zi, me)); }
+    return me;
+#undef HEL
+}
+
+template <typename R>
+__device__ __noinline__ double me2_gg_ttg_impl(const double* pflat, double mt, double gs)
+{
+    constexpr int NEXT = Me_gg_ttg::NEXT, NHEL = Me_gg_ttg::NHEL, NGLUON = Me_gg_ttg::NGLUON;
+    constexpr double COLOUR_DEN = Me_gg_ttg::COLOUR_DEN, AVG = Me_gg_ttg::AVG, SYM = Me_gg_ttg::SYM;
+    double p[NEXT][4];
+    for (int i = 0; i < NEXT; ++i)
+        for (int c = 0; c < 4; ++c) p[i][c] = pflat[4 * i + c];
+    Me_gg_ttg::Inv<R> v;
+    // gluon momenta, incoming convention: gluons 0,1 incoming, the rest outgoing
+    const double kd1[4] = {p[0][0], p[0][1], p[0][2], p[0][3]};
+    const double kd2[4] = {p[1][0], p[1][1], p[1][2], p[1][3]};
+    const double kd4[4] = {-p[4][0], -p[4][1], -p[4][2], -p[4][3]};
+    const double kd3[4] = {kd1[0] + kd2[0], kd1[1] + kd2[1], kd1[2] + kd2[2], kd1[3] + kd2[3]};
+    const double kd5[4] = {kd1[0] + kd4[0], kd1[1] + kd4[1], kd1[2] + kd4[2], kd1[3] + kd4[3]};
+    const double kd6[4] = {kd2[0] + kd4[0], kd2[1] + kd4[1], kd2[2] + kd4[2], kd2[3] + kd4[3]};
+    const double kd7[4] = {kd1[0] + kd2[0] + kd4[0], kd1[1] + kd2[1] + kd4[1], kd1[2] + kd2[2] + kd4[2], kd1[3] + kd2[3] + kd4[3]};
+    for (int c = 0; c < 4; ++c) v.kr[0][c] = R(kd1[c]);
+    for (int c = 0; c < 4; ++c) v.kr[1][c] = R(kd2[c]);
+    for (int c = 0; c < 4; ++c) v.kr[2][c] = R(kd4[c]);
+    for (int c = 0; c < 4; ++c) v.p3r[c] = R(p[2][c]);
+    v.iG[0] = R(1.0 / mdot(kd3, kd3));
+    v.iG[1] = R(1.0 / mdot(kd5, kd5));
+    v.iG[2] = R(1.0 / mdot(kd6, kd6));
+    v.iG[3] = R(1.0 / mdot(kd7, kd7));
+    { const double q[4] = {p[2][0] - kd1[0], p[2][1] - kd1[1], p[2][2] - kd1[2], p[2][3] - kd1[3]};
+      v.iQ[0] = R(1.0 / (mdot(q, q) - mt * mt)); }
+    { const double q[4] = {p[2][0] - kd2[0], p[2][1] - kd2[1], p[2][2] - kd2[2], p[2][3] - kd2[3]};
+      v.iQ[1] = R(1.0 / (mdot(q, q) - mt * mt)); }
+    { const double q[4] = {p[2][0] - kd3[0], p[2][1] - kd3[1], p[2][2] - kd3[2], p[2][3] - kd3[3]};
+      v.iQ[2] = R(1.0 / (mdot(q, q) - mt * mt)); }
+    { const double q[4] = {p[2][0] - kd4[0], p[2][1] - kd4[1], p[2][2] - kd4[2], p[2][3] - kd4[3]};
+      v.iQ[3] = R(1.0 / (mdot(q, q) - mt * mt)); }
+    { const double q[4] = {p[2][0] - kd5[0], p[2][1] - kd5[1], p[2][2] - kd5[2], p[2][3] - kd5[3]};
+      v.iQ[4] = R(1.0 / (mdot(q, q) - mt * mt)); }
+    { const double q[4] = {p[2][0] - kd6[0], p[2][1] - kd6[1], p[2][2] - kd6[2], p[2][3] - kd6[3]};
+      v.iQ[5] = R(1.0 / (mdot(q, q) - mt * mt)); }
+    { double a[3], b[3]; gluon_basis(p[0], a, b);
+      for (int j = 0; j < 3; ++j) { v.e1[0][j] = R(a[j]); v.e2[0][j] = R(b[j]); } }
+    { double a[3], b[3]; gluon_basis(p[1], a, b);
+      for (int j = 0; j < 3; ++j) { v.e1[1][j] = R(a[j]); v.e2[1][j] = R(b[j]); } }
+    { double a[3], b[3]; gluon_basis(p[4], a, b);
+      for (int j = 0; j < 3; ++j) { v.e1[2][j] = R(a[j]); v.e2[2][j] = R(b[j]); } }
+    v.fb3 = fermion_basis<R>(p[2], mt);
+    v.fb4 = fermion_basis<R>(p[3], mt);
+    v.mt = R(mt);
+    R acc = R(0);
+#pragma unroll 1
+    for (int ih = 0; ih < NHEL; ++ih) acc += hel_gg_ttg<R>(v, ih);
+    double gk = 1.0;
+    for (int i = 0; i < NGLUON; ++i) gk *= gs * gs;
+    return double(acc) / COLOUR_DEN * gk * AVG * SYM;
+}
+
+template <typename R>
+__device__ double Me_gg_ttg::me2(const double (&p)[NEXT][4], double mt, double gs)
+{
+    return me2_gg_ttg_impl<R>(&p[0][0], mt, gs);
+}
+}  // namespace mf

@@ -1,0 +1,400 @@
+// C ABI of the library (declared in include/madflow_gb300.h).
+#include <cuda_runtime.h>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "mf_dispatch.cuh"
+#include "../../include/madflow_gb300.h"
+
+using namespace mf;
+
+struct mf_ctx {
+    mf_config cfg;
+    cudaStream_t stream = nullptr;
+    int device = 0, n_sm = 0;
+    int n_flav = 0, nx = 0, nq = 0;
+    double x_min = 0, q2_min = 0, q2_max = 0;
+    double* d_pdf = nullptr;
+    double* d_grid = nullptr;        // [MAX_DIM][MAX_BINS+1]
+    double* d_partials = nullptr;    // [max_blocks][2 + MAX_DIM MAX_BINS]
+    double* d_iter = nullptr;        // [MAX_ITER][2]
+    double* d_sums = nullptr;        // [2 + MAX_DIM MAX_BINS]
+    unsigned long long* d_counters = nullptr;
+    int max_blocks = 0;
+    std::string err;
+};
+
+namespace mf {
+// ------------------------------------------------------------------ end of a pass
+
+// Sums the per-CTA partials in CTA order, stores (I_k, var_k) for the
+// iteration and, unless this is the last iteration, refines the grid
+// (Lepage 1978: smoothing, normalisation, damping ((r-1)/ln r)^alpha,
+// equal-share rebinning).  One CTA; column c of the partials is summed by
+// thread c.
+__global__ void finish_pass_kernel(const double* partials, int nblk, int D, int nb, long long n, double alpha,
+                                   int refine, double* grid, double* iter_stats, double* sums_out)
+{
+    extern __shared__ double sh[];     // [2 + D nb] sums, then refine scratch
+    const int ncol = 2 + D * nb;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += partials[(size_t)b * ncol + c];
+        sh[c] = s;
+        if (sums_out) sums_out[c] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && iter_stats) {
+        const double I = sh[0], I2 = sh[1];
+        iter_stats[0] = I;
+        iter_stats[1] = ((double)n * I2 - I * I) / (double)(n - 1);
+    }
+    if (!refine) return;
+    const int d = threadIdx.x;
+    if (d >= D) return;
+    const double* h = sh + 2 + d * nb;
+    double* e = grid + d * (nb + 1);
+    double tot = 0.0;
+    for (int i = 0; i < nb; ++i) tot += h[i];
+    if (!(tot > 0.0)) return;
+    double s[MAX_BINS], w[MAX_BINS], ne[MAX_BINS + 1];
+    s[0] = (7.0 * h[0] + h[1]) / 8.0;
+    for (int i = 1; i < nb - 1; ++i) s[i] = (h[i - 1] + 6.0 * h[i] + h[i + 1]) / 8.0;
+    s[nb - 1] = (h[nb - 2] + 7.0 * h[nb - 1]) / 8.0;
+    double sum = 0.0;
+    for (int i = 0; i < nb; ++i) sum += s[i];
+    double wsum = 0.0;
+    for (int i = 0; i < nb; ++i) {
+        const double r = s[i] / sum;
+        w[i] = (r > 0.0 && r < 1.0) ? pow((r - 1.0) / log(r), alpha) : (r >= 1.0 ? 1.0 : 0.0);
+        wsum += w[i];
+    }
+    const double delta = wsum / (double)nb;
+    ne[0] = 0.0; ne[nb] = 1.0;
+    double acc = 0.0;
+    int j = 0;
+    for (int k = 1; k < nb; ++k) {
+        const double target = (double)k * delta;
+        while (j < nb - 1 && acc + w[j] < target) { acc += w[j]; ++j; }
+        double frac = w[j] > 0.0 ? (target - acc) / w[j] : 0.0;
+        frac = frac > 1.0 ? 1.0 : frac;
+        ne[k] = e[j] + frac * (e[j + 1] - e[j]);
+    }
+    for (int k = 0; k <= nb; ++k) e[k] = ne[k];
+}
+
+}  // namespace mf
+
+namespace {
+
+constexpr int MAX_ITER = 1000;
+constexpr double PI = 3.14159265358979323846;
+
+const ProcOps* proc_ops(int p)
+{
+    switch (p) {
+    case MF_EE_MUMU: return ops_ee_mumu();
+    case MF_GG_TT: return ops_gg_tt();
+    case MF_GG_TTG: return ops_gg_ttg();
+    case MF_GG_TTGG: return ops_gg_ttgg();
+    default: return nullptr;
+    }
+}
+
+int fail(mf_ctx* c, int code, const std::string& msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+#define MF_CUDA(ctx, call)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess)                                                               \
+            return fail(ctx, MF_ERR_CUDA, std::string(#call ": ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+double factorial(int n)
+{
+    double f = 1.0;
+    for (int i = 2; i <= n; ++i) f *= i;
+    return f;
+}
+
+// fills the process-independent and process-dependent kernel parameters
+int make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KParams& kp)
+{
+    const mf_config& g = c->cfg;
+    std::memset(&kp, 0, sizeof(kp));
+    kp.sqrt_s = sqrt_s;
+    kp.S = sqrt_s * sqrt_s;
+    kp.mt = g.mt;
+    kp.gs = std::sqrt(4.0 * PI * g.alpha_s);
+    const int nf = ops->NEXT - 2;
+    // massless n-body volume without its shat^(n-2): (2 pi)^(4-3n) (pi/2)^(n-1) / ((n-1)! (n-2)!)
+    kp.vol_const = std::pow(2.0 * PI, 4.0 - 3.0 * nf) * std::pow(PI / 2.0, nf - 1) / (factorial(nf - 1) * factorial(nf - 2));
+    if (process != MF_EE_MUMU) {
+        const double tau0 = 4.0 * g.mt * g.mt / kp.S;
+        if (!(tau0 > 0.0 && tau0 < 1.0)) return fail(c, MF_ERR_ARG, "sqrt_s below the t tbar threshold");
+        kp.ln_tau0 = std::log(tau0);
+    }
+    kp.pt_min2 = g.pt_min > 0.0 ? g.pt_min * g.pt_min : 0.0;
+    kp.sinh_eta = g.eta_max > 0.0 ? std::sinh(g.eta_max) : 0.0;
+    kp.dr_min2 = g.dr_min > 0.0 ? g.dr_min * g.dr_min : 0.0;
+    {
+        const double a = 1.0 / g.alpha_em_inv, mz2 = g.mz * g.mz;
+        const double mw2 = 0.5 * mz2 + std::sqrt(0.25 * mz2 * mz2 - PI * a * mz2 / (std::sqrt(2.0) * g.gf));
+        kp.ew.sw2 = 1.0 - mw2 / mz2;
+        kp.ew.cw2 = 1.0 - kp.ew.sw2;
+        kp.ew.e2 = 4.0 * PI * a;
+        kp.ew.mz = g.mz;
+        kp.ew.wz = g.wz;
+    }
+    kp.key = make_uint2((uint32_t)g.seed, (uint32_t)(g.seed >> 32));
+    kp.channel = g.channel;
+    kp.nb = g.n_bins;
+    kp.pdfg.nx = c->nx;
+    kp.pdfg.nq = c->nq;
+    kp.pdfg.lx0 = std::log(c->x_min);
+    kp.pdfg.hx = (0.0 - kp.pdfg.lx0) / (double)(c->nx - 1);
+    kp.pdfg.lq0 = std::log(c->q2_min);
+    kp.pdfg.lq1 = std::log(c->q2_max);
+    kp.pdfg.hq = (kp.pdfg.lq1 - kp.pdfg.lq0) / (double)(c->nq - 1);
+    kp.pdf = c->d_pdf;
+    kp.partials = c->d_partials;
+    kp.counters = c->d_counters;
+    return MF_OK;
+}
+
+int pick_blocks(mf_ctx* c, const ProcOps* ops, size_t sm, int prec, int* nblk)
+{
+    int per_sm = 0;
+    MF_CUDA(c, ops->occupancy(prec, sm, &per_sm));
+    if (per_sm < 1) return fail(c, MF_ERR_CUDA, "integrand kernel does not fit on an SM");
+    int n = per_sm * c->n_sm;
+    if (n > c->max_blocks) n = c->max_blocks;
+    *nblk = n;
+    return MF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mf_default_config(mf_config* cfg)
+{
+    if (!cfg) return MF_ERR_ARG;
+    cfg->mt = 173.0;
+    cfg->alpha_s = 0.118;
+    cfg->mz = 91.188;
+    cfg->wz = 2.441404;
+    cfg->alpha_em_inv = 132.507;
+    cfg->gf = 1.16639e-5;
+    cfg->pt_min = 30.0;
+    cfg->eta_max = 2.5;
+    cfg->dr_min = 0.4;
+    cfg->seed = 0;
+    cfg->channel = 0;
+    cfg->n_bins = 50;
+    cfg->alpha = 1.5;
+    cfg->precision = MF_MIXED;
+    return MF_OK;
+}
+
+int mf_process_info(int process, int* n_ext, int* dim)
+{
+    const ProcOps* o = proc_ops(process);
+    if (!o) return (process == MF_UU_TT || process == MF_UG_TTU) ? MF_ERR_UNSUPPORTED : MF_ERR_ARG;
+    if (n_ext) *n_ext = o->NEXT;
+    if (dim) *dim = o->D;
+    return MF_OK;
+}
+
+int mf_create(mf_ctx** out, const mf_config* cfg, const double* pdf_grid_host, int n_flav, int nx, int nq,
+              double x_min, double q2_min, double q2_max, void* stream)
+{
+    if (!out || !cfg || !pdf_grid_host) return MF_ERR_ARG;
+    *out = nullptr;
+    if (n_flav < 1 || n_flav > 3 || nx < 4 || nq < 4 || nx * nq > 8192) return MF_ERR_ARG;
+    if (!(x_min > 0.0 && x_min < 1.0 && q2_min > 0.0 && q2_max > q2_min)) return MF_ERR_ARG;
+    if (cfg->n_bins < 2 || cfg->n_bins > MAX_BINS || cfg->channel >= (1u << 24)) return MF_ERR_ARG;
+    if (cfg->precision != MF_FP64 && cfg->precision != MF_MIXED) return MF_ERR_ARG;
+    mf_ctx* c = new (std::nothrow) mf_ctx;
+    if (!c) return MF_ERR_ARG;
+    c->cfg = *cfg;
+    c->stream = (cudaStream_t)stream;
+    c->n_flav = n_flav; c->nx = nx; c->nq = nq;
+    c->x_min = x_min; c->q2_min = q2_min; c->q2_max = q2_max;
+    auto bail = [&](int code) { mf_destroy(c); return code; };
+    if (cudaGetDevice(&c->device) != cudaSuccess) return bail(MF_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) return bail(MF_ERR_CUDA);
+    c->max_blocks = c->n_sm * 32;
+    const size_t npdf = (size_t)n_flav * nx * nq;
+    const size_t ncol = 2 + (size_t)MAX_DIM * MAX_BINS;
+    if (cudaMalloc(&c->d_pdf, npdf * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_grid, (size_t)MAX_DIM * (MAX_BINS + 1) * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_partials, (size_t)c->max_blocks * ncol * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_iter, (size_t)MAX_ITER * 2 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_sums, ncol * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_counters, 2 * sizeof(unsigned long long)) != cudaSuccess)
+        return bail(MF_ERR_CUDA);
+    if (cudaMemcpy(c->d_pdf, pdf_grid_host, npdf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
+        return bail(MF_ERR_CUDA);
+    for (int p : { MF_EE_MUMU, MF_GG_TT, MF_GG_TTG, MF_GG_TTGG }) {
+        const ProcOps* o = proc_ops(p);
+        if (o->prepare(o->smem(MAX_BINS, nx * nq)) != cudaSuccess) return bail(MF_ERR_CUDA);
+    }
+    *out = c;
+    return MF_OK;
+}
+
+void mf_destroy(mf_ctx* c)
+{
+    if (!c) return;
+    cudaFree(c->d_pdf);
+    cudaFree(c->d_grid);
+    cudaFree(c->d_partials);
+    cudaFree(c->d_iter);
+    cudaFree(c->d_sums);
+    cudaFree(c->d_counters);
+    delete c;
+}
+
+const char* mf_last_error(const mf_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int mf_set_precision(mf_ctx* c, int precision)
+{
+    if (!c || (precision != MF_FP64 && precision != MF_MIXED)) return MF_ERR_ARG;
+    c->cfg.precision = precision;
+    return MF_OK;
+}
+
+int mf_set_pdf(mf_ctx* c, const double* pdf_grid_host)
+{
+    if (!c || !pdf_grid_host) return MF_ERR_ARG;
+    MF_CUDA(c, cudaMemcpyAsync(c->d_pdf, pdf_grid_host, (size_t)c->n_flav * c->nx * c->nq * sizeof(double),
+                               cudaMemcpyHostToDevice, c->stream));
+    return MF_OK;
+}
+
+int mf_vegas_pass(mf_ctx* c, int process, double sqrt_s, const double* grid_dev, long long n_events,
+                  long long ev_offset, unsigned int iteration, const unsigned char* mask_in_dev, double* sums_dev,
+                  const mf_event_arrays* ev)
+{
+    if (!c) return MF_ERR_ARG;
+    const ProcOps* ops = proc_ops(process);
+    if (!ops) return fail(c, MF_ERR_UNSUPPORTED, "process not built");
+    if (!grid_dev || !sums_dev || n_events < 1 || ev_offset < 0 || !(sqrt_s > 0.0))
+        return fail(c, MF_ERR_ARG, "mf_vegas_pass: bad argument");
+    KParams kp;
+    int rc = make_params(c, process, ops, sqrt_s, kp);
+    if (rc) return rc;
+    kp.iteration = iteration;
+    kp.n_events = n_events;
+    kp.ev_offset = ev_offset;
+    kp.inv_n = 1.0 / (double)n_events;
+    kp.grid = grid_dev;
+    kp.mask_in = mask_in_dev;
+    const bool write = ev != nullptr;
+    if (ev) {
+        kp.ev_u = ev->u; kp.ev_x = ev->x; kp.ev_bins = ev->bins; kp.ev_w = ev->w;
+        kp.ev_mask = ev->mask; kp.ev_me2 = ev->me2; kp.ev_p = ev->momenta;
+    }
+    const size_t sm = ops->smem(c->cfg.n_bins, c->nx * c->nq);
+    int nblk = 0;
+    rc = pick_blocks(c, ops, sm, c->cfg.precision, &nblk);
+    if (rc) return rc;
+    MF_CUDA(c, cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), c->stream));
+    MF_CUDA(c, ops->integrand(c->cfg.precision, write, kp, nblk, sm, c->stream));
+    const int ncol = 2 + ops->D * c->cfg.n_bins;
+    finish_pass_kernel<<<1, 1024, ncol * sizeof(double), c->stream>>>(c->d_partials, nblk, ops->D, c->cfg.n_bins,
+                                                                     n_events, c->cfg.alpha, 0, nullptr, nullptr,
+                                                                     sums_dev);
+    MF_CUDA(c, cudaGetLastError());
+    return MF_OK;
+}
+
+int mf_integrate(mf_ctx* c, int process, double sqrt_s, long long n_events, int n_iter, mf_result* out,
+                 double* iter_host, double* grid_host)
+{
+    if (!c) return MF_ERR_ARG;
+    const ProcOps* ops = proc_ops(process);
+    if (!ops) return fail(c, MF_ERR_UNSUPPORTED, "process not built");
+    if (!out || n_events < 2 || n_iter < 1 || n_iter > MAX_ITER || !(sqrt_s > 0.0))
+        return fail(c, MF_ERR_ARG, "mf_integrate: bad argument");
+    KParams kp;
+    int rc = make_params(c, process, ops, sqrt_s, kp);
+    if (rc) return rc;
+    const int D = ops->D, nb = c->cfg.n_bins;
+    kp.n_events = n_events;
+    kp.ev_offset = 0;
+    kp.inv_n = 1.0 / (double)n_events;
+    kp.grid = c->d_grid;
+    const size_t sm = ops->smem(nb, c->nx * c->nq);
+    int nblk = 0;
+    rc = pick_blocks(c, ops, sm, c->cfg.precision, &nblk);
+    if (rc) return rc;
+    std::vector<double> g0((size_t)D * (nb + 1));
+    for (int d = 0; d < D; ++d)
+        for (int i = 0; i <= nb; ++i) g0[(size_t)d * (nb + 1) + i] = (double)i / (double)nb;
+    MF_CUDA(c, cudaMemcpyAsync(c->d_grid, g0.data(), g0.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    MF_CUDA(c, cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), c->stream));
+    const int ncol = 2 + D * nb;
+    for (int it = 0; it < n_iter; ++it) {
+        kp.iteration = (uint32_t)it;
+        MF_CUDA(c, ops->integrand(c->cfg.precision, false, kp, nblk, sm, c->stream));
+        finish_pass_kernel<<<1, 1024, ncol * sizeof(double), c->stream>>>(
+            c->d_partials, nblk, D, nb, n_events, c->cfg.alpha, it < n_iter - 1, c->d_grid, c->d_iter + 2 * it, nullptr);
+        MF_CUDA(c, cudaGetLastError());
+    }
+    std::vector<double> iters((size_t)2 * n_iter);
+    unsigned long long cnt[2];
+    MF_CUDA(c, cudaMemcpyAsync(iters.data(), c->d_iter, iters.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    MF_CUDA(c, cudaMemcpyAsync(cnt, c->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+    if (grid_host)
+        MF_CUDA(c, cudaMemcpyAsync(grid_host, c->d_grid, (size_t)D * (nb + 1) * sizeof(double), cudaMemcpyDeviceToHost,
+                                   c->stream));
+    MF_CUDA(c, cudaStreamSynchronize(c->stream));
+    double sw = 0.0, swi = 0.0;
+    for (int k = 0; k < n_iter; ++k) {
+        const double wk = 1.0 / iters[2 * k + 1];
+        sw += wk;
+        swi += wk * iters[2 * k];
+    }
+    const double mean = swi / sw;
+    double chi2 = 0.0;
+    for (int k = 0; k < n_iter; ++k) chi2 += (iters[2 * k] - mean) * (iters[2 * k] - mean) / iters[2 * k + 1];
+    out->sigma_pb = mean;
+    out->error_pb = std::sqrt(1.0 / sw);
+    out->chi2_dof = n_iter > 1 ? chi2 / (n_iter - 1) : 0.0;
+    out->n_events_total = n_events * (long long)n_iter;
+    out->n_pass = (long long)cnt[0];
+    out->n_nan = (long long)cnt[1];
+    out->n_iter = n_iter;
+    if (iter_host) std::memcpy(iter_host, iters.data(), iters.size() * sizeof(double));
+    if (cnt[1] > (unsigned long long)(n_events * (long long)n_iter) / 1000)
+        return fail(c, MF_ERR_NUMERIC, "more than 0.1% of the event weights were not finite");
+    return MF_OK;
+}
+
+int mf_evaluate(mf_ctx* c, int process, const double* momenta_dev, long long n, double* me2_dev)
+{
+    if (!c) return MF_ERR_ARG;
+    const ProcOps* ops = proc_ops(process);
+    if (!ops) return fail(c, MF_ERR_UNSUPPORTED, "process not built");
+    if (n == 0) return MF_OK;
+    if (!momenta_dev || !me2_dev || n < 0) return fail(c, MF_ERR_ARG, "mf_evaluate: bad argument");
+    KParams kp;
+    int rc = make_params(c, process, ops, 1.0e4, kp);
+    if (rc) return rc;
+    long long nb = (n + 127) / 128;
+    const long long cap = (long long)c->n_sm * 16;
+    const int nblk = (int)(nb < cap ? nb : cap);
+    MF_CUDA(c, ops->evaluate(c->cfg.precision, momenta_dev, n, me2_dev, kp.mt, kp.gs, kp.ew, nblk, c->stream));
+    return MF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,211 @@
+// Device building blocks of the per-event integrand of arXiv:2105.10529
+// (Sec. 2.1: random numbers -> phase-space kinematics -> matrix element ->
+// histogram accumulation; Sec. 1: VEGAS integrator, PDF interpolation,
+// phase-space generator with fiducial cuts).
+//
+// Bit-exactness contract with the reference implementation: the random
+// stream, the VEGAS bin indices and mapped points are integer or correctly
+// rounded single operations written with explicit *_rn intrinsics, so no
+// contraction or reassociation can change them.
+#pragma once
+#include <cstdint>
+
+namespace mf {
+
+// ------------------------------------------------------------------ a1: Philox4x32-10
+// Salmon, Moraes, Dror, Shaw, SC'11: ten rounds of the 4x32 Philox S-box,
+// key bumped by the golden-ratio Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint2 k)
+{
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        const uint32_t hi0 = __umulhi(0xD2511F53u, c.x), lo0 = 0xD2511F53u * c.x;
+        const uint32_t hi1 = __umulhi(0xCD9E8D57u, c.z), lo1 = 0xCD9E8D57u * c.z;
+        uint4 n;
+        n.x = hi1 ^ c.y ^ k.x;
+        n.y = lo1;
+        n.z = hi0 ^ c.w ^ k.y;
+        n.w = lo0;
+        c = n;
+        k.x += 0x9E3779B9u;
+        k.y += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// Two words -> double in (0,1): 52-bit integer from the top 26 bits of each
+// word, u = (k + 1/2) 2^-52 (exact).
+__device__ __forceinline__ double u01_from(uint32_t a, uint32_t b)
+{
+    const unsigned long long k = ((unsigned long long)(a >> 6) << 26) | (unsigned long long)(b >> 6);
+    return __dmul_rn(__dadd_rn(__ull2double_rn(k), 0.5), 2.220446049250313080847e-16);
+}
+
+// Uniforms of one event: block b of the counter (event lo, event hi,
+// iteration, channel<<8 | b) under key (seed lo, seed hi) gives dims 2b, 2b+1.
+template <int D>
+__device__ __forceinline__ void event_uniforms(unsigned long long ev, uint32_t iteration, uint32_t channel,
+                                               uint2 key, double (&u)[D])
+{
+#pragma unroll
+    for (int b = 0; 2 * b < D; ++b) {
+        const uint4 c = make_uint4((uint32_t)ev, (uint32_t)(ev >> 32), iteration, (channel << 8) | (uint32_t)b);
+        const uint4 o = philox4x32_10(c, key);
+        u[2 * b] = u01_from(o.x, o.y);
+        if (2 * b + 1 < D) u[2 * b + 1] = u01_from(o.z, o.w);
+    }
+}
+
+// ------------------------------------------------------------------ a2: VEGAS map
+// bin = floor(nb u) (clamped), x = e_b + w (nb u - b), J *= nb w (Lepage 1978).
+// grid: [d][nb+1] edges in shared memory.
+template <int D>
+__device__ __forceinline__ double vegas_map(const double* grid, int nb, const double (&u)[D], double (&x)[D],
+                                            uint8_t (&bins)[D])
+{
+    double jac = 1.0;
+    const double nbd = (double)nb;
+#pragma unroll
+    for (int d = 0; d < D; ++d) {
+        const double y = __dmul_rn(u[d], nbd);
+        int b = __double2int_rz(y);
+        b = b > nb - 1 ? nb - 1 : b;
+        const double frac = __dsub_rn(y, (double)b);
+        const double* e = grid + d * (nb + 1);
+        const double lo = e[b], hi = e[b + 1];
+        const double width = __dsub_rn(hi, lo);
+        x[d] = __fma_rn(width, frac, lo);
+        jac = __dmul_rn(jac, __dmul_rn(nbd, width));
+        bins[d] = (uint8_t)b;
+    }
+    return jac;
+}
+
+// ------------------------------------------------------------------ a3: parton map
+// tau = tau0^x0, x1 = tau^v, x2 = tau^(1-v), J = tau |ln tau| |ln tau0|.
+__device__ __forceinline__ void parton_map(double x0, double v, double ln_tau0, double& x1, double& x2, double& jac)
+{
+    const double lt = x0 * ln_tau0;
+    const double tau = exp(lt);
+    x1 = exp(v * lt);
+    x2 = exp((1.0 - v) * lt);
+    jac = tau * (-lt) * (-ln_tau0);
+}
+
+// ------------------------------------------------------------------ a4: RAMBO
+// Kleiss, Stirling, Ellis, CPC 40 (1986) 359: N isotropic massless momenta
+// from 4N uniforms, conformal boost + scale to (sqrt(shat), 0), massive
+// rescaling xi by Newton's method (bounded iterations) and the massive
+// weight factor.  Returns the phase-space weight; p gets (E,px,py,pz).
+template <int N>
+__device__ __forceinline__ double rambo(double rs, const double (&m)[N], const double* u, double (&p)[N][4],
+                                        double vol_massless)
+{
+    double Q0 = 0.0, Q1 = 0.0, Q2 = 0.0, Q3 = 0.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const double c = 2.0 * u[4 * i] - 1.0;
+        const double s = sqrt(1.0 - c * c);
+        double sf, cf;
+        sincospi(2.0 * u[4 * i + 1], &sf, &cf);
+        const double e = -log(u[4 * i + 2] * u[4 * i + 3]);
+        p[i][0] = e;
+        p[i][1] = e * s * cf;
+        p[i][2] = e * s * sf;
+        p[i][3] = e * c;
+        Q0 += p[i][0]; Q1 += p[i][1]; Q2 += p[i][2]; Q3 += p[i][3];
+    }
+    const double M = sqrt(Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3);
+    const double b1 = -Q1 / M, b2 = -Q2 / M, b3 = -Q3 / M;
+    const double x = rs / M, g = Q0 / M, a = 1.0 / (1.0 + g);
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const double bq = b1 * p[i][1] + b2 * p[i][2] + b3 * p[i][3];
+        const double q0 = p[i][0];
+        p[i][0] = x * (g * q0 + bq);
+        p[i][1] = x * (p[i][1] + b1 * q0 + a * bq * b1);
+        p[i][2] = x * (p[i][2] + b2 * q0 + a * bq * b2);
+        p[i][3] = x * (p[i][3] + b3 * q0 + a * bq * b3);
+    }
+    double msum = 0.0;
+    bool massive = false;
+#pragma unroll
+    for (int i = 0; i < N; ++i) { msum += m[i]; massive |= (m[i] != 0.0); }
+    if (!massive) return vol_massless;
+    if (msum >= rs) return 0.0;
+    double xi = sqrt(1.0 - (msum / rs) * (msum / rs));
+    double e2[N];
+#pragma unroll
+    for (int i = 0; i < N; ++i) e2[i] = p[i][0] * p[i][0];
+    for (int it = 0; it < 100; ++it) {
+        double f = -rs, fp = 0.0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const double ei = sqrt(m[i] * m[i] + xi * xi * e2[i]);
+            f += ei;
+            fp += xi * e2[i] / ei;
+        }
+        xi -= f / fp;
+        if (fabs(f) < 1e-15 * rs) break;
+    }
+    double sk = 0.0, sk2e = 0.0, prod = 1.0;
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const double ka = xi * p[i][0];
+        const double e = sqrt(m[i] * m[i] + ka * ka);
+        p[i][1] *= xi; p[i][2] *= xi; p[i][3] *= xi;
+        p[i][0] = e;
+        sk += ka;
+        sk2e += ka * ka / e;
+        prod *= ka / e;
+    }
+    double pw = 1.0;
+    const double r = sk / rs;
+#pragma unroll
+    for (int i = 0; i < 2 * N - 3; ++i) pw *= r;
+    return vol_massless * pw * prod * rs / sk2e;
+}
+
+// ------------------------------------------------------------------ a7: log-bicubic PDF
+// Cubic Hermite in ln x along the Q^2 rows j-1..j+2, then in ln Q^2 over those
+// row values; node derivatives are central differences inside, one-sided at
+// the ends (LHAPDF6 log-bicubic, EPJC 75 (2015) 132).  g: [ix][iq] x f values.
+struct PdfGeom { int nx, nq; double lx0, hx, lq0, lq1, hq; };
+
+__device__ __forceinline__ double hermite3(double f0, double f1, double d0, double d1, double h, double t)
+{
+    const double t2 = t * t, t3 = t2 * t;
+    return (2.0 * t3 - 3.0 * t2 + 1.0) * f0 + (t3 - 2.0 * t2 + t) * h * d0 + (-2.0 * t3 + 3.0 * t2) * f1
+           + (t3 - t2) * h * d1;
+}
+
+__device__ __forceinline__ double pdf_row(const double* g, const PdfGeom& G, int i, int jr, double t)
+{
+    const int nq = G.nq, nx = G.nx;
+    const double f0 = g[i * nq + jr], f1 = g[(i + 1) * nq + jr];
+    const double d0 = i == 0 ? (f1 - f0) / G.hx : (f1 - g[(i - 1) * nq + jr]) / (2.0 * G.hx);
+    const double d1 = (i + 1 == nx - 1) ? (f1 - f0) / G.hx : (g[(i + 2) * nq + jr] - f0) / (2.0 * G.hx);
+    return hermite3(f0, f1, d0, d1, G.hx, t);
+}
+
+__device__ __forceinline__ double pdf_xf(const double* g, const PdfGeom& G, double x, double q2)
+{
+    const double lx = log(x);
+    double lq = log(q2);
+    lq = lq < G.lq0 ? G.lq0 : (lq > G.lq1 ? G.lq1 : lq);
+    int i = (int)floor((lx - G.lx0) / G.hx);
+    i = i < 0 ? 0 : (i > G.nx - 2 ? G.nx - 2 : i);
+    int j = (int)floor((lq - G.lq0) / G.hq);
+    j = j < 0 ? 0 : (j > G.nq - 2 ? G.nq - 2 : j);
+    const double t = (lx - (G.lx0 + i * G.hx)) / G.hx;
+    const double s = (lq - (G.lq0 + j * G.hq)) / G.hq;
+    const double r1 = pdf_row(g, G, i, j, t);
+    const double r2 = pdf_row(g, G, i, j + 1, t);
+    const double r0 = j > 0 ? pdf_row(g, G, i, j - 1, t) : 0.0;
+    const double r3 = (j + 2 < G.nq) ? pdf_row(g, G, i, j + 2, t) : 0.0;
+    const double dj = j == 0 ? (r2 - r1) / G.hq : (r2 - r0) / (2.0 * G.hq);
+    const double dj1 = (j + 1 == G.nq - 1) ? (r2 - r1) / G.hq : (r3 - r1) / (2.0 * G.hq);
+    return hermite3(r1, r2, dj, dj1, G.hq, s);
+}
+
+}  // namespace mf

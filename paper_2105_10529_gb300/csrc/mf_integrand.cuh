@@ -1,0 +1,367 @@
+// Fused per-event integrand, VEGAS pass reduction/refinement and the
+// matrix-element evaluation kernel (Sec. 2.1 of arXiv:2105.10529: the
+// event pipeline from random numbers through kinematics and matrix element
+// to histogram filling, all resident on the GPU, Sec. 3.1).
+//
+// One thread evaluates one event at a time (grid-stride over the pass).  All
+// per-event state (uniforms, momenta, wavefunctions) lives in registers; the
+// only HBM traffic is the per-CTA partial sums at the end of the kernel.
+// Reductions are deterministic: fixed warp-shuffle trees, per-warp shared
+// histograms updated by one leader lane per distinct bin in lane order,
+// warps combined in index order, CTAs combined in index order.
+#pragma once
+#include <cstdint>
+#include "mf_device.cuh"
+#include "mf_helas.cuh"
+
+namespace mf {
+
+constexpr double GEV2_TO_PB = 0.3893793721e9;   // (hbar c)^2 in pb GeV^2
+constexpr int MAX_DIM = 18;
+constexpr int MAX_BINS = 64;
+
+struct EwParams { double e2, sw2, cw2, mz, wz; };
+
+struct KParams {
+    double sqrt_s, S, ln_tau0, mt, gs, vol_const;   // vol_const * shat^(n-2) = massless n-body volume
+    double pt_min2, sinh_eta, dr_min2;              // <= 0 disables
+    EwParams ew;
+    uint2 key;
+    uint32_t channel, iteration;
+    int nb;
+    long long n_events, ev_offset;
+    double inv_n;
+    PdfGeom pdfg;
+    const double* grid;     // [D][nb+1]
+    const double* pdf;      // [3][nx][nq]
+    double* partials;       // [gridDim.x][2 + D nb]
+    unsigned long long* counters;   // [0] events passing cuts, [1] non-finite weights zeroed
+    const uint8_t* mask_in; // frozen cut masks (nullable)
+    // per-event outputs (nullable; only the inspection kernel writes them)
+    double* ev_u; double* ev_x; uint8_t* ev_bins; double* ev_w; uint8_t* ev_mask; double* ev_me2; double* ev_p;
+};
+
+// ------------------------------------------------------------------ e+ e- -> mu+ mu-
+
+// Photon and Z exchange between chirality-split currents (massless
+// fermions): M = -i e^2 sum_ij A_ij(s)/s J^e_i . J^mu_j with
+// A_ij = Q_e Q_mu + g_i g_j s / (sW^2 cW^2 (s - MZ^2 + i MZ GZ)).
+struct MeEeMumu {
+    static constexpr int NEXT = 4, NHEL = 16;
+    template <typename R>
+    __device__ static double me2(const double (&p)[4][4], const EwParams& ew)
+    {
+        const double s = 2.0 * mdot(p[0], p[1]);
+        const double gL = -0.5 + ew.sw2, gR = ew.sw2;     // T3 - Q sW^2, -Q sW^2 with Q = -1
+        const double dre = s - ew.mz * ew.mz, dim = ew.mz * ew.wz;
+        const double dd = dre * dre + dim * dim;
+        const double chr = s * dre / dd / (ew.sw2 * ew.cw2), chi = -s * dim / dd / (ew.sw2 * ew.cw2);
+        const double g[2] = { gL, gR };
+        cx<R> A[2][2];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j)
+                A[i][j] = mkc(R(ew.e2 / s * (1.0 + g[i] * g[j] * chr)), R(ew.e2 / s * g[i] * g[j] * chi));
+        const FermionBasis<R> f1 = fermion_basis<R>(p[0], 0.0), f2 = fermion_basis<R>(p[1], 0.0);
+        const FermionBasis<R> f3 = fermion_basis<R>(p[2], 0.0), f4 = fermion_basis<R>(p[3], 0.0);
+        R acc = R(0);
+#pragma unroll 1
+        for (int ih = 0; ih < NHEL; ++ih) {
+            const int h1 = (ih & 1) ? 1 : -1, h2 = (ih & 2) ? 1 : -1, h3 = (ih & 4) ? 1 : -1, h4 = (ih & 8) ? 1 : -1;
+            W4<R> eL, eR, mL, mR;
+            ffv_cur_lr(ext_vbar(f2, h2), ext_u(f1, h1), eL, eR);
+            ffv_cur_lr(ext_ubar(f3, h3), ext_v(f4, h4), mL, mR);
+            cx<R> amp = cmul(A[0][0], cdot(eL, mL));
+            amp = cfma(A[0][1], cdot(eL, mR), amp);
+            amp = cfma(A[1][0], cdot(eR, mL), amp);
+            amp = cfma(A[1][1], cdot(eR, mR), amp);
+            acc += amp.r * amp.r + amp.i * amp.i;
+        }
+        return 0.25 * double(acc);
+    }
+};
+
+// ------------------------------------------------------------------ process traits
+
+struct ProcEe {
+    static constexpr int NEXT = 4, NF = 2, D = 2, NPDF = 0;
+};
+
+template <class ME>
+struct ProcTops {
+    using Me = ME;
+    static constexpr int NEXT = ME::NEXT;
+    static constexpr int NF = NEXT - 2;        // t, tbar, light partons
+    static constexpr int D = 2 + 4 * NF;
+    static constexpr int NLIGHT = NF - 2;
+    static constexpr int NPDF = 1;             // gluon grid only
+};
+
+// per-event result
+template <int D>
+struct EventOut {
+    double u[D], x[D];
+    uint8_t bins[D];
+    double w, me2;
+    int mask;
+};
+
+// ------------------------------------------------------------------ one event
+
+template <typename R>
+__device__ __forceinline__ void event_ee(const KParams& kp, const double* sgrid, unsigned long long ev,
+                                         EventOut<2>& o, double (&p)[4][4])
+{
+    event_uniforms<2>(ev, kp.iteration, kp.channel, kp.key, o.u);
+    const double jv = vegas_map<2>(sgrid, kp.nb, o.u, o.x, o.bins);
+    const double E = 0.5 * kp.sqrt_s;
+    const double c = 2.0 * o.x[0] - 1.0, sn = sqrt(1.0 - c * c);
+    double sf, cf;
+    sincospi(2.0 * o.x[1], &sf, &cf);
+    const double pp[4][4] = { { E, 0, 0, E }, { E, 0, 0, -E }, { E, E * sn * cf, E * sn * sf, E * c },
+                              { E, -E * sn * cf, -E * sn * sf, -E * c } };
+    for (int i = 0; i < 4; ++i)
+        for (int m = 0; m < 4; ++m) p[i][m] = pp[i][m];
+    o.mask = kp.mask_in ? kp.mask_in[ev - kp.ev_offset] : 1;
+    o.me2 = o.mask ? MeEeMumu::me2<R>(p, kp.ew) : 0.0;
+    const double s = kp.S;
+    o.w = o.mask ? o.me2 / (2.0 * s) * (1.0 / (8.0 * 3.14159265358979323846)) * jv * GEV2_TO_PB : 0.0;
+}
+
+// light-parton cuts in the lab frame: pT > pt_min, |pz| < pT sinh(eta_max),
+// and Delta R between the two final gluons
+template <class P>
+__device__ __forceinline__ int cuts_tops(const KParams& kp, const double (&pl)[P::NEXT][4])
+{
+    int ok = 1;
+#pragma unroll
+    for (int j = 0; j < P::NLIGHT; ++j) {
+        const double* q = pl[4 + j];
+        const double pt2 = q[1] * q[1] + q[2] * q[2];
+        if (kp.pt_min2 > 0.0) ok &= (pt2 > kp.pt_min2);
+        if (kp.sinh_eta > 0.0) ok &= (fabs(q[3]) < sqrt(pt2) * kp.sinh_eta);
+    }
+    if (P::NLIGHT == 2 && kp.dr_min2 > 0.0 && ok) {
+        const double* a = pl[4];
+        const double* b = pl[P::NLIGHT == 2 ? 5 : 4];
+        const double pta = sqrt(a[1] * a[1] + a[2] * a[2]), ptb = sqrt(b[1] * b[1] + b[2] * b[2]);
+        const double ea = asinh(a[3] / pta), eb = asinh(b[3] / ptb);
+        double dphi = atan2(a[2], a[1]) - atan2(b[2], b[1]);
+        const double pi = 3.14159265358979323846;
+        if (dphi > pi) dphi -= 2.0 * pi;
+        if (dphi < -pi) dphi += 2.0 * pi;
+        ok &= ((ea - eb) * (ea - eb) + dphi * dphi > kp.dr_min2);
+    }
+    return ok;
+}
+
+template <class P, typename R>
+__device__ __forceinline__ void event_tops(const KParams& kp, const double* sgrid, const double* spdf,
+                                           unsigned long long ev, EventOut<P::D>& o, double (&p)[P::NEXT][4])
+{
+    constexpr int NF = P::NF, D = P::D;
+    event_uniforms<D>(ev, kp.iteration, kp.channel, kp.key, o.u);
+    const double jv = vegas_map<D>(sgrid, kp.nb, o.u, o.x, o.bins);
+    double x1, x2, jp;
+    parton_map(o.x[0], o.x[1], kp.ln_tau0, x1, x2, jp);
+    const double shat = x1 * x2 * kp.S;
+    const double rs = sqrt(shat);
+    double m[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) m[i] = i < 2 ? kp.mt : 0.0;
+    double pf[NF][4];
+    double vol = kp.vol_const;
+#pragma unroll
+    for (int i = 0; i < NF - 2; ++i) vol *= shat;
+    const double wps = rambo<NF>(rs, m, o.x + 2, pf, vol);
+    const double h = 0.5 * rs;
+    p[0][0] = h; p[0][1] = 0.0; p[0][2] = 0.0; p[0][3] = h;
+    p[1][0] = h; p[1][1] = 0.0; p[1][2] = 0.0; p[1][3] = -h;
+#pragma unroll
+    for (int i = 0; i < NF; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) p[2 + i][c] = pf[i][c];
+    // longitudinal boost to the lab frame, rapidity ln(x1/x2)/2
+    const double sq = sqrt(x1 * x2);
+    const double ch = (x1 + x2) / (2.0 * sq), sh = (x1 - x2) / (2.0 * sq);
+    double pl[P::NEXT][4];
+#pragma unroll
+    for (int i = 0; i < P::NEXT; ++i) {
+        pl[i][0] = ch * p[i][0] + sh * p[i][3];
+        pl[i][1] = p[i][1];
+        pl[i][2] = p[i][2];
+        pl[i][3] = ch * p[i][3] + sh * p[i][0];
+    }
+    o.mask = kp.mask_in ? (int)kp.mask_in[ev - kp.ev_offset] : cuts_tops<P>(kp, pl);
+    if (wps <= 0.0) o.mask = 0;
+    // factorisation scale: m_t for 2 -> 2, H_T / 2 otherwise
+    double muf2;
+    if (NF == 2) {
+        muf2 = kp.mt * kp.mt;
+    } else {
+        double ht = 0.0;
+#pragma unroll
+        for (int i = 2; i < P::NEXT; ++i) {
+            const double mi = (i < 4) ? kp.mt : 0.0;
+            ht += sqrt(mi * mi + p[i][1] * p[i][1] + p[i][2] * p[i][2]);
+        }
+        muf2 = 0.25 * ht * ht;
+    }
+    const double f1 = pdf_xf(spdf, kp.pdfg, x1, muf2) / x1;
+    const double f2 = pdf_xf(spdf, kp.pdfg, x2, muf2) / x2;
+    o.me2 = 0.0;
+    o.w = 0.0;
+    // matrix element only for events that pass; the warp skips it when no lane needs it
+    if (__any_sync(__activemask(), o.mask)) {
+        if (o.mask) o.me2 = P::Me::template me2<R>(p, kp.mt, kp.gs);
+    }
+    if (o.mask) o.w = f1 * f2 * o.me2 / (2.0 * shat) * wps * jp * jv * GEV2_TO_PB;
+}
+
+// ------------------------------------------------------------------ shared-memory layout
+
+template <int D, int TPB, int NPDF>
+struct SmemLayout {
+    static constexpr int WARPS = TPB / 32;
+    __host__ __device__ static size_t grid_off() { return 0; }
+    __host__ __device__ static size_t pdf_off(int nb) { return ((size_t)D * (nb + 1) + 1) & ~(size_t)1; }
+    __host__ __device__ static size_t hist_off(int nb, int npdf_vals) { return pdf_off(nb) + (size_t)NPDF * npdf_vals; }
+    __host__ __device__ static size_t vbuf_off(int nb, int npdf_vals) { return hist_off(nb, npdf_vals) + (size_t)WARPS * D * nb; }
+    __host__ __device__ static size_t red_off(int nb, int npdf_vals) { return vbuf_off(nb, npdf_vals) + TPB; }
+    __host__ __device__ static size_t bytes(int nb, int npdf_vals) { return (red_off(nb, npdf_vals) + 2 * WARPS) * sizeof(double); }
+};
+
+// ------------------------------------------------------------------ the fused integrand kernel
+
+template <class P, typename R, int TPB, bool WRITE>
+__global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
+{
+    constexpr int D = P::D;
+    constexpr int WARPS = TPB / 32;
+    using L = SmemLayout<D, TPB, P::NPDF>;
+    extern __shared__ double smem[];
+    const int nb = kp.nb;
+    const int npv = kp.pdfg.nx * kp.pdfg.nq;
+    double* sgrid = smem + L::grid_off();
+    double* spdf = smem + L::pdf_off(nb);
+    double* shist = smem + L::hist_off(nb, npv);
+    double* svbuf = smem + L::vbuf_off(nb, npv);
+    double* sred = smem + L::red_off(nb, npv);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (int i = tid; i < D * (nb + 1); i += TPB) sgrid[i] = kp.grid[i];
+    for (int i = tid; i < P::NPDF * npv; i += TPB) spdf[i] = kp.pdf[i];
+    for (int i = tid; i < WARPS * D * nb; i += TPB) shist[i] = 0.0;
+    __syncthreads();
+
+    double* myhist = shist + warp * D * nb;
+    double sw = 0.0, sw2 = 0.0;
+    unsigned long long npass = 0, nnan = 0;
+    const long long n = kp.n_events;
+    const long long total = (long long)gridDim.x * TPB;
+    const long long rounds = (n + total - 1) / total;
+    for (long long r = 0; r < rounds; ++r) {
+        const long long e = r * total + (long long)blockIdx.x * TPB + tid;
+        const bool valid = e < n;
+        EventOut<D> o;
+        double pm[P::NEXT][4];
+        o.w = 0.0; o.me2 = 0.0; o.mask = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) o.bins[d] = 0;
+        if (valid) {
+            const unsigned long long ev = (unsigned long long)(kp.ev_offset + e);
+            if constexpr (P::NPDF == 0) event_ee<R>(kp, sgrid, ev, o, pm);
+            else event_tops<P, R>(kp, sgrid, spdf, ev, o, pm);
+            if (!isfinite(o.w)) { o.w = 0.0; ++nnan; }
+            npass += o.mask ? 1 : 0;
+            if constexpr (WRITE) {
+                for (int d = 0; d < D; ++d) {
+                    if (kp.ev_u) kp.ev_u[e * D + d] = o.u[d];
+                    if (kp.ev_x) kp.ev_x[e * D + d] = o.x[d];
+                    if (kp.ev_bins) kp.ev_bins[e * D + d] = o.bins[d];
+                }
+                if (kp.ev_w) kp.ev_w[e] = o.w;
+                if (kp.ev_mask) kp.ev_mask[e] = (uint8_t)o.mask;
+                if (kp.ev_me2) kp.ev_me2[e] = o.me2;
+                if (kp.ev_p)
+                    for (int i = 0; i < P::NEXT; ++i)
+                        for (int c = 0; c < 4; ++c) kp.ev_p[(e * P::NEXT + i) * 4 + c] = pm[i][c];
+            }
+        }
+        const double wn = o.w * kp.inv_n;
+        const double v = wn * wn;
+        sw += wn;
+        sw2 += v;
+        // deterministic per-warp histogram: one leader per distinct bin sums its
+        // peers' values in lane order
+        svbuf[tid] = v;
+        __syncwarp();
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)o.bins[d]);
+            if (lane == __ffs(peers) - 1) {
+                double s = 0.0;
+                for (unsigned m = peers; m; m &= m - 1) s += svbuf[warp * 32 + __ffs(m) - 1];
+                myhist[d * nb + o.bins[d]] += s;
+            }
+        }
+        __syncwarp();
+    }
+
+    // block reduction of the two sums: warp trees, then warps in order
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        sw += __shfl_down_sync(0xffffffffu, sw, off);
+        sw2 += __shfl_down_sync(0xffffffffu, sw2, off);
+    }
+    if (lane == 0) { sred[2 * warp] = sw; sred[2 * warp + 1] = sw2; }
+    // counters: integer sums are order independent
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        npass += __shfl_down_sync(0xffffffffu, npass, off);
+        nnan += __shfl_down_sync(0xffffffffu, nnan, off);
+    }
+    if (lane == 0 && (npass || nnan)) {
+        atomicAdd(kp.counters + 0, npass);
+        atomicAdd(kp.counters + 1, nnan);
+    }
+    __syncthreads();
+    double* out = kp.partials + (size_t)blockIdx.x * (2 + D * nb);
+    if (tid == 0) {
+        double a = 0.0, b = 0.0;
+        for (int w = 0; w < WARPS; ++w) { a += sred[2 * w]; b += sred[2 * w + 1]; }
+        out[0] = a; out[1] = b;
+    }
+    for (int i = tid; i < D * nb; i += TPB) {
+        double s = 0.0;
+        for (int w = 0; w < WARPS; ++w) s += shist[w * D * nb + i];
+        out[2 + i] = s;
+    }
+}
+
+// ------------------------------------------------------------------ evaluate
+
+template <class ME, typename R>
+__global__ void __launch_bounds__(128) evaluate_kernel(const double* __restrict__ mom, long long n, double* __restrict__ me2,
+                                                       double mt, double gs)
+{
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double p[ME::NEXT][4];
+        for (int i = 0; i < ME::NEXT; ++i)
+            for (int c = 0; c < 4; ++c) p[i][c] = mom[(e * ME::NEXT + i) * 4 + c];
+        me2[e] = ME::template me2<R>(p, mt, gs);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(128) evaluate_ee_kernel(const double* __restrict__ mom, long long n, double* __restrict__ me2,
+                                                          EwParams ew)
+{
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double p[4][4];
+        for (int i = 0; i < 4; ++i)
+            for (int c = 0; c < 4; ++c) p[i][c] = mom[(e * 4 + i) * 4 + c];
+        me2[e] = MeEeMumu::me2<R>(p, ew);
+    }
+}
+
+}  // namespace mf

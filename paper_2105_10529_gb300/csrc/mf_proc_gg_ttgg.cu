@@ -1,0 +1,23 @@
+// Kernels of the process gg_ttgg: fused integrand (FP64 and mixed) and
+// matrix-element evaluation, instantiated in their own translation unit.
+#include "mf_dispatch.cuh"
+#include "generated/me_gg_ttgg.cuh"
+
+namespace mf {
+namespace {
+using P = ProcTops<Me_gg_ttgg>;
+using I = IntegrandOps<P, 128>;
+
+cudaError_t evaluate(int prec, const double* mom, long long n, double* me2, double mt, double gs, const EwParams&,
+                     int nblk, cudaStream_t s)
+{
+    if (prec) evaluate_kernel<Me_gg_ttgg, float><<<nblk, 128, 0, s>>>(mom, n, me2, mt, gs);
+    else evaluate_kernel<Me_gg_ttgg, double><<<nblk, 128, 0, s>>>(mom, n, me2, mt, gs);
+    return cudaGetLastError();
+}
+
+const ProcOps kOps = { P::D, P::NEXT, P::NPDF, 128, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate };
+}  // namespace
+
+const ProcOps* ops_gg_ttgg() { return &kOps; }
+}  // namespace mf

@@ -1,0 +1,36 @@
+"""Write the generated matrix-element headers into csrc/generated/.
+
+    python -m paper_2105_10529_gb300.gen
+"""
+import os
+from fractions import Fraction
+
+from . import qcd_diagrams
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+OUT = os.path.join(os.path.dirname(HERE), "csrc", "generated")
+
+PROCESSES = [
+    (2, "gg_tt", Fraction(1)),
+    (3, "gg_ttg", Fraction(1)),
+    (4, "gg_ttgg", Fraction(1, 2)),
+]
+
+
+def write_all(out_dir: str = OUT) -> list:
+    os.makedirs(out_dir, exist_ok=True)
+    written = []
+    for k, name, sym in PROCESSES:
+        src, _ = qcd_diagrams.generate_gluon_process(k, name, sym)
+        path = os.path.join(out_dir, f"me_{name}.cuh")
+        old = open(path).read() if os.path.exists(path) else None
+        if old != src:
+            with open(path, "w") as f:
+                f.write(src)
+        written.append(path)
+    return written
+
+
+if __name__ == "__main__":
+    for p in write_all():
+        print(p)

@@ -1,0 +1,176 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.  Bit-exact for random streams, VEGAS bins and mapped
+points and cut masks (away from a threshold); per-event weights within 1e-12
+(FP64 path) and 1e-5 (mixed path) relative."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2105_10529_gb300 import inputs as IN
+from tests.gpu_common import PHYS, assert_fp_parity, cut_margin, oracle_events, random_grid, rel_err
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PROCS = [IN.EE_MUMU, IN.GG_TT, IN.GG_TTG, IN.GG_TTGG]
+N_SMALL = {IN.EE_MUMU: 4099, IN.GG_TT: 3001, IN.GG_TTG: 1501, IN.GG_TTGG: 301}
+TOL = {0: 1e-12, 1: 1e-5}
+
+
+@pytest.fixture(scope="module")
+def pdf_grid():
+    return IN.make_pdf_grid()
+
+
+@pytest.fixture(scope="module")
+def opdf(pdf_grid):
+    return O.Pdf(pdf_grid)
+
+
+def ctx_for(proc, prec, pdf_grid):
+    from paper_2105_10529_gb300.api import Context
+    return Context(PHYS[proc], pdf_grid, precision=prec)
+
+
+@pytest.mark.parametrize("proc", PROCS)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_event_parity(proc, prec, pdf_grid, opdf):
+    phys = PHYS[proc]
+    dim = IN.DIM[proc]
+    n = N_SMALL[proc]
+    grid = random_grid(dim, seed=proc)
+    ctx = ctx_for(proc, prec, pdf_grid)
+    g = torch.tensor(grid, device="cuda")
+    it = 3
+    sums, ev = ctx.vegas_pass(proc, phys.sqrt_s, g, n, ev_offset=0, iteration=it, want_events=True)
+    torch.cuda.synchronize()
+    ref = oracle_events(proc, phys, opdf, grid, n, iteration=it)
+    u = ev["u"].cpu().numpy(); x = ev["x"].cpu().numpy(); b = ev["bins"].cpu().numpy()
+    # random stream, bins and mapped points: bit-exact
+    assert np.array_equal(u, ref["u"])
+    assert np.array_equal(b, ref["bins"])
+    assert np.array_equal(x, ref["x"])
+    # cut masks: bit-exact except for events within rounding of a threshold
+    mk = ev["mask"].cpu().numpy().astype(int)
+    flips = np.nonzero(mk != ref["mask"])[0]
+    for i in flips:
+        assert cut_margin(proc, phys, ref["plab"][i]) < 1e-9, f"mask flip far from threshold at event {i}"
+    same = mk == ref["mask"]
+    w = ev["w"].cpu().numpy()
+    assert_fp_parity(rel_err(w[same], ref["w"][same]), prec, "w")
+    me = ev["me2"].cpu().numpy()
+    assert_fp_parity(rel_err(me[same], ref["me2"][same]), prec, "me2")
+    # momenta in the partonic frame
+    pm = ev["momenta"].cpu().numpy()
+    scale = np.abs(ref["p"]).max()
+    assert np.abs(pm - ref["p"]).max() < 1e-12 * scale
+    # pass sums (w includes 1/n)
+    s = sums.cpu().numpy()
+    sw = ref["w"].sum() / n
+    assert abs(s[0] - sw) <= (1e-11 if prec == 0 else 1e-5) * abs(sw) + 1e-300
+    ctx.close()
+
+
+@pytest.mark.parametrize("proc", PROCS)
+@pytest.mark.parametrize("prec", [0, 1])
+def test_evaluate_parity(proc, prec, pdf_grid):
+    phys = PHYS[proc]
+    rng = np.random.default_rng(100 + proc)
+    n_ext = IN.N_EXT[proc]
+    nf = n_ext - 2
+    masses = {IN.EE_MUMU: [0.0, 0.0]}.get(proc, [phys.mt, phys.mt] + [0.0] * (nf - 2))
+    moms, refs = [], []
+    for shat_tev2 in (0.5, 1.0, 3.0, 13.0):
+        rs = math.sqrt(shat_tev2) * 1000.0 if proc != IN.EE_MUMU else 91.19 * shat_tev2
+        for _ in range(8):
+            pf, _ = O.rambo(nf, rs, masses, rng.random(4 * nf))
+            p = np.vstack([[[rs / 2, 0, 0, rs / 2], [rs / 2, 0, 0, -rs / 2]], pf])
+            moms.append(p)
+            refs.append(O.me2(proc, phys, p))
+    ctx = ctx_for(proc, prec, pdf_grid)
+    out = ctx.evaluate(proc, torch.tensor(np.array(moms), device="cuda")).cpu().numpy()
+    assert_fp_parity(rel_err(out, refs), prec, "evaluate")
+    # empty batch is a no-op
+    ctx.evaluate(proc, torch.zeros((0, n_ext, 4), dtype=torch.float64, device="cuda"))
+    ctx.close()
+
+
+def test_ragged_offsets_and_single_event(pdf_grid, opdf):
+    proc = IN.GG_TT
+    phys = PHYS[proc]
+    grid = random_grid(IN.DIM[proc], seed=7)
+    ctx = ctx_for(proc, 0, pdf_grid)
+    g = torch.tensor(grid, device="cuda")
+    for n, off in [(1, 0), (1, 123456789), (37, 5), (1025, 99)]:
+        sums, ev = ctx.vegas_pass(proc, phys.sqrt_s, g, n, ev_offset=off, iteration=1, want_events=True,
+                                  fields=("u", "w"))
+        ref = oracle_events(proc, phys, opdf, grid, n, iteration=1, first=off)
+        assert np.array_equal(ev["u"].cpu().numpy(), ref["u"])
+        assert_fp_parity(rel_err(ev["w"].cpu().numpy(), ref["w"]), 0, "w")
+        assert abs(sums[0].item() - ref["w"].sum() / n) <= 1e-11 * abs(ref["w"].sum() / n)
+    ctx.close()
+
+
+def test_frozen_masks(pdf_grid, opdf):
+    proc = IN.GG_TTG
+    phys = PHYS[proc]
+    grid = random_grid(IN.DIM[proc], seed=8)
+    ctx = ctx_for(proc, 0, pdf_grid)
+    g = torch.tensor(grid, device="cuda")
+    n = 500
+    mask = torch.zeros(n, dtype=torch.uint8, device="cuda")
+    mask[::3] = 1
+    sums, ev = ctx.vegas_pass(proc, phys.sqrt_s, g, n, mask_in=mask, want_events=True, fields=("mask", "w"))
+    assert np.array_equal(ev["mask"].cpu().numpy(), mask.cpu().numpy())
+    w = ev["w"].cpu().numpy()
+    assert np.all(w[1::3] == 0) and np.all(w[2::3] == 0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_integrate_matches_oracle_ee(prec, pdf_grid, opdf):
+    """Same random numbers, same algorithm: GPU and oracle integrals agree far
+    below the MC error, and both agree with the closed form within it."""
+    proc = IN.EE_MUMU
+    phys = PHYS[proc]
+    ctx = ctx_for(proc, prec, pdf_grid)
+    r = ctx.integrate(proc, phys.sqrt_s, 100_000, 5, want_grid=True)
+    ref = O.integrate(proc, phys, opdf, 100_000, 5)
+    assert abs(r["sigma"] - ref["sigma"]) < (1e-9 if prec == 0 else 1e-5) * ref["sigma"]
+    assert abs(r["error"] / ref["error"] - 1) < (1e-6 if prec == 0 else 1e-3)
+    assert np.abs(r["grid"] - ref["grid"]).max() < (1e-9 if prec == 0 else 1e-6)
+    from tests.test_oracle_integration import sigma_ee_quadrature
+    assert abs(r["sigma"] - sigma_ee_quadrature(phys)) < 3 * r["error"]
+    assert r["n_pass"] == 500_000 and r["n_nan"] == 0
+    ctx.close()
+
+
+def test_integrate_matches_oracle_gg_tt(pdf_grid, opdf):
+    proc = IN.GG_TT
+    phys = PHYS[proc]
+    ctx = ctx_for(proc, 0, pdf_grid)
+    r = ctx.integrate(proc, phys.sqrt_s, 50_000, 3, want_grid=True)
+    ref = O.integrate(proc, phys, opdf, 50_000, 3)
+    assert abs(r["sigma"] - ref["sigma"]) < 1e-9 * ref["sigma"]
+    assert np.abs(r["grid"] - ref["grid"]).max() < 1e-9
+    ctx.close()
+
+
+def test_bad_arguments(pdf_grid):
+    from paper_2105_10529_gb300._lib import MfError
+    ctx = ctx_for(IN.GG_TT, 0, pdf_grid)
+    g = torch.tensor(random_grid(10), device="cuda")
+    with pytest.raises(MfError):
+        ctx.integrate(IN.GG_TT, 13000.0, 1, 2)           # n_events < 2
+    with pytest.raises(MfError):
+        ctx.integrate(IN.GG_TT, 100.0, 1000, 2)          # below threshold
+    with pytest.raises(MfError) as e:
+        ctx.integrate(IN.UU_TT, 13000.0, 1000, 2)        # not built
+    assert e.value.code == 5
+    with pytest.raises(MfError):
+        ctx.vegas_pass(IN.GG_TT, 13000.0, g, 0)
+    with pytest.raises(MfError):
+        ctx.integrate(17, 13000.0, 1000, 2)
+    ctx.close()
