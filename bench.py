@@ -1,0 +1,357 @@
+"""Throughput benchmark of the leading-order integrand (one JSON line on stdout).
+
+A step is one VEGAS iteration of the g g -> t tbar g g integrand at 13 TeV
+(4e6 events: Philox -> VEGAS map -> parton map -> RAMBO -> cuts -> PDF ->
+|M|^2 with 123 diagrams, 64 helicities, 24 colour flows -> weights and
+histograms -> grid refinement), mixed FP32/FP64 precision, on synthetic
+inputs.  The FP64 GPU path, the per-event error of the mixed path and the
+FP64 CPU oracle are measured in the same run.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun (N > 1) every rank processes its own block of events
+(weak scaling); the per-iteration pass sums are all-reduced before every
+rank refines the same grid.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+HBM_FALLBACK = 6800.0
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+SM_MAX_MHZ = 2070.0
+FP64_PEAK_NOMINAL_TFLOPS = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--events", type=int, default=4_000_000)
+    ap.add_argument("--fp64-events", type=int, default=200_000)
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    ap.add_argument("--only-timed", action="store_true",
+                    help="run only the warm-up and timed mixed-precision steps (for profiler captures)")
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": HBM_FALLBACK, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    def __init__(self, index: int):
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+                 "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(index), f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": []}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1])); mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        if sm:
+            sm.sort()
+            out = {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                   "samples": len(sm)}
+        return out
+
+
+def flops_per_event_me(process: int) -> float:
+    from fractions import Fraction
+    from paper_2105_10529_gb300.gen import qcd_diagrams as Q
+    k = {1: 2, 3: 3, 5: 4}[process]
+    _, st = Q.generate_gluon_process(k, "x", Fraction(1))
+    return float(st["flops_me"])
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, on this host's cores,
+    a bounded sample of the same workload per step."""
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import numpy as np
+    import oracle as O
+    from paper_2105_10529_gb300 import inputs as IN
+    proc = IN.GG_TTGG
+    phys = IN.Physics(seed=3)
+    pdf = O.Pdf(IN.make_pdf_grid())
+    cores = os.cpu_count() or 1
+    n = max(200, 250 * cores)
+    grid = O.vegas_init(IN.DIM[proc], phys.n_bins)
+    for w in range(args.warmup):
+        O.vegas_pass(proc, phys, pdf, grid, min(n, 64 * cores), iteration=w, n_threads=cores)
+    t0 = time.perf_counter()
+    for s in range(args.steps):
+        r = O.vegas_pass(proc, phys, pdf, grid, n, iteration=args.warmup + s, n_threads=cores)
+        grid = O.vegas_refine(r["hist"], grid, phys.alpha)
+    dt = time.perf_counter() - t0
+    v = n * args.steps / dt
+    line = {
+        "impl": "reference", "metric": "gg->ttbar gg weighted events/s", "value": v, "unit": "events/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "gg -> t tbar g g, 13 TeV, VEGAS iterations of the FP64 CPU oracle",
+                   "events_per_step": n, "process": "gg_ttgg"},
+        "cpu_baseline": {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
+                         "sample": f"{n} events per step x {args.steps} steps (bounded sample of the 4e6-event iteration)"},
+        "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    from paper_2105_10529_gb300 import inputs as IN
+    from paper_2105_10529_gb300._lib import MF_FP64, MF_MIXED
+    from paper_2105_10529_gb300.api import Context, process_info
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    proc = IN.GG_TTGG
+    phys = IN.Physics(seed=3)
+    pdf = IN.make_pdf_grid()
+    n_ext, dim = process_info(proc)
+    nb = phys.n_bins
+    N = args.events
+    stream = torch.cuda.current_stream()
+    ctx = Context(phys, pdf, precision=MF_MIXED, stream=stream)
+    dev = torch.device("cuda", local)
+    grid = torch.linspace(0, 1, nb + 1, dtype=torch.float64, device=dev).repeat(dim, 1).contiguous()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
+
+    from paper_2105_10529_gb300 import _lib
+    import ctypes as C
+    L = _lib.lib()
+
+    def step(it, grid, n, offset, ev_it, timed_events=None):
+        """One VEGAS iteration: pass over n events, (all-reduce), refine."""
+        sums = torch.empty(2 + dim * nb, dtype=torch.float64, device=dev)
+        if timed_events is not None:
+            timed_events[0].record(stream)
+        rc = L.mf_vegas_pass(ctx.ptr, proc, phys.sqrt_s, C.c_void_p(grid.data_ptr()), n, offset, ev_it, None,
+                             C.c_void_p(sums.data_ptr()), None)
+        if timed_events is not None:
+            timed_events[1].record(stream)
+        if rc:
+            raise RuntimeError(L.mf_last_error(ctx.ptr))
+        if world > 1:
+            import torch.distributed as dist
+            dist.all_reduce(sums)
+            sums /= world           # every rank's pass is normalised by its own n
+        rc = L.mf_vegas_refine(ctx.ptr, dim, nb, phys.alpha, C.c_void_p(sums.data_ptr()), C.c_void_p(grid.data_ptr()))
+        if rc:
+            raise RuntimeError(L.mf_last_error(ctx.ptr))
+        return sums
+
+    offset = rank * N
+    for w in range(args.warmup):
+        step(w, grid, N, offset, w)
+    torch.cuda.synchronize()
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    sampler = ClockSampler(local) if rank == 0 else None
+    ev_pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    step_pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    sums_list = []
+    for s in range(args.steps):
+        flush.zero_()                                  # L2 flush outside the timed step
+        step_pairs[s][0].record(stream)
+        sums_list.append(step(args.warmup + s, grid, N, offset, args.warmup + s, ev_pairs[s]))
+        step_pairs[s][1].record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop() if sampler else None
+    step_ms = [a.elapsed_time(b) for a, b in step_pairs]
+    kern_ms = [a.elapsed_time(b) for a, b in ev_pairs]
+    t_total = sum(step_ms) / 1e3
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([t_total], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        t_total = float(t.item())
+    value = N * world * args.steps / t_total
+
+    if rank != 0:
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        return
+    if args.only_timed:
+        print(json.dumps({"only_timed": True, "value": value, "unit": "events/s", "steps": args.steps,
+                          "events_per_step": N, "kernel_ms": [a.elapsed_time(b) for a, b in ev_pairs]}), flush=True)
+        return
+
+    # per-step estimate of the last iteration and the pass rate
+    cnt = np.zeros(2, dtype=np.uint64)
+    # dominant kernel: the fused integrand (pass) -- algorithmic FLOPs per launch
+    fl_me = flops_per_event_me(proc)
+    # pass fraction from one extra inspection pass of the final grid
+    sums_chk, evs = ctx.vegas_pass(proc, phys.sqrt_s, grid, 200_000, ev_offset=10**9, iteration=999,
+                                   want_events=True, fields=("mask",))
+    pass_frac = float(evs["mask"].float().mean().item())
+    flops_launch = fl_me * N * pass_frac
+    kern_avg_s = sum(kern_ms) / len(kern_ms) / 1e3
+    achieved_tflops = flops_launch / kern_avg_s / 1e12
+    pk, pk_kind = peaks()
+    fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+
+    # ---- FP64 GPU path on a bounded sample and the per-event error of the mixed path
+    n64 = args.fp64_events
+    ctx64 = Context(phys, pdf, precision=MF_FP64, stream=stream)
+    ctx64.vegas_pass(proc, phys.sqrt_s, grid, 2000, iteration=0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s64, ev64 = ctx64.vegas_pass(proc, phys.sqrt_s, grid, n64, ev_offset=0, iteration=10**6,
+                                 want_events=True, fields=("w", "mask"))
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1) / 1e3
+    s32, ev32 = ctx.vegas_pass(proc, phys.sqrt_s, grid, n64, ev_offset=0, iteration=10**6,
+                               want_events=True, fields=("w", "mask"))
+    torch.cuda.synchronize()
+    w64 = ev64["w"].cpu().numpy(); w32 = ev32["w"].cpu().numpy()
+    ok = (w64 != 0)
+    rel = np.abs(w32[ok] - w64[ok]) / np.abs(w64[ok])
+    sig_rel = abs(float(s32[0]) - float(s64[0])) / abs(float(s64[0]))
+    err_mc = math.sqrt(max(float(s64[1]) * n64 - float(s64[0]) ** 2, 0.0) / (n64 - 1)) / abs(float(s64[0]))
+    fp64_value = n64 / t64
+    fp64_tflops = fl_me * n64 * float(ok.mean()) / t64 / 1e12
+
+    # ---- end to end through the C ABI with host buffers: PDF upload, one
+    # iteration from a uniform grid, host result
+    import ctypes as C2
+    pinned = torch.from_numpy(pdf).pin_memory()
+    res = _lib.MfResult()
+    it_host = np.zeros(2)
+    e2e_steps = max(2, min(args.steps, 5))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(e2e_steps):
+        L.mf_set_pdf(ctx.ptr, C2.cast(pinned.data_ptr(), C2.POINTER(C2.c_double)))
+        rc = L.mf_integrate(ctx.ptr, proc, phys.sqrt_s, N, 1, C2.byref(res),
+                            it_host.ctypes.data_as(C2.POINTER(C2.c_double)), None)
+        if rc:
+            raise RuntimeError(L.mf_last_error(ctx.ptr))
+    t_e2e = time.perf_counter() - t0
+    e2e = {"value": N * e2e_steps / t_e2e, "unit": "events/s",
+           "h2d_bytes_per_step": int(pdf.nbytes + dim * (nb + 1) * 8),
+           "d2h_bytes_per_step": int(2 * 8 + 2 * 8)}
+
+    # ---- FP64 CPU oracle on the host cores (bounded sample)
+    cpu = None
+    if not args.no_cpu:
+        import oracle as O
+        cores = os.cpu_count() or 1
+        n_cpu = max(200, 1500 * cores)
+        opdf = O.Pdf(pdf)
+        gnp = grid.cpu().numpy()
+        O.vegas_pass(proc, phys, opdf, gnp, 64, iteration=0, n_threads=cores)
+        t0 = time.perf_counter()
+        O.vegas_pass(proc, phys, opdf, gnp, n_cpu, iteration=7, n_threads=cores)
+        dt = time.perf_counter() - t0
+        cpu = {"value": n_cpu / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+               "sample": f"{n_cpu} events of one iteration at the adapted grid ({dt:.1f} s)"}
+
+    line = {
+        "metric": "gg->ttbar gg weighted events/s, FP32-mixed vs FP64 GPU at stated err; % FP peak",
+        "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": "gg -> t tbar g g LO, 13 TeV, 4e6 events per VEGAS iteration, mixed FP32/FP64",
+                   "process": "gg_ttgg", "events_per_step": N, "dims": dim, "bins": nb,
+                   "cuts": "pT(g)>30, |eta(g)|<2.5, dR(g,g)>0.4", "pdf": "synthetic 100x50 log-bicubic grid",
+                   "l2": "inputs far below L2; a 256 MB buffer is written between timed steps"},
+        "gpu_launches": 2 * args.steps,
+        "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved_tflops / fp32_peak, "traffic": None,
+                     "kernel": "integrand_kernel<gg_ttgg, float>",
+                     "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz (nominal units and max clock)",
+                     "flops_per_event_me": fl_me, "pass_fraction": pass_frac, "kernel_ms_avg": kern_avg_s * 1e3},
+        "fp64_gpu": {"value": fp64_value, "unit": "events/s", "events": n64,
+                     "achieved_tflops": fp64_tflops, "peak_nominal_tflops": FP64_PEAK_NOMINAL_TFLOPS,
+                     "mixed_speedup": value / fp64_value},
+        "stated_err": {"per_event_rel_max": float(rel.max()), "per_event_rel_p999": float(np.quantile(rel, 0.999)),
+                       "per_event_rel_median": float(np.median(rel)), "sigma_rel_mixed_vs_fp64": sig_rel,
+                       "mc_rel_error_of_sample": err_mc, "events": int(ok.sum())},
+        "e2e": e2e,
+        "clocks": clocks,
+        "peaks_source": pk_kind,
+    }
+    if cpu:
+        line["cpu_baseline"] = cpu
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

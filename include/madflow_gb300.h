@@ -145,6 +145,14 @@ int mf_vegas_pass(struct mf_ctx *ctx, int process, double sqrt_s, const double *
                   long long ev_offset, unsigned int iteration, const unsigned char *mask_in_dev, double *sums_dev,
                   const mf_event_arrays *ev);
 
+/* VEGAS grid refinement (Sec. 1, the VegasFlow integrator; Lepage 1978)
+ * from the sums of one or more passes: sums_dev [2 + dim n_bins] as
+ * written by mf_vegas_pass (several ranks' sums may be averaged first),
+ * grid_dev [dim][n_bins+1] updated in place; a dimension whose histogram is
+ * all zero keeps its edges.  dim <= 18, 2 <= n_bins <= 64, alpha >= 0.
+ * Does not synchronise. */
+int mf_vegas_refine(struct mf_ctx *ctx, int dim, int n_bins, double alpha, const double *sums_dev, double *grid_dev);
+
 /* evaluate (Sec. 2.2): spin- and colour-averaged |M|^2 (identical-particle
  * factor included) of n phase-space points.  momenta_dev: [n][n_ext][4];
  * me2_dev: [n].  Does not synchronise. */

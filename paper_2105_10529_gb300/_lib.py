@@ -64,6 +64,7 @@ def lib():
             "mf_integrate": (C.c_int, [vp, C.c_int, C.c_double, i64, C.c_int, C.POINTER(MfResult), dp, dp]),
             "mf_vegas_pass": (C.c_int, [vp, C.c_int, C.c_double, vp, i64, i64, C.c_uint, vp, vp,
                                         C.POINTER(MfEventArrays)]),
+            "mf_vegas_refine": (C.c_int, [vp, C.c_int, C.c_int, C.c_double, vp, vp]),
             "mf_evaluate": (C.c_int, [vp, C.c_int, vp, i64, vp]),
         }
         for name, (res, args) in sig.items():
@@ -76,4 +77,4 @@ def lib():
 
 def exported_symbols():
     return ["mf_default_config", "mf_process_info", "mf_create", "mf_destroy", "mf_last_error",
-            "mf_set_precision", "mf_set_pdf", "mf_integrate", "mf_vegas_pass", "mf_evaluate"]
+            "mf_set_precision", "mf_set_pdf", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate"]

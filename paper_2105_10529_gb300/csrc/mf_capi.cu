@@ -30,33 +30,13 @@ struct mf_ctx {
 namespace mf {
 // ------------------------------------------------------------------ end of a pass
 
-// Sums the per-CTA partials in CTA order, stores (I_k, var_k) for the
-// iteration and, unless this is the last iteration, refines the grid
-// (Lepage 1978: smoothing, normalisation, damping ((r-1)/ln r)^alpha,
-// equal-share rebinning).  One CTA; column c of the partials is summed by
-// thread c.
-__global__ void finish_pass_kernel(const double* partials, int nblk, int D, int nb, long long n, double alpha,
-                                   int refine, double* grid, double* iter_stats, double* sums_out)
+// VEGAS grid refinement of one dimension from its histogram h of (f J)^2
+// (Lepage 1978): neighbour smoothing, normalisation, damping
+// ((r-1)/ln r)^alpha, then edges moved so that every new bin holds the same
+// share of the damped weights.  A dimension with an empty histogram keeps
+// its grid.
+__device__ void refine_dim(const double* h, double* e, int nb, double alpha)
 {
-    extern __shared__ double sh[];     // [2 + D nb] sums, then refine scratch
-    const int ncol = 2 + D * nb;
-    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
-        double s = 0.0;
-        for (int b = 0; b < nblk; ++b) s += partials[(size_t)b * ncol + c];
-        sh[c] = s;
-        if (sums_out) sums_out[c] = s;
-    }
-    __syncthreads();
-    if (threadIdx.x == 0 && iter_stats) {
-        const double I = sh[0], I2 = sh[1];
-        iter_stats[0] = I;
-        iter_stats[1] = ((double)n * I2 - I * I) / (double)(n - 1);
-    }
-    if (!refine) return;
-    const int d = threadIdx.x;
-    if (d >= D) return;
-    const double* h = sh + 2 + d * nb;
-    double* e = grid + d * (nb + 1);
     double tot = 0.0;
     for (int i = 0; i < nb; ++i) tot += h[i];
     if (!(tot > 0.0)) return;
@@ -84,6 +64,35 @@ __global__ void finish_pass_kernel(const double* partials, int nblk, int D, int 
         ne[k] = e[j] + frac * (e[j + 1] - e[j]);
     }
     for (int k = 0; k <= nb; ++k) e[k] = ne[k];
+}
+
+// Sums the per-CTA partials in CTA order, stores (I_k, var_k) for the
+// iteration and, when asked, refines the grid.  One CTA; column c of the
+// partials is summed by thread c, dimension d is refined by thread d.
+__global__ void finish_pass_kernel(const double* partials, int nblk, int D, int nb, long long n, double alpha,
+                                   int refine, double* grid, double* iter_stats, double* sums_out)
+{
+    extern __shared__ double sh[];     // [2 + D nb] sums
+    const int ncol = 2 + D * nb;
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) {
+        double s = 0.0;
+        for (int b = 0; b < nblk; ++b) s += partials[(size_t)b * ncol + c];
+        sh[c] = s;
+        if (sums_out) sums_out[c] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && iter_stats) {
+        const double I = sh[0], I2 = sh[1];
+        iter_stats[0] = I;
+        iter_stats[1] = ((double)n * I2 - I * I) / (double)(n - 1);
+    }
+    if (refine && (int)threadIdx.x < D) refine_dim(sh + 2 + threadIdx.x * nb, grid + threadIdx.x * (nb + 1), nb, alpha);
+}
+
+// refinement from already reduced pass sums [2 + D nb]
+__global__ void refine_kernel(const double* sums, int D, int nb, double alpha, double* grid)
+{
+    if ((int)threadIdx.x < D) refine_dim(sums + 2 + threadIdx.x * nb, grid + threadIdx.x * (nb + 1), nb, alpha);
 }
 
 }  // namespace mf
@@ -313,6 +322,16 @@ int mf_vegas_pass(mf_ctx* c, int process, double sqrt_s, const double* grid_dev,
     finish_pass_kernel<<<1, 1024, ncol * sizeof(double), c->stream>>>(c->d_partials, nblk, ops->D, c->cfg.n_bins,
                                                                      n_events, c->cfg.alpha, 0, nullptr, nullptr,
                                                                      sums_dev);
+    MF_CUDA(c, cudaGetLastError());
+    return MF_OK;
+}
+
+int mf_vegas_refine(mf_ctx* c, int dim, int n_bins, double alpha, const double* sums_dev, double* grid_dev)
+{
+    if (!c) return MF_ERR_ARG;
+    if (dim < 1 || dim > MAX_DIM || n_bins < 2 || n_bins > MAX_BINS || !sums_dev || !grid_dev || !(alpha >= 0.0))
+        return fail(c, MF_ERR_ARG, "mf_vegas_refine: bad argument");
+    refine_kernel<<<1, 32, 0, c->stream>>>(sums_dev, dim, n_bins, alpha, grid_dev);
     MF_CUDA(c, cudaGetLastError());
     return MF_OK;
 }

@@ -634,7 +634,40 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("}")
     src.append("}  // namespace mf")
     stats = dict(n_diag=n_diag, n_amp=len(diags), ncol=ncol, counts=dict(em.counts), colour_den=den)
+    stats["flops_per_helicity"] = helicity_flops(em, ncol, CI)
+    stats["n_hel"] = 1 << n_ext
+    stats["flops_me"] = stats["flops_per_helicity"] * stats["n_hel"]
     return "\n".join(src) + "\n", stats
+
+
+# Floating-point operations of each routine of mf_helas.cuh as written
+# (add, sub, mul = 1; fused multiply-add = 2), read off the routine bodies.
+ROUTINE_FLOPS = dict(
+    vvv=158,        # vvv_cur: 3 momentum combinations, J1.J2, 2 momentum dots, 4 components
+    vvvv=264,       # vvvv_cur: 3 dots + 3 two-term combinations per component
+    ffv_row=152,    # ffv_row: Sigma/Sigmabar of J, two 2x2 products, two (q-slash + m) halves
+    ffv_col=152,    # ffv_col: same structure on a column spinor
+    ffv_amp=102,    # ffv_amp: Sigma/Sigmabar of J and two spinor contractions
+    vvv_amp=166,    # vvv_amp: 3 dots, 3 momentum dots, 3 products
+    vvvv_amp=222,   # vvvv_amp: 6 dots and 3 two-term differences
+    ffv_cur=80,     # ffv_cur: 8 complex products and the 4 components
+)
+
+
+def helicity_flops(em: "Emitter", ncol: int, CI) -> int:
+    """Algorithmic FLOPs of one helicity configuration of the generated body:
+    vertex routines, external states, momentum sums, colour-flow
+    accumulation and the colour sum."""
+    f = sum(ROUTINE_FLOPS[k] * v for k, v in em.counts.items())
+    f += 6 * em.k + 2 * 10                     # external gluon and fermion states
+    for line in em.lines:
+        if line.startswith("const R k") or line.startswith("const R q"):
+            f += line.count("+") + line.count(" - ")
+        if line.startswith("jamp[") or ".r +=" in line or ".r -=" in line or "fma(R(" in line:
+            f += 2
+    nz = sum(1 for i in range(ncol) for j in range(i, ncol) if CI[i][j] != 0)
+    f += 2 * 2 * nz + 4 * ncol                  # symmetric colour sum (re and im) and the final products
+    return f
 
 
 if __name__ == "__main__":
