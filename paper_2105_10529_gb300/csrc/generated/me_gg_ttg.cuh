@@ -15,14 +15,20 @@ struct Me_gg_ttg {
   static constexpr double AVG = 1.0 / 256.0;
   static constexpr double SYM = 1.0;
   // helicity-independent per-event pieces
+  // per-thread slot: internal momenta, FP64-computed inverse denominators,
+  // polarisation bases and spinor pieces of the event (kept in shared memory)
   template <typename R> struct Inv {
-    R kr[3][4]; R p3r[4]; R iG[4]; R iQ[6];
+    R K[7][4]; R p3[4]; R iG[4]; R iQ[6];
     R e1[3][3]; R e2[3][3]; FermionBasis<R> fb3, fb4; R mt;
+    cx<R> jamp[6];   // colour-flow amplitudes of the helicity being summed
+    float pad[2];
   };
   // averaged |M|^2 (spin/colour average and identical-particle factor included);
   // p: momenta (E,px,py,pz) incoming first: g, g, t, tbar, g...
+  // slot: this thread's Inv<R> in shared memory, or null for a private local copy
   template <typename R>
-  __device__ static double me2(const double (&p)[NEXT][4], double mt, double gs);
+  __device__ static double me2(const double (&p)[NEXT][4], double mt, double gs, void* slot);
+  template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }
 };
 
 // one helicity configuration: amplitudes, colour flows and the colour sum;
@@ -32,49 +38,53 @@ __device__ __noinline__ R hel_gg_ttg(const Me_gg_ttg::Inv<R>& v, int ih)
 {
     constexpr int NCOL = Me_gg_ttg::NCOL;
 #define HEL(i) ((ih >> (i)) & 1 ? 1 : -1)
-    cx<R> jamp[NCOL];
+    // colour-flow amplitudes accumulate in the slot (shared memory), not in registers
+    volatile cx<R>* jamp = reinterpret_cast<volatile cx<R>*>(const_cast<cx<R>*>(v.jamp));
     #pragma unroll
-    for (int c = 0; c < NCOL; ++c) jamp[c] = mkc(R(0), R(0));
-    const W4<R> g0 = ext_gluon(v.e1[0], v.e2[0], HEL(0), false);
-    const W4<R> g1 = ext_gluon(v.e1[1], v.e2[1], HEL(1), false);
-    const W4<R> g2 = ext_gluon(v.e1[2], v.e2[2], HEL(4), true);
-    const W4<R> ub3 = ext_ubar(v.fb3, HEL(2));
-    const W4<R> v4 = ext_v(v.fb4, HEL(3));
-    const R k1_1[4] = {v.kr[0][0], v.kr[0][1], v.kr[0][2], v.kr[0][3]};
-    const R k2_2[4] = {v.kr[1][0], v.kr[1][1], v.kr[1][2], v.kr[1][3]};
-    const W4<R> w3 = vvv_cur(g0, g1, k1_1, k2_2, v.iG[0]);
-    const R k1_4[4] = {v.kr[0][0], v.kr[0][1], v.kr[0][2], v.kr[0][3]};
-    const R k4_5[4] = {v.kr[2][0], v.kr[2][1], v.kr[2][2], v.kr[2][3]};
-    const W4<R> w6 = vvv_cur(g0, g2, k1_4, k4_5, v.iG[1]);
-    const R k2_7[4] = {v.kr[1][0], v.kr[1][1], v.kr[1][2], v.kr[1][3]};
-    const R k4_8[4] = {v.kr[2][0], v.kr[2][1], v.kr[2][2], v.kr[2][3]};
-    const W4<R> w9 = vvv_cur(g1, g2, k2_7, k4_8, v.iG[2]);
-    const R q1_10[4] = {v.p3r[0] - (v.kr[0][0]), v.p3r[1] - (v.kr[0][1]), v.p3r[2] - (v.kr[0][2]), v.p3r[3] - (v.kr[0][3])};
-    const W4<R> w11 = ffv_row(ub3, g0, q1_10, v.mt, v.iQ[0]);
-    const R q3_13[4] = {v.p3r[0] - (v.kr[0][0] + v.kr[1][0]), v.p3r[1] - (v.kr[0][1] + v.kr[1][1]), v.p3r[2] - (v.kr[0][2] + v.kr[1][2]), v.p3r[3] - (v.kr[0][3] + v.kr[1][3])};
-    const W4<R> w12 = ffv_col(g2, v4, q3_13, v.mt, v.iQ[2]);
+    for (int c = 0; c < NCOL; ++c) { jamp[c].r = R(0); jamp[c].i = R(0); }
+    W4<R> g0; { R a[3], b[3]; for (int j = 0; j < 3; ++j) { a[j] = ldv(v.e1[0][j]); b[j] = ldv(v.e2[0][j]); }
+      g0 = ext_gluon(a, b, HEL(0), false); }
+    W4<R> g1; { R a[3], b[3]; for (int j = 0; j < 3; ++j) { a[j] = ldv(v.e1[1][j]); b[j] = ldv(v.e2[1][j]); }
+      g1 = ext_gluon(a, b, HEL(1), false); }
+    W4<R> g2; { R a[3], b[3]; for (int j = 0; j < 3; ++j) { a[j] = ldv(v.e1[2][j]); b[j] = ldv(v.e2[2][j]); }
+      g2 = ext_gluon(a, b, HEL(4), true); }
+    const W4<R> ub3 = ext_ubar(load_basis(v.fb3), HEL(2));
+    const W4<R> v4 = ext_v(load_basis(v.fb4), HEL(3));
+    const R k1_1[4] = {ldv(v.K[0][0]), ldv(v.K[0][1]), ldv(v.K[0][2]), ldv(v.K[0][3])};
+    const R k2_2[4] = {ldv(v.K[1][0]), ldv(v.K[1][1]), ldv(v.K[1][2]), ldv(v.K[1][3])};
+    const W4<R> w3 = vvv_cur(g0, g1, k1_1, k2_2, ldv(v.iG[0]));
+    const R k1_4[4] = {ldv(v.K[0][0]), ldv(v.K[0][1]), ldv(v.K[0][2]), ldv(v.K[0][3])};
+    const R k4_5[4] = {ldv(v.K[3][0]), ldv(v.K[3][1]), ldv(v.K[3][2]), ldv(v.K[3][3])};
+    const W4<R> w6 = vvv_cur(g0, g2, k1_4, k4_5, ldv(v.iG[1]));
+    const R k2_7[4] = {ldv(v.K[1][0]), ldv(v.K[1][1]), ldv(v.K[1][2]), ldv(v.K[1][3])};
+    const R k4_8[4] = {ldv(v.K[3][0]), ldv(v.K[3][1]), ldv(v.K[3][2]), ldv(v.K[3][3])};
+    const W4<R> w9 = vvv_cur(g1, g2, k2_7, k4_8, ldv(v.iG[2]));
+    const R q1_10[4] = {ldv(v.p3[0]) - ldv(v.K[0][0]), ldv(v.p3[1]) - ldv(v.K[0][1]), ldv(v.p3[2]) - ldv(v.K[0][2]), ldv(v.p3[3]) - ldv(v.K[0][3])};
+    const W4<R> w11 = ffv_row(ub3, g0, q1_10, ldv(v.mt), ldv(v.iQ[0]));
+    const R q3_13[4] = {ldv(v.p3[0]) - ldv(v.K[2][0]), ldv(v.p3[1]) - ldv(v.K[2][1]), ldv(v.p3[2]) - ldv(v.K[2][2]), ldv(v.p3[3]) - ldv(v.K[2][3])};
+    const W4<R> w12 = ffv_col(g2, v4, q3_13, ldv(v.mt), ldv(v.iQ[2]));
     const cx<R> a1 = ffv_amp(w11, w12, g1);
     jamp[0].r -= a1.i; jamp[0].i += a1.r;
-    const R q5_15[4] = {v.p3r[0] - (v.kr[0][0] + v.kr[2][0]), v.p3r[1] - (v.kr[0][1] + v.kr[2][1]), v.p3r[2] - (v.kr[0][2] + v.kr[2][2]), v.p3r[3] - (v.kr[0][3] + v.kr[2][3])};
-    const W4<R> w14 = ffv_col(g1, v4, q5_15, v.mt, v.iQ[4]);
+    const R q5_15[4] = {ldv(v.p3[0]) - ldv(v.K[4][0]), ldv(v.p3[1]) - ldv(v.K[4][1]), ldv(v.p3[2]) - ldv(v.K[4][2]), ldv(v.p3[3]) - ldv(v.K[4][3])};
+    const W4<R> w14 = ffv_col(g1, v4, q5_15, ldv(v.mt), ldv(v.iQ[4]));
     const cx<R> a2 = ffv_amp(w11, w14, g2);
     jamp[1].r -= a2.i; jamp[1].i += a2.r;
     const cx<R> a3 = ffv_amp(w11, v4, w9);
     jamp[0].r -= a3.i; jamp[0].i += a3.r;
     jamp[1].r += a3.i; jamp[1].i -= a3.r;
-    const R q2_16[4] = {v.p3r[0] - (v.kr[1][0]), v.p3r[1] - (v.kr[1][1]), v.p3r[2] - (v.kr[1][2]), v.p3r[3] - (v.kr[1][3])};
-    const W4<R> w17 = ffv_row(ub3, g1, q2_16, v.mt, v.iQ[1]);
+    const R q2_16[4] = {ldv(v.p3[0]) - ldv(v.K[1][0]), ldv(v.p3[1]) - ldv(v.K[1][1]), ldv(v.p3[2]) - ldv(v.K[1][2]), ldv(v.p3[3]) - ldv(v.K[1][3])};
+    const W4<R> w17 = ffv_row(ub3, g1, q2_16, ldv(v.mt), ldv(v.iQ[1]));
     const cx<R> a4 = ffv_amp(w17, w12, g0);
     jamp[2].r -= a4.i; jamp[2].i += a4.r;
-    const R q6_19[4] = {v.p3r[0] - (v.kr[1][0] + v.kr[2][0]), v.p3r[1] - (v.kr[1][1] + v.kr[2][1]), v.p3r[2] - (v.kr[1][2] + v.kr[2][2]), v.p3r[3] - (v.kr[1][3] + v.kr[2][3])};
-    const W4<R> w18 = ffv_col(g0, v4, q6_19, v.mt, v.iQ[5]);
+    const R q6_19[4] = {ldv(v.p3[0]) - ldv(v.K[5][0]), ldv(v.p3[1]) - ldv(v.K[5][1]), ldv(v.p3[2]) - ldv(v.K[5][2]), ldv(v.p3[3]) - ldv(v.K[5][3])};
+    const W4<R> w18 = ffv_col(g0, v4, q6_19, ldv(v.mt), ldv(v.iQ[5]));
     const cx<R> a5 = ffv_amp(w17, w18, g2);
     jamp[3].r -= a5.i; jamp[3].i += a5.r;
     const cx<R> a6 = ffv_amp(w17, v4, w6);
     jamp[2].r -= a6.i; jamp[2].i += a6.r;
     jamp[3].r += a6.i; jamp[3].i -= a6.r;
-    const R q4_20[4] = {v.p3r[0] - (v.kr[2][0]), v.p3r[1] - (v.kr[2][1]), v.p3r[2] - (v.kr[2][2]), v.p3r[3] - (v.kr[2][3])};
-    const W4<R> w21 = ffv_row(ub3, g2, q4_20, v.mt, v.iQ[3]);
+    const R q4_20[4] = {ldv(v.p3[0]) - ldv(v.K[3][0]), ldv(v.p3[1]) - ldv(v.K[3][1]), ldv(v.p3[2]) - ldv(v.K[3][2]), ldv(v.p3[3]) - ldv(v.K[3][3])};
+    const W4<R> w21 = ffv_row(ub3, g2, q4_20, ldv(v.mt), ldv(v.iQ[3]));
     const cx<R> a7 = ffv_amp(w21, w14, g0);
     jamp[4].r -= a7.i; jamp[4].i += a7.r;
     const cx<R> a8 = ffv_amp(w21, w18, g1);
@@ -91,28 +101,28 @@ __device__ __noinline__ R hel_gg_ttg(const Me_gg_ttg::Inv<R>& v, int ih)
     const cx<R> a12 = ffv_amp(ub3, w18, w9);
     jamp[3].r -= a12.i; jamp[3].i += a12.r;
     jamp[5].r += a12.i; jamp[5].i -= a12.r;
-    const W4<R> jq = ffv_cur(ub3, v4, v.iG[3]);
-    const R k1_22[4] = {v.kr[0][0], v.kr[0][1], v.kr[0][2], v.kr[0][3]};
-    const R k6_23[4] = {v.kr[1][0] + v.kr[2][0], v.kr[1][1] + v.kr[2][1], v.kr[1][2] + v.kr[2][2], v.kr[1][3] + v.kr[2][3]};
-    const R k7_24[4] = {v.kr[0][0] + v.kr[1][0] + v.kr[2][0], v.kr[0][1] + v.kr[1][1] + v.kr[2][1], v.kr[0][2] + v.kr[1][2] + v.kr[2][2], v.kr[0][3] + v.kr[1][3] + v.kr[2][3]};
+    const W4<R> jq = ffv_cur(ub3, v4, ldv(v.iG[3]));
+    const R k1_22[4] = {ldv(v.K[0][0]), ldv(v.K[0][1]), ldv(v.K[0][2]), ldv(v.K[0][3])};
+    const R k6_23[4] = {ldv(v.K[5][0]), ldv(v.K[5][1]), ldv(v.K[5][2]), ldv(v.K[5][3])};
+    const R k7_24[4] = {ldv(v.K[6][0]), ldv(v.K[6][1]), ldv(v.K[6][2]), ldv(v.K[6][3])};
     const R nkk7_24[4] = {-k7_24[0], -k7_24[1], -k7_24[2], -k7_24[3]};
     const cx<R> a13 = vvv_amp(g0, w9, jq, k1_22, k6_23, nkk7_24);
     jamp[0].r -= a13.i; jamp[0].i += a13.r;
     jamp[1].r += a13.i; jamp[1].i -= a13.r;
     jamp[3].r += a13.i; jamp[3].i -= a13.r;
     jamp[5].r -= a13.i; jamp[5].i += a13.r;
-    const R k3_25[4] = {v.kr[0][0] + v.kr[1][0], v.kr[0][1] + v.kr[1][1], v.kr[0][2] + v.kr[1][2], v.kr[0][3] + v.kr[1][3]};
-    const R k4_26[4] = {v.kr[2][0], v.kr[2][1], v.kr[2][2], v.kr[2][3]};
-    const R k7_27[4] = {v.kr[0][0] + v.kr[1][0] + v.kr[2][0], v.kr[0][1] + v.kr[1][1] + v.kr[2][1], v.kr[0][2] + v.kr[1][2] + v.kr[2][2], v.kr[0][3] + v.kr[1][3] + v.kr[2][3]};
+    const R k3_25[4] = {ldv(v.K[2][0]), ldv(v.K[2][1]), ldv(v.K[2][2]), ldv(v.K[2][3])};
+    const R k4_26[4] = {ldv(v.K[3][0]), ldv(v.K[3][1]), ldv(v.K[3][2]), ldv(v.K[3][3])};
+    const R k7_27[4] = {ldv(v.K[6][0]), ldv(v.K[6][1]), ldv(v.K[6][2]), ldv(v.K[6][3])};
     const R nkk7_27[4] = {-k7_27[0], -k7_27[1], -k7_27[2], -k7_27[3]};
     const cx<R> a14 = vvv_amp(w3, g2, jq, k3_25, k4_26, nkk7_27);
     jamp[0].r -= a14.i; jamp[0].i += a14.r;
     jamp[2].r += a14.i; jamp[2].i -= a14.r;
     jamp[4].r += a14.i; jamp[4].i -= a14.r;
     jamp[5].r -= a14.i; jamp[5].i += a14.r;
-    const R k5_28[4] = {v.kr[0][0] + v.kr[2][0], v.kr[0][1] + v.kr[2][1], v.kr[0][2] + v.kr[2][2], v.kr[0][3] + v.kr[2][3]};
-    const R k2_29[4] = {v.kr[1][0], v.kr[1][1], v.kr[1][2], v.kr[1][3]};
-    const R k7_30[4] = {v.kr[0][0] + v.kr[1][0] + v.kr[2][0], v.kr[0][1] + v.kr[1][1] + v.kr[2][1], v.kr[0][2] + v.kr[1][2] + v.kr[2][2], v.kr[0][3] + v.kr[1][3] + v.kr[2][3]};
+    const R k5_28[4] = {ldv(v.K[4][0]), ldv(v.K[4][1]), ldv(v.K[4][2]), ldv(v.K[4][3])};
+    const R k2_29[4] = {ldv(v.K[1][0]), ldv(v.K[1][1]), ldv(v.K[1][2]), ldv(v.K[1][3])};
+    const R k7_30[4] = {ldv(v.K[6][0]), ldv(v.K[6][1]), ldv(v.K[6][2]), ldv(v.K[6][3])};
     const R nkk7_30[4] = {-k7_30[0], -k7_30[1], -k7_30[2], -k7_30[3]};
     const cx<R> a15 = vvv_amp(w6, g1, jq, k5_28, k2_29, nkk7_30);
     jamp[1].r -= a15.i; jamp[1].i += a15.r;
@@ -133,32 +143,36 @@ __device__ __noinline__ R hel_gg_ttg(const Me_gg_ttg::Inv<R>& v, int ih)
     jamp[1].r -= a18.i; jamp[1].i += a18.r;
     jamp[3].r -= a18.i; jamp[3].i += a18.r;
     jamp[5].r += a18.i; jamp[5].i -= a18.r;
+    cx<R> J[NCOL];
+    #pragma unroll
+    for (int c = 0; c < NCOL; ++c) J[c] = mkc(R(jamp[c].r), R(jamp[c].i));
     R me = R(0);
-    { const R zr = R(64.0) * jamp[0].r + R(-16.0) * jamp[1].r + R(-16.0) * jamp[2].r + R(2.0) * jamp[3].r + R(2.0) * jamp[4].r + R(20.0) * jamp[5].r; const R zi = R(64.0) * jamp[0].i + R(-16.0) * jamp[1].i + R(-16.0) * jamp[2].i + R(2.0) * jamp[3].i + R(2.0) * jamp[4].i + R(20.0) * jamp[5].i;
-      me = fma(jamp[0].r, zr, fma(jamp[0].i, zi, me)); }
-    { const R zr = R(64.0) * jamp[1].r + R(2.0) * jamp[2].r + R(20.0) * jamp[3].r + R(-16.0) * jamp[4].r + R(2.0) * jamp[5].r; const R zi = R(64.0) * jamp[1].i + R(2.0) * jamp[2].i + R(20.0) * jamp[3].i + R(-16.0) * jamp[4].i + R(2.0) * jamp[5].i;
-      me = fma(jamp[1].r, zr, fma(jamp[1].i, zi, me)); }
-    { const R zr = R(64.0) * jamp[2].r + R(-16.0) * jamp[3].r + R(20.0) * jamp[4].r + R(2.0) * jamp[5].r; const R zi = R(64.0) * jamp[2].i + R(-16.0) * jamp[3].i + R(20.0) * jamp[4].i + R(2.0) * jamp[5].i;
-      me = fma(jamp[2].r, zr, fma(jamp[2].i, zi, me)); }
-    { const R zr = R(64.0) * jamp[3].r + R(2.0) * jamp[4].r + R(-16.0) * jamp[5].r; const R zi = R(64.0) * jamp[3].i + R(2.0) * jamp[4].i + R(-16.0) * jamp[5].i;
-      me = fma(jamp[3].r, zr, fma(jamp[3].i, zi, me)); }
-    { const R zr = R(64.0) * jamp[4].r + R(-16.0) * jamp[5].r; const R zi = R(64.0) * jamp[4].i + R(-16.0) * jamp[5].i;
-      me = fma(jamp[4].r, zr, fma(jamp[4].i, zi, me)); }
-    { const R zr = R(64.0) * jamp[5].r; const R zi = R(64.0) * jamp[5].i;
-      me = fma(jamp[5].r, zr, fma(jamp[5].i, zi, me)); }
+    { const R zr = R(64.0) * J[0].r + R(-16.0) * J[1].r + R(-16.0) * J[2].r + R(2.0) * J[3].r + R(2.0) * J[4].r + R(20.0) * J[5].r; const R zi = R(64.0) * J[0].i + R(-16.0) * J[1].i + R(-16.0) * J[2].i + R(2.0) * J[3].i + R(2.0) * J[4].i + R(20.0) * J[5].i;
+      me = fma(J[0].r, zr, fma(J[0].i, zi, me)); }
+    { const R zr = R(64.0) * J[1].r + R(2.0) * J[2].r + R(20.0) * J[3].r + R(-16.0) * J[4].r + R(2.0) * J[5].r; const R zi = R(64.0) * J[1].i + R(2.0) * J[2].i + R(20.0) * J[3].i + R(-16.0) * J[4].i + R(2.0) * J[5].i;
+      me = fma(J[1].r, zr, fma(J[1].i, zi, me)); }
+    { const R zr = R(64.0) * J[2].r + R(-16.0) * J[3].r + R(20.0) * J[4].r + R(2.0) * J[5].r; const R zi = R(64.0) * J[2].i + R(-16.0) * J[3].i + R(20.0) * J[4].i + R(2.0) * J[5].i;
+      me = fma(J[2].r, zr, fma(J[2].i, zi, me)); }
+    { const R zr = R(64.0) * J[3].r + R(2.0) * J[4].r + R(-16.0) * J[5].r; const R zi = R(64.0) * J[3].i + R(2.0) * J[4].i + R(-16.0) * J[5].i;
+      me = fma(J[3].r, zr, fma(J[3].i, zi, me)); }
+    { const R zr = R(64.0) * J[4].r + R(-16.0) * J[5].r; const R zi = R(64.0) * J[4].i + R(-16.0) * J[5].i;
+      me = fma(J[4].r, zr, fma(J[4].i, zi, me)); }
+    { const R zr = R(64.0) * J[5].r; const R zi = R(64.0) * J[5].i;
+      me = fma(J[5].r, zr, fma(J[5].i, zi, me)); }
     return me;
 #undef HEL
 }
 
 template <typename R>
-__device__ __noinline__ double me2_gg_ttg_impl(const double* pflat, double mt, double gs)
+__device__ __noinline__ double me2_gg_ttg_impl(const double* pflat, double mt, double gs, void* slot)
 {
     constexpr int NEXT = Me_gg_ttg::NEXT, NHEL = Me_gg_ttg::NHEL, NGLUON = Me_gg_ttg::NGLUON;
     constexpr double COLOUR_DEN = Me_gg_ttg::COLOUR_DEN, AVG = Me_gg_ttg::AVG, SYM = Me_gg_ttg::SYM;
     double p[NEXT][4];
     for (int i = 0; i < NEXT; ++i)
         for (int c = 0; c < 4; ++c) p[i][c] = pflat[4 * i + c];
-    Me_gg_ttg::Inv<R> v;
+    Me_gg_ttg::Inv<R> local;   // used when the caller has no shared-memory slot
+    Me_gg_ttg::Inv<R>& v = slot ? *static_cast<Me_gg_ttg::Inv<R>*>(slot) : local;
     // gluon momenta, incoming convention: gluons 0,1 incoming, the rest outgoing
     const double kd1[4] = {p[0][0], p[0][1], p[0][2], p[0][3]};
     const double kd2[4] = {p[1][0], p[1][1], p[1][2], p[1][3]};
@@ -167,10 +181,14 @@ __device__ __noinline__ double me2_gg_ttg_impl(const double* pflat, double mt, d
     const double kd5[4] = {kd1[0] + kd4[0], kd1[1] + kd4[1], kd1[2] + kd4[2], kd1[3] + kd4[3]};
     const double kd6[4] = {kd2[0] + kd4[0], kd2[1] + kd4[1], kd2[2] + kd4[2], kd2[3] + kd4[3]};
     const double kd7[4] = {kd1[0] + kd2[0] + kd4[0], kd1[1] + kd2[1] + kd4[1], kd1[2] + kd2[2] + kd4[2], kd1[3] + kd2[3] + kd4[3]};
-    for (int c = 0; c < 4; ++c) v.kr[0][c] = R(kd1[c]);
-    for (int c = 0; c < 4; ++c) v.kr[1][c] = R(kd2[c]);
-    for (int c = 0; c < 4; ++c) v.kr[2][c] = R(kd4[c]);
-    for (int c = 0; c < 4; ++c) v.p3r[c] = R(p[2][c]);
+    for (int c = 0; c < 4; ++c) v.K[0][c] = R(kd1[c]);
+    for (int c = 0; c < 4; ++c) v.K[1][c] = R(kd2[c]);
+    for (int c = 0; c < 4; ++c) v.K[2][c] = R(kd3[c]);
+    for (int c = 0; c < 4; ++c) v.K[3][c] = R(kd4[c]);
+    for (int c = 0; c < 4; ++c) v.K[4][c] = R(kd5[c]);
+    for (int c = 0; c < 4; ++c) v.K[5][c] = R(kd6[c]);
+    for (int c = 0; c < 4; ++c) v.K[6][c] = R(kd7[c]);
+    for (int c = 0; c < 4; ++c) v.p3[c] = R(p[2][c]);
     v.iG[0] = R(1.0 / mdot(kd3, kd3));
     v.iG[1] = R(1.0 / mdot(kd5, kd5));
     v.iG[2] = R(1.0 / mdot(kd6, kd6));
@@ -196,17 +214,21 @@ __device__ __noinline__ double me2_gg_ttg_impl(const double* pflat, double mt, d
     v.fb3 = fermion_basis<R>(p[2], mt);
     v.fb4 = fermion_basis<R>(p[3], mt);
     v.mt = R(mt);
+    // Parity: flipping every helicity leaves the colour-summed |M_h|^2 of these
+    // tree amplitudes unchanged, so the sum over all helicities is twice the
+    // sum over the configurations with the first gluon at helicity +1.
     R acc = R(0);
 #pragma unroll 1
-    for (int ih = 0; ih < NHEL; ++ih) acc += hel_gg_ttg<R>(v, ih);
+    for (int ih = 1; ih < NHEL; ih += 2) acc += hel_gg_ttg<R>(v, ih);
+    acc *= R(2);
     double gk = 1.0;
     for (int i = 0; i < NGLUON; ++i) gk *= gs * gs;
     return double(acc) / COLOUR_DEN * gk * AVG * SYM;
 }
 
 template <typename R>
-__device__ double Me_gg_ttg::me2(const double (&p)[NEXT][4], double mt, double gs)
+__device__ double Me_gg_ttg::me2(const double (&p)[NEXT][4], double mt, double gs, void* slot)
 {
-    return me2_gg_ttg_impl<R>(&p[0][0], mt, gs);
+    return me2_gg_ttg_impl<R>(&p[0][0], mt, gs, slot);
 }
 }  // namespace mf

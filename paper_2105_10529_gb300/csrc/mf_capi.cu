@@ -2,6 +2,7 @@
 #include <cuda_runtime.h>
 #include <cmath>
 #include <cstdio>
+#include <algorithm>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -254,7 +255,7 @@ int mf_create(mf_ctx** out, const mf_config* cfg, const double* pdf_grid_host, i
         return bail(MF_ERR_CUDA);
     for (int p : { MF_EE_MUMU, MF_GG_TT, MF_GG_TTG, MF_GG_TTGG }) {
         const ProcOps* o = proc_ops(p);
-        if (o->prepare(o->smem(MAX_BINS, nx * nq)) != cudaSuccess) return bail(MF_ERR_CUDA);
+        if (o->prepare(std::max(o->smem(0, MAX_BINS, nx * nq), o->smem(1, MAX_BINS, nx * nq))) != cudaSuccess) return bail(MF_ERR_CUDA);
     }
     *out = c;
     return MF_OK;
@@ -312,7 +313,7 @@ int mf_vegas_pass(mf_ctx* c, int process, double sqrt_s, const double* grid_dev,
         kp.ev_u = ev->u; kp.ev_x = ev->x; kp.ev_bins = ev->bins; kp.ev_w = ev->w;
         kp.ev_mask = ev->mask; kp.ev_me2 = ev->me2; kp.ev_p = ev->momenta;
     }
-    const size_t sm = ops->smem(c->cfg.n_bins, c->nx * c->nq);
+    const size_t sm = ops->smem(c->cfg.precision, c->cfg.n_bins, c->nx * c->nq);
     int nblk = 0;
     rc = pick_blocks(c, ops, sm, c->cfg.precision, &nblk);
     if (rc) return rc;
@@ -352,7 +353,7 @@ int mf_integrate(mf_ctx* c, int process, double sqrt_s, long long n_events, int 
     kp.ev_offset = 0;
     kp.inv_n = 1.0 / (double)n_events;
     kp.grid = c->d_grid;
-    const size_t sm = ops->smem(nb, c->nx * c->nq);
+    const size_t sm = ops->smem(c->cfg.precision, nb, c->nx * c->nq);
     int nblk = 0;
     rc = pick_blocks(c, ops, sm, c->cfg.precision, &nblk);
     if (rc) return rc;

@@ -8,7 +8,7 @@ namespace mf {
 
 struct ProcOps {
     int D, NEXT, npdf, tpb;
-    size_t (*smem)(int nb, int npv);
+    size_t (*smem)(int prec, int nb, int npv);
     cudaError_t (*prepare)(size_t smem);
     cudaError_t (*occupancy)(int prec, size_t smem, int* blocks_per_sm);
     cudaError_t (*integrand)(int prec, bool write, const KParams& kp, int nblk, size_t smem, cudaStream_t s);
@@ -24,8 +24,10 @@ const ProcOps* ops_gg_ttgg();
 // integrand launch helpers for a process trait P with TPB threads per CTA
 template <class P, int TPB>
 struct IntegrandOps {
-    using L = SmemLayout<P::D, TPB, P::NPDF>;
-    static size_t smem(int nb, int npv) { return L::bytes(nb, npv); }
+    static size_t smem(int prec, int nb, int npv)
+    {
+        return prec ? SmemLayout<P, float, TPB>::bytes(nb, npv) : SmemLayout<P, double, TPB>::bytes(nb, npv);
+    }
     template <typename R, bool W>
     static const void* fn() { return (const void*)integrand_kernel<P, R, TPB, W>; }
     static cudaError_t prepare(size_t sm)

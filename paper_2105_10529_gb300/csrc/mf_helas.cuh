@@ -84,6 +84,20 @@ template <typename R> struct FermionBasis { cx<R> chi[2][2]; R om[2]; };
 
 template <typename R> __device__ __forceinline__ cx<R> conjc(cx<R> a) { return mkc(a.r, -a.i); }
 
+// volatile read of a per-event invariant: re-read at every use instead of
+// being held in a register across the helicity body
+template <typename R> __device__ __forceinline__ R ldv(const R& x) { return *(const volatile R*)&x; }
+
+template <typename R> __device__ __forceinline__ FermionBasis<R> load_basis(const FermionBasis<R>& f)
+{
+    FermionBasis<R> o;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b) o.chi[a][b] = mkc(ldv(f.chi[a][b].r), ldv(f.chi[a][b].i));
+    o.om[0] = ldv(f.om[0]);
+    o.om[1] = ldv(f.om[1]);
+    return o;
+}
+
 template <typename R> __device__ __forceinline__ W4<R> ext_u(const FermionBasis<R>& f, int hel)
 {
     int l = hel > 0 ? 0 : 1;          // chi_l

@@ -84,6 +84,8 @@ struct MeEeMumu {
 
 struct ProcEe {
     static constexpr int NEXT = 4, NF = 2, D = 2, NPDF = 0;
+    static constexpr bool HEAVY = false;
+    template <typename R> static constexpr size_t slot_bytes() { return 0; }
 };
 
 template <class ME>
@@ -94,6 +96,11 @@ struct ProcTops {
     static constexpr int D = 2 + 4 * NF;
     static constexpr int NLIGHT = NF - 2;
     static constexpr int NPDF = 1;             // gluon grid only
+    // heavy matrix elements: PDF read through L1 instead of staged, one
+    // CTA-level histogram, and a shared-memory slot per thread for the
+    // matrix element's per-event invariants
+    static constexpr bool HEAVY = NEXT >= 5;
+    template <typename R> static constexpr size_t slot_bytes() { return HEAVY ? ME::template slot_bytes<R>() : 0; }
 };
 
 // per-event result
@@ -156,7 +163,8 @@ __device__ __forceinline__ int cuts_tops(const KParams& kp, const double (&pl)[P
 
 template <class P, typename R>
 __device__ __forceinline__ void event_tops(const KParams& kp, const double* sgrid, const double* spdf,
-                                           unsigned long long ev, EventOut<P::D>& o, double (&p)[P::NEXT][4])
+                                           unsigned long long ev, EventOut<P::D>& o, double (&p)[P::NEXT][4],
+                                           void* slot)
 {
     constexpr int NF = P::NF, D = P::D;
     event_uniforms<D>(ev, kp.iteration, kp.channel, kp.key, o.u);
@@ -212,22 +220,36 @@ __device__ __forceinline__ void event_tops(const KParams& kp, const double* sgri
     o.w = 0.0;
     // matrix element only for events that pass; the warp skips it when no lane needs it
     if (__any_sync(__activemask(), o.mask)) {
-        if (o.mask) o.me2 = P::Me::template me2<R>(p, kp.mt, kp.gs);
+        if (o.mask) o.me2 = P::Me::template me2<R>(p, kp.mt, kp.gs, slot);
     }
     if (o.mask) o.w = f1 * f2 * o.me2 / (2.0 * shat) * wps * jp * jv * GEV2_TO_PB;
 }
 
 // ------------------------------------------------------------------ shared-memory layout
 
-template <int D, int TPB, int NPDF>
+// Byte offsets of the kernel's dynamic shared memory:
+//   grid [D][nb+1] | PDF [nx nq] (light processes) | histograms | value buffer |
+//   bins buffer (heavy) | block-sum scratch | per-thread slots (heavy)
+// Light processes keep one histogram per warp (updated by bin leaders);
+// heavy ones keep one per CTA, filled by one thread per dimension in event
+// order after every round.
+template <class P, typename R, int TPB>
 struct SmemLayout {
     static constexpr int WARPS = TPB / 32;
-    __host__ __device__ static size_t grid_off() { return 0; }
-    __host__ __device__ static size_t pdf_off(int nb) { return ((size_t)D * (nb + 1) + 1) & ~(size_t)1; }
-    __host__ __device__ static size_t hist_off(int nb, int npdf_vals) { return pdf_off(nb) + (size_t)NPDF * npdf_vals; }
-    __host__ __device__ static size_t vbuf_off(int nb, int npdf_vals) { return hist_off(nb, npdf_vals) + (size_t)WARPS * D * nb; }
-    __host__ __device__ static size_t red_off(int nb, int npdf_vals) { return vbuf_off(nb, npdf_vals) + TPB; }
-    __host__ __device__ static size_t bytes(int nb, int npdf_vals) { return (red_off(nb, npdf_vals) + 2 * WARPS) * sizeof(double); }
+    static constexpr int D = P::D;
+    static constexpr int NHIST = P::HEAVY ? 1 : WARPS;
+    static __host__ __device__ size_t al(size_t x) { return (x + 15) & ~(size_t)15; }
+    static __host__ __device__ size_t grid_off() { return 0; }
+    static __host__ __device__ size_t pdf_off(int nb) { return al(grid_off() + sizeof(double) * D * (nb + 1)); }
+    static __host__ __device__ size_t hist_off(int nb, int npv)
+    {
+        return al(pdf_off(nb) + (P::HEAVY ? 0 : sizeof(double) * (size_t)P::NPDF * npv));
+    }
+    static __host__ __device__ size_t vbuf_off(int nb, int npv) { return al(hist_off(nb, npv) + sizeof(double) * NHIST * D * nb); }
+    static __host__ __device__ size_t bbuf_off(int nb, int npv) { return al(vbuf_off(nb, npv) + sizeof(double) * TPB); }
+    static __host__ __device__ size_t red_off(int nb, int npv) { return al(bbuf_off(nb, npv) + (P::HEAVY ? (size_t)TPB * D : 0)); }
+    static __host__ __device__ size_t slot_off(int nb, int npv) { return al(red_off(nb, npv) + sizeof(double) * 2 * WARPS); }
+    static __host__ __device__ size_t bytes(int nb, int npv) { return slot_off(nb, npv) + (size_t)TPB * P::template slot_bytes<R>(); }
 };
 
 // ------------------------------------------------------------------ the fused integrand kernel
@@ -237,23 +259,27 @@ __global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
 {
     constexpr int D = P::D;
     constexpr int WARPS = TPB / 32;
-    using L = SmemLayout<D, TPB, P::NPDF>;
-    extern __shared__ double smem[];
+    using L = SmemLayout<P, R, TPB>;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
     const int nb = kp.nb;
     const int npv = kp.pdfg.nx * kp.pdfg.nq;
-    double* sgrid = smem + L::grid_off();
-    double* spdf = smem + L::pdf_off(nb);
-    double* shist = smem + L::hist_off(nb, npv);
-    double* svbuf = smem + L::vbuf_off(nb, npv);
-    double* sred = smem + L::red_off(nb, npv);
+    double* sgrid = reinterpret_cast<double*>(smem_raw + L::grid_off());
+    double* spdf = P::HEAVY ? const_cast<double*>(kp.pdf) : reinterpret_cast<double*>(smem_raw + L::pdf_off(nb));
+    double* shist = reinterpret_cast<double*>(smem_raw + L::hist_off(nb, npv));
+    double* svbuf = reinterpret_cast<double*>(smem_raw + L::vbuf_off(nb, npv));
+    uint8_t* sbins = smem_raw + L::bbuf_off(nb, npv);
+    double* sred = reinterpret_cast<double*>(smem_raw + L::red_off(nb, npv));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    void* slot = P::template slot_bytes<R>() ? (void*)(smem_raw + L::slot_off(nb, npv) + (size_t)tid * P::template slot_bytes<R>())
+                                             : nullptr;
 
     for (int i = tid; i < D * (nb + 1); i += TPB) sgrid[i] = kp.grid[i];
-    for (int i = tid; i < P::NPDF * npv; i += TPB) spdf[i] = kp.pdf[i];
-    for (int i = tid; i < WARPS * D * nb; i += TPB) shist[i] = 0.0;
+    if (!P::HEAVY)
+        for (int i = tid; i < P::NPDF * npv; i += TPB) spdf[i] = kp.pdf[i];
+    for (int i = tid; i < L::NHIST * D * nb; i += TPB) shist[i] = 0.0;
     __syncthreads();
 
-    double* myhist = shist + warp * D * nb;
+    double* myhist = shist + (P::HEAVY ? 0 : warp * D * nb);
     double sw = 0.0, sw2 = 0.0;
     unsigned long long npass = 0, nnan = 0;
     const long long n = kp.n_events;
@@ -270,7 +296,7 @@ __global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
         if (valid) {
             const unsigned long long ev = (unsigned long long)(kp.ev_offset + e);
             if constexpr (P::NPDF == 0) event_ee<R>(kp, sgrid, ev, o, pm);
-            else event_tops<P, R>(kp, sgrid, spdf, ev, o, pm);
+            else event_tops<P, R>(kp, sgrid, spdf, ev, o, pm, slot);
             if (!isfinite(o.w)) { o.w = 0.0; ++nnan; }
             npass += o.mask ? 1 : 0;
             if constexpr (WRITE) {
@@ -291,20 +317,32 @@ __global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
         const double v = wn * wn;
         sw += wn;
         sw2 += v;
-        // deterministic per-warp histogram: one leader per distinct bin sums its
-        // peers' values in lane order
         svbuf[tid] = v;
-        __syncwarp();
+        if constexpr (P::HEAVY) {
+            // CTA histogram: thread d adds the round's events to dimension d in event order
 #pragma unroll
-        for (int d = 0; d < D; ++d) {
-            const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)o.bins[d]);
-            if (lane == __ffs(peers) - 1) {
-                double s = 0.0;
-                for (unsigned m = peers; m; m &= m - 1) s += svbuf[warp * 32 + __ffs(m) - 1];
-                myhist[d * nb + o.bins[d]] += s;
+            for (int d = 0; d < D; ++d) sbins[d * TPB + tid] = o.bins[d];
+            __syncthreads();
+            if (tid < D) {
+                double* h = shist + tid * nb;
+                const uint8_t* b = sbins + tid * TPB;
+                for (int t = 0; t < TPB; ++t) h[b[t]] += svbuf[t];
             }
+            __syncthreads();
+        } else {
+            // per-warp histogram: one leader per distinct bin sums its peers in lane order
+            __syncwarp();
+#pragma unroll
+            for (int d = 0; d < D; ++d) {
+                const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)o.bins[d]);
+                if (lane == __ffs(peers) - 1) {
+                    double s = 0.0;
+                    for (unsigned m = peers; m; m &= m - 1) s += svbuf[warp * 32 + __ffs(m) - 1];
+                    myhist[d * nb + o.bins[d]] += s;
+                }
+            }
+            __syncwarp();
         }
-        __syncwarp();
     }
 
     // block reduction of the two sums: warp trees, then warps in order
@@ -333,7 +371,7 @@ __global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
     }
     for (int i = tid; i < D * nb; i += TPB) {
         double s = 0.0;
-        for (int w = 0; w < WARPS; ++w) s += shist[w * D * nb + i];
+        for (int w = 0; w < L::NHIST; ++w) s += shist[w * D * nb + i];
         out[2 + i] = s;
     }
 }
@@ -344,11 +382,13 @@ template <class ME, typename R>
 __global__ void __launch_bounds__(128) evaluate_kernel(const double* __restrict__ mom, long long n, double* __restrict__ me2,
                                                        double mt, double gs)
 {
+    extern __shared__ __align__(16) unsigned char slots[];
+    void* slot = slots + (size_t)threadIdx.x * ME::template slot_bytes<R>();
     for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
         double p[ME::NEXT][4];
         for (int i = 0; i < ME::NEXT; ++i)
             for (int c = 0; c < 4; ++c) p[i][c] = mom[(e * ME::NEXT + i) * 4 + c];
-        me2[e] = ME::template me2<R>(p, mt, gs);
+        me2[e] = ME::template me2<R>(p, mt, gs, slot);
     }
 }
 

@@ -11,8 +11,15 @@ using I = IntegrandOps<P, 128>;
 cudaError_t evaluate(int prec, const double* mom, long long n, double* me2, double mt, double gs, const EwParams&,
                      int nblk, cudaStream_t s)
 {
-    if (prec) evaluate_kernel<Me_gg_ttgg, float><<<nblk, 128, 0, s>>>(mom, n, me2, mt, gs);
-    else evaluate_kernel<Me_gg_ttgg, double><<<nblk, 128, 0, s>>>(mom, n, me2, mt, gs);
+    const size_t s32 = 128 * Me_gg_ttgg::slot_bytes<float>(), s64 = 128 * Me_gg_ttgg::slot_bytes<double>();
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute((const void*)evaluate_kernel<Me_gg_ttgg, float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32);
+        cudaFuncSetAttribute((const void*)evaluate_kernel<Me_gg_ttgg, double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64);
+        attr = true;
+    }
+    if (prec) evaluate_kernel<Me_gg_ttgg, float><<<nblk, 128, s32, s>>>(mom, n, me2, mt, gs);
+    else evaluate_kernel<Me_gg_ttgg, double><<<nblk, 128, s64, s>>>(mom, n, me2, mt, gs);
     return cudaGetLastError();
 }
 

@@ -194,6 +194,7 @@ class Emitter:
         self.kvars = set()       # gluon subsets whose momentum (R) is needed
         self.gden = set()        # gluon subsets whose 1/K^2 is needed
         self.qsub = set()        # quark propagator subsets (absorbed from the ubar side)
+        self.kmasks = set()      # gluon subsets whose momentum is read in the body
         self.counts = dict(vvv=0, vvvv=0, ffv_row=0, ffv_col=0, ffv_amp=0, vvv_amp=0, vvvv_amp=0, ffv_cur=0)
 
     @staticmethod
@@ -205,20 +206,21 @@ class Emitter:
         return f"w{self.n_w}"
 
     def mom(self, m: int) -> str:
-        """R-typed momentum sum of the gluons in mask m, built at its point of use."""
+        """R-typed momentum of the gluons in mask m, loaded from the per-event
+        slot at its point of use (a volatile load, so it is not kept live)."""
         self.n_w += 1
+        self.kmasks.add(m)
         v = f"k{m}_{self.n_w}"
-        bits = [i for i in range(self.k) if m >> i & 1]
-        comps = ", ".join(" + ".join(f"kr{b}[{c}]" for b in bits) for c in range(4))
+        comps = ", ".join(f"ldv(v.K[@K{m}@][{c}])" for c in range(4))
         self.lines.append(f"const R {v}[4] = {{{comps}}};")
         return v
 
     def qmom(self, m: int) -> str:
-        """R-typed quark propagator momentum p3 - K(mask m), built at its point of use."""
+        """R-typed quark propagator momentum p3 - K(mask m) at its point of use."""
         self.n_w += 1
+        self.kmasks.add(m)
         v = f"q{m}_{self.n_w}"
-        bits = [i for i in range(self.k) if m >> i & 1]
-        comps = ", ".join("p3r[%d] - (%s)" % (c, " + ".join(f"kr{b}[{c}]" for b in bits)) for c in range(4))
+        comps = ", ".join(f"ldv(v.p3[{c}]) - ldv(v.K[@K{m}@][{c}])" for c in range(4))
         self.lines.append(f"const R {v}[4] = {{{comps}}};")
         return v
 
@@ -505,20 +507,22 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     gidx = {m: i for i, m in enumerate(gden)}
     qidx = {m: i for i, m in enumerate(qsub)}
 
-    # prologue: helicity-independent pieces, FP64 arithmetic, stored as R
+    kmasks = sorted(em.kmasks)
+    kidx = {m: i for i, m in enumerate(kmasks)}
+    # prologue: helicity-independent pieces, FP64 arithmetic, stored as R in the slot
     pro: List[str] = []
     pro.append("// gluon momenta, incoming convention: gluons 0,1 incoming, the rest outgoing")
     for i, e in enumerate(gl_ext):
         sgn = "" if i < n_in else "-"
         pro.append(f"const double kd{1 << i}[4] = {{{sgn}p[{e}][0], {sgn}p[{e}][1], {sgn}p[{e}][2], {sgn}p[{e}][3]}};")
-    needed_sums = {m for m in set(gden) | set(qsub) if bin(m).count("1") > 1}
+    needed_sums = {m for m in set(gden) | set(qsub) | set(kmasks) if bin(m).count("1") > 1}
     for m in sorted(needed_sums, key=lambda x: (bin(x).count("1"), x)):
         bits = [1 << i for i in range(k) if m >> i & 1]
         comps = ", ".join(" + ".join(f"kd{b}[{c}]" for b in bits) for c in range(4))
         pro.append(f"const double kd{m}[4] = {{{comps}}};")
-    for i in range(k):
-        pro.append(f"for (int c = 0; c < 4; ++c) v.kr[{i}][c] = R(kd{1 << i}[c]);")
-    pro.append("for (int c = 0; c < 4; ++c) v.p3r[c] = R(p[2][c]);")
+    for m in kmasks:
+        pro.append(f"for (int c = 0; c < 4; ++c) v.K[{kidx[m]}][c] = R(kd{m}[c]);")
+    pro.append("for (int c = 0; c < 4; ++c) v.p3[c] = R(p[2][c]);")
     for m in gden:
         pro.append(f"v.iG[{gidx[m]}] = R(1.0 / mdot(kd{m}, kd{m}));")
     for m in qsub:
@@ -534,35 +538,40 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     import re as _re
 
     def subst(line: str) -> str:
-        line = _re.sub(r"\biG(\d+)\b", lambda mm: f"v.iG[{gidx[int(mm.group(1))]}]", line)
-        line = _re.sub(r"\biQ(\d+)\b", lambda mm: f"v.iQ[{qidx[int(mm.group(1))]}]", line)
-        line = _re.sub(r"\bkr(\d+)\[", lambda mm: f"v.kr[{mm.group(1)}][", line)
-        line = line.replace("p3r[", "v.p3r[").replace(", mt, ", ", v.mt, ")
+        line = _re.sub(r"\biG(\d+)\b", lambda mm: f"ldv(v.iG[{gidx[int(mm.group(1))]}])", line)
+        line = _re.sub(r"\biQ(\d+)\b", lambda mm: f"ldv(v.iQ[{qidx[int(mm.group(1))]}])", line)
+        line = _re.sub(r"@K(\d+)@", lambda mm: str(kidx[int(mm.group(1))]), line)
+        line = line.replace(", mt, ", ", ldv(v.mt), ")
         return line
 
     body: List[str] = []
-    body.append("cx<R> jamp[NCOL];")
+    body.append("// colour-flow amplitudes accumulate in the slot (shared memory), not in registers")
+    body.append("volatile cx<R>* jamp = reinterpret_cast<volatile cx<R>*>(const_cast<cx<R>*>(v.jamp));")
     body.append("#pragma unroll")
-    body.append("for (int c = 0; c < NCOL; ++c) jamp[c] = mkc(R(0), R(0));")
+    body.append("for (int c = 0; c < NCOL; ++c) { jamp[c].r = R(0); jamp[c].i = R(0); }")
     for i, e in enumerate(gl_ext):
         out = "false" if i < n_in else "true"
-        body.append(f"const W4<R> g{i} = ext_gluon(v.e1[{i}], v.e2[{i}], HEL({e}), {out});")
-    body.append("const W4<R> ub3 = ext_ubar(v.fb3, HEL(2));")
-    body.append("const W4<R> v4 = ext_v(v.fb4, HEL(3));")
+        body.append(f"W4<R> g{i}; {{ R a[3], b[3]; for (int j = 0; j < 3; ++j) {{ a[j] = ldv(v.e1[{i}][j]); b[j] = ldv(v.e2[{i}][j]); }}")
+        body.append(f"  g{i} = ext_gluon(a, b, HEL({e}), {out}); }}")
+    body.append("const W4<R> ub3 = ext_ubar(load_basis(v.fb3), HEL(2));")
+    body.append("const W4<R> v4 = ext_v(load_basis(v.fb4), HEL(3));")
     body.extend(subst(l) for l in em.lines)
 
     # colour sum, symmetric form: sum_ij C_ij J_i J_j = sum_i J_i (C_ii J_i + 2 sum_{j>i} C_ij J_j)
     cs: List[str] = []
+    cs.append("cx<R> J[NCOL];")
+    cs.append("#pragma unroll")
+    cs.append("for (int c = 0; c < NCOL; ++c) J[c] = mkc(R(jamp[c].r), R(jamp[c].i));")
     cs.append("R me = R(0);")
     for i in range(ncol):
-        tr = [f"R({float(CI[i][i])!r}) * jamp[{i}].r"]
-        ti = [f"R({float(CI[i][i])!r}) * jamp[{i}].i"]
+        tr = [f"R({float(CI[i][i])!r}) * J[{i}].r"]
+        ti = [f"R({float(CI[i][i])!r}) * J[{i}].i"]
         for j in range(i + 1, ncol):
             if CI[i][j] != 0:
-                tr.append(f"R({float(2 * CI[i][j])!r}) * jamp[{j}].r")
-                ti.append(f"R({float(2 * CI[i][j])!r}) * jamp[{j}].i")
+                tr.append(f"R({float(2 * CI[i][j])!r}) * J[{j}].r")
+                ti.append(f"R({float(2 * CI[i][j])!r}) * J[{j}].i")
         cs.append(f"{{ const R zr = {' + '.join(tr)}; const R zi = {' + '.join(ti)};")
-        cs.append(f"  me = fma(jamp[{i}].r, zr, fma(jamp[{i}].i, zi, me)); }}")
+        cs.append(f"  me = fma(J[{i}].r, zr, fma(J[{i}].i, zi, me)); }}")
     cs.append("return me;")
 
     n_diag = count_feynman_diagrams(k)
@@ -584,14 +593,22 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append(f"  static constexpr double AVG = 1.0 / 256.0;")
     src.append(f"  static constexpr double SYM = {float(sym)!r};")
     src.append("  // helicity-independent per-event pieces")
+    n_words = 4 * len(kmasks) + 4 + max(1, len(gden)) + max(1, len(qsub)) + 6 * k + 20 + 1 + 2 * ncol
+    pad = 1 if n_words % 2 == 0 else 2   # odd number of 32-bit words per slot: conflict-free in shared memory
+    src.append("  // per-thread slot: internal momenta, FP64-computed inverse denominators,")
+    src.append("  // polarisation bases and spinor pieces of the event (kept in shared memory)")
     src.append("  template <typename R> struct Inv {")
-    src.append(f"    R kr[{k}][4]; R p3r[4]; R iG[{max(1, len(gden))}]; R iQ[{max(1, len(qsub))}];")
+    src.append(f"    R K[{len(kmasks)}][4]; R p3[4]; R iG[{max(1, len(gden))}]; R iQ[{max(1, len(qsub))}];")
     src.append(f"    R e1[{k}][3]; R e2[{k}][3]; FermionBasis<R> fb3, fb4; R mt;")
+    src.append(f"    cx<R> jamp[{ncol}];   // colour-flow amplitudes of the helicity being summed")
+    src.append(f"    float pad[{pad}];")
     src.append("  };")
     src.append("  // averaged |M|^2 (spin/colour average and identical-particle factor included);")
     src.append("  // p: momenta (E,px,py,pz) incoming first: g, g, t, tbar, g...")
+    src.append("  // slot: this thread's Inv<R> in shared memory, or null for a private local copy")
     src.append("  template <typename R>")
-    src.append("  __device__ static double me2(const double (&p)[NEXT][4], double mt, double gs);")
+    src.append("  __device__ static double me2(const double (&p)[NEXT][4], double mt, double gs, void* slot);")
+    src.append("  template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }")
     src.append("};")
     src.append("")
     src.append("// one helicity configuration: amplitudes, colour flows and the colour sum;")
@@ -609,34 +626,41 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("}")
     src.append("")
     src.append("template <typename R>")
-    src.append(f"__device__ __noinline__ double me2_{name}_impl(const double* pflat, double mt, double gs)")
+    src.append(f"__device__ __noinline__ double me2_{name}_impl(const double* pflat, double mt, double gs, void* slot)")
     src.append("{")
     src.append(f"    constexpr int NEXT = Me_{name}::NEXT, NHEL = Me_{name}::NHEL, NGLUON = Me_{name}::NGLUON;")
     src.append(f"    constexpr double COLOUR_DEN = Me_{name}::COLOUR_DEN, AVG = Me_{name}::AVG, SYM = Me_{name}::SYM;")
     src.append("    double p[NEXT][4];")
     src.append("    for (int i = 0; i < NEXT; ++i)")
     src.append("        for (int c = 0; c < 4; ++c) p[i][c] = pflat[4 * i + c];")
-    src.append(f"    Me_{name}::Inv<R> v;")
+    src.append(f"    Me_{name}::Inv<R> local;   // used when the caller has no shared-memory slot")
+    src.append(f"    Me_{name}::Inv<R>& v = slot ? *static_cast<Me_{name}::Inv<R>*>(slot) : local;")
     for l in pro:
         src.append("    " + l)
+    src.append("    // Parity: flipping every helicity leaves the colour-summed |M_h|^2 of these")
+    src.append("    // tree amplitudes unchanged, so the sum over all helicities is twice the")
+    src.append("    // sum over the configurations with the first gluon at helicity +1.")
     src.append("    R acc = R(0);")
     src.append("#pragma unroll 1")
-    src.append("    for (int ih = 0; ih < NHEL; ++ih) acc += hel_" + name + "<R>(v, ih);")
+    src.append("    for (int ih = 1; ih < NHEL; ih += 2) acc += hel_" + name + "<R>(v, ih);")
+    src.append("    acc *= R(2);")
     src.append("    double gk = 1.0;")
     src.append("    for (int i = 0; i < NGLUON; ++i) gk *= gs * gs;")
     src.append("    return double(acc) / COLOUR_DEN * gk * AVG * SYM;")
     src.append("}")
     src.append("")
     src.append("template <typename R>")
-    src.append(f"__device__ double Me_{name}::me2(const double (&p)[NEXT][4], double mt, double gs)")
+    src.append(f"__device__ double Me_{name}::me2(const double (&p)[NEXT][4], double mt, double gs, void* slot)")
     src.append("{")
-    src.append(f"    return me2_{name}_impl<R>(&p[0][0], mt, gs);")
+    src.append(f"    return me2_{name}_impl<R>(&p[0][0], mt, gs, slot);")
     src.append("}")
     src.append("}  // namespace mf")
     stats = dict(n_diag=n_diag, n_amp=len(diags), ncol=ncol, counts=dict(em.counts), colour_den=den)
     stats["flops_per_helicity"] = helicity_flops(em, ncol, CI)
     stats["n_hel"] = 1 << n_ext
-    stats["flops_me"] = stats["flops_per_helicity"] * stats["n_hel"]
+    # parity halves the helicity configurations evaluated
+    stats["flops_me"] = stats["flops_per_helicity"] * stats["n_hel"] // 2
+    stats["flops_me_all_helicities"] = stats["flops_per_helicity"] * stats["n_hel"]
     return "\n".join(src) + "\n", stats
 
 

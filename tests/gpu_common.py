@@ -91,4 +91,5 @@ def assert_fp_parity(err, prec, what=""):
     frac_bad = float(np.mean(err > 1e-12))
     assert frac_bad <= 5e-3 or int(np.sum(err > 1e-12)) <= 1, (what, frac_bad, err.max())
     assert err.max() < 1e-10, (what, err.max(), int(np.argmax(err)))
-    assert np.median(err) < 1e-14, (what, np.median(err))
+    if err.size >= 100:
+        assert np.median(err) < 1e-14, (what, np.median(err))
