@@ -153,6 +153,27 @@ int mf_vegas_pass(struct mf_ctx *ctx, int process, double sqrt_s, const double *
  * Does not synchronise. */
 int mf_vegas_refine(struct mf_ctx *ctx, int dim, int n_bins, double alpha, const double *sums_dev, double *grid_dev);
 
+/* One VEGAS pass like mf_vegas_pass, for callers that cannot allocate GPU
+ * memory (no context is created and nothing is allocated).  The paper has
+ * no counterpart: this exists for hosts that own all device memory and
+ * forbid allocation in their callbacks, or that must not let a call
+ * synchronise the device as cudaMalloc may.
+ * Inputs: cfg (host), pdf_dev [n_flav][nx][nq] and grid_dev [dim][n_bins+1]
+ * (device, caller-owned, same meaning as for mf_create / mf_vegas_pass).
+ * Output: sums_dev [2 + dim n_bins] (device): sum w, sum w^2, histogram.
+ * Scratch: a fixed 4 MiB array inside the library (the per-CTA partial
+ * sums and two counters), held by every GPU that loads the library until the
+ * process exits.  The first call on a device looks up that array's device
+ * address; make that first call before any stream capture.  Every call
+ * shares the array and overwrites it, so calls whose work overlaps on the GPU
+ * (other streams, other host threads) race: serialise them.  Sizes whose
+ * partial sums do not fit (2 + dim n_bins doubles per CTA) return MF_ERR_ARG;
+ * other errors as for mf_vegas_pass.  stream: cudaStream_t or NULL.  Does not
+ * synchronise. */
+int mf_vegas_pass_static(int process, const mf_config *cfg, double sqrt_s, const double *pdf_dev, int n_flav, int nx,
+                         int nq, double x_min, double q2_min, double q2_max, const double *grid_dev, long long n_events,
+                         long long ev_offset, unsigned int iteration, double *sums_dev, void *stream);
+
 /* evaluate (Sec. 2.2): spin- and colour-averaged |M|^2 (identical-particle
  * factor included) of n phase-space points.  momenta_dev: [n][n_ext][4];
  * me2_dev: [n].  Does not synchronise. */

@@ -66,6 +66,8 @@ def lib():
                                         C.POINTER(MfEventArrays)]),
             "mf_vegas_refine": (C.c_int, [vp, C.c_int, C.c_int, C.c_double, vp, vp]),
             "mf_evaluate": (C.c_int, [vp, C.c_int, vp, i64, vp]),
+            "mf_vegas_pass_static": (C.c_int, [C.c_int, C.POINTER(MfConfig), C.c_double, vp, C.c_int, C.c_int, C.c_int,
+                                               C.c_double, C.c_double, C.c_double, vp, i64, i64, C.c_uint, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -77,4 +79,5 @@ def lib():
 
 def exported_symbols():
     return ["mf_default_config", "mf_process_info", "mf_create", "mf_destroy", "mf_last_error",
-            "mf_set_precision", "mf_set_pdf", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate"]
+            "mf_set_precision", "mf_set_pdf", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
+            "mf_vegas_pass_static"]
