@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--events", type=int, default=4_000_000)
     ap.add_argument("--fp64-events", type=int, default=200_000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
+    ap.add_argument("--sched", type=int, default=None, help="integrand schedule (0 free warps, 1 CTA barrier per helicity)")
     ap.add_argument("--only-timed", action="store_true",
                     help="run only the warm-up and timed mixed-precision steps (for profiler captures)")
     return ap.parse_args()
@@ -174,6 +175,8 @@ def run_ours(args):
     N = args.events
     stream = torch.cuda.current_stream()
     ctx = Context(phys, pdf, precision=MF_MIXED, stream=stream)
+    if args.sched is not None:
+        ctx.set_schedule(args.sched)
     dev = torch.device("cuda", local)
     grid = torch.linspace(0, 1, nb + 1, dtype=torch.float64, device=dev).repeat(dim, 1).contiguous()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)

@@ -123,6 +123,11 @@ int mf_create(struct mf_ctx **out, const mf_config *cfg, const double *pdf_grid_
 void mf_destroy(struct mf_ctx *ctx);
 const char *mf_last_error(const struct mf_ctx *ctx);
 int mf_set_precision(struct mf_ctx *ctx, int precision);
+/* Integrand schedule for the heavy processes (gg -> t tbar g, gg -> t tbar g g):
+ * 0 = warps run freely through the helicity sum, 1 = a CTA barrier after every
+ * helicity keeps the CTA's warps on the same instructions (the default).
+ * Results do not depend on it.  MF_ERR_ARG for other values. */
+int mf_set_schedule(struct mf_ctx *ctx, int sched);
 /* Replace the PDF grid (same shape as at creation) by a host copy. */
 int mf_set_pdf(struct mf_ctx *ctx, const double *pdf_grid_host);
 

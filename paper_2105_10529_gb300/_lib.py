@@ -61,6 +61,7 @@ def lib():
             "mf_last_error": (C.c_char_p, [vp]),
             "mf_set_precision": (C.c_int, [vp, C.c_int]),
             "mf_set_pdf": (C.c_int, [vp, dp]),
+            "mf_set_schedule": (C.c_int, [vp, C.c_int]),
             "mf_integrate": (C.c_int, [vp, C.c_int, C.c_double, i64, C.c_int, C.POINTER(MfResult), dp, dp]),
             "mf_vegas_pass": (C.c_int, [vp, C.c_int, C.c_double, vp, i64, i64, C.c_uint, vp, vp,
                                         C.POINTER(MfEventArrays)]),
@@ -79,5 +80,5 @@ def lib():
 
 def exported_symbols():
     return ["mf_default_config", "mf_process_info", "mf_create", "mf_destroy", "mf_last_error",
-            "mf_set_precision", "mf_set_pdf", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
+            "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
             "mf_vegas_pass_static"]

@@ -80,6 +80,9 @@ class Context:
     def set_precision(self, precision: int):
         _check(self.ptr, _lib.lib().mf_set_precision(self.ptr, precision))
 
+    def set_schedule(self, sched: int):
+        _check(self.ptr, _lib.lib().mf_set_schedule(self.ptr, sched))
+
     def set_pdf(self, grid_host: np.ndarray):
         """Upload a host PDF grid (same shape as at creation); asynchronous on the stream."""
         g = np.ascontiguousarray(grid_host, dtype=np.float64)

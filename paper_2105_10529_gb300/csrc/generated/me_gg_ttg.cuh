@@ -26,7 +26,8 @@ struct Me_gg_ttg {
   // averaged |M|^2 (spin/colour average and identical-particle factor included);
   // p: momenta (E,px,py,pz) incoming first: g, g, t, tbar, g...
   // slot: this thread's Inv<R> in shared memory, or null for a private local copy
-  template <typename R>
+  // SYNC: a CTA barrier after every helicity (every thread of the CTA must call)
+  template <typename R, bool SYNC = false>
   __device__ static double me2(const double (&p)[NEXT][4], double mt, double gs, void* slot);
   template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }
 };
@@ -163,7 +164,7 @@ __device__ __noinline__ R hel_gg_ttg(const Me_gg_ttg::Inv<R>& v, int ih)
 #undef HEL
 }
 
-template <typename R>
+template <typename R, bool SYNC>
 __device__ __noinline__ double me2_gg_ttg_impl(const double* pflat, double mt, double gs, void* slot)
 {
     constexpr int NEXT = Me_gg_ttg::NEXT, NHEL = Me_gg_ttg::NHEL, NGLUON = Me_gg_ttg::NGLUON;
@@ -219,16 +220,19 @@ __device__ __noinline__ double me2_gg_ttg_impl(const double* pflat, double mt, d
     // sum over the configurations with the first gluon at helicity +1.
     R acc = R(0);
 #pragma unroll 1
-    for (int ih = 1; ih < NHEL; ih += 2) acc += hel_gg_ttg<R>(v, ih);
+    for (int ih = 1; ih < NHEL; ih += 2) {
+        acc += hel_gg_ttg<R>(v, ih);
+        if (SYNC) __syncthreads();
+    }
     acc *= R(2);
     double gk = 1.0;
     for (int i = 0; i < NGLUON; ++i) gk *= gs * gs;
     return double(acc) / COLOUR_DEN * gk * AVG * SYM;
 }
 
-template <typename R>
+template <typename R, bool SYNC>
 __device__ double Me_gg_ttg::me2(const double (&p)[NEXT][4], double mt, double gs, void* slot)
 {
-    return me2_gg_ttg_impl<R>(&p[0][0], mt, gs, slot);
+    return me2_gg_ttg_impl<R, SYNC>(&p[0][0], mt, gs, slot);
 }
 }  // namespace mf

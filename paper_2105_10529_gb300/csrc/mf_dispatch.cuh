@@ -11,7 +11,8 @@ struct ProcOps {
     size_t (*smem)(int prec, int nb, int npv);
     cudaError_t (*prepare)(size_t smem);
     cudaError_t (*occupancy)(int prec, size_t smem, int* blocks_per_sm);
-    cudaError_t (*integrand)(int prec, bool write, const KParams& kp, int nblk, size_t smem, cudaStream_t s);
+    // sched: 0 free-running warps, 1 CTA barrier between helicities (heavy processes)
+    cudaError_t (*integrand)(int prec, bool write, int sched, const KParams& kp, int nblk, size_t smem, cudaStream_t s);
     cudaError_t (*evaluate)(int prec, const double* mom, long long n, double* me2, double mt, double gs,
                             const EwParams& ew, int nblk, cudaStream_t s);
 };
@@ -28,11 +29,14 @@ struct IntegrandOps {
     {
         return prec ? SmemLayout<P, float, TPB>::bytes(nb, npv) : SmemLayout<P, double, TPB>::bytes(nb, npv);
     }
-    template <typename R, bool W>
-    static const void* fn() { return (const void*)integrand_kernel<P, R, TPB, W>; }
+    static constexpr bool HS = P::HEAVY;   // the barrier variant exists for heavy processes only
+    template <typename R, bool W, bool S>
+    static const void* fn() { return (const void*)integrand_kernel<P, R, TPB, W, S && HS>; }
     static cudaError_t prepare(size_t sm)
     {
-        const void* fns[4] = { fn<double, false>(), fn<double, true>(), fn<float, false>(), fn<float, true>() };
+        const void* fns[8] = { fn<double, false, false>(), fn<double, true, false>(), fn<float, false, false>(),
+                               fn<float, true, false>(), fn<double, false, true>(), fn<double, true, true>(),
+                               fn<float, false, true>(), fn<float, true, true>() };
         for (const void* f : fns) {
             cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
@@ -41,16 +45,23 @@ struct IntegrandOps {
     }
     static cudaError_t occupancy(int prec, size_t sm, int* b)
     {
-        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, prec ? fn<float, false>() : fn<double, false>(), TPB, sm);
+        return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, prec ? fn<float, false, false>() : fn<double, false, false>(),
+                                                             TPB, sm);
     }
-    static cudaError_t integrand(int prec, bool write, const KParams& kp, int nblk, size_t sm, cudaStream_t s)
+    template <typename R, bool W>
+    static void launch(int sched, const KParams& kp, int nblk, size_t sm, cudaStream_t s)
+    {
+        if (sched && HS) integrand_kernel<P, R, TPB, W, HS><<<nblk, TPB, sm, s>>>(kp);
+        else integrand_kernel<P, R, TPB, W, false><<<nblk, TPB, sm, s>>>(kp);
+    }
+    static cudaError_t integrand(int prec, bool write, int sched, const KParams& kp, int nblk, size_t sm, cudaStream_t s)
     {
         if (prec) {
-            if (write) integrand_kernel<P, float, TPB, true><<<nblk, TPB, sm, s>>>(kp);
-            else integrand_kernel<P, float, TPB, false><<<nblk, TPB, sm, s>>>(kp);
+            if (write) launch<float, true>(sched, kp, nblk, sm, s);
+            else launch<float, false>(sched, kp, nblk, sm, s);
         } else {
-            if (write) integrand_kernel<P, double, TPB, true><<<nblk, TPB, sm, s>>>(kp);
-            else integrand_kernel<P, double, TPB, false><<<nblk, TPB, sm, s>>>(kp);
+            if (write) launch<double, true>(sched, kp, nblk, sm, s);
+            else launch<double, false>(sched, kp, nblk, sm, s);
         }
         return cudaGetLastError();
     }

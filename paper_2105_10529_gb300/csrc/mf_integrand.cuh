@@ -161,10 +161,14 @@ __device__ __forceinline__ int cuts_tops(const KParams& kp, const double (&pl)[P
     return ok;
 }
 
-template <class P, typename R>
-__device__ __forceinline__ void event_tops(const KParams& kp, const double* sgrid, const double* spdf,
-                                           unsigned long long ev, EventOut<P::D>& o, double (&p)[P::NEXT][4],
-                                           void* slot)
+// Everything of one event except the matrix element: uniforms, VEGAS map,
+// parton map, RAMBO, lab boost, cuts, scale and PDFs.  pref receives the
+// weight factor that multiplies |M|^2: f1 f2 / (2 shat) W J_parton J_VEGAS
+// in pb GeV^2.
+template <class P>
+__device__ __forceinline__ void kinematics_tops(const KParams& kp, const double* sgrid, const double* spdf,
+                                                unsigned long long ev, EventOut<P::D>& o, double (&p)[P::NEXT][4],
+                                                double& pref)
 {
     constexpr int NF = P::NF, D = P::D;
     event_uniforms<D>(ev, kp.iteration, kp.channel, kp.key, o.u);
@@ -216,20 +220,31 @@ __device__ __forceinline__ void event_tops(const KParams& kp, const double* sgri
     }
     const double f1 = pdf_xf(spdf, kp.pdfg, x1, muf2) / x1;
     const double f2 = pdf_xf(spdf, kp.pdfg, x2, muf2) / x2;
+    pref = f1 * f2 / (2.0 * shat) * wps * jp * jv * GEV2_TO_PB;
     o.me2 = 0.0;
     o.w = 0.0;
+}
+
+template <class P, typename R>
+__device__ __forceinline__ void event_tops(const KParams& kp, const double* sgrid, const double* spdf,
+                                           unsigned long long ev, EventOut<P::D>& o, double (&p)[P::NEXT][4],
+                                           void* slot)
+{
+    double pref;
+    kinematics_tops<P>(kp, sgrid, spdf, ev, o, p, pref);
     // matrix element only for events that pass; the warp skips it when no lane needs it
     if (__any_sync(__activemask(), o.mask)) {
         if (o.mask) o.me2 = P::Me::template me2<R>(p, kp.mt, kp.gs, slot);
     }
-    if (o.mask) o.w = f1 * f2 * o.me2 / (2.0 * shat) * wps * jp * jv * GEV2_TO_PB;
+    if (o.mask) o.w = pref * o.me2;
 }
 
 // ------------------------------------------------------------------ shared-memory layout
 
 // Byte offsets of the kernel's dynamic shared memory:
 //   grid [D][nb+1] | PDF [nx nq] (light processes) | histograms | value buffer |
-//   bins buffer (heavy) | block-sum scratch | per-thread slots (heavy)
+//   bins buffer (heavy) | event queue and counts (heavy) | block-sum scratch |
+//   per-thread slots (heavy)
 // Light processes keep one histogram per warp (updated by bin leaders);
 // heavy ones keep one per CTA, filled by one thread per dimension in event
 // order after every round.
@@ -247,105 +262,23 @@ struct SmemLayout {
     }
     static __host__ __device__ size_t vbuf_off(int nb, int npv) { return al(hist_off(nb, npv) + sizeof(double) * NHIST * D * nb); }
     static __host__ __device__ size_t bbuf_off(int nb, int npv) { return al(vbuf_off(nb, npv) + sizeof(double) * TPB); }
-    static __host__ __device__ size_t red_off(int nb, int npv) { return al(bbuf_off(nb, npv) + (P::HEAVY ? (size_t)TPB * D : 0)); }
+    static __host__ __device__ size_t queue_off(int nb, int npv) { return al(bbuf_off(nb, npv) + (P::HEAVY ? (size_t)TPB * D : 0)); }
+    static __host__ __device__ size_t red_off(int nb, int npv)
+    {
+        return al(queue_off(nb, npv) + (P::HEAVY ? sizeof(long long) * 2 * TPB + sizeof(int) * (WARPS + 2) : 0));
+    }
     static __host__ __device__ size_t slot_off(int nb, int npv) { return al(red_off(nb, npv) + sizeof(double) * 2 * WARPS); }
     static __host__ __device__ size_t bytes(int nb, int npv) { return slot_off(nb, npv) + (size_t)TPB * P::template slot_bytes<R>(); }
 };
 
-// ------------------------------------------------------------------ the fused integrand kernel
-
-template <class P, typename R, int TPB, bool WRITE>
-__global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
+// end of the kernel: two sums per CTA (warp trees, then warps in order), the
+// CTA histogram(s) summed in warp order, written to this CTA's partials
+template <class P, int TPB, int NHIST>
+__device__ __forceinline__ void write_partials(const KParams& kp, double sw, double sw2, unsigned long long npass,
+                                               unsigned long long nnan, double* sred, const double* shist)
 {
-    constexpr int D = P::D;
-    constexpr int WARPS = TPB / 32;
-    using L = SmemLayout<P, R, TPB>;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const int nb = kp.nb;
-    const int npv = kp.pdfg.nx * kp.pdfg.nq;
-    double* sgrid = reinterpret_cast<double*>(smem_raw + L::grid_off());
-    double* spdf = P::HEAVY ? const_cast<double*>(kp.pdf) : reinterpret_cast<double*>(smem_raw + L::pdf_off(nb));
-    double* shist = reinterpret_cast<double*>(smem_raw + L::hist_off(nb, npv));
-    double* svbuf = reinterpret_cast<double*>(smem_raw + L::vbuf_off(nb, npv));
-    uint8_t* sbins = smem_raw + L::bbuf_off(nb, npv);
-    double* sred = reinterpret_cast<double*>(smem_raw + L::red_off(nb, npv));
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    void* slot = P::template slot_bytes<R>() ? (void*)(smem_raw + L::slot_off(nb, npv) + (size_t)tid * P::template slot_bytes<R>())
-                                             : nullptr;
-
-    for (int i = tid; i < D * (nb + 1); i += TPB) sgrid[i] = kp.grid[i];
-    if (!P::HEAVY)
-        for (int i = tid; i < P::NPDF * npv; i += TPB) spdf[i] = kp.pdf[i];
-    for (int i = tid; i < L::NHIST * D * nb; i += TPB) shist[i] = 0.0;
-    __syncthreads();
-
-    double* myhist = shist + (P::HEAVY ? 0 : warp * D * nb);
-    double sw = 0.0, sw2 = 0.0;
-    unsigned long long npass = 0, nnan = 0;
-    const long long n = kp.n_events;
-    const long long total = (long long)gridDim.x * TPB;
-    const long long rounds = (n + total - 1) / total;
-    for (long long r = 0; r < rounds; ++r) {
-        const long long e = r * total + (long long)blockIdx.x * TPB + tid;
-        const bool valid = e < n;
-        EventOut<D> o;
-        double pm[P::NEXT][4];
-        o.w = 0.0; o.me2 = 0.0; o.mask = 0;
-#pragma unroll
-        for (int d = 0; d < D; ++d) o.bins[d] = 0;
-        if (valid) {
-            const unsigned long long ev = (unsigned long long)(kp.ev_offset + e);
-            if constexpr (P::NPDF == 0) event_ee<R>(kp, sgrid, ev, o, pm);
-            else event_tops<P, R>(kp, sgrid, spdf, ev, o, pm, slot);
-            if (!isfinite(o.w)) { o.w = 0.0; ++nnan; }
-            npass += o.mask ? 1 : 0;
-            if constexpr (WRITE) {
-                for (int d = 0; d < D; ++d) {
-                    if (kp.ev_u) kp.ev_u[e * D + d] = o.u[d];
-                    if (kp.ev_x) kp.ev_x[e * D + d] = o.x[d];
-                    if (kp.ev_bins) kp.ev_bins[e * D + d] = o.bins[d];
-                }
-                if (kp.ev_w) kp.ev_w[e] = o.w;
-                if (kp.ev_mask) kp.ev_mask[e] = (uint8_t)o.mask;
-                if (kp.ev_me2) kp.ev_me2[e] = o.me2;
-                if (kp.ev_p)
-                    for (int i = 0; i < P::NEXT; ++i)
-                        for (int c = 0; c < 4; ++c) kp.ev_p[(e * P::NEXT + i) * 4 + c] = pm[i][c];
-            }
-        }
-        const double wn = o.w * kp.inv_n;
-        const double v = wn * wn;
-        sw += wn;
-        sw2 += v;
-        svbuf[tid] = v;
-        if constexpr (P::HEAVY) {
-            // CTA histogram: thread d adds the round's events to dimension d in event order
-#pragma unroll
-            for (int d = 0; d < D; ++d) sbins[d * TPB + tid] = o.bins[d];
-            __syncthreads();
-            if (tid < D) {
-                double* h = shist + tid * nb;
-                const uint8_t* b = sbins + tid * TPB;
-                for (int t = 0; t < TPB; ++t) h[b[t]] += svbuf[t];
-            }
-            __syncthreads();
-        } else {
-            // per-warp histogram: one leader per distinct bin sums its peers in lane order
-            __syncwarp();
-#pragma unroll
-            for (int d = 0; d < D; ++d) {
-                const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)o.bins[d]);
-                if (lane == __ffs(peers) - 1) {
-                    double s = 0.0;
-                    for (unsigned m = peers; m; m &= m - 1) s += svbuf[warp * 32 + __ffs(m) - 1];
-                    myhist[d * nb + o.bins[d]] += s;
-                }
-            }
-            __syncwarp();
-        }
-    }
-
-    // block reduction of the two sums: warp trees, then warps in order
+    constexpr int D = P::D, WARPS = TPB / 32;
+    const int nb = kp.nb, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         sw += __shfl_down_sync(0xffffffffu, sw, off);
@@ -371,9 +304,215 @@ __global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
     }
     for (int i = tid; i < D * nb; i += TPB) {
         double s = 0.0;
-        for (int w = 0; w < L::NHIST; ++w) s += shist[w * D * nb + i];
+        for (int w = 0; w < NHIST; ++w) s += shist[w * D * nb + i];
         out[2 + i] = s;
     }
+}
+
+template <int D>
+__device__ __forceinline__ void write_event(const KParams& kp, long long e, const EventOut<D>& o, bool kin)
+{
+    if (kin) {
+        for (int d = 0; d < D; ++d) {
+            if (kp.ev_u) kp.ev_u[e * D + d] = o.u[d];
+            if (kp.ev_x) kp.ev_x[e * D + d] = o.x[d];
+            if (kp.ev_bins) kp.ev_bins[e * D + d] = o.bins[d];
+        }
+        if (kp.ev_mask) kp.ev_mask[e] = (uint8_t)o.mask;
+    }
+    if (kp.ev_w) kp.ev_w[e] = o.w;
+    if (kp.ev_me2) kp.ev_me2[e] = o.me2;
+}
+
+template <int NEXT>
+__device__ __forceinline__ void write_momenta(const KParams& kp, long long e, const double (&pm)[NEXT][4])
+{
+    if (kp.ev_p)
+        for (int i = 0; i < NEXT; ++i)
+            for (int c = 0; c < 4; ++c) kp.ev_p[(e * NEXT + i) * 4 + c] = pm[i][c];
+}
+
+// Light processes (cheap matrix elements): one event per thread per round,
+// per-warp histograms updated by bin leaders.
+template <class P, typename R, int TPB, bool WRITE>
+__device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char* smem_raw)
+{
+    constexpr int D = P::D;
+    using L = SmemLayout<P, R, TPB>;
+    const int nb = kp.nb;
+    const int npv = kp.pdfg.nx * kp.pdfg.nq;
+    double* sgrid = reinterpret_cast<double*>(smem_raw + L::grid_off());
+    double* spdf = reinterpret_cast<double*>(smem_raw + L::pdf_off(nb));
+    double* shist = reinterpret_cast<double*>(smem_raw + L::hist_off(nb, npv));
+    double* svbuf = reinterpret_cast<double*>(smem_raw + L::vbuf_off(nb, npv));
+    double* sred = reinterpret_cast<double*>(smem_raw + L::red_off(nb, npv));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+
+    for (int i = tid; i < D * (nb + 1); i += TPB) sgrid[i] = kp.grid[i];
+    for (int i = tid; i < P::NPDF * npv; i += TPB) spdf[i] = kp.pdf[i];
+    for (int i = tid; i < L::NHIST * D * nb; i += TPB) shist[i] = 0.0;
+    __syncthreads();
+
+    double* myhist = shist + warp * D * nb;
+    double sw = 0.0, sw2 = 0.0;
+    unsigned long long npass = 0, nnan = 0;
+    const long long n = kp.n_events;
+    const long long total = (long long)gridDim.x * TPB;
+    const long long rounds = (n + total - 1) / total;
+    for (long long r = 0; r < rounds; ++r) {
+        const long long e = r * total + (long long)blockIdx.x * TPB + tid;
+        const bool valid = e < n;
+        EventOut<D> o;
+        double pm[P::NEXT][4];
+        o.w = 0.0; o.me2 = 0.0; o.mask = 0;
+#pragma unroll
+        for (int d = 0; d < D; ++d) o.bins[d] = 0;
+        if (valid) {
+            const unsigned long long ev = (unsigned long long)(kp.ev_offset + e);
+            if constexpr (P::NPDF == 0) event_ee<R>(kp, sgrid, ev, o, pm);
+            else event_tops<P, R>(kp, sgrid, spdf, ev, o, pm, nullptr);
+            if (!isfinite(o.w)) { o.w = 0.0; ++nnan; }
+            npass += o.mask ? 1 : 0;
+            if constexpr (WRITE) { write_event<D>(kp, e, o, true); write_momenta<P::NEXT>(kp, e, pm); }
+        }
+        const double wn = o.w * kp.inv_n;
+        const double v = wn * wn;
+        sw += wn;
+        sw2 += v;
+        // per-warp histogram: one leader per distinct bin sums its peers in lane order
+        svbuf[tid] = v;
+        __syncwarp();
+#pragma unroll
+        for (int d = 0; d < D; ++d) {
+            const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)o.bins[d]);
+            if (lane == __ffs(peers) - 1) {
+                double s = 0.0;
+                for (unsigned m = peers; m; m &= m - 1) s += svbuf[warp * 32 + __ffs(m) - 1];
+                myhist[d * nb + o.bins[d]] += s;
+            }
+        }
+        __syncwarp();
+    }
+    write_partials<P, TPB, L::NHIST>(kp, sw, sw2, npass, nnan, sred, shist);
+}
+
+// Heavy processes (expensive matrix elements): kinematics first, then the
+// events that pass the cuts are queued in event order and their matrix
+// elements are evaluated TPB at a time, so no lane idles through a matrix
+// element for an event that the cuts reject.  Every thread of the CTA takes
+// part in each batch (the final partial batch repeats the first queued
+// event on the idle lanes and discards it), which allows an optional CTA
+// barrier between helicities (SYNC) that keeps the warps on the same code.
+// The histogram is filled by one thread per dimension in queue order.
+template <class P, typename R, int TPB, bool WRITE, bool SYNC>
+__device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char* smem_raw)
+{
+    constexpr int D = P::D, WARPS = TPB / 32;
+    using L = SmemLayout<P, R, TPB>;
+    const int nb = kp.nb;
+    const int npv = kp.pdfg.nx * kp.pdfg.nq;
+    double* sgrid = reinterpret_cast<double*>(smem_raw + L::grid_off());
+    double* shist = reinterpret_cast<double*>(smem_raw + L::hist_off(nb, npv));
+    double* svbuf = reinterpret_cast<double*>(smem_raw + L::vbuf_off(nb, npv));
+    uint8_t* sbins = smem_raw + L::bbuf_off(nb, npv);
+    long long* squeue = reinterpret_cast<long long*>(smem_raw + L::queue_off(nb, npv));
+    int* scount = reinterpret_cast<int*>(squeue + 2 * TPB);      // [0] queue length, [2 + w] warp counts
+    double* sred = reinterpret_cast<double*>(smem_raw + L::red_off(nb, npv));
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    void* slot = (void*)(smem_raw + L::slot_off(nb, npv) + (size_t)tid * P::template slot_bytes<R>());
+    const double* gpdf = kp.pdf;
+
+    for (int i = tid; i < D * (nb + 1); i += TPB) sgrid[i] = kp.grid[i];
+    for (int i = tid; i < D * nb; i += TPB) shist[i] = 0.0;
+    if (tid == 0) scount[0] = 0;
+    __syncthreads();
+
+    double sw = 0.0, sw2 = 0.0;
+    unsigned long long npass = 0, nnan = 0;
+    const long long n = kp.n_events;
+    const long long total = (long long)gridDim.x * TPB;
+    const long long rounds = (n + total - 1) / total;
+    for (long long r = 0; r <= rounds; ++r) {
+        const bool flush = (r == rounds);
+        if (!flush) {
+            // kinematics of this round's events; queue the ones that pass, in event order
+            const long long e = r * total + (long long)blockIdx.x * TPB + tid;
+            int pass = 0;
+            if (e < n) {
+                EventOut<D> o;
+                double pm[P::NEXT][4], pref;
+                kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
+                pass = o.mask ? 1 : 0;
+                npass += pass;
+                if constexpr (WRITE) {
+                    write_event<D>(kp, e, o, true);
+                    if (!pass) write_momenta<P::NEXT>(kp, e, pm);
+                }
+            }
+            const unsigned bal = __ballot_sync(0xffffffffu, pass);
+            if (lane == 0) scount[2 + warp] = __popc(bal);
+            __syncthreads();
+            const int base = scount[0];
+            int woff = 0, tot = 0;
+            for (int w = 0; w < WARPS; ++w) { woff += (w < warp) ? scount[2 + w] : 0; tot += scount[2 + w]; }
+            if (pass) squeue[base + woff + __popc(bal & ((1u << lane) - 1u))] = e;
+            __syncthreads();
+            if (tid == 0) scount[0] = base + tot;
+            __syncthreads();
+        }
+        // evaluate full batches (and, at the end, whatever is left)
+        for (;;) {
+            const int cnt = scount[0];
+            if (cnt == 0 || (!flush && cnt < TPB)) break;
+            const int take = cnt < TPB ? cnt : TPB;
+            const bool mine = tid < take;
+            const long long e = squeue[mine ? tid : 0];
+            EventOut<D> o;
+            double pm[P::NEXT][4], pref;
+            kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
+            const double me = P::Me::template me2<R, SYNC>(pm, kp.mt, kp.gs, slot);
+            double w = mine ? pref * me : 0.0;
+            if (!isfinite(w)) { w = 0.0; if (mine) ++nnan; }
+            if constexpr (WRITE) {
+                if (mine) {
+                    o.me2 = me; o.w = w;
+                    write_event<D>(kp, e, o, false);
+                    write_momenta<P::NEXT>(kp, e, pm);
+                }
+            }
+            const double wn = w * kp.inv_n;
+            const double v = wn * wn;
+            sw += wn;
+            sw2 += v;
+            svbuf[tid] = v;
+#pragma unroll
+            for (int d = 0; d < D; ++d) sbins[d * TPB + tid] = o.bins[d];
+            __syncthreads();
+            if (tid < D) {
+                double* h = shist + tid * nb;
+                const uint8_t* b = sbins + tid * TPB;
+                for (int t = 0; t < take; ++t) h[b[t]] += svbuf[t];
+            }
+            // move the unprocessed entries to the front of the queue
+            const int rest = cnt - take;
+            const long long mv = tid < rest ? squeue[take + tid] : 0;
+            __syncthreads();
+            if (tid < rest) squeue[tid] = mv;
+            if (tid == 0) scount[0] = rest;
+            __syncthreads();
+        }
+    }
+    write_partials<P, TPB, 1>(kp, sw, sw2, npass, nnan, sred, shist);
+}
+
+// ------------------------------------------------------------------ the fused integrand kernel
+
+template <class P, typename R, int TPB, bool WRITE, bool SYNC>
+__global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
+{
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    if constexpr (P::HEAVY) integrand_heavy<P, R, TPB, WRITE, SYNC>(kp, smem_raw);
+    else integrand_light<P, R, TPB, WRITE>(kp, smem_raw);
 }
 
 // ------------------------------------------------------------------ evaluate

@@ -606,7 +606,8 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("  // averaged |M|^2 (spin/colour average and identical-particle factor included);")
     src.append("  // p: momenta (E,px,py,pz) incoming first: g, g, t, tbar, g...")
     src.append("  // slot: this thread's Inv<R> in shared memory, or null for a private local copy")
-    src.append("  template <typename R>")
+    src.append("  // SYNC: a CTA barrier after every helicity (every thread of the CTA must call)")
+    src.append("  template <typename R, bool SYNC = false>")
     src.append("  __device__ static double me2(const double (&p)[NEXT][4], double mt, double gs, void* slot);")
     src.append("  template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }")
     src.append("};")
@@ -625,7 +626,7 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("#undef HEL")
     src.append("}")
     src.append("")
-    src.append("template <typename R>")
+    src.append("template <typename R, bool SYNC>")
     src.append(f"__device__ __noinline__ double me2_{name}_impl(const double* pflat, double mt, double gs, void* slot)")
     src.append("{")
     src.append(f"    constexpr int NEXT = Me_{name}::NEXT, NHEL = Me_{name}::NHEL, NGLUON = Me_{name}::NGLUON;")
@@ -642,17 +643,20 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("    // sum over the configurations with the first gluon at helicity +1.")
     src.append("    R acc = R(0);")
     src.append("#pragma unroll 1")
-    src.append("    for (int ih = 1; ih < NHEL; ih += 2) acc += hel_" + name + "<R>(v, ih);")
+    src.append("    for (int ih = 1; ih < NHEL; ih += 2) {")
+    src.append("        acc += hel_" + name + "<R>(v, ih);")
+    src.append("        if (SYNC) __syncthreads();")
+    src.append("    }")
     src.append("    acc *= R(2);")
     src.append("    double gk = 1.0;")
     src.append("    for (int i = 0; i < NGLUON; ++i) gk *= gs * gs;")
     src.append("    return double(acc) / COLOUR_DEN * gk * AVG * SYM;")
     src.append("}")
     src.append("")
-    src.append("template <typename R>")
+    src.append("template <typename R, bool SYNC>")
     src.append(f"__device__ double Me_{name}::me2(const double (&p)[NEXT][4], double mt, double gs, void* slot)")
     src.append("{")
-    src.append(f"    return me2_{name}_impl<R>(&p[0][0], mt, gs, slot);")
+    src.append(f"    return me2_{name}_impl<R, SYNC>(&p[0][0], mt, gs, slot);")
     src.append("}")
     src.append("}  // namespace mf")
     stats = dict(n_diag=n_diag, n_amp=len(diags), ncol=ncol, counts=dict(em.counts), colour_den=den)

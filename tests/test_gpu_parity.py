@@ -174,3 +174,17 @@ def test_bad_arguments(pdf_grid):
     with pytest.raises(MfError):
         ctx.integrate(17, 13000.0, 1000, 2)
     ctx.close()
+
+
+@pytest.mark.parametrize("proc", [IN.GG_TTG, IN.GG_TTGG])
+def test_schedules_give_identical_sums(proc, pdf_grid):
+    """The CTA-barrier schedule changes only when warps wait, not what they compute."""
+    phys = PHYS[proc]
+    grid = torch.tensor(random_grid(IN.DIM[proc], seed=11), device="cuda")
+    ctx = ctx_for(proc, 1, pdf_grid)
+    n = 3000
+    a, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=4)
+    ctx.set_schedule(1)
+    b, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=4)
+    assert torch.equal(a, b)
+    ctx.close()
