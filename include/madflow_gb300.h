@@ -179,6 +179,32 @@ int mf_vegas_pass_static(int process, const mf_config *cfg, double sqrt_s, const
                          int nq, double x_min, double q2_min, double q2_max, const double *grid_dev, long long n_events,
                          long long ev_offset, unsigned int iteration, double *sums_dev, void *stream);
 
+/* Replace m_t and alpha_s of the context (both > 0; MF_ERR_ARG otherwise). */
+int mf_set_couplings(struct mf_ctx *ctx, double mt, double alpha_s);
+
+/* Derivative pass of the estimator sigma_hat = (1/N) sum_e w_e at a fixed
+ * grid (grid_dev [dim][n_bins+1]), events [ev_offset, ev_offset + n_events)
+ * of Philox iteration `iteration`, with every cut mask fixed at the base point
+ * (or given by mask_in_dev [n_events], nullable): the pathwise derivative
+ * of the Monte Carlo estimate.  Forward mode: each event's weight and its
+ * m_t derivative come out of one evaluation of the whole integrand (parton
+ * map, RAMBO with its mass rescaling, scale, PDFs, matrix element),
+ * recomputed from the random numbers and stored nowhere.
+ * out_dev [4] (device): sigma_hat, d sigma_hat / d m_t, sum_e (dw_e/dm_t / N)^2
+ * (for the MC error of the derivative) and d sigma_hat / d alpha_s.
+ * Gluon processes only (MF_ERR_UNSUPPORTED otherwise); for g g -> t tbar g g
+ * only the MF_MIXED derivative is built.  Does not synchronise. */
+int mf_vegas_pass_grad(struct mf_ctx *ctx, int process, double sqrt_s, const double *grid_dev, long long n_events,
+                       long long ev_offset, unsigned int iteration, const unsigned char *mask_in_dev, double *out_dev);
+
+/* d|M|^2/dp: the derivatives of the averaged |M|^2 of mf_evaluate with
+ * respect to every momentum component, the components taken as independent
+ * variables.  momenta_dev [n][n_ext][4]; me2_dev [n] (nullable) receives
+ * |M|^2; dme2_dp_dev [n][n_ext][4].  Gluon processes only (g g -> t tbar g g:
+ * MF_MIXED only).  Does not synchronise. */
+int mf_evaluate_grad(struct mf_ctx *ctx, int process, const double *momenta_dev, long long n, double *me2_dev,
+                     double *dme2_dp_dev);
+
 /* evaluate (Sec. 2.2): spin- and colour-averaged |M|^2 (identical-particle
  * factor included) of n phase-space points.  momenta_dev: [n][n_ext][4];
  * me2_dev: [n].  Does not synchronise. */

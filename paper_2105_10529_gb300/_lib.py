@@ -67,6 +67,9 @@ def lib():
                                         C.POINTER(MfEventArrays)]),
             "mf_vegas_refine": (C.c_int, [vp, C.c_int, C.c_int, C.c_double, vp, vp]),
             "mf_evaluate": (C.c_int, [vp, C.c_int, vp, i64, vp]),
+            "mf_set_couplings": (C.c_int, [vp, C.c_double, C.c_double]),
+            "mf_vegas_pass_grad": (C.c_int, [vp, C.c_int, C.c_double, vp, i64, i64, C.c_uint, vp, vp]),
+            "mf_evaluate_grad": (C.c_int, [vp, C.c_int, vp, i64, vp, vp]),
             "mf_vegas_pass_static": (C.c_int, [C.c_int, C.POINTER(MfConfig), C.c_double, vp, C.c_int, C.c_int, C.c_int,
                                                C.c_double, C.c_double, C.c_double, vp, i64, i64, C.c_uint, vp, vp]),
         }
@@ -81,4 +84,4 @@ def lib():
 def exported_symbols():
     return ["mf_default_config", "mf_process_info", "mf_create", "mf_destroy", "mf_last_error",
             "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
-            "mf_vegas_pass_static"]
+            "mf_vegas_pass_static", "mf_set_couplings", "mf_vegas_pass_grad", "mf_evaluate_grad"]

@@ -131,6 +131,39 @@ class Context:
         _check(self.ptr, rc)
         return sums, evs
 
+    def set_couplings(self, mt: float, alpha_s: float):
+        _check(self.ptr, _lib.lib().mf_set_couplings(self.ptr, float(mt), float(alpha_s)))
+        self.cfg.mt, self.cfg.alpha_s = float(mt), float(alpha_s)
+
+    def vegas_pass_grad(self, process: int, sqrt_s: float, grid, n_events: int, ev_offset: int = 0,
+                        iteration: int = 0, mask_in=None):
+        """Derivative pass at a fixed grid and base-point masks: tensor [4] =
+        (sigma_hat, d sigma_hat/d m_t, sum (dw/dm_t / N)^2, d sigma_hat/d alpha_s)."""
+        torch = _torch()
+        dev = torch.device("cuda", torch.cuda.current_device())
+        grid = grid.to(device=dev, dtype=torch.float64).contiguous()
+        out = torch.empty(4, dtype=torch.float64, device=dev)
+        mptr = None
+        if mask_in is not None:
+            mask_in = mask_in.to(device=dev, dtype=torch.uint8).contiguous()
+            mptr = C.c_void_p(mask_in.data_ptr())
+        rc = _lib.lib().mf_vegas_pass_grad(self.ptr, process, sqrt_s, C.c_void_p(grid.data_ptr()), n_events,
+                                           ev_offset, iteration, mptr, C.c_void_p(out.data_ptr()))
+        _check(self.ptr, rc)
+        return out
+
+    def evaluate_grad(self, process: int, momenta):
+        """(|M|^2 [n], d|M|^2/dp [n, n_ext, 4]) of momenta [n, n_ext, 4] on the device."""
+        torch = _torch()
+        mom = momenta.to(dtype=torch.float64).contiguous()
+        n = mom.shape[0]
+        me = torch.empty(n, dtype=torch.float64, device=mom.device)
+        dme = torch.empty_like(mom)
+        rc = _lib.lib().mf_evaluate_grad(self.ptr, process, C.c_void_p(mom.data_ptr()), n, C.c_void_p(me.data_ptr()),
+                                         C.c_void_p(dme.data_ptr()))
+        _check(self.ptr, rc)
+        return me, dme
+
     def evaluate(self, process: int, momenta):
         """Averaged |M|^2 of momenta [n, n_ext, 4] (float64, on the device)."""
         torch = _torch()

@@ -27,8 +27,11 @@ struct Me_gg_tt {
   // p: momenta (E,px,py,pz) incoming first: g, g, t, tbar, g...
   // slot: this thread's Inv<R> in shared memory, or null for a private local copy
   // SYNC: a CTA barrier after every helicity (every thread of the CTA must call)
+  // R: float or double (or Dual of them for derivatives); the momenta, masses and
+  // the result use the matching FP64 scalar S = Widen<R>::type
   template <typename R, bool SYNC = false>
-  __device__ static double me2(const double (&p)[NEXT][4], double mt, double gs, void* slot);
+  __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],
+                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot);
   template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }
 };
 
@@ -42,7 +45,7 @@ __device__ __noinline__ R hel_gg_tt(const Me_gg_tt::Inv<R>& v, int ih)
     // colour-flow amplitudes accumulate in the slot (shared memory), not in registers
     volatile cx<R>* jamp = reinterpret_cast<volatile cx<R>*>(const_cast<cx<R>*>(v.jamp));
     #pragma unroll
-    for (int c = 0; c < NCOL; ++c) { jamp[c].r = R(0); jamp[c].i = R(0); }
+    for (int c = 0; c < NCOL; ++c) { vset(jamp[c].r, R(0)); vset(jamp[c].i, R(0)); }
     W4<R> g0; { R a[3], b[3]; for (int j = 0; j < 3; ++j) { a[j] = ldv(v.e1[0][j]); b[j] = ldv(v.e2[0][j]); }
       g0 = ext_gluon(a, b, HEL(0), false); }
     W4<R> g1; { R a[3], b[3]; for (int j = 0; j < 3; ++j) { a[j] = ldv(v.e1[1][j]); b[j] = ldv(v.e2[1][j]); }
@@ -52,22 +55,22 @@ __device__ __noinline__ R hel_gg_tt(const Me_gg_tt::Inv<R>& v, int ih)
     const R q1_2[4] = {ldv(v.p3[0]) - ldv(v.K[0][0]), ldv(v.p3[1]) - ldv(v.K[0][1]), ldv(v.p3[2]) - ldv(v.K[0][2]), ldv(v.p3[3]) - ldv(v.K[0][3])};
     const W4<R> w1 = ffv_col(g1, v4, q1_2, ldv(v.mt), ldv(v.iQ[0]));
     const cx<R> a1 = ffv_amp(ub3, w1, g0);
-    jamp[0].r += a1.i; jamp[0].i -= a1.r;
+    jadd_mi(jamp[0], a1);
     const R q2_4[4] = {ldv(v.p3[0]) - ldv(v.K[1][0]), ldv(v.p3[1]) - ldv(v.K[1][1]), ldv(v.p3[2]) - ldv(v.K[1][2]), ldv(v.p3[3]) - ldv(v.K[1][3])};
     const W4<R> w3 = ffv_col(g0, v4, q2_4, ldv(v.mt), ldv(v.iQ[1]));
     const cx<R> a2 = ffv_amp(ub3, w3, g1);
-    jamp[1].r += a2.i; jamp[1].i -= a2.r;
+    jadd_mi(jamp[1], a2);
     const W4<R> jq = ffv_cur(ub3, v4, ldv(v.iG[0]));
     const R k1_5[4] = {ldv(v.K[0][0]), ldv(v.K[0][1]), ldv(v.K[0][2]), ldv(v.K[0][3])};
     const R k2_6[4] = {ldv(v.K[1][0]), ldv(v.K[1][1]), ldv(v.K[1][2]), ldv(v.K[1][3])};
     const R k3_7[4] = {ldv(v.K[2][0]), ldv(v.K[2][1]), ldv(v.K[2][2]), ldv(v.K[2][3])};
     const R nkk3_7[4] = {-k3_7[0], -k3_7[1], -k3_7[2], -k3_7[3]};
     const cx<R> a3 = vvv_amp(g0, g1, jq, k1_5, k2_6, nkk3_7);
-    jamp[0].r += a3.i; jamp[0].i -= a3.r;
-    jamp[1].r -= a3.i; jamp[1].i += a3.r;
+    jadd_mi(jamp[0], a3);
+    jadd_pi(jamp[1], a3);
     cx<R> J[NCOL];
     #pragma unroll
-    for (int c = 0; c < NCOL; ++c) J[c] = mkc(R(jamp[c].r), R(jamp[c].i));
+    for (int c = 0; c < NCOL; ++c) J[c] = mkc(vget(jamp[c].r), vget(jamp[c].i));
     R me = R(0);
     { const R zr = R(16.0) * J[0].r + R(-4.0) * J[1].r; const R zi = R(16.0) * J[0].i + R(-4.0) * J[1].i;
       me = fma(J[0].r, zr, fma(J[0].i, zi, me)); }
@@ -78,31 +81,33 @@ __device__ __noinline__ R hel_gg_tt(const Me_gg_tt::Inv<R>& v, int ih)
 }
 
 template <typename R, bool SYNC>
-__device__ __noinline__ double me2_gg_tt_impl(const double* pflat, double mt, double gs, void* slot)
+__device__ __noinline__ typename Widen<R>::type me2_gg_tt_impl(const typename Widen<R>::type* pflat,
+    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot)
 {
+    using S = typename Widen<R>::type;
     constexpr int NEXT = Me_gg_tt::NEXT, NHEL = Me_gg_tt::NHEL, NGLUON = Me_gg_tt::NGLUON;
     constexpr double COLOUR_DEN = Me_gg_tt::COLOUR_DEN, AVG = Me_gg_tt::AVG, SYM = Me_gg_tt::SYM;
-    double p[NEXT][4];
+    S p[NEXT][4];
     for (int i = 0; i < NEXT; ++i)
         for (int c = 0; c < 4; ++c) p[i][c] = pflat[4 * i + c];
     Me_gg_tt::Inv<R> local;   // used when the caller has no shared-memory slot
     Me_gg_tt::Inv<R>& v = slot ? *static_cast<Me_gg_tt::Inv<R>*>(slot) : local;
     // gluon momenta, incoming convention: gluons 0,1 incoming, the rest outgoing
-    const double kd1[4] = {p[0][0], p[0][1], p[0][2], p[0][3]};
-    const double kd2[4] = {p[1][0], p[1][1], p[1][2], p[1][3]};
-    const double kd3[4] = {kd1[0] + kd2[0], kd1[1] + kd2[1], kd1[2] + kd2[2], kd1[3] + kd2[3]};
+    const S kd1[4] = {p[0][0], p[0][1], p[0][2], p[0][3]};
+    const S kd2[4] = {p[1][0], p[1][1], p[1][2], p[1][3]};
+    const S kd3[4] = {kd1[0] + kd2[0], kd1[1] + kd2[1], kd1[2] + kd2[2], kd1[3] + kd2[3]};
     for (int c = 0; c < 4; ++c) v.K[0][c] = R(kd1[c]);
     for (int c = 0; c < 4; ++c) v.K[1][c] = R(kd2[c]);
     for (int c = 0; c < 4; ++c) v.K[2][c] = R(kd3[c]);
     for (int c = 0; c < 4; ++c) v.p3[c] = R(p[2][c]);
     v.iG[0] = R(1.0 / mdot(kd3, kd3));
-    { const double q[4] = {p[2][0] - kd1[0], p[2][1] - kd1[1], p[2][2] - kd1[2], p[2][3] - kd1[3]};
+    { const S q[4] = {p[2][0] - kd1[0], p[2][1] - kd1[1], p[2][2] - kd1[2], p[2][3] - kd1[3]};
       v.iQ[0] = R(1.0 / (mdot(q, q) - mt * mt)); }
-    { const double q[4] = {p[2][0] - kd2[0], p[2][1] - kd2[1], p[2][2] - kd2[2], p[2][3] - kd2[3]};
+    { const S q[4] = {p[2][0] - kd2[0], p[2][1] - kd2[1], p[2][2] - kd2[2], p[2][3] - kd2[3]};
       v.iQ[1] = R(1.0 / (mdot(q, q) - mt * mt)); }
-    { double a[3], b[3]; gluon_basis(p[0], a, b);
+    { S a[3], b[3]; gluon_basis(p[0], a, b);
       for (int j = 0; j < 3; ++j) { v.e1[0][j] = R(a[j]); v.e2[0][j] = R(b[j]); } }
-    { double a[3], b[3]; gluon_basis(p[1], a, b);
+    { S a[3], b[3]; gluon_basis(p[1], a, b);
       for (int j = 0; j < 3; ++j) { v.e1[1][j] = R(a[j]); v.e2[1][j] = R(b[j]); } }
     v.fb3 = fermion_basis<R>(p[2], mt);
     v.fb4 = fermion_basis<R>(p[3], mt);
@@ -117,13 +122,14 @@ __device__ __noinline__ double me2_gg_tt_impl(const double* pflat, double mt, do
         if (SYNC) __syncthreads();
     }
     acc *= R(2);
-    double gk = 1.0;
-    for (int i = 0; i < NGLUON; ++i) gk *= gs * gs;
-    return double(acc) / COLOUR_DEN * gk * AVG * SYM;
+    S gk = S(1.0);
+    for (int i = 0; i < NGLUON; ++i) gk = gk * (gs * gs);
+    return S(acc) / COLOUR_DEN * gk * AVG * SYM;
 }
 
 template <typename R, bool SYNC>
-__device__ double Me_gg_tt::me2(const double (&p)[NEXT][4], double mt, double gs, void* slot)
+__device__ typename Widen<R>::type Me_gg_tt::me2(const typename Widen<R>::type (&p)[NEXT][4],
+    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot)
 {
     return me2_gg_tt_impl<R, SYNC>(&p[0][0], mt, gs, slot);
 }

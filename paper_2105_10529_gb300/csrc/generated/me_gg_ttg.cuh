@@ -27,8 +27,11 @@ struct Me_gg_ttg {
   // p: momenta (E,px,py,pz) incoming first: g, g, t, tbar, g...
   // slot: this thread's Inv<R> in shared memory, or null for a private local copy
   // SYNC: a CTA barrier after every helicity (every thread of the CTA must call)
+  // R: float or double (or Dual of them for derivatives); the momenta, masses and
+  // the result use the matching FP64 scalar S = Widen<R>::type
   template <typename R, bool SYNC = false>
-  __device__ static double me2(const double (&p)[NEXT][4], double mt, double gs, void* slot);
+  __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],
+                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot);
   template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }
 };
 
@@ -42,7 +45,7 @@ __device__ __noinline__ R hel_gg_ttg(const Me_gg_ttg::Inv<R>& v, int ih)
     // colour-flow amplitudes accumulate in the slot (shared memory), not in registers
     volatile cx<R>* jamp = reinterpret_cast<volatile cx<R>*>(const_cast<cx<R>*>(v.jamp));
     #pragma unroll
-    for (int c = 0; c < NCOL; ++c) { jamp[c].r = R(0); jamp[c].i = R(0); }
+    for (int c = 0; c < NCOL; ++c) { vset(jamp[c].r, R(0)); vset(jamp[c].i, R(0)); }
     W4<R> g0; { R a[3], b[3]; for (int j = 0; j < 3; ++j) { a[j] = ldv(v.e1[0][j]); b[j] = ldv(v.e2[0][j]); }
       g0 = ext_gluon(a, b, HEL(0), false); }
     W4<R> g1; { R a[3], b[3]; for (int j = 0; j < 3; ++j) { a[j] = ldv(v.e1[1][j]); b[j] = ldv(v.e2[1][j]); }
@@ -65,88 +68,88 @@ __device__ __noinline__ R hel_gg_ttg(const Me_gg_ttg::Inv<R>& v, int ih)
     const R q3_13[4] = {ldv(v.p3[0]) - ldv(v.K[2][0]), ldv(v.p3[1]) - ldv(v.K[2][1]), ldv(v.p3[2]) - ldv(v.K[2][2]), ldv(v.p3[3]) - ldv(v.K[2][3])};
     const W4<R> w12 = ffv_col(g2, v4, q3_13, ldv(v.mt), ldv(v.iQ[2]));
     const cx<R> a1 = ffv_amp(w11, w12, g1);
-    jamp[0].r -= a1.i; jamp[0].i += a1.r;
+    jadd_pi(jamp[0], a1);
     const R q5_15[4] = {ldv(v.p3[0]) - ldv(v.K[4][0]), ldv(v.p3[1]) - ldv(v.K[4][1]), ldv(v.p3[2]) - ldv(v.K[4][2]), ldv(v.p3[3]) - ldv(v.K[4][3])};
     const W4<R> w14 = ffv_col(g1, v4, q5_15, ldv(v.mt), ldv(v.iQ[4]));
     const cx<R> a2 = ffv_amp(w11, w14, g2);
-    jamp[1].r -= a2.i; jamp[1].i += a2.r;
+    jadd_pi(jamp[1], a2);
     const cx<R> a3 = ffv_amp(w11, v4, w9);
-    jamp[0].r -= a3.i; jamp[0].i += a3.r;
-    jamp[1].r += a3.i; jamp[1].i -= a3.r;
+    jadd_pi(jamp[0], a3);
+    jadd_mi(jamp[1], a3);
     const R q2_16[4] = {ldv(v.p3[0]) - ldv(v.K[1][0]), ldv(v.p3[1]) - ldv(v.K[1][1]), ldv(v.p3[2]) - ldv(v.K[1][2]), ldv(v.p3[3]) - ldv(v.K[1][3])};
     const W4<R> w17 = ffv_row(ub3, g1, q2_16, ldv(v.mt), ldv(v.iQ[1]));
     const cx<R> a4 = ffv_amp(w17, w12, g0);
-    jamp[2].r -= a4.i; jamp[2].i += a4.r;
+    jadd_pi(jamp[2], a4);
     const R q6_19[4] = {ldv(v.p3[0]) - ldv(v.K[5][0]), ldv(v.p3[1]) - ldv(v.K[5][1]), ldv(v.p3[2]) - ldv(v.K[5][2]), ldv(v.p3[3]) - ldv(v.K[5][3])};
     const W4<R> w18 = ffv_col(g0, v4, q6_19, ldv(v.mt), ldv(v.iQ[5]));
     const cx<R> a5 = ffv_amp(w17, w18, g2);
-    jamp[3].r -= a5.i; jamp[3].i += a5.r;
+    jadd_pi(jamp[3], a5);
     const cx<R> a6 = ffv_amp(w17, v4, w6);
-    jamp[2].r -= a6.i; jamp[2].i += a6.r;
-    jamp[3].r += a6.i; jamp[3].i -= a6.r;
+    jadd_pi(jamp[2], a6);
+    jadd_mi(jamp[3], a6);
     const R q4_20[4] = {ldv(v.p3[0]) - ldv(v.K[3][0]), ldv(v.p3[1]) - ldv(v.K[3][1]), ldv(v.p3[2]) - ldv(v.K[3][2]), ldv(v.p3[3]) - ldv(v.K[3][3])};
     const W4<R> w21 = ffv_row(ub3, g2, q4_20, ldv(v.mt), ldv(v.iQ[3]));
     const cx<R> a7 = ffv_amp(w21, w14, g0);
-    jamp[4].r -= a7.i; jamp[4].i += a7.r;
+    jadd_pi(jamp[4], a7);
     const cx<R> a8 = ffv_amp(w21, w18, g1);
-    jamp[5].r -= a8.i; jamp[5].i += a8.r;
+    jadd_pi(jamp[5], a8);
     const cx<R> a9 = ffv_amp(w21, v4, w3);
-    jamp[4].r -= a9.i; jamp[4].i += a9.r;
-    jamp[5].r += a9.i; jamp[5].i -= a9.r;
+    jadd_pi(jamp[4], a9);
+    jadd_mi(jamp[5], a9);
     const cx<R> a10 = ffv_amp(ub3, w12, w3);
-    jamp[0].r -= a10.i; jamp[0].i += a10.r;
-    jamp[2].r += a10.i; jamp[2].i -= a10.r;
+    jadd_pi(jamp[0], a10);
+    jadd_mi(jamp[2], a10);
     const cx<R> a11 = ffv_amp(ub3, w14, w6);
-    jamp[1].r -= a11.i; jamp[1].i += a11.r;
-    jamp[4].r += a11.i; jamp[4].i -= a11.r;
+    jadd_pi(jamp[1], a11);
+    jadd_mi(jamp[4], a11);
     const cx<R> a12 = ffv_amp(ub3, w18, w9);
-    jamp[3].r -= a12.i; jamp[3].i += a12.r;
-    jamp[5].r += a12.i; jamp[5].i -= a12.r;
+    jadd_pi(jamp[3], a12);
+    jadd_mi(jamp[5], a12);
     const W4<R> jq = ffv_cur(ub3, v4, ldv(v.iG[3]));
     const R k1_22[4] = {ldv(v.K[0][0]), ldv(v.K[0][1]), ldv(v.K[0][2]), ldv(v.K[0][3])};
     const R k6_23[4] = {ldv(v.K[5][0]), ldv(v.K[5][1]), ldv(v.K[5][2]), ldv(v.K[5][3])};
     const R k7_24[4] = {ldv(v.K[6][0]), ldv(v.K[6][1]), ldv(v.K[6][2]), ldv(v.K[6][3])};
     const R nkk7_24[4] = {-k7_24[0], -k7_24[1], -k7_24[2], -k7_24[3]};
     const cx<R> a13 = vvv_amp(g0, w9, jq, k1_22, k6_23, nkk7_24);
-    jamp[0].r -= a13.i; jamp[0].i += a13.r;
-    jamp[1].r += a13.i; jamp[1].i -= a13.r;
-    jamp[3].r += a13.i; jamp[3].i -= a13.r;
-    jamp[5].r -= a13.i; jamp[5].i += a13.r;
+    jadd_pi(jamp[0], a13);
+    jadd_mi(jamp[1], a13);
+    jadd_mi(jamp[3], a13);
+    jadd_pi(jamp[5], a13);
     const R k3_25[4] = {ldv(v.K[2][0]), ldv(v.K[2][1]), ldv(v.K[2][2]), ldv(v.K[2][3])};
     const R k4_26[4] = {ldv(v.K[3][0]), ldv(v.K[3][1]), ldv(v.K[3][2]), ldv(v.K[3][3])};
     const R k7_27[4] = {ldv(v.K[6][0]), ldv(v.K[6][1]), ldv(v.K[6][2]), ldv(v.K[6][3])};
     const R nkk7_27[4] = {-k7_27[0], -k7_27[1], -k7_27[2], -k7_27[3]};
     const cx<R> a14 = vvv_amp(w3, g2, jq, k3_25, k4_26, nkk7_27);
-    jamp[0].r -= a14.i; jamp[0].i += a14.r;
-    jamp[2].r += a14.i; jamp[2].i -= a14.r;
-    jamp[4].r += a14.i; jamp[4].i -= a14.r;
-    jamp[5].r -= a14.i; jamp[5].i += a14.r;
+    jadd_pi(jamp[0], a14);
+    jadd_mi(jamp[2], a14);
+    jadd_mi(jamp[4], a14);
+    jadd_pi(jamp[5], a14);
     const R k5_28[4] = {ldv(v.K[4][0]), ldv(v.K[4][1]), ldv(v.K[4][2]), ldv(v.K[4][3])};
     const R k2_29[4] = {ldv(v.K[1][0]), ldv(v.K[1][1]), ldv(v.K[1][2]), ldv(v.K[1][3])};
     const R k7_30[4] = {ldv(v.K[6][0]), ldv(v.K[6][1]), ldv(v.K[6][2]), ldv(v.K[6][3])};
     const R nkk7_30[4] = {-k7_30[0], -k7_30[1], -k7_30[2], -k7_30[3]};
     const cx<R> a15 = vvv_amp(w6, g1, jq, k5_28, k2_29, nkk7_30);
-    jamp[1].r -= a15.i; jamp[1].i += a15.r;
-    jamp[2].r += a15.i; jamp[2].i -= a15.r;
-    jamp[3].r -= a15.i; jamp[3].i += a15.r;
-    jamp[4].r += a15.i; jamp[4].i -= a15.r;
+    jadd_pi(jamp[1], a15);
+    jadd_mi(jamp[2], a15);
+    jadd_pi(jamp[3], a15);
+    jadd_mi(jamp[4], a15);
     cx<R> a16, a17, a18;
     vvvv_amp(g0, g1, g2, jq, a16, a17, a18);
-    jamp[0].r -= a16.i; jamp[0].i += a16.r;
-    jamp[2].r += a16.i; jamp[2].i -= a16.r;
-    jamp[4].r += a16.i; jamp[4].i -= a16.r;
-    jamp[5].r -= a16.i; jamp[5].i += a16.r;
-    jamp[1].r -= a17.i; jamp[1].i += a17.r;
-    jamp[2].r += a17.i; jamp[2].i -= a17.r;
-    jamp[3].r -= a17.i; jamp[3].i += a17.r;
-    jamp[4].r += a17.i; jamp[4].i -= a17.r;
-    jamp[0].r += a18.i; jamp[0].i -= a18.r;
-    jamp[1].r -= a18.i; jamp[1].i += a18.r;
-    jamp[3].r -= a18.i; jamp[3].i += a18.r;
-    jamp[5].r += a18.i; jamp[5].i -= a18.r;
+    jadd_pi(jamp[0], a16);
+    jadd_mi(jamp[2], a16);
+    jadd_mi(jamp[4], a16);
+    jadd_pi(jamp[5], a16);
+    jadd_pi(jamp[1], a17);
+    jadd_mi(jamp[2], a17);
+    jadd_pi(jamp[3], a17);
+    jadd_mi(jamp[4], a17);
+    jadd_mi(jamp[0], a18);
+    jadd_pi(jamp[1], a18);
+    jadd_pi(jamp[3], a18);
+    jadd_mi(jamp[5], a18);
     cx<R> J[NCOL];
     #pragma unroll
-    for (int c = 0; c < NCOL; ++c) J[c] = mkc(R(jamp[c].r), R(jamp[c].i));
+    for (int c = 0; c < NCOL; ++c) J[c] = mkc(vget(jamp[c].r), vget(jamp[c].i));
     R me = R(0);
     { const R zr = R(64.0) * J[0].r + R(-16.0) * J[1].r + R(-16.0) * J[2].r + R(2.0) * J[3].r + R(2.0) * J[4].r + R(20.0) * J[5].r; const R zi = R(64.0) * J[0].i + R(-16.0) * J[1].i + R(-16.0) * J[2].i + R(2.0) * J[3].i + R(2.0) * J[4].i + R(20.0) * J[5].i;
       me = fma(J[0].r, zr, fma(J[0].i, zi, me)); }
@@ -165,23 +168,25 @@ __device__ __noinline__ R hel_gg_ttg(const Me_gg_ttg::Inv<R>& v, int ih)
 }
 
 template <typename R, bool SYNC>
-__device__ __noinline__ double me2_gg_ttg_impl(const double* pflat, double mt, double gs, void* slot)
+__device__ __noinline__ typename Widen<R>::type me2_gg_ttg_impl(const typename Widen<R>::type* pflat,
+    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot)
 {
+    using S = typename Widen<R>::type;
     constexpr int NEXT = Me_gg_ttg::NEXT, NHEL = Me_gg_ttg::NHEL, NGLUON = Me_gg_ttg::NGLUON;
     constexpr double COLOUR_DEN = Me_gg_ttg::COLOUR_DEN, AVG = Me_gg_ttg::AVG, SYM = Me_gg_ttg::SYM;
-    double p[NEXT][4];
+    S p[NEXT][4];
     for (int i = 0; i < NEXT; ++i)
         for (int c = 0; c < 4; ++c) p[i][c] = pflat[4 * i + c];
     Me_gg_ttg::Inv<R> local;   // used when the caller has no shared-memory slot
     Me_gg_ttg::Inv<R>& v = slot ? *static_cast<Me_gg_ttg::Inv<R>*>(slot) : local;
     // gluon momenta, incoming convention: gluons 0,1 incoming, the rest outgoing
-    const double kd1[4] = {p[0][0], p[0][1], p[0][2], p[0][3]};
-    const double kd2[4] = {p[1][0], p[1][1], p[1][2], p[1][3]};
-    const double kd4[4] = {-p[4][0], -p[4][1], -p[4][2], -p[4][3]};
-    const double kd3[4] = {kd1[0] + kd2[0], kd1[1] + kd2[1], kd1[2] + kd2[2], kd1[3] + kd2[3]};
-    const double kd5[4] = {kd1[0] + kd4[0], kd1[1] + kd4[1], kd1[2] + kd4[2], kd1[3] + kd4[3]};
-    const double kd6[4] = {kd2[0] + kd4[0], kd2[1] + kd4[1], kd2[2] + kd4[2], kd2[3] + kd4[3]};
-    const double kd7[4] = {kd1[0] + kd2[0] + kd4[0], kd1[1] + kd2[1] + kd4[1], kd1[2] + kd2[2] + kd4[2], kd1[3] + kd2[3] + kd4[3]};
+    const S kd1[4] = {p[0][0], p[0][1], p[0][2], p[0][3]};
+    const S kd2[4] = {p[1][0], p[1][1], p[1][2], p[1][3]};
+    const S kd4[4] = {-p[4][0], -p[4][1], -p[4][2], -p[4][3]};
+    const S kd3[4] = {kd1[0] + kd2[0], kd1[1] + kd2[1], kd1[2] + kd2[2], kd1[3] + kd2[3]};
+    const S kd5[4] = {kd1[0] + kd4[0], kd1[1] + kd4[1], kd1[2] + kd4[2], kd1[3] + kd4[3]};
+    const S kd6[4] = {kd2[0] + kd4[0], kd2[1] + kd4[1], kd2[2] + kd4[2], kd2[3] + kd4[3]};
+    const S kd7[4] = {kd1[0] + kd2[0] + kd4[0], kd1[1] + kd2[1] + kd4[1], kd1[2] + kd2[2] + kd4[2], kd1[3] + kd2[3] + kd4[3]};
     for (int c = 0; c < 4; ++c) v.K[0][c] = R(kd1[c]);
     for (int c = 0; c < 4; ++c) v.K[1][c] = R(kd2[c]);
     for (int c = 0; c < 4; ++c) v.K[2][c] = R(kd3[c]);
@@ -194,23 +199,23 @@ __device__ __noinline__ double me2_gg_ttg_impl(const double* pflat, double mt, d
     v.iG[1] = R(1.0 / mdot(kd5, kd5));
     v.iG[2] = R(1.0 / mdot(kd6, kd6));
     v.iG[3] = R(1.0 / mdot(kd7, kd7));
-    { const double q[4] = {p[2][0] - kd1[0], p[2][1] - kd1[1], p[2][2] - kd1[2], p[2][3] - kd1[3]};
+    { const S q[4] = {p[2][0] - kd1[0], p[2][1] - kd1[1], p[2][2] - kd1[2], p[2][3] - kd1[3]};
       v.iQ[0] = R(1.0 / (mdot(q, q) - mt * mt)); }
-    { const double q[4] = {p[2][0] - kd2[0], p[2][1] - kd2[1], p[2][2] - kd2[2], p[2][3] - kd2[3]};
+    { const S q[4] = {p[2][0] - kd2[0], p[2][1] - kd2[1], p[2][2] - kd2[2], p[2][3] - kd2[3]};
       v.iQ[1] = R(1.0 / (mdot(q, q) - mt * mt)); }
-    { const double q[4] = {p[2][0] - kd3[0], p[2][1] - kd3[1], p[2][2] - kd3[2], p[2][3] - kd3[3]};
+    { const S q[4] = {p[2][0] - kd3[0], p[2][1] - kd3[1], p[2][2] - kd3[2], p[2][3] - kd3[3]};
       v.iQ[2] = R(1.0 / (mdot(q, q) - mt * mt)); }
-    { const double q[4] = {p[2][0] - kd4[0], p[2][1] - kd4[1], p[2][2] - kd4[2], p[2][3] - kd4[3]};
+    { const S q[4] = {p[2][0] - kd4[0], p[2][1] - kd4[1], p[2][2] - kd4[2], p[2][3] - kd4[3]};
       v.iQ[3] = R(1.0 / (mdot(q, q) - mt * mt)); }
-    { const double q[4] = {p[2][0] - kd5[0], p[2][1] - kd5[1], p[2][2] - kd5[2], p[2][3] - kd5[3]};
+    { const S q[4] = {p[2][0] - kd5[0], p[2][1] - kd5[1], p[2][2] - kd5[2], p[2][3] - kd5[3]};
       v.iQ[4] = R(1.0 / (mdot(q, q) - mt * mt)); }
-    { const double q[4] = {p[2][0] - kd6[0], p[2][1] - kd6[1], p[2][2] - kd6[2], p[2][3] - kd6[3]};
+    { const S q[4] = {p[2][0] - kd6[0], p[2][1] - kd6[1], p[2][2] - kd6[2], p[2][3] - kd6[3]};
       v.iQ[5] = R(1.0 / (mdot(q, q) - mt * mt)); }
-    { double a[3], b[3]; gluon_basis(p[0], a, b);
+    { S a[3], b[3]; gluon_basis(p[0], a, b);
       for (int j = 0; j < 3; ++j) { v.e1[0][j] = R(a[j]); v.e2[0][j] = R(b[j]); } }
-    { double a[3], b[3]; gluon_basis(p[1], a, b);
+    { S a[3], b[3]; gluon_basis(p[1], a, b);
       for (int j = 0; j < 3; ++j) { v.e1[1][j] = R(a[j]); v.e2[1][j] = R(b[j]); } }
-    { double a[3], b[3]; gluon_basis(p[4], a, b);
+    { S a[3], b[3]; gluon_basis(p[4], a, b);
       for (int j = 0; j < 3; ++j) { v.e1[2][j] = R(a[j]); v.e2[2][j] = R(b[j]); } }
     v.fb3 = fermion_basis<R>(p[2], mt);
     v.fb4 = fermion_basis<R>(p[3], mt);
@@ -225,13 +230,14 @@ __device__ __noinline__ double me2_gg_ttg_impl(const double* pflat, double mt, d
         if (SYNC) __syncthreads();
     }
     acc *= R(2);
-    double gk = 1.0;
-    for (int i = 0; i < NGLUON; ++i) gk *= gs * gs;
-    return double(acc) / COLOUR_DEN * gk * AVG * SYM;
+    S gk = S(1.0);
+    for (int i = 0; i < NGLUON; ++i) gk = gk * (gs * gs);
+    return S(acc) / COLOUR_DEN * gk * AVG * SYM;
 }
 
 template <typename R, bool SYNC>
-__device__ double Me_gg_ttg::me2(const double (&p)[NEXT][4], double mt, double gs, void* slot)
+__device__ typename Widen<R>::type Me_gg_ttg::me2(const typename Widen<R>::type (&p)[NEXT][4],
+    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot)
 {
     return me2_gg_ttg_impl<R, SYNC>(&p[0][0], mt, gs, slot);
 }

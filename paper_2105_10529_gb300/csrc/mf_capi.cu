@@ -115,6 +115,16 @@ const ProcOps* proc_ops(int p)
     }
 }
 
+const GradOpsTable* grad_ops(int p)
+{
+    switch (p) {
+    case MF_GG_TT: return grad_gg_tt();
+    case MF_GG_TTG: return grad_gg_ttg();
+    case MF_GG_TTGG: return grad_gg_ttgg();
+    default: return nullptr;
+    }
+}
+
 int fail(mf_ctx* c, int code, const std::string& msg)
 {
     if (c) c->err = msg;
@@ -405,6 +415,62 @@ int mf_integrate(mf_ctx* c, int process, double sqrt_s, long long n_events, int 
     if (iter_host) std::memcpy(iter_host, iters.data(), iters.size() * sizeof(double));
     if (cnt[1] > (unsigned long long)(n_events * (long long)n_iter) / 1000)
         return fail(c, MF_ERR_NUMERIC, "more than 0.1% of the event weights were not finite");
+    return MF_OK;
+}
+
+int mf_set_couplings(mf_ctx* c, double mt, double alpha_s)
+{
+    if (!c || !(mt > 0.0) || !(alpha_s > 0.0)) return MF_ERR_ARG;
+    c->cfg.mt = mt;
+    c->cfg.alpha_s = alpha_s;
+    return MF_OK;
+}
+
+int mf_vegas_pass_grad(mf_ctx* c, int process, double sqrt_s, const double* grid_dev, long long n_events,
+                       long long ev_offset, unsigned int iteration, const unsigned char* mask_in_dev, double* out_dev)
+{
+    if (!c) return MF_ERR_ARG;
+    const ProcOps* ops = proc_ops(process);
+    const GradOpsTable* g = grad_ops(process);
+    if (!ops || !g) return fail(c, MF_ERR_UNSUPPORTED, "no derivative pass for this process");
+    if (c->cfg.precision == MF_FP64 && !g->has_fp64)
+        return fail(c, MF_ERR_UNSUPPORTED, "FP64 derivative of this process not built; use MF_MIXED");
+    if (!grid_dev || !out_dev || n_events < 1 || ev_offset < 0 || !(sqrt_s > 0.0))
+        return fail(c, MF_ERR_ARG, "mf_vegas_pass_grad: bad argument");
+    KParams kp;
+    int rc = make_params(c, process, ops, sqrt_s, kp);
+    if (rc) return rc;
+    kp.iteration = iteration;
+    kp.n_events = n_events;
+    kp.ev_offset = ev_offset;
+    kp.inv_n = 1.0 / (double)n_events;
+    kp.grid = grid_dev;
+    kp.mask_in = mask_in_dev;
+    long long want = (n_events + 127) / 128;
+    const long long cap = (long long)c->n_sm * 8;
+    const int nblk = (int)(want < cap ? want : cap);
+    MF_CUDA(c, g->grad(c->cfg.precision, kp, nblk, c->d_partials, g->k_as, c->cfg.alpha_s, c->stream));
+    finish_pass_kernel<<<1, 32, 4 * sizeof(double), c->stream>>>(c->d_partials, nblk, 1, 2, n_events, 0.0, 0, nullptr,
+                                                                 nullptr, out_dev);
+    MF_CUDA(c, cudaGetLastError());
+    return MF_OK;
+}
+
+int mf_evaluate_grad(mf_ctx* c, int process, const double* momenta_dev, long long n, double* me2_dev, double* dme2_dp_dev)
+{
+    if (!c) return MF_ERR_ARG;
+    const GradOpsTable* g = grad_ops(process);
+    if (!g) return fail(c, MF_ERR_UNSUPPORTED, "no derivative for this process");
+    if (c->cfg.precision == MF_FP64 && !g->has_fp64)
+        return fail(c, MF_ERR_UNSUPPORTED, "FP64 derivative of this process not built; use MF_MIXED");
+    if (n == 0) return MF_OK;
+    if (!momenta_dev || !dme2_dp_dev || n < 0) return fail(c, MF_ERR_ARG, "mf_evaluate_grad: bad argument");
+    const double gs = std::sqrt(4.0 * PI * c->cfg.alpha_s);
+    long long nb = (n + 127) / 128;
+    const long long cap = (long long)c->n_sm * 8;
+    const int nblk = (int)(nb < cap ? nb : cap);
+    MF_CUDA(c, g->evaluate_grad(c->cfg.precision, momenta_dev, n, me2_dev, dme2_dp_dev, c->cfg.mt, gs, nblk,
+                                c->stream));
     return MF_OK;
 }
 

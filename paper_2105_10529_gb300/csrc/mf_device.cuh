@@ -9,6 +9,7 @@
 // contraction or reassociation can change them.
 #pragma once
 #include <cstdint>
+#include "mf_dual.cuh"
 
 namespace mf {
 
@@ -83,10 +84,12 @@ __device__ __forceinline__ double vegas_map(const double* grid, int nb, const do
 
 // ------------------------------------------------------------------ a3: parton map
 // tau = tau0^x0, x1 = tau^v, x2 = tau^(1-v), J = tau |ln tau| |ln tau0|.
-__device__ __forceinline__ void parton_map(double x0, double v, double ln_tau0, double& x1, double& x2, double& jac)
+// S: double, or Dual<double> when tau0 carries a derivative.
+template <typename S>
+__device__ __forceinline__ void parton_map(double x0, double v, S ln_tau0, S& x1, S& x2, S& jac)
 {
-    const double lt = x0 * ln_tau0;
-    const double tau = exp(lt);
+    const S lt = x0 * ln_tau0;
+    const S tau = exp(lt);
     x1 = exp(v * lt);
     x2 = exp((1.0 - v) * lt);
     jac = tau * (-lt) * (-ln_tau0);
@@ -97,10 +100,10 @@ __device__ __forceinline__ void parton_map(double x0, double v, double ln_tau0, 
 // from 4N uniforms, conformal boost + scale to (sqrt(shat), 0), massive
 // rescaling xi by Newton's method (bounded iterations) and the massive
 // weight factor.  Returns the phase-space weight; p gets (E,px,py,pz).
-template <int N>
-__device__ __forceinline__ double rambo(double rs, const double (&m)[N], const double* u, double (&p)[N][4],
-                                        double vol_massless)
+template <int N, typename S>
+__device__ __forceinline__ S rambo(S rs, const S (&m)[N], const double* u, S (&p)[N][4], S vol_massless)
 {
+    double q[N][4];
     double Q0 = 0.0, Q1 = 0.0, Q2 = 0.0, Q3 = 0.0;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
@@ -109,60 +112,73 @@ __device__ __forceinline__ double rambo(double rs, const double (&m)[N], const d
         double sf, cf;
         sincospi(2.0 * u[4 * i + 1], &sf, &cf);
         const double e = -log(u[4 * i + 2] * u[4 * i + 3]);
-        p[i][0] = e;
-        p[i][1] = e * s * cf;
-        p[i][2] = e * s * sf;
-        p[i][3] = e * c;
-        Q0 += p[i][0]; Q1 += p[i][1]; Q2 += p[i][2]; Q3 += p[i][3];
+        q[i][0] = e;
+        q[i][1] = e * s * cf;
+        q[i][2] = e * s * sf;
+        q[i][3] = e * c;
+        Q0 += q[i][0]; Q1 += q[i][1]; Q2 += q[i][2]; Q3 += q[i][3];
     }
     const double M = sqrt(Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3);
     const double b1 = -Q1 / M, b2 = -Q2 / M, b3 = -Q3 / M;
-    const double x = rs / M, g = Q0 / M, a = 1.0 / (1.0 + g);
+    const S x = rs / M;
+    const double g = Q0 / M, a = 1.0 / (1.0 + g);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        const double bq = b1 * p[i][1] + b2 * p[i][2] + b3 * p[i][3];
-        const double q0 = p[i][0];
+        const double bq = b1 * q[i][1] + b2 * q[i][2] + b3 * q[i][3];
+        const double q0 = q[i][0];
         p[i][0] = x * (g * q0 + bq);
-        p[i][1] = x * (p[i][1] + b1 * q0 + a * bq * b1);
-        p[i][2] = x * (p[i][2] + b2 * q0 + a * bq * b2);
-        p[i][3] = x * (p[i][3] + b3 * q0 + a * bq * b3);
+        p[i][1] = x * (q[i][1] + b1 * q0 + a * bq * b1);
+        p[i][2] = x * (q[i][2] + b2 * q0 + a * bq * b2);
+        p[i][3] = x * (q[i][3] + b3 * q0 + a * bq * b3);
     }
-    double msum = 0.0;
+    S msum = S(0.0);
     bool massive = false;
 #pragma unroll
-    for (int i = 0; i < N; ++i) { msum += m[i]; massive |= (m[i] != 0.0); }
+    for (int i = 0; i < N; ++i) { msum = msum + m[i]; massive |= (val(m[i]) != 0.0); }
     if (!massive) return vol_massless;
-    if (msum >= rs) return 0.0;
-    double xi = sqrt(1.0 - (msum / rs) * (msum / rs));
-    double e2[N];
+    if (msum >= rs) return S(0.0);
+    S xi = sqrt(1.0 - (msum / rs) * (msum / rs));
+    S e2[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) e2[i] = p[i][0] * p[i][0];
     for (int it = 0; it < 100; ++it) {
-        double f = -rs, fp = 0.0;
+        S f = -rs, fp = S(0.0);
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            const double ei = sqrt(m[i] * m[i] + xi * xi * e2[i]);
-            f += ei;
-            fp += xi * e2[i] / ei;
+            const S ei = sqrt(m[i] * m[i] + xi * xi * e2[i]);
+            f = f + ei;
+            fp = fp + xi * e2[i] / ei;
         }
-        xi -= f / fp;
-        if (fabs(f) < 1e-15 * rs) break;
+        xi = xi - f / fp;
+        if (fabs(val(f)) < 1e-15 * val(rs)) break;
     }
-    double sk = 0.0, sk2e = 0.0, prod = 1.0;
+    if constexpr (is_dual<S>::value) {
+        // one more Newton step at the converged point carries the derivative
+        // of xi through the implicit-function relation sum_i E_i(xi) = rs
+        S f = -rs, fp = S(0.0);
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const S ei = sqrt(m[i] * m[i] + xi * xi * e2[i]);
+            f = f + ei;
+            fp = fp + xi * e2[i] / ei;
+        }
+        xi = xi - f / fp;
+    }
+    S sk = S(0.0), sk2e = S(0.0), prod = S(1.0);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
-        const double ka = xi * p[i][0];
-        const double e = sqrt(m[i] * m[i] + ka * ka);
-        p[i][1] *= xi; p[i][2] *= xi; p[i][3] *= xi;
+        const S ka = xi * p[i][0];
+        const S e = sqrt(m[i] * m[i] + ka * ka);
+        p[i][1] = p[i][1] * xi; p[i][2] = p[i][2] * xi; p[i][3] = p[i][3] * xi;
         p[i][0] = e;
-        sk += ka;
-        sk2e += ka * ka / e;
-        prod *= ka / e;
+        sk = sk + ka;
+        sk2e = sk2e + ka * ka / e;
+        prod = prod * (ka / e);
     }
-    double pw = 1.0;
-    const double r = sk / rs;
+    S pw = S(1.0);
+    const S r = sk / rs;
 #pragma unroll
-    for (int i = 0; i < 2 * N - 3; ++i) pw *= r;
+    for (int i = 0; i < 2 * N - 3; ++i) pw = pw * r;
     return vol_massless * pw * prod * rs / sk2e;
 }
 
@@ -172,14 +188,16 @@ __device__ __forceinline__ double rambo(double rs, const double (&m)[N], const d
 // the ends (LHAPDF6 log-bicubic, EPJC 75 (2015) 132).  g: [ix][iq] x f values.
 struct PdfGeom { int nx, nq; double lx0, hx, lq0, lq1, hq; };
 
-__device__ __forceinline__ double hermite3(double f0, double f1, double d0, double d1, double h, double t)
+template <typename A, typename B>
+__device__ __forceinline__ B hermite3(A f0, A f1, A d0, A d1, double h, B t)
 {
-    const double t2 = t * t, t3 = t2 * t;
-    return (2.0 * t3 - 3.0 * t2 + 1.0) * f0 + (t3 - 2.0 * t2 + t) * h * d0 + (-2.0 * t3 + 3.0 * t2) * f1
-           + (t3 - t2) * h * d1;
+    const B t2 = t * t, t3 = t2 * t;
+    return (2.0 * t3 - 3.0 * t2 + 1.0) * f0 + (t3 - 2.0 * t2 + t) * (h * d0) + (-2.0 * t3 + 3.0 * t2) * f1
+           + (t3 - t2) * (h * d1);
 }
 
-__device__ __forceinline__ double pdf_row(const double* g, const PdfGeom& G, int i, int jr, double t)
+template <typename S>
+__device__ __forceinline__ S pdf_row(const double* g, const PdfGeom& G, int i, int jr, S t)
 {
     const int nq = G.nq, nx = G.nx;
     const double f0 = g[i * nq + jr], f1 = g[(i + 1) * nq + jr];
@@ -188,23 +206,26 @@ __device__ __forceinline__ double pdf_row(const double* g, const PdfGeom& G, int
     return hermite3(f0, f1, d0, d1, G.hx, t);
 }
 
-__device__ __forceinline__ double pdf_xf(const double* g, const PdfGeom& G, double x, double q2)
+// x f(x, Q^2); S is double or Dual<double> (the cells are chosen from the values)
+template <typename S>
+__device__ __forceinline__ S pdf_xf(const double* g, const PdfGeom& G, S x, S q2)
 {
-    const double lx = log(x);
-    double lq = log(q2);
-    lq = lq < G.lq0 ? G.lq0 : (lq > G.lq1 ? G.lq1 : lq);
-    int i = (int)floor((lx - G.lx0) / G.hx);
+    const S lx = log(x);
+    S lq = log(q2);
+    if (val(lq) < G.lq0) lq = S(G.lq0);
+    if (val(lq) > G.lq1) lq = S(G.lq1);
+    int i = (int)floor((val(lx) - G.lx0) / G.hx);
     i = i < 0 ? 0 : (i > G.nx - 2 ? G.nx - 2 : i);
-    int j = (int)floor((lq - G.lq0) / G.hq);
+    int j = (int)floor((val(lq) - G.lq0) / G.hq);
     j = j < 0 ? 0 : (j > G.nq - 2 ? G.nq - 2 : j);
-    const double t = (lx - (G.lx0 + i * G.hx)) / G.hx;
-    const double s = (lq - (G.lq0 + j * G.hq)) / G.hq;
-    const double r1 = pdf_row(g, G, i, j, t);
-    const double r2 = pdf_row(g, G, i, j + 1, t);
-    const double r0 = j > 0 ? pdf_row(g, G, i, j - 1, t) : 0.0;
-    const double r3 = (j + 2 < G.nq) ? pdf_row(g, G, i, j + 2, t) : 0.0;
-    const double dj = j == 0 ? (r2 - r1) / G.hq : (r2 - r0) / (2.0 * G.hq);
-    const double dj1 = (j + 1 == G.nq - 1) ? (r2 - r1) / G.hq : (r3 - r1) / (2.0 * G.hq);
+    const S t = (lx - (G.lx0 + i * G.hx)) / G.hx;
+    const S s = (lq - (G.lq0 + j * G.hq)) / G.hq;
+    const S r1 = pdf_row(g, G, i, j, t);
+    const S r2 = pdf_row(g, G, i, j + 1, t);
+    const S r0 = j > 0 ? pdf_row(g, G, i, j - 1, t) : S(0.0);
+    const S r3 = (j + 2 < G.nq) ? pdf_row(g, G, i, j + 2, t) : S(0.0);
+    const S dj = j == 0 ? (r2 - r1) / G.hq : (r2 - r0) / (2.0 * G.hq);
+    const S dj1 = (j + 1 == G.nq - 1) ? (r2 - r1) / G.hq : (r3 - r1) / (2.0 * G.hq);
     return hermite3(r1, r2, dj, dj1, G.hq, s);
 }
 

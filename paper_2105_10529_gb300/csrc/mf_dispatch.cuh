@@ -17,6 +17,41 @@ struct ProcOps {
                             const EwParams& ew, int nblk, cudaStream_t s);
 };
 
+// Derivative kernels of one process, built in their own translation units.
+struct GradOpsTable {
+    cudaError_t (*grad)(int prec, const KParams& kp, int nblk, double* partials, int k_as, double alpha_s,
+                        cudaStream_t s);
+    cudaError_t (*evaluate_grad)(int prec, const double* mom, long long n, double* me2, double* dme2, double mt,
+                                 double gs, int nblk, cudaStream_t s);
+    int k_as;          // power of alpha_s in |M|^2
+    bool has_fp64;     // FP64 (Dual<double>) derivative built
+};
+
+const GradOpsTable* grad_gg_tt();
+const GradOpsTable* grad_gg_ttg();
+const GradOpsTable* grad_gg_ttgg();
+
+template <class P, class ME, bool FP64>
+struct GradOps {
+    static cudaError_t grad(int prec, const KParams& kp, int nblk, double* partials, int k_as, double alpha_s,
+                            cudaStream_t s)
+    {
+        const size_t sm = sizeof(double) * (P::D * (kp.nb + 1) + 16);
+        if (prec) grad_kernel<P, Dual<float>><<<nblk, 128, sm, s>>>(kp, partials, k_as, alpha_s);
+        else if constexpr (FP64) grad_kernel<P, Dual<double>><<<nblk, 128, sm, s>>>(kp, partials, k_as, alpha_s);
+        else return cudaErrorNotSupported;
+        return cudaGetLastError();
+    }
+    static cudaError_t evaluate_grad(int prec, const double* mom, long long n, double* me2, double* dme2, double mt,
+                                     double gs, int nblk, cudaStream_t s)
+    {
+        if (prec) evaluate_grad_kernel<ME, Dual<float>><<<nblk, 128, 0, s>>>(mom, n, me2, dme2, mt, gs);
+        else if constexpr (FP64) evaluate_grad_kernel<ME, Dual<double>><<<nblk, 128, 0, s>>>(mom, n, me2, dme2, mt, gs);
+        else return cudaErrorNotSupported;
+        return cudaGetLastError();
+    }
+};
+
 const ProcOps* ops_ee_mumu();
 const ProcOps* ops_gg_tt();
 const ProcOps* ops_gg_ttg();

@@ -21,6 +21,7 @@
 // propagator denominators, the spinor normalisations omega) are computed
 // per event in FP64 and passed in as R.
 #pragma once
+#include "mf_dual.cuh"
 
 namespace mf {
 
@@ -87,6 +88,34 @@ template <typename R> __device__ __forceinline__ cx<R> conjc(cx<R> a) { return m
 // volatile read of a per-event invariant: re-read at every use instead of
 // being held in a register across the helicity body
 template <typename R> __device__ __forceinline__ R ldv(const R& x) { return *(const volatile R*)&x; }
+template <typename T> __device__ __forceinline__ Dual<T> ldv(const Dual<T>& x) { return Dual<T>(ldv(x.v), ldv(x.d)); }
+
+// reads and writes of the colour-flow accumulators kept in shared memory
+template <typename R> __device__ __forceinline__ R vget(const volatile R& x) { return x; }
+template <typename T> __device__ __forceinline__ Dual<T> vget(const volatile Dual<T>& x) { return Dual<T>(x.v, x.d); }
+template <typename R> __device__ __forceinline__ void vset(volatile R& x, R a) { x = a; }
+template <typename T> __device__ __forceinline__ void vset(volatile Dual<T>& x, Dual<T> a) { x.v = a.v; x.d = a.d; }
+// jamp += c a for c = +1, -1, +i, -i, and a general complex c
+template <typename R> __device__ __forceinline__ void jadd_p(volatile cx<R>& j, cx<R> a)
+{
+    vset(j.r, vget(j.r) + a.r); vset(j.i, vget(j.i) + a.i);
+}
+template <typename R> __device__ __forceinline__ void jadd_m(volatile cx<R>& j, cx<R> a)
+{
+    vset(j.r, vget(j.r) - a.r); vset(j.i, vget(j.i) - a.i);
+}
+template <typename R> __device__ __forceinline__ void jadd_pi(volatile cx<R>& j, cx<R> a)
+{
+    vset(j.r, vget(j.r) - a.i); vset(j.i, vget(j.i) + a.r);
+}
+template <typename R> __device__ __forceinline__ void jadd_mi(volatile cx<R>& j, cx<R> a)
+{
+    vset(j.r, vget(j.r) + a.i); vset(j.i, vget(j.i) - a.r);
+}
+template <typename R> __device__ __forceinline__ void jadd_c(volatile cx<R>& j, cx<R> a, R cr, R ci)
+{
+    vset(j.r, vget(j.r) + (cr * a.r - ci * a.i)); vset(j.i, vget(j.i) + (cr * a.i + ci * a.r));
+}
 
 template <typename R> __device__ __forceinline__ FermionBasis<R> load_basis(const FermionBasis<R>& f)
 {
@@ -351,37 +380,38 @@ template <typename R> __device__ __forceinline__ void vvvv_amp(const W4<R>& J1, 
 
 // ------------------------------------------------------------------ per-event external pieces (FP64)
 
-__device__ __forceinline__ double mdot(const double* a, const double* b)
+template <typename S> __device__ __forceinline__ S mdot(const S* a, const S* b)
 {
     return a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3];
 }
 
 // Transverse basis of a massless momentum p (e1, e2 spatial parts, scaled by 1/sqrt 2).
-__device__ __forceinline__ void gluon_basis(const double* p, double* e1, double* e2)
+template <typename S>
+__device__ __forceinline__ void gluon_basis(const S* p, S* e1, S* e2)
 {
     const double r2 = 0.70710678118654752440;
-    double pt2 = p[1] * p[1] + p[2] * p[2];
-    double pa = sqrt(pt2 + p[3] * p[3]);
-    double pt = sqrt(pt2);
-    double ct = p[3] / pa, st = pt / pa;
-    double cp = pt > 0.0 ? p[1] / pt : 1.0;
-    double sp = pt > 0.0 ? p[2] / pt : 0.0;
+    const S pt2 = p[1] * p[1] + p[2] * p[2];
+    const S pa = sqrt(pt2 + p[3] * p[3]);
+    const S pt = sqrt(pt2);
+    const S ct = p[3] / pa, st = pt / pa;
+    const S cp = val(pt) > 0.0 ? p[1] / pt : S(1.0);
+    const S sp = val(pt) > 0.0 ? p[2] / pt : S(0.0);
     e1[0] = r2 * ct * cp; e1[1] = r2 * ct * sp; e1[2] = -r2 * st;
-    e2[0] = -r2 * sp;     e2[1] = r2 * cp;      e2[2] = 0.0;
+    e2[0] = -r2 * sp;     e2[1] = r2 * cp;      e2[2] = S(0.0);
 }
 
 // Helicity eigenspinors and omega_+/- of a fermion of mass m (FP64);
 // omega_- = m / omega_+ avoids the cancellation in E - |p|.
-template <typename R> __device__ __forceinline__ FermionBasis<R> fermion_basis(const double* p, double m)
+template <typename R, typename S> __device__ __forceinline__ FermionBasis<R> fermion_basis(const S* p, S m)
 {
     FermionBasis<R> f;
-    double pa = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
-    double ppz = pa + p[3];
-    double omp = sqrt(p[0] + pa);
-    double omm = m > 0.0 ? m / omp : sqrt(fmax(p[0] - pa, 0.0));
+    const S pa = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
+    const S ppz = pa + p[3];
+    const S omp = sqrt(p[0] + pa);
+    const S omm = val(m) > 0.0 ? m / omp : sqrt(fmax(p[0] - pa, 0.0));
     f.om[0] = R(omp); f.om[1] = R(omm);
-    if (ppz > 1e-12 * (pa + 1e-300)) {
-        double n = 1.0 / sqrt(2.0 * pa * ppz);
+    if (val(ppz) > 1e-12 * (val(pa) + 1e-300)) {
+        const S n = 1.0 / sqrt(2.0 * pa * ppz);
         f.chi[0][0] = mkc(R(ppz * n), R(0));
         f.chi[0][1] = mkc(R(p[1] * n), R(p[2] * n));
         f.chi[1][0] = mkc(R(-p[1] * n), R(p[2] * n));

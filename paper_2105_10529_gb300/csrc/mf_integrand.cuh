@@ -164,65 +164,78 @@ __device__ __forceinline__ int cuts_tops(const KParams& kp, const double (&pl)[P
 // Everything of one event except the matrix element: uniforms, VEGAS map,
 // parton map, RAMBO, lab boost, cuts, scale and PDFs.  pref receives the
 // weight factor that multiplies |M|^2: f1 f2 / (2 shat) W J_parton J_VEGAS
-// in pb GeV^2.
+// in pb GeV^2.  S is double, or Dual<double> carrying d/d m_t (then the cut
+// decisions are taken on the values, i.e. at the base point).
+template <class P, typename S>
+__device__ __forceinline__ void kinematics_tops_t(const KParams& kp, const double* sgrid, const double* spdf,
+                                                  unsigned long long ev, S mt, EventOut<P::D>& o,
+                                                  S (&p)[P::NEXT][4], S& pref)
+{
+    constexpr int NF = P::NF, D = P::D;
+    event_uniforms<D>(ev, kp.iteration, kp.channel, kp.key, o.u);
+    const double jv = vegas_map<D>(sgrid, kp.nb, o.u, o.x, o.bins);
+    S ln_tau0;
+    if constexpr (is_dual<S>::value) ln_tau0 = log(4.0 * mt * mt / kp.S);
+    else ln_tau0 = kp.ln_tau0;
+    S x1, x2, jp;
+    parton_map(o.x[0], o.x[1], ln_tau0, x1, x2, jp);
+    const S shat = x1 * x2 * kp.S;
+    const S rs = sqrt(shat);
+    S m[NF];
+#pragma unroll
+    for (int i = 0; i < NF; ++i) m[i] = i < 2 ? mt : S(0.0);
+    S pf[NF][4];
+    S vol = S(kp.vol_const);
+#pragma unroll
+    for (int i = 0; i < NF - 2; ++i) vol = vol * shat;
+    const S wps = rambo<NF>(rs, m, o.x + 2, pf, vol);
+    const S h = 0.5 * rs;
+    p[0][0] = h; p[0][1] = S(0.0); p[0][2] = S(0.0); p[0][3] = h;
+    p[1][0] = h; p[1][1] = S(0.0); p[1][2] = S(0.0); p[1][3] = -h;
+#pragma unroll
+    for (int i = 0; i < NF; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) p[2 + i][c] = pf[i][c];
+    // longitudinal boost to the lab frame, rapidity ln(x1/x2)/2 (values only: it feeds the cuts)
+    const double x1v = val(x1), x2v = val(x2);
+    const double sq = sqrt(x1v * x2v);
+    const double ch = (x1v + x2v) / (2.0 * sq), sh = (x1v - x2v) / (2.0 * sq);
+    double pl[P::NEXT][4];
+#pragma unroll
+    for (int i = 0; i < P::NEXT; ++i) {
+        pl[i][0] = ch * val(p[i][0]) + sh * val(p[i][3]);
+        pl[i][1] = val(p[i][1]);
+        pl[i][2] = val(p[i][2]);
+        pl[i][3] = ch * val(p[i][3]) + sh * val(p[i][0]);
+    }
+    o.mask = kp.mask_in ? (int)kp.mask_in[ev - kp.ev_offset] : cuts_tops<P>(kp, pl);
+    if (val(wps) <= 0.0) o.mask = 0;
+    // factorisation scale: m_t for 2 -> 2, H_T / 2 otherwise
+    S muf2;
+    if (NF == 2) {
+        muf2 = mt * mt;
+    } else {
+        S ht = S(0.0);
+#pragma unroll
+        for (int i = 2; i < P::NEXT; ++i) {
+            const S mi = (i < 4) ? mt : S(0.0);
+            ht = ht + sqrt(mi * mi + p[i][1] * p[i][1] + p[i][2] * p[i][2]);
+        }
+        muf2 = 0.25 * ht * ht;
+    }
+    const S f1 = pdf_xf(spdf, kp.pdfg, x1, muf2) / x1;
+    const S f2 = pdf_xf(spdf, kp.pdfg, x2, muf2) / x2;
+    pref = f1 * f2 / (2.0 * shat) * wps * jp * jv * GEV2_TO_PB;
+    o.me2 = 0.0;
+    o.w = 0.0;
+}
+
 template <class P>
 __device__ __forceinline__ void kinematics_tops(const KParams& kp, const double* sgrid, const double* spdf,
                                                 unsigned long long ev, EventOut<P::D>& o, double (&p)[P::NEXT][4],
                                                 double& pref)
 {
-    constexpr int NF = P::NF, D = P::D;
-    event_uniforms<D>(ev, kp.iteration, kp.channel, kp.key, o.u);
-    const double jv = vegas_map<D>(sgrid, kp.nb, o.u, o.x, o.bins);
-    double x1, x2, jp;
-    parton_map(o.x[0], o.x[1], kp.ln_tau0, x1, x2, jp);
-    const double shat = x1 * x2 * kp.S;
-    const double rs = sqrt(shat);
-    double m[NF];
-#pragma unroll
-    for (int i = 0; i < NF; ++i) m[i] = i < 2 ? kp.mt : 0.0;
-    double pf[NF][4];
-    double vol = kp.vol_const;
-#pragma unroll
-    for (int i = 0; i < NF - 2; ++i) vol *= shat;
-    const double wps = rambo<NF>(rs, m, o.x + 2, pf, vol);
-    const double h = 0.5 * rs;
-    p[0][0] = h; p[0][1] = 0.0; p[0][2] = 0.0; p[0][3] = h;
-    p[1][0] = h; p[1][1] = 0.0; p[1][2] = 0.0; p[1][3] = -h;
-#pragma unroll
-    for (int i = 0; i < NF; ++i)
-#pragma unroll
-        for (int c = 0; c < 4; ++c) p[2 + i][c] = pf[i][c];
-    // longitudinal boost to the lab frame, rapidity ln(x1/x2)/2
-    const double sq = sqrt(x1 * x2);
-    const double ch = (x1 + x2) / (2.0 * sq), sh = (x1 - x2) / (2.0 * sq);
-    double pl[P::NEXT][4];
-#pragma unroll
-    for (int i = 0; i < P::NEXT; ++i) {
-        pl[i][0] = ch * p[i][0] + sh * p[i][3];
-        pl[i][1] = p[i][1];
-        pl[i][2] = p[i][2];
-        pl[i][3] = ch * p[i][3] + sh * p[i][0];
-    }
-    o.mask = kp.mask_in ? (int)kp.mask_in[ev - kp.ev_offset] : cuts_tops<P>(kp, pl);
-    if (wps <= 0.0) o.mask = 0;
-    // factorisation scale: m_t for 2 -> 2, H_T / 2 otherwise
-    double muf2;
-    if (NF == 2) {
-        muf2 = kp.mt * kp.mt;
-    } else {
-        double ht = 0.0;
-#pragma unroll
-        for (int i = 2; i < P::NEXT; ++i) {
-            const double mi = (i < 4) ? kp.mt : 0.0;
-            ht += sqrt(mi * mi + p[i][1] * p[i][1] + p[i][2] * p[i][2]);
-        }
-        muf2 = 0.25 * ht * ht;
-    }
-    const double f1 = pdf_xf(spdf, kp.pdfg, x1, muf2) / x1;
-    const double f2 = pdf_xf(spdf, kp.pdfg, x2, muf2) / x2;
-    pref = f1 * f2 / (2.0 * shat) * wps * jp * jv * GEV2_TO_PB;
-    o.me2 = 0.0;
-    o.w = 0.0;
+    kinematics_tops_t<P, double>(kp, sgrid, spdf, ev, kp.mt, o, p, pref);
 }
 
 template <class P, typename R>
@@ -540,6 +553,81 @@ __global__ void __launch_bounds__(128) evaluate_ee_kernel(const double* __restri
         for (int i = 0; i < 4; ++i)
             for (int c = 0; c < 4; ++c) p[i][c] = mom[(e * 4 + i) * 4 + c];
         me2[e] = MeEeMumu::me2<R>(p, ew);
+    }
+}
+
+// ------------------------------------------------------------------ derivatives
+
+// Derivative pass (forward mode): every event's weight and its derivative
+// with respect to m_t in one evaluation (R = Dual<float> or Dual<double> in
+// the matrix element, Dual<double> elsewhere), at the base-point cut masks
+// and a fixed VEGAS grid.  Per CTA: sum w, sum dw/dm_t, sum (dw/dm_t)^2 and
+// sum k w / alpha_s (|M|^2 is proportional to alpha_s^k), all with the
+// estimator's 1/N, reduced deterministically.
+template <class P, typename R>
+__global__ void __launch_bounds__(128) grad_kernel(KParams kp, double* partials, int k_as, double alpha_s)
+{
+    using S = Dual<double>;
+    constexpr int D = P::D, TPB = 128, WARPS = TPB / 32;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    double* sgrid = reinterpret_cast<double*>(smem_raw);
+    double* sred = sgrid + D * (kp.nb + 1);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int i = tid; i < D * (kp.nb + 1); i += TPB) sgrid[i] = kp.grid[i];
+    __syncthreads();
+    double acc[4] = { 0.0, 0.0, 0.0, 0.0 };
+    const long long n = kp.n_events;
+    const S mt(kp.mt, 1.0), gs(kp.gs, 0.0);
+    for (long long e = (long long)blockIdx.x * TPB + tid; e < n; e += (long long)gridDim.x * TPB) {
+        EventOut<D> o;
+        S pm[P::NEXT][4], pref;
+        kinematics_tops_t<P, S>(kp, sgrid, kp.pdf, (unsigned long long)(kp.ev_offset + e), mt, o, pm, pref);
+        if (!o.mask) continue;
+        const S me = P::Me::template me2<R>(pm, mt, gs, nullptr);
+        S w = pref * me;
+        if (!isfinite(w.v) || !isfinite(w.d)) continue;
+        const double wn = w.v * kp.inv_n, dn = w.d * kp.inv_n;
+        acc[0] += wn;
+        acc[1] += dn;
+        acc[2] += dn * dn;
+        acc[3] += k_as * wn / alpha_s;
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sred[4 * warp + k] = v;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        double v = 0.0;
+        for (int w = 0; w < WARPS; ++w) v += sred[4 * w + tid];
+        partials[(size_t)blockIdx.x * 4 + tid] = v;
+    }
+}
+
+// d|M|^2 / d p for every momentum component (the components treated as
+// independent variables): one forward-mode evaluation per component.
+template <class ME, typename R>
+__global__ void __launch_bounds__(128) evaluate_grad_kernel(const double* __restrict__ mom, long long n,
+                                                            double* __restrict__ me2, double* __restrict__ dme2,
+                                                            double mt, double gs)
+{
+    using S = Dual<double>;
+    constexpr int NC = 4 * ME::NEXT;
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double p0[ME::NEXT][4];
+        for (int i = 0; i < ME::NEXT; ++i)
+            for (int c = 0; c < 4; ++c) p0[i][c] = mom[(e * ME::NEXT + i) * 4 + c];
+        for (int j = 0; j < NC; ++j) {
+            S p[ME::NEXT][4];
+            for (int i = 0; i < ME::NEXT; ++i)
+                for (int c = 0; c < 4; ++c) p[i][c] = S(p0[i][c], (4 * i + c) == j ? 1.0 : 0.0);
+            const S m = ME::template me2<R>(p, S(mt, 0.0), S(gs, 0.0), nullptr);
+            dme2[e * NC + j] = m.d;
+            if (j == 0 && me2) me2[e] = m.v;
+        }
     }
 }
 

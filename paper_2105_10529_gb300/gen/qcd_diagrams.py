@@ -309,20 +309,15 @@ def _split_cost(em: Emitter, blocks: Tuple, j: int) -> int:
 def _jadd(jv: str, a: str, c: complex) -> str:
     c = complex(c)
     re, im = c.real, c.imag
-    if im == 0:
-        if re == 1:
-            return f"{jv}.r += {a}.r; {jv}.i += {a}.i;"
-        if re == -1:
-            return f"{jv}.r -= {a}.r; {jv}.i -= {a}.i;"
-        return f"{jv}.r = fma(R({re!r}), {a}.r, {jv}.r); {jv}.i = fma(R({re!r}), {a}.i, {jv}.i);"
-    if re == 0:
-        if im == 1:
-            return f"{jv}.r -= {a}.i; {jv}.i += {a}.r;"
-        if im == -1:
-            return f"{jv}.r += {a}.i; {jv}.i -= {a}.r;"
-        return f"{jv}.r = fma(R({-im!r}), {a}.i, {jv}.r); {jv}.i = fma(R({im!r}), {a}.r, {jv}.i);"
-    return (f"{jv}.r += R({re!r}) * {a}.r - R({im!r}) * {a}.i; "
-            f"{jv}.i += R({re!r}) * {a}.i + R({im!r}) * {a}.r;")
+    if (re, im) == (1, 0):
+        return f"jadd_p({jv}, {a});"
+    if (re, im) == (-1, 0):
+        return f"jadd_m({jv}, {a});"
+    if (re, im) == (0, 1):
+        return f"jadd_pi({jv}, {a});"
+    if (re, im) == (0, -1):
+        return f"jadd_mi({jv}, {a});"
+    return f"jadd_c({jv}, {a}, R({re!r}), R({im!r}));"
 
 
 def _block_size(T) -> int:
@@ -514,22 +509,22 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     pro.append("// gluon momenta, incoming convention: gluons 0,1 incoming, the rest outgoing")
     for i, e in enumerate(gl_ext):
         sgn = "" if i < n_in else "-"
-        pro.append(f"const double kd{1 << i}[4] = {{{sgn}p[{e}][0], {sgn}p[{e}][1], {sgn}p[{e}][2], {sgn}p[{e}][3]}};")
+        pro.append(f"const S kd{1 << i}[4] = {{{sgn}p[{e}][0], {sgn}p[{e}][1], {sgn}p[{e}][2], {sgn}p[{e}][3]}};")
     needed_sums = {m for m in set(gden) | set(qsub) | set(kmasks) if bin(m).count("1") > 1}
     for m in sorted(needed_sums, key=lambda x: (bin(x).count("1"), x)):
         bits = [1 << i for i in range(k) if m >> i & 1]
         comps = ", ".join(" + ".join(f"kd{b}[{c}]" for b in bits) for c in range(4))
-        pro.append(f"const double kd{m}[4] = {{{comps}}};")
+        pro.append(f"const S kd{m}[4] = {{{comps}}};")
     for m in kmasks:
         pro.append(f"for (int c = 0; c < 4; ++c) v.K[{kidx[m]}][c] = R(kd{m}[c]);")
     pro.append("for (int c = 0; c < 4; ++c) v.p3[c] = R(p[2][c]);")
     for m in gden:
         pro.append(f"v.iG[{gidx[m]}] = R(1.0 / mdot(kd{m}, kd{m}));")
     for m in qsub:
-        pro.append(f"{{ const double q[4] = {{p[2][0] - kd{m}[0], p[2][1] - kd{m}[1], p[2][2] - kd{m}[2], p[2][3] - kd{m}[3]}};")
+        pro.append(f"{{ const S q[4] = {{p[2][0] - kd{m}[0], p[2][1] - kd{m}[1], p[2][2] - kd{m}[2], p[2][3] - kd{m}[3]}};")
         pro.append(f"  v.iQ[{qidx[m]}] = R(1.0 / (mdot(q, q) - mt * mt)); }}")
     for i, e in enumerate(gl_ext):
-        pro.append(f"{{ double a[3], b[3]; gluon_basis(p[{e}], a, b);")
+        pro.append(f"{{ S a[3], b[3]; gluon_basis(p[{e}], a, b);")
         pro.append(f"  for (int j = 0; j < 3; ++j) {{ v.e1[{i}][j] = R(a[j]); v.e2[{i}][j] = R(b[j]); }} }}")
     pro.append("v.fb3 = fermion_basis<R>(p[2], mt);")
     pro.append("v.fb4 = fermion_basis<R>(p[3], mt);")
@@ -548,7 +543,7 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     body.append("// colour-flow amplitudes accumulate in the slot (shared memory), not in registers")
     body.append("volatile cx<R>* jamp = reinterpret_cast<volatile cx<R>*>(const_cast<cx<R>*>(v.jamp));")
     body.append("#pragma unroll")
-    body.append("for (int c = 0; c < NCOL; ++c) { jamp[c].r = R(0); jamp[c].i = R(0); }")
+    body.append("for (int c = 0; c < NCOL; ++c) { vset(jamp[c].r, R(0)); vset(jamp[c].i, R(0)); }")
     for i, e in enumerate(gl_ext):
         out = "false" if i < n_in else "true"
         body.append(f"W4<R> g{i}; {{ R a[3], b[3]; for (int j = 0; j < 3; ++j) {{ a[j] = ldv(v.e1[{i}][j]); b[j] = ldv(v.e2[{i}][j]); }}")
@@ -561,7 +556,7 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     cs: List[str] = []
     cs.append("cx<R> J[NCOL];")
     cs.append("#pragma unroll")
-    cs.append("for (int c = 0; c < NCOL; ++c) J[c] = mkc(R(jamp[c].r), R(jamp[c].i));")
+    cs.append("for (int c = 0; c < NCOL; ++c) J[c] = mkc(vget(jamp[c].r), vget(jamp[c].i));")
     cs.append("R me = R(0);")
     for i in range(ncol):
         tr = [f"R({float(CI[i][i])!r}) * J[{i}].r"]
@@ -607,8 +602,11 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("  // p: momenta (E,px,py,pz) incoming first: g, g, t, tbar, g...")
     src.append("  // slot: this thread's Inv<R> in shared memory, or null for a private local copy")
     src.append("  // SYNC: a CTA barrier after every helicity (every thread of the CTA must call)")
+    src.append("  // R: float or double (or Dual of them for derivatives); the momenta, masses and")
+    src.append("  // the result use the matching FP64 scalar S = Widen<R>::type")
     src.append("  template <typename R, bool SYNC = false>")
-    src.append("  __device__ static double me2(const double (&p)[NEXT][4], double mt, double gs, void* slot);")
+    src.append("  __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],")
+    src.append("                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot);")
     src.append("  template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }")
     src.append("};")
     src.append("")
@@ -627,11 +625,13 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("}")
     src.append("")
     src.append("template <typename R, bool SYNC>")
-    src.append(f"__device__ __noinline__ double me2_{name}_impl(const double* pflat, double mt, double gs, void* slot)")
+    src.append(f"__device__ __noinline__ typename Widen<R>::type me2_{name}_impl(const typename Widen<R>::type* pflat,")
+    src.append("    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot)")
     src.append("{")
+    src.append("    using S = typename Widen<R>::type;")
     src.append(f"    constexpr int NEXT = Me_{name}::NEXT, NHEL = Me_{name}::NHEL, NGLUON = Me_{name}::NGLUON;")
     src.append(f"    constexpr double COLOUR_DEN = Me_{name}::COLOUR_DEN, AVG = Me_{name}::AVG, SYM = Me_{name}::SYM;")
-    src.append("    double p[NEXT][4];")
+    src.append("    S p[NEXT][4];")
     src.append("    for (int i = 0; i < NEXT; ++i)")
     src.append("        for (int c = 0; c < 4; ++c) p[i][c] = pflat[4 * i + c];")
     src.append(f"    Me_{name}::Inv<R> local;   // used when the caller has no shared-memory slot")
@@ -648,13 +648,14 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("        if (SYNC) __syncthreads();")
     src.append("    }")
     src.append("    acc *= R(2);")
-    src.append("    double gk = 1.0;")
-    src.append("    for (int i = 0; i < NGLUON; ++i) gk *= gs * gs;")
-    src.append("    return double(acc) / COLOUR_DEN * gk * AVG * SYM;")
+    src.append("    S gk = S(1.0);")
+    src.append("    for (int i = 0; i < NGLUON; ++i) gk = gk * (gs * gs);")
+    src.append("    return S(acc) / COLOUR_DEN * gk * AVG * SYM;")
     src.append("}")
     src.append("")
     src.append("template <typename R, bool SYNC>")
-    src.append(f"__device__ double Me_{name}::me2(const double (&p)[NEXT][4], double mt, double gs, void* slot)")
+    src.append(f"__device__ typename Widen<R>::type Me_{name}::me2(const typename Widen<R>::type (&p)[NEXT][4],")
+    src.append("    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot)")
     src.append("{")
     src.append(f"    return me2_{name}_impl<R, SYNC>(&p[0][0], mt, gs, slot);")
     src.append("}")

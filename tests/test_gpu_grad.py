@@ -1,0 +1,175 @@
+"""Derivatives on the GPU: d sigma/d alpha_s exact, d sigma/d m_t against
+central finite differences (GPU and oracle, frozen masks, h = 1e-3 m_t),
+mixed against FP64, d|M|^2/dp against finite differences and Lorentz
+invariance, the gg -> t tbar pathwise derivative against the derivative of a
+deterministic quadrature, and the torch.autograd wrappers."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2105_10529_gb300 import inputs as IN
+from tests.gpu_common import PHYS, random_grid
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+K_AS = {IN.GG_TT: 2, IN.GG_TTG: 3, IN.GG_TTGG: 4}
+
+
+@pytest.fixture(scope="module")
+def pdf_grid():
+    return IN.make_pdf_grid()
+
+
+def ctx_for(proc, prec, pdf_grid):
+    from paper_2105_10529_gb300.api import Context
+    return Context(PHYS[proc], pdf_grid, precision=prec)
+
+
+def gpu_fd(ctx, proc, phys, grid, n, mask, h, it):
+    vals = []
+    for m in (phys.mt + h, phys.mt - h):
+        ctx.set_couplings(m, phys.alpha_s)
+        s, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=it, mask_in=mask)
+        vals.append(float(s[0]))
+    ctx.set_couplings(phys.mt, phys.alpha_s)
+    return (vals[0] - vals[1]) / (2 * h)
+
+
+@pytest.mark.parametrize("proc,prec", [(IN.GG_TT, 0), (IN.GG_TTG, 0), (IN.GG_TT, 1), (IN.GG_TTG, 1), (IN.GG_TTGG, 1)])
+def test_mt_and_alphas_derivatives(proc, prec, pdf_grid):
+    phys = PHYS[proc]
+    grid = torch.tensor(random_grid(IN.DIM[proc], seed=20 + proc), device="cuda")
+    n = {IN.GG_TT: 20000, IN.GG_TTG: 4000, IN.GG_TTGG: 1000}[proc]
+    it = 6
+    ctx = ctx_for(proc, prec, pdf_grid)
+    d = ctx.vegas_pass_grad(proc, phys.sqrt_s, grid, n, iteration=it).cpu().numpy()
+    base, ev = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=it, want_events=True, fields=("mask",))
+    # the derivative pass reproduces the value of the pass
+    assert abs(d[0] / float(base[0]) - 1) < (1e-12 if prec == 0 else 1e-5)
+    # d sigma / d alpha_s = k sigma / alpha_s exactly
+    assert abs(d[3] - K_AS[proc] * d[0] / phys.alpha_s) <= 1e-12 * abs(d[3])
+    # d sigma / d m_t against central differences of the FP64 value pass with frozen masks
+    ctx64 = ctx_for(proc, 0, pdf_grid)
+    fd = gpu_fd(ctx64, proc, phys, grid, n, ev["mask"], 1e-3 * phys.mt, it)
+    assert abs(d[1] - fd) < 1e-4 * abs(fd), (d[1], fd)
+    ctx.close(); ctx64.close()
+
+
+@pytest.mark.parametrize("proc", [IN.GG_TT, IN.GG_TTG])
+def test_mt_derivative_matches_oracle_fd(proc, pdf_grid):
+    phys = PHYS[proc]
+    gnp = random_grid(IN.DIM[proc], seed=30 + proc)
+    grid = torch.tensor(gnp, device="cuda")
+    n = 3000 if proc == IN.GG_TT else 600
+    it = 2
+    ctx = ctx_for(proc, 0, pdf_grid)
+    d = ctx.vegas_pass_grad(proc, phys.sqrt_s, grid, n, iteration=it).cpu().numpy()
+    opdf = O.Pdf(pdf_grid)
+    base = O.vegas_pass(proc, phys, opdf, gnp, n, iteration=it, want_mask=True)
+    h = 1e-3 * phys.mt
+    hi = O.vegas_pass(proc, IN.Physics(**{**phys.as_dict(), "mt": phys.mt + h}), opdf, gnp, n, it, mask_in=base["mask"])
+    lo = O.vegas_pass(proc, IN.Physics(**{**phys.as_dict(), "mt": phys.mt - h}), opdf, gnp, n, it, mask_in=base["mask"])
+    fd = (hi["sum_w"] - lo["sum_w"]) / (2 * h)
+    assert abs(d[1] - fd) < 1e-4 * abs(fd), (d[1], fd)
+    ctx.close()
+
+
+@pytest.mark.parametrize("proc", [IN.GG_TT, IN.GG_TTG])
+def test_mixed_derivative_matches_fp64(proc, pdf_grid):
+    phys = PHYS[proc]
+    grid = torch.tensor(random_grid(IN.DIM[proc], seed=40 + proc), device="cuda")
+    n = 20000
+    a = ctx_for(proc, 0, pdf_grid).vegas_pass_grad(proc, phys.sqrt_s, grid, n, iteration=3).cpu().numpy()
+    b = ctx_for(proc, 1, pdf_grid).vegas_pass_grad(proc, phys.sqrt_s, grid, n, iteration=3).cpu().numpy()
+    assert abs(b[1] / a[1] - 1) < 1e-5
+
+
+def boost_direction(p):
+    """Infinitesimal boost along z of every momentum: dE = p_z, dp_z = E."""
+    d = np.zeros_like(p)
+    d[..., 0] = p[..., 3]
+    d[..., 3] = p[..., 0]
+    return d
+
+
+@pytest.mark.parametrize("proc,prec", [(IN.GG_TT, 0), (IN.GG_TTG, 0), (IN.GG_TTGG, 1)])
+def test_evaluate_gradient(proc, prec, pdf_grid):
+    phys = PHYS[proc]
+    rng = np.random.default_rng(50 + proc)
+    n_ext = IN.N_EXT[proc]
+    nf = n_ext - 2
+    moms = []
+    for rs in (800.0, 2500.0):
+        for _ in range(3):
+            pf, _ = O.rambo(nf, rs, [phys.mt, phys.mt] + [0.0] * (nf - 2), rng.random(4 * nf))
+            moms.append(np.vstack([[[rs / 2, 0, 0, rs / 2], [rs / 2, 0, 0, -rs / 2]], pf]))
+    P = np.array(moms)
+    ctx = ctx_for(proc, prec, pdf_grid)
+    ctx64 = ctx_for(proc, 0, pdf_grid)
+    me, g = ctx.evaluate_grad(proc, torch.tensor(P, device="cuda"))
+    g = g.cpu().numpy()
+    for e in range(len(P)):
+        for (i, c) in [(2, 0), (2, 3), (3, 1), (0, 0), (n_ext - 1, 2)]:
+            # fourth-order central difference (error O(h^4))
+            h = 1e-4 * abs(P[e, i, 0])
+            q = np.repeat(P[e:e + 1], 4, axis=0)
+            for r, k in enumerate((2, 1, -1, -2)):
+                q[r, i, c] += k * h
+            v = ctx64.evaluate(proc, torch.tensor(q, device="cuda")).cpu().numpy()
+            fd = (-v[0] + 8 * v[1] - 8 * v[2] + v[3]) / (12 * h)
+            scale = np.abs(g[e]).max() * abs(P[e, i, 0])
+            assert abs(g[e, i, c] - fd) * abs(P[e, i, 0]) < (1e-7 if prec == 0 else 3e-5) * scale, (e, i, c, g[e, i, c], fd)
+        # |M|^2 is boost invariant: no derivative along the boost generator
+        d = boost_direction(P[e])
+        along = float(np.sum(g[e] * d))
+        assert abs(along) < (1e-9 if prec == 0 else 1e-4) * float(np.sum(np.abs(g[e] * d))), along
+    ctx.close(); ctx64.close()
+
+
+def test_gg_tt_pathwise_derivative_matches_quadrature(pdf_grid):
+    """Without cuts the pathwise derivative is unbiased for d sigma/d m_t:
+    compare with the m_t derivative of a deterministic quadrature."""
+    from tests.test_oracle_integration import sigma_hadronic_quadrature, sig_hat_gg
+    proc = IN.GG_TT
+    phys = PHYS[proc]
+    opdf = O.Pdf(pdf_grid)
+    h = 1e-3 * phys.mt
+    q = [sigma_hadronic_quadrature(IN.Physics(**{**phys.as_dict(), "mt": m}), opdf,
+                                   sig_hat_gg(IN.Physics(**{**phys.as_dict(), "mt": m})), 0, 0, n=96)
+         for m in (phys.mt + h, phys.mt - h)]
+    dq = (q[0] - q[1]) / (2 * h)
+    ctx = ctx_for(proc, 0, pdf_grid)
+    grid = torch.tensor(O.vegas_init(IN.DIM[proc]), device="cuda")
+    n = 4_000_000
+    d = ctx.vegas_pass_grad(proc, phys.sqrt_s, grid, n, iteration=0).cpu().numpy()
+    err = math.sqrt(max(d[2] * n - d[1] ** 2, 0.0) / (n - 1))
+    assert abs(d[1] - dq) < 4 * err, (d[1], dq, err)
+    ctx.close()
+
+
+def test_autograd_wrappers(pdf_grid):
+    from paper_2105_10529_gb300.autograd import cross_section, matrix_element
+    proc = IN.GG_TTG
+    phys = PHYS[proc]
+    ctx = ctx_for(proc, 0, pdf_grid)
+    grid = torch.tensor(random_grid(IN.DIM[proc], seed=60), device="cuda")
+    mt = torch.tensor(phys.mt, dtype=torch.float64, requires_grad=True)
+    a_s = torch.tensor(phys.alpha_s, dtype=torch.float64, requires_grad=True)
+    sig = cross_section(mt, a_s, ctx, proc, phys.sqrt_s, grid, 3000, iteration=1)
+    sig.backward()
+    d = ctx.vegas_pass_grad(proc, phys.sqrt_s, grid, 3000, iteration=1).cpu().numpy()
+    assert abs(sig.item() - d[0]) <= 1e-12 * abs(d[0])
+    assert abs(mt.grad.item() - d[1]) <= 1e-12 * abs(d[1])
+    assert abs(a_s.grad.item() - d[3]) <= 1e-12 * abs(d[3])
+    rng = np.random.default_rng(61)
+    pf, _ = O.rambo(3, 1500.0, [phys.mt, phys.mt, 0.0], rng.random(12))
+    P = torch.tensor(np.vstack([[[750.0, 0, 0, 750.0], [750.0, 0, 0, -750.0]], pf])[None], device="cuda",
+                     requires_grad=True)
+    m2 = matrix_element(P, ctx, proc)
+    m2.sum().backward()
+    _, g = ctx.evaluate_grad(proc, P.detach())
+    assert torch.allclose(P.grad, g, rtol=1e-14, atol=0)
+    ctx.close()
