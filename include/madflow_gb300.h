@@ -40,9 +40,9 @@ extern "C" {
 /* Processes (particle order of the momenta):
  *   MF_EE_MUMU  e-(1) e+(2) -> mu-(3) mu+(4), photon + Z, massless
  *   MF_GG_TT    g(1) g(2) -> t(3) tbar(4)
- *   MF_UU_TT    u(1) ubar(2) -> t(3) tbar(4)           (reserved, not built)
+ *   MF_UU_TT    u(1) ubar(2) -> t(3) tbar(4)
  *   MF_GG_TTG   g(1) g(2) -> t(3) tbar(4) g(5)
- *   MF_UG_TTU   u(1) g(2) -> t(3) tbar(4) u(5)         (reserved, not built)
+ *   MF_UG_TTU   u(1) g(2) -> t(3) tbar(4) u(5)
  *   MF_GG_TTGG  g(1) g(2) -> t(3) tbar(4) g(5) g(6)                          */
 enum mf_process { MF_EE_MUMU = 0, MF_GG_TT = 1, MF_UU_TT = 2, MF_GG_TTG = 3, MF_UG_TTU = 4, MF_GG_TTGG = 5 };
 
@@ -192,16 +192,17 @@ int mf_set_couplings(struct mf_ctx *ctx, double mt, double alpha_s);
  * recomputed from the random numbers and stored nowhere.
  * out_dev [4] (device): sigma_hat, d sigma_hat / d m_t, sum_e (dw_e/dm_t / N)^2
  * (for the MC error of the derivative) and d sigma_hat / d alpha_s.
- * Gluon processes only (MF_ERR_UNSUPPORTED otherwise); for g g -> t tbar g g
- * only the MF_MIXED derivative is built.  Does not synchronise. */
+ * Top-pair processes only (MF_ERR_UNSUPPORTED for e+ e- -> mu+ mu-); for
+ * g g -> t tbar g g only the MF_MIXED derivative is built.  Does not
+ * synchronise. */
 int mf_vegas_pass_grad(struct mf_ctx *ctx, int process, double sqrt_s, const double *grid_dev, long long n_events,
                        long long ev_offset, unsigned int iteration, const unsigned char *mask_in_dev, double *out_dev);
 
 /* d|M|^2/dp: the derivatives of the averaged |M|^2 of mf_evaluate with
  * respect to every momentum component, the components taken as independent
  * variables.  momenta_dev [n][n_ext][4]; me2_dev [n] (nullable) receives
- * |M|^2; dme2_dp_dev [n][n_ext][4].  Gluon processes only (g g -> t tbar g g:
- * MF_MIXED only).  Does not synchronise. */
+ * |M|^2; dme2_dp_dev [n][n_ext][4].  Top-pair processes only
+ * (g g -> t tbar g g: MF_MIXED only).  Does not synchronise. */
 int mf_evaluate_grad(struct mf_ctx *ctx, int process, const double *momenta_dev, long long n, double *me2_dev,
                      double *dme2_dp_dev);
 
@@ -209,6 +210,61 @@ int mf_evaluate_grad(struct mf_ctx *ctx, int process, const double *momenta_dev,
  * factor included) of n phase-space points.  momenta_dev: [n][n_ext][4];
  * me2_dev: [n].  Does not synchronise. */
 int mf_evaluate(struct mf_ctx *ctx, int process, const double *momenta_dev, long long n, double *me2_dev);
+
+/* Batched channels: several partonic subprocesses of one hadronic process
+ * (p p -> t tbar + jets), each integrated on its own VEGAS grid, the sum
+ * being the hadronic cross section.  The paper integrates one process at a
+ * time (Sec. 2.1, the integrate(process, ...) call); batching them into one
+ * launch has no counterpart there.  n_ch (1..8) channels, processes[i] one of the top-pair
+ * processes (MF_GG_TT, MF_GG_TTG, MF_GG_TTGG, MF_UU_TT, MF_UG_TTU, a
+ * process may repeat), n_events[i] >= 2 events per iteration.  Channel i
+ * draws its random numbers with Philox channel id cfg.channel + i.  Each of
+ * the n_iter (1..1000) iterations is ONE persistent launch over all
+ * channels: CTAs take (channel, tile) work items from a device counter,
+ * tiles of the schedule's size (mf_set_batch_schedule, mf_autotune_batch;
+ * 4096 events by default), and each channel's sums are reduced in tile
+ * order, so the result does not depend on the CTA schedule.  The iterations (launch, reductions, refinements) are
+ * captured once as a CUDA graph on a private stream and replayed while the
+ * channel list, sizes, sqrt_s and schedule stay the same.
+ * Outputs (host): per_ch_host [n_ch] results as mf_integrate;
+ * total_host: sigma = sum of the channels' sigma, error = their errors in
+ * quadrature, chi2_dof = 0, counts summed; grids_host (nullable)
+ * [n_ch][18][n_bins+1] final grids (rows past the channel's dimension are not
+ * written).  MF_MIXED contexts only (MF_ERR_UNSUPPORTED otherwise).
+ * Orders itself after work already queued on the context's stream and
+ * synchronises before returning. */
+int mf_integrate_batch(struct mf_ctx *ctx, int n_ch, const int *processes, const long long *n_events, double sqrt_s,
+                       int n_iter, struct mf_result *per_ch_host, struct mf_result *total_host, double *grids_host);
+
+/* d sigma_total / d m_t of a batch: one derivative pass per channel (as
+ * mf_vegas_pass_grad, mixed precision) at the final grids left by the last
+ * mf_integrate_batch call, which must have had the same channel list
+ * (MF_ERR_ARG otherwise).  Channel i uses Philox channel cfg.channel + i and
+ * iteration `iteration` (take one not used in training for an independent
+ * estimate), events [0, n_events[i]).  out_host [n_ch + 1][4]: per channel,
+ * then the sum over channels: sigma_hat, d sigma_hat/d m_t, its Monte Carlo
+ * error (the channels' errors in quadrature for the sum), d sigma_hat/d
+ * alpha_s.  Synchronises. */
+int mf_batch_grad(struct mf_ctx *ctx, int n_ch, const int *processes, const long long *n_events, double sqrt_s,
+                  unsigned int iteration, double *out_host);
+
+/* Sets the mf_integrate_batch schedule explicitly (no counterpart in the
+ * paper): sched 0/1 (helicity barrier off/on in the heavy matrix elements),
+ * tile_events in [32, 2^26] events per work item, ctas_per_sm in [0, 16]
+ * (0 = as many as fit; values above what fits are clamped).  MF_ERR_ARG
+ * outside these ranges.  Defaults: 1, 4096, 0. */
+int mf_set_batch_schedule(struct mf_ctx *ctx, int sched, long long tile_events, int ctas_per_sm);
+
+/* Launch-schedule autotuner for mf_integrate_batch (no counterpart in the
+ * paper).  Times one iteration over an eighth of each channel's events for
+ * every combination of helicity-barrier schedule {0, 1}, tile size
+ * {2048, 4096, 16384} events and CTAs per SM {1, 2}, and keeps the fastest
+ * for later mf_integrate_batch calls on this context.  choice_host [3]
+ * (nullable) receives (schedule, tile events, CTAs per SM).  The tile size
+ * changes how the sums are grouped, so results differ from the defaults'
+ * in the last bits.  Arguments as mf_integrate_batch.  Synchronises. */
+int mf_autotune_batch(struct mf_ctx *ctx, int n_ch, const int *processes, const long long *n_events, double sqrt_s,
+                      int *choice_host);
 
 #ifdef __cplusplus
 }

@@ -72,6 +72,12 @@ def lib():
             "mf_evaluate_grad": (C.c_int, [vp, C.c_int, vp, i64, vp, vp]),
             "mf_vegas_pass_static": (C.c_int, [C.c_int, C.POINTER(MfConfig), C.c_double, vp, C.c_int, C.c_int, C.c_int,
                                                C.c_double, C.c_double, C.c_double, vp, i64, i64, C.c_uint, vp, vp]),
+            "mf_integrate_batch": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double, C.c_int,
+                                             C.POINTER(MfResult), C.POINTER(MfResult), dp]),
+            "mf_batch_grad": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double, C.c_uint, dp]),
+            "mf_set_batch_schedule": (C.c_int, [vp, C.c_int, i64, C.c_int]),
+            "mf_autotune_batch": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double,
+                                            C.POINTER(C.c_int)]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -84,4 +90,5 @@ def lib():
 def exported_symbols():
     return ["mf_default_config", "mf_process_info", "mf_create", "mf_destroy", "mf_last_error",
             "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
-            "mf_vegas_pass_static", "mf_set_couplings", "mf_vegas_pass_grad", "mf_evaluate_grad"]
+            "mf_vegas_pass_static", "mf_set_couplings", "mf_vegas_pass_grad", "mf_evaluate_grad",
+            "mf_integrate_batch", "mf_batch_grad", "mf_set_batch_schedule", "mf_autotune_batch"]

@@ -102,6 +102,51 @@ class Context:
         _check(self.ptr, rc)
         return out
 
+    def integrate_batch(self, processes, n_events, sqrt_s: float, n_iter: int, want_grids: bool = False):
+        """Several channels in one persistent launch per iteration (mf_integrate_batch).
+        Returns (total dict, list of per-channel dicts)."""
+        n_ch = len(processes)
+        procs = (C.c_int * n_ch)(*[int(p) for p in processes])
+        ns = (C.c_longlong * n_ch)(*[int(n) for n in n_events])
+        per = (MfResult * n_ch)()
+        tot = MfResult()
+        grids = np.zeros((n_ch, 18, self.cfg.n_bins + 1)) if want_grids else None
+        rc = _lib.lib().mf_integrate_batch(self.ptr, n_ch, procs, ns, sqrt_s, n_iter, per, C.byref(tot),
+                                           grids.ctypes.data_as(C.POINTER(C.c_double)) if grids is not None else None)
+        _check(self.ptr, rc)
+
+        def d(r):
+            return dict(sigma=r.sigma_pb, error=r.error_pb, chi2dof=r.chi2_dof, n_events=r.n_events_total,
+                        n_pass=r.n_pass, n_nan=r.n_nan)
+        chans = [d(per[i]) for i in range(n_ch)]
+        if grids is not None:
+            for i, p in enumerate(processes):
+                chans[i]["grid"] = grids[i, :process_info(p)[1]].copy()
+        return d(tot), chans
+
+    def batch_grad(self, processes, n_events, sqrt_s: float, iteration: int):
+        """Derivative passes at the grids of the last integrate_batch: array [n_ch + 1, 4] of
+        (sigma_hat, d sigma_hat/d m_t, its MC error, d sigma_hat/d alpha_s); last row = sum."""
+        n_ch = len(processes)
+        procs = (C.c_int * n_ch)(*[int(p) for p in processes])
+        ns = (C.c_longlong * n_ch)(*[int(n) for n in n_events])
+        out = np.zeros((n_ch + 1, 4))
+        _check(self.ptr, _lib.lib().mf_batch_grad(self.ptr, n_ch, procs, ns, sqrt_s, iteration,
+                                                  out.ctypes.data_as(C.POINTER(C.c_double))))
+        return out
+
+    def set_batch_schedule(self, sched: int, tile_events: int, ctas_per_sm: int = 0):
+        _check(self.ptr, _lib.lib().mf_set_batch_schedule(self.ptr, sched, tile_events, ctas_per_sm))
+
+    def autotune_batch(self, processes, n_events, sqrt_s: float):
+        """Pick the batch schedule (barrier schedule, tile events, CTAs per SM) by timing."""
+        n_ch = len(processes)
+        procs = (C.c_int * n_ch)(*[int(p) for p in processes])
+        ns = (C.c_longlong * n_ch)(*[int(n) for n in n_events])
+        ch = (C.c_int * 3)()
+        _check(self.ptr, _lib.lib().mf_autotune_batch(self.ptr, n_ch, procs, ns, sqrt_s, ch))
+        return tuple(ch)
+
     def vegas_pass(self, process: int, sqrt_s: float, grid, n_events: int, ev_offset: int = 0,
                    iteration: int = 0, mask_in=None, want_events: bool = False, fields=None):
         """One pass at a device grid; returns (sums tensor, events dict or None)."""

@@ -7,27 +7,11 @@
 #include <string>
 #include <vector>
 
-#include "mf_dispatch.cuh"
-#include "../../include/madflow_gb300.h"
+#include "mf_ctx.h"
 
 using namespace mf;
 
-struct mf_ctx {
-    mf_config cfg;
-    cudaStream_t stream = nullptr;
-    int device = 0, n_sm = 0;
-    int n_flav = 0, nx = 0, nq = 0;
-    double x_min = 0, q2_min = 0, q2_max = 0;
-    double* d_pdf = nullptr;
-    double* d_grid = nullptr;        // [MAX_DIM][MAX_BINS+1]
-    double* d_partials = nullptr;    // [max_blocks][2 + MAX_DIM MAX_BINS]
-    double* d_iter = nullptr;        // [MAX_ITER][2]
-    double* d_sums = nullptr;        // [2 + MAX_DIM MAX_BINS]
-    unsigned long long* d_counters = nullptr;
-    int max_blocks = 0;
-    int sched = 1;                   // integrand schedule (see mf_set_schedule)
-    std::string err;
-};
+
 
 namespace mf {
 // ------------------------------------------------------------------ end of a pass
@@ -111,6 +95,8 @@ const ProcOps* proc_ops(int p)
     case MF_GG_TT: return ops_gg_tt();
     case MF_GG_TTG: return ops_gg_ttg();
     case MF_GG_TTGG: return ops_gg_ttgg();
+    case MF_UU_TT: return ops_uu_tt();
+    case MF_UG_TTU: return ops_ug_ttu();
     default: return nullptr;
     }
 }
@@ -121,6 +107,8 @@ const GradOpsTable* grad_ops(int p)
     case MF_GG_TT: return grad_gg_tt();
     case MF_GG_TTG: return grad_gg_ttg();
     case MF_GG_TTGG: return grad_gg_ttgg();
+    case MF_UU_TT: return grad_uu_tt();
+    case MF_UG_TTU: return grad_ug_ttu();
     default: return nullptr;
     }
 }
@@ -149,6 +137,9 @@ double factorial(int n)
 int make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KParams& kp)
 {
     const mf_config& g = c->cfg;
+    const int need_flav = process == MF_UU_TT ? 3 : (process == MF_UG_TTU ? 2 : 1);
+    if (process != MF_EE_MUMU && c->n_flav < need_flav)
+        return fail(c, MF_ERR_ARG, "the PDF grid lacks a flavour this process needs");
     std::memset(&kp, 0, sizeof(kp));
     kp.sqrt_s = sqrt_s;
     kp.S = sqrt_s * sqrt_s;
@@ -203,6 +194,14 @@ int pick_blocks(mf_ctx* c, const ProcOps* ops, size_t sm, int prec, int* nblk)
 
 }  // namespace
 
+int mf_fail(mf_ctx* c, int code, const std::string& msg) { return fail(c, code, msg); }
+int mf_make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KParams& kp)
+{
+    return make_params(c, process, ops, sqrt_s, kp);
+}
+const ProcOps* mf_proc_ops(int process) { return proc_ops(process); }
+const GradOpsTable* mf_grad_ops(int process) { return grad_ops(process); }
+
 extern "C" {
 
 int mf_default_config(mf_config* cfg)
@@ -228,7 +227,7 @@ int mf_default_config(mf_config* cfg)
 int mf_process_info(int process, int* n_ext, int* dim)
 {
     const ProcOps* o = proc_ops(process);
-    if (!o) return (process == MF_UU_TT || process == MF_UG_TTU) ? MF_ERR_UNSUPPORTED : MF_ERR_ARG;
+    if (!o) return MF_ERR_ARG;
     if (n_ext) *n_ext = o->NEXT;
     if (dim) *dim = o->D;
     return MF_OK;
@@ -264,7 +263,7 @@ int mf_create(mf_ctx** out, const mf_config* cfg, const double* pdf_grid_host, i
         return bail(MF_ERR_CUDA);
     if (cudaMemcpy(c->d_pdf, pdf_grid_host, npdf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(MF_ERR_CUDA);
-    for (int p : { MF_EE_MUMU, MF_GG_TT, MF_GG_TTG, MF_GG_TTGG }) {
+    for (int p : { MF_EE_MUMU, MF_GG_TT, MF_GG_TTG, MF_GG_TTGG, MF_UU_TT, MF_UG_TTU }) {
         const ProcOps* o = proc_ops(p);
         if (o->prepare(std::max(o->smem(0, MAX_BINS, nx * nq), o->smem(1, MAX_BINS, nx * nq))) != cudaSuccess) return bail(MF_ERR_CUDA);
     }
@@ -275,12 +274,23 @@ int mf_create(mf_ctx** out, const mf_config* cfg, const double* pdf_grid_host, i
 void mf_destroy(mf_ctx* c)
 {
     if (!c) return;
+    if (c->cap_stream) cudaStreamSynchronize(c->cap_stream);
     cudaFree(c->d_pdf);
     cudaFree(c->d_grid);
     cudaFree(c->d_partials);
     cudaFree(c->d_iter);
     cudaFree(c->d_sums);
     cudaFree(c->d_counters);
+    cudaFree(c->d_kps);
+    cudaFree(c->d_tiles);
+    cudaFree(c->d_bgrids);
+    cudaFree(c->d_biter);
+    cudaFree(c->d_bsums);
+    cudaFree(c->d_bcount);
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->ev_user) cudaEventDestroy(c->ev_user);
+    if (c->ev_cap) cudaEventDestroy(c->ev_cap);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     delete c;
 }
 
@@ -314,7 +324,7 @@ int mf_vegas_pass(mf_ctx* c, int process, double sqrt_s, const double* grid_dev,
 {
     if (!c) return MF_ERR_ARG;
     const ProcOps* ops = proc_ops(process);
-    if (!ops) return fail(c, MF_ERR_UNSUPPORTED, "process not built");
+    if (!ops) return fail(c, MF_ERR_ARG, "unknown process");
     if (!grid_dev || !sums_dev || n_events < 1 || ev_offset < 0 || !(sqrt_s > 0.0))
         return fail(c, MF_ERR_ARG, "mf_vegas_pass: bad argument");
     KParams kp;
@@ -360,7 +370,7 @@ int mf_integrate(mf_ctx* c, int process, double sqrt_s, long long n_events, int 
 {
     if (!c) return MF_ERR_ARG;
     const ProcOps* ops = proc_ops(process);
-    if (!ops) return fail(c, MF_ERR_UNSUPPORTED, "process not built");
+    if (!ops) return fail(c, MF_ERR_ARG, "unknown process");
     if (!out || n_events < 2 || n_iter < 1 || n_iter > MAX_ITER || !(sqrt_s > 0.0))
         return fail(c, MF_ERR_ARG, "mf_integrate: bad argument");
     KParams kp;
@@ -478,7 +488,7 @@ int mf_evaluate(mf_ctx* c, int process, const double* momenta_dev, long long n, 
 {
     if (!c) return MF_ERR_ARG;
     const ProcOps* ops = proc_ops(process);
-    if (!ops) return fail(c, MF_ERR_UNSUPPORTED, "process not built");
+    if (!ops) return fail(c, MF_ERR_ARG, "unknown process");
     if (n == 0) return MF_OK;
     if (!momenta_dev || !me2_dev || n < 0) return fail(c, MF_ERR_ARG, "mf_evaluate: bad argument");
     KParams kp;

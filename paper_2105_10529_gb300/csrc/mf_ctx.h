@@ -1,0 +1,46 @@
+// Internal state of an mf_ctx and the helpers shared by the C ABI sources.
+#pragma once
+#include <cuda_runtime.h>
+#include <string>
+
+#include "mf_batch.cuh"
+#include "mf_dispatch.cuh"
+#include "../../include/madflow_gb300.h"
+
+struct mf_ctx {
+    mf_config cfg;
+    cudaStream_t stream = nullptr;
+    int device = 0, n_sm = 0;
+    int n_flav = 0, nx = 0, nq = 0;
+    double x_min = 0, q2_min = 0, q2_max = 0;
+    double* d_pdf = nullptr;
+    double* d_grid = nullptr;        // [MAX_DIM][MAX_BINS+1]
+    double* d_partials = nullptr;    // [max_blocks][2 + MAX_DIM MAX_BINS]
+    double* d_iter = nullptr;        // [MAX_ITER][2]
+    double* d_sums = nullptr;        // [2 + MAX_DIM MAX_BINS]
+    unsigned long long* d_counters = nullptr;
+    int max_blocks = 0;
+    int sched = 1;                   // integrand schedule (see mf_set_schedule)
+    std::string err;
+    // batched channels: workspace, tuned schedule and the cached CUDA graph
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture and replay
+    cudaEvent_t ev_user = nullptr, ev_cap = nullptr;
+    mf::KParams* d_kps = nullptr;        // [MAX_CH]
+    double* d_tiles = nullptr;           // tile partial sums of all channels
+    size_t tiles_cap = 0;                // doubles
+    double* d_bgrids = nullptr;          // [MAX_CH][MAX_DIM][MAX_BINS+1]
+    double* d_biter = nullptr;           // [MAX_CH][1000][2]
+    double* d_bsums = nullptr;           // [MAX_CH][2 + MAX_DIM MAX_BINS]
+    unsigned long long* d_bcount = nullptr;   // [MAX_CH][2] counters, then the tile counter
+    int b_sched = 1, b_bps = 0;          // tuned: barrier schedule, CTAs per SM (0 = occupancy)
+    long long b_tile = 4096;             // tuned: events per tile
+    cudaGraphExec_t graph = nullptr;
+    std::string graph_key;
+    int b_last_nch = 0;                  // channel list of the grids in d_bgrids
+    int b_last_proc[mf::MAX_CH] = {};
+};
+
+int mf_fail(mf_ctx* c, int code, const std::string& msg);
+int mf_make_params(mf_ctx* c, int process, const mf::ProcOps* ops, double sqrt_s, mf::KParams& kp);
+const mf::ProcOps* mf_proc_ops(int process);
+const mf::GradOpsTable* mf_grad_ops(int process);

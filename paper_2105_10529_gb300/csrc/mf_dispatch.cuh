@@ -30,6 +30,8 @@ struct GradOpsTable {
 const GradOpsTable* grad_gg_tt();
 const GradOpsTable* grad_gg_ttg();
 const GradOpsTable* grad_gg_ttgg();
+const GradOpsTable* grad_uu_tt();
+const GradOpsTable* grad_ug_ttu();
 
 template <class P, class ME, bool FP64>
 struct GradOps {
@@ -56,6 +58,8 @@ const ProcOps* ops_ee_mumu();
 const ProcOps* ops_gg_tt();
 const ProcOps* ops_gg_ttg();
 const ProcOps* ops_gg_ttgg();
+const ProcOps* ops_uu_tt();
+const ProcOps* ops_ug_ttu();
 
 // integrand launch helpers for a process trait P with TPB threads per CTA
 template <class P, int TPB>

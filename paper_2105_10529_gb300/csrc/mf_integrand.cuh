@@ -88,18 +88,19 @@ struct ProcEe {
     template <typename R> static constexpr size_t slot_bytes() { return 0; }
 };
 
-template <class ME>
+// F1, F2: PDF flavours of the two incoming partons (0 gluon, 1 u, 2 ubar)
+template <class ME, int F1 = 0, int F2 = 0>
 struct ProcTops {
     using Me = ME;
     static constexpr int NEXT = ME::NEXT;
     static constexpr int NF = NEXT - 2;        // t, tbar, light partons
     static constexpr int D = 2 + 4 * NF;
     static constexpr int NLIGHT = NF - 2;
-    static constexpr int NPDF = 1;             // gluon grid only
-    // heavy matrix elements: PDF read through L1 instead of staged, one
-    // CTA-level histogram, and a shared-memory slot per thread for the
-    // matrix element's per-event invariants
-    static constexpr bool HEAVY = NEXT >= 5;
+    static constexpr int NPDF = 1;             // PDFs are read from the global grid (through L1)
+    static constexpr int FLAV1 = F1, FLAV2 = F2;
+    // heavy matrix elements (2 -> 3 and more with a per-thread invariant slot): queue of
+    // the events that pass the cuts, one CTA-level histogram, shared-memory slots
+    static constexpr bool HEAVY = NEXT >= 5 && ME::template slot_bytes<float>() > 0;
     template <typename R> static constexpr size_t slot_bytes() { return HEAVY ? ME::template slot_bytes<R>() : 0; }
 };
 
@@ -223,8 +224,9 @@ __device__ __forceinline__ void kinematics_tops_t(const KParams& kp, const doubl
         }
         muf2 = 0.25 * ht * ht;
     }
-    const S f1 = pdf_xf(spdf, kp.pdfg, x1, muf2) / x1;
-    const S f2 = pdf_xf(spdf, kp.pdfg, x2, muf2) / x2;
+    const int npv = kp.pdfg.nx * kp.pdfg.nq;
+    const S f1 = pdf_xf(spdf + P::FLAV1 * npv, kp.pdfg, x1, muf2) / x1;
+    const S f2 = pdf_xf(spdf + P::FLAV2 * npv, kp.pdfg, x2, muf2) / x2;
     pref = f1 * f2 / (2.0 * shat) * wps * jp * jv * GEV2_TO_PB;
     o.me2 = 0.0;
     o.w = 0.0;
@@ -255,7 +257,7 @@ __device__ __forceinline__ void event_tops(const KParams& kp, const double* sgri
 // ------------------------------------------------------------------ shared-memory layout
 
 // Byte offsets of the kernel's dynamic shared memory:
-//   grid [D][nb+1] | PDF [nx nq] (light processes) | histograms | value buffer |
+//   grid [D][nb+1] | histograms | value buffer |
 //   bins buffer (heavy) | event queue and counts (heavy) | block-sum scratch |
 //   per-thread slots (heavy)
 // Light processes keep one histogram per warp (updated by bin leaders);
@@ -269,10 +271,7 @@ struct SmemLayout {
     static __host__ __device__ size_t al(size_t x) { return (x + 15) & ~(size_t)15; }
     static __host__ __device__ size_t grid_off() { return 0; }
     static __host__ __device__ size_t pdf_off(int nb) { return al(grid_off() + sizeof(double) * D * (nb + 1)); }
-    static __host__ __device__ size_t hist_off(int nb, int npv)
-    {
-        return al(pdf_off(nb) + (P::HEAVY ? 0 : sizeof(double) * (size_t)P::NPDF * npv));
-    }
+    static __host__ __device__ size_t hist_off(int nb, int npv) { return al(pdf_off(nb)); }
     static __host__ __device__ size_t vbuf_off(int nb, int npv) { return al(hist_off(nb, npv) + sizeof(double) * NHIST * D * nb); }
     static __host__ __device__ size_t bbuf_off(int nb, int npv) { return al(vbuf_off(nb, npv) + sizeof(double) * TPB); }
     static __host__ __device__ size_t queue_off(int nb, int npv) { return al(bbuf_off(nb, npv) + (P::HEAVY ? (size_t)TPB * D : 0)); }
@@ -288,7 +287,7 @@ struct SmemLayout {
 // CTA histogram(s) summed in warp order, written to this CTA's partials
 template <class P, int TPB, int NHIST>
 __device__ __forceinline__ void write_partials(const KParams& kp, double sw, double sw2, unsigned long long npass,
-                                               unsigned long long nnan, double* sred, const double* shist)
+                                               unsigned long long nnan, double* sred, const double* shist, double* out)
 {
     constexpr int D = P::D, WARPS = TPB / 32;
     const int nb = kp.nb, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -309,7 +308,6 @@ __device__ __forceinline__ void write_partials(const KParams& kp, double sw, dou
         atomicAdd(kp.counters + 1, nnan);
     }
     __syncthreads();
-    double* out = kp.partials + (size_t)blockIdx.x * (2 + D * nb);
     if (tid == 0) {
         double a = 0.0, b = 0.0;
         for (int w = 0; w < WARPS; ++w) { a += sred[2 * w]; b += sred[2 * w + 1]; }
@@ -347,34 +345,33 @@ __device__ __forceinline__ void write_momenta(const KParams& kp, long long e, co
 
 // Light processes (cheap matrix elements): one event per thread per round,
 // per-warp histograms updated by bin leaders.
+// Events first + r * step + tid (r = 0, 1, ...) below end; the CTA's sums go to out.
 template <class P, typename R, int TPB, bool WRITE>
-__device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char* smem_raw)
+__device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char* smem_raw, long long first,
+                                                long long step, long long end, double* out)
 {
     constexpr int D = P::D;
     using L = SmemLayout<P, R, TPB>;
     const int nb = kp.nb;
     const int npv = kp.pdfg.nx * kp.pdfg.nq;
     double* sgrid = reinterpret_cast<double*>(smem_raw + L::grid_off());
-    double* spdf = reinterpret_cast<double*>(smem_raw + L::pdf_off(nb));
+    const double* spdf = kp.pdf;
     double* shist = reinterpret_cast<double*>(smem_raw + L::hist_off(nb, npv));
     double* svbuf = reinterpret_cast<double*>(smem_raw + L::vbuf_off(nb, npv));
     double* sred = reinterpret_cast<double*>(smem_raw + L::red_off(nb, npv));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
     for (int i = tid; i < D * (nb + 1); i += TPB) sgrid[i] = kp.grid[i];
-    for (int i = tid; i < P::NPDF * npv; i += TPB) spdf[i] = kp.pdf[i];
     for (int i = tid; i < L::NHIST * D * nb; i += TPB) shist[i] = 0.0;
     __syncthreads();
 
     double* myhist = shist + warp * D * nb;
     double sw = 0.0, sw2 = 0.0;
     unsigned long long npass = 0, nnan = 0;
-    const long long n = kp.n_events;
-    const long long total = (long long)gridDim.x * TPB;
-    const long long rounds = (n + total - 1) / total;
+    const long long rounds = end > first ? (end - first + step - 1) / step : 0;
     for (long long r = 0; r < rounds; ++r) {
-        const long long e = r * total + (long long)blockIdx.x * TPB + tid;
-        const bool valid = e < n;
+        const long long e = first + r * step + tid;
+        const bool valid = e < end;
         EventOut<D> o;
         double pm[P::NEXT][4];
         o.w = 0.0; o.me2 = 0.0; o.mask = 0;
@@ -406,7 +403,7 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
         }
         __syncwarp();
     }
-    write_partials<P, TPB, L::NHIST>(kp, sw, sw2, npass, nnan, sred, shist);
+    write_partials<P, TPB, L::NHIST>(kp, sw, sw2, npass, nnan, sred, shist, out);
 }
 
 // Heavy processes (expensive matrix elements): kinematics first, then the
@@ -418,7 +415,8 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
 // barrier between helicities (SYNC) that keeps the warps on the same code.
 // The histogram is filled by one thread per dimension in queue order.
 template <class P, typename R, int TPB, bool WRITE, bool SYNC>
-__device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char* smem_raw)
+__device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char* smem_raw, long long first,
+                                                long long step, long long end, double* out)
 {
     constexpr int D = P::D, WARPS = TPB / 32;
     using L = SmemLayout<P, R, TPB>;
@@ -442,16 +440,14 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
 
     double sw = 0.0, sw2 = 0.0;
     unsigned long long npass = 0, nnan = 0;
-    const long long n = kp.n_events;
-    const long long total = (long long)gridDim.x * TPB;
-    const long long rounds = (n + total - 1) / total;
+    const long long rounds = end > first ? (end - first + step - 1) / step : 0;
     for (long long r = 0; r <= rounds; ++r) {
         const bool flush = (r == rounds);
         if (!flush) {
             // kinematics of this round's events; queue the ones that pass, in event order
-            const long long e = r * total + (long long)blockIdx.x * TPB + tid;
+            const long long e = first + r * step + tid;
             int pass = 0;
-            if (e < n) {
+            if (e < end) {
                 EventOut<D> o;
                 double pm[P::NEXT][4], pref;
                 kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
@@ -515,7 +511,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             __syncthreads();
         }
     }
-    write_partials<P, TPB, 1>(kp, sw, sw2, npass, nnan, sred, shist);
+    write_partials<P, TPB, 1>(kp, sw, sw2, npass, nnan, sred, shist, out);
 }
 
 // ------------------------------------------------------------------ the fused integrand kernel
@@ -524,8 +520,10 @@ template <class P, typename R, int TPB, bool WRITE, bool SYNC>
 __global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    if constexpr (P::HEAVY) integrand_heavy<P, R, TPB, WRITE, SYNC>(kp, smem_raw);
-    else integrand_light<P, R, TPB, WRITE>(kp, smem_raw);
+    const long long first = (long long)blockIdx.x * TPB, step = (long long)gridDim.x * TPB;
+    double* out = kp.partials + (size_t)blockIdx.x * (2 + P::D * kp.nb);
+    if constexpr (P::HEAVY) integrand_heavy<P, R, TPB, WRITE, SYNC>(kp, smem_raw, first, step, kp.n_events, out);
+    else integrand_light<P, R, TPB, WRITE>(kp, smem_raw, first, step, kp.n_events, out);
 }
 
 // ------------------------------------------------------------------ evaluate

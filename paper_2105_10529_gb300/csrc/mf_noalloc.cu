@@ -45,6 +45,8 @@ const ProcOps* ops_for(int p)
     case MF_GG_TT: return ops_gg_tt();
     case MF_GG_TTG: return ops_gg_ttg();
     case MF_GG_TTGG: return ops_gg_ttgg();
+    case MF_UU_TT: return ops_uu_tt();
+    case MF_UG_TTU: return ops_ug_ttu();
     default: return nullptr;
     }
 }
@@ -81,12 +83,14 @@ extern "C" int mf_vegas_pass_static(int process, const mf_config* cfg, double sq
                                     void* stream)
 {
     const ProcOps* ops = ops_for(process);
-    if (!ops) return (process == MF_UU_TT || process == MF_UG_TTU) ? MF_ERR_UNSUPPORTED : MF_ERR_ARG;
+    if (!ops) return MF_ERR_ARG;
     if (!cfg || !pdf_dev || !grid_dev || !sums_dev || n_events < 1 || ev_offset < 0 || !(sqrt_s > 0.0)) return MF_ERR_ARG;
     if (n_flav < 1 || n_flav > 3 || nx < 4 || nq < 4 || nx * nq > 8192) return MF_ERR_ARG;
     if (!(x_min > 0.0 && x_min < 1.0 && q2_min > 0.0 && q2_max > q2_min)) return MF_ERR_ARG;
     if (cfg->n_bins < 2 || cfg->n_bins > MAX_BINS || cfg->channel >= (1u << 24)) return MF_ERR_ARG;
     if (cfg->precision != MF_FP64 && cfg->precision != MF_MIXED) return MF_ERR_ARG;
+    const int need_flav = process == MF_UU_TT ? 3 : (process == MF_UG_TTU ? 2 : 1);
+    if (process != MF_EE_MUMU && n_flav < need_flav) return MF_ERR_ARG;
     const int D = ops->D, nb = cfg->n_bins;
     const size_t ncol = 2 + (size_t)D * nb;
     // the scratch must hold at least one CTA's partials beyond the counters

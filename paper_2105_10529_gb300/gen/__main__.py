@@ -5,7 +5,7 @@
 import os
 from fractions import Fraction
 
-from . import qcd_diagrams
+from . import qcd_diagrams, qq_processes
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(os.path.dirname(HERE), "csrc", "generated")
@@ -20,9 +20,13 @@ PROCESSES = [
 def write_all(out_dir: str = OUT) -> list:
     os.makedirs(out_dir, exist_ok=True)
     written = []
-    for k, name, sym in PROCESSES:
-        src, _ = qcd_diagrams.generate_gluon_process(k, name, sym)
-        path = os.path.join(out_dir, f"me_{name}.cuh")
+    items = [(f"me_{name}.cuh", lambda k=k, name=name, sym=sym: qcd_diagrams.generate_gluon_process(k, name, sym)[0])
+             for k, name, sym in PROCESSES]
+    items += [("me_uu_tt.cuh", lambda: qq_processes.generate_uu_tt()[0]),
+              ("me_ug_ttu.cuh", lambda: qq_processes.generate_ug_ttu()[0])]
+    for fname, make in items:
+        src = make()
+        path = os.path.join(out_dir, fname)
         old = open(path).read() if os.path.exists(path) else None
         if old != src:
             with open(path, "w") as f:

@@ -13,6 +13,8 @@ PHYS = {
     IN.GG_TT: IN.Physics(seed=1),
     IN.GG_TTG: IN.Physics(seed=2),
     IN.GG_TTGG: IN.Physics(seed=3),
+    IN.UU_TT: IN.Physics(seed=4, channel=1),
+    IN.UG_TTU: IN.Physics(seed=5, channel=3),
 }
 
 
@@ -67,6 +69,23 @@ def cut_margin(proc, phys, plab):
         dphi = (dphi + math.pi) % (2 * math.pi) - math.pi
         m = min(m, abs(((ea - eb) ** 2 + dphi ** 2) / phys.dr_min ** 2 - 1.0))
     return m
+
+
+def rambo_gamma(x, n_final):
+    """Boost factor Q0/M of RAMBO's conformal map for each event, from the
+    VEGAS-mapped points x [n, D] (dimensions 2.. hold 4 uniforms per final
+    particle: cos theta = 2u1 - 1, phi = 2 pi u2, E = -ln(u3 u4))."""
+    x = np.asarray(x, float)
+    Q = np.zeros((x.shape[0], 4))
+    for i in range(n_final):
+        u = x[:, 2 + 4 * i: 6 + 4 * i]
+        c = 2.0 * u[:, 0] - 1.0
+        s = np.sqrt(1.0 - c * c)
+        f = 2.0 * np.pi * u[:, 1]
+        e = -np.log(u[:, 2] * u[:, 3])
+        Q += np.stack([e, e * s * np.cos(f), e * s * np.sin(f), e * c], axis=1)
+    M = np.sqrt(Q[:, 0] ** 2 - Q[:, 1] ** 2 - Q[:, 2] ** 2 - Q[:, 3] ** 2)
+    return Q[:, 0] / M
 
 
 def rel_err(a, b):

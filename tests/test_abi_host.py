@@ -38,8 +38,10 @@ def test_default_config_and_process_info_without_gpu():
     assert cfg.mt == 173.0 and cfg.n_bins == 50 and cfg.precision == _lib.MF_MIXED
     assert process_info(_lib.MF_GG_TTGG) == (6, 18)
     assert process_info(_lib.MF_EE_MUMU) == (4, 2)
+    assert process_info(_lib.MF_UU_TT) == (4, 10)
+    assert process_info(_lib.MF_UG_TTU) == (5, 14)
     with pytest.raises(_lib.MfError):
-        process_info(_lib.MF_UU_TT)
+        process_info(17)
 
 
 def test_oracle_and_cuda_path_share_no_code():

@@ -1,0 +1,176 @@
+"""Batched channels (mf_integrate_batch): several partonic subprocesses in
+one persistent launch per VEGAS iteration, each on its own grid and Philox
+channel id.  Checked against the FP64 oracle channel by channel, against the
+single-process path, and for independence of the CTA schedule."""
+import dataclasses
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2105_10529_gb300 import inputs as IN
+from paper_2105_10529_gb300._lib import MfError
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+PHYS = IN.Physics(seed=7, channel=2)
+CHANNELS = [IN.GG_TT, IN.UU_TT, IN.UG_TTU, IN.GG_TTG, IN.GG_TTGG]
+# uneven sizes, none a multiple of the tile
+N_EV = [20011, 8003, 4001, 2503, 509]
+TILE = 1000
+
+
+@pytest.fixture(scope="module")
+def pdf_grid():
+    return IN.make_pdf_grid()
+
+
+@pytest.fixture(scope="module")
+def opdf(pdf_grid):
+    return O.Pdf(pdf_grid)
+
+
+@pytest.fixture(scope="module")
+def ctx(pdf_grid):
+    from paper_2105_10529_gb300.api import Context
+    c = Context(PHYS, pdf_grid, precision=1)
+    yield c
+    c.close()
+
+
+def test_batch_one_iteration_matches_oracle(ctx, opdf):
+    """One iteration at the uniform grid: channel i is the oracle pass of that
+    process with channel id PHYS.channel + i (mixed precision: 1e-5)."""
+    ctx.set_batch_schedule(1, TILE, 0)
+    tot, chans = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 1)
+    s_sum, v_sum = 0.0, 0.0
+    for i, (p, n) in enumerate(zip(CHANNELS, N_EV)):
+        ph = dataclasses.replace(PHYS, channel=PHYS.channel + i)
+        ref = O.vegas_pass(p, ph, opdf, O.vegas_init(IN.DIM[p], PHYS.n_bins), n)
+        var = (n * ref["sum_w2"] - ref["sum_w"] ** 2) / (n - 1)
+        c = chans[i]
+        assert abs(c["sigma"] - ref["sum_w"]) <= 1e-5 * abs(ref["sum_w"]), (p, c["sigma"], ref["sum_w"])
+        assert abs(c["error"] - np.sqrt(var)) <= 1e-5 * np.sqrt(var), (p, c["error"], np.sqrt(var))
+        # events near a cut threshold may flip; none expected at these sizes
+        assert abs(c["n_pass"] - ref["n_pass"]) <= 1, (p, c["n_pass"], ref["n_pass"])
+        assert c["n_events"] == n and c["n_nan"] == 0
+        s_sum += c["sigma"]; v_sum += c["error"] ** 2
+    assert tot["sigma"] == pytest.approx(s_sum, rel=1e-15)
+    assert tot["error"] == pytest.approx(np.sqrt(v_sum), rel=1e-15)
+    assert tot["n_events"] == sum(N_EV)
+
+
+def test_batch_iterations_match_single_process(ctx, pdf_grid):
+    """Three iterations with refinement: each channel equals mf_integrate of
+    that process alone (same channel id); only the grouping of the sums
+    differs (tiles against CTAs)."""
+    from paper_2105_10529_gb300.api import Context
+    ctx.set_batch_schedule(1, TILE, 0)
+    tot, chans = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 3, want_grids=True)
+    for i, (p, n) in enumerate(zip(CHANNELS, N_EV)):
+        single = Context(dataclasses.replace(PHYS, channel=PHYS.channel + i), pdf_grid, precision=1)
+        r = single.integrate(p, PHYS.sqrt_s, n, 3, want_grid=True)
+        single.close()
+        assert chans[i]["sigma"] == pytest.approx(r["sigma"], rel=1e-9), p
+        assert chans[i]["error"] == pytest.approx(r["error"], rel=1e-7), p
+        assert chans[i]["n_pass"] == r["n_pass"], p
+        assert np.abs(chans[i]["grid"] - r["grid"]).max() < 1e-9, p
+
+
+def test_batch_light_channels_match_oracle_integrate(ctx, opdf):
+    """Iterated VEGAS of the light channels against the oracle's integrate."""
+    procs, ns = [IN.GG_TT, IN.UU_TT], [30001, 12001]
+    ctx.set_batch_schedule(0, 2048, 0)
+    tot, chans = ctx.integrate_batch(procs, ns, PHYS.sqrt_s, 3)
+    for i, (p, n) in enumerate(zip(procs, ns)):
+        ref = O.integrate(p, dataclasses.replace(PHYS, channel=PHYS.channel + i), opdf, n, 3)
+        assert chans[i]["sigma"] == pytest.approx(ref["sigma"], rel=1e-5), p
+        assert chans[i]["error"] == pytest.approx(ref["error"], rel=1e-4), p
+
+
+def test_batch_schedule_independent(ctx):
+    """At a fixed tile size the result is bit-identical for every barrier
+    schedule and CTA count, and on repeated (graph-replayed) calls."""
+    ref = None
+    for sched, bps in [(1, 0), (0, 0), (1, 1), (0, 2), (1, 0)]:
+        ctx.set_batch_schedule(sched, TILE, bps)
+        tot, chans = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 2, want_grids=True)
+        key = [(c["sigma"], c["error"], c["n_pass"]) for c in chans]
+        grids = [c["grid"] for c in chans]
+        if ref is None:
+            ref = (key, grids)
+        else:
+            assert key == ref[0], (sched, bps)
+            for a, b in zip(grids, ref[1]):
+                assert np.array_equal(a, b)
+
+
+def test_batch_graph_cache_invalidation(ctx):
+    """A different channel list in between re-captures; the original list
+    then gives the same numbers again."""
+    ctx.set_batch_schedule(1, TILE, 0)
+    a, ca = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 2)
+    b, cb = ctx.integrate_batch([IN.GG_TT], [5003], PHYS.sqrt_s, 2)
+    assert cb[0]["n_events"] == 2 * 5003
+    a2, ca2 = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 2)
+    assert [c["sigma"] for c in ca] == [c["sigma"] for c in ca2]
+    # the same process twice: different channel ids, different streams
+    d, cd = ctx.integrate_batch([IN.GG_TT, IN.GG_TT], [5003, 5003], PHYS.sqrt_s, 1)
+    assert cd[0]["sigma"] != cd[1]["sigma"]
+    assert cd[0]["sigma"] == pytest.approx(cd[1]["sigma"], rel=0.1)
+
+
+def test_batch_autotune(ctx):
+    choice = ctx.autotune_batch(CHANNELS, [40000, 10000, 10000, 8000, 4000], PHYS.sqrt_s)
+    assert choice[0] in (0, 1) and choice[1] in (2048, 4096, 16384) and choice[2] in (1, 2)
+    tot, chans = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 1)
+    ctx.set_batch_schedule(*choice)
+    tot2, chans2 = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 1)
+    assert [c["sigma"] for c in chans] == [c["sigma"] for c in chans2]
+
+
+def test_batch_bad_arguments(ctx, pdf_grid):
+    from paper_2105_10529_gb300.api import Context
+    for procs, ns in [([], []), ([IN.GG_TT] * 9, [100] * 9), ([IN.EE_MUMU], [100]), ([IN.GG_TT], [1]),
+                      ([17], [100])]:
+        with pytest.raises(MfError) as e:
+            ctx.integrate_batch(procs, ns, PHYS.sqrt_s, 1)
+        assert e.value.code == 1, procs
+    with pytest.raises(MfError) as e:
+        ctx.integrate_batch([IN.GG_TT], [100], PHYS.sqrt_s, 0)
+    assert e.value.code == 1
+    for bad in [(2, 4096, 0), (1, 16, 0), (1, 4096, -1)]:
+        with pytest.raises(MfError):
+            ctx.set_batch_schedule(*bad)
+    f64 = Context(PHYS, pdf_grid, precision=0)
+    with pytest.raises(MfError) as e:
+        f64.integrate_batch([IN.GG_TT], [100], PHYS.sqrt_s, 1)
+    assert e.value.code == 5
+    f64.close()
+
+
+def test_batch_grad_matches_single_process(ctx, pdf_grid):
+    """d sigma_total/d m_t: per channel equal to mf_vegas_pass_grad of that
+    process at the batch's final grid (same kernel, same channel id), and the
+    total is the sum over channels."""
+    from paper_2105_10529_gb300.api import Context
+    ctx.set_batch_schedule(1, TILE, 0)
+    tot, chans = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 2, want_grids=True)
+    it = 7
+    g = ctx.batch_grad(CHANNELS, N_EV, PHYS.sqrt_s, it)
+    for i, (p, n) in enumerate(zip(CHANNELS, N_EV)):
+        single = Context(dataclasses.replace(PHYS, channel=PHYS.channel + i), pdf_grid, precision=1)
+        o = single.vegas_pass_grad(p, PHYS.sqrt_s, torch.tensor(chans[i]["grid"], device="cuda"), n,
+                                   iteration=it).cpu().numpy()
+        single.close()
+        assert g[i, 0] == o[0] and g[i, 1] == o[1] and g[i, 3] == o[3], p
+        var = (n * o[2] - o[1] ** 2) / (n - 1)
+        assert g[i, 2] == pytest.approx(np.sqrt(var), rel=1e-12)
+        # the top mass derivative of a top-pair rate is negative
+        assert g[i, 1] < 0.0, p
+    assert g[-1, 0] == pytest.approx(g[:-1, 0].sum(), rel=1e-14)
+    assert g[-1, 1] == pytest.approx(g[:-1, 1].sum(), rel=1e-14)
+    assert g[-1, 2] == pytest.approx(np.sqrt((g[:-1, 2] ** 2).sum()), rel=1e-14)
+    with pytest.raises(MfError):
+        ctx.batch_grad([IN.GG_TT], [100], PHYS.sqrt_s, it)

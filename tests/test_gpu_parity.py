@@ -9,13 +9,13 @@ import pytest
 
 import oracle as O
 from paper_2105_10529_gb300 import inputs as IN
-from tests.gpu_common import PHYS, assert_fp_parity, cut_margin, oracle_events, random_grid, rel_err
+from tests.gpu_common import PHYS, assert_fp_parity, cut_margin, oracle_events, rambo_gamma, random_grid, rel_err
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-PROCS = [IN.EE_MUMU, IN.GG_TT, IN.GG_TTG, IN.GG_TTGG]
-N_SMALL = {IN.EE_MUMU: 4099, IN.GG_TT: 3001, IN.GG_TTG: 1501, IN.GG_TTGG: 301}
+PROCS = [IN.EE_MUMU, IN.GG_TT, IN.GG_TTG, IN.GG_TTGG, IN.UU_TT, IN.UG_TTU]
+N_SMALL = {IN.EE_MUMU: 4099, IN.GG_TT: 3001, IN.GG_TTG: 1501, IN.GG_TTGG: 301, IN.UU_TT: 3001, IN.UG_TTU: 1201}
 TOL = {0: 1e-12, 1: 1e-5}
 
 
@@ -62,10 +62,19 @@ def test_event_parity(proc, prec, pdf_grid, opdf):
     assert_fp_parity(rel_err(w[same], ref["w"][same]), prec, "w")
     me = ev["me2"].cpu().numpy()
     assert_fp_parity(rel_err(me[same], ref["me2"][same]), prec, "me2")
-    # momenta in the partonic frame
+    # momenta in the partonic frame, per event relative to the event's largest
+    # component.  RAMBO's conformal map scales the massless momenta by
+    # sqrt(shat)/M and boosts them with gamma = Q0/M (Q the sum of the isotropic
+    # momenta, M its mass), so a relative rounding difference eps of the inputs
+    # (libm against CUDA log / sincospi) reaches the outputs as about
+    # gamma^2 eps; the bound is 1e-12 or 8 gamma^2 eps, whichever is larger.
     pm = ev["momenta"].cpu().numpy()
-    scale = np.abs(ref["p"]).max()
-    assert np.abs(pm - ref["p"]).max() < 1e-12 * scale
+    scale = np.abs(ref["p"]).reshape(n, -1).max(axis=1)
+    dev = np.abs(pm - ref["p"]).reshape(n, -1).max(axis=1) / scale
+    gam = np.ones(n) if proc == IN.EE_MUMU else rambo_gamma(ref["x"], IN.N_EXT[proc] - 2)
+    bound = np.maximum(1e-12, 8.0 * gam ** 2 * np.finfo(float).eps)
+    assert np.all(dev <= bound), (int(np.argmax(dev / bound)), float(np.max(dev / bound)))
+    assert np.mean(dev > 1e-12) <= 5e-3 or int(np.sum(dev > 1e-12)) <= 1
     # pass sums (w includes 1/n)
     s = sums.cpu().numpy()
     sw = ref["w"].sum() / n
@@ -166,9 +175,12 @@ def test_bad_arguments(pdf_grid):
         ctx.integrate(IN.GG_TT, 13000.0, 1, 2)           # n_events < 2
     with pytest.raises(MfError):
         ctx.integrate(IN.GG_TT, 100.0, 1000, 2)          # below threshold
+    from paper_2105_10529_gb300.api import Context
+    one_flavour = Context(PHYS[IN.GG_TT], IN.make_pdf_grid()[:1], precision=0)
     with pytest.raises(MfError) as e:
-        ctx.integrate(IN.UU_TT, 13000.0, 1000, 2)        # not built
-    assert e.value.code == 5
+        one_flavour.integrate(IN.UU_TT, 13000.0, 1000, 2)   # the grid has no u / ubar
+    assert e.value.code == 1
+    one_flavour.close()
     with pytest.raises(MfError):
         ctx.vegas_pass(IN.GG_TT, 13000.0, g, 0)
     with pytest.raises(MfError):
