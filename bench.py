@@ -130,20 +130,32 @@ def run_batch(ctx, phys, IN, n_iter):
     ns = [int(n) for _, n in IN.BATCH_CHANNELS]
     names = {IN.GG_TT: "gg_tt", IN.UU_TT: "uu_tt", IN.GG_TTG: "gg_ttg", IN.UG_TTU: "ug_ttu", IN.GG_TTGG: "gg_ttgg"}
     choice = ctx.autotune_batch(procs, ns, phys.sqrt_s)
-    ctx.integrate_batch(procs, ns, phys.sqrt_s, n_iter)
-    t0 = time.perf_counter()
-    tot, chans = ctx.integrate_batch(procs, ns, phys.sqrt_s, n_iter)
-    t_batch = time.perf_counter() - t0
+    per_mode = {}
+    for mode in (0, 1):
+        ctx.set_batch_schedule(mode, *choice[1:])
+        ctx.integrate_batch(procs, ns, phys.sqrt_s, n_iter)          # graph capture
+        t0 = time.perf_counter()
+        r = ctx.integrate_batch(procs, ns, phys.sqrt_s, n_iter)
+        per_mode[mode] = (time.perf_counter() - t0, r)
+    t_batch, (tot, chans) = per_mode[choice[0]]
+    ctx.set_batch_schedule(*choice)
+    ctx.integrate_batch(procs, ns, phys.sqrt_s, n_iter)               # grids of the chosen schedule
     g = ctx.batch_grad(procs, ns, phys.sqrt_s, 1000)
-    t0 = time.perf_counter()
-    seq = [ctx.integrate(p, phys.sqrt_s, n, n_iter) for p, n in zip(procs, ns)]
-    t_seq = time.perf_counter() - t0
+    seq, t_ch = [], []
+    for p, n in zip(procs, ns):
+        t0 = time.perf_counter()
+        seq.append(ctx.integrate(p, phys.sqrt_s, n, n_iter))
+        t_ch.append(time.perf_counter() - t0)
+    t_seq = sum(t_ch)
     ev = sum(ns) * n_iter
     return {"workload": "p p -> t tbar + jets: " + ", ".join(f"{names[p]} {n:.0e}" for p, n in zip(procs, ns))
                         + f" events per iteration, {n_iter} iterations, mixed precision",
             "events_per_s": ev / t_batch, "s_per_call": t_batch,
             "sequential_events_per_s": ev / t_seq, "speedup_vs_sequential": t_seq / t_batch,
-            "schedule": {"helicity_barrier": choice[0], "tile_events": choice[1], "ctas_per_sm": choice[2]},
+            "sequential_s_by_channel": {names[p]: t for p, t in zip(procs, t_ch)},
+            "schedule": {"mode": ["one launch", "split"][choice[0]], "helicity_barrier": choice[1],
+                         "tile_heavy": choice[2], "tile_light": choice[3], "ctas_per_sm": choice[4]},
+            "events_per_s_by_mode": {"one launch": ev / per_mode[0][0], "split": ev / per_mode[1][0]},
             "sigma_pb": tot["sigma"], "error_pb": tot["error"],
             "channels": {names[p]: {"sigma_pb": c["sigma"], "error_pb": c["error"], "chi2dof": c["chi2dof"],
                                     "sequential_sigma_pb": q["sigma"]} for p, c, q in zip(procs, chans, seq)},

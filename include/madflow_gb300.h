@@ -214,18 +214,24 @@ int mf_evaluate(struct mf_ctx *ctx, int process, const double *momenta_dev, long
 /* Batched channels: several partonic subprocesses of one hadronic process
  * (p p -> t tbar + jets), each integrated on its own VEGAS grid, the sum
  * being the hadronic cross section.  The paper integrates one process at a
- * time (Sec. 2.1, the integrate(process, ...) call); batching them into one
- * launch has no counterpart there.  n_ch (1..8) channels, processes[i] one of the top-pair
- * processes (MF_GG_TT, MF_GG_TTG, MF_GG_TTGG, MF_UU_TT, MF_UG_TTU, a
- * process may repeat), n_events[i] >= 2 events per iteration.  Channel i
- * draws its random numbers with Philox channel id cfg.channel + i.  Each of
- * the n_iter (1..1000) iterations is ONE persistent launch over all
- * channels: CTAs take (channel, tile) work items from a device counter,
- * tiles of the schedule's size (mf_set_batch_schedule, mf_autotune_batch;
- * 4096 events by default), and each channel's sums are reduced in tile
- * order, so the result does not depend on the CTA schedule.  The iterations (launch, reductions, refinements) are
- * captured once as a CUDA graph on a private stream and replayed while the
- * channel list, sizes, sqrt_s and schedule stay the same.
+ * time (Sec. 2.1, the integrate(process, ...) call); batching them has no
+ * counterpart there.  n_ch (1..8) channels, processes[i] one of the top-pair
+ * processes (MF_GG_TT, MF_GG_TTG, MF_GG_TTGG, MF_UU_TT, MF_UG_TTU; a process
+ * may repeat), n_events[i] >= 2 events per iteration.  Channel i draws its
+ * random numbers with Philox channel id cfg.channel + i.
+ * Every iteration hands out (channel, tile) work items, most expensive
+ * channel first, to persistent CTAs through a device counter; each tile
+ * writes its own row of partial sums and a channel's rows are reduced in
+ * tile order, so the result does not depend on which CTA ran which tile.
+ * Schedule (mf_set_batch_schedule, mf_autotune_batch): 0 = one persistent
+ * launch for all channels; 1 = the g g -> t tbar g and t tbar g g channels
+ * in the persistent launch on a high-priority stream and the cheaper
+ * channels as their own integrand kernels on a forked low-priority stream,
+ * which fill the SMs as the expensive work runs out.  All iterations
+ * (launches, reductions, refinements) are captured once as a CUDA graph on a
+ * private stream and replayed while the channel list, sizes, sqrt_s, n_iter,
+ * couplings and schedule stay the same.  The schedule changes how sums are
+ * grouped (results agree to rounding), the CTA count and timing do not.
  * Outputs (host): per_ch_host [n_ch] results as mf_integrate;
  * total_host: sigma = sum of the channels' sigma, error = their errors in
  * quadrature, chi2_dof = 0, counts summed; grids_host (nullable)
@@ -249,20 +255,23 @@ int mf_batch_grad(struct mf_ctx *ctx, int n_ch, const int *processes, const long
                   unsigned int iteration, double *out_host);
 
 /* Sets the mf_integrate_batch schedule explicitly (no counterpart in the
- * paper): sched 0/1 (helicity barrier off/on in the heavy matrix elements),
- * tile_events in [32, 2^26] events per work item, ctas_per_sm in [0, 16]
- * (0 = as many as fit; values above what fits are clamped).  MF_ERR_ARG
- * outside these ranges.  Defaults: 1, 4096, 0. */
-int mf_set_batch_schedule(struct mf_ctx *ctx, int sched, long long tile_events, int ctas_per_sm);
+ * paper): mode 0/1 (one launch / split, see mf_integrate_batch), sched 0/1
+ * (helicity barrier off/on in the g g -> t tbar g(g) matrix elements),
+ * tile_heavy and tile_light in [32, 2^26] events per work item for the
+ * g g -> t tbar g(g) channels and for the others (in the split mode, the
+ * other channels' kernels get one CTA per tile_light events), ctas_per_sm in
+ * [0, 16] (0 = as many as fit; values above that are clamped).  MF_ERR_ARG
+ * outside these ranges.  Defaults: 0, 1, 4096, 4096, 0. */
+int mf_set_batch_schedule(struct mf_ctx *ctx, int mode, int sched, long long tile_heavy, long long tile_light,
+                          int ctas_per_sm);
 
 /* Launch-schedule autotuner for mf_integrate_batch (no counterpart in the
- * paper).  Times one iteration over an eighth of each channel's events for
- * every combination of helicity-barrier schedule {0, 1}, tile size
- * {2048, 4096, 16384} events and CTAs per SM {1, 2}, and keeps the fastest
- * for later mf_integrate_batch calls on this context.  choice_host [3]
- * (nullable) receives (schedule, tile events, CTAs per SM).  The tile size
- * changes how the sums are grouped, so results differ from the defaults'
- * in the last bits.  Arguments as mf_integrate_batch.  Synchronises. */
+ * paper).  Times one iteration of the given channels and sizes at uniform
+ * grids for every mode {0, 1} x helicity barrier {0, 1} x tile_heavy
+ * {1024, 2048, 4096} x tile_light {2048, 4096} (CTAs per SM as fit) and
+ * keeps the fastest for later mf_integrate_batch calls on this context.
+ * choice_host [5] (nullable) receives (mode, sched, tile_heavy, tile_light,
+ * ctas_per_sm).  Arguments as mf_integrate_batch.  Synchronises. */
 int mf_autotune_batch(struct mf_ctx *ctx, int n_ch, const int *processes, const long long *n_events, double sqrt_s,
                       int *choice_host);
 

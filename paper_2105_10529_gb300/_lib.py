@@ -75,7 +75,7 @@ def lib():
             "mf_integrate_batch": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double, C.c_int,
                                              C.POINTER(MfResult), C.POINTER(MfResult), dp]),
             "mf_batch_grad": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double, C.c_uint, dp]),
-            "mf_set_batch_schedule": (C.c_int, [vp, C.c_int, i64, C.c_int]),
+            "mf_set_batch_schedule": (C.c_int, [vp, C.c_int, C.c_int, i64, i64, C.c_int]),
             "mf_autotune_batch": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double,
                                             C.POINTER(C.c_int)]),
         }

@@ -135,15 +135,15 @@ class Context:
                                                   out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
 
-    def set_batch_schedule(self, sched: int, tile_events: int, ctas_per_sm: int = 0):
-        _check(self.ptr, _lib.lib().mf_set_batch_schedule(self.ptr, sched, tile_events, ctas_per_sm))
+    def set_batch_schedule(self, mode: int, sched: int, tile_heavy: int, tile_light: int, ctas_per_sm: int = 0):
+        _check(self.ptr, _lib.lib().mf_set_batch_schedule(self.ptr, mode, sched, tile_heavy, tile_light, ctas_per_sm))
 
     def autotune_batch(self, processes, n_events, sqrt_s: float):
-        """Pick the batch schedule (barrier schedule, tile events, CTAs per SM) by timing."""
+        """Pick the batch schedule by timing: (mode, sched, tile_heavy, tile_light, ctas_per_sm)."""
         n_ch = len(processes)
         procs = (C.c_int * n_ch)(*[int(p) for p in processes])
         ns = (C.c_longlong * n_ch)(*[int(n) for n in n_events])
-        ch = (C.c_int * 3)()
+        ch = (C.c_int * 5)()
         _check(self.ptr, _lib.lib().mf_autotune_batch(self.ptr, n_ch, procs, ns, sqrt_s, ch))
         return tuple(ch)
 

@@ -1,18 +1,26 @@
-// Batched channels in one persistent launch, with the VEGAS iterations
-// captured as a CUDA graph and the launch schedule picked by a small
-// autotuner (declared in include/madflow_gb300.h: mf_integrate_batch,
-// mf_autotune_batch).
+// Batched channels: several partonic subprocesses in one graph-captured
+// VEGAS run (declared in include/madflow_gb300.h: mf_integrate_batch,
+// mf_batch_grad, mf_set_batch_schedule, mf_autotune_batch).
 //
-// The work is a list of (channel, tile) pairs: tile t of channel c holds
-// events [t T, (t+1) T) of that channel.  Persistent CTAs take tiles from a
-// device counter (an atomic increment: no CTA ever waits for another), run
-// the channel's own integrand on them with the channel's own VEGAS grid and
-// Philox channel id, and write one set of partial sums per tile.  The
-// end-of-pass reduction sums the tiles of each channel in tile order, so the
-// result does not depend on which CTA ran which tile.
+// The work of one iteration is a list of (channel, tile) items: tile t of a
+// channel holds events [t T, (t+1) T) of that channel.  Persistent CTAs take
+// items from a device counter (an atomic increment: no CTA ever waits for
+// another), run the channel's own integrand with the channel's own VEGAS grid
+// and Philox channel id, and write one row of partial sums per tile.  The
+// end-of-pass reduction sums a channel's rows in tile order, so the result
+// does not depend on which CTA ran which tile.  Items are handed out most
+// expensive channel first, so that the cheap tiles fill the end.
+//
+// Two schedules:
+//   0  one persistent launch over every channel;
+//   1  split: the 2 -> 3 and 2 -> 4 gluon channels (255 registers a thread)
+//      in the persistent launch on a high-priority stream, the cheaper
+//      channels as their own integrand kernels (fewer registers, more
+//      resident warps) on a low-priority stream forked from it; their CTAs
+//      take the SMs that the persistent CTAs leave when the expensive work
+//      runs out.
 #include <cuda_runtime.h>
 #include <algorithm>
-#include <chrono>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -44,42 +52,43 @@ __global__ void __launch_bounds__(BATCH_TPB) batch_kernel(BatchParams bp)
     __shared__ KParams s_kp;
     __shared__ long long s_tile;
     const int tid = threadIdx.x;
-    const long long total = bp.tile_begin[bp.n_ch];
+    const long long total = bp.tile_begin[bp.n_slot];
     for (;;) {
         if (tid == 0) s_tile = (long long)atomicAdd(bp.tile_counter, 1ull);
         __syncthreads();
         const long long t = s_tile;
         if (t >= total) break;
         int c = 0;
-        while (c + 1 < bp.n_ch && t >= bp.tile_begin[c + 1]) ++c;
+        while (c + 1 < bp.n_slot && t >= bp.tile_begin[c + 1]) ++c;
         if (tid == 0) {
             s_kp = bp.kps[c];
             s_kp.iteration = bp.iteration;
         }
         __syncthreads();
-        const long long lt = t - bp.tile_begin[c];
-        const long long e0 = lt * bp.tile_events;
-        const long long e1 = e0 + bp.tile_events < s_kp.n_events ? e0 + bp.tile_events : s_kp.n_events;
+        const long long lt = t - bp.tile_begin[c], te = bp.tile_events[c];
+        const long long e0 = lt * te;
+        const long long e1 = e0 + te < s_kp.n_events ? e0 + te : s_kp.n_events;
+        double* out = nullptr;   // this tile's row of partial sums
         switch (bp.proc[c]) {
         case MF_GG_TT:
-            integrand_light<PGgTt, float, BATCH_TPB, false>(s_kp, smem_raw, e0, BATCH_TPB, e1,
-                                                            bp.tile_out[c] + lt * (2 + PGgTt::D * s_kp.nb));
+            out = bp.tile_out[c] + lt * (2 + PGgTt::D * s_kp.nb);
+            integrand_light<PGgTt, float, BATCH_TPB, false>(s_kp, smem_raw, e0, BATCH_TPB, e1, out);
             break;
         case MF_UU_TT:
-            integrand_light<PUuTt, float, BATCH_TPB, false>(s_kp, smem_raw, e0, BATCH_TPB, e1,
-                                                            bp.tile_out[c] + lt * (2 + PUuTt::D * s_kp.nb));
+            out = bp.tile_out[c] + lt * (2 + PUuTt::D * s_kp.nb);
+            integrand_light<PUuTt, float, BATCH_TPB, false>(s_kp, smem_raw, e0, BATCH_TPB, e1, out);
             break;
         case MF_UG_TTU:
-            integrand_light<PUgTtu, float, BATCH_TPB, false>(s_kp, smem_raw, e0, BATCH_TPB, e1,
-                                                             bp.tile_out[c] + lt * (2 + PUgTtu::D * s_kp.nb));
+            out = bp.tile_out[c] + lt * (2 + PUgTtu::D * s_kp.nb);
+            integrand_light<PUgTtu, float, BATCH_TPB, false>(s_kp, smem_raw, e0, BATCH_TPB, e1, out);
             break;
         case MF_GG_TTG:
-            integrand_heavy<PGgTtg, float, BATCH_TPB, false, SYNC>(s_kp, smem_raw, e0, BATCH_TPB, e1,
-                                                                   bp.tile_out[c] + lt * (2 + PGgTtg::D * s_kp.nb));
+            out = bp.tile_out[c] + lt * (2 + PGgTtg::D * s_kp.nb);
+            integrand_heavy<PGgTtg, float, BATCH_TPB, false, SYNC>(s_kp, smem_raw, e0, BATCH_TPB, e1, out);
             break;
         case MF_GG_TTGG:
-            integrand_heavy<PGgTtgg, float, BATCH_TPB, false, SYNC>(s_kp, smem_raw, e0, BATCH_TPB, e1,
-                                                                    bp.tile_out[c] + lt * (2 + PGgTtgg::D * s_kp.nb));
+            out = bp.tile_out[c] + lt * (2 + PGgTtgg::D * s_kp.nb);
+            integrand_heavy<PGgTtgg, float, BATCH_TPB, false, SYNC>(s_kp, smem_raw, e0, BATCH_TPB, e1, out);
             break;
         default:
             break;
@@ -105,6 +114,21 @@ size_t batch_smem(int nb, int npv)
     return m;
 }
 
+// relative cost of one event (orders the work list; the expensive channels first)
+int event_cost(int p)
+{
+    switch (p) {
+    case MF_GG_TTGG: return 64;
+    case MF_GG_TTG: return 8;
+    case MF_UG_TTU: return 3;
+    case MF_GG_TT: return 1;
+    case MF_UU_TT: return 1;
+    default: return 0;
+    }
+}
+
+bool heavy_channel(int p) { return p == MF_GG_TTG || p == MF_GG_TTGG; }
+
 #define MF_BCUDA(ctx, call)                                                                      \
     do {                                                                                         \
         cudaError_t e_ = (call);                                                                 \
@@ -115,9 +139,13 @@ size_t batch_smem(int nb, int npv)
 int ensure_batch_buffers(mf_ctx* c, size_t tile_doubles)
 {
     if (!c->cap_stream) {
-        MF_BCUDA(c, cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+        int least = 0, greatest = 0;
+        MF_BCUDA(c, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+        MF_BCUDA(c, cudaStreamCreateWithPriority(&c->cap_stream, cudaStreamNonBlocking, greatest));
+        MF_BCUDA(c, cudaStreamCreateWithPriority(&c->cap_low, cudaStreamNonBlocking, least));
         MF_BCUDA(c, cudaEventCreateWithFlags(&c->ev_user, cudaEventDisableTiming));
         MF_BCUDA(c, cudaEventCreateWithFlags(&c->ev_cap, cudaEventDisableTiming));
+        MF_BCUDA(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
         MF_BCUDA(c, cudaMalloc(&c->d_kps, sizeof(KParams) * MAX_CH));
         MF_BCUDA(c, cudaMalloc(&c->d_bgrids, sizeof(double) * MAX_CH * MAX_DIM * (MAX_BINS + 1)));
         MF_BCUDA(c, cudaMalloc(&c->d_biter, sizeof(double) * MAX_CH * 1000 * 2));
@@ -128,39 +156,55 @@ int ensure_batch_buffers(mf_ctx* c, size_t tile_doubles)
         MF_BCUDA(c, cudaFuncSetAttribute((const void*)batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     }
     if (tile_doubles > c->tiles_cap) {
+        if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_key.clear(); }
         cudaFree(c->d_tiles);
         c->d_tiles = nullptr;
         c->tiles_cap = 0;
         MF_BCUDA(c, cudaMalloc(&c->d_tiles, sizeof(double) * tile_doubles));
         c->tiles_cap = tile_doubles;
-        if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_key.clear(); }
     }
     return MF_OK;
 }
+
+struct Schedule {
+    int mode, sched, bps;
+    long long tile_heavy, tile_light;
+};
+
+// a cheaper channel of the split schedule: its own integrand kernel
+struct SideLaunch {
+    int ch;
+    const ProcOps* ops;
+    KParams kp;
+    int nblk;
+    size_t sm;
+};
 
 struct Plan {
     int n_ch = 0;
     int proc[MAX_CH];
     long long n[MAX_CH];
     int dim[MAX_CH];
-    long long tiles[MAX_CH];
-    BatchParams bp;
-    std::vector<KParams> kps;
+    long long rows[MAX_CH];        // partial-sum rows of each channel (tiles or CTAs)
+    double* out[MAX_CH];           // each channel's rows
+    Schedule sch;
+    BatchParams bp;                // persistent launch (slots = its channels, expensive first)
+    std::vector<KParams> slot_kp;
+    std::vector<SideLaunch> side;  // split schedule: cheaper channels, expensive first
     int nblk = 0;
     size_t sm = 0;
-    int sched = 1;
 };
 
-int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, double sqrt_s, long long tile,
-              int sched, int bps, Plan& pl)
+int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, double sqrt_s, const Schedule& sch,
+              Plan& pl)
 {
     if (n_ch < 1 || n_ch > MAX_CH || !procs || !n_events) return mf_fail(c, MF_ERR_ARG, "batch: bad channel list");
     if (c->cfg.precision != MF_MIXED) return mf_fail(c, MF_ERR_UNSUPPORTED, "batch: only the mixed precision is built");
     pl.n_ch = n_ch;
-    pl.sched = sched;
-    pl.kps.resize(n_ch);
+    pl.sch = sch;
     const int nb = c->cfg.n_bins;
-    size_t tile_doubles = 0;
+    const int npv = c->nx * c->nq;
+    std::vector<int> order(n_ch);
     for (int i = 0; i < n_ch; ++i) {
         const ProcOps* ops = mf_proc_ops(procs[i]);
         if (!ops || procs[i] == MF_EE_MUMU) return mf_fail(c, MF_ERR_ARG, "batch: channels must be hadronic top processes");
@@ -168,21 +212,47 @@ int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, 
         pl.proc[i] = procs[i];
         pl.n[i] = n_events[i];
         pl.dim[i] = ops->D;
-        pl.tiles[i] = (n_events[i] + tile - 1) / tile;
-        tile_doubles += (size_t)pl.tiles[i] * (2 + ops->D * nb);
+        order[i] = i;
+    }
+    // expensive channels first; equal costs keep the caller's order
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return event_cost(procs[a]) > event_cost(procs[b]); });
+    bool in_kernel[MAX_CH];
+    size_t tile_doubles = 0;
+    for (int i = 0; i < n_ch; ++i) {
+        const ProcOps* ops = mf_proc_ops(procs[i]);
+        in_kernel[i] = sch.mode == 0 || heavy_channel(procs[i]);
+        if (in_kernel[i]) {
+            const long long te = heavy_channel(procs[i]) ? sch.tile_heavy : sch.tile_light;
+            pl.rows[i] = (n_events[i] + te - 1) / te;
+        } else {
+            int per_sm = 0;
+            const size_t sm = ops->smem(MF_MIXED, nb, npv);
+            MF_BCUDA(c, ops->occupancy(MF_MIXED, sm, &per_sm));
+            if (per_sm < 1) return mf_fail(c, MF_ERR_CUDA, "integrand kernel does not fit on an SM");
+            const long long want = (n_events[i] + sch.tile_light - 1) / sch.tile_light;
+            pl.rows[i] = std::max(1LL, std::min(want, (long long)c->max_blocks));
+        }
+        tile_doubles += (size_t)pl.rows[i] * (2 + ops->D * nb);
     }
     int rc = ensure_batch_buffers(c, tile_doubles);
     if (rc) return rc;
+    size_t off = 0;
+    for (int i = 0; i < n_ch; ++i) {
+        pl.out[i] = c->d_tiles + off;
+        off += (size_t)pl.rows[i] * (2 + pl.dim[i] * nb);
+    }
     std::memset(&pl.bp, 0, sizeof(pl.bp));
     pl.bp.kps = c->d_kps;
-    pl.bp.n_ch = n_ch;
-    pl.bp.tile_events = tile;
     pl.bp.tile_counter = c->d_bcount + 2 * MAX_CH;
-    size_t off = 0;
+    pl.slot_kp.clear();
+    pl.side.clear();
     long long tb = 0;
-    for (int i = 0; i < n_ch; ++i) {
-        KParams& kp = pl.kps[i];
-        rc = mf_make_params(c, procs[i], mf_proc_ops(procs[i]), sqrt_s, kp);
+    for (int k = 0; k < n_ch; ++k) {
+        const int i = order[k];
+        const ProcOps* ops = mf_proc_ops(procs[i]);
+        KParams kp;
+        rc = mf_make_params(c, procs[i], ops, sqrt_s, kp);
         if (rc) return rc;
         kp.channel = c->cfg.channel + (uint32_t)i;
         kp.n_events = n_events[i];
@@ -190,26 +260,41 @@ int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, 
         kp.inv_n = 1.0 / (double)n_events[i];
         kp.grid = c->d_bgrids + (size_t)i * MAX_DIM * (MAX_BINS + 1);
         kp.counters = c->d_bcount + 2 * i;
-        kp.partials = nullptr;
-        pl.bp.proc[i] = procs[i];
-        pl.bp.tile_begin[i] = tb;
-        pl.bp.tile_out[i] = c->d_tiles + off;
-        tb += pl.tiles[i];
-        off += (size_t)pl.tiles[i] * (2 + pl.dim[i] * nb);
+        kp.partials = pl.out[i];
+        if (in_kernel[i]) {
+            const int s = pl.bp.n_slot++;
+            pl.bp.proc[s] = procs[i];
+            pl.bp.tile_begin[s] = tb;
+            pl.bp.tile_events[s] = heavy_channel(procs[i]) ? sch.tile_heavy : sch.tile_light;
+            pl.bp.tile_out[s] = pl.out[i];
+            tb += pl.rows[i];
+            pl.slot_kp.push_back(kp);
+        } else {
+            SideLaunch sl;
+            sl.ch = i;
+            sl.ops = ops;
+            sl.kp = kp;
+            sl.nblk = (int)pl.rows[i];
+            sl.sm = ops->smem(MF_MIXED, nb, npv);
+            pl.side.push_back(sl);
+        }
     }
-    pl.bp.tile_begin[n_ch] = tb;
-    pl.sm = batch_smem(nb, c->nx * c->nq);
-    int per_sm = 0;
-    MF_BCUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sched ? (const void*)batch_kernel<true>
-                                                                               : (const void*)batch_kernel<false>,
-                                                               BATCH_TPB, pl.sm));
-    if (per_sm < 1) return mf_fail(c, MF_ERR_CUDA, "batch kernel does not fit on an SM");
-    if (bps > 0 && bps < per_sm) per_sm = bps;
-    pl.nblk = per_sm * c->n_sm;
+    pl.bp.tile_begin[pl.bp.n_slot] = tb;
+    pl.sm = batch_smem(nb, npv);
+    pl.nblk = 0;
+    if (pl.bp.n_slot > 0) {
+        int per_sm = 0;
+        MF_BCUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sch.sched ? (const void*)batch_kernel<true>
+                                                                                      : (const void*)batch_kernel<false>,
+                                                                   BATCH_TPB, pl.sm));
+        if (per_sm < 1) return mf_fail(c, MF_ERR_CUDA, "batch kernel does not fit on an SM");
+        if (sch.bps > 0 && sch.bps < per_sm) per_sm = sch.bps;
+        pl.nblk = (int)std::min<long long>((long long)per_sm * c->n_sm, tb);
+    }
     return MF_OK;
 }
 
-// the uniform starting grids of every channel and the counters
+// the uniform starting grids of every channel, the slot parameters and the counters
 int reset_batch(mf_ctx* c, const Plan& pl, cudaStream_t s)
 {
     const int nb = c->cfg.n_bins;
@@ -219,26 +304,44 @@ int reset_batch(mf_ctx* c, const Plan& pl, cudaStream_t s)
             for (int k = 0; k <= nb; ++k)
                 g[(size_t)i * MAX_DIM * (MAX_BINS + 1) + (size_t)d * (nb + 1) + k] = (double)k / (double)nb;
     MF_BCUDA(c, cudaMemcpyAsync(c->d_bgrids, g.data(), g.size() * sizeof(double), cudaMemcpyHostToDevice, s));
-    MF_BCUDA(c, cudaMemcpyAsync(c->d_kps, pl.kps.data(), sizeof(KParams) * pl.n_ch, cudaMemcpyHostToDevice, s));
+    if (!pl.slot_kp.empty())
+        MF_BCUDA(c, cudaMemcpyAsync(c->d_kps, pl.slot_kp.data(), sizeof(KParams) * pl.slot_kp.size(),
+                                    cudaMemcpyHostToDevice, s));
     MF_BCUDA(c, cudaMemsetAsync(c->d_bcount, 0, sizeof(unsigned long long) * 2 * MAX_CH, s));
-    // the pageable staging above must complete before the host vector goes away
+    // the pageable staging above must complete before the host vectors go away
     MF_BCUDA(c, cudaStreamSynchronize(s));
     return MF_OK;
 }
 
-// one iteration: the persistent launch, then per channel the tile reduction and the refinement
-int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s)
+// one iteration: the persistent launch (and, split, the side kernels on the
+// forked low-priority stream), then per channel the row reduction and refinement
+int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s, cudaStream_t low)
 {
     const int nb = c->cfg.n_bins;
-    MF_BCUDA(c, cudaMemsetAsync(pl.bp.tile_counter, 0, sizeof(unsigned long long), s));
-    pl.bp.iteration = (unsigned)it;
-    if (pl.sched) batch_kernel<true><<<pl.nblk, BATCH_TPB, pl.sm, s>>>(pl.bp);
-    else batch_kernel<false><<<pl.nblk, BATCH_TPB, pl.sm, s>>>(pl.bp);
-    MF_BCUDA(c, cudaGetLastError());
+    const bool fork = !pl.side.empty();
+    if (fork) {
+        MF_BCUDA(c, cudaEventRecord(c->ev_cap, s));
+        MF_BCUDA(c, cudaStreamWaitEvent(low, c->ev_cap, 0));
+    }
+    if (pl.bp.n_slot > 0) {
+        MF_BCUDA(c, cudaMemsetAsync(pl.bp.tile_counter, 0, sizeof(unsigned long long), s));
+        pl.bp.iteration = (unsigned)it;
+        if (pl.sch.sched) batch_kernel<true><<<pl.nblk, BATCH_TPB, pl.sm, s>>>(pl.bp);
+        else batch_kernel<false><<<pl.nblk, BATCH_TPB, pl.sm, s>>>(pl.bp);
+        MF_BCUDA(c, cudaGetLastError());
+    }
+    for (SideLaunch& sl : pl.side) {
+        sl.kp.iteration = (unsigned)it;
+        MF_BCUDA(c, sl.ops->integrand(MF_MIXED, false, pl.sch.sched, sl.kp, sl.nblk, sl.sm, low));
+    }
+    if (fork) {
+        MF_BCUDA(c, cudaEventRecord(c->ev_join, low));
+        MF_BCUDA(c, cudaStreamWaitEvent(s, c->ev_join, 0));
+    }
     for (int i = 0; i < pl.n_ch; ++i) {
         const int ncol = 2 + pl.dim[i] * nb;
         finish_pass_kernel<<<1, 1024, ncol * sizeof(double), s>>>(
-            pl.bp.tile_out[i], (int)pl.tiles[i], pl.dim[i], nb, pl.n[i], c->cfg.alpha, it < n_iter - 1,
+            pl.out[i], (int)pl.rows[i], pl.dim[i], nb, pl.n[i], c->cfg.alpha, it < n_iter - 1,
             c->d_bgrids + (size_t)i * MAX_DIM * (MAX_BINS + 1), c->d_biter + ((size_t)i * 1000 + it) * 2,
             c->d_bsums + (size_t)i * (2 + MAX_DIM * MAX_BINS));
         MF_BCUDA(c, cudaGetLastError());
@@ -246,11 +349,41 @@ int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s)
     return MF_OK;
 }
 
+// The persistent kernels run at the stream's high priority and the side
+// kernels at the low one; set on the captured nodes explicitly and honoured
+// through cudaGraphInstantiateFlagUseNodePriority.
+int set_node_priorities(mf_ctx* c, cudaGraph_t g)
+{
+    int least = 0, greatest = 0;
+    MF_BCUDA(c, cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    size_t n = 0;
+    MF_BCUDA(c, cudaGraphGetNodes(g, nullptr, &n));
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (n) MF_BCUDA(c, cudaGraphGetNodes(g, nodes.data(), &n));
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType ty;
+        MF_BCUDA(c, cudaGraphNodeGetType(nd, &ty));
+        if (ty != cudaGraphNodeTypeKernel) continue;
+        cudaKernelNodeParams kp;
+        MF_BCUDA(c, cudaGraphKernelNodeGetParams(nd, &kp));
+        const bool hi = kp.func == (void*)batch_kernel<true> || kp.func == (void*)batch_kernel<false>;
+        cudaLaunchAttributeValue v;
+        std::memset(&v, 0, sizeof(v));
+        v.priority = hi ? greatest : least;
+        MF_BCUDA(c, cudaGraphKernelNodeSetAttribute(nd, cudaLaunchAttributePriority, &v));
+    }
+    return MF_OK;
+}
+
 std::string plan_key(const mf_ctx* c, const Plan& pl, int n_iter, double sqrt_s)
 {
-    std::string k = std::to_string(n_iter) + "|" + std::to_string(sqrt_s) + "|" + std::to_string(pl.sched) + "|" +
-                    std::to_string(pl.bp.tile_events) + "|" + std::to_string(pl.nblk) + "|" +
-                    std::to_string(c->cfg.n_bins) + "|" + std::to_string(c->cfg.alpha) + "|" + std::to_string((unsigned long long)c->d_tiles);
+    // the side kernels' parameters are baked into the graph: couplings are part of the key
+    std::string k = std::to_string(n_iter) + "|" + std::to_string(sqrt_s) + "|" + std::to_string(pl.sch.mode) + "|" +
+                    std::to_string(pl.sch.sched) + "|" + std::to_string(pl.sch.tile_heavy) + "|" +
+                    std::to_string(pl.sch.tile_light) + "|" + std::to_string(pl.nblk) + "|" +
+                    std::to_string(c->cfg.n_bins) + "|" + std::to_string(c->cfg.alpha) + "|" +
+                    std::to_string(c->cfg.mt) + "|" + std::to_string(c->cfg.alpha_s) + "|" +
+                    std::to_string((unsigned long long)c->d_tiles) + "|" + std::to_string((unsigned long long)c->d_pdf);
     for (int i = 0; i < pl.n_ch; ++i) k += "|" + std::to_string(pl.proc[i]) + ":" + std::to_string(pl.n[i]);
     return k;
 }
@@ -270,6 +403,11 @@ void combine(const double* it, int n_iter, double& mean, double& err, double& ch
     chi2dof = n_iter > 1 ? chi2 / (n_iter - 1) : 0.0;
 }
 
+Schedule current_schedule(const mf_ctx* c)
+{
+    return Schedule{ c->b_mode, c->b_sched, c->b_bps, c->b_tile_heavy, c->b_tile_light };
+}
+
 }  // namespace
 
 extern "C" {
@@ -281,7 +419,7 @@ int mf_integrate_batch(mf_ctx* c, int n_ch, const int* processes, const long lon
     if (n_iter < 1 || n_iter > 1000 || !per_ch_host || !total_host || !(sqrt_s > 0.0))
         return mf_fail(c, MF_ERR_ARG, "mf_integrate_batch: bad argument");
     Plan pl;
-    int rc = make_plan(c, n_ch, processes, n_events, sqrt_s, c->b_tile, c->b_sched, c->b_bps, pl);
+    int rc = make_plan(c, n_ch, processes, n_events, sqrt_s, current_schedule(c), pl);
     if (rc) return rc;
     // order against the caller's stream, then work on the private capture stream
     MF_BCUDA(c, cudaEventRecord(c->ev_user, c->stream));
@@ -290,17 +428,22 @@ int mf_integrate_batch(mf_ctx* c, int n_ch, const int* processes, const long lon
     if (rc) return rc;
     const std::string key = plan_key(c, pl, n_iter, sqrt_s);
     if (!c->graph || c->graph_key != key) {
-        if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; }
+        if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_key.clear(); }
         cudaGraph_t g = nullptr;
         MF_BCUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         int erc = MF_OK;
-        for (int it = 0; it < n_iter && erc == MF_OK; ++it) erc = enqueue_iteration(c, pl, it, n_iter, c->cap_stream);
+        for (int it = 0; it < n_iter && erc == MF_OK; ++it)
+            erc = enqueue_iteration(c, pl, it, n_iter, c->cap_stream, c->cap_low);
         cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
+        if (erc == MF_OK && ce == cudaSuccess) erc = set_node_priorities(c, g);
         if (erc) { if (g) cudaGraphDestroy(g); return erc; }
         if (ce != cudaSuccess) return mf_fail(c, MF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
-        ce = cudaGraphInstantiate(&c->graph, g, 0);
+        ce = cudaGraphInstantiateWithFlags(&c->graph, g, cudaGraphInstantiateFlagUseNodePriority);
         cudaGraphDestroy(g);
-        if (ce != cudaSuccess) { c->graph = nullptr; return mf_fail(c, MF_ERR_CUDA, "graph instantiate failed"); }
+        if (ce != cudaSuccess) {
+            c->graph = nullptr;
+            return mf_fail(c, MF_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        }
         c->graph_key = key;
     }
     MF_BCUDA(c, cudaGraphLaunch(c->graph, c->cap_stream));
@@ -385,12 +528,13 @@ int mf_batch_grad(mf_ctx* c, int n_ch, const int* processes, const long long* n_
     double t[4] = { 0.0, 0.0, 0.0, 0.0 };
     for (int i = 0; i < n_ch; ++i) {
         const double n = (double)n_events[i], d = o[4 * i + 1], s2 = o[4 * i + 2];
-        const double var = (n * s2 - d * d) / (n - 1.0);
+        double var = (n * s2 - d * d) / (n - 1.0);
+        var = var > 0.0 ? var : 0.0;
         out_host[4 * i + 0] = o[4 * i + 0];
         out_host[4 * i + 1] = d;
-        out_host[4 * i + 2] = std::sqrt(var > 0.0 ? var : 0.0);
+        out_host[4 * i + 2] = std::sqrt(var);
         out_host[4 * i + 3] = o[4 * i + 3];
-        t[0] += o[4 * i]; t[1] += d; t[2] += var > 0.0 ? var : 0.0; t[3] += o[4 * i + 3];
+        t[0] += o[4 * i]; t[1] += d; t[2] += var; t[3] += o[4 * i + 3];
     }
     out_host[4 * n_ch + 0] = t[0];
     out_host[4 * n_ch + 1] = t[1];
@@ -399,14 +543,16 @@ int mf_batch_grad(mf_ctx* c, int n_ch, const int* processes, const long long* n_
     return MF_OK;
 }
 
-int mf_set_batch_schedule(mf_ctx* c, int sched, long long tile_events, int ctas_per_sm)
+int mf_set_batch_schedule(mf_ctx* c, int mode, int sched, long long tile_heavy, long long tile_light, int ctas_per_sm)
 {
     if (!c) return MF_ERR_ARG;
-    if ((sched != 0 && sched != 1) || tile_events < 32 || tile_events > (1LL << 26) || ctas_per_sm < 0 ||
-        ctas_per_sm > 16)
+    if ((mode != 0 && mode != 1) || (sched != 0 && sched != 1) || tile_heavy < 32 || tile_heavy > (1LL << 26) ||
+        tile_light < 32 || tile_light > (1LL << 26) || ctas_per_sm < 0 || ctas_per_sm > 16)
         return mf_fail(c, MF_ERR_ARG, "mf_set_batch_schedule: bad argument");
+    c->b_mode = mode;
     c->b_sched = sched;
-    c->b_tile = tile_events;
+    c->b_tile_heavy = tile_heavy;
+    c->b_tile_light = tile_light;
     c->b_bps = ctas_per_sm;
     return MF_OK;
 }
@@ -415,44 +561,60 @@ int mf_autotune_batch(mf_ctx* c, int n_ch, const int* processes, const long long
                       int* choice_host)
 {
     if (!c) return MF_ERR_ARG;
-    if (!(sqrt_s > 0.0) || !n_events) return mf_fail(c, MF_ERR_ARG, "mf_autotune_batch: bad argument");
-    // pilot: one pass over an eighth of every channel's events at the uniform grid
-    std::vector<long long> pilot(n_ch > 0 && n_ch <= MAX_CH ? n_ch : 1);
-    for (int i = 0; i < (int)pilot.size(); ++i) pilot[i] = std::max(2LL, n_events[i] / 8);
-    const long long tiles[3] = { 2048, 4096, 16384 };
+    if (!(sqrt_s > 0.0) || !n_events || !processes || n_ch < 1 || n_ch > MAX_CH)
+        return mf_fail(c, MF_ERR_ARG, "mf_autotune_batch: bad argument");
+    // candidates, each timed over one iteration of the full sizes at the uniform grid
+    std::vector<Schedule> cand;
+    for (int mode = 0; mode <= 1; ++mode)
+        for (int sched = 0; sched <= 1; ++sched)
+            for (long long th : { 1024LL, 2048LL, 4096LL })
+                for (long long tl : { 2048LL, 4096LL })
+                    cand.push_back(Schedule{ mode, sched, 0, th, tl });
     float best = 1e30f;
-    int best_s = c->b_sched, best_b = c->b_bps;
-    long long best_t = c->b_tile;
-    cudaEvent_t e0, e1;
+    Schedule pick = current_schedule(c);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
     MF_BCUDA(c, cudaEventCreate(&e0));
     MF_BCUDA(c, cudaEventCreate(&e1));
     int rc = MF_OK;
-    for (int sched = 0; sched <= 1 && rc == MF_OK; ++sched)
-        for (long long tile : tiles)
-            for (int bps = 1; bps <= 2 && rc == MF_OK; ++bps) {
-                Plan pl;
-                rc = make_plan(c, n_ch, processes, pilot.data(), sqrt_s, tile, sched, bps, pl);
-                if (rc) break;
-                rc = reset_batch(c, pl, c->cap_stream);
-                if (rc) break;
-                rc = enqueue_iteration(c, pl, 0, 1, c->cap_stream);   // warm-up
-                if (rc) break;
-                cudaEventRecord(e0, c->cap_stream);
-                rc = enqueue_iteration(c, pl, 1, 2, c->cap_stream);
-                if (rc) break;
-                cudaEventRecord(e1, c->cap_stream);
-                if (cudaEventSynchronize(e1) != cudaSuccess) { rc = mf_fail(c, MF_ERR_CUDA, "autotune timing"); break; }
-                float ms = 0.0f;
-                cudaEventElapsedTime(&ms, e0, e1);
-                if (ms < best) { best = ms; best_s = sched; best_t = tile; best_b = bps; }
-            }
+    bool warmed[2] = { false, false };
+    for (const Schedule& s : cand) {
+        Plan pl;
+        rc = make_plan(c, n_ch, processes, n_events, sqrt_s, s, pl);
+        if (rc) break;
+        if (!warmed[s.mode]) {
+            rc = reset_batch(c, pl, c->cap_stream);
+            if (!rc) rc = enqueue_iteration(c, pl, 0, 1, c->cap_stream, c->cap_low);
+            if (rc) break;
+            warmed[s.mode] = true;
+        }
+        rc = reset_batch(c, pl, c->cap_stream);
+        if (rc) break;
+        if (cudaEventRecord(e0, c->cap_stream) != cudaSuccess) { rc = mf_fail(c, MF_ERR_CUDA, "autotune timing"); break; }
+        rc = enqueue_iteration(c, pl, 0, 1, c->cap_stream, c->cap_low);
+        if (rc) break;
+        if (cudaEventRecord(e1, c->cap_stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+            rc = mf_fail(c, MF_ERR_CUDA, "autotune timing");
+            break;
+        }
+        float ms = 0.0f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; pick = s; }
+    }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     if (rc) return rc;
-    c->b_sched = best_s;
-    c->b_tile = best_t;
-    c->b_bps = best_b;
-    if (choice_host) { choice_host[0] = best_s; choice_host[1] = (int)best_t; choice_host[2] = best_b; }
+    c->b_mode = pick.mode;
+    c->b_sched = pick.sched;
+    c->b_tile_heavy = pick.tile_heavy;
+    c->b_tile_light = pick.tile_light;
+    c->b_bps = pick.bps;
+    if (choice_host) {
+        choice_host[0] = pick.mode;
+        choice_host[1] = pick.sched;
+        choice_host[2] = (int)pick.tile_heavy;
+        choice_host[3] = (int)pick.tile_light;
+        choice_host[4] = pick.bps;
+    }
     return MF_OK;
 }
 

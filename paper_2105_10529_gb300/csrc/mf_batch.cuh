@@ -8,13 +8,15 @@ namespace mf {
 
 constexpr int MAX_CH = 8;
 
+// The work list of one persistent launch: slots (channels) in the order
+// their tiles are handed out, most expensive events first.
 struct BatchParams {
-    const KParams* kps;                 // [n_ch] per-channel parameters (device memory)
-    int proc[MAX_CH];                   // mf_process of each channel
-    long long tile_begin[MAX_CH + 1];   // global tile index where each channel starts
-    double* tile_out[MAX_CH];           // [tiles of the channel][2 + D nb] partial sums per tile
-    int n_ch;
-    long long tile_events;              // events per tile
+    const KParams* kps;                 // [n_slot] per-slot parameters (device memory)
+    int proc[MAX_CH];                   // mf_process of each slot
+    long long tile_begin[MAX_CH + 1];   // global tile index where each slot starts
+    long long tile_events[MAX_CH];      // events per tile of each slot
+    double* tile_out[MAX_CH];           // [tiles of the slot][2 + D nb] partial sums per tile
+    int n_slot;
     unsigned long long* tile_counter;   // next tile to hand out (zeroed before the launch)
     unsigned int iteration;             // Philox iteration of this pass
 };

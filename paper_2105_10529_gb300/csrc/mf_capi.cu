@@ -290,7 +290,9 @@ void mf_destroy(mf_ctx* c)
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->ev_user) cudaEventDestroy(c->ev_user);
     if (c->ev_cap) cudaEventDestroy(c->ev_cap);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->cap_low) cudaStreamDestroy(c->cap_low);
     delete c;
 }
 

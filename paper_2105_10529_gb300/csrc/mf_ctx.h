@@ -23,8 +23,9 @@ struct mf_ctx {
     int sched = 1;                   // integrand schedule (see mf_set_schedule)
     std::string err;
     // batched channels: workspace, tuned schedule and the cached CUDA graph
-    cudaStream_t cap_stream = nullptr;   // private stream for graph capture and replay
-    cudaEvent_t ev_user = nullptr, ev_cap = nullptr;
+    cudaStream_t cap_stream = nullptr;   // private stream for graph capture and replay (high priority)
+    cudaStream_t cap_low = nullptr;      // forked low-priority stream of the split schedule
+    cudaEvent_t ev_user = nullptr, ev_cap = nullptr, ev_join = nullptr;
     mf::KParams* d_kps = nullptr;        // [MAX_CH]
     double* d_tiles = nullptr;           // tile partial sums of all channels
     size_t tiles_cap = 0;                // doubles
@@ -32,8 +33,10 @@ struct mf_ctx {
     double* d_biter = nullptr;           // [MAX_CH][1000][2]
     double* d_bsums = nullptr;           // [MAX_CH][2 + MAX_DIM MAX_BINS]
     unsigned long long* d_bcount = nullptr;   // [MAX_CH][2] counters, then the tile counter
+    int b_mode = 0;                      // tuned: 0 one launch for all channels, 1 split (see mf_set_batch_schedule)
     int b_sched = 1, b_bps = 0;          // tuned: barrier schedule, CTAs per SM (0 = occupancy)
-    long long b_tile = 4096;             // tuned: events per tile
+    long long b_tile_heavy = 4096;       // tuned: events per tile of the 2 -> 3 and 2 -> 4 gluon channels
+    long long b_tile_light = 4096;       // tuned: events per tile of the other channels
     cudaGraphExec_t graph = nullptr;
     std::string graph_key;
     int b_last_nch = 0;                  // channel list of the grids in d_bgrids

@@ -39,10 +39,11 @@ def ctx(pdf_grid):
     c.close()
 
 
-def test_batch_one_iteration_matches_oracle(ctx, opdf):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_one_iteration_matches_oracle(ctx, opdf, mode):
     """One iteration at the uniform grid: channel i is the oracle pass of that
     process with channel id PHYS.channel + i (mixed precision: 1e-5)."""
-    ctx.set_batch_schedule(1, TILE, 0)
+    ctx.set_batch_schedule(mode, 1, TILE, 3 * TILE, 0)
     tot, chans = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 1)
     s_sum, v_sum = 0.0, 0.0
     for i, (p, n) in enumerate(zip(CHANNELS, N_EV)):
@@ -61,12 +62,13 @@ def test_batch_one_iteration_matches_oracle(ctx, opdf):
     assert tot["n_events"] == sum(N_EV)
 
 
-def test_batch_iterations_match_single_process(ctx, pdf_grid):
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_iterations_match_single_process(ctx, pdf_grid, mode):
     """Three iterations with refinement: each channel equals mf_integrate of
     that process alone (same channel id); only the grouping of the sums
     differs (tiles against CTAs)."""
     from paper_2105_10529_gb300.api import Context
-    ctx.set_batch_schedule(1, TILE, 0)
+    ctx.set_batch_schedule(mode, 1, TILE, 3 * TILE, 0)
     tot, chans = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 3, want_grids=True)
     for i, (p, n) in enumerate(zip(CHANNELS, N_EV)):
         single = Context(dataclasses.replace(PHYS, channel=PHYS.channel + i), pdf_grid, precision=1)
@@ -81,7 +83,7 @@ def test_batch_iterations_match_single_process(ctx, pdf_grid):
 def test_batch_light_channels_match_oracle_integrate(ctx, opdf):
     """Iterated VEGAS of the light channels against the oracle's integrate."""
     procs, ns = [IN.GG_TT, IN.UU_TT], [30001, 12001]
-    ctx.set_batch_schedule(0, 2048, 0)
+    ctx.set_batch_schedule(0, 0, 2048, 2048, 0)
     tot, chans = ctx.integrate_batch(procs, ns, PHYS.sqrt_s, 3)
     for i, (p, n) in enumerate(zip(procs, ns)):
         ref = O.integrate(p, dataclasses.replace(PHYS, channel=PHYS.channel + i), opdf, n, 3)
@@ -89,12 +91,13 @@ def test_batch_light_channels_match_oracle_integrate(ctx, opdf):
         assert chans[i]["error"] == pytest.approx(ref["error"], rel=1e-4), p
 
 
-def test_batch_schedule_independent(ctx):
-    """At a fixed tile size the result is bit-identical for every barrier
-    schedule and CTA count, and on repeated (graph-replayed) calls."""
+@pytest.mark.parametrize("mode", [0, 1])
+def test_batch_schedule_independent(ctx, mode):
+    """At fixed mode and tile sizes the result is bit-identical for every
+    barrier schedule and CTA count, and on repeated (graph-replayed) calls."""
     ref = None
     for sched, bps in [(1, 0), (0, 0), (1, 1), (0, 2), (1, 0)]:
-        ctx.set_batch_schedule(sched, TILE, bps)
+        ctx.set_batch_schedule(mode, sched, TILE, 3 * TILE, bps)
         tot, chans = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 2, want_grids=True)
         key = [(c["sigma"], c["error"], c["n_pass"]) for c in chans]
         grids = [c["grid"] for c in chans]
@@ -109,7 +112,7 @@ def test_batch_schedule_independent(ctx):
 def test_batch_graph_cache_invalidation(ctx):
     """A different channel list in between re-captures; the original list
     then gives the same numbers again."""
-    ctx.set_batch_schedule(1, TILE, 0)
+    ctx.set_batch_schedule(1, 1, TILE, 3 * TILE, 0)
     a, ca = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 2)
     b, cb = ctx.integrate_batch([IN.GG_TT], [5003], PHYS.sqrt_s, 2)
     assert cb[0]["n_events"] == 2 * 5003
@@ -123,7 +126,8 @@ def test_batch_graph_cache_invalidation(ctx):
 
 def test_batch_autotune(ctx):
     choice = ctx.autotune_batch(CHANNELS, [40000, 10000, 10000, 8000, 4000], PHYS.sqrt_s)
-    assert choice[0] in (0, 1) and choice[1] in (2048, 4096, 16384) and choice[2] in (1, 2)
+    assert choice[0] in (0, 1) and choice[1] in (0, 1) and choice[2] in (1024, 2048, 4096)
+    assert choice[3] in (2048, 4096) and choice[4] == 0
     tot, chans = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 1)
     ctx.set_batch_schedule(*choice)
     tot2, chans2 = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 1)
@@ -140,7 +144,8 @@ def test_batch_bad_arguments(ctx, pdf_grid):
     with pytest.raises(MfError) as e:
         ctx.integrate_batch([IN.GG_TT], [100], PHYS.sqrt_s, 0)
     assert e.value.code == 1
-    for bad in [(2, 4096, 0), (1, 16, 0), (1, 4096, -1)]:
+    for bad in [(2, 1, 1024, 4096, 0), (1, 2, 1024, 4096, 0), (1, 1, 16, 4096, 0), (1, 1, 1024, 16, 0),
+                (1, 1, 1024, 4096, -1)]:
         with pytest.raises(MfError):
             ctx.set_batch_schedule(*bad)
     f64 = Context(PHYS, pdf_grid, precision=0)
@@ -155,7 +160,7 @@ def test_batch_grad_matches_single_process(ctx, pdf_grid):
     process at the batch's final grid (same kernel, same channel id), and the
     total is the sum over channels."""
     from paper_2105_10529_gb300.api import Context
-    ctx.set_batch_schedule(1, TILE, 0)
+    ctx.set_batch_schedule(1, 1, TILE, 3 * TILE, 0)
     tot, chans = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 2, want_grids=True)
     it = 7
     g = ctx.batch_grad(CHANNELS, N_EV, PHYS.sqrt_s, it)
