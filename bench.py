@@ -31,6 +31,11 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_NOMINAL_TFLOPS = 1.25
+# DRAM bytes (read + write) per event of the mixed g g -> t tbar g g integrand with the
+# tensor-core colour sum, from the ncu capture summarised in
+# profiles/integrand_gg_ttgg_mixed_100k_ncu.txt (283.6 MB over 100k events; the traffic,
+# evicted local-memory lines, grows with the number of events)
+DRAM_BYTES_PER_EVENT_P3_TC = 2836.3
 
 
 def parse():
@@ -44,7 +49,9 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched p p -> t tbar + jets leg")
     ap.add_argument("--batch-iters", type=int, default=10)
-    ap.add_argument("--sched", type=int, default=None, help="integrand schedule (0 free warps, 1 CTA barrier per helicity)")
+    ap.add_argument("--sched", type=int, default=None,
+                    help="integrand schedule (0 free warps, 1 CTA barrier per helicity, 2 = 1 + colour sum on the "
+                         "tensor cores; default 2)")
     ap.add_argument("--only-timed", action="store_true",
                     help="run only the warm-up and timed mixed-precision steps (for profiler captures)")
     return ap.parse_args()
@@ -374,10 +381,16 @@ def run_ours(args):
         "config": {"workload": "gg -> t tbar g g LO, 13 TeV, 4e6 events per VEGAS iteration, mixed FP32/FP64",
                    "process": "gg_ttgg", "events_per_step": N, "dims": dim, "bins": nb,
                    "cuts": "pT(g)>30, |eta(g)|<2.5, dR(g,g)>0.4", "pdf": "synthetic 100x50 log-bicubic grid",
-                   "l2": "inputs far below L2; a 256 MB buffer is written between timed steps"},
+                   "l2": "inputs far below L2; a 256 MB buffer is written between timed steps",
+                   "colour_sum": ("tensor cores: tcgen05.mma kind::f16, (128 events x 24) x (24 x 24) per helicity, "
+                                  "bf16x2 split of the colour flows, FP32 accumulation in TMEM")
+                   if (args.sched is None or args.sched == 2) else "FP32 FMA"},
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved_tflops / fp32_peak, "traffic": None,
+                     "frac": achieved_tflops / fp32_peak,
+                     "traffic": (DRAM_BYTES_PER_EVENT_P3_TC * N) if (args.sched is None or args.sched == 2) else None,
+                     "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of a 1e5-event ncu capture of the "
+                                      "same kernel, scaled to the launch's events (spill lines; grows with events)",
                      "kernel": "integrand_kernel<gg_ttgg, float>",
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz (nominal units and max clock)",
                      "flops_per_event_me": fl_me, "pass_fraction": pass_frac, "kernel_ms_avg": kern_avg_s * 1e3},

@@ -125,9 +125,19 @@ const char *mf_last_error(const struct mf_ctx *ctx);
 int mf_set_precision(struct mf_ctx *ctx, int precision);
 /* Integrand schedule for the heavy processes (gg -> t tbar g, gg -> t tbar g g):
  * 0 = warps run freely through the helicity sum, 1 = a CTA barrier after every
- * helicity keeps the CTA's warps on the same instructions (the default).
- * Results do not depend on it.  MF_ERR_ARG for other values. */
+ * helicity keeps the CTA's warps on the same instructions,
+ * 2 (the default) = as 1, and for g g -> t tbar g g in MF_MIXED the colour sum of every
+ * helicity (24 x 24 colour matrix, Sec. 2.2) runs on the tensor cores as one
+ * (128 events x 24) x (24 x 24) contraction per CTA (tcgen05, bf16 split of the
+ * colour-flow amplitudes, FP32 accumulation in tensor memory); elsewhere 2 acts
+ * as 1.  Schedules 0 and 1 give identical results; 2 differs from them by FP32
+ * rounding.  MF_ERR_ARG for other values. */
 int mf_set_schedule(struct mf_ctx *ctx, int sched);
+
+/* Synchronises the context's stream and reports whether a bounded device-side
+ * wait ran out since the last check (MF_ERR_TIMEOUT; the flag is cleared) or
+ * not (MF_OK).  mf_integrate makes the same check before returning. */
+int mf_device_status(struct mf_ctx *ctx);
 /* Replace the PDF grid (same shape as at creation) by a host copy. */
 int mf_set_pdf(struct mf_ctx *ctx, const double *pdf_grid_host);
 

@@ -83,6 +83,10 @@ class Context:
     def set_schedule(self, sched: int):
         _check(self.ptr, _lib.lib().mf_set_schedule(self.ptr, sched))
 
+    def device_status(self):
+        """Raises MfError(MF_ERR_TIMEOUT) if a bounded device wait ran out since the last check."""
+        _check(self.ptr, _lib.lib().mf_device_status(self.ptr))
+
     def set_pdf(self, grid_host: np.ndarray):
         """Upload a host PDF grid (same shape as at creation); asynchronous on the stream."""
         g = np.ascontiguousarray(grid_host, dtype=np.float64)

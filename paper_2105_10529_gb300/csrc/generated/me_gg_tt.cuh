@@ -4,6 +4,7 @@
 // Wavefunction/vertex calls per helicity: {'vvv': 0, 'vvvv': 0, 'ffv_row': 0, 'ffv_col': 2, 'ffv_amp': 2, 'vvv_amp': 1, 'vvvv_amp': 0, 'ffv_cur': 1}
 #pragma once
 #include "mf_helas.cuh"
+#include "mf_tc.cuh"
 namespace mf {
 struct Me_gg_tt {
   static constexpr int NEXT = 4;
@@ -14,6 +15,8 @@ struct Me_gg_tt {
   static constexpr double COLOUR_DEN = 3.0;
   static constexpr double AVG = 1.0 / 256.0;
   static constexpr double SYM = 1.0;
+  // colour sum on the tensor cores available (a dense 24 x 24 contraction)
+  static constexpr bool TC_COLOUR = false;
   // helicity-independent per-event pieces
   // per-thread slot: internal momenta, FP64-computed inverse denominators,
   // polarisation bases and spinor pieces of the event (kept in shared memory)
@@ -29,15 +32,17 @@ struct Me_gg_tt {
   // SYNC: a CTA barrier after every helicity (every thread of the CTA must call)
   // R: float or double (or Dual of them for derivatives); the momenta, masses and
   // the result use the matching FP64 scalar S = Widen<R>::type
-  template <typename R, bool SYNC = false>
+  // TC: colour sum on the tensor cores (float, SYNC, 128-thread CTAs; cta: the CTA's TcCta)
+  template <typename R, bool SYNC = false, bool TC = false>
   __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],
-                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot);
+                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot,
+                                                void* cta = nullptr);
   template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }
 };
 
-// one helicity configuration: amplitudes, colour flows and the colour sum;
+// one helicity configuration: amplitudes, colour flows and (CSUM) the colour sum;
 // out of line so that its register allocation sees only one helicity
-template <typename R>
+template <typename R, bool CSUM = true>
 __device__ __noinline__ R hel_gg_tt(const Me_gg_tt::Inv<R>& v, int ih)
 {
     constexpr int NCOL = Me_gg_tt::NCOL;
@@ -68,6 +73,7 @@ __device__ __noinline__ R hel_gg_tt(const Me_gg_tt::Inv<R>& v, int ih)
     const cx<R> a3 = vvv_amp(g0, g1, jq, k1_5, k2_6, nkk3_7);
     jadd_mi(jamp[0], a3);
     jadd_pi(jamp[1], a3);
+    if constexpr (!CSUM) return R(0);   // the caller sums the colour flows left in the slot
     cx<R> J[NCOL];
     #pragma unroll
     for (int c = 0; c < NCOL; ++c) J[c] = mkc(vget(jamp[c].r), vget(jamp[c].i));
@@ -80,9 +86,9 @@ __device__ __noinline__ R hel_gg_tt(const Me_gg_tt::Inv<R>& v, int ih)
 #undef HEL
 }
 
-template <typename R, bool SYNC>
+template <typename R, bool SYNC, bool TC>
 __device__ __noinline__ typename Widen<R>::type me2_gg_tt_impl(const typename Widen<R>::type* pflat,
-    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot)
+    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta)
 {
     using S = typename Widen<R>::type;
     constexpr int NEXT = Me_gg_tt::NEXT, NHEL = Me_gg_tt::NHEL, NGLUON = Me_gg_tt::NGLUON;
@@ -118,6 +124,7 @@ __device__ __noinline__ typename Widen<R>::type me2_gg_tt_impl(const typename Wi
     R acc = R(0);
 #pragma unroll 1
     for (int ih = 1; ih < NHEL; ih += 2) {
+        static_assert(!TC, "no tensor-core colour sum for this colour basis");
         acc += hel_gg_tt<R>(v, ih);
         if (SYNC) __syncthreads();
     }
@@ -127,10 +134,10 @@ __device__ __noinline__ typename Widen<R>::type me2_gg_tt_impl(const typename Wi
     return S(acc) / COLOUR_DEN * gk * AVG * SYM;
 }
 
-template <typename R, bool SYNC>
+template <typename R, bool SYNC, bool TC>
 __device__ typename Widen<R>::type Me_gg_tt::me2(const typename Widen<R>::type (&p)[NEXT][4],
-    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot)
+    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta)
 {
-    return me2_gg_tt_impl<R, SYNC>(&p[0][0], mt, gs, slot);
+    return me2_gg_tt_impl<R, SYNC, TC>(&p[0][0], mt, gs, slot, cta);
 }
 }  // namespace mf

@@ -4,7 +4,10 @@
 // Wavefunction/vertex calls per helicity: {'vvv': 18, 'vvvv': 4, 'ffv_row': 26, 'ffv_col': 8, 'ffv_amp': 114, 'vvv_amp': 27, 'vvvv_amp': 6, 'ffv_cur': 1}
 #pragma once
 #include "mf_helas.cuh"
+#include "mf_tc.cuh"
 namespace mf {
+// 54 C: the colour matrix times its common denominator, for the tensor-core colour sum
+static __constant__ short colour54_gg_ttgg[576] = {512, -64, -64, 8, 8, 80, -64, 8, 8, -1, -1, -10, 8, -1, 80, -10, 71, 62, -1, -10, -10, 62, 62, -28, -64, 512, 8, 80, -64, 8, 8, -64, -1, -10, 8, -1, -1, -10, -10, 62, 62, -28, 8, -1, 80, -10, 71, 62, -64, 8, 512, -64, 80, 8, 8, -1, 80, -10, 71, 62, -64, 8, 8, -1, -1, -10, -10, -1, 62, -28, -10, 62, 8, 80, -64, 512, 8, -64, -1, -10, -10, 62, 62, -28, 8, -64, -1, -10, 8, -1, -1, 8, 71, 62, 80, -10, 8, -64, 80, 8, 512, -64, -1, 8, 71, 62, 80, -10, -10, -1, 62, -28, -10, 62, -64, 8, 8, -1, -1, -10, 80, 8, 8, -64, -64, 512, -10, -1, 62, -28, -10, 62, -1, 8, 71, 62, 80, -10, 8, -64, -1, -10, 8, -1, -64, 8, 8, -1, -1, -10, 512, -64, -64, 8, 8, 80, 80, -10, 8, -1, 62, 71, -10, 62, -1, -10, -28, 62, 8, -64, -1, -10, 8, -1, -64, 512, 8, 80, -64, 8, -10, 62, -1, -10, -28, 62, 80, -10, 8, -1, 62, 71, 8, -1, 80, -10, 71, 62, -64, 8, 512, -64, 80, 8, 8, -1, -64, 8, -10, -1, 62, -28, -10, -1, 62, -10, -1, -10, -10, 62, 62, -28, 8, 80, -64, 512, 8, -64, -1, -10, 8, -64, -1, 8, 71, 62, -1, 8, -10, 80, -1, 8, 71, 62, 80, -10, 8, -64, 80, 8, 512, -64, 62, -28, -10, -1, 62, -10, 8, -1, -64, 8, -10, -1, -10, -1, 62, -28, -10, 62, 80, 8, 8, -64, -64, 512, 71, 62, -1, 8, -10, 80, -1, -10, 8, -64, -1, 8, 8, -1, -64, 8, -10, -1, 80, -10, 8, -1, 62, 71, 512, -64, -64, 8, 8, 80, 62, -10, -28, 62, -1, -10, -1, -10, 8, -64, -1, 8, -10, 62, -1, -10, -28, 62, -64, 512, 8, 80, -64, 8, -10, 80, 62, 71, 8, -1, 80, -10, 8, -1, 62, 71, 8, -1, -64, 8, -10, -1, -64, 8, 512, -64, 80, 8, -28, 62, 62, -10, -10, -1, -10, 62, -1, -10, -28, 62, -1, -10, 8, -64, -1, 8, 8, 80, -64, 512, 8, -64, 62, 71, -10, 80, -1, 8, 71, 62, -1, 8, -10, 80, 62, -28, -10, -1, 62, -10, 8, -64, 80, 8, 512, -64, -1, 8, -10, -1, -64, 8, 62, -28, -10, -1, 62, -10, 71, 62, -1, 8, -10, 80, 80, 8, 8, -64, -64, 512, -10, -1, -1, 8, 8, -64, -1, 8, -10, -1, -64, 8, -10, 80, 62, 71, 8, -1, 62, -10, -28, 62, -1, -10, 512, -64, -64, 8, 8, 80, -10, -1, -1, 8, 8, -64, 62, -10, -28, 62, -1, -10, -10, 80, 62, 71, 8, -1, -64, 512, 8, 80, -64, 8, -10, 80, 62, 71, 8, -1, -1, 8, -10, -1, -64, 8, -28, 62, 62, -10, -10, -1, -64, 8, 512, -64, 80, 8, 62, -10, -28, 62, -1, -10, -10, -1, -1, 8, 8, -64, 62, 71, -10, 80, -1, 8, 8, 80, -64, 512, 8, -64, 62, 71, -10, 80, -1, 8, -28, 62, 62, -10, -10, -1, -1, 8, -10, -1, -64, 8, 8, -64, 80, 8, 512, -64, -28, 62, 62, -10, -10, -1, 62, 71, -10, 80, -1, 8, -10, -1, -1, 8, 8, -64, 80, 8, 8, -64, -64, 512};
 struct Me_gg_ttgg {
   static constexpr int NEXT = 6;
   static constexpr int NCOL = 24;
@@ -14,6 +17,9 @@ struct Me_gg_ttgg {
   static constexpr double COLOUR_DEN = 54.0;
   static constexpr double AVG = 1.0 / 256.0;
   static constexpr double SYM = 0.5;
+  // colour sum on the tensor cores available (a dense 24 x 24 contraction)
+  static constexpr bool TC_COLOUR = true;
+  __device__ static const short* colour54() { return colour54_gg_ttgg; }
   // helicity-independent per-event pieces
   // per-thread slot: internal momenta, FP64-computed inverse denominators,
   // polarisation bases and spinor pieces of the event (kept in shared memory)
@@ -29,15 +35,17 @@ struct Me_gg_ttgg {
   // SYNC: a CTA barrier after every helicity (every thread of the CTA must call)
   // R: float or double (or Dual of them for derivatives); the momenta, masses and
   // the result use the matching FP64 scalar S = Widen<R>::type
-  template <typename R, bool SYNC = false>
+  // TC: colour sum on the tensor cores (float, SYNC, 128-thread CTAs; cta: the CTA's TcCta)
+  template <typename R, bool SYNC = false, bool TC = false>
   __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],
-                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot);
+                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot,
+                                                void* cta = nullptr);
   template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }
 };
 
-// one helicity configuration: amplitudes, colour flows and the colour sum;
+// one helicity configuration: amplitudes, colour flows and (CSUM) the colour sum;
 // out of line so that its register allocation sees only one helicity
-template <typename R>
+template <typename R, bool CSUM = true>
 __device__ __noinline__ R hel_gg_ttgg(const Me_gg_ttgg::Inv<R>& v, int ih)
 {
     constexpr int NCOL = Me_gg_ttgg::NCOL;
@@ -1160,6 +1168,7 @@ __device__ __noinline__ R hel_gg_ttgg(const Me_gg_ttgg::Inv<R>& v, int ih)
     jadd_mi(jamp[15], a159);
     jadd_mi(jamp[18], a159);
     jadd_pi(jamp[19], a159);
+    if constexpr (!CSUM) return R(0);   // the caller sums the colour flows left in the slot
     cx<R> J[NCOL];
     #pragma unroll
     for (int c = 0; c < NCOL; ++c) J[c] = mkc(vget(jamp[c].r), vget(jamp[c].i));
@@ -1216,9 +1225,9 @@ __device__ __noinline__ R hel_gg_ttgg(const Me_gg_ttgg::Inv<R>& v, int ih)
 #undef HEL
 }
 
-template <typename R, bool SYNC>
+template <typename R, bool SYNC, bool TC>
 __device__ __noinline__ typename Widen<R>::type me2_gg_ttgg_impl(const typename Widen<R>::type* pflat,
-    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot)
+    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta)
 {
     using S = typename Widen<R>::type;
     constexpr int NEXT = Me_gg_ttgg::NEXT, NHEL = Me_gg_ttgg::NHEL, NGLUON = Me_gg_ttgg::NGLUON;
@@ -1316,8 +1325,16 @@ __device__ __noinline__ typename Widen<R>::type me2_gg_ttgg_impl(const typename 
     R acc = R(0);
 #pragma unroll 1
     for (int ih = 1; ih < NHEL; ih += 2) {
-        acc += hel_gg_ttgg<R>(v, ih);
-        if (SYNC) __syncthreads();
+        if constexpr (TC) {
+            // the colour sum synchronises the CTA itself (its barriers replace SYNC's)
+            static_assert(SYNC && sizeof(R) == 4, "tensor-core colour sum: float, whole-CTA calls");
+            hel_gg_ttgg<R, false>(v, ih);
+            acc += tc_colour_sum<Me_gg_ttgg::NCOL>(static_cast<TcCta*>(cta),
+                                                  reinterpret_cast<const volatile float*>(v.jamp));
+        } else {
+            acc += hel_gg_ttgg<R>(v, ih);
+            if (SYNC) __syncthreads();
+        }
     }
     acc *= R(2);
     S gk = S(1.0);
@@ -1325,10 +1342,10 @@ __device__ __noinline__ typename Widen<R>::type me2_gg_ttgg_impl(const typename 
     return S(acc) / COLOUR_DEN * gk * AVG * SYM;
 }
 
-template <typename R, bool SYNC>
+template <typename R, bool SYNC, bool TC>
 __device__ typename Widen<R>::type Me_gg_ttgg::me2(const typename Widen<R>::type (&p)[NEXT][4],
-    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot)
+    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta)
 {
-    return me2_gg_ttgg_impl<R, SYNC>(&p[0][0], mt, gs, slot);
+    return me2_gg_ttgg_impl<R, SYNC, TC>(&p[0][0], mt, gs, slot, cta);
 }
 }  // namespace mf

@@ -8,12 +8,14 @@ struct Me_ug_ttu {
   static constexpr int NHEL = 32;
   static constexpr int NGS = 3;   // powers of g in the amplitude
   static constexpr double AVG = 1.0 / 96.0;
+  static constexpr bool TC_COLOUR = false;
   template <typename R> struct Inv { float unused; };
   template <typename R> static constexpr size_t slot_bytes() { return 0; }
   // averaged |M|^2 (S = Widen<R>::type carries the FP64 momenta and the result)
-  template <typename R, bool SYNC = false>
+  template <typename R, bool SYNC = false, bool TC = false>
   __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],
-                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void*)
+                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void*,
+                                                void* = nullptr)
   {
     using S = typename Widen<R>::type;
     // momenta of the internal lines

@@ -8,12 +8,14 @@ struct Me_uu_tt {
   static constexpr int NHEL = 16;
   static constexpr int NGS = 2;   // powers of g in the amplitude
   static constexpr double AVG = 1.0 / 36.0;
+  static constexpr bool TC_COLOUR = false;
   template <typename R> struct Inv { float unused; };
   template <typename R> static constexpr size_t slot_bytes() { return 0; }
   // averaged |M|^2 (S = Widen<R>::type carries the FP64 momenta and the result)
-  template <typename R, bool SYNC = false>
+  template <typename R, bool SYNC = false, bool TC = false>
   __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],
-                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void*)
+                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void*,
+                                                void* = nullptr)
   {
     using S = typename Widen<R>::type;
     const S q[4] = {p[0][0] + p[1][0], p[0][1] + p[1][1], p[0][2] + p[1][2], p[0][3] + p[1][3]};

@@ -178,7 +178,17 @@ int make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KPara
     kp.pdf = c->d_pdf;
     kp.partials = c->d_partials;
     kp.counters = c->d_counters;
+    kp.dev_err = c->d_err;
     return MF_OK;
+}
+
+// reads and clears the device error flag (the stream must be synchronised)
+bool take_device_error(mf_ctx* c)
+{
+    unsigned h = 0;
+    if (cudaMemcpy(&h, c->d_err, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess) return true;
+    if (h) cudaMemset(c->d_err, 0, sizeof(unsigned));
+    return h != 0;
 }
 
 int pick_blocks(mf_ctx* c, const ProcOps* ops, size_t sm, int prec, int* nblk)
@@ -259,7 +269,8 @@ int mf_create(mf_ctx** out, const mf_config* cfg, const double* pdf_grid_host, i
         cudaMalloc(&c->d_partials, (size_t)c->max_blocks * ncol * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->d_iter, (size_t)MAX_ITER * 2 * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->d_sums, ncol * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->d_counters, 2 * sizeof(unsigned long long)) != cudaSuccess)
+        cudaMalloc(&c->d_counters, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+        cudaMalloc(&c->d_err, sizeof(unsigned)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess)
         return bail(MF_ERR_CUDA);
     if (cudaMemcpy(c->d_pdf, pdf_grid_host, npdf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(MF_ERR_CUDA);
@@ -281,6 +292,7 @@ void mf_destroy(mf_ctx* c)
     cudaFree(c->d_iter);
     cudaFree(c->d_sums);
     cudaFree(c->d_counters);
+    cudaFree(c->d_err);
     cudaFree(c->d_kps);
     cudaFree(c->d_tiles);
     cudaFree(c->d_bgrids);
@@ -298,6 +310,14 @@ void mf_destroy(mf_ctx* c)
 
 const char* mf_last_error(const mf_ctx* c) { return c ? c->err.c_str() : "null context"; }
 
+int mf_device_status(mf_ctx* c)
+{
+    if (!c) return MF_ERR_ARG;
+    MF_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (take_device_error(c)) return fail(c, MF_ERR_TIMEOUT, "a bounded device wait ran out");
+    return MF_OK;
+}
+
 int mf_set_precision(mf_ctx* c, int precision)
 {
     if (!c || (precision != MF_FP64 && precision != MF_MIXED)) return MF_ERR_ARG;
@@ -307,7 +327,7 @@ int mf_set_precision(mf_ctx* c, int precision)
 
 int mf_set_schedule(mf_ctx* c, int sched)
 {
-    if (!c || sched < 0 || sched > 1) return MF_ERR_ARG;
+    if (!c || sched < 0 || sched > 2) return MF_ERR_ARG;
     c->sched = sched;
     return MF_OK;
 }
@@ -408,6 +428,7 @@ int mf_integrate(mf_ctx* c, int process, double sqrt_s, long long n_events, int 
         MF_CUDA(c, cudaMemcpyAsync(grid_host, c->d_grid, (size_t)D * (nb + 1) * sizeof(double), cudaMemcpyDeviceToHost,
                                    c->stream));
     MF_CUDA(c, cudaStreamSynchronize(c->stream));
+    if (take_device_error(c)) return fail(c, MF_ERR_TIMEOUT, "a bounded device wait ran out");
     double sw = 0.0, swi = 0.0;
     for (int k = 0; k < n_iter; ++k) {
         const double wk = 1.0 / iters[2 * k + 1];

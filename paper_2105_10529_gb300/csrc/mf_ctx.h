@@ -19,8 +19,9 @@ struct mf_ctx {
     double* d_iter = nullptr;        // [MAX_ITER][2]
     double* d_sums = nullptr;        // [2 + MAX_DIM MAX_BINS]
     unsigned long long* d_counters = nullptr;
+    unsigned* d_err = nullptr;       // raised by a device wait that ran out
     int max_blocks = 0;
-    int sched = 1;                   // integrand schedule (see mf_set_schedule)
+    int sched = 2;                   // integrand schedule (see mf_set_schedule)
     std::string err;
     // batched channels: workspace, tuned schedule and the cached CUDA graph
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture and replay (high priority)

@@ -11,7 +11,8 @@ struct ProcOps {
     size_t (*smem)(int prec, int nb, int npv);
     cudaError_t (*prepare)(size_t smem);
     cudaError_t (*occupancy)(int prec, size_t smem, int* blocks_per_sm);
-    // sched: 0 free-running warps, 1 CTA barrier between helicities (heavy processes)
+    // sched: 0 free-running warps, 1 CTA barrier between helicities (heavy processes),
+    // 2 barrier and the colour sum on the tensor cores (processes with P::TC, mixed precision)
     cudaError_t (*integrand)(int prec, bool write, int sched, const KParams& kp, int nblk, size_t smem, cudaStream_t s);
     cudaError_t (*evaluate)(int prec, const double* mom, long long n, double* me2, double mt, double gs,
                             const EwParams& ew, int nblk, cudaStream_t s);
@@ -69,13 +70,16 @@ struct IntegrandOps {
         return prec ? SmemLayout<P, float, TPB>::bytes(nb, npv) : SmemLayout<P, double, TPB>::bytes(nb, npv);
     }
     static constexpr bool HS = P::HEAVY;   // the barrier variant exists for heavy processes only
+    static constexpr bool HT = P::TC;      // and the tensor-core colour sum for P::TC processes
     template <typename R, bool W, bool S>
     static const void* fn() { return (const void*)integrand_kernel<P, R, TPB, W, S && HS>; }
+    template <bool W>
+    static const void* fn_tc() { return (const void*)integrand_kernel<P, float, TPB, W, HT, HT>; }
     static cudaError_t prepare(size_t sm)
     {
-        const void* fns[8] = { fn<double, false, false>(), fn<double, true, false>(), fn<float, false, false>(),
-                               fn<float, true, false>(), fn<double, false, true>(), fn<double, true, true>(),
-                               fn<float, false, true>(), fn<float, true, true>() };
+        const void* fns[10] = { fn<double, false, false>(), fn<double, true, false>(), fn<float, false, false>(),
+                                fn<float, true, false>(), fn<double, false, true>(), fn<double, true, true>(),
+                                fn<float, false, true>(), fn<float, true, true>(), fn_tc<false>(), fn_tc<true>() };
         for (const void* f : fns) {
             cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
@@ -90,6 +94,12 @@ struct IntegrandOps {
     template <typename R, bool W>
     static void launch(int sched, const KParams& kp, int nblk, size_t sm, cudaStream_t s)
     {
+        if constexpr (HT && sizeof(R) == 4) {
+            if (sched == 2) {
+                integrand_kernel<P, float, TPB, W, true, true><<<nblk, TPB, sm, s>>>(kp);
+                return;
+            }
+        }
         if (sched && HS) integrand_kernel<P, R, TPB, W, HS><<<nblk, TPB, sm, s>>>(kp);
         else integrand_kernel<P, R, TPB, W, false><<<nblk, TPB, sm, s>>>(kp);
     }

@@ -13,6 +13,7 @@
 #include <cstdint>
 #include "mf_device.cuh"
 #include "mf_helas.cuh"
+#include "mf_tc.cuh"
 
 namespace mf {
 
@@ -36,6 +37,7 @@ struct KParams {
     const double* pdf;      // [3][nx][nq]
     double* partials;       // [gridDim.x][2 + D nb]
     unsigned long long* counters;   // [0] events passing cuts, [1] non-finite weights zeroed
+    unsigned* dev_err;      // raised when a bounded device wait runs out (nullable)
     const uint8_t* mask_in; // frozen cut masks (nullable)
     // per-event outputs (nullable; only the inspection kernel writes them)
     double* ev_u; double* ev_x; uint8_t* ev_bins; double* ev_w; uint8_t* ev_mask; double* ev_me2; double* ev_p;
@@ -85,6 +87,7 @@ struct MeEeMumu {
 struct ProcEe {
     static constexpr int NEXT = 4, NF = 2, D = 2, NPDF = 0;
     static constexpr bool HEAVY = false;
+    static constexpr bool TC = false;
     template <typename R> static constexpr size_t slot_bytes() { return 0; }
 };
 
@@ -101,6 +104,8 @@ struct ProcTops {
     // heavy matrix elements (2 -> 3 and more with a per-thread invariant slot): queue of
     // the events that pass the cuts, one CTA-level histogram, shared-memory slots
     static constexpr bool HEAVY = NEXT >= 5 && ME::template slot_bytes<float>() > 0;
+    // the colour sum can run on the tensor cores (heavy processes with a 24-flow basis)
+    static constexpr bool TC = HEAVY && ME::TC_COLOUR;
     template <typename R> static constexpr size_t slot_bytes() { return HEAVY ? ME::template slot_bytes<R>() : 0; }
 };
 
@@ -259,7 +264,7 @@ __device__ __forceinline__ void event_tops(const KParams& kp, const double* sgri
 // Byte offsets of the kernel's dynamic shared memory:
 //   grid [D][nb+1] | histograms | value buffer |
 //   bins buffer (heavy) | event queue and counts (heavy) | block-sum scratch |
-//   per-thread slots (heavy)
+//   tensor-core colour-sum state (TC processes) | per-thread slots (heavy)
 // Light processes keep one histogram per warp (updated by bin leaders);
 // heavy ones keep one per CTA, filled by one thread per dimension in event
 // order after every round.
@@ -277,9 +282,16 @@ struct SmemLayout {
     static __host__ __device__ size_t queue_off(int nb, int npv) { return al(bbuf_off(nb, npv) + (P::HEAVY ? (size_t)TPB * D : 0)); }
     static __host__ __device__ size_t red_off(int nb, int npv)
     {
-        return al(queue_off(nb, npv) + (P::HEAVY ? sizeof(long long) * 2 * TPB + sizeof(int) * (WARPS + 2) : 0));
+        return al(queue_off(nb, npv) + (P::HEAVY ? sizeof(int) * 2 * TPB + sizeof(int) * (WARPS + 2) : 0));
     }
-    static __host__ __device__ size_t slot_off(int nb, int npv) { return al(red_off(nb, npv) + sizeof(double) * 2 * WARPS); }
+    static __host__ __device__ size_t tc_off(int nb, int npv)
+    {
+        return (red_off(nb, npv) + sizeof(double) * 2 * WARPS + 127) & ~(size_t)127;
+    }
+    static __host__ __device__ size_t slot_off(int nb, int npv)
+    {
+        return al(P::TC ? tc_off(nb, npv) + sizeof(TcCta) : red_off(nb, npv) + sizeof(double) * 2 * WARPS);
+    }
     static __host__ __device__ size_t bytes(int nb, int npv) { return slot_off(nb, npv) + (size_t)TPB * P::template slot_bytes<R>(); }
 };
 
@@ -414,10 +426,12 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
 // event on the idle lanes and discards it), which allows an optional CTA
 // barrier between helicities (SYNC) that keeps the warps on the same code.
 // The histogram is filled by one thread per dimension in queue order.
-template <class P, typename R, int TPB, bool WRITE, bool SYNC>
+template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false>
 __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char* smem_raw, long long first,
                                                 long long step, long long end, double* out)
 {
+    static_assert(!TC || (P::TC && SYNC && TPB == 128 && sizeof(R) == 4),
+                  "tensor-core colour sum: float, barrier schedule, one TMEM lane per thread");
     constexpr int D = P::D, WARPS = TPB / 32;
     using L = SmemLayout<P, R, TPB>;
     const int nb = kp.nb;
@@ -426,8 +440,9 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     double* shist = reinterpret_cast<double*>(smem_raw + L::hist_off(nb, npv));
     double* svbuf = reinterpret_cast<double*>(smem_raw + L::vbuf_off(nb, npv));
     uint8_t* sbins = smem_raw + L::bbuf_off(nb, npv);
-    long long* squeue = reinterpret_cast<long long*>(smem_raw + L::queue_off(nb, npv));
-    int* scount = reinterpret_cast<int*>(squeue + 2 * TPB);      // [0] queue length, [2 + w] warp counts
+    // queued events as r TPB + tid (event first + r step + tid)
+    int* squeue = reinterpret_cast<int*>(smem_raw + L::queue_off(nb, npv));
+    int* scount = squeue + 2 * TPB;                              // [0] queue length, [2 + w] warp counts
     double* sred = reinterpret_cast<double*>(smem_raw + L::red_off(nb, npv));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     void* slot = (void*)(smem_raw + L::slot_off(nb, npv) + (size_t)tid * P::template slot_bytes<R>());
@@ -436,6 +451,11 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     for (int i = tid; i < D * (nb + 1); i += TPB) sgrid[i] = kp.grid[i];
     for (int i = tid; i < D * nb; i += TPB) shist[i] = 0.0;
     if (tid == 0) scount[0] = 0;
+    TcCta* tc = nullptr;
+    if constexpr (TC) {
+        tc = reinterpret_cast<TcCta*>(smem_raw + L::tc_off(nb, npv));
+        tc_setup<P::Me::NCOL>(tc, P::Me::colour54(), kp.dev_err);
+    }
     __syncthreads();
 
     double sw = 0.0, sw2 = 0.0;
@@ -464,7 +484,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             const int base = scount[0];
             int woff = 0, tot = 0;
             for (int w = 0; w < WARPS; ++w) { woff += (w < warp) ? scount[2 + w] : 0; tot += scount[2 + w]; }
-            if (pass) squeue[base + woff + __popc(bal & ((1u << lane) - 1u))] = e;
+            if (pass) squeue[base + woff + __popc(bal & ((1u << lane) - 1u))] = (int)r * TPB + tid;
             __syncthreads();
             if (tid == 0) scount[0] = base + tot;
             __syncthreads();
@@ -475,11 +495,14 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             if (cnt == 0 || (!flush && cnt < TPB)) break;
             const int take = cnt < TPB ? cnt : TPB;
             const bool mine = tid < take;
-            const long long e = squeue[mine ? tid : 0];
+            const int li = squeue[mine ? tid : 0];
+            const long long e = first + (long long)(li / TPB) * step + (li % TPB);
             EventOut<D> o;
             double pm[P::NEXT][4], pref;
             kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
-            const double me = P::Me::template me2<R, SYNC>(pm, kp.mt, kp.gs, slot);
+            double me;
+            if constexpr (TC) me = P::Me::template me2<R, SYNC, true>(pm, kp.mt, kp.gs, slot, tc);
+            else me = P::Me::template me2<R, SYNC>(pm, kp.mt, kp.gs, slot);
             double w = mine ? pref * me : 0.0;
             if (!isfinite(w)) { w = 0.0; if (mine) ++nnan; }
             if constexpr (WRITE) {
@@ -504,25 +527,26 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             }
             // move the unprocessed entries to the front of the queue
             const int rest = cnt - take;
-            const long long mv = tid < rest ? squeue[take + tid] : 0;
+            const int mv = tid < rest ? squeue[take + tid] : 0;
             __syncthreads();
             if (tid < rest) squeue[tid] = mv;
             if (tid == 0) scount[0] = rest;
             __syncthreads();
         }
     }
+    if constexpr (TC) tc_teardown(tc);
     write_partials<P, TPB, 1>(kp, sw, sw2, npass, nnan, sred, shist, out);
 }
 
 // ------------------------------------------------------------------ the fused integrand kernel
 
-template <class P, typename R, int TPB, bool WRITE, bool SYNC>
+template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false>
 __global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
+    extern __shared__ __align__(128) unsigned char smem_raw[];
     const long long first = (long long)blockIdx.x * TPB, step = (long long)gridDim.x * TPB;
     double* out = kp.partials + (size_t)blockIdx.x * (2 + P::D * kp.nb);
-    if constexpr (P::HEAVY) integrand_heavy<P, R, TPB, WRITE, SYNC>(kp, smem_raw, first, step, kp.n_events, out);
+    if constexpr (P::HEAVY) integrand_heavy<P, R, TPB, WRITE, SYNC, TC>(kp, smem_raw, first, step, kp.n_events, out);
     else integrand_light<P, R, TPB, WRITE>(kp, smem_raw, first, step, kp.n_events, out);
 }
 

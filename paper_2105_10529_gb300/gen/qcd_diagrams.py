@@ -575,9 +575,16 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append(f"// {name}: {n_diag} Feynman diagrams ({len(diags)} amplitudes with the four-gluon")
     src.append(f"// colour structures counted apart), {ncol} colour flows, {1 << n_ext} helicities.")
     src.append(f"// Wavefunction/vertex calls per helicity: {em.counts}")
+    tc = ncol >= 24
     src.append("#pragma once")
     src.append('#include "mf_helas.cuh"')
+    src.append('#include "mf_tc.cuh"')
     src.append("namespace mf {")
+    if tc:
+        src.append(f"// 54 C: the colour matrix times its common denominator, for the tensor-core colour sum")
+        vals = ", ".join(str(int(CI[i][j])) for i in range(ncol) for j in range(ncol))
+        src.append(f"static __constant__ short colour54_{name}[{ncol * ncol}] = {{{vals}}};")
+        assert den == 54
     src.append(f"struct Me_{name} {{")
     src.append(f"  static constexpr int NEXT = {n_ext};")
     src.append(f"  static constexpr int NCOL = {ncol};")
@@ -587,6 +594,10 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append(f"  static constexpr double COLOUR_DEN = {den}.0;")
     src.append(f"  static constexpr double AVG = 1.0 / 256.0;")
     src.append(f"  static constexpr double SYM = {float(sym)!r};")
+    src.append(f"  // colour sum on the tensor cores available (a dense 24 x 24 contraction)")
+    src.append(f"  static constexpr bool TC_COLOUR = {'true' if tc else 'false'};")
+    if tc:
+        src.append(f"  __device__ static const short* colour54() {{ return colour54_{name}; }}")
     src.append("  // helicity-independent per-event pieces")
     n_words = 4 * len(kmasks) + 4 + max(1, len(gden)) + max(1, len(qsub)) + 6 * k + 20 + 1 + 2 * ncol
     pad = 1 if n_words % 2 == 0 else 2   # odd number of 32-bit words per slot: conflict-free in shared memory
@@ -604,29 +615,32 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("  // SYNC: a CTA barrier after every helicity (every thread of the CTA must call)")
     src.append("  // R: float or double (or Dual of them for derivatives); the momenta, masses and")
     src.append("  // the result use the matching FP64 scalar S = Widen<R>::type")
-    src.append("  template <typename R, bool SYNC = false>")
+    src.append("  // TC: colour sum on the tensor cores (float, SYNC, 128-thread CTAs; cta: the CTA's TcCta)")
+    src.append("  template <typename R, bool SYNC = false, bool TC = false>")
     src.append("  __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],")
-    src.append("                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot);")
+    src.append("                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot,")
+    src.append("                                                void* cta = nullptr);")
     src.append("  template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }")
     src.append("};")
     src.append("")
-    src.append("// one helicity configuration: amplitudes, colour flows and the colour sum;")
+    src.append("// one helicity configuration: amplitudes, colour flows and (CSUM) the colour sum;")
     src.append("// out of line so that its register allocation sees only one helicity")
-    src.append("template <typename R>")
+    src.append("template <typename R, bool CSUM = true>")
     src.append(f"__device__ __noinline__ R hel_{name}(const Me_{name}::Inv<R>& v, int ih)")
     src.append("{")
     src.append(f"    constexpr int NCOL = Me_{name}::NCOL;")
     src.append("#define HEL(i) ((ih >> (i)) & 1 ? 1 : -1)")
     for l in body:
         src.append("    " + l)
+    src.append("    if constexpr (!CSUM) return R(0);   // the caller sums the colour flows left in the slot")
     for l in cs:
         src.append("    " + l)
     src.append("#undef HEL")
     src.append("}")
     src.append("")
-    src.append("template <typename R, bool SYNC>")
+    src.append("template <typename R, bool SYNC, bool TC>")
     src.append(f"__device__ __noinline__ typename Widen<R>::type me2_{name}_impl(const typename Widen<R>::type* pflat,")
-    src.append("    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot)")
+    src.append("    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta)")
     src.append("{")
     src.append("    using S = typename Widen<R>::type;")
     src.append(f"    constexpr int NEXT = Me_{name}::NEXT, NHEL = Me_{name}::NHEL, NGLUON = Me_{name}::NGLUON;")
@@ -644,8 +658,21 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("    R acc = R(0);")
     src.append("#pragma unroll 1")
     src.append("    for (int ih = 1; ih < NHEL; ih += 2) {")
-    src.append("        acc += hel_" + name + "<R>(v, ih);")
-    src.append("        if (SYNC) __syncthreads();")
+    if tc:
+        src.append("        if constexpr (TC) {")
+        src.append("            // the colour sum synchronises the CTA itself (its barriers replace SYNC's)")
+        src.append("            static_assert(SYNC && sizeof(R) == 4, \"tensor-core colour sum: float, whole-CTA calls\");")
+        src.append("            hel_" + name + "<R, false>(v, ih);")
+        src.append(f"            acc += tc_colour_sum<Me_{name}::NCOL>(static_cast<TcCta*>(cta),")
+        src.append("                                                  reinterpret_cast<const volatile float*>(v.jamp));")
+        src.append("        } else {")
+        src.append("            acc += hel_" + name + "<R>(v, ih);")
+        src.append("            if (SYNC) __syncthreads();")
+        src.append("        }")
+    else:
+        src.append("        static_assert(!TC, \"no tensor-core colour sum for this colour basis\");")
+        src.append("        acc += hel_" + name + "<R>(v, ih);")
+        src.append("        if (SYNC) __syncthreads();")
     src.append("    }")
     src.append("    acc *= R(2);")
     src.append("    S gk = S(1.0);")
@@ -653,11 +680,11 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("    return S(acc) / COLOUR_DEN * gk * AVG * SYM;")
     src.append("}")
     src.append("")
-    src.append("template <typename R, bool SYNC>")
+    src.append("template <typename R, bool SYNC, bool TC>")
     src.append(f"__device__ typename Widen<R>::type Me_{name}::me2(const typename Widen<R>::type (&p)[NEXT][4],")
-    src.append("    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot)")
+    src.append("    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta)")
     src.append("{")
-    src.append(f"    return me2_{name}_impl<R, SYNC>(&p[0][0], mt, gs, slot);")
+    src.append(f"    return me2_{name}_impl<R, SYNC, TC>(&p[0][0], mt, gs, slot, cta);")
     src.append("}")
     src.append("}  // namespace mf")
     stats = dict(n_diag=n_diag, n_amp=len(diags), ncol=ncol, counts=dict(em.counts), colour_den=den)

@@ -86,12 +86,14 @@ def _struct(name: str, n_ext: int, n_hel: int, avg: str, k: int, prologue: List[
     s.append(f"  static constexpr int NHEL = {n_hel};")
     s.append(f"  static constexpr int NGS = {k};   // powers of g in the amplitude")
     s.append(f"  static constexpr double AVG = {avg};")
+    s.append("  static constexpr bool TC_COLOUR = false;")
     s.append("  template <typename R> struct Inv { float unused; };")
     s.append("  template <typename R> static constexpr size_t slot_bytes() { return 0; }")
     s.append("  // averaged |M|^2 (S = Widen<R>::type carries the FP64 momenta and the result)")
-    s.append("  template <typename R, bool SYNC = false>")
+    s.append("  template <typename R, bool SYNC = false, bool TC = false>")
     s.append("  __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],")
-    s.append("                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void*)")
+    s.append("                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void*,")
+    s.append("                                                void* = nullptr)")
     s.append("  {")
     s.append("    using S = typename Widen<R>::type;")
     for l in prologue:

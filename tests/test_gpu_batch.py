@@ -72,6 +72,7 @@ def test_batch_iterations_match_single_process(ctx, pdf_grid, mode):
     tot, chans = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 3, want_grids=True)
     for i, (p, n) in enumerate(zip(CHANNELS, N_EV)):
         single = Context(dataclasses.replace(PHYS, channel=PHYS.channel + i), pdf_grid, precision=1)
+        single.set_schedule(1)      # the batch sums colour flows with FP32 FMAs
         r = single.integrate(p, PHYS.sqrt_s, n, 3, want_grid=True)
         single.close()
         assert chans[i]["sigma"] == pytest.approx(r["sigma"], rel=1e-9), p

@@ -185,6 +185,9 @@ def test_bad_arguments(pdf_grid):
         ctx.vegas_pass(IN.GG_TT, 13000.0, g, 0)
     with pytest.raises(MfError):
         ctx.integrate(17, 13000.0, 1000, 2)
+    with pytest.raises(MfError):
+        ctx.set_schedule(3)
+    ctx.device_status()
     ctx.close()
 
 
@@ -195,8 +198,53 @@ def test_schedules_give_identical_sums(proc, pdf_grid):
     grid = torch.tensor(random_grid(IN.DIM[proc], seed=11), device="cuda")
     ctx = ctx_for(proc, 1, pdf_grid)
     n = 3000
+    ctx.set_schedule(0)
     a, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=4)
     ctx.set_schedule(1)
     b, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=4)
     assert torch.equal(a, b)
+    ctx.close()
+
+
+def test_tensor_core_colour_sum_event_parity(pdf_grid, opdf):
+    """Schedule 2 (g g -> t tbar g g colour sum on the tensor cores): every
+    event within the mixed-precision bound of the oracle, the same masks and
+    bins as schedule 1, and |M|^2 within 1e-6 of schedule 1 (FP32 rounding of
+    the two colour-sum orders)."""
+    proc = IN.GG_TTGG
+    phys = PHYS[proc]
+    n = 1001     # several CTAs of 128 events and a ragged last batch
+    grid = random_grid(IN.DIM[proc], seed=21)
+    g = torch.tensor(grid, device="cuda")
+    ctx = ctx_for(proc, 1, pdf_grid)
+    ctx.set_schedule(1)
+    s1, e1 = ctx.vegas_pass(proc, phys.sqrt_s, g, n, iteration=2, want_events=True)
+    ctx.set_schedule(2)
+    s2, e2 = ctx.vegas_pass(proc, phys.sqrt_s, g, n, iteration=2, want_events=True)
+    ctx.device_status()
+    assert torch.equal(e1["mask"], e2["mask"]) and torch.equal(e1["bins"], e2["bins"])
+    m1 = e1["me2"].cpu().numpy(); m2 = e2["me2"].cpu().numpy()
+    assert rel_err(m2, m1).max() < 1e-6
+    ref = oracle_events(proc, phys, opdf, grid, n, iteration=2)
+    same = e2["mask"].cpu().numpy().astype(int) == ref["mask"]
+    assert_fp_parity(rel_err(m2[same], ref["me2"][same]), 1, "me2 (tensor-core colour sum)")
+    w = e2["w"].cpu().numpy()
+    assert_fp_parity(rel_err(w[same], ref["w"][same]), 1, "w (tensor-core colour sum)")
+    assert abs(float(s2[0]) - float(s1[0])) <= 1e-6 * abs(float(s1[0]))
+    ctx.close()
+
+
+def test_tensor_core_colour_sum_integrate(pdf_grid):
+    """Iterated VEGAS with the tensor-core colour sum agrees with schedule 1
+    to rounding, and the device reports no expired wait."""
+    proc = IN.GG_TTGG
+    phys = PHYS[proc]
+    ctx = ctx_for(proc, 1, pdf_grid)
+    ctx.set_schedule(1)
+    r1 = ctx.integrate(proc, phys.sqrt_s, 20000, 2)
+    ctx.set_schedule(2)
+    r2 = ctx.integrate(proc, phys.sqrt_s, 20000, 2)
+    ctx.device_status()
+    assert r2["sigma"] == pytest.approx(r1["sigma"], rel=1e-6)
+    assert r2["n_pass"] == r1["n_pass"]
     ctx.close()
