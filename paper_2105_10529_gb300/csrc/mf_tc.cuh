@@ -110,6 +110,25 @@ __device__ __forceinline__ void tc_ld16(uint32_t taddr, uint32_t (&v)[16])
                  : "memory");
 }
 __device__ __forceinline__ void tc_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// two x16 loads and the wait in one statement, so that no use of the
+// registers can be scheduled before the data has arrived
+__device__ __forceinline__ void tc_ld16x2(uint32_t ta, uint32_t (&a)[16], uint32_t tb, uint32_t (&b)[16])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                 "%13, %14, %15}, [%32];\n\t"
+                 "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, "
+                 "%27, %28, %29, %30, %31}, [%33];\n\t"
+                 "tcgen05.wait::ld.sync.aligned;"
+                 : "=r"(a[0]), "=r"(a[1]), "=r"(a[2]), "=r"(a[3]), "=r"(a[4]), "=r"(a[5]), "=r"(a[6]), "=r"(a[7]),
+                   "=r"(a[8]), "=r"(a[9]), "=r"(a[10]), "=r"(a[11]), "=r"(a[12]), "=r"(a[13]), "=r"(a[14]),
+                   "=r"(a[15]), "=r"(b[0]), "=r"(b[1]), "=r"(b[2]), "=r"(b[3]), "=r"(b[4]), "=r"(b[5]), "=r"(b[6]),
+                   "=r"(b[7]), "=r"(b[8]), "=r"(b[9]), "=r"(b[10]), "=r"(b[11]), "=r"(b[12]), "=r"(b[13]),
+                   "=r"(b[14]), "=r"(b[15])
+                 : "r"(ta), "r"(tb)
+                 : "memory");
+}
+
 __device__ __forceinline__ void tc_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // D[tmem] (+)= A[tmem] B[smem desc]; accumulate = 0 overwrites D
@@ -206,6 +225,12 @@ __device__ __forceinline__ void tc_teardown(TcCta* tc)
     if (threadIdx.x < 32) tc_dealloc(tc->tmem);
 }
 
+// TMEM address of this thread's lane at column 0 of the CTA's allocation
+__device__ __forceinline__ uint32_t tc_lane(const TcCta* tc)
+{
+    return tc->tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
+}
+
 // Colour sum of this thread's colour-flow amplitudes (jamp: NCOL complex in
 // shared memory, re/im interleaved), scaled by 54.  Every thread of the
 // 128-thread CTA calls it for the same helicity.  tc->err is set to 1 when a
@@ -278,9 +303,7 @@ __device__ __forceinline__ float tc_colour_sum(TcCta* tc, const volatile float* 
     float acc = 0.0f;
 #pragma unroll
     for (int half = 0; half < 2; ++half) {
-        tc_ld16(lane_base + TC_D_RE + 16 * half, dre);
-        tc_ld16(lane_base + TC_D_IM + 16 * half, dim);
-        tc_wait_ld();
+        tc_ld16x2(lane_base + TC_D_RE + 16 * half, dre, lane_base + TC_D_IM + 16 * half, dim);
 #pragma unroll
         for (int c = 0; c < 16; ++c) {
             const int k = 16 * half + c;
