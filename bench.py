@@ -213,6 +213,7 @@ def run_ours(args):
     from paper_2105_10529_gb300 import inputs as IN
     from paper_2105_10529_gb300._lib import MF_FP64, MF_MIXED
     from paper_2105_10529_gb300.api import Context, process_info
+    from paper_2105_10529_gb300.shard import allreduce_pass_sums, event_range
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -249,15 +250,13 @@ def run_ours(args):
         if rc:
             raise RuntimeError(L.mf_last_error(ctx.ptr))
         if world > 1:
-            import torch.distributed as dist
-            dist.all_reduce(sums)
-            sums /= world           # every rank's pass is normalised by its own n
+            allreduce_pass_sums(sums, world)   # the sums of one pass over all ranks' events
         rc = L.mf_vegas_refine(ctx.ptr, dim, nb, phys.alpha, C.c_void_p(sums.data_ptr()), C.c_void_p(grid.data_ptr()))
         if rc:
             raise RuntimeError(L.mf_last_error(ctx.ptr))
         return sums
 
-    offset = rank * N
+    offset, _ = event_range(N, rank)
     for w in range(args.warmup):
         step(w, grid, N, offset, w)
     torch.cuda.synchronize()
