@@ -342,7 +342,7 @@ def run_ours(args):
     t0 = time.perf_counter()
     for s in range(e2e_steps):
         L.mf_set_pdf(ctx.ptr, C2.cast(pinned.data_ptr(), C2.POINTER(C2.c_double)))
-        rc = L.mf_integrate(ctx.ptr, proc, phys.sqrt_s, N, 1, C2.byref(res),
+        rc = L.mf_integrate(ctx.ptr, proc, phys.sqrt_s, None, N, 1, 0, C2.byref(res),
                             it_host.ctypes.data_as(C2.POINTER(C2.c_double)), None)
         if rc:
             raise RuntimeError(L.mf_last_error(ctx.ptr))

@@ -90,7 +90,18 @@ typedef struct mf_result {
     long long n_pass;         /* events passing the cuts                            */
     long long n_nan;          /* non-finite weights set to zero                     */
     int n_iter;
+    /* with want_grads: d sigma / d m_t [pb/GeV] and its Monte Carlo error, and
+     * d sigma / d alpha_s [pb], from one derivative pass at the final grid
+     * (fresh random numbers); 0 otherwise */
+    double dsigma_dmt, dsigma_dmt_error, dsigma_dalphas;
 } mf_result;
+
+/* Fiducial cuts on the final light partons (Sec. 1: phase space with cuts):
+ * pT > pt_min [GeV], |eta| < eta_max, Delta R between light partons > dr_min.
+ * A value <= 0 (or an infinite eta_max) disables that cut. */
+typedef struct mf_cuts {
+    double pt_min, eta_max, dr_min;
+} mf_cuts;
 
 /* Per-event outputs of mf_vegas_pass (device pointers, each nullable):
  * u, x: [n][dim] uniforms and VEGAS-mapped points; bins: [n][dim] bin
@@ -143,12 +154,16 @@ int mf_set_pdf(struct mf_ctx *ctx, const double *pdf_grid_host);
 
 /* integrate (Sec. 2.1): n_iter VEGAS iterations of n_events each on a
  * uniform starting grid, the grid refined after every iteration but the
- * last; all iterations enter the weighted mean.  n_events >= 2,
- * 1 <= n_iter <= 1000.  iter_host (nullable): [n_iter][2] estimate and
- * variance per iteration; grid_host (nullable): [dim][n_bins+1] final grid.
+ * last; all iterations enter the weighted mean.  cuts (host, nullable): the
+ * fiducial cuts of this call, NULL for those of the configuration.
+ * n_events >= 2, 1 <= n_iter <= 1000.  want_grads != 0: one more pass of
+ * n_events at the final grid gives out->dsigma_dmt (with its error) and
+ * out->dsigma_dalphas (as mf_vegas_pass_grad; MF_ERR_UNSUPPORTED where that
+ * has no kernel).  iter_host (nullable): [n_iter][2] estimate and variance
+ * per iteration; grid_host (nullable): [dim][n_bins+1] final grid.
  * Synchronises the stream. */
-int mf_integrate(struct mf_ctx *ctx, int process, double sqrt_s, long long n_events, int n_iter,
-                 mf_result *out_host, double *iter_host, double *grid_host);
+int mf_integrate(struct mf_ctx *ctx, int process, double sqrt_s, const mf_cuts *cuts, long long n_events, int n_iter,
+                 int want_grads, mf_result *out_host, double *iter_host, double *grid_host);
 
 /* One VEGAS pass over events [ev_offset, ev_offset + n_events) of Philox
  * iteration `iteration` at a caller grid (grid_dev: [dim][n_bins+1]).
@@ -208,18 +223,16 @@ int mf_set_couplings(struct mf_ctx *ctx, double mt, double alpha_s);
 int mf_vegas_pass_grad(struct mf_ctx *ctx, int process, double sqrt_s, const double *grid_dev, long long n_events,
                        long long ev_offset, unsigned int iteration, const unsigned char *mask_in_dev, double *out_dev);
 
-/* d|M|^2/dp: the derivatives of the averaged |M|^2 of mf_evaluate with
- * respect to every momentum component, the components taken as independent
- * variables.  momenta_dev [n][n_ext][4]; me2_dev [n] (nullable) receives
- * |M|^2; dme2_dp_dev [n][n_ext][4].  Top-pair processes only
- * (g g -> t tbar g g: MF_MIXED only).  Does not synchronise. */
-int mf_evaluate_grad(struct mf_ctx *ctx, int process, const double *momenta_dev, long long n, double *me2_dev,
-                     double *dme2_dp_dev);
-
 /* evaluate (Sec. 2.2): spin- and colour-averaged |M|^2 (identical-particle
- * factor included) of n phase-space points.  momenta_dev: [n][n_ext][4];
- * me2_dev: [n].  Does not synchronise. */
-int mf_evaluate(struct mf_ctx *ctx, int process, const double *momenta_dev, long long n, double *me2_dev);
+ * factor included) of n phase-space points.  momenta_dev: [n][n_ext][4]
+ * (E, px, py, pz), incoming first; me2_dev: [n] (nullable when dme2_dp_dev
+ * is given).  dme2_dp_dev (nullable): [n][n_ext][4] derivatives of |M|^2 with
+ * respect to every momentum component, the components taken as independent
+ * variables (forward mode, one tangent per component; top-pair processes
+ * only, g g -> t tbar g g in MF_MIXED only, MF_ERR_UNSUPPORTED otherwise).
+ * Device pointers, caller-owned.  Does not synchronise. */
+int mf_evaluate(struct mf_ctx *ctx, int process, const double *momenta_dev, long long n, double *me2_dev,
+                double *dme2_dp_dev);
 
 /* Batched channels: several partonic subprocesses of one hadronic process
  * (p p -> t tbar + jets), each integrated on its own VEGAS grid, the sum
@@ -242,6 +255,10 @@ int mf_evaluate(struct mf_ctx *ctx, int process, const double *momenta_dev, long
  * private stream and replayed while the channel list, sizes, sqrt_s, n_iter,
  * couplings and schedule stay the same.  The schedule changes how sums are
  * grouped (results agree to rounding), the CTA count and timing do not.
+ * cuts (host, nullable): as mf_integrate.  want_grads != 0: after the
+ * iterations one derivative pass per channel at its final grid (Philox
+ * iteration n_iter, as mf_batch_grad) fills the dsigma_* fields, the total's
+ * being the channel sums (errors in quadrature).
  * Outputs (host): per_ch_host [n_ch] results as mf_integrate;
  * total_host: sigma = sum of the channels' sigma, error = their errors in
  * quadrature, chi2_dof = 0, counts summed; grids_host (nullable)
@@ -250,19 +267,21 @@ int mf_evaluate(struct mf_ctx *ctx, int process, const double *momenta_dev, long
  * Orders itself after work already queued on the context's stream and
  * synchronises before returning. */
 int mf_integrate_batch(struct mf_ctx *ctx, int n_ch, const int *processes, const long long *n_events, double sqrt_s,
-                       int n_iter, struct mf_result *per_ch_host, struct mf_result *total_host, double *grids_host);
+                       const mf_cuts *cuts, int n_iter, int want_grads, struct mf_result *per_ch_host,
+                       struct mf_result *total_host, double *grids_host);
 
 /* d sigma_total / d m_t of a batch: one derivative pass per channel (as
  * mf_vegas_pass_grad, mixed precision) at the final grids left by the last
  * mf_integrate_batch call, which must have had the same channel list
  * (MF_ERR_ARG otherwise).  Channel i uses Philox channel cfg.channel + i and
  * iteration `iteration` (take one not used in training for an independent
- * estimate), events [0, n_events[i]).  out_host [n_ch + 1][4]: per channel,
+ * estimate), events [0, n_events[i]), cuts as mf_integrate (use the same as
+ * the integration).  out_host [n_ch + 1][4]: per channel,
  * then the sum over channels: sigma_hat, d sigma_hat/d m_t, its Monte Carlo
  * error (the channels' errors in quadrature for the sum), d sigma_hat/d
  * alpha_s.  Synchronises. */
 int mf_batch_grad(struct mf_ctx *ctx, int n_ch, const int *processes, const long long *n_events, double sqrt_s,
-                  unsigned int iteration, double *out_host);
+                  const mf_cuts *cuts, unsigned int iteration, double *out_host);
 
 /* Sets the mf_integrate_batch schedule explicitly (no counterpart in the
  * paper): mode 0/1 (one launch / split, see mf_integrate_batch), sched 0/1
@@ -281,7 +300,8 @@ int mf_set_batch_schedule(struct mf_ctx *ctx, int mode, int sched, long long til
  * {1024, 2048, 4096} x tile_light {2048, 4096} (CTAs per SM as fit) and
  * keeps the fastest for later mf_integrate_batch calls on this context.
  * choice_host [5] (nullable) receives (mode, sched, tile_heavy, tile_light,
- * ctas_per_sm).  Arguments as mf_integrate_batch.  Synchronises. */
+ * ctas_per_sm).  Arguments as mf_integrate_batch; the cuts are the
+ * configuration's.  Synchronises. */
 int mf_autotune_batch(struct mf_ctx *ctx, int n_ch, const int *processes, const long long *n_events, double sqrt_s,
                       int *choice_host);
 

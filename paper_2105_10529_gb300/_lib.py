@@ -27,7 +27,12 @@ class MfConfig(C.Structure):
 class MfResult(C.Structure):
     _fields_ = [("sigma_pb", C.c_double), ("error_pb", C.c_double), ("chi2_dof", C.c_double),
                 ("n_events_total", C.c_longlong), ("n_pass", C.c_longlong), ("n_nan", C.c_longlong),
-                ("n_iter", C.c_int)]
+                ("n_iter", C.c_int), ("dsigma_dmt", C.c_double), ("dsigma_dmt_error", C.c_double),
+                ("dsigma_dalphas", C.c_double)]
+
+
+class MfCuts(C.Structure):
+    _fields_ = [("pt_min", C.c_double), ("eta_max", C.c_double), ("dr_min", C.c_double)]
 
 
 class MfEventArrays(C.Structure):
@@ -63,19 +68,21 @@ def lib():
             "mf_set_pdf": (C.c_int, [vp, dp]),
             "mf_set_schedule": (C.c_int, [vp, C.c_int]),
             "mf_device_status": (C.c_int, [vp]),
-            "mf_integrate": (C.c_int, [vp, C.c_int, C.c_double, i64, C.c_int, C.POINTER(MfResult), dp, dp]),
+            "mf_integrate": (C.c_int, [vp, C.c_int, C.c_double, C.POINTER(MfCuts), i64, C.c_int, C.c_int,
+                                       C.POINTER(MfResult), dp, dp]),
             "mf_vegas_pass": (C.c_int, [vp, C.c_int, C.c_double, vp, i64, i64, C.c_uint, vp, vp,
                                         C.POINTER(MfEventArrays)]),
             "mf_vegas_refine": (C.c_int, [vp, C.c_int, C.c_int, C.c_double, vp, vp]),
-            "mf_evaluate": (C.c_int, [vp, C.c_int, vp, i64, vp]),
+            "mf_evaluate": (C.c_int, [vp, C.c_int, vp, i64, vp, vp]),
             "mf_set_couplings": (C.c_int, [vp, C.c_double, C.c_double]),
             "mf_vegas_pass_grad": (C.c_int, [vp, C.c_int, C.c_double, vp, i64, i64, C.c_uint, vp, vp]),
-            "mf_evaluate_grad": (C.c_int, [vp, C.c_int, vp, i64, vp, vp]),
             "mf_vegas_pass_static": (C.c_int, [C.c_int, C.POINTER(MfConfig), C.c_double, vp, C.c_int, C.c_int, C.c_int,
                                                C.c_double, C.c_double, C.c_double, vp, i64, i64, C.c_uint, vp, vp]),
-            "mf_integrate_batch": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double, C.c_int,
-                                             C.POINTER(MfResult), C.POINTER(MfResult), dp]),
-            "mf_batch_grad": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double, C.c_uint, dp]),
+            "mf_integrate_batch": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double,
+                                             C.POINTER(MfCuts), C.c_int, C.c_int, C.POINTER(MfResult),
+                                             C.POINTER(MfResult), dp]),
+            "mf_batch_grad": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double,
+                                        C.POINTER(MfCuts), C.c_uint, dp]),
             "mf_set_batch_schedule": (C.c_int, [vp, C.c_int, C.c_int, i64, i64, C.c_int]),
             "mf_autotune_batch": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double,
                                             C.POINTER(C.c_int)]),
@@ -91,5 +98,5 @@ def lib():
 def exported_symbols():
     return ["mf_default_config", "mf_process_info", "mf_create", "mf_destroy", "mf_last_error",
             "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_device_status", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
-            "mf_vegas_pass_static", "mf_set_couplings", "mf_vegas_pass_grad", "mf_evaluate_grad",
+            "mf_vegas_pass_static", "mf_set_couplings", "mf_vegas_pass_grad",
             "mf_integrate_batch", "mf_batch_grad", "mf_set_batch_schedule", "mf_autotune_batch"]

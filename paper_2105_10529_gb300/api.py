@@ -9,7 +9,7 @@ from typing import Optional
 import numpy as np
 
 from . import _lib
-from ._lib import MfConfig, MfError, MfEventArrays, MfResult
+from ._lib import MfConfig, MfCuts, MfError, MfEventArrays, MfResult
 from . import inputs as IN
 
 
@@ -30,6 +30,21 @@ def process_info(process: int):
     if rc:
         raise MfError(rc, f"process {process}")
     return n_ext.value, dim.value
+
+
+def _cuts(cuts):
+    """None, an MfCuts, or (pt_min, eta_max, dr_min) -> ctypes pointer or None."""
+    if cuts is None:
+        return None
+    if not isinstance(cuts, MfCuts):
+        cuts = MfCuts(*[float(x) for x in cuts])
+    return C.byref(cuts)
+
+
+def _result(r: MfResult) -> dict:
+    return dict(sigma=r.sigma_pb, error=r.error_pb, chi2dof=r.chi2_dof, n_events=r.n_events_total,
+                n_pass=r.n_pass, n_nan=r.n_nan, dsigma_dmt=r.dsigma_dmt, dsigma_dmt_error=r.dsigma_dmt_error,
+                dsigma_dalphas=r.dsigma_dalphas)
 
 
 def make_config(physics: Optional[IN.Physics] = None, precision: int = _lib.MF_MIXED) -> MfConfig:
@@ -93,20 +108,23 @@ class Context:
         self._pending_pdf = g
         _check(self.ptr, _lib.lib().mf_set_pdf(self.ptr, g.ctypes.data_as(C.POINTER(C.c_double))))
 
-    def integrate(self, process: int, sqrt_s: float, n_events: int, n_iter: int, want_grid: bool = False):
+    def integrate(self, process: int, sqrt_s: float, n_events: int, n_iter: int, want_grid: bool = False,
+                  want_grads: bool = False, cuts=None):
+        """mf_integrate; cuts: None (the configuration's) or (pt_min, eta_max, dr_min)."""
         res = MfResult()
         it = np.zeros((n_iter, 2))
         _, dim = process_info(process)
         grid = np.zeros((dim, self.cfg.n_bins + 1)) if want_grid else None
-        rc = _lib.lib().mf_integrate(self.ptr, process, sqrt_s, n_events, n_iter, C.byref(res),
-                                     it.ctypes.data_as(C.POINTER(C.c_double)),
+        rc = _lib.lib().mf_integrate(self.ptr, process, sqrt_s, _cuts(cuts), n_events, n_iter, int(want_grads),
+                                     C.byref(res), it.ctypes.data_as(C.POINTER(C.c_double)),
                                      grid.ctypes.data_as(C.POINTER(C.c_double)) if grid is not None else None)
-        out = dict(sigma=res.sigma_pb, error=res.error_pb, chi2dof=res.chi2_dof, n_events=res.n_events_total,
-                   n_pass=res.n_pass, n_nan=res.n_nan, per_iter=it, grid=grid, status=rc)
+        out = _result(res)
+        out.update(per_iter=it, grid=grid, status=rc)
         _check(self.ptr, rc)
         return out
 
-    def integrate_batch(self, processes, n_events, sqrt_s: float, n_iter: int, want_grids: bool = False):
+    def integrate_batch(self, processes, n_events, sqrt_s: float, n_iter: int, want_grids: bool = False,
+                        want_grads: bool = False, cuts=None):
         """Several channels in one persistent launch per iteration (mf_integrate_batch).
         Returns (total dict, list of per-channel dicts)."""
         n_ch = len(processes)
@@ -115,27 +133,25 @@ class Context:
         per = (MfResult * n_ch)()
         tot = MfResult()
         grids = np.zeros((n_ch, 18, self.cfg.n_bins + 1)) if want_grids else None
-        rc = _lib.lib().mf_integrate_batch(self.ptr, n_ch, procs, ns, sqrt_s, n_iter, per, C.byref(tot),
+        rc = _lib.lib().mf_integrate_batch(self.ptr, n_ch, procs, ns, sqrt_s, _cuts(cuts), n_iter, int(want_grads),
+                                           per, C.byref(tot),
                                            grids.ctypes.data_as(C.POINTER(C.c_double)) if grids is not None else None)
         _check(self.ptr, rc)
-
-        def d(r):
-            return dict(sigma=r.sigma_pb, error=r.error_pb, chi2dof=r.chi2_dof, n_events=r.n_events_total,
-                        n_pass=r.n_pass, n_nan=r.n_nan)
+        d = _result
         chans = [d(per[i]) for i in range(n_ch)]
         if grids is not None:
             for i, p in enumerate(processes):
                 chans[i]["grid"] = grids[i, :process_info(p)[1]].copy()
         return d(tot), chans
 
-    def batch_grad(self, processes, n_events, sqrt_s: float, iteration: int):
+    def batch_grad(self, processes, n_events, sqrt_s: float, iteration: int, cuts=None):
         """Derivative passes at the grids of the last integrate_batch: array [n_ch + 1, 4] of
         (sigma_hat, d sigma_hat/d m_t, its MC error, d sigma_hat/d alpha_s); last row = sum."""
         n_ch = len(processes)
         procs = (C.c_int * n_ch)(*[int(p) for p in processes])
         ns = (C.c_longlong * n_ch)(*[int(n) for n in n_events])
         out = np.zeros((n_ch + 1, 4))
-        _check(self.ptr, _lib.lib().mf_batch_grad(self.ptr, n_ch, procs, ns, sqrt_s, iteration,
+        _check(self.ptr, _lib.lib().mf_batch_grad(self.ptr, n_ch, procs, ns, sqrt_s, _cuts(cuts), iteration,
                                                   out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
 
@@ -208,8 +224,8 @@ class Context:
         n = mom.shape[0]
         me = torch.empty(n, dtype=torch.float64, device=mom.device)
         dme = torch.empty_like(mom)
-        rc = _lib.lib().mf_evaluate_grad(self.ptr, process, C.c_void_p(mom.data_ptr()), n, C.c_void_p(me.data_ptr()),
-                                         C.c_void_p(dme.data_ptr()))
+        rc = _lib.lib().mf_evaluate(self.ptr, process, C.c_void_p(mom.data_ptr()), n, C.c_void_p(me.data_ptr()),
+                                    C.c_void_p(dme.data_ptr()))
         _check(self.ptr, rc)
         return me, dme
 
@@ -219,7 +235,7 @@ class Context:
         mom = momenta.to(dtype=torch.float64).contiguous()
         n = mom.shape[0]
         out = torch.empty(n, dtype=torch.float64, device=mom.device)
-        rc = _lib.lib().mf_evaluate(self.ptr, process, C.c_void_p(mom.data_ptr()), n, C.c_void_p(out.data_ptr()))
+        rc = _lib.lib().mf_evaluate(self.ptr, process, C.c_void_p(mom.data_ptr()), n, C.c_void_p(out.data_ptr()), None)
         _check(self.ptr, rc)
         return out
 

@@ -195,8 +195,8 @@ struct Plan {
     size_t sm = 0;
 };
 
-int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, double sqrt_s, const Schedule& sch,
-              Plan& pl)
+int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, double sqrt_s, const mf_cuts* cuts,
+              const Schedule& sch, Plan& pl)
 {
     if (n_ch < 1 || n_ch > MAX_CH || !procs || !n_events) return mf_fail(c, MF_ERR_ARG, "batch: bad channel list");
     if (c->cfg.precision != MF_MIXED) return mf_fail(c, MF_ERR_UNSUPPORTED, "batch: only the mixed precision is built");
@@ -252,7 +252,7 @@ int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, 
         const int i = order[k];
         const ProcOps* ops = mf_proc_ops(procs[i]);
         KParams kp;
-        rc = mf_make_params(c, procs[i], ops, sqrt_s, kp);
+        rc = mf_make_params(c, procs[i], ops, sqrt_s, kp, cuts);
         if (rc) return rc;
         kp.channel = c->cfg.channel + (uint32_t)i;
         kp.n_events = n_events[i];
@@ -375,7 +375,7 @@ int set_node_priorities(mf_ctx* c, cudaGraph_t g)
     return MF_OK;
 }
 
-std::string plan_key(const mf_ctx* c, const Plan& pl, int n_iter, double sqrt_s)
+std::string plan_key(const mf_ctx* c, const Plan& pl, int n_iter, double sqrt_s, const mf_cuts* cuts)
 {
     // the side kernels' parameters are baked into the graph: couplings are part of the key
     std::string k = std::to_string(n_iter) + "|" + std::to_string(sqrt_s) + "|" + std::to_string(pl.sch.mode) + "|" +
@@ -385,6 +385,8 @@ std::string plan_key(const mf_ctx* c, const Plan& pl, int n_iter, double sqrt_s)
                     std::to_string(c->cfg.mt) + "|" + std::to_string(c->cfg.alpha_s) + "|" +
                     std::to_string((unsigned long long)c->d_tiles) + "|" + std::to_string((unsigned long long)c->d_pdf);
     for (int i = 0; i < pl.n_ch; ++i) k += "|" + std::to_string(pl.proc[i]) + ":" + std::to_string(pl.n[i]);
+    if (cuts) k += "|cuts:" + std::to_string(cuts->pt_min) + "," + std::to_string(cuts->eta_max) + "," +
+                   std::to_string(cuts->dr_min);
     return k;
 }
 
@@ -408,25 +410,78 @@ Schedule current_schedule(const mf_ctx* c)
     return Schedule{ c->b_mode, c->b_sched, c->b_bps, c->b_tile_heavy, c->b_tile_light };
 }
 
+// derivative passes of every channel at the grids in d_bgrids; out_host [n_ch + 1][4]
+int batch_grads(mf_ctx* c, int n_ch, const int* processes, const long long* n_events, double sqrt_s,
+                const mf_cuts* cuts, unsigned int iteration, double* out_host)
+{
+    // per channel: sigma_hat, d sigma_hat/d m_t, sum (dw/N)^2, d sigma_hat/d alpha_s
+    double* d_out = c->d_bsums;   // [n_ch][4]; d_bsums is free between batch calls
+    MF_BCUDA(c, cudaEventRecord(c->ev_user, c->stream));
+    MF_BCUDA(c, cudaStreamWaitEvent(c->cap_stream, c->ev_user, 0));
+    for (int i = 0; i < n_ch; ++i) {
+        const ProcOps* ops = mf_proc_ops(processes[i]);
+        const GradOpsTable* g = mf_grad_ops(processes[i]);
+        KParams kp;
+        int rc = mf_make_params(c, processes[i], ops, sqrt_s, kp, cuts);
+        if (rc) return rc;
+        kp.channel = c->cfg.channel + (uint32_t)i;
+        kp.iteration = iteration;
+        kp.n_events = n_events[i];
+        kp.ev_offset = 0;
+        kp.inv_n = 1.0 / (double)n_events[i];
+        kp.grid = c->d_bgrids + (size_t)i * MAX_DIM * (MAX_BINS + 1);
+        kp.mask_in = nullptr;
+        const long long want = (n_events[i] + 127) / 128, cap = (long long)c->n_sm * 8;
+        const int nblk = (int)(want < cap ? want : cap);
+        // the single-process partials buffer: this call is ordered after the caller's
+        // stream and synchronises before returning, so nothing else uses it meanwhile
+        double* part = c->d_partials;
+        MF_BCUDA(c, g->grad(MF_MIXED, kp, nblk, part, g->k_as, c->cfg.alpha_s, c->cap_stream));
+        finish_pass_kernel<<<1, 32, 4 * sizeof(double), c->cap_stream>>>(part, nblk, 1, 2, n_events[i], 0.0, 0, nullptr,
+                                                                        nullptr, d_out + 4 * i);
+        MF_BCUDA(c, cudaGetLastError());
+    }
+    std::vector<double> o(4 * (size_t)n_ch);
+    MF_BCUDA(c, cudaMemcpyAsync(o.data(), d_out, o.size() * sizeof(double), cudaMemcpyDeviceToHost, c->cap_stream));
+    MF_BCUDA(c, cudaStreamSynchronize(c->cap_stream));
+    double t[4] = { 0.0, 0.0, 0.0, 0.0 };
+    for (int i = 0; i < n_ch; ++i) {
+        const double n = (double)n_events[i], d = o[4 * i + 1], s2 = o[4 * i + 2];
+        double var = (n * s2 - d * d) / (n - 1.0);
+        var = var > 0.0 ? var : 0.0;
+        out_host[4 * i + 0] = o[4 * i + 0];
+        out_host[4 * i + 1] = d;
+        out_host[4 * i + 2] = std::sqrt(var);
+        out_host[4 * i + 3] = o[4 * i + 3];
+        t[0] += o[4 * i]; t[1] += d; t[2] += var; t[3] += o[4 * i + 3];
+    }
+    out_host[4 * n_ch + 0] = t[0];
+    out_host[4 * n_ch + 1] = t[1];
+    out_host[4 * n_ch + 2] = std::sqrt(t[2]);
+    out_host[4 * n_ch + 3] = t[3];
+    return MF_OK;
+}
+
 }  // namespace
 
 extern "C" {
 
 int mf_integrate_batch(mf_ctx* c, int n_ch, const int* processes, const long long* n_events, double sqrt_s,
-                       int n_iter, mf_result* per_ch_host, mf_result* total_host, double* grids_host)
+                       const mf_cuts* cuts, int n_iter, int want_grads, mf_result* per_ch_host, mf_result* total_host,
+                       double* grids_host)
 {
     if (!c) return MF_ERR_ARG;
     if (n_iter < 1 || n_iter > 1000 || !per_ch_host || !total_host || !(sqrt_s > 0.0))
         return mf_fail(c, MF_ERR_ARG, "mf_integrate_batch: bad argument");
     Plan pl;
-    int rc = make_plan(c, n_ch, processes, n_events, sqrt_s, current_schedule(c), pl);
+    int rc = make_plan(c, n_ch, processes, n_events, sqrt_s, cuts, current_schedule(c), pl);
     if (rc) return rc;
     // order against the caller's stream, then work on the private capture stream
     MF_BCUDA(c, cudaEventRecord(c->ev_user, c->stream));
     MF_BCUDA(c, cudaStreamWaitEvent(c->cap_stream, c->ev_user, 0));
     rc = reset_batch(c, pl, c->cap_stream);
     if (rc) return rc;
-    const std::string key = plan_key(c, pl, n_iter, sqrt_s);
+    const std::string key = plan_key(c, pl, n_iter, sqrt_s, cuts);
     if (!c->graph || c->graph_key != key) {
         if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_key.clear(); }
         cudaGraph_t g = nullptr;
@@ -474,6 +529,18 @@ int mf_integrate_batch(mf_ctx* c, int n_ch, const int* processes, const long lon
         var += r.error_pb * r.error_pb;
         ne += r.n_events_total; np += r.n_pass; nn += r.n_nan;
     }
+    std::vector<double> g(4 * (size_t)(n_ch + 1), 0.0);
+    if (want_grads) {
+        // derivative passes at the final grids on fresh random numbers (Philox iteration n_iter)
+        rc = batch_grads(c, n_ch, processes, n_events, sqrt_s, cuts, (unsigned)n_iter, g.data());
+        if (rc) return rc;
+    }
+    for (int i = 0; i <= n_ch; ++i) {
+        mf_result& r = i < n_ch ? per_ch_host[i] : *total_host;
+        r.dsigma_dmt = g[4 * i + 1];
+        r.dsigma_dmt_error = g[4 * i + 2];
+        r.dsigma_dalphas = g[4 * i + 3];
+    }
     total_host->sigma_pb = tot;
     total_host->error_pb = std::sqrt(var);
     total_host->chi2_dof = 0.0;
@@ -485,7 +552,7 @@ int mf_integrate_batch(mf_ctx* c, int n_ch, const int* processes, const long lon
 }
 
 int mf_batch_grad(mf_ctx* c, int n_ch, const int* processes, const long long* n_events, double sqrt_s,
-                  unsigned int iteration, double* out_host)
+                  const mf_cuts* cuts, unsigned int iteration, double* out_host)
 {
     if (!c) return MF_ERR_ARG;
     if (n_ch < 1 || n_ch > MAX_CH || !processes || !n_events || !out_host || !(sqrt_s > 0.0))
@@ -495,52 +562,7 @@ int mf_batch_grad(mf_ctx* c, int n_ch, const int* processes, const long long* n_
         return mf_fail(c, MF_ERR_ARG, "mf_batch_grad: the channel list differs from the last mf_integrate_batch");
     for (int i = 0; i < n_ch; ++i)
         if (n_events[i] < 2) return mf_fail(c, MF_ERR_ARG, "mf_batch_grad: every channel needs at least 2 events");
-    // per channel: sigma_hat, d sigma_hat/d m_t, sum (dw/N)^2, d sigma_hat/d alpha_s
-    double* d_out = c->d_bsums;   // [n_ch][4]; d_bsums is free between batch calls
-    MF_BCUDA(c, cudaEventRecord(c->ev_user, c->stream));
-    MF_BCUDA(c, cudaStreamWaitEvent(c->cap_stream, c->ev_user, 0));
-    for (int i = 0; i < n_ch; ++i) {
-        const ProcOps* ops = mf_proc_ops(processes[i]);
-        const GradOpsTable* g = mf_grad_ops(processes[i]);
-        KParams kp;
-        int rc = mf_make_params(c, processes[i], ops, sqrt_s, kp);
-        if (rc) return rc;
-        kp.channel = c->cfg.channel + (uint32_t)i;
-        kp.iteration = iteration;
-        kp.n_events = n_events[i];
-        kp.ev_offset = 0;
-        kp.inv_n = 1.0 / (double)n_events[i];
-        kp.grid = c->d_bgrids + (size_t)i * MAX_DIM * (MAX_BINS + 1);
-        kp.mask_in = nullptr;
-        const long long want = (n_events[i] + 127) / 128, cap = (long long)c->n_sm * 8;
-        const int nblk = (int)(want < cap ? want : cap);
-        // the single-process partials buffer: this call is ordered after the caller's
-        // stream and synchronises before returning, so nothing else uses it meanwhile
-        double* part = c->d_partials;
-        MF_BCUDA(c, g->grad(MF_MIXED, kp, nblk, part, g->k_as, c->cfg.alpha_s, c->cap_stream));
-        finish_pass_kernel<<<1, 32, 4 * sizeof(double), c->cap_stream>>>(part, nblk, 1, 2, n_events[i], 0.0, 0, nullptr,
-                                                                        nullptr, d_out + 4 * i);
-        MF_BCUDA(c, cudaGetLastError());
-    }
-    std::vector<double> o(4 * (size_t)n_ch);
-    MF_BCUDA(c, cudaMemcpyAsync(o.data(), d_out, o.size() * sizeof(double), cudaMemcpyDeviceToHost, c->cap_stream));
-    MF_BCUDA(c, cudaStreamSynchronize(c->cap_stream));
-    double t[4] = { 0.0, 0.0, 0.0, 0.0 };
-    for (int i = 0; i < n_ch; ++i) {
-        const double n = (double)n_events[i], d = o[4 * i + 1], s2 = o[4 * i + 2];
-        double var = (n * s2 - d * d) / (n - 1.0);
-        var = var > 0.0 ? var : 0.0;
-        out_host[4 * i + 0] = o[4 * i + 0];
-        out_host[4 * i + 1] = d;
-        out_host[4 * i + 2] = std::sqrt(var);
-        out_host[4 * i + 3] = o[4 * i + 3];
-        t[0] += o[4 * i]; t[1] += d; t[2] += var; t[3] += o[4 * i + 3];
-    }
-    out_host[4 * n_ch + 0] = t[0];
-    out_host[4 * n_ch + 1] = t[1];
-    out_host[4 * n_ch + 2] = std::sqrt(t[2]);
-    out_host[4 * n_ch + 3] = t[3];
-    return MF_OK;
+    return batch_grads(c, n_ch, processes, n_events, sqrt_s, cuts, iteration, out_host);
 }
 
 int mf_set_batch_schedule(mf_ctx* c, int mode, int sched, long long tile_heavy, long long tile_light, int ctas_per_sm)
@@ -579,7 +601,7 @@ int mf_autotune_batch(mf_ctx* c, int n_ch, const int* processes, const long long
     bool warmed[2] = { false, false };
     for (const Schedule& s : cand) {
         Plan pl;
-        rc = make_plan(c, n_ch, processes, n_events, sqrt_s, s, pl);
+        rc = make_plan(c, n_ch, processes, n_events, sqrt_s, nullptr, s, pl);
         if (rc) break;
         if (!warmed[s.mode]) {
             rc = reset_batch(c, pl, c->cap_stream);

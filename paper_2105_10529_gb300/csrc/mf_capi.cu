@@ -134,7 +134,7 @@ double factorial(int n)
 }
 
 // fills the process-independent and process-dependent kernel parameters
-int make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KParams& kp)
+int make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KParams& kp, const mf_cuts* cuts = nullptr)
 {
     const mf_config& g = c->cfg;
     const int need_flav = process == MF_UU_TT ? 3 : (process == MF_UG_TTU ? 2 : 1);
@@ -153,9 +153,12 @@ int make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KPara
         if (!(tau0 > 0.0 && tau0 < 1.0)) return fail(c, MF_ERR_ARG, "sqrt_s below the t tbar threshold");
         kp.ln_tau0 = std::log(tau0);
     }
-    kp.pt_min2 = g.pt_min > 0.0 ? g.pt_min * g.pt_min : 0.0;
-    kp.sinh_eta = g.eta_max > 0.0 ? std::sinh(g.eta_max) : 0.0;
-    kp.dr_min2 = g.dr_min > 0.0 ? g.dr_min * g.dr_min : 0.0;
+    // fiducial cuts of this call, else those of the configuration
+    const double pt_min = cuts ? cuts->pt_min : g.pt_min, eta_max = cuts ? cuts->eta_max : g.eta_max;
+    const double dr_min = cuts ? cuts->dr_min : g.dr_min;
+    kp.pt_min2 = pt_min > 0.0 ? pt_min * pt_min : 0.0;
+    kp.sinh_eta = eta_max > 0.0 && std::isfinite(eta_max) ? std::sinh(eta_max) : 0.0;
+    kp.dr_min2 = dr_min > 0.0 ? dr_min * dr_min : 0.0;
     {
         const double a = 1.0 / g.alpha_em_inv, mz2 = g.mz * g.mz;
         const double mw2 = 0.5 * mz2 + std::sqrt(0.25 * mz2 * mz2 - PI * a * mz2 / (std::sqrt(2.0) * g.gf));
@@ -205,9 +208,9 @@ int pick_blocks(mf_ctx* c, const ProcOps* ops, size_t sm, int prec, int* nblk)
 }  // namespace
 
 int mf_fail(mf_ctx* c, int code, const std::string& msg) { return fail(c, code, msg); }
-int mf_make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KParams& kp)
+int mf_make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KParams& kp, const mf_cuts* cuts)
 {
-    return make_params(c, process, ops, sqrt_s, kp);
+    return make_params(c, process, ops, sqrt_s, kp, cuts);
 }
 const ProcOps* mf_proc_ops(int process) { return proc_ops(process); }
 const GradOpsTable* mf_grad_ops(int process) { return grad_ops(process); }
@@ -387,16 +390,23 @@ int mf_vegas_refine(mf_ctx* c, int dim, int n_bins, double alpha, const double* 
     return MF_OK;
 }
 
-int mf_integrate(mf_ctx* c, int process, double sqrt_s, long long n_events, int n_iter, mf_result* out,
-                 double* iter_host, double* grid_host)
+int mf_integrate(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, long long n_events, int n_iter,
+                 int want_grads, mf_result* out, double* iter_host, double* grid_host)
 {
     if (!c) return MF_ERR_ARG;
     const ProcOps* ops = proc_ops(process);
     if (!ops) return fail(c, MF_ERR_ARG, "unknown process");
     if (!out || n_events < 2 || n_iter < 1 || n_iter > MAX_ITER || !(sqrt_s > 0.0))
         return fail(c, MF_ERR_ARG, "mf_integrate: bad argument");
+    const GradOpsTable* gops = nullptr;
+    if (want_grads) {
+        gops = grad_ops(process);
+        if (!gops) return fail(c, MF_ERR_UNSUPPORTED, "no derivative pass for this process");
+        if (c->cfg.precision == MF_FP64 && !gops->has_fp64)
+            return fail(c, MF_ERR_UNSUPPORTED, "FP64 derivative of this process not built; use MF_MIXED");
+    }
     KParams kp;
-    int rc = make_params(c, process, ops, sqrt_s, kp);
+    int rc = make_params(c, process, ops, sqrt_s, kp, cuts);
     if (rc) return rc;
     const int D = ops->D, nb = c->cfg.n_bins;
     kp.n_events = n_events;
@@ -420,6 +430,21 @@ int mf_integrate(mf_ctx* c, int process, double sqrt_s, long long n_events, int 
             c->d_partials, nblk, D, nb, n_events, c->cfg.alpha, it < n_iter - 1, c->d_grid, c->d_iter + 2 * it, nullptr);
         MF_CUDA(c, cudaGetLastError());
     }
+    if (want_grads) {
+        // one derivative pass at the final grid on fresh random numbers (Philox iteration n_iter)
+        KParams kg = kp;
+        kg.iteration = (uint32_t)n_iter;
+        kg.mask_in = nullptr;
+        const long long want = (n_events + 127) / 128, cap = (long long)c->n_sm * 8;
+        const int gblk = (int)(want < cap ? want : cap);
+        MF_CUDA(c, gops->grad(c->cfg.precision, kg, gblk, c->d_partials, gops->k_as, c->cfg.alpha_s, c->stream));
+        finish_pass_kernel<<<1, 32, 4 * sizeof(double), c->stream>>>(c->d_partials, gblk, 1, 2, n_events, 0.0, 0,
+                                                                     nullptr, nullptr, c->d_sums);
+        MF_CUDA(c, cudaGetLastError());
+    }
+    double gsum[4] = { 0.0, 0.0, 0.0, 0.0 };
+    if (want_grads)
+        MF_CUDA(c, cudaMemcpyAsync(gsum, c->d_sums, sizeof(gsum), cudaMemcpyDeviceToHost, c->stream));
     std::vector<double> iters((size_t)2 * n_iter);
     unsigned long long cnt[2];
     MF_CUDA(c, cudaMemcpyAsync(iters.data(), c->d_iter, iters.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
@@ -445,6 +470,13 @@ int mf_integrate(mf_ctx* c, int process, double sqrt_s, long long n_events, int 
     out->n_pass = (long long)cnt[0];
     out->n_nan = (long long)cnt[1];
     out->n_iter = n_iter;
+    out->dsigma_dmt = out->dsigma_dmt_error = out->dsigma_dalphas = 0.0;
+    if (want_grads) {
+        const double nd = (double)n_events, var = (nd * gsum[2] - gsum[1] * gsum[1]) / (nd - 1.0);
+        out->dsigma_dmt = gsum[1];
+        out->dsigma_dmt_error = std::sqrt(var > 0.0 ? var : 0.0);
+        out->dsigma_dalphas = gsum[3];
+    }
     if (iter_host) std::memcpy(iter_host, iters.data(), iters.size() * sizeof(double));
     if (cnt[1] > (unsigned long long)(n_events * (long long)n_iter) / 1000)
         return fail(c, MF_ERR_NUMERIC, "more than 0.1% of the event weights were not finite");
@@ -489,29 +521,26 @@ int mf_vegas_pass_grad(mf_ctx* c, int process, double sqrt_s, const double* grid
     return MF_OK;
 }
 
-int mf_evaluate_grad(mf_ctx* c, int process, const double* momenta_dev, long long n, double* me2_dev, double* dme2_dp_dev)
-{
-    if (!c) return MF_ERR_ARG;
-    const GradOpsTable* g = grad_ops(process);
-    if (!g) return fail(c, MF_ERR_UNSUPPORTED, "no derivative for this process");
-    if (c->cfg.precision == MF_FP64 && !g->has_fp64)
-        return fail(c, MF_ERR_UNSUPPORTED, "FP64 derivative of this process not built; use MF_MIXED");
-    if (n == 0) return MF_OK;
-    if (!momenta_dev || !dme2_dp_dev || n < 0) return fail(c, MF_ERR_ARG, "mf_evaluate_grad: bad argument");
-    const double gs = std::sqrt(4.0 * PI * c->cfg.alpha_s);
-    long long nb = (n + 127) / 128;
-    const long long cap = (long long)c->n_sm * 8;
-    const int nblk = (int)(nb < cap ? nb : cap);
-    MF_CUDA(c, g->evaluate_grad(c->cfg.precision, momenta_dev, n, me2_dev, dme2_dp_dev, c->cfg.mt, gs, nblk,
-                                c->stream));
-    return MF_OK;
-}
-
-int mf_evaluate(mf_ctx* c, int process, const double* momenta_dev, long long n, double* me2_dev)
+int mf_evaluate(mf_ctx* c, int process, const double* momenta_dev, long long n, double* me2_dev, double* dme2_dp_dev)
 {
     if (!c) return MF_ERR_ARG;
     const ProcOps* ops = proc_ops(process);
     if (!ops) return fail(c, MF_ERR_ARG, "unknown process");
+    if (dme2_dp_dev) {
+        // |M|^2 and its momentum derivatives in one kernel (forward mode, one tangent per component)
+        const GradOpsTable* g = grad_ops(process);
+        if (!g) return fail(c, MF_ERR_UNSUPPORTED, "no derivative for this process");
+        if (c->cfg.precision == MF_FP64 && !g->has_fp64)
+            return fail(c, MF_ERR_UNSUPPORTED, "FP64 derivative of this process not built; use MF_MIXED");
+        if (n == 0) return MF_OK;
+        if (!momenta_dev || n < 0) return fail(c, MF_ERR_ARG, "mf_evaluate: bad argument");
+        const double gs = std::sqrt(4.0 * PI * c->cfg.alpha_s);
+        const long long nb = (n + 127) / 128, cap = (long long)c->n_sm * 8;
+        const int nblk = (int)(nb < cap ? nb : cap);
+        MF_CUDA(c, g->evaluate_grad(c->cfg.precision, momenta_dev, n, me2_dev, dme2_dp_dev, c->cfg.mt, gs, nblk,
+                                    c->stream));
+        return MF_OK;
+    }
     if (n == 0) return MF_OK;
     if (!momenta_dev || !me2_dev || n < 0) return fail(c, MF_ERR_ARG, "mf_evaluate: bad argument");
     KParams kp;

@@ -45,6 +45,7 @@ struct mf_ctx {
 };
 
 int mf_fail(mf_ctx* c, int code, const std::string& msg);
-int mf_make_params(mf_ctx* c, int process, const mf::ProcOps* ops, double sqrt_s, mf::KParams& kp);
+int mf_make_params(mf_ctx* c, int process, const mf::ProcOps* ops, double sqrt_s, mf::KParams& kp,
+                   const mf_cuts* cuts = nullptr);
 const mf::ProcOps* mf_proc_ops(int process);
 const mf::GradOpsTable* mf_grad_ops(int process);

@@ -180,3 +180,10 @@ def test_batch_grad_matches_single_process(ctx, pdf_grid):
     assert g[-1, 2] == pytest.approx(np.sqrt((g[:-1, 2] ** 2).sum()), rel=1e-14)
     with pytest.raises(MfError):
         ctx.batch_grad([IN.GG_TT], [100], PHYS.sqrt_s, it)
+    # want_grads in the batch call: the same passes on Philox iteration n_iter
+    tot2, chans2 = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 2, want_grads=True)
+    g2 = ctx.batch_grad(CHANNELS, N_EV, PHYS.sqrt_s, 2)
+    for i in range(len(CHANNELS)):
+        assert chans2[i]["dsigma_dmt"] == g2[i, 1] and chans2[i]["dsigma_dalphas"] == g2[i, 3]
+        assert chans2[i]["dsigma_dmt_error"] == g2[i, 2]
+    assert tot2["dsigma_dmt"] == g2[-1, 1] and tot2["dsigma_dmt_error"] == g2[-1, 2]

@@ -173,3 +173,22 @@ def test_autograd_wrappers(pdf_grid):
     _, g = ctx.evaluate_grad(proc, P.detach())
     assert torch.allclose(P.grad, g, rtol=1e-14, atol=0)
     ctx.close()
+
+
+@pytest.mark.parametrize("proc,prec", [(IN.GG_TT, 0), (IN.UG_TTU, 1), (IN.GG_TTGG, 1)])
+def test_integrate_want_grads(proc, prec, pdf_grid):
+    """mf_integrate with want_grads: the derivative fields are the derivative
+    pass at the returned final grid on Philox iteration n_iter."""
+    phys = PHYS[proc]
+    ctx = ctx_for(proc, prec, pdf_grid)
+    n, n_iter = 4000, 2
+    r = ctx.integrate(proc, phys.sqrt_s, n, n_iter, want_grid=True, want_grads=True)
+    g = ctx.vegas_pass_grad(proc, phys.sqrt_s, torch.tensor(r["grid"], device="cuda"), n,
+                            iteration=n_iter).cpu().numpy()
+    assert r["dsigma_dmt"] == g[1] and r["dsigma_dalphas"] == g[3]
+    var = (n * g[2] - g[1] ** 2) / (n - 1)
+    assert r["dsigma_dmt_error"] == pytest.approx(math.sqrt(var), rel=1e-12)
+    assert r["dsigma_dmt"] < 0.0 < r["dsigma_dalphas"]
+    plain = ctx.integrate(proc, phys.sqrt_s, n, n_iter)
+    assert plain["sigma"] == r["sigma"] and plain["dsigma_dmt"] == 0.0
+    ctx.close()

@@ -248,3 +248,20 @@ def test_tensor_core_colour_sum_integrate(pdf_grid):
     assert r2["sigma"] == pytest.approx(r1["sigma"], rel=1e-6)
     assert r2["n_pass"] == r1["n_pass"]
     ctx.close()
+
+
+def test_cuts_argument(pdf_grid):
+    """The per-call cuts of mf_integrate: the configuration's values give the
+    same result as no argument, a looser pT cut a larger cross section, and
+    the grad pass honours them too."""
+    proc = IN.GG_TTG
+    phys = PHYS[proc]
+    ctx = ctx_for(proc, 1, pdf_grid)
+    a = ctx.integrate(proc, phys.sqrt_s, 20000, 2)
+    b = ctx.integrate(proc, phys.sqrt_s, 20000, 2, cuts=(phys.pt_min, phys.eta_max, phys.dr_min))
+    assert a["sigma"] == b["sigma"] and a["n_pass"] == b["n_pass"]
+    c = ctx.integrate(proc, phys.sqrt_s, 20000, 2, cuts=(20.0, phys.eta_max, phys.dr_min))
+    assert c["n_pass"] > a["n_pass"] and c["sigma"] > a["sigma"]
+    d = ctx.integrate(proc, phys.sqrt_s, 20000, 2, cuts=(20.0, 0.0, 0.0))     # no eta cut
+    assert d["n_pass"] > c["n_pass"]
+    ctx.close()
