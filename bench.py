@@ -171,6 +171,17 @@ def run_batch(ctx, phys, IN, n_iter):
             "timing": "host wall clock around the synchronous C-ABI call (graph launch, reductions, host results)"}
 
 
+METRIC = "gg->ttbar gg weighted events/s, FP32-mixed vs FP64 GPU at stated err; % FP peak"
+
+
+def workload_config(n_events: int, dim: int, nb: int) -> dict:
+    """The benchmark's workload, shared by both arms."""
+    return {"workload": "gg -> t tbar g g LO, 13 TeV, 4e6 events per VEGAS iteration, mixed FP32/FP64",
+            "process": "gg_ttgg", "events_per_step": n_events, "dims": dim, "bins": nb,
+            "cuts": "pT(g)>30, |eta(g)|<2.5, dR(g,g)>0.4", "pdf": "synthetic 100x50 log-bicubic grid",
+            "l2": "inputs far below L2; a 256 MB buffer is written between timed steps"}
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle as it stands, on this host's cores,
     a bounded sample of the same workload per step."""
@@ -195,13 +206,13 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = n * args.steps / dt
     line = {
-        "impl": "reference", "metric": "gg->ttbar gg weighted events/s", "value": v, "unit": "events/s",
+        "impl": "reference", "metric": METRIC, "value": v, "unit": "events/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": "gg -> t tbar g g, 13 TeV, VEGAS iterations of the FP64 CPU oracle",
-                   "events_per_step": n, "process": "gg_ttgg"},
+        "config": workload_config(args.events, IN.DIM[proc], phys.n_bins),
         "cpu_baseline": {"value": v, "unit": "events/s", "cores": cores, "kind": "oracle",
-                         "sample": f"{n} events per step x {args.steps} steps (bounded sample of the 4e6-event iteration)"},
+                         "sample": f"{n} events per step x {args.steps} steps of the FP64 oracle (bounded sample "
+                                   f"of the {args.events:.0e}-event iteration)"},
         "e2e": {"value": v, "unit": "events/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -373,17 +384,13 @@ def run_ours(args):
                "sample": f"{n_cpu} events of one iteration at the adapted grid ({dt:.1f} s)"}
 
     line = {
-        "metric": "gg->ttbar gg weighted events/s, FP32-mixed vs FP64 GPU at stated err; % FP peak",
+        "metric": METRIC,
         "value": value, "unit": "events/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": "gg -> t tbar g g LO, 13 TeV, 4e6 events per VEGAS iteration, mixed FP32/FP64",
-                   "process": "gg_ttgg", "events_per_step": N, "dims": dim, "bins": nb,
-                   "cuts": "pT(g)>30, |eta(g)|<2.5, dR(g,g)>0.4", "pdf": "synthetic 100x50 log-bicubic grid",
-                   "l2": "inputs far below L2; a 256 MB buffer is written between timed steps",
-                   "colour_sum": ("tensor cores: tcgen05.mma kind::f16, (128 events x 24) x (24 x 24) per helicity, "
-                                  "bf16x2 split of the colour flows, FP32 accumulation in TMEM")
-                   if (args.sched is None or args.sched == 2) else "FP32 FMA"},
+        "config": dict(workload_config(N, dim, nb), colour_sum=(
+            "tensor cores: tcgen05.mma kind::f16, (128 events x 24) x (24 x 24) per helicity, bf16x2 split of "
+            "the colour flows, FP32 accumulation in TMEM") if (args.sched is None or args.sched == 2) else "FP32 FMA"),
         "gpu_launches": 2 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved_tflops / fp32_peak,
