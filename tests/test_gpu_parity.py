@@ -265,3 +265,69 @@ def test_cuts_argument(pdf_grid):
     d = ctx.integrate(proc, phys.sqrt_s, 20000, 2, cuts=(20.0, 0.0, 0.0))     # no eta cut
     assert d["n_pass"] > c["n_pass"]
     ctx.close()
+
+
+def test_full_size_pass_sampled_against_oracle(pdf_grid, opdf):
+    """The benchmark's workload at full size: one mixed-precision pass of
+    4e6 g g -> t tbar g g events in the launch configuration the benchmark
+    times (default schedule, as many CTAs as fit), with per-event outputs; a
+    seeded sample of events is recomputed one by one by the oracle, and the
+    pass sums equal the sums of the per-event weights."""
+    proc = IN.GG_TTGG
+    phys = IN.Physics(seed=3)            # the benchmark's physics
+    n = 4_000_000
+    grid = random_grid(IN.DIM[proc], seed=31)
+    from paper_2105_10529_gb300.api import Context
+    ctx = Context(phys, pdf_grid, precision=1)
+    g = torch.tensor(grid, device="cuda")
+    sums, ev = ctx.vegas_pass(proc, phys.sqrt_s, g, n, iteration=5, want_events=True,
+                              fields=("bins", "w", "mask", "me2"))
+    ctx.device_status()
+    w = ev["w"].cpu().numpy()
+    # pass sums from the per-event weights (sum order differs: 1e-12)
+    assert abs(float(sums[0]) - w.sum() / n) <= 1e-12 * abs(w.sum() / n)
+    rng = np.random.default_rng(2024)
+    sample = np.concatenate([[0, n - 1], rng.choice(n, 150, replace=False)])
+    ref = oracle_events(proc, phys, opdf, grid, 0, iteration=5, events=sample)
+    assert np.array_equal(ev["bins"].cpu().numpy()[sample], ref["bins"])
+    mk = ev["mask"].cpu().numpy()[sample].astype(int)
+    for i in np.nonzero(mk != ref["mask"])[0]:
+        assert cut_margin(proc, phys, ref["plab"][i]) < 1e-9
+    same = mk == ref["mask"]
+    assert_fp_parity(rel_err(w[sample][same], ref["w"][same]), 1, "w (full size, sampled)")
+    assert_fp_parity(rel_err(ev["me2"].cpu().numpy()[sample][same], ref["me2"][same]), 1, "me2 (full size, sampled)")
+    ctx.close()
+
+
+def test_philox_counter_crosses_32_bits(pdf_grid, opdf):
+    """Event numbers across 2^32 (the counter's second word) and a large
+    iteration number: the random stream stays bit-exact."""
+    proc = IN.GG_TT
+    phys = PHYS[proc]
+    grid = random_grid(IN.DIM[proc], seed=9)
+    ctx = ctx_for(proc, 0, pdf_grid)
+    g = torch.tensor(grid, device="cuda")
+    off = (1 << 32) - 40
+    sums, ev = ctx.vegas_pass(proc, phys.sqrt_s, g, 80, ev_offset=off, iteration=70000, want_events=True,
+                              fields=("u", "x", "bins"))
+    ref = oracle_events(proc, phys, opdf, grid, 80, iteration=70000, first=off)
+    assert np.array_equal(ev["u"].cpu().numpy(), ref["u"])
+    assert np.array_equal(ev["x"].cpu().numpy(), ref["x"])
+    assert np.array_equal(ev["bins"].cpu().numpy(), ref["bins"])
+    ctx.close()
+
+
+@pytest.mark.parametrize("n_bins", [2, 64])
+def test_bin_count_extremes(n_bins, pdf_grid, opdf):
+    """The smallest and largest VEGAS grids: integrate e+ e- -> mu+ mu- and
+    compare with the oracle's integrate at the same bin count."""
+    import dataclasses
+    from paper_2105_10529_gb300.api import Context
+    proc = IN.EE_MUMU
+    phys = dataclasses.replace(PHYS[proc], n_bins=n_bins)
+    ctx = Context(phys, pdf_grid, precision=0)
+    r = ctx.integrate(proc, phys.sqrt_s, 20000, 3, want_grid=True)
+    ref = O.integrate(proc, phys, opdf, 20000, 3)
+    assert r["sigma"] == pytest.approx(ref["sigma"], rel=1e-9)
+    assert np.abs(r["grid"] - ref["grid"]).max() < 1e-9
+    ctx.close()
