@@ -88,6 +88,7 @@ struct ProcEe {
     static constexpr int NEXT = 4, NF = 2, D = 2, NPDF = 0;
     static constexpr bool HEAVY = false;
     static constexpr bool TC = false;
+    static constexpr bool STORE_KIN = false;
     template <typename R> static constexpr size_t slot_bytes() { return 0; }
 };
 
@@ -106,6 +107,9 @@ struct ProcTops {
     static constexpr bool HEAVY = NEXT >= 5 && ME::template slot_bytes<float>() > 0;
     // the colour sum can run on the tensor cores (heavy processes with a 24-flow basis)
     static constexpr bool TC = HEAVY && ME::TC_COLOUR;
+    // the kinematics of queued events are kept in shared memory (where it fits: 2 -> 3),
+    // so that the matrix-element batch does not recompute them in FP64
+    static constexpr bool STORE_KIN = HEAVY && NEXT == 5;
     template <typename R> static constexpr size_t slot_bytes() { return HEAVY ? ME::template slot_bytes<R>() : 0; }
 };
 
@@ -280,10 +284,19 @@ struct SmemLayout {
     static __host__ __device__ size_t vbuf_off(int nb, int npv) { return al(hist_off(nb, npv) + sizeof(double) * NHIST * D * nb); }
     static __host__ __device__ size_t bbuf_off(int nb, int npv) { return al(vbuf_off(nb, npv) + sizeof(double) * TPB); }
     static __host__ __device__ size_t queue_off(int nb, int npv) { return al(bbuf_off(nb, npv) + (P::HEAVY ? (size_t)TPB * D : 0)); }
-    static __host__ __device__ size_t red_off(int nb, int npv)
+    // ring of 2 TPB queued events; with KIN their momenta [NEXT 4][2 TPB],
+    // weight factors [2 TPB] and bins [2 TPB][D] follow
+    static constexpr int CAP = 2 * TPB;
+    static constexpr bool KIN = P::STORE_KIN && sizeof(R) == 4;   // mixed precision only
+    static __host__ __device__ size_t kin_off(int nb, int npv)
     {
-        return al(queue_off(nb, npv) + (P::HEAVY ? sizeof(int) * 2 * TPB + sizeof(int) * (WARPS + 2) : 0));
+        return al(queue_off(nb, npv) + (P::HEAVY ? sizeof(int) * CAP + sizeof(int) * (WARPS + 2) : 0));
     }
+    static __host__ __device__ size_t kin_bytes()
+    {
+        return KIN ? sizeof(double) * (P::NEXT * 4 + 1) * CAP + (size_t)D * CAP : 0;
+    }
+    static __host__ __device__ size_t red_off(int nb, int npv) { return al(kin_off(nb, npv) + kin_bytes()); }
     static __host__ __device__ size_t tc_off(int nb, int npv)
     {
         return (red_off(nb, npv) + sizeof(double) * 2 * WARPS + 127) & ~(size_t)127;
@@ -440,17 +453,22 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     double* shist = reinterpret_cast<double*>(smem_raw + L::hist_off(nb, npv));
     double* svbuf = reinterpret_cast<double*>(smem_raw + L::vbuf_off(nb, npv));
     uint8_t* sbins = smem_raw + L::bbuf_off(nb, npv);
-    // queued events as r TPB + tid (event first + r step + tid)
+    // ring of queued events as r TPB + tid (event first + r step + tid)
+    constexpr int CAP = L::CAP;
     int* squeue = reinterpret_cast<int*>(smem_raw + L::queue_off(nb, npv));
-    int* scount = squeue + 2 * TPB;                              // [0] queue length, [2 + w] warp counts
+    int* scount = squeue + CAP;                                  // [0] length, [1] head, [2 + w] warp counts
+    double* kpm = reinterpret_cast<double*>(smem_raw + L::kin_off(nb, npv));   // [NEXT 4][CAP]
+    double* kpref = kpm + P::NEXT * 4 * CAP;                                      // [CAP]
+    uint8_t* kbins = reinterpret_cast<uint8_t*>(kpref + CAP);                     // [D][CAP]
     double* sred = reinterpret_cast<double*>(smem_raw + L::red_off(nb, npv));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     void* slot = (void*)(smem_raw + L::slot_off(nb, npv) + (size_t)tid * P::template slot_bytes<R>());
     const double* gpdf = kp.pdf;
+    constexpr bool REUSE = L::KIN && !WRITE;   // batches read the stored kinematics
 
     for (int i = tid; i < D * (nb + 1); i += TPB) sgrid[i] = kp.grid[i];
     for (int i = tid; i < D * nb; i += TPB) shist[i] = 0.0;
-    if (tid == 0) scount[0] = 0;
+    if (tid == 0) { scount[0] = 0; scount[1] = 0; }
     TcCta* tc = nullptr;
     if constexpr (TC) {
         tc = reinterpret_cast<TcCta*>(smem_raw + L::tc_off(nb, npv));
@@ -467,9 +485,9 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             // kinematics of this round's events; queue the ones that pass, in event order
             const long long e = first + r * step + tid;
             int pass = 0;
+            EventOut<D> o;
+            double pm[P::NEXT][4], pref = 0.0;
             if (e < end) {
-                EventOut<D> o;
-                double pm[P::NEXT][4], pref;
                 kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
                 pass = o.mask ? 1 : 0;
                 npass += pass;
@@ -481,25 +499,48 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             const unsigned bal = __ballot_sync(0xffffffffu, pass);
             if (lane == 0) scount[2 + warp] = __popc(bal);
             __syncthreads();
-            const int base = scount[0];
+            const int cnt = scount[0], head = scount[1];
             int woff = 0, tot = 0;
             for (int w = 0; w < WARPS; ++w) { woff += (w < warp) ? scount[2 + w] : 0; tot += scount[2 + w]; }
-            if (pass) squeue[base + woff + __popc(bal & ((1u << lane) - 1u))] = (int)r * TPB + tid;
+            if (pass) {
+                const int pos = (head + cnt + woff + __popc(bal & ((1u << lane) - 1u))) % CAP;
+                squeue[pos] = (int)r * TPB + tid;
+                if constexpr (REUSE) {
+#pragma unroll
+                    for (int i = 0; i < P::NEXT; ++i)
+#pragma unroll
+                        for (int c = 0; c < 4; ++c) kpm[(i * 4 + c) * CAP + pos] = pm[i][c];
+                    kpref[pos] = pref;
+#pragma unroll
+                    for (int d = 0; d < D; ++d) kbins[d * CAP + pos] = o.bins[d];
+                }
+            }
             __syncthreads();
-            if (tid == 0) scount[0] = base + tot;
+            if (tid == 0) scount[0] = cnt + tot;
             __syncthreads();
         }
         // evaluate full batches (and, at the end, whatever is left)
         for (;;) {
-            const int cnt = scount[0];
+            const int cnt = scount[0], head = scount[1];
             if (cnt == 0 || (!flush && cnt < TPB)) break;
             const int take = cnt < TPB ? cnt : TPB;
             const bool mine = tid < take;
-            const int li = squeue[mine ? tid : 0];
+            const int pos = (head + (mine ? tid : 0)) % CAP;
+            const int li = squeue[pos];
             const long long e = first + (long long)(li / TPB) * step + (li % TPB);
             EventOut<D> o;
             double pm[P::NEXT][4], pref;
-            kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
+            if constexpr (REUSE) {
+#pragma unroll
+                for (int i = 0; i < P::NEXT; ++i)
+#pragma unroll
+                    for (int c = 0; c < 4; ++c) pm[i][c] = kpm[(i * 4 + c) * CAP + pos];
+                pref = kpref[pos];
+#pragma unroll
+                for (int d = 0; d < D; ++d) o.bins[d] = kbins[d * CAP + pos];
+            } else {
+                kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
+            }
             double me;
             if constexpr (TC) me = P::Me::template me2<R, SYNC, true>(pm, kp.mt, kp.gs, slot, tc);
             else me = P::Me::template me2<R, SYNC>(pm, kp.mt, kp.gs, slot);
@@ -525,12 +566,9 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
                 const uint8_t* b = sbins + tid * TPB;
                 for (int t = 0; t < take; ++t) h[b[t]] += svbuf[t];
             }
-            // move the unprocessed entries to the front of the queue
-            const int rest = cnt - take;
-            const int mv = tid < rest ? squeue[take + tid] : 0;
+            // the batch's entries leave the ring
             __syncthreads();
-            if (tid < rest) squeue[tid] = mv;
-            if (tid == 0) scount[0] = rest;
+            if (tid == 0) { scount[1] = (head + take) % CAP; scount[0] = cnt - take; }
             __syncthreads();
         }
     }

@@ -331,3 +331,19 @@ def test_bin_count_extremes(n_bins, pdf_grid, opdf):
     assert r["sigma"] == pytest.approx(ref["sigma"], rel=1e-9)
     assert np.abs(r["grid"] - ref["grid"]).max() < 1e-9
     ctx.close()
+
+
+def test_stored_kinematics_match_recompute(pdf_grid):
+    """g g -> t tbar g in mixed precision keeps the kinematics of queued events
+    in shared memory; the pass that recomputes them (the one with per-event
+    outputs) gives bit-identical sums."""
+    proc = IN.GG_TTG
+    phys = PHYS[proc]
+    grid = torch.tensor(random_grid(IN.DIM[proc], seed=41), device="cuda")
+    ctx = ctx_for(proc, 1, pdf_grid)
+    for sched in (0, 1):
+        ctx.set_schedule(sched)
+        a, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, 20011, iteration=6)
+        b, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, 20011, iteration=6, want_events=True, fields=("w",))
+        assert torch.equal(a, b), sched
+    ctx.close()
