@@ -179,6 +179,7 @@ int make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KPara
     kp.pdfg.lq1 = std::log(c->q2_max);
     kp.pdfg.hq = (kp.pdfg.lq1 - kp.pdfg.lq0) / (double)(c->nq - 1);
     kp.pdf = c->d_pdf;
+    kp.ln_muf2_fixed = std::log(g.mt * g.mt);
     kp.partials = c->d_partials;
     kp.counters = c->d_counters;
     kp.dev_err = c->d_err;

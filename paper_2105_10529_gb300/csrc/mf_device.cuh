@@ -85,13 +85,16 @@ __device__ __forceinline__ double vegas_map(const double* grid, int nb, const do
 // ------------------------------------------------------------------ a3: parton map
 // tau = tau0^x0, x1 = tau^v, x2 = tau^(1-v), J = tau |ln tau| |ln tau0|.
 // S: double, or Dual<double> when tau0 carries a derivative.
+// lx1, lx2 receive ln x1 = v ln tau and ln x2 = (1 - v) ln tau (for the PDF lookups).
 template <typename S>
-__device__ __forceinline__ void parton_map(double x0, double v, S ln_tau0, S& x1, S& x2, S& jac)
+__device__ __forceinline__ void parton_map(double x0, double v, S ln_tau0, S& x1, S& x2, S& jac, S& lx1, S& lx2)
 {
     const S lt = x0 * ln_tau0;
     const S tau = exp(lt);
-    x1 = exp(v * lt);
-    x2 = exp((1.0 - v) * lt);
+    lx1 = v * lt;
+    lx2 = (1.0 - v) * lt;
+    x1 = exp(lx1);
+    x2 = exp(lx2);
     jac = tau * (-lt) * (-ln_tau0);
 }
 
@@ -206,12 +209,11 @@ __device__ __forceinline__ S pdf_row(const double* g, const PdfGeom& G, int i, i
     return hermite3(f0, f1, d0, d1, G.hx, t);
 }
 
-// x f(x, Q^2); S is double or Dual<double> (the cells are chosen from the values)
+// x f(x, Q^2) from lx = ln x and lq = ln Q^2; S is double or Dual<double>
+// (the cells are chosen from the values)
 template <typename S>
-__device__ __forceinline__ S pdf_xf(const double* g, const PdfGeom& G, S x, S q2)
+__device__ __forceinline__ S pdf_xf_log(const double* g, const PdfGeom& G, S lx, S lq)
 {
-    const S lx = log(x);
-    S lq = log(q2);
     if (val(lq) < G.lq0) lq = S(G.lq0);
     if (val(lq) > G.lq1) lq = S(G.lq1);
     int i = (int)floor((val(lx) - G.lx0) / G.hx);

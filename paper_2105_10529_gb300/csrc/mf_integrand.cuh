@@ -35,6 +35,7 @@ struct KParams {
     PdfGeom pdfg;
     const double* grid;     // [D][nb+1]
     const double* pdf;      // [3][nx][nq]
+    double ln_muf2_fixed;   // ln m_t^2, the fixed 2 -> 2 factorisation scale
     double* partials;       // [gridDim.x][2 + D nb]
     unsigned long long* counters;   // [0] events passing cuts, [1] non-finite weights zeroed
     unsigned* dev_err;      // raised when a bounded device wait runs out (nullable)
@@ -187,8 +188,8 @@ __device__ __forceinline__ void kinematics_tops_t(const KParams& kp, const doubl
     S ln_tau0;
     if constexpr (is_dual<S>::value) ln_tau0 = log(4.0 * mt * mt / kp.S);
     else ln_tau0 = kp.ln_tau0;
-    S x1, x2, jp;
-    parton_map(o.x[0], o.x[1], ln_tau0, x1, x2, jp);
+    S x1, x2, jp, lx1, lx2;
+    parton_map(o.x[0], o.x[1], ln_tau0, x1, x2, jp, lx1, lx2);
     const S shat = x1 * x2 * kp.S;
     const S rs = sqrt(shat);
     S m[NF];
@@ -220,10 +221,11 @@ __device__ __forceinline__ void kinematics_tops_t(const KParams& kp, const doubl
     }
     o.mask = kp.mask_in ? (int)kp.mask_in[ev - kp.ev_offset] : cuts_tops<P>(kp, pl);
     if (val(wps) <= 0.0) o.mask = 0;
-    // factorisation scale: m_t for 2 -> 2, H_T / 2 otherwise
-    S muf2;
-    if (NF == 2) {
-        muf2 = mt * mt;
+    // factorisation scale: m_t for 2 -> 2, H_T / 2 otherwise (as ln mu_F^2)
+    S lq;
+    if constexpr (NF == 2) {
+        if constexpr (is_dual<S>::value) lq = log(mt * mt);
+        else lq = kp.ln_muf2_fixed;
     } else {
         S ht = S(0.0);
 #pragma unroll
@@ -231,11 +233,11 @@ __device__ __forceinline__ void kinematics_tops_t(const KParams& kp, const doubl
             const S mi = (i < 4) ? mt : S(0.0);
             ht = ht + sqrt(mi * mi + p[i][1] * p[i][1] + p[i][2] * p[i][2]);
         }
-        muf2 = 0.25 * ht * ht;
+        lq = log(0.25 * ht * ht);
     }
     const int npv = kp.pdfg.nx * kp.pdfg.nq;
-    const S f1 = pdf_xf(spdf + P::FLAV1 * npv, kp.pdfg, x1, muf2) / x1;
-    const S f2 = pdf_xf(spdf + P::FLAV2 * npv, kp.pdfg, x2, muf2) / x2;
+    const S f1 = pdf_xf_log(spdf + P::FLAV1 * npv, kp.pdfg, lx1, lq) / x1;
+    const S f2 = pdf_xf_log(spdf + P::FLAV2 * npv, kp.pdfg, lx2, lq) / x2;
     pref = f1 * f2 / (2.0 * shat) * wps * jp * jv * GEV2_TO_PB;
     o.me2 = 0.0;
     o.w = 0.0;

@@ -155,6 +155,7 @@ extern "C" int mf_vegas_pass_static(int process, const mf_config* cfg, double sq
     kp.pdfg.lq1 = std::log(q2_max);
     kp.pdfg.hq = (kp.pdfg.lq1 - kp.pdfg.lq0) / (double)(nq - 1);
     kp.pdf = pdf_dev;
+    kp.ln_muf2_fixed = std::log(cfg->mt * cfg->mt);
     kp.grid = grid_dev;
     // layout of the shared scratch: [0..1] counters, then the partial sums
     kp.counters = reinterpret_cast<unsigned long long*>(scratch);
