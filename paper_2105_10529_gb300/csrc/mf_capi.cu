@@ -178,6 +178,8 @@ int make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KPara
     kp.pdfg.lq0 = std::log(c->q2_min);
     kp.pdfg.lq1 = std::log(c->q2_max);
     kp.pdfg.hq = (kp.pdfg.lq1 - kp.pdfg.lq0) / (double)(c->nq - 1);
+    kp.pdfg.ihx = 1.0 / kp.pdfg.hx;
+    kp.pdfg.ihq = 1.0 / kp.pdfg.hq;
     kp.pdf = c->d_pdf;
     kp.ln_muf2_fixed = std::log(g.mt * g.mt);
     kp.partials = c->d_partials;

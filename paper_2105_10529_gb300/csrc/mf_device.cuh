@@ -90,11 +90,11 @@ template <typename S>
 __device__ __forceinline__ void parton_map(double x0, double v, S ln_tau0, S& x1, S& x2, S& jac, S& lx1, S& lx2)
 {
     const S lt = x0 * ln_tau0;
-    const S tau = exp(lt);
     lx1 = v * lt;
     lx2 = (1.0 - v) * lt;
     x1 = exp(lx1);
     x2 = exp(lx2);
+    const S tau = x1 * x2;     // = exp(lt) up to rounding
     jac = tau * (-lt) * (-ln_tau0);
 }
 
@@ -122,9 +122,10 @@ __device__ __forceinline__ S rambo(S rs, const S (&m)[N], const double* u, S (&p
         Q0 += q[i][0]; Q1 += q[i][1]; Q2 += q[i][2]; Q3 += q[i][3];
     }
     const double M = sqrt(Q0 * Q0 - Q1 * Q1 - Q2 * Q2 - Q3 * Q3);
-    const double b1 = -Q1 / M, b2 = -Q2 / M, b3 = -Q3 / M;
-    const S x = rs / M;
-    const double g = Q0 / M, a = 1.0 / (1.0 + g);
+    const double iM = 1.0 / M;
+    const double b1 = -Q1 * iM, b2 = -Q2 * iM, b3 = -Q3 * iM;
+    const S x = rs * iM;
+    const double g = Q0 * iM, a = 1.0 / (1.0 + g);
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         const double bq = b1 * q[i][1] + b2 * q[i][2] + b3 * q[i][3];
@@ -172,11 +173,12 @@ __device__ __forceinline__ S rambo(S rs, const S (&m)[N], const double* u, S (&p
     for (int i = 0; i < N; ++i) {
         const S ka = xi * p[i][0];
         const S e = sqrt(m[i] * m[i] + ka * ka);
+        const S ie = 1.0 / e;
         p[i][1] = p[i][1] * xi; p[i][2] = p[i][2] * xi; p[i][3] = p[i][3] * xi;
         p[i][0] = e;
         sk = sk + ka;
-        sk2e = sk2e + ka * ka / e;
-        prod = prod * (ka / e);
+        sk2e = sk2e + ka * ka * ie;
+        prod = prod * (ka * ie);
     }
     S pw = S(1.0);
     const S r = sk / rs;
@@ -189,14 +191,18 @@ __device__ __forceinline__ S rambo(S rs, const S (&m)[N], const double* u, S (&p
 // Cubic Hermite in ln x along the Q^2 rows j-1..j+2, then in ln Q^2 over those
 // row values; node derivatives are central differences inside, one-sided at
 // the ends (LHAPDF6 log-bicubic, EPJC 75 (2015) 132).  g: [ix][iq] x f values.
-struct PdfGeom { int nx, nq; double lx0, hx, lq0, lq1, hq; };
+// ihx = 1 / hx, ihq = 1 / hq
+struct PdfGeom { int nx, nq; double lx0, hx, lq0, lq1, hq, ihx, ihq; };
 
+// cubic Hermite on one cell, the end tangents given as their change over the
+// cell (h d): central or one-sided differences of the node values need no
+// division by the spacing
 template <typename A, typename B>
-__device__ __forceinline__ B hermite3(A f0, A f1, A d0, A d1, double h, B t)
+__device__ __forceinline__ B hermite3h(A f0, A f1, A hd0, A hd1, B t)
 {
     const B t2 = t * t, t3 = t2 * t;
-    return (2.0 * t3 - 3.0 * t2 + 1.0) * f0 + (t3 - 2.0 * t2 + t) * (h * d0) + (-2.0 * t3 + 3.0 * t2) * f1
-           + (t3 - t2) * (h * d1);
+    return (2.0 * t3 - 3.0 * t2 + 1.0) * f0 + (t3 - 2.0 * t2 + t) * hd0 + (-2.0 * t3 + 3.0 * t2) * f1 +
+           (t3 - t2) * hd1;
 }
 
 template <typename S>
@@ -204,9 +210,9 @@ __device__ __forceinline__ S pdf_row(const double* g, const PdfGeom& G, int i, i
 {
     const int nq = G.nq, nx = G.nx;
     const double f0 = g[i * nq + jr], f1 = g[(i + 1) * nq + jr];
-    const double d0 = i == 0 ? (f1 - f0) / G.hx : (f1 - g[(i - 1) * nq + jr]) / (2.0 * G.hx);
-    const double d1 = (i + 1 == nx - 1) ? (f1 - f0) / G.hx : (g[(i + 2) * nq + jr] - f0) / (2.0 * G.hx);
-    return hermite3(f0, f1, d0, d1, G.hx, t);
+    const double hd0 = i == 0 ? f1 - f0 : 0.5 * (f1 - g[(i - 1) * nq + jr]);
+    const double hd1 = (i + 1 == nx - 1) ? f1 - f0 : 0.5 * (g[(i + 2) * nq + jr] - f0);
+    return hermite3h(f0, f1, hd0, hd1, t);
 }
 
 // x f(x, Q^2) from lx = ln x and lq = ln Q^2; S is double or Dual<double>
@@ -216,19 +222,19 @@ __device__ __forceinline__ S pdf_xf_log(const double* g, const PdfGeom& G, S lx,
 {
     if (val(lq) < G.lq0) lq = S(G.lq0);
     if (val(lq) > G.lq1) lq = S(G.lq1);
-    int i = (int)floor((val(lx) - G.lx0) / G.hx);
+    int i = (int)floor((val(lx) - G.lx0) * G.ihx);
     i = i < 0 ? 0 : (i > G.nx - 2 ? G.nx - 2 : i);
-    int j = (int)floor((val(lq) - G.lq0) / G.hq);
+    int j = (int)floor((val(lq) - G.lq0) * G.ihq);
     j = j < 0 ? 0 : (j > G.nq - 2 ? G.nq - 2 : j);
-    const S t = (lx - (G.lx0 + i * G.hx)) / G.hx;
-    const S s = (lq - (G.lq0 + j * G.hq)) / G.hq;
+    const S t = (lx - (G.lx0 + i * G.hx)) * G.ihx;
+    const S s = (lq - (G.lq0 + j * G.hq)) * G.ihq;
     const S r1 = pdf_row(g, G, i, j, t);
     const S r2 = pdf_row(g, G, i, j + 1, t);
     const S r0 = j > 0 ? pdf_row(g, G, i, j - 1, t) : S(0.0);
     const S r3 = (j + 2 < G.nq) ? pdf_row(g, G, i, j + 2, t) : S(0.0);
-    const S dj = j == 0 ? (r2 - r1) / G.hq : (r2 - r0) / (2.0 * G.hq);
-    const S dj1 = (j + 1 == G.nq - 1) ? (r2 - r1) / G.hq : (r3 - r1) / (2.0 * G.hq);
-    return hermite3(r1, r2, dj, dj1, G.hq, s);
+    const S hdj = j == 0 ? r2 - r1 : 0.5 * (r2 - r0);
+    const S hdj1 = (j + 1 == G.nq - 1) ? r2 - r1 : 0.5 * (r3 - r1);
+    return hermite3h(r1, r2, hdj, hdj1, s);
 }
 
 }  // namespace mf

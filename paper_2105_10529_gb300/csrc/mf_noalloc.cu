@@ -154,6 +154,8 @@ extern "C" int mf_vegas_pass_static(int process, const mf_config* cfg, double sq
     kp.pdfg.lq0 = std::log(q2_min);
     kp.pdfg.lq1 = std::log(q2_max);
     kp.pdfg.hq = (kp.pdfg.lq1 - kp.pdfg.lq0) / (double)(nq - 1);
+    kp.pdfg.ihx = 1.0 / kp.pdfg.hx;
+    kp.pdfg.ihq = 1.0 / kp.pdfg.hq;
     kp.pdf = pdf_dev;
     kp.ln_muf2_fixed = std::log(cfg->mt * cfg->mt);
     kp.grid = grid_dev;
