@@ -151,23 +151,28 @@ template <class P>
 __device__ __forceinline__ int cuts_tops(const KParams& kp, const double (&pl)[P::NEXT][4])
 {
     int ok = 1;
+    const double sh2 = kp.sinh_eta * kp.sinh_eta;
 #pragma unroll
     for (int j = 0; j < P::NLIGHT; ++j) {
         const double* q = pl[4 + j];
         const double pt2 = q[1] * q[1] + q[2] * q[2];
         if (kp.pt_min2 > 0.0) ok &= (pt2 > kp.pt_min2);
-        if (kp.sinh_eta > 0.0) ok &= (fabs(q[3]) < sqrt(pt2) * kp.sinh_eta);
+        // |eta| < eta_max  <=>  p_z^2 < p_T^2 sinh^2(eta_max)
+        if (kp.sinh_eta > 0.0) ok &= (q[3] * q[3] < pt2 * sh2);
     }
     if (P::NLIGHT == 2 && kp.dr_min2 > 0.0 && ok) {
         const double* a = pl[4];
         const double* b = pl[P::NLIGHT == 2 ? 5 : 4];
-        const double pta = sqrt(a[1] * a[1] + a[2] * a[2]), ptb = sqrt(b[1] * b[1] + b[2] * b[2]);
-        const double ea = asinh(a[3] / pta), eb = asinh(b[3] / ptb);
-        double dphi = atan2(a[2], a[1]) - atan2(b[2], b[1]);
-        const double pi = 3.14159265358979323846;
-        if (dphi > pi) dphi -= 2.0 * pi;
-        if (dphi < -pi) dphi += 2.0 * pi;
-        ok &= ((ea - eb) * (ea - eb) + dphi * dphi > kp.dr_min2);
+        const double pta2 = a[1] * a[1] + a[2] * a[2], ptb2 = b[1] * b[1] + b[2] * b[2];
+        const double pa = sqrt(pta2 + a[3] * a[3]), pb = sqrt(ptb2 + b[3] * b[3]);
+        // eta = ln((|p| + p_z) / p_T), so eta_a - eta_b in one logarithm (|p| + p_z formed
+        // as p_T^2 / (|p| - p_z) for p_z < 0, without cancellation); the azimuthal
+        // difference in (-pi, pi] from one atan2 of the transverse cross and dot products
+        const double ua = a[3] >= 0.0 ? pa + a[3] : pta2 / (pa - a[3]);
+        const double ub = b[3] >= 0.0 ? pb + b[3] : ptb2 / (pb - b[3]);
+        const double deta = log(ua * sqrt(ptb2) / (ub * sqrt(pta2)));
+        const double dphi = atan2(a[1] * b[2] - a[2] * b[1], a[1] * b[1] + a[2] * b[2]);
+        ok &= (deta * deta + dphi * dphi > kp.dr_min2);
     }
     return ok;
 }
