@@ -33,9 +33,9 @@ SM_MAX_MHZ = 2070.0
 FP64_PEAK_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) per event of the mixed g g -> t tbar g g integrand with the
 # tensor-core colour sum, from the ncu capture summarised in
-# profiles/integrand_gg_ttgg_mixed_100k_ncu.txt (283.6 MB over 100k events; the traffic,
+# profiles/integrand_gg_ttgg_mixed_100k_ncu.txt (224.2 MB over 100k events; the traffic,
 # evicted local-memory lines, grows with the number of events)
-DRAM_BYTES_PER_EVENT_P3_TC = 2836.3
+DRAM_BYTES_PER_EVENT_P3_TC = 2242.2
 
 
 def parse():
