@@ -185,6 +185,9 @@ int make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KPara
     kp.partials = c->d_partials;
     kp.counters = c->d_counters;
     kp.dev_err = c->d_err;
+    kp.kin = c->d_kin;
+    kp.kin_bins = c->d_kin_bins;
+    kp.kin_ctas = c->kin_ctas;
     return MF_OK;
 }
 
@@ -278,6 +281,11 @@ int mf_create(mf_ctx** out, const mf_config* cfg, const double* pdf_grid_host, i
         cudaMalloc(&c->d_counters, 2 * sizeof(unsigned long long)) != cudaSuccess ||
         cudaMalloc(&c->d_err, sizeof(unsigned)) != cudaSuccess || cudaMemset(c->d_err, 0, sizeof(unsigned)) != cudaSuccess)
         return bail(MF_ERR_CUDA);
+    // global kinematics store of the heavy integrand: up to 4 CTAs per SM of 256 queued events
+    c->kin_ctas = 4 * c->n_sm;
+    if (cudaMalloc(&c->d_kin, (size_t)c->kin_ctas * (KIN_NEXT_MAX * 4 + 1) * 256 * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_kin_bins, (size_t)c->kin_ctas * MAX_DIM * 256) != cudaSuccess)
+        return bail(MF_ERR_CUDA);
     if (cudaMemcpy(c->d_pdf, pdf_grid_host, npdf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(MF_ERR_CUDA);
     for (int p : { MF_EE_MUMU, MF_GG_TT, MF_GG_TTG, MF_GG_TTGG, MF_UU_TT, MF_UG_TTU }) {
@@ -299,6 +307,8 @@ void mf_destroy(mf_ctx* c)
     cudaFree(c->d_sums);
     cudaFree(c->d_counters);
     cudaFree(c->d_err);
+    cudaFree(c->d_kin);
+    cudaFree(c->d_kin_bins);
     cudaFree(c->d_kps);
     cudaFree(c->d_tiles);
     cudaFree(c->d_bgrids);

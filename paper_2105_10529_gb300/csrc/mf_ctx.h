@@ -20,6 +20,9 @@ struct mf_ctx {
     double* d_sums = nullptr;        // [2 + MAX_DIM MAX_BINS]
     unsigned long long* d_counters = nullptr;
     unsigned* d_err = nullptr;       // raised by a device wait that ran out
+    double* d_kin = nullptr;         // kinematics of queued events (heavy integrand), per CTA
+    uint8_t* d_kin_bins = nullptr;
+    int kin_ctas = 0;
     int max_blocks = 0;
     int sched = 2;                   // integrand schedule (see mf_set_schedule)
     std::string err;

@@ -19,6 +19,7 @@ namespace mf {
 
 constexpr double GEV2_TO_PB = 0.3893793721e9;   // (hbar c)^2 in pb GeV^2
 constexpr int MAX_DIM = 18;
+constexpr int KIN_NEXT_MAX = 6;      // largest process (2 -> 4) for the global kinematics store
 constexpr int MAX_BINS = 64;
 
 struct EwParams { double e2, sw2, cw2, mz, wz; };
@@ -39,6 +40,12 @@ struct KParams {
     double* partials;       // [gridDim.x][2 + D nb]
     unsigned long long* counters;   // [0] events passing cuts, [1] non-finite weights zeroed
     unsigned* dev_err;      // raised when a bounded device wait runs out (nullable)
+    // global storage of queued events' kinematics for heavy processes whose shared
+    // memory has no room for it (nullable): per CTA (blockIdx.x < kin_ctas)
+    // [NEXT_MAX 4 + 1][256] doubles and [D_MAX][256] bins
+    double* kin;
+    uint8_t* kin_bins;
+    int kin_ctas;
     const uint8_t* mask_in; // frozen cut masks (nullable)
     // per-event outputs (nullable; only the inspection kernel writes them)
     double* ev_u; double* ev_x; uint8_t* ev_bins; double* ev_w; uint8_t* ev_mask; double* ev_me2; double* ev_p;
@@ -471,7 +478,19 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     void* slot = (void*)(smem_raw + L::slot_off(nb, npv) + (size_t)tid * P::template slot_bytes<R>());
     const double* gpdf = kp.pdf;
-    constexpr bool REUSE = L::KIN && !WRITE;   // batches read the stored kinematics
+    // batches read back the kinematics stored when the events were queued: in shared
+    // memory (L::KIN), else for mixed precision in this CTA's global region (kp.kin)
+    constexpr bool GKIN = !L::KIN && !WRITE && sizeof(R) == 4 && CAP == 256;
+    constexpr bool MAYREUSE = (L::KIN && !WRITE) || GKIN;
+    bool reuse = L::KIN && !WRITE;
+    if constexpr (GKIN) {
+        if (kp.kin != nullptr && (int)blockIdx.x < kp.kin_ctas) {
+            reuse = true;
+            kpm = kp.kin + (size_t)blockIdx.x * (KIN_NEXT_MAX * 4 + 1) * 256;
+            kpref = kpm + P::NEXT * 4 * CAP;
+            kbins = kp.kin_bins + (size_t)blockIdx.x * MAX_DIM * 256;
+        }
+    }
 
     for (int i = tid; i < D * (nb + 1); i += TPB) sgrid[i] = kp.grid[i];
     for (int i = tid; i < D * nb; i += TPB) shist[i] = 0.0;
@@ -512,7 +531,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             if (pass) {
                 const int pos = (head + cnt + woff + __popc(bal & ((1u << lane) - 1u))) % CAP;
                 squeue[pos] = (int)r * TPB + tid;
-                if constexpr (REUSE) {
+                if (MAYREUSE && reuse) {
 #pragma unroll
                     for (int i = 0; i < P::NEXT; ++i)
 #pragma unroll
@@ -537,7 +556,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             const long long e = first + (long long)(li / TPB) * step + (li % TPB);
             EventOut<D> o;
             double pm[P::NEXT][4], pref;
-            if constexpr (REUSE) {
+            if (MAYREUSE && reuse) {
 #pragma unroll
                 for (int i = 0; i < P::NEXT; ++i)
 #pragma unroll

@@ -333,17 +333,25 @@ def test_bin_count_extremes(n_bins, pdf_grid, opdf):
     ctx.close()
 
 
-def test_stored_kinematics_match_recompute(pdf_grid):
-    """g g -> t tbar g in mixed precision keeps the kinematics of queued events
-    in shared memory; the pass that recomputes them (the one with per-event
+@pytest.mark.parametrize("proc", [IN.GG_TTG, IN.GG_TTGG])
+def test_stored_kinematics_match_recompute(proc, pdf_grid):
+    """In mixed precision the heavy integrand keeps the kinematics of queued
+    events (shared memory for g g -> t tbar g, a global per-CTA store for
+    g g -> t tbar g g); the pass that recomputes them (the one with per-event
     outputs) gives bit-identical sums."""
-    proc = IN.GG_TTG
     phys = PHYS[proc]
     grid = torch.tensor(random_grid(IN.DIM[proc], seed=41), device="cuda")
     ctx = ctx_for(proc, 1, pdf_grid)
-    for sched in (0, 1):
+    for sched in (0, 1, 2):
         ctx.set_schedule(sched)
-        a, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, 20011, iteration=6)
-        b, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, 20011, iteration=6, want_events=True, fields=("w",))
-        assert torch.equal(a, b), sched
+        n = 20011 if proc == IN.GG_TTG else 3001
+        a, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=6)
+        b, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=6, want_events=True, fields=("w",))
+        if sched < 2:
+            assert torch.equal(a, b), sched
+        else:
+            # the tensor-core kernels with and without per-event outputs are compiled
+            # apart; their FP32 rounding may differ in the last bits
+            rel = float((a - b).abs().max() / a.abs().max())
+            assert rel < 1e-9, rel
     ctx.close()
