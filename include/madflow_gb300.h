@@ -10,8 +10,8 @@
  * the squared matrix element of Sec. 2.2 and accumulates histograms, with
  * every step on the GPU and results kept in GPU memory (Sec. 3.1).  The two
  * user calls are therefore
- *     integrate(process, sqrt_s, n_events, n_iter) -> sigma, error
- *     evaluate(process, momenta)                   -> |M|^2
+ *     integrate(process, sqrt_s, cuts, n_events, n_iter) -> sigma, error
+ *     evaluate(process, momenta)                         -> |M|^2
  * plus the single-pass and inspection calls that the tests and the
  * benchmark use.
  *
@@ -128,7 +128,9 @@ int mf_process_info(int process, int *n_ext, int *dim);
  * on ln-uniform nodes, layout [flavour][ix][iq] with flavours 0 gluon,
  * 1 u, 2 ubar (n_flav >= 1; the gluon processes read flavour 0), copied to
  * the device.  stream: a cudaStream_t or NULL.  On success *out owns device
- * buffers sized for every built process; release with mf_destroy. */
+ * buffers sized for every built process (about 80 MB on a 152-SM GPU:
+ * per-CTA partial sums and the heavy integrand's kinematics store; the
+ * batch calls add their own on first use); release with mf_destroy. */
 int mf_create(struct mf_ctx **out, const mf_config *cfg, const double *pdf_grid_host, int n_flav, int nx, int nq,
               double x_min, double q2_min, double q2_max, void *stream);
 void mf_destroy(struct mf_ctx *ctx);
@@ -177,7 +179,8 @@ int mf_vegas_pass(struct mf_ctx *ctx, int process, double sqrt_s, const double *
 
 /* VEGAS grid refinement (Sec. 1, the VegasFlow integrator; Lepage 1978)
  * from the sums of one or more passes: sums_dev [2 + dim n_bins] as
- * written by mf_vegas_pass (several ranks' sums may be averaged first),
+ * written by mf_vegas_pass (several ranks' sums may be combined first: the
+ * refinement depends only on the shape of each dimension's histogram),
  * grid_dev [dim][n_bins+1] updated in place; a dimension whose histogram is
  * all zero keeps its edges.  dim <= 18, 2 <= n_bins <= 64, alpha >= 0.
  * Does not synchronise. */
