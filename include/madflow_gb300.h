@@ -151,6 +151,14 @@ int mf_set_schedule(struct mf_ctx *ctx, int sched);
  * wait ran out since the last check (MF_ERR_TIMEOUT; the flag is cleared) or
  * not (MF_OK).  mf_integrate makes the same check before returning. */
 int mf_device_status(struct mf_ctx *ctx);
+
+/* Self-test of the bounded device waits (no counterpart in the paper): one
+ * warp waits on an mbarrier phase that nothing completes, with at most
+ * `iterations` (1 .. 2^20) polls, the same bounded wait the tensor-core colour
+ * sum uses; the expiry raises the context's device error flag.  Returns what
+ * mf_device_status then returns: MF_ERR_TIMEOUT when the mechanism works.
+ * The context stays usable.  Synchronises. */
+int mf_selftest_wait(struct mf_ctx *ctx, unsigned int iterations);
 /* Replace the PDF grid (same shape as at creation) by a host copy. */
 int mf_set_pdf(struct mf_ctx *ctx, const double *pdf_grid_host);
 

@@ -102,6 +102,10 @@ class Context:
         """Raises MfError(MF_ERR_TIMEOUT) if a bounded device wait ran out since the last check."""
         _check(self.ptr, _lib.lib().mf_device_status(self.ptr))
 
+    def selftest_wait(self, iterations: int = 4096) -> int:
+        """Status of the bounded-wait self-test (MF_ERR_TIMEOUT = 3 when the expiry is detected)."""
+        return _lib.lib().mf_selftest_wait(self.ptr, iterations)
+
     def set_pdf(self, grid_host: np.ndarray):
         """Upload a host PDF grid (same shape as at creation); asynchronous on the stream."""
         g = np.ascontiguousarray(grid_host, dtype=np.float64)

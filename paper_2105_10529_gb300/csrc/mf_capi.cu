@@ -75,6 +75,17 @@ __global__ void finish_pass_kernel(const double* partials, int nblk, int D, int 
     if (refine && (int)threadIdx.x < D) refine_dim(sh + 2 + threadIdx.x * nb, grid + threadIdx.x * (nb + 1), nb, alpha);
 }
 
+// Self-test of the bounded device waits: every thread waits on an mbarrier
+// phase that nothing completes, with the given iteration limit, and the
+// expiry raises the context's error flag (as in the tensor-core colour sum).
+__global__ void wait_selftest_kernel(unsigned* err, unsigned limit)
+{
+    __shared__ unsigned long long mbar;
+    if (threadIdx.x == 0) mbar_init(&mbar, 1);
+    __syncthreads();
+    if (!mbar_wait(&mbar, 0, limit)) atomicExch(err, 1u);
+}
+
 // refinement from already reduced pass sums [2 + D nb]
 __global__ void refine_kernel(const double* sums, int D, int nb, double alpha, double* grid)
 {
@@ -325,6 +336,14 @@ void mf_destroy(mf_ctx* c)
 }
 
 const char* mf_last_error(const mf_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int mf_selftest_wait(mf_ctx* c, unsigned int iterations)
+{
+    if (!c || iterations < 1 || iterations > (1u << 20)) return MF_ERR_ARG;
+    wait_selftest_kernel<<<1, 32, 0, c->stream>>>(c->d_err, iterations);
+    MF_CUDA(c, cudaGetLastError());
+    return mf_device_status(c);
+}
 
 int mf_device_status(mf_ctx* c)
 {

@@ -153,10 +153,10 @@ __device__ __forceinline__ void mbar_init(unsigned long long* mbar, unsigned cou
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(mbar)), "r"(count) : "memory");
 }
 // bounded wait for the completion of the phase with the given parity; false on expiry
-__device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(unsigned long long* mbar, uint32_t parity, unsigned limit = TC_WAIT_LIMIT)
 {
     const uint32_t a = smem_u32(mbar);
-    for (unsigned it = 0; it < TC_WAIT_LIMIT; ++it) {
+    for (unsigned it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\t"
                      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"

@@ -355,3 +355,19 @@ def test_stored_kinematics_match_recompute(proc, pdf_grid):
             rel = float((a - b).abs().max() / a.abs().max())
             assert rel < 1e-9, rel
     ctx.close()
+
+
+def test_bounded_wait_expiry_is_reported(pdf_grid):
+    """A device wait on an mbarrier phase that nothing completes runs out after
+    its iteration limit; the host sees MF_ERR_TIMEOUT once, and the context
+    keeps working."""
+    proc = IN.GG_TT
+    phys = PHYS[proc]
+    ctx = ctx_for(proc, 1, pdf_grid)
+    assert ctx.selftest_wait(2048) == 3
+    ctx.device_status()                      # the flag was cleared
+    g = torch.tensor(random_grid(IN.DIM[proc], seed=3), device="cuda")
+    s, _ = ctx.vegas_pass(proc, phys.sqrt_s, g, 1000)
+    ctx.device_status()
+    assert float(s[0]) > 0.0
+    ctx.close()
