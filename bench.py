@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--sched", type=int, default=None,
                     help="integrand schedule (0 free warps, 1 CTA barrier per helicity, 2 = 1 + colour sum on the "
                          "tensor cores; default 2)")
+    ap.add_argument("--hsplit", type=int, default=None,
+                    help="threads per event of the heavy integrand (1 or 2; default 1)")
     ap.add_argument("--only-timed", action="store_true",
                     help="run only the warm-up and timed mixed-precision steps (for profiler captures)")
     ap.add_argument("--process", default="gg_ttgg",
@@ -164,7 +166,8 @@ def run_batch(ctx, phys, IN, n_iter):
             "sequential_events_per_s": ev / t_seq, "speedup_vs_sequential": t_seq / t_batch,
             "sequential_s_by_channel": {names[p]: t for p, t in zip(procs, t_ch)},
             "schedule": {"mode": ["one launch", "split"][choice[0]], "helicity_barrier": choice[1],
-                         "tile_heavy": choice[2], "tile_light": choice[3], "ctas_per_sm": choice[4]},
+                         "tile_heavy": choice[2], "tile_light": choice[3], "ctas_per_sm": choice[4],
+                         "helicity_split": choice[5]},
             "events_per_s_by_mode": {"one launch": ev / per_mode[0][0], "split": ev / per_mode[1][0]},
             "sigma_pb": tot["sigma"], "error_pb": tot["error"],
             "channels": {names[p]: {"sigma_pb": c["sigma"], "error_pb": c["error"], "chi2dof": c["chi2dof"],
@@ -247,6 +250,8 @@ def run_ours(args):
     ctx = Context(phys, pdf, precision=MF_MIXED, stream=stream)
     if args.sched is not None:
         ctx.set_schedule(args.sched)
+    if args.hsplit is not None:
+        ctx.set_helicity_split(args.hsplit)
     dev = torch.device("cuda", local)
     grid = torch.linspace(0, 1, nb + 1, dtype=torch.float64, device=dev).repeat(dim, 1).contiguous()
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # > L2 (129 MB)
@@ -396,12 +401,14 @@ def run_ours(args):
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": dict(workload_config(N, dim, nb), colour_sum=(
             "tensor cores: tcgen05.mma kind::f16, (128 events x 24) x (24 x 24) per helicity, bf16x2 split of "
-            "the colour flows, FP32 accumulation in TMEM") if (args.sched is None or args.sched == 2) else "FP32 FMA"),
+            "the colour flows, FP32 accumulation in TMEM") if (args.sched is None or args.sched == 2) else "FP32 FMA",
+                      helicity_split=args.hsplit or 1),
         # per step: the integrand and the end-of-pass reduction (mf_vegas_pass) and the refinement
         "gpu_launches": 3 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved_tflops / fp32_peak,
-                     "traffic": (DRAM_BYTES_PER_EVENT_P3_TC * N) if (args.sched is None or args.sched == 2) else None,
+                     "traffic": (DRAM_BYTES_PER_EVENT_P3_TC * N)
+                     if (args.sched is None or args.sched == 2) and (args.hsplit or 1) == 1 else None,
                      "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of a 1e5-event ncu capture of the "
                                       "same kernel, scaled to the launch's events (spill lines; grows with events)",
                      "kernel": "integrand_kernel<gg_ttgg, float>",

@@ -146,6 +146,17 @@ int mf_set_precision(struct mf_ctx *ctx, int precision);
  * as 1.  Schedules 0 and 1 give identical results; 2 differs from them by FP32
  * rounding.  MF_ERR_ARG for other values. */
 int mf_set_schedule(struct mf_ctx *ctx, int sched);
+/* Helicity split of the heavy integrand (no counterpart in the paper, whose
+ * kernels give one thread per event): parts = 1 (the default), one thread
+ * sums every helicity of its event; parts = 2, two adjacent threads share an
+ * event, each summing every other one of the helicities the matrix element
+ * evaluates (Sec. 2.2's helicity sum split in two), and the pair adds its
+ * halves; a CTA then holds half as many events at a time.  Applies to
+ * g g -> t tbar g and g g -> t tbar g g in MF_MIXED under schedules 1 and 2,
+ * in mf_vegas_pass without per-event outputs and in mf_integrate; elsewhere
+ * it acts as 1.  Results differ from parts = 1 by FP32 rounding only.
+ * MF_ERR_ARG for other values. */
+int mf_set_helicity_split(struct mf_ctx *ctx, int parts);
 
 /* Synchronises the context's stream and reports whether a bounded device-side
  * wait ran out since the last check (MF_ERR_TIMEOUT; the flag is cleared) or
@@ -300,18 +311,21 @@ int mf_batch_grad(struct mf_ctx *ctx, int n_ch, const int *processes, const long
  * tile_heavy and tile_light in [32, 2^26] events per work item for the
  * g g -> t tbar g(g) channels and for the others (in the split mode, the
  * other channels' kernels get one CTA per tile_light events), ctas_per_sm in
- * [0, 16] (0 = as many as fit; values above that are clamped).  MF_ERR_ARG
- * outside these ranges.  Defaults: 0, 1, 4096, 4096, 0. */
+ * [0, 16] (0 = as many as fit; values above that are clamped), hsplit 1 or 2
+ * (helicity split of the g g -> t tbar g(g) channels as mf_set_helicity_split;
+ * 2 needs sched 1).  MF_ERR_ARG outside these ranges.  Defaults: 0, 1, 4096,
+ * 4096, 0, 1. */
 int mf_set_batch_schedule(struct mf_ctx *ctx, int mode, int sched, long long tile_heavy, long long tile_light,
-                          int ctas_per_sm);
+                          int ctas_per_sm, int hsplit);
 
 /* Launch-schedule autotuner for mf_integrate_batch (no counterpart in the
  * paper).  Times one iteration of the given channels and sizes at uniform
- * grids for every mode {0, 1} x helicity barrier {0, 1} x tile_heavy
- * {1024, 2048, 4096} x tile_light {2048, 4096} (CTAs per SM as fit) and
- * keeps the fastest for later mf_integrate_batch calls on this context.
- * choice_host [5] (nullable) receives (mode, sched, tile_heavy, tile_light,
- * ctas_per_sm).  Arguments as mf_integrate_batch; the cuts are the
+ * grids for every mode {0, 1} x (helicity barrier, helicity split) {(0, 1),
+ * (1, 1), (1, 2)} x tile_heavy {1024, 2048, 4096} x tile_light {2048, 4096}
+ * (CTAs per SM as fit; 36 candidates) and keeps the fastest for later
+ * mf_integrate_batch calls on this context.  choice_host [6] (nullable)
+ * receives (mode, sched, tile_heavy, tile_light, ctas_per_sm, hsplit), the
+ * arguments of mf_set_batch_schedule.  Arguments as mf_integrate_batch; the cuts are the
  * configuration's.  Synchronises. */
 int mf_autotune_batch(struct mf_ctx *ctx, int n_ch, const int *processes, const long long *n_events, double sqrt_s,
                       int *choice_host);

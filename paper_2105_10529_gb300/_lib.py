@@ -67,6 +67,7 @@ def lib():
             "mf_set_precision": (C.c_int, [vp, C.c_int]),
             "mf_set_pdf": (C.c_int, [vp, dp]),
             "mf_set_schedule": (C.c_int, [vp, C.c_int]),
+            "mf_set_helicity_split": (C.c_int, [vp, C.c_int]),
             "mf_device_status": (C.c_int, [vp]),
             "mf_selftest_wait": (C.c_int, [vp, C.c_uint]),
             "mf_integrate": (C.c_int, [vp, C.c_int, C.c_double, C.POINTER(MfCuts), i64, C.c_int, C.c_int,
@@ -84,7 +85,7 @@ def lib():
                                              C.POINTER(MfResult), dp]),
             "mf_batch_grad": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double,
                                         C.POINTER(MfCuts), C.c_uint, dp]),
-            "mf_set_batch_schedule": (C.c_int, [vp, C.c_int, C.c_int, i64, i64, C.c_int]),
+            "mf_set_batch_schedule": (C.c_int, [vp, C.c_int, C.c_int, i64, i64, C.c_int, C.c_int]),
             "mf_autotune_batch": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double,
                                             C.POINTER(C.c_int)]),
         }
@@ -98,6 +99,6 @@ def lib():
 
 def exported_symbols():
     return ["mf_default_config", "mf_process_info", "mf_create", "mf_destroy", "mf_last_error",
-            "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_device_status", "mf_selftest_wait", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
+            "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_set_helicity_split", "mf_device_status", "mf_selftest_wait", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
             "mf_vegas_pass_static", "mf_set_couplings", "mf_vegas_pass_grad",
             "mf_integrate_batch", "mf_batch_grad", "mf_set_batch_schedule", "mf_autotune_batch"]

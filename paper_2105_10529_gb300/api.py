@@ -98,6 +98,10 @@ class Context:
     def set_schedule(self, sched: int):
         _check(self.ptr, _lib.lib().mf_set_schedule(self.ptr, sched))
 
+    def set_helicity_split(self, parts: int):
+        """Threads per event of the heavy integrand (1 or 2), as mf_set_helicity_split."""
+        _check(self.ptr, _lib.lib().mf_set_helicity_split(self.ptr, parts))
+
     def device_status(self):
         """Raises MfError(MF_ERR_TIMEOUT) if a bounded device wait ran out since the last check."""
         _check(self.ptr, _lib.lib().mf_device_status(self.ptr))
@@ -159,15 +163,17 @@ class Context:
                                                   out.ctypes.data_as(C.POINTER(C.c_double))))
         return out
 
-    def set_batch_schedule(self, mode: int, sched: int, tile_heavy: int, tile_light: int, ctas_per_sm: int = 0):
-        _check(self.ptr, _lib.lib().mf_set_batch_schedule(self.ptr, mode, sched, tile_heavy, tile_light, ctas_per_sm))
+    def set_batch_schedule(self, mode: int, sched: int, tile_heavy: int, tile_light: int, ctas_per_sm: int = 0,
+                           hsplit: int = 1):
+        _check(self.ptr, _lib.lib().mf_set_batch_schedule(self.ptr, mode, sched, tile_heavy, tile_light,
+                                                           ctas_per_sm, hsplit))
 
     def autotune_batch(self, processes, n_events, sqrt_s: float):
-        """Pick the batch schedule by timing: (mode, sched, tile_heavy, tile_light, ctas_per_sm)."""
+        """Pick the batch schedule by timing: (mode, sched, tile_heavy, tile_light, ctas_per_sm, hsplit)."""
         n_ch = len(processes)
         procs = (C.c_int * n_ch)(*[int(p) for p in processes])
         ns = (C.c_longlong * n_ch)(*[int(n) for n in n_events])
-        ch = (C.c_int * 5)()
+        ch = (C.c_int * 6)()
         _check(self.ptr, _lib.lib().mf_autotune_batch(self.ptr, n_ch, procs, ns, sqrt_s, ch))
         return tuple(ch)
 

@@ -36,10 +36,12 @@ struct Me_gg_ttgg {
   // R: float or double (or Dual of them for derivatives); the momenta, masses and
   // the result use the matching FP64 scalar S = Widen<R>::type
   // TC: colour sum on the tensor cores (float, SYNC, 128-thread CTAs; cta: the CTA's TcCta)
+  // hpart, hparts: helicity split, this call sums every hparts-th evaluated helicity
+  // from the hpart-th on (the caller adds the hparts partial sums)
   template <typename R, bool SYNC = false, bool TC = false>
   __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],
                                                 typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot,
-                                                void* cta = nullptr);
+                                                void* cta = nullptr, int hpart = 0, int hparts = 1);
   template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }
 };
 
@@ -1227,7 +1229,7 @@ __device__ __noinline__ R hel_gg_ttgg(const Me_gg_ttgg::Inv<R>& v, int ih)
 
 template <typename R, bool SYNC, bool TC>
 __device__ __noinline__ typename Widen<R>::type me2_gg_ttgg_impl(const typename Widen<R>::type* pflat,
-    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta)
+    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta, int hpart, int hparts)
 {
     using S = typename Widen<R>::type;
     constexpr int NEXT = Me_gg_ttgg::NEXT, NHEL = Me_gg_ttgg::NHEL, NGLUON = Me_gg_ttgg::NGLUON;
@@ -1324,7 +1326,7 @@ __device__ __noinline__ typename Widen<R>::type me2_gg_ttgg_impl(const typename 
     // sum over the configurations with the first gluon at helicity +1.
     R acc = R(0);
 #pragma unroll 1
-    for (int ih = 1; ih < NHEL; ih += 2) {
+    for (int ih = 1 + 2 * hpart; ih < NHEL; ih += 2 * hparts) {
         if constexpr (TC) {
             // the colour sum synchronises the CTA itself (its barriers replace SYNC's)
             static_assert(SYNC && sizeof(R) == 4, "tensor-core colour sum: float, whole-CTA calls");
@@ -1344,8 +1346,8 @@ __device__ __noinline__ typename Widen<R>::type me2_gg_ttgg_impl(const typename 
 
 template <typename R, bool SYNC, bool TC>
 __device__ typename Widen<R>::type Me_gg_ttgg::me2(const typename Widen<R>::type (&p)[NEXT][4],
-    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta)
+    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta, int hpart, int hparts)
 {
-    return me2_gg_ttgg_impl<R, SYNC, TC>(&p[0][0], mt, gs, slot, cta);
+    return me2_gg_ttgg_impl<R, SYNC, TC>(&p[0][0], mt, gs, slot, cta, hpart, hparts);
 }
 }  // namespace mf

@@ -15,7 +15,7 @@ struct Me_ug_ttu {
   template <typename R, bool SYNC = false, bool TC = false>
   __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],
                                                 typename Widen<R>::type mt, typename Widen<R>::type gs, void*,
-                                                void* = nullptr)
+                                                void* = nullptr, int = 0, int = 1)
   {
     using S = typename Widen<R>::type;
     // momenta of the internal lines

@@ -15,7 +15,7 @@ struct Me_uu_tt {
   template <typename R, bool SYNC = false, bool TC = false>
   __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],
                                                 typename Widen<R>::type mt, typename Widen<R>::type gs, void*,
-                                                void* = nullptr)
+                                                void* = nullptr, int = 0, int = 1)
   {
     using S = typename Widen<R>::type;
     const S q[4] = {p[0][0] + p[1][0], p[0][1] + p[1][1], p[0][2] + p[1][2], p[0][3] + p[1][3]};

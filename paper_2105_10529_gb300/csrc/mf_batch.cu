@@ -45,7 +45,8 @@ using PGgTtgg = ProcTops<Me_gg_ttgg>;
 using PUuTt = ProcTops<Me_uu_tt, 1, 2>;
 using PUgTtu = ProcTops<Me_ug_ttu, 1, 0>;
 
-template <bool SYNC>
+// HS: helicity split of the 2 -> 3 and 2 -> 4 gluon channels (1, or 2 with SYNC)
+template <bool SYNC, int HS>
 __global__ void __launch_bounds__(BATCH_TPB) batch_kernel(BatchParams bp)
 {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -84,11 +85,13 @@ __global__ void __launch_bounds__(BATCH_TPB) batch_kernel(BatchParams bp)
             break;
         case MF_GG_TTG:
             out = bp.tile_out[c] + lt * (2 + PGgTtg::D * s_kp.nb);
-            integrand_heavy<PGgTtg, float, BATCH_TPB, false, SYNC>(s_kp, smem_raw, e0, BATCH_TPB, e1, out);
+            integrand_heavy<PGgTtg, float, BATCH_TPB, false, SYNC, false, HS>(s_kp, smem_raw, e0, BATCH_TPB / HS, e1,
+                                                                    out);
             break;
         case MF_GG_TTGG:
             out = bp.tile_out[c] + lt * (2 + PGgTtgg::D * s_kp.nb);
-            integrand_heavy<PGgTtgg, float, BATCH_TPB, false, SYNC>(s_kp, smem_raw, e0, BATCH_TPB, e1, out);
+            integrand_heavy<PGgTtgg, float, BATCH_TPB, false, SYNC, false, HS>(s_kp, smem_raw, e0, BATCH_TPB / HS, e1,
+                                                                    out);
             break;
         default:
             break;
@@ -152,8 +155,9 @@ int ensure_batch_buffers(mf_ctx* c, size_t tile_doubles)
         MF_BCUDA(c, cudaMalloc(&c->d_bsums, sizeof(double) * MAX_CH * (2 + MAX_DIM * MAX_BINS)));
         MF_BCUDA(c, cudaMalloc(&c->d_bcount, sizeof(unsigned long long) * (2 * MAX_CH + 1)));
         const size_t sm = batch_smem(MAX_BINS, 8192);
-        MF_BCUDA(c, cudaFuncSetAttribute((const void*)batch_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-        MF_BCUDA(c, cudaFuncSetAttribute((const void*)batch_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+        for (const void* f : { (const void*)batch_kernel<false, 1>, (const void*)batch_kernel<true, 1>,
+                               (const void*)batch_kernel<true, 2> })
+            MF_BCUDA(c, cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
     }
     if (tile_doubles > c->tiles_cap) {
         if (c->graph) { cudaGraphExecDestroy(c->graph); c->graph = nullptr; c->graph_key.clear(); }
@@ -169,7 +173,14 @@ int ensure_batch_buffers(mf_ctx* c, size_t tile_doubles)
 struct Schedule {
     int mode, sched, bps;
     long long tile_heavy, tile_light;
+    int hsplit;   // lanes per event of the heavy channels (2 needs sched 1)
 };
+
+const void* batch_fn(const Schedule& sch)
+{
+    if (!sch.sched) return (const void*)batch_kernel<false, 1>;
+    return sch.hsplit == 2 ? (const void*)batch_kernel<true, 2> : (const void*)batch_kernel<true, 1>;
+}
 
 // a cheaper channel of the split schedule: its own integrand kernel
 struct SideLaunch {
@@ -284,9 +295,7 @@ int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, 
     pl.nblk = 0;
     if (pl.bp.n_slot > 0) {
         int per_sm = 0;
-        MF_BCUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, sch.sched ? (const void*)batch_kernel<true>
-                                                                                      : (const void*)batch_kernel<false>,
-                                                                   BATCH_TPB, pl.sm));
+        MF_BCUDA(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, batch_fn(sch), BATCH_TPB, pl.sm));
         if (per_sm < 1) return mf_fail(c, MF_ERR_CUDA, "batch kernel does not fit on an SM");
         if (sch.bps > 0 && sch.bps < per_sm) per_sm = sch.bps;
         pl.nblk = (int)std::min<long long>((long long)per_sm * c->n_sm, tb);
@@ -326,13 +335,14 @@ int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s, c
     if (pl.bp.n_slot > 0) {
         MF_BCUDA(c, cudaMemsetAsync(pl.bp.tile_counter, 0, sizeof(unsigned long long), s));
         pl.bp.iteration = (unsigned)it;
-        if (pl.sch.sched) batch_kernel<true><<<pl.nblk, BATCH_TPB, pl.sm, s>>>(pl.bp);
-        else batch_kernel<false><<<pl.nblk, BATCH_TPB, pl.sm, s>>>(pl.bp);
+        if (!pl.sch.sched) batch_kernel<false, 1><<<pl.nblk, BATCH_TPB, pl.sm, s>>>(pl.bp);
+        else if (pl.sch.hsplit == 2) batch_kernel<true, 2><<<pl.nblk, BATCH_TPB, pl.sm, s>>>(pl.bp);
+        else batch_kernel<true, 1><<<pl.nblk, BATCH_TPB, pl.sm, s>>>(pl.bp);
         MF_BCUDA(c, cudaGetLastError());
     }
     for (SideLaunch& sl : pl.side) {
         sl.kp.iteration = (unsigned)it;
-        MF_BCUDA(c, sl.ops->integrand(MF_MIXED, false, pl.sch.sched, sl.kp, sl.nblk, sl.sm, low));
+        MF_BCUDA(c, sl.ops->integrand(MF_MIXED, false, pl.sch.sched, 1, sl.kp, sl.nblk, sl.sm, low));
     }
     if (fork) {
         MF_BCUDA(c, cudaEventRecord(c->ev_join, low));
@@ -366,7 +376,8 @@ int set_node_priorities(mf_ctx* c, cudaGraph_t g)
         if (ty != cudaGraphNodeTypeKernel) continue;
         cudaKernelNodeParams kp;
         MF_BCUDA(c, cudaGraphKernelNodeGetParams(nd, &kp));
-        const bool hi = kp.func == (void*)batch_kernel<true> || kp.func == (void*)batch_kernel<false>;
+        const bool hi = kp.func == (void*)batch_kernel<true, 1> || kp.func == (void*)batch_kernel<true, 2> ||
+                        kp.func == (void*)batch_kernel<false, 1>;
         cudaLaunchAttributeValue v;
         std::memset(&v, 0, sizeof(v));
         v.priority = hi ? greatest : least;
@@ -379,7 +390,8 @@ std::string plan_key(const mf_ctx* c, const Plan& pl, int n_iter, double sqrt_s,
 {
     // the side kernels' parameters are baked into the graph: couplings are part of the key
     std::string k = std::to_string(n_iter) + "|" + std::to_string(sqrt_s) + "|" + std::to_string(pl.sch.mode) + "|" +
-                    std::to_string(pl.sch.sched) + "|" + std::to_string(pl.sch.tile_heavy) + "|" +
+                    std::to_string(pl.sch.sched) + "|" + std::to_string(pl.sch.hsplit) + "|" +
+                    std::to_string(pl.sch.tile_heavy) + "|" +
                     std::to_string(pl.sch.tile_light) + "|" + std::to_string(pl.nblk) + "|" +
                     std::to_string(c->cfg.n_bins) + "|" + std::to_string(c->cfg.alpha) + "|" +
                     std::to_string(c->cfg.mt) + "|" + std::to_string(c->cfg.alpha_s) + "|" +
@@ -407,7 +419,7 @@ void combine(const double* it, int n_iter, double& mean, double& err, double& ch
 
 Schedule current_schedule(const mf_ctx* c)
 {
-    return Schedule{ c->b_mode, c->b_sched, c->b_bps, c->b_tile_heavy, c->b_tile_light };
+    return Schedule{ c->b_mode, c->b_sched, c->b_bps, c->b_tile_heavy, c->b_tile_light, c->b_hsplit };
 }
 
 // derivative passes of every channel at the grids in d_bgrids; out_host [n_ch + 1][4]
@@ -565,12 +577,15 @@ int mf_batch_grad(mf_ctx* c, int n_ch, const int* processes, const long long* n_
     return batch_grads(c, n_ch, processes, n_events, sqrt_s, cuts, iteration, out_host);
 }
 
-int mf_set_batch_schedule(mf_ctx* c, int mode, int sched, long long tile_heavy, long long tile_light, int ctas_per_sm)
+int mf_set_batch_schedule(mf_ctx* c, int mode, int sched, long long tile_heavy, long long tile_light, int ctas_per_sm,
+                          int hsplit)
 {
     if (!c) return MF_ERR_ARG;
     if ((mode != 0 && mode != 1) || (sched != 0 && sched != 1) || tile_heavy < 32 || tile_heavy > (1LL << 26) ||
-        tile_light < 32 || tile_light > (1LL << 26) || ctas_per_sm < 0 || ctas_per_sm > 16)
+        tile_light < 32 || tile_light > (1LL << 26) || ctas_per_sm < 0 || ctas_per_sm > 16 ||
+        (hsplit != 1 && hsplit != 2) || (hsplit == 2 && sched != 1))
         return mf_fail(c, MF_ERR_ARG, "mf_set_batch_schedule: bad argument");
+    c->b_hsplit = hsplit;
     c->b_mode = mode;
     c->b_sched = sched;
     c->b_tile_heavy = tile_heavy;
@@ -589,9 +604,10 @@ int mf_autotune_batch(mf_ctx* c, int n_ch, const int* processes, const long long
     std::vector<Schedule> cand;
     for (int mode = 0; mode <= 1; ++mode)
         for (int sched = 0; sched <= 1; ++sched)
-            for (long long th : { 1024LL, 2048LL, 4096LL })
-                for (long long tl : { 2048LL, 4096LL })
-                    cand.push_back(Schedule{ mode, sched, 0, th, tl });
+            for (int hs = 1; hs <= 1 + sched; ++hs)
+                for (long long th : { 1024LL, 2048LL, 4096LL })
+                    for (long long tl : { 2048LL, 4096LL })
+                        cand.push_back(Schedule{ mode, sched, 0, th, tl, hs });
     float best = 1e30f;
     Schedule pick = current_schedule(c);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -630,12 +646,14 @@ int mf_autotune_batch(mf_ctx* c, int n_ch, const int* processes, const long long
     c->b_tile_heavy = pick.tile_heavy;
     c->b_tile_light = pick.tile_light;
     c->b_bps = pick.bps;
+    c->b_hsplit = pick.hsplit;
     if (choice_host) {
         choice_host[0] = pick.mode;
         choice_host[1] = pick.sched;
         choice_host[2] = (int)pick.tile_heavy;
         choice_host[3] = (int)pick.tile_light;
         choice_host[4] = pick.bps;
+        choice_host[5] = pick.hsplit;
     }
     return MF_OK;
 }

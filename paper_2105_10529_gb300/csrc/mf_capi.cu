@@ -367,6 +367,13 @@ int mf_set_schedule(mf_ctx* c, int sched)
     return MF_OK;
 }
 
+int mf_set_helicity_split(mf_ctx* c, int parts)
+{
+    if (!c || (parts != 1 && parts != 2)) return MF_ERR_ARG;
+    c->hsplit = parts;
+    return MF_OK;
+}
+
 int mf_set_pdf(mf_ctx* c, const double* pdf_grid_host)
 {
     if (!c || !pdf_grid_host) return MF_ERR_ARG;
@@ -403,7 +410,7 @@ int mf_vegas_pass(mf_ctx* c, int process, double sqrt_s, const double* grid_dev,
     rc = pick_blocks(c, ops, sm, c->cfg.precision, &nblk);
     if (rc) return rc;
     MF_CUDA(c, cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), c->stream));
-    MF_CUDA(c, ops->integrand(c->cfg.precision, write, c->sched, kp, nblk, sm, c->stream));
+    MF_CUDA(c, ops->integrand(c->cfg.precision, write, c->sched, c->hsplit, kp, nblk, sm, c->stream));
     const int ncol = 2 + ops->D * c->cfg.n_bins;
     finish_pass_kernel<<<1, 1024, ncol * sizeof(double), c->stream>>>(c->d_partials, nblk, ops->D, c->cfg.n_bins,
                                                                      n_events, c->cfg.alpha, 0, nullptr, nullptr,
@@ -457,7 +464,7 @@ int mf_integrate(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, lon
     const int ncol = 2 + D * nb;
     for (int it = 0; it < n_iter; ++it) {
         kp.iteration = (uint32_t)it;
-        MF_CUDA(c, ops->integrand(c->cfg.precision, false, c->sched, kp, nblk, sm, c->stream));
+        MF_CUDA(c, ops->integrand(c->cfg.precision, false, c->sched, c->hsplit, kp, nblk, sm, c->stream));
         finish_pass_kernel<<<1, 1024, ncol * sizeof(double), c->stream>>>(
             c->d_partials, nblk, D, nb, n_events, c->cfg.alpha, it < n_iter - 1, c->d_grid, c->d_iter + 2 * it, nullptr);
         MF_CUDA(c, cudaGetLastError());

@@ -25,6 +25,7 @@ struct mf_ctx {
     int kin_ctas = 0;
     int max_blocks = 0;
     int sched = 2;                   // integrand schedule (see mf_set_schedule)
+    int hsplit = 1;                  // lanes per event in the heavy integrand (see mf_set_helicity_split)
     std::string err;
     // batched channels: workspace, tuned schedule and the cached CUDA graph
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture and replay (high priority)
@@ -41,6 +42,7 @@ struct mf_ctx {
     int b_sched = 1, b_bps = 0;          // tuned: barrier schedule, CTAs per SM (0 = occupancy)
     long long b_tile_heavy = 4096;       // tuned: events per tile of the 2 -> 3 and 2 -> 4 gluon channels
     long long b_tile_light = 4096;       // tuned: events per tile of the other channels
+    int b_hsplit = 1;                    // tuned: lanes per event of the 2 -> 3 and 2 -> 4 gluon channels
     cudaGraphExec_t graph = nullptr;
     std::string graph_key;
     int b_last_nch = 0;                  // channel list of the grids in d_bgrids

@@ -12,8 +12,11 @@ struct ProcOps {
     cudaError_t (*prepare)(size_t smem);
     cudaError_t (*occupancy)(int prec, size_t smem, int* blocks_per_sm);
     // sched: 0 free-running warps, 1 CTA barrier between helicities (heavy processes),
-    // 2 barrier and the colour sum on the tensor cores (processes with P::TC, mixed precision)
-    cudaError_t (*integrand)(int prec, bool write, int sched, const KParams& kp, int nblk, size_t smem, cudaStream_t s);
+    // 2 barrier and the colour sum on the tensor cores (processes with P::TC, mixed precision);
+    // hsplit: 1, or 2 lanes per event each summing half the helicities (heavy processes,
+    // mixed precision, sched >= 1, no per-event outputs; otherwise 1)
+    cudaError_t (*integrand)(int prec, bool write, int sched, int hsplit, const KParams& kp, int nblk, size_t smem,
+                             cudaStream_t s);
     cudaError_t (*evaluate)(int prec, const double* mom, long long n, double* me2, double mt, double gs,
                             const EwParams& ew, int nblk, cudaStream_t s);
 };
@@ -75,11 +78,15 @@ struct IntegrandOps {
     static const void* fn() { return (const void*)integrand_kernel<P, R, TPB, W, S && HS>; }
     template <bool W>
     static const void* fn_tc() { return (const void*)integrand_kernel<P, float, TPB, W, HT, HT>; }
+    // helicity split variants (mixed precision, barrier schedule, no per-event outputs)
+    static const void* fn_hs() { return (const void*)integrand_kernel<P, float, TPB, false, HS, false, HS ? 2 : 1>; }
+    static const void* fn_hs_tc() { return (const void*)integrand_kernel<P, float, TPB, false, HT, HT, HT ? 2 : 1>; }
     static cudaError_t prepare(size_t sm)
     {
-        const void* fns[10] = { fn<double, false, false>(), fn<double, true, false>(), fn<float, false, false>(),
+        const void* fns[12] = { fn<double, false, false>(), fn<double, true, false>(), fn<float, false, false>(),
                                 fn<float, true, false>(), fn<double, false, true>(), fn<double, true, true>(),
-                                fn<float, false, true>(), fn<float, true, true>(), fn_tc<false>(), fn_tc<true>() };
+                                fn<float, false, true>(), fn<float, true, true>(), fn_tc<false>(), fn_tc<true>(),
+                                fn_hs(), fn_hs_tc() };
         for (const void* f : fns) {
             cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
@@ -92,8 +99,20 @@ struct IntegrandOps {
                                                              TPB, sm);
     }
     template <typename R, bool W>
-    static void launch(int sched, const KParams& kp, int nblk, size_t sm, cudaStream_t s)
+    static void launch(int sched, int hsplit, const KParams& kp, int nblk, size_t sm, cudaStream_t s)
     {
+        if constexpr (HS && sizeof(R) == 4 && !W) {
+            if (hsplit == 2 && sched >= 1) {
+                if constexpr (HT) {
+                    if (sched == 2) {
+                        integrand_kernel<P, float, TPB, false, true, true, 2><<<nblk, TPB, sm, s>>>(kp);
+                        return;
+                    }
+                }
+                integrand_kernel<P, float, TPB, false, true, false, 2><<<nblk, TPB, sm, s>>>(kp);
+                return;
+            }
+        }
         if constexpr (HT && sizeof(R) == 4) {
             if (sched == 2) {
                 integrand_kernel<P, float, TPB, W, true, true><<<nblk, TPB, sm, s>>>(kp);
@@ -103,14 +122,15 @@ struct IntegrandOps {
         if (sched && HS) integrand_kernel<P, R, TPB, W, HS><<<nblk, TPB, sm, s>>>(kp);
         else integrand_kernel<P, R, TPB, W, false><<<nblk, TPB, sm, s>>>(kp);
     }
-    static cudaError_t integrand(int prec, bool write, int sched, const KParams& kp, int nblk, size_t sm, cudaStream_t s)
+    static cudaError_t integrand(int prec, bool write, int sched, int hsplit, const KParams& kp, int nblk, size_t sm,
+                                 cudaStream_t s)
     {
         if (prec) {
-            if (write) launch<float, true>(sched, kp, nblk, sm, s);
-            else launch<float, false>(sched, kp, nblk, sm, s);
+            if (write) launch<float, true>(sched, hsplit, kp, nblk, sm, s);
+            else launch<float, false>(sched, hsplit, kp, nblk, sm, s);
         } else {
-            if (write) launch<double, true>(sched, kp, nblk, sm, s);
-            else launch<double, false>(sched, kp, nblk, sm, s);
+            if (write) launch<double, true>(sched, hsplit, kp, nblk, sm, s);
+            else launch<double, false>(sched, hsplit, kp, nblk, sm, s);
         }
         return cudaGetLastError();
     }

@@ -453,10 +453,16 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
 // event on the idle lanes and discards it), which allows an optional CTA
 // barrier between helicities (SYNC) that keeps the warps on the same code.
 // The histogram is filled by one thread per dimension in queue order.
-template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false>
+// HS: helicity split (HS = 1 or 2).  With 2, thread t and thread t + TPB/2
+// share one event and each sums every other helicity; a CTA then takes
+// TPB / 2 events per round (step is a multiple of TPB / HS), a batch holds
+// TPB / 2 events, and every warp still evaluates one helicity at a time (the
+// halves live in different warps, so the helicity stays warp-uniform).
+template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false, int HS = 1>
 __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char* smem_raw, long long first,
                                                 long long step, long long end, double* out)
 {
+    static_assert(HS == 1 || (HS == 2 && SYNC && !WRITE), "helicity split: pairs of lanes, barrier schedule");
     static_assert(!TC || (P::TC && SYNC && TPB == 128 && sizeof(R) == 4),
                   "tensor-core colour sum: float, barrier schedule, one TMEM lane per thread");
     constexpr int D = P::D, WARPS = TPB / 32;
@@ -467,7 +473,9 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     double* shist = reinterpret_cast<double*>(smem_raw + L::hist_off(nb, npv));
     double* svbuf = reinterpret_cast<double*>(smem_raw + L::vbuf_off(nb, npv));
     uint8_t* sbins = smem_raw + L::bbuf_off(nb, npv);
-    // ring of queued events as r TPB + tid (event first + r step + tid)
+    // events per round and per batch
+    constexpr int EPB = TPB / HS;
+    // ring of queued events as r EPB + tid (event first + r step + tid)
     constexpr int CAP = L::CAP;
     int* squeue = reinterpret_cast<int*>(smem_raw + L::queue_off(nb, npv));
     int* scount = squeue + CAP;                                  // [0] length, [1] head, [2 + w] warp counts
@@ -513,7 +521,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             int pass = 0;
             EventOut<D> o;
             double pm[P::NEXT][4], pref = 0.0;
-            if (e < end) {
+            if (tid < EPB && e < end) {
                 kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
                 pass = o.mask ? 1 : 0;
                 npass += pass;
@@ -530,7 +538,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             for (int w = 0; w < WARPS; ++w) { woff += (w < warp) ? scount[2 + w] : 0; tot += scount[2 + w]; }
             if (pass) {
                 const int pos = (head + cnt + woff + __popc(bal & ((1u << lane) - 1u))) % CAP;
-                squeue[pos] = (int)r * TPB + tid;
+                squeue[pos] = (int)r * EPB + tid;
                 if (MAYREUSE && reuse) {
 #pragma unroll
                     for (int i = 0; i < P::NEXT; ++i)
@@ -548,12 +556,14 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
         // evaluate full batches (and, at the end, whatever is left)
         for (;;) {
             const int cnt = scount[0], head = scount[1];
-            if (cnt == 0 || (!flush && cnt < TPB)) break;
-            const int take = cnt < TPB ? cnt : TPB;
-            const bool mine = tid < take;
-            const int pos = (head + (mine ? tid : 0)) % CAP;
+            if (cnt == 0 || (!flush && cnt < EPB)) break;
+            const int take = cnt < EPB ? cnt : EPB;
+            const int eidx = tid % EPB, hpart = tid / EPB;
+            const bool mine = eidx < take;
+            const bool owner = mine && hpart == 0;     // the lane that books the event
+            const int pos = (head + (mine ? eidx : 0)) % CAP;
             const int li = squeue[pos];
-            const long long e = first + (long long)(li / TPB) * step + (li % TPB);
+            const long long e = first + (long long)(li / EPB) * step + (li % EPB);
             EventOut<D> o;
             double pm[P::NEXT][4], pref;
             if (MAYREUSE && reuse) {
@@ -568,12 +578,19 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
                 kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
             }
             double me;
-            if constexpr (TC) me = P::Me::template me2<R, SYNC, true>(pm, kp.mt, kp.gs, slot, tc);
-            else me = P::Me::template me2<R, SYNC>(pm, kp.mt, kp.gs, slot);
-            double w = mine ? pref * me : 0.0;
-            if (!isfinite(w)) { w = 0.0; if (mine) ++nnan; }
+            if constexpr (TC) me = P::Me::template me2<R, SYNC, true>(pm, kp.mt, kp.gs, slot, tc, hpart, HS);
+            else me = P::Me::template me2<R, SYNC>(pm, kp.mt, kp.gs, slot, nullptr, hpart, HS);
+            if constexpr (HS == 2) {
+                // the owner adds the second half, evaluated in another warp
+                svbuf[tid] = me;
+                __syncthreads();
+                if (hpart == 0) me += svbuf[tid + EPB];
+                __syncthreads();
+            }
+            double w = owner ? pref * me : 0.0;
+            if (!isfinite(w)) { w = 0.0; if (owner) ++nnan; }
             if constexpr (WRITE) {
-                if (mine) {
+                if (owner) {
                     o.me2 = me; o.w = w;
                     write_event<D>(kp, e, o, false);
                     write_momenta<P::NEXT>(kp, e, pm);
@@ -590,7 +607,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             if (tid < D) {
                 double* h = shist + tid * nb;
                 const uint8_t* b = sbins + tid * TPB;
-                for (int t = 0; t < take; ++t) h[b[t]] += svbuf[t];
+                for (int t = 0; t < take; ++t) h[b[t]] += svbuf[t];   // the owners, in queue order
             }
             // the batch's entries leave the ring
             __syncthreads();
@@ -604,14 +621,19 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
 
 // ------------------------------------------------------------------ the fused integrand kernel
 
-template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false>
+template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false, int HS = 1>
 __global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    const long long first = (long long)blockIdx.x * TPB, step = (long long)gridDim.x * TPB;
     double* out = kp.partials + (size_t)blockIdx.x * (2 + P::D * kp.nb);
-    if constexpr (P::HEAVY) integrand_heavy<P, R, TPB, WRITE, SYNC, TC>(kp, smem_raw, first, step, kp.n_events, out);
-    else integrand_light<P, R, TPB, WRITE>(kp, smem_raw, first, step, kp.n_events, out);
+    if constexpr (P::HEAVY) {
+        constexpr int EPB = TPB / HS;   // events per CTA and round
+        const long long first = (long long)blockIdx.x * EPB, step = (long long)gridDim.x * EPB;
+        integrand_heavy<P, R, TPB, WRITE, SYNC, TC, HS>(kp, smem_raw, first, step, kp.n_events, out);
+    } else {
+        const long long first = (long long)blockIdx.x * TPB, step = (long long)gridDim.x * TPB;
+        integrand_light<P, R, TPB, WRITE>(kp, smem_raw, first, step, kp.n_events, out);
+    }
 }
 
 // ------------------------------------------------------------------ evaluate

@@ -166,7 +166,7 @@ extern "C" int mf_vegas_pass_static(int process, const mf_config* cfg, double sq
     cudaStream_t s = (cudaStream_t)stream;
     // the counters start at zero on every call; the partials are fully overwritten by the kernel
     if (cudaMemsetAsync(scratch, 0, 2 * sizeof(double), s) != cudaSuccess) return MF_ERR_CUDA;
-    if (ops->integrand(cfg->precision, false, 0, kp, (int)nblk, sm, s) != cudaSuccess) return MF_ERR_CUDA;
+    if (ops->integrand(cfg->precision, false, 0, 1, kp, (int)nblk, sm, s) != cudaSuccess) return MF_ERR_CUDA;
     finish_pass_kernel<<<1, 1024, ncol * sizeof(double), s>>>(kp.partials, (int)nblk, D, nb, n_events, cfg->alpha, 0,
                                                               nullptr, nullptr, sums_dev);
     if (cudaGetLastError() != cudaSuccess) return MF_ERR_CUDA;

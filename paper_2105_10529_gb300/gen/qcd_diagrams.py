@@ -616,10 +616,12 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("  // R: float or double (or Dual of them for derivatives); the momenta, masses and")
     src.append("  // the result use the matching FP64 scalar S = Widen<R>::type")
     src.append("  // TC: colour sum on the tensor cores (float, SYNC, 128-thread CTAs; cta: the CTA's TcCta)")
+    src.append("  // hpart, hparts: helicity split, this call sums every hparts-th evaluated helicity")
+    src.append("  // from the hpart-th on (the caller adds the hparts partial sums)")
     src.append("  template <typename R, bool SYNC = false, bool TC = false>")
     src.append("  __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],")
     src.append("                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot,")
-    src.append("                                                void* cta = nullptr);")
+    src.append("                                                void* cta = nullptr, int hpart = 0, int hparts = 1);")
     src.append("  template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }")
     src.append("};")
     src.append("")
@@ -640,7 +642,7 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("")
     src.append("template <typename R, bool SYNC, bool TC>")
     src.append(f"__device__ __noinline__ typename Widen<R>::type me2_{name}_impl(const typename Widen<R>::type* pflat,")
-    src.append("    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta)")
+    src.append("    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta, int hpart, int hparts)")
     src.append("{")
     src.append("    using S = typename Widen<R>::type;")
     src.append(f"    constexpr int NEXT = Me_{name}::NEXT, NHEL = Me_{name}::NHEL, NGLUON = Me_{name}::NGLUON;")
@@ -657,7 +659,7 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("    // sum over the configurations with the first gluon at helicity +1.")
     src.append("    R acc = R(0);")
     src.append("#pragma unroll 1")
-    src.append("    for (int ih = 1; ih < NHEL; ih += 2) {")
+    src.append("    for (int ih = 1 + 2 * hpart; ih < NHEL; ih += 2 * hparts) {")
     if tc:
         src.append("        if constexpr (TC) {")
         src.append("            // the colour sum synchronises the CTA itself (its barriers replace SYNC's)")
@@ -682,9 +684,9 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("")
     src.append("template <typename R, bool SYNC, bool TC>")
     src.append(f"__device__ typename Widen<R>::type Me_{name}::me2(const typename Widen<R>::type (&p)[NEXT][4],")
-    src.append("    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta)")
+    src.append("    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta, int hpart, int hparts)")
     src.append("{")
-    src.append(f"    return me2_{name}_impl<R, SYNC, TC>(&p[0][0], mt, gs, slot, cta);")
+    src.append(f"    return me2_{name}_impl<R, SYNC, TC>(&p[0][0], mt, gs, slot, cta, hpart, hparts);")
     src.append("}")
     src.append("}  // namespace mf")
     stats = dict(n_diag=n_diag, n_amp=len(diags), ncol=ncol, counts=dict(em.counts), colour_den=den)

@@ -93,7 +93,7 @@ def _struct(name: str, n_ext: int, n_hel: int, avg: str, k: int, prologue: List[
     s.append("  template <typename R, bool SYNC = false, bool TC = false>")
     s.append("  __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],")
     s.append("                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void*,")
-    s.append("                                                void* = nullptr)")
+    s.append("                                                void* = nullptr, int = 0, int = 1)")
     s.append("  {")
     s.append("    using S = typename Widen<R>::type;")
     for l in prologue:

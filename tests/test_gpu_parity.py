@@ -357,6 +357,57 @@ def test_stored_kinematics_match_recompute(proc, pdf_grid):
     ctx.close()
 
 
+@pytest.mark.parametrize("proc", [IN.GG_TTG, IN.GG_TTGG])
+def test_helicity_split_pass(proc, pdf_grid, opdf):
+    """Two threads per event, each summing half of the helicities: under the
+    barrier schedules the pass sums agree with one thread per event to FP32
+    rounding of the two summation orders (every entry, histogram included),
+    and the sum of weights with the oracle's sum over the same events."""
+    phys = PHYS[proc]
+    n = 1001 if proc == IN.GG_TTGG else 5003    # several batches and a ragged tail
+    g = random_grid(IN.DIM[proc], seed=51)
+    grid = torch.tensor(g, device="cuda")
+    ctx = ctx_for(proc, 1, pdf_grid)
+    scheds = (1, 2) if proc == IN.GG_TTGG else (1,)
+    ref = oracle_events(proc, phys, opdf, g, n, iteration=3)
+    ref_sum = float(np.sum(ref["w"])) / n
+    for sched in scheds:
+        ctx.set_schedule(sched)
+        ctx.set_helicity_split(1)
+        a, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=3)
+        ctx.set_helicity_split(2)
+        b, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=3)
+        ctx.device_status()
+        assert torch.all((a - b).abs() <= 1e-6 * a.abs() + 1e-300), sched
+        assert float(b[0]) == pytest.approx(ref_sum, rel=1e-5), sched
+    from paper_2105_10529_gb300._lib import MfError
+    ctx.set_helicity_split(1)
+    with pytest.raises(MfError):
+        ctx.set_helicity_split(3)
+    ctx.close()
+
+
+def test_helicity_split_integrate(pdf_grid):
+    """Iterated VEGAS of g g -> t tbar g g with the helicity split on the
+    default (tensor-core) schedule agrees with no split to rounding; the pass
+    with per-event outputs ignores the split."""
+    proc = IN.GG_TTGG
+    phys = PHYS[proc]
+    ctx = ctx_for(proc, 1, pdf_grid)
+    r1 = ctx.integrate(proc, phys.sqrt_s, 20000, 2)
+    ctx.set_helicity_split(2)
+    r2 = ctx.integrate(proc, phys.sqrt_s, 20000, 2)
+    ctx.device_status()
+    assert r2["sigma"] == pytest.approx(r1["sigma"], rel=1e-6)
+    assert r2["n_pass"] == r1["n_pass"]
+    grid = torch.tensor(random_grid(IN.DIM[proc], seed=52), device="cuda")
+    _, e2 = ctx.vegas_pass(proc, phys.sqrt_s, grid, 300, iteration=1, want_events=True, fields=("me2",))
+    ctx.set_helicity_split(1)
+    _, e1 = ctx.vegas_pass(proc, phys.sqrt_s, grid, 300, iteration=1, want_events=True, fields=("me2",))
+    assert torch.equal(e1["me2"], e2["me2"])
+    ctx.close()
+
+
 def test_bounded_wait_expiry_is_reported(pdf_grid):
     """A device wait on an mbarrier phase that nothing completes runs out after
     its iteration limit; the host sees MF_ERR_TIMEOUT once, and the context
