@@ -400,7 +400,8 @@ def run_ours(args):
         "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": dict(workload_config(N, dim, nb), colour_sum=(
-            "tensor cores: tcgen05.mma kind::f16, (128 events x 24) x (24 x 24) per helicity, bf16x2 split of "
+            "tensor cores: tcgen05.mma kind::f16, two (128 events x 24) x (24 x 24) per helicity and 256-thread CTA, "
+            "bf16x2 split of "
             "the colour flows, FP32 accumulation in TMEM") if (args.sched is None or args.sched == 2) else "FP32 FMA",
                       helicity_split=args.hsplit or 1),
         # per step: the integrand and the end-of-pass reduction (mf_vegas_pass) and the refinement

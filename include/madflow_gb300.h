@@ -141,7 +141,7 @@ int mf_set_precision(struct mf_ctx *ctx, int precision);
  * helicity keeps the CTA's warps on the same instructions,
  * 2 (the default) = as 1, and for g g -> t tbar g g in MF_MIXED the colour sum of every
  * helicity (24 x 24 colour matrix, Sec. 2.2) runs on the tensor cores as one
- * (128 events x 24) x (24 x 24) contraction per CTA (tcgen05, bf16 split of the
+ * (128 events x 24) x (24 x 24) contraction per 128 threads (tcgen05, bf16 split of the
  * colour-flow amplitudes, FP32 accumulation in tensor memory); elsewhere 2 acts
  * as 1.  Schedules 0 and 1 give identical results; 2 differs from them by FP32
  * rounding.  MF_ERR_ARG for other values. */

@@ -35,7 +35,7 @@ struct Me_gg_ttgg {
   // SYNC: a CTA barrier after every helicity (every thread of the CTA must call)
   // R: float or double (or Dual of them for derivatives); the momenta, masses and
   // the result use the matching FP64 scalar S = Widen<R>::type
-  // TC: colour sum on the tensor cores (float, SYNC, 128-thread CTAs; cta: the CTA's TcCta)
+  // TC: colour sum on the tensor cores (float, SYNC, CTAs of 128 or 256 threads; cta: the CTA's TcCta)
   // hpart, hparts: helicity split, this call sums every hparts-th evaluated helicity
   // from the hpart-th on (the caller adds the hparts partial sums)
   template <typename R, bool SYNC = false, bool TC = false>

@@ -294,14 +294,15 @@ int mf_create(mf_ctx** out, const mf_config* cfg, const double* pdf_grid_host, i
         return bail(MF_ERR_CUDA);
     // global kinematics store of the heavy integrand: up to 4 CTAs per SM of 256 queued events
     c->kin_ctas = 4 * c->n_sm;
-    if (cudaMalloc(&c->d_kin, (size_t)c->kin_ctas * (KIN_NEXT_MAX * 4 + 1) * 256 * sizeof(double)) != cudaSuccess ||
-        cudaMalloc(&c->d_kin_bins, (size_t)c->kin_ctas * MAX_DIM * 256) != cudaSuccess)
+    if (cudaMalloc(&c->d_kin, (size_t)c->kin_ctas * (KIN_NEXT_MAX * 4 + 1) * KIN_CAP_UNIT * sizeof(double)) !=
+            cudaSuccess ||
+        cudaMalloc(&c->d_kin_bins, (size_t)c->kin_ctas * MAX_DIM * KIN_CAP_UNIT) != cudaSuccess)
         return bail(MF_ERR_CUDA);
     if (cudaMemcpy(c->d_pdf, pdf_grid_host, npdf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(MF_ERR_CUDA);
     for (int p : { MF_EE_MUMU, MF_GG_TT, MF_GG_TTG, MF_GG_TTGG, MF_UU_TT, MF_UG_TTU }) {
         const ProcOps* o = proc_ops(p);
-        if (o->prepare(std::max(o->smem(0, MAX_BINS, nx * nq), o->smem(1, MAX_BINS, nx * nq))) != cudaSuccess) return bail(MF_ERR_CUDA);
+        if (o->prepare(o->smem(1, MAX_BINS, nx * nq), o->smem(0, MAX_BINS, nx * nq)) != cudaSuccess) return bail(MF_ERR_CUDA);
     }
     *out = c;
     return MF_OK;

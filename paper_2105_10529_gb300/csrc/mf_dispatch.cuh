@@ -9,7 +9,7 @@ namespace mf {
 struct ProcOps {
     int D, NEXT, npdf, tpb;
     size_t (*smem)(int prec, int nb, int npv);
-    cudaError_t (*prepare)(size_t smem);
+    cudaError_t (*prepare)(size_t smem_mixed, size_t smem_fp64);
     cudaError_t (*occupancy)(int prec, size_t smem, int* blocks_per_sm);
     // sched: 0 free-running warps, 1 CTA barrier between helicities (heavy processes),
     // 2 barrier and the colour sum on the tensor cores (processes with P::TC, mixed precision);
@@ -65,30 +65,37 @@ const ProcOps* ops_gg_ttgg();
 const ProcOps* ops_uu_tt();
 const ProcOps* ops_ug_ttu();
 
-// integrand launch helpers for a process trait P with TPB threads per CTA
-template <class P, int TPB>
+// integrand launch helpers for a process trait P: T32 threads per CTA for the
+// mixed-precision kernels, T64 for the FP64 ones
+template <class P, int T32, int T64 = T32>
 struct IntegrandOps {
+    template <typename R> static constexpr int tpb() { return sizeof(R) == 4 ? T32 : T64; }
     static size_t smem(int prec, int nb, int npv)
     {
-        return prec ? SmemLayout<P, float, TPB>::bytes(nb, npv) : SmemLayout<P, double, TPB>::bytes(nb, npv);
+        return prec ? SmemLayout<P, float, T32>::bytes(nb, npv) : SmemLayout<P, double, T64>::bytes(nb, npv);
     }
     static constexpr bool HS = P::HEAVY;   // the barrier variant exists for heavy processes only
     static constexpr bool HT = P::TC;      // and the tensor-core colour sum for P::TC processes
     template <typename R, bool W, bool S>
-    static const void* fn() { return (const void*)integrand_kernel<P, R, TPB, W, S && HS>; }
+    static const void* fn() { return (const void*)integrand_kernel<P, R, tpb<R>(), W, S && HS>; }
     template <bool W>
-    static const void* fn_tc() { return (const void*)integrand_kernel<P, float, TPB, W, HT, HT>; }
+    static const void* fn_tc() { return (const void*)integrand_kernel<P, float, T32, W, HT, HT>; }
     // helicity split variants (mixed precision, barrier schedule, no per-event outputs)
-    static const void* fn_hs() { return (const void*)integrand_kernel<P, float, TPB, false, HS, false, HS ? 2 : 1>; }
-    static const void* fn_hs_tc() { return (const void*)integrand_kernel<P, float, TPB, false, HT, HT, HT ? 2 : 1>; }
-    static cudaError_t prepare(size_t sm)
+    static const void* fn_hs() { return (const void*)integrand_kernel<P, float, T32, false, HS, false, HS ? 2 : 1>; }
+    static const void* fn_hs_tc() { return (const void*)integrand_kernel<P, float, T32, false, HT, HT, HT ? 2 : 1>; }
+    // the dynamic shared memory of every variant of one precision (sm32, sm64: bytes)
+    static cudaError_t prepare(size_t sm32, size_t sm64)
     {
-        const void* fns[12] = { fn<double, false, false>(), fn<double, true, false>(), fn<float, false, false>(),
-                                fn<float, true, false>(), fn<double, false, true>(), fn<double, true, true>(),
-                                fn<float, false, true>(), fn<float, true, true>(), fn_tc<false>(), fn_tc<true>(),
-                                fn_hs(), fn_hs_tc() };
-        for (const void* f : fns) {
-            cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        const void* f32[8] = { fn<float, false, false>(), fn<float, true, false>(), fn<float, false, true>(),
+                               fn<float, true, true>(), fn_tc<false>(), fn_tc<true>(), fn_hs(), fn_hs_tc() };
+        const void* f64[4] = { fn<double, false, false>(), fn<double, true, false>(), fn<double, false, true>(),
+                               fn<double, true, true>() };
+        for (const void* f : f32) {
+            cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32);
+            if (e != cudaSuccess) return e;
+        }
+        for (const void* f : f64) {
+            cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm64);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -96,11 +103,12 @@ struct IntegrandOps {
     static cudaError_t occupancy(int prec, size_t sm, int* b)
     {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, prec ? fn<float, false, false>() : fn<double, false, false>(),
-                                                             TPB, sm);
+                                                             prec ? T32 : T64, sm);
     }
     template <typename R, bool W>
     static void launch(int sched, int hsplit, const KParams& kp, int nblk, size_t sm, cudaStream_t s)
     {
+        constexpr int TPB = tpb<R>();
         if constexpr (HS && sizeof(R) == 4 && !W) {
             if (hsplit == 2 && sched >= 1) {
                 if constexpr (HT) {

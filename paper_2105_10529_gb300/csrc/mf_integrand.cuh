@@ -20,6 +20,7 @@ namespace mf {
 constexpr double GEV2_TO_PB = 0.3893793721e9;   // (hbar c)^2 in pb GeV^2
 constexpr int MAX_DIM = 18;
 constexpr int KIN_NEXT_MAX = 6;      // largest process (2 -> 4) for the global kinematics store
+constexpr int KIN_CAP_UNIT = 256;    // ring entries per region of the global kinematics store
 constexpr int MAX_BINS = 64;
 
 struct EwParams { double e2, sw2, cw2, mz, wz; };
@@ -41,8 +42,9 @@ struct KParams {
     unsigned long long* counters;   // [0] events passing cuts, [1] non-finite weights zeroed
     unsigned* dev_err;      // raised when a bounded device wait runs out (nullable)
     // global storage of queued events' kinematics for heavy processes whose shared
-    // memory has no room for it (nullable): per CTA (blockIdx.x < kin_ctas)
-    // [NEXT_MAX 4 + 1][256] doubles and [D_MAX][256] bins
+    // memory has no room for it (nullable): kin_ctas regions of [NEXT_MAX 4 + 1]
+    // [KIN_CAP_UNIT] doubles and [D_MAX][KIN_CAP_UNIT] bins; a CTA whose ring holds
+    // u KIN_CAP_UNIT entries uses regions u b .. u b + u - 1 as one (CTA b)
     double* kin;
     uint8_t* kin_bins;
     int kin_ctas;
@@ -463,7 +465,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
                                                 long long step, long long end, double* out)
 {
     static_assert(HS == 1 || (HS == 2 && SYNC && !WRITE), "helicity split: pairs of lanes, barrier schedule");
-    static_assert(!TC || (P::TC && SYNC && TPB == 128 && sizeof(R) == 4),
+    static_assert(!TC || (P::TC && SYNC && (TPB == 128 || TPB == 256) && sizeof(R) == 4),
                   "tensor-core colour sum: float, barrier schedule, one TMEM lane per thread");
     constexpr int D = P::D, WARPS = TPB / 32;
     using L = SmemLayout<P, R, TPB>;
@@ -488,15 +490,17 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     const double* gpdf = kp.pdf;
     // batches read back the kinematics stored when the events were queued: in shared
     // memory (L::KIN), else for mixed precision in this CTA's global region (kp.kin)
-    constexpr bool GKIN = !L::KIN && !WRITE && sizeof(R) == 4 && CAP == 256;
+    constexpr bool GKIN = !L::KIN && !WRITE && sizeof(R) == 4 && CAP <= KIN_CAP_UNIT * 2;
     constexpr bool MAYREUSE = (L::KIN && !WRITE) || GKIN;
     bool reuse = L::KIN && !WRITE;
     if constexpr (GKIN) {
-        if (kp.kin != nullptr && (int)blockIdx.x < kp.kin_ctas) {
+        // kp.kin_ctas regions of KIN_CAP_UNIT entries; this CTA takes CAP / KIN_CAP_UNIT of them
+        constexpr int UNITS = (CAP + KIN_CAP_UNIT - 1) / KIN_CAP_UNIT;
+        if (kp.kin != nullptr && ((int)blockIdx.x + 1) * UNITS <= kp.kin_ctas) {
             reuse = true;
-            kpm = kp.kin + (size_t)blockIdx.x * (KIN_NEXT_MAX * 4 + 1) * 256;
+            kpm = kp.kin + (size_t)blockIdx.x * (KIN_NEXT_MAX * 4 + 1) * (UNITS * KIN_CAP_UNIT);
             kpref = kpm + P::NEXT * 4 * CAP;
-            kbins = kp.kin_bins + (size_t)blockIdx.x * MAX_DIM * 256;
+            kbins = kp.kin_bins + (size_t)blockIdx.x * MAX_DIM * (UNITS * KIN_CAP_UNIT);
         }
     }
 

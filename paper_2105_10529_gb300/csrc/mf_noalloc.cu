@@ -102,11 +102,7 @@ extern "C" int mf_vegas_pass_static(int process, const mf_config* cfg, double sq
     if (cudaGetDevice(&dev) != cudaSuccess) return MF_ERR_CUDA;
     const size_t sm = ops->smem(cfg->precision, nb, nx * nq);
     // allow this process's kernels the largest shared-memory size any argument set can need
-    {
-        const size_t need = ops->smem(0, MAX_BINS, 8192) > ops->smem(1, MAX_BINS, 8192) ? ops->smem(0, MAX_BINS, 8192)
-                                                                                        : ops->smem(1, MAX_BINS, 8192);
-        if (ops->prepare(need) != cudaSuccess) return MF_ERR_CUDA;
-    }
+    if (ops->prepare(ops->smem(1, MAX_BINS, 8192), ops->smem(0, MAX_BINS, 8192)) != cudaSuccess) return MF_ERR_CUDA;
     int n_sm = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MF_ERR_CUDA;
     if (ops->occupancy(cfg->precision, sm, &per_sm) != cudaSuccess || per_sm < 1) return MF_ERR_CUDA;

@@ -6,7 +6,10 @@
 namespace mf {
 namespace {
 using P = ProcTops<Me_gg_ttgg>;
-using I = IntegrandOps<P, 128>;
+// mixed precision: one 256-thread CTA per SM (255 registers a thread), whose
+// eight warps pass every helicity barrier together; FP64: 128 threads (its
+// per-thread slot is twice as large)
+using I = IntegrandOps<P, 256, 128>;
 
 cudaError_t evaluate(int prec, const double* mom, long long n, double* me2, double mt, double gs, const EwParams&,
                      int nblk, cudaStream_t s)
@@ -23,7 +26,7 @@ cudaError_t evaluate(int prec, const double* mom, long long n, double* me2, doub
     return cudaGetLastError();
 }
 
-const ProcOps kOps = { P::D, P::NEXT, P::NPDF, 128, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate };
+const ProcOps kOps = { P::D, P::NEXT, P::NPDF, 256, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate };
 }  // namespace
 
 const ProcOps* ops_gg_ttgg() { return &kOps; }

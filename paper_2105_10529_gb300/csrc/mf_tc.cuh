@@ -2,9 +2,10 @@
 //
 // Per helicity, |M_h|^2 = sum_ij Re(conj(J_i) C_ij J_j) = Re(J)^T C Re(J) +
 // Im(J)^T C Im(J) for the symmetric colour matrix C (Sec. 2.2: the colour
-// sum of the colour-flow amplitudes).  With 128 events per CTA (one per
-// thread) the products D = J C for all events form two dense
-// (128 x 24) x (24 x 24) contractions, one MMA group per helicity:
+// sum of the colour-flow amplitudes).  With one event per thread, every
+// group of 128 threads (warps 4g .. 4g+3) forms two dense (128 x 24) x
+// (24 x 24) contractions D = J C per helicity, on 128 TMEM columns of its
+// own (group g at column 128 g; CTAs of 128 or 256 threads):
 //
 //   A = J, one TMEM lane per event (the thread writes its own row with
 //       tcgen05.st), split into two bf16 pieces J = J1 + J2 + r with
@@ -26,8 +27,9 @@
 
 namespace mf {
 
-// TMEM columns of the CTA's allocation (lane = event/thread)
-constexpr uint32_t TC_COLS = 128;        // allocation: power of two >= 32
+// TMEM columns of one 128-thread group (lane = event/thread); a CTA of G
+// groups allocates G x 128 columns (a power of two)
+constexpr uint32_t TC_COLS = 128;
 constexpr uint32_t TC_A_RE1 = 0, TC_A_RE2 = 16, TC_A_IM1 = 32, TC_A_IM2 = 48;   // 16 columns each (32 bf16)
 constexpr uint32_t TC_D_RE = 64, TC_D_IM = 96;                                  // 32 FP32 columns each
 constexpr int TC_N = 32, TC_K = 32;      // padded N (output columns) and K of the contraction
@@ -79,16 +81,19 @@ __host__ __device__ constexpr uint32_t tc_idesc(int M, int N)
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// one warp: allocate TC_COLS columns, the address lands in *dst (shared memory)
-__device__ __forceinline__ void tc_alloc(uint32_t* dst)
+// 128-thread groups of this CTA (blockDim.x is 128 or 256)
+__device__ __forceinline__ uint32_t tc_groups() { return blockDim.x >> 7; }
+
+// one warp: allocate ncols columns, the address lands in *dst (shared memory)
+__device__ __forceinline__ void tc_alloc(uint32_t* dst, uint32_t ncols)
 {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)),
-                 "r"(TC_COLS)
+                 "r"(ncols)
                  : "memory");
 }
-__device__ __forceinline__ void tc_dealloc(uint32_t taddr)
+__device__ __forceinline__ void tc_dealloc(uint32_t taddr, uint32_t ncols)
 {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(TC_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
 }
 
 __device__ __forceinline__ void tc_st16(uint32_t taddr, const uint32_t (&v)[16])
@@ -206,7 +211,7 @@ __device__ __forceinline__ void tc_setup(TcCta* tc, const short* c54, unsigned* 
     // generic-proxy writes of B become visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (threadIdx.x < 32) {
-        tc_alloc(&tc->tmem);
+        tc_alloc(&tc->tmem, TC_COLS * tc_groups());
         // give up the right to allocate again: while a CTA holds it, no further
         // CTA of the kernel is placed on the SM
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -222,24 +227,26 @@ __device__ __forceinline__ void tc_teardown(TcCta* tc)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (threadIdx.x < 32) tc_dealloc(tc->tmem);
+    if (threadIdx.x < 32) tc_dealloc(tc->tmem, TC_COLS * tc_groups());
 }
 
-// TMEM address of this thread's lane at column 0 of the CTA's allocation
+// TMEM address of this thread's lane at column 0 of its group's columns: a
+// warp reaches lanes 32 (w mod 4) .. +31, the group w / 4 its own columns
 __device__ __forceinline__ uint32_t tc_lane(const TcCta* tc)
 {
-    return tc->tmem + ((uint32_t)((threadIdx.x >> 5) * 32) << 16);
+    const uint32_t warp = threadIdx.x >> 5;
+    return tc->tmem + (((warp & 3u) * 32u) << 16) + (warp >> 2) * TC_COLS;
 }
 
 // Colour sum of this thread's colour-flow amplitudes (jamp: NCOL complex in
 // shared memory, re/im interleaved), scaled by 54.  Every thread of the
-// 128-thread CTA calls it for the same helicity.  tc->err is set to 1 when a
-// wait runs out.
+// CTA (128 or 256 threads) calls it for the same helicity.  tc->err is set to
+// 1 when a wait runs out.
 template <int NCOL>
 __device__ __forceinline__ float tc_colour_sum(TcCta* tc, const volatile float* jamp)
 {
-    const int tid = threadIdx.x, warp = tid >> 5;
-    const uint32_t lane_base = tc->tmem + ((uint32_t)(warp * 32) << 16);
+    const int tid = threadIdx.x;
+    const uint32_t lane_base = tc_lane(tc);
     // parity of this call's completion, read by every thread before the barrier
     // after which thread 0 flips it
     const uint32_t parity = tc->phase & 1u;
@@ -279,20 +286,24 @@ __device__ __forceinline__ float tc_colour_sum(TcCta* tc, const volatile float* 
         tc->phase = parity ^ 1u;
         constexpr uint32_t idesc = tc_idesc(128, TC_N);
         const uint32_t b0 = smem_u32(tc->B);
-        // D_re = (A_re1 + A_re2) B, D_im = (A_im1 + A_im2) B; K = 32 in two steps of 16
+        // per group: D_re = (A_re1 + A_re2) B, D_im = (A_im1 + A_im2) B; K = 32 in two steps of 16
+        const uint32_t groups = tc_groups();
+        for (uint32_t g = 0; g < groups; ++g) {
+            const uint32_t base = tc->tmem + g * TC_COLS;
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {
-            const uint32_t d = tc->tmem + (part ? TC_D_IM : TC_D_RE);
-            const uint32_t a1 = tc->tmem + (part ? TC_A_IM1 : TC_A_RE1);
-            const uint32_t a2 = tc->tmem + (part ? TC_A_IM2 : TC_A_RE2);
+            for (int part = 0; part < 2; ++part) {
+                const uint32_t d = base + (part ? TC_D_IM : TC_D_RE);
+                const uint32_t a1 = base + (part ? TC_A_IM1 : TC_A_RE1);
+                const uint32_t a2 = base + (part ? TC_A_IM2 : TC_A_RE2);
 #pragma unroll
-            for (int ks = 0; ks < 2; ++ks) {
-                const uint64_t bd = tc_smem_desc(b0 + (uint32_t)ks * 1024u, 512u, 128u);
-                tc_mma_ts(d, a1 + 8u * ks, bd, idesc, ks > 0 ? 1u : 0u);
-                tc_mma_ts(d, a2 + 8u * ks, bd, idesc, 1u);
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint64_t bd = tc_smem_desc(b0 + (uint32_t)ks * 1024u, 512u, 128u);
+                    tc_mma_ts(d, a1 + 8u * ks, bd, idesc, ks > 0 ? 1u : 0u);
+                    tc_mma_ts(d, a2 + 8u * ks, bd, idesc, 1u);
+                }
             }
         }
-        tc_commit(&tc->mbar);
+        tc_commit(&tc->mbar);   // one arrival once every MMA above has completed
     }
     if (!mbar_wait(&tc->mbar, parity)) {
         tc->dead = 1u;

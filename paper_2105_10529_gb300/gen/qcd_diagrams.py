@@ -615,7 +615,7 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("  // SYNC: a CTA barrier after every helicity (every thread of the CTA must call)")
     src.append("  // R: float or double (or Dual of them for derivatives); the momenta, masses and")
     src.append("  // the result use the matching FP64 scalar S = Widen<R>::type")
-    src.append("  // TC: colour sum on the tensor cores (float, SYNC, 128-thread CTAs; cta: the CTA's TcCta)")
+    src.append("  // TC: colour sum on the tensor cores (float, SYNC, CTAs of 128 or 256 threads; cta: the CTA's TcCta)")
     src.append("  // hpart, hparts: helicity split, this call sums every hparts-th evaluated helicity")
     src.append("  // from the hpart-th on (the caller adds the hparts partial sums)")
     src.append("  template <typename R, bool SYNC = false, bool TC = false>")
