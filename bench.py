@@ -32,10 +32,10 @@ FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) per event of the mixed g g -> t tbar g g integrand with the
-# tensor-core colour sum, from the ncu capture summarised in
-# profiles/integrand_gg_ttgg_mixed_100k_ncu.txt (224.2 MB over 100k events; the traffic,
-# evicted local-memory lines, grows with the number of events)
-DRAM_BYTES_PER_EVENT_P3_TC = 2242.2
+# tensor-core colour sum (256-thread CTAs), from the dram__bytes capture in
+# profiles/launches_bench_gg_ttgg.txt (3.156 GB over 1e6 events; the traffic, evicted
+# local-memory lines, grows with the number of events)
+DRAM_BYTES_PER_EVENT_P3_TC = 3156.3
 
 
 def parse():
@@ -410,7 +410,7 @@ def run_ours(args):
                      "frac": achieved_tflops / fp32_peak,
                      "traffic": (DRAM_BYTES_PER_EVENT_P3_TC * N)
                      if (args.sched is None or args.sched == 2) and (args.hsplit or 1) == 1 else None,
-                     "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of a 1e5-event ncu capture of the "
+                     "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of a 1e6-event ncu capture of the "
                                       "same kernel, scaled to the launch's events (spill lines; grows with events)",
                      "kernel": "integrand_kernel<gg_ttgg, float>",
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz (nominal units and max clock)",
