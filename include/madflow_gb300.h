@@ -148,10 +148,11 @@ int mf_set_precision(struct mf_ctx *ctx, int precision);
 int mf_set_schedule(struct mf_ctx *ctx, int sched);
 /* Helicity split of the heavy integrand (no counterpart in the paper, whose
  * kernels give one thread per event): parts = 1 (the default), one thread
- * sums every helicity of its event; parts = 2, two adjacent threads share an
- * event, each summing every other one of the helicities the matrix element
- * evaluates (Sec. 2.2's helicity sum split in two), and the pair adds its
- * halves; a CTA then holds half as many events at a time.  Applies to
+ * sums every helicity of its event; parts = 2, two threads of a CTA (t and
+ * t + half the CTA, in different warps) share an event, each summing every
+ * other one of the helicities the matrix element evaluates (Sec. 2.2's
+ * helicity sum split in two), and the pair adds its halves; a CTA then
+ * holds half as many events at a time.  Applies to
  * g g -> t tbar g and g g -> t tbar g g in MF_MIXED under schedules 1 and 2,
  * in mf_vegas_pass without per-event outputs and in mf_integrate; elsewhere
  * it acts as 1.  Results differ from parts = 1 by FP32 rounding only.
