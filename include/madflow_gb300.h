@@ -146,6 +146,32 @@ int mf_set_precision(struct mf_ctx *ctx, int precision);
  * as 1.  Schedules 0 and 1 give identical results; 2 differs from them by FP32
  * rounding.  MF_ERR_ARG for other values. */
 int mf_set_schedule(struct mf_ctx *ctx, int sched);
+/* Observable histogram (Sec. 2.1: the pipeline ends in histogram accumulation;
+ * Sec. 3, Fig. 2: the leading-order cross section differential in p_T): the
+ * transverse momentum of the first final-state particle (the top quark in the
+ * top-pair processes, the muon in e+ e- -> mu+ mu-), sqrt(px^2 + py^2) in FP64,
+ * in n_bins (1 .. 100) uniform bins on [lo, hi).  Bin j = 0 holds p_T < lo
+ * (and a non-finite p_T), j = n_bins + 1 holds p_T >= hi, else
+ * j = 1 + floor((p_T - lo) n_bins / (hi - lo)). */
+typedef struct mf_obs {
+    int n_bins;
+    double lo, hi;
+} mf_obs;
+/* Enables (spec with n_bins >= 1) or disables (NULL or n_bins = 0) the
+ * histogram for the following mf_integrate calls (not the batch or pass
+ * calls).  Every iteration fills sum w/N per bin from the same weights as
+ * the integral; the iterations combine with the integral's inverse-variance
+ * weights, so the n_bins + 2 bins add up to sigma.  Allocates about 10 MB on
+ * first use.  MF_ERR_ARG for a bad spec (n_bins outside 0..100, hi <= lo,
+ * non-finite edges). */
+int mf_set_observable(struct mf_ctx *ctx, const mf_obs *spec);
+/* The histogram of the last mf_integrate since mf_set_observable (host
+ * buffers, caller-owned, each nullable): hist_host [n_bins + 2] in pb per bin
+ * (divide by the bin width for d sigma / d p_T), err_host [n_bins + 2] their
+ * Monte Carlo errors, iter_host [n_iter][n_bins + 2][2] each iteration's
+ * (sum w/N, variance) per bin.  MF_ERR_ARG when there is none. */
+int mf_get_observable(struct mf_ctx *ctx, double *hist_host, double *err_host, double *iter_host);
+
 /* Helicity split of the heavy integrand (no counterpart in the paper, whose
  * kernels give one thread per event): parts = 1 (the default), one thread
  * sums every helicity of its event; parts = 2, two threads of a CTA (t and

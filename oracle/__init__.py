@@ -92,6 +92,12 @@ def lib():
                                   _U8, _U8, _D, _D, _D, C.POINTER(C.c_int64), C.c_int]),
             "or_integrate": (C.c_int, [C.c_int, C.POINTER(OrParams), C.POINTER(OrPdf), C.c_int64, C.c_int,
                                        _D, _D, C.POINTER(OrResult), C.c_int]),
+            "or_obs_bin": (C.c_int, [C.c_double, C.c_double, C.c_int, C.c_double, C.c_double]),
+            "or_pass_obs": (C.c_int, [C.c_int, C.POINTER(OrParams), C.POINTER(OrPdf), _D, C.c_int64, C.c_uint32,
+                                      C.c_int, C.c_double, C.c_double, _D, _D, _D, C.c_int]),
+            "or_integrate_obs": (C.c_int, [C.c_int, C.POINTER(OrParams), C.POINTER(OrPdf), C.c_int64, C.c_int,
+                                           C.c_int, C.c_double, C.c_double, _D, _D, _D, C.POINTER(OrResult),
+                                           C.c_int]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -294,6 +300,36 @@ def vegas_pass(proc: int, phys, pdf: Pdf, grid: np.ndarray, n: int, iteration: i
     if rc:
         raise RuntimeError(f"or_pass failed ({rc})")
     return dict(sum_w=sw.value, sum_w2=sw2.value, hist=hist, n_pass=npass.value, mask=mo)
+
+
+def obs_bin(px: float, py: float, nobs: int, lo: float, hi: float) -> int:
+    return lib().or_obs_bin(px, py, nobs, lo, hi)
+
+
+def vegas_pass_obs(proc: int, phys, pdf: Pdf, grid: np.ndarray, n: int, nobs: int, lo: float, hi: float,
+                   iteration: int = 0, n_threads: int = 0):
+    """One pass with the observable histogram: obs [nobs + 2][2] (sum w/N, sum (w/N)^2)."""
+    P = params(phys); g = _f64(grid)
+    sw, sw2 = C.c_double(), C.c_double()
+    obs = np.zeros((nobs + 2, 2))
+    rc = lib().or_pass_obs(proc, C.byref(P), C.byref(pdf.c), _dp(g), n, iteration, nobs, lo, hi,
+                           C.byref(sw), C.byref(sw2), _dp(obs), n_threads)
+    if rc:
+        raise RuntimeError(f"or_pass_obs failed ({rc})")
+    return dict(sum_w=sw.value, sum_w2=sw2.value, obs=obs)
+
+
+def integrate_obs(proc: int, phys, pdf: Pdf, n: int, n_iter: int, nobs: int, lo: float, hi: float,
+                  n_threads: int = 0):
+    """VEGAS integration with the observable histogram (combined over iterations)."""
+    P = params(phys); res = OrResult()
+    h = np.zeros(nobs + 2); e = np.zeros(nobs + 2); it = np.zeros((n_iter, nobs + 2, 2))
+    rc = lib().or_integrate_obs(proc, C.byref(P), C.byref(pdf.c), n, n_iter, nobs, lo, hi, _dp(h), _dp(e),
+                                _dp(it), C.byref(res), n_threads)
+    if rc:
+        raise RuntimeError(f"or_integrate_obs failed ({rc})")
+    return dict(sigma=res.sigma, error=res.error, chi2dof=res.chi2dof, n_pass=res.n_pass,
+                hist=h, err=e, per_iter=it)
 
 
 def integrate(proc: int, phys, pdf: Pdf, n: int, n_iter: int, n_threads: int = 0):

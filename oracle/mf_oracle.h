@@ -152,6 +152,11 @@ int or_event(int proc, const or_params *P, const or_pdf *pdf, const double *grid
 int or_pass(int proc, const or_params *P, const or_pdf *pdf, const double *grid, int64_t n,
             uint32_t iteration, const uint8_t *mask_in, uint8_t *mask_out,
             double *sum_w, double *sum_w2, double *hist, int64_t *n_pass, int n_threads);
+/* observable histogram (p_T of the first final-state particle), see or_integrand.c */
+int or_obs_bin(double px, double py, int nobs, double lo, double hi);
+int or_pass_obs(int proc, const or_params *P, const or_pdf *pdf, const double *grid, int64_t n,
+                uint32_t iteration, int nobs, double lo, double hi, double *sum_w, double *sum_w2,
+                double *obs, int n_threads);
 
 typedef struct {
     double sigma, error, chi2dof;
@@ -162,6 +167,11 @@ typedef struct {
  * final grid; per_iter (nullable) receives I_k, var_k pairs. */
 int or_integrate(int proc, const or_params *P, const or_pdf *pdf, int64_t n, int n_iter,
                  double *grid_io, double *per_iter, or_result *res, int n_threads);
+/* the same with the observable histogram: obs_hist, obs_err [nobs + 2] combined over the
+ * iterations, obs_iter (nullable) [n_iter][nobs + 2][2] per-iteration (sum w/N, variance) */
+int or_integrate_obs(int proc, const or_params *P, const or_pdf *pdf, int64_t n, int n_iter,
+                     int nobs, double lo, double hi, double *obs_hist, double *obs_err, double *obs_iter,
+                     or_result *res, int n_threads);
 
 #ifdef __cplusplus
 }

@@ -108,9 +108,28 @@ int or_event(int proc, const or_params *P, const or_pdf *pdf, const double *grid
     return 0;
 }
 
-int or_pass(int proc, const or_params *P, const or_pdf *pdf, const double *grid, int64_t n,
-            uint32_t iteration, const uint8_t *mask_in, uint8_t *mask_out,
-            double *sum_w, double *sum_w2, double *hist, int64_t *n_pass, int n_threads)
+/*
+ * Observable histogram (the pipeline's histogram accumulation, Sec. 2.1; the
+ * p_T distribution of Sec. 3, Fig. 2): the transverse momentum of the first
+ * final-state particle, p_T = sqrt(px^2 + py^2), in nobs uniform bins on
+ * [lo, hi) with an underflow bin 0 (also for a non-finite p_T) and an
+ * overflow bin nobs + 1.
+ */
+int or_obs_bin(double px, double py, int nobs, double lo, double hi)
+{
+    double pt = sqrt(px * px + py * py);
+    double inv_w = (double)nobs / (hi - lo);
+    if (!(pt >= lo)) return 0;
+    double t = (pt - lo) * inv_w;
+    if (!(t < (double)nobs)) return nobs + 1;
+    return 1 + (int)t;
+}
+
+/* one pass; with nobs > 0 also obs[(nobs + 2) * 2]: per bin sum w/N and sum (w/N)^2 */
+static int pass_impl(int proc, const or_params *P, const or_pdf *pdf, const double *grid, int64_t n,
+                     uint32_t iteration, const uint8_t *mask_in, uint8_t *mask_out,
+                     double *sum_w, double *sum_w2, double *hist, int64_t *n_pass, int n_threads,
+                     int nobs, double lo, double hi, double *obs)
 {
     or_proc_info info;
     if (or_proc_info_get(proc, &info) || n <= 0) return 1;
@@ -118,7 +137,8 @@ int or_pass(int proc, const or_params *P, const or_pdf *pdf, const double *grid,
     double *w = (double *)malloc(sizeof(double) * (size_t)n);
     uint8_t *bins = (uint8_t *)malloc((size_t)n * (size_t)D);
     uint8_t *mk = (uint8_t *)malloc((size_t)n);
-    if (!w || !bins || !mk) { free(w); free(bins); free(mk); return 2; }
+    int *ob = (int *)malloc(sizeof(int) * (size_t)n);
+    if (!w || !bins || !mk || !ob) { free(w); free(bins); free(mk); free(ob); return 2; }
     /* one serial event first so that lazily built colour tables exist before the threads start */
     {
         or_event_out o;
@@ -138,10 +158,12 @@ int or_pass(int proc, const or_params *P, const or_pdf *pdf, const double *grid,
         w[e] = o.w;
         mk[e] = (uint8_t)o.mask;
         memcpy(bins + (size_t)e * D, o.bins, (size_t)D);
+        ob[e] = nobs > 0 ? or_obs_bin(o.p[2][1], o.p[2][2], nobs, lo, hi) : 0;
     }
     double sw = 0.0, sw2 = 0.0;
     int64_t np = 0;
     if (hist) memset(hist, 0, sizeof(double) * (size_t)D * nb);
+    if (nobs > 0) memset(obs, 0, sizeof(double) * 2 * (size_t)(nobs + 2));
     for (int64_t e = 0; e < n; ++e) {
         double we = w[e] / (double)n;
         double w2 = we * we;
@@ -149,11 +171,90 @@ int or_pass(int proc, const or_params *P, const or_pdf *pdf, const double *grid,
         np += mk[e];
         if (hist)
             for (int d = 0; d < D; ++d) hist[d * nb + bins[(size_t)e * D + d]] += w2;
+        if (nobs > 0) { obs[2 * ob[e]] += we; obs[2 * ob[e] + 1] += w2; }
         if (mask_out) mask_out[e] = mk[e];
     }
     *sum_w = sw; *sum_w2 = sw2;
     if (n_pass) *n_pass = np;
-    free(w); free(bins); free(mk);
+    free(w); free(bins); free(mk); free(ob);
+    return 0;
+}
+
+int or_pass(int proc, const or_params *P, const or_pdf *pdf, const double *grid, int64_t n,
+            uint32_t iteration, const uint8_t *mask_in, uint8_t *mask_out,
+            double *sum_w, double *sum_w2, double *hist, int64_t *n_pass, int n_threads)
+{
+    return pass_impl(proc, P, pdf, grid, n, iteration, mask_in, mask_out, sum_w, sum_w2, hist, n_pass,
+                     n_threads, 0, 0.0, 1.0, NULL);
+}
+
+int or_pass_obs(int proc, const or_params *P, const or_pdf *pdf, const double *grid, int64_t n,
+                uint32_t iteration, int nobs, double lo, double hi, double *sum_w, double *sum_w2,
+                double *obs, int n_threads)
+{
+    if (nobs < 1 || !(hi > lo) || !obs) return 1;
+    return pass_impl(proc, P, pdf, grid, n, iteration, NULL, NULL, sum_w, sum_w2, NULL, NULL, n_threads,
+                     nobs, lo, hi, obs);
+}
+
+/*
+ * VEGAS integration with the observable histogram.  Reading (the paper does
+ * not say how iterations combine into a distribution): every iteration fills
+ * per bin I_jk = sum w/N and its variance V_jk = (N sum (w/N)^2 - I_jk^2)/(N-1);
+ * the bins combine with the integral's inverse-variance weights
+ * l_k = (1/V_k) / sum_i (1/V_i): H_j = sum_k l_k I_jk, err_j^2 = sum_k l_k^2 V_jk,
+ * so that sum_j H_j equals the combined cross section.
+ */
+int or_integrate_obs(int proc, const or_params *P, const or_pdf *pdf, int64_t n, int n_iter,
+                     int nobs, double lo, double hi, double *obs_hist, double *obs_err, double *obs_iter,
+                     or_result *res, int n_threads)
+{
+    or_proc_info info;
+    if (or_proc_info_get(proc, &info) || n < 2 || n_iter < 1 || nobs < 1 || !(hi > lo)) return 1;
+    int D = info.dim, nb = P->n_bins, n2 = nobs + 2;
+    double *grid = (double *)malloc(sizeof(double) * (size_t)D * (nb + 1));
+    double *hist = (double *)malloc(sizeof(double) * (size_t)D * nb);
+    double *I = (double *)malloc(sizeof(double) * (size_t)n_iter);
+    double *V = (double *)malloc(sizeof(double) * (size_t)n_iter);
+    double *IJ = (double *)malloc(sizeof(double) * (size_t)n_iter * n2);
+    double *VJ = (double *)malloc(sizeof(double) * (size_t)n_iter * n2);
+    double *obs = (double *)malloc(sizeof(double) * 2 * (size_t)n2);
+    or_vegas_init(grid, D, nb);
+    int64_t np_tot = 0;
+    for (int it = 0; it < n_iter; ++it) {
+        double sw, sw2; int64_t np;
+        int rc = pass_impl(proc, P, pdf, grid, n, (uint32_t)it, NULL, NULL, &sw, &sw2, hist, &np, n_threads,
+                           nobs, lo, hi, obs);
+        if (rc) { free(grid); free(hist); free(I); free(V); free(IJ); free(VJ); free(obs); return rc; }
+        I[it] = sw;
+        V[it] = ((double)n * sw2 - sw * sw) / (double)(n - 1);
+        for (int j = 0; j < n2; ++j) {
+            double a = obs[2 * j], b = obs[2 * j + 1];
+            IJ[(size_t)it * n2 + j] = a;
+            VJ[(size_t)it * n2 + j] = ((double)n * b - a * a) / (double)(n - 1);
+            if (obs_iter) {
+                obs_iter[((size_t)it * n2 + j) * 2] = a;
+                obs_iter[((size_t)it * n2 + j) * 2 + 1] = VJ[(size_t)it * n2 + j];
+            }
+        }
+        np_tot += np;
+        if (it < n_iter - 1) or_vegas_refine(hist, grid, D, nb, P->alpha);
+    }
+    or_vegas_combine(n_iter, I, V, &res->sigma, &res->error, &res->chi2dof);
+    res->n_pass = np_tot;
+    double inv_sum = 0.0;
+    for (int k = 0; k < n_iter; ++k) inv_sum += 1.0 / V[k];
+    for (int j = 0; j < n2; ++j) {
+        double h = 0.0, e2 = 0.0;
+        for (int k = 0; k < n_iter; ++k) {
+            double l = (1.0 / V[k]) / inv_sum;
+            h += l * IJ[(size_t)k * n2 + j];
+            e2 += l * l * VJ[(size_t)k * n2 + j];
+        }
+        obs_hist[j] = h;
+        obs_err[j] = sqrt(e2 > 0.0 ? e2 : 0.0);
+    }
+    free(grid); free(hist); free(I); free(V); free(IJ); free(VJ); free(obs);
     return 0;
 }
 

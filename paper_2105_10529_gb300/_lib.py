@@ -35,6 +35,10 @@ class MfCuts(C.Structure):
     _fields_ = [("pt_min", C.c_double), ("eta_max", C.c_double), ("dr_min", C.c_double)]
 
 
+class MfObs(C.Structure):
+    _fields_ = [("n_bins", C.c_int), ("lo", C.c_double), ("hi", C.c_double)]
+
+
 class MfEventArrays(C.Structure):
     _fields_ = [("u", C.c_void_p), ("x", C.c_void_p), ("bins", C.c_void_p), ("w", C.c_void_p),
                 ("mask", C.c_void_p), ("me2", C.c_void_p), ("momenta", C.c_void_p)]
@@ -68,6 +72,8 @@ def lib():
             "mf_set_pdf": (C.c_int, [vp, dp]),
             "mf_set_schedule": (C.c_int, [vp, C.c_int]),
             "mf_set_helicity_split": (C.c_int, [vp, C.c_int]),
+            "mf_set_observable": (C.c_int, [vp, C.POINTER(MfObs)]),
+            "mf_get_observable": (C.c_int, [vp, dp, dp, dp]),
             "mf_device_status": (C.c_int, [vp]),
             "mf_selftest_wait": (C.c_int, [vp, C.c_uint]),
             "mf_integrate": (C.c_int, [vp, C.c_int, C.c_double, C.POINTER(MfCuts), i64, C.c_int, C.c_int,
@@ -99,6 +105,6 @@ def lib():
 
 def exported_symbols():
     return ["mf_default_config", "mf_process_info", "mf_create", "mf_destroy", "mf_last_error",
-            "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_set_helicity_split", "mf_device_status", "mf_selftest_wait", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
+            "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_set_helicity_split", "mf_set_observable", "mf_get_observable", "mf_device_status", "mf_selftest_wait", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
             "mf_vegas_pass_static", "mf_set_couplings", "mf_vegas_pass_grad",
             "mf_integrate_batch", "mf_batch_grad", "mf_set_batch_schedule", "mf_autotune_batch"]

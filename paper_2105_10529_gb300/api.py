@@ -9,7 +9,7 @@ from typing import Optional
 import numpy as np
 
 from . import _lib
-from ._lib import MfConfig, MfCuts, MfError, MfEventArrays, MfResult
+from ._lib import MfConfig, MfCuts, MfError, MfEventArrays, MfObs, MfResult
 from . import inputs as IN
 
 
@@ -101,6 +101,25 @@ class Context:
     def set_helicity_split(self, parts: int):
         """Threads per event of the heavy integrand (1 or 2), as mf_set_helicity_split."""
         _check(self.ptr, _lib.lib().mf_set_helicity_split(self.ptr, parts))
+
+    def set_observable(self, n_bins: int = 0, lo: float = 0.0, hi: float = 0.0):
+        """p_T histogram of the first final-state particle for the next integrate calls
+        (n_bins = 0 disables), as mf_set_observable."""
+        spec = MfObs(int(n_bins), float(lo), float(hi)) if n_bins else None
+        self._obs_n = 0
+        _check(self.ptr, _lib.lib().mf_set_observable(self.ptr, C.byref(spec) if spec is not None else None))
+        self._obs_n = int(n_bins)
+
+    def observable(self, n_iter: Optional[int] = None):
+        """The last integrate call's histogram: (pb per bin [n+2], errors [n+2]) and, with
+        n_iter, each iteration's [n_iter][n+2][2] (sum w/N, variance)."""
+        n2 = getattr(self, "_obs_n", 0) + 2
+        h = np.zeros(n2); e = np.zeros(n2)
+        it = np.zeros((n_iter, n2, 2)) if n_iter else None
+        dp = C.POINTER(C.c_double)
+        _check(self.ptr, _lib.lib().mf_get_observable(self.ptr, h.ctypes.data_as(dp), e.ctypes.data_as(dp),
+                                                      it.ctypes.data_as(dp) if it is not None else None))
+        return (h, e) if it is None else (h, e, it)
 
     def device_status(self):
         """Raises MfError(MF_ERR_TIMEOUT) if a bounded device wait ran out since the last check."""

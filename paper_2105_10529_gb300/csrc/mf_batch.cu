@@ -238,7 +238,7 @@ int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, 
             pl.rows[i] = (n_events[i] + te - 1) / te;
         } else {
             int per_sm = 0;
-            const size_t sm = ops->smem(MF_MIXED, nb, npv);
+            const size_t sm = ops->smem(MF_MIXED, nb, npv, false);
             MF_BCUDA(c, ops->occupancy(MF_MIXED, sm, &per_sm));
             if (per_sm < 1) return mf_fail(c, MF_ERR_CUDA, "integrand kernel does not fit on an SM");
             const long long want = (n_events[i] + sch.tile_light - 1) / sch.tile_light;
@@ -286,7 +286,7 @@ int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, 
             sl.ops = ops;
             sl.kp = kp;
             sl.nblk = (int)pl.rows[i];
-            sl.sm = ops->smem(MF_MIXED, nb, npv);
+            sl.sm = ops->smem(MF_MIXED, nb, npv, false);
             pl.side.push_back(sl);
         }
     }

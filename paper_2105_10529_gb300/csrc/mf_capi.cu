@@ -86,6 +86,21 @@ __global__ void wait_selftest_kernel(unsigned* err, unsigned limit)
     if (!mbar_wait(&mbar, 0, limit)) atomicExch(err, 1u);
 }
 
+// Observable of one pass: bin j of the per-CTA rows summed in CTA order by thread j,
+// stored as (I_j, var_j) with the integral's variance estimate (n sum (w/N)^2 - I^2)/(n - 1)
+__global__ void obs_reduce_kernel(const double* rows, int nblk, int nbins2, long long n, double* out)
+{
+    for (int j = threadIdx.x; j < nbins2; j += blockDim.x) {
+        double I = 0.0, I2 = 0.0;
+        for (int b = 0; b < nblk; ++b) {
+            I += rows[(size_t)b * 2 * nbins2 + 2 * j];
+            I2 += rows[(size_t)b * 2 * nbins2 + 2 * j + 1];
+        }
+        out[2 * j] = I;
+        out[2 * j + 1] = ((double)n * I2 - I * I) / (double)(n - 1);
+    }
+}
+
 // refinement from already reduced pass sums [2 + D nb]
 __global__ void refine_kernel(const double* sums, int D, int nb, double alpha, double* grid)
 {
@@ -302,7 +317,8 @@ int mf_create(mf_ctx** out, const mf_config* cfg, const double* pdf_grid_host, i
         return bail(MF_ERR_CUDA);
     for (int p : { MF_EE_MUMU, MF_GG_TT, MF_GG_TTG, MF_GG_TTGG, MF_UU_TT, MF_UG_TTU }) {
         const ProcOps* o = proc_ops(p);
-        if (o->prepare(o->smem(1, MAX_BINS, nx * nq), o->smem(0, MAX_BINS, nx * nq)) != cudaSuccess) return bail(MF_ERR_CUDA);
+        if (o->prepare(o->smem(1, MAX_BINS, nx * nq, true), o->smem(0, MAX_BINS, nx * nq, true)) != cudaSuccess)
+            return bail(MF_ERR_CUDA);
     }
     *out = c;
     return MF_OK;
@@ -321,6 +337,8 @@ void mf_destroy(mf_ctx* c)
     cudaFree(c->d_err);
     cudaFree(c->d_kin);
     cudaFree(c->d_kin_bins);
+    cudaFree(c->d_obs_partials);
+    cudaFree(c->d_obs_iter);
     cudaFree(c->d_kps);
     cudaFree(c->d_tiles);
     cudaFree(c->d_bgrids);
@@ -368,6 +386,40 @@ int mf_set_schedule(mf_ctx* c, int sched)
     return MF_OK;
 }
 
+int mf_set_observable(mf_ctx* c, const mf_obs* spec)
+{
+    if (!c) return MF_ERR_ARG;
+    c->obs_iters = 0;
+    if (!spec || spec->n_bins == 0) {
+        c->obs_n = 0;
+        return MF_OK;
+    }
+    if (spec->n_bins < 1 || spec->n_bins > MAX_OBS_BINS || !std::isfinite(spec->lo) || !std::isfinite(spec->hi) ||
+        !(spec->hi > spec->lo))
+        return fail(c, MF_ERR_ARG, "mf_set_observable: bad histogram");
+    if (!c->d_obs_partials) {
+        MF_CUDA(c, cudaMalloc(&c->d_obs_partials, sizeof(double) * (size_t)c->max_blocks * 2 * (MAX_OBS_BINS + 2)));
+        MF_CUDA(c, cudaMalloc(&c->d_obs_iter, sizeof(double) * (size_t)MAX_ITER * 2 * (MAX_OBS_BINS + 2)));
+    }
+    c->obs_n = spec->n_bins;
+    c->obs_lo = spec->lo;
+    c->obs_hi = spec->hi;
+    c->obs_inv_w = (double)spec->n_bins / (spec->hi - spec->lo);
+    return MF_OK;
+}
+
+int mf_get_observable(mf_ctx* c, double* hist_host, double* err_host, double* iter_host)
+{
+    if (!c) return MF_ERR_ARG;
+    if (c->obs_n == 0 || c->obs_iters == 0)
+        return fail(c, MF_ERR_ARG, "mf_get_observable: no histogram since mf_set_observable");
+    const size_t n2 = (size_t)c->obs_n + 2;
+    if (hist_host) std::memcpy(hist_host, c->obs_hist.data(), n2 * sizeof(double));
+    if (err_host) std::memcpy(err_host, c->obs_err.data(), n2 * sizeof(double));
+    if (iter_host) std::memcpy(iter_host, c->obs_iter_host.data(), (size_t)c->obs_iters * 2 * n2 * sizeof(double));
+    return MF_OK;
+}
+
 int mf_set_helicity_split(mf_ctx* c, int parts)
 {
     if (!c || (parts != 1 && parts != 2)) return MF_ERR_ARG;
@@ -406,7 +458,7 @@ int mf_vegas_pass(mf_ctx* c, int process, double sqrt_s, const double* grid_dev,
         kp.ev_u = ev->u; kp.ev_x = ev->x; kp.ev_bins = ev->bins; kp.ev_w = ev->w;
         kp.ev_mask = ev->mask; kp.ev_me2 = ev->me2; kp.ev_p = ev->momenta;
     }
-    const size_t sm = ops->smem(c->cfg.precision, c->cfg.n_bins, c->nx * c->nq);
+    const size_t sm = ops->smem(c->cfg.precision, c->cfg.n_bins, c->nx * c->nq, false);
     int nblk = 0;
     rc = pick_blocks(c, ops, sm, c->cfg.precision, &nblk);
     if (rc) return rc;
@@ -453,7 +505,15 @@ int mf_integrate(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, lon
     kp.ev_offset = 0;
     kp.inv_n = 1.0 / (double)n_events;
     kp.grid = c->d_grid;
-    const size_t sm = ops->smem(c->cfg.precision, nb, c->nx * c->nq);
+    const bool obs = c->obs_n > 0;
+    const int nobs2 = c->obs_n + 2;
+    if (obs) {
+        kp.nobs = c->obs_n;
+        kp.obs_lo = c->obs_lo;
+        kp.obs_inv_w = c->obs_inv_w;
+        kp.obs_partials = c->d_obs_partials;
+    }
+    const size_t sm = ops->smem(c->cfg.precision, nb, c->nx * c->nq, obs);
     int nblk = 0;
     rc = pick_blocks(c, ops, sm, c->cfg.precision, &nblk);
     if (rc) return rc;
@@ -469,6 +529,11 @@ int mf_integrate(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, lon
         finish_pass_kernel<<<1, 1024, ncol * sizeof(double), c->stream>>>(
             c->d_partials, nblk, D, nb, n_events, c->cfg.alpha, it < n_iter - 1, c->d_grid, c->d_iter + 2 * it, nullptr);
         MF_CUDA(c, cudaGetLastError());
+        if (obs) {
+            obs_reduce_kernel<<<1, 128, 0, c->stream>>>(c->d_obs_partials, nblk, nobs2, n_events,
+                                                        c->d_obs_iter + (size_t)it * 2 * nobs2);
+            MF_CUDA(c, cudaGetLastError());
+        }
     }
     if (want_grads) {
         // one derivative pass at the final grid on fresh random numbers (Philox iteration n_iter)
@@ -492,6 +557,11 @@ int mf_integrate(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, lon
     if (grid_host)
         MF_CUDA(c, cudaMemcpyAsync(grid_host, c->d_grid, (size_t)D * (nb + 1) * sizeof(double), cudaMemcpyDeviceToHost,
                                    c->stream));
+    if (obs) {
+        c->obs_iter_host.resize((size_t)n_iter * 2 * nobs2);
+        MF_CUDA(c, cudaMemcpyAsync(c->obs_iter_host.data(), c->d_obs_iter, c->obs_iter_host.size() * sizeof(double),
+                                   cudaMemcpyDeviceToHost, c->stream));
+    }
     MF_CUDA(c, cudaStreamSynchronize(c->stream));
     if (take_device_error(c)) return fail(c, MF_ERR_TIMEOUT, "a bounded device wait ran out");
     double sw = 0.0, swi = 0.0;
@@ -505,6 +575,22 @@ int mf_integrate(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, lon
     for (int k = 0; k < n_iter; ++k) chi2 += (iters[2 * k] - mean) * (iters[2 * k] - mean) / iters[2 * k + 1];
     out->sigma_pb = mean;
     out->error_pb = std::sqrt(1.0 / sw);
+    if (obs) {
+        // every bin combines its iterations with the integral's weights lambda_k = (1/var_k) / sum_j (1/var_j),
+        // so that the bins add up to the combined cross section
+        c->obs_hist.assign(nobs2, 0.0);
+        c->obs_err.assign(nobs2, 0.0);
+        for (int k = 0; k < n_iter; ++k) {
+            const double lam = (1.0 / iters[2 * k + 1]) / sw;
+            const double* r = c->obs_iter_host.data() + (size_t)k * 2 * nobs2;
+            for (int j = 0; j < nobs2; ++j) {
+                c->obs_hist[j] += lam * r[2 * j];
+                c->obs_err[j] += lam * lam * r[2 * j + 1];
+            }
+        }
+        for (int j = 0; j < nobs2; ++j) c->obs_err[j] = std::sqrt(c->obs_err[j] > 0.0 ? c->obs_err[j] : 0.0);
+        c->obs_iters = n_iter;
+    }
     out->chi2_dof = n_iter > 1 ? chi2 / (n_iter - 1) : 0.0;
     out->n_events_total = n_events * (long long)n_iter;
     out->n_pass = (long long)cnt[0];

@@ -26,6 +26,13 @@ struct mf_ctx {
     int max_blocks = 0;
     int sched = 2;                   // integrand schedule (see mf_set_schedule)
     int hsplit = 1;                  // lanes per event in the heavy integrand (see mf_set_helicity_split)
+    // observable histogram (mf_set_observable): n bins from obs_lo, obs_inv_w = n / (hi - lo)
+    int obs_n = 0;
+    double obs_lo = 0.0, obs_hi = 0.0, obs_inv_w = 0.0;
+    double* d_obs_partials = nullptr;   // [max_blocks][obs_n + 2][2]
+    double* d_obs_iter = nullptr;       // [MAX_ITER][obs_n + 2][2]: per-bin (I, var) of each iteration
+    int obs_iters = 0;                  // iterations behind obs_hist (0: none yet)
+    std::vector<double> obs_hist, obs_err, obs_iter_host;
     std::string err;
     // batched channels: workspace, tuned schedule and the cached CUDA graph
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture and replay (high priority)

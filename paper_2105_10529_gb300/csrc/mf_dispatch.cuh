@@ -8,7 +8,7 @@ namespace mf {
 
 struct ProcOps {
     int D, NEXT, npdf, tpb;
-    size_t (*smem)(int prec, int nb, int npv);
+    size_t (*smem)(int prec, int nb, int npv, bool obs);   // obs: room for the observable histogram
     cudaError_t (*prepare)(size_t smem_mixed, size_t smem_fp64);
     cudaError_t (*occupancy)(int prec, size_t smem, int* blocks_per_sm);
     // sched: 0 free-running warps, 1 CTA barrier between helicities (heavy processes),
@@ -70,9 +70,9 @@ const ProcOps* ops_ug_ttu();
 template <class P, int T32, int T64 = T32>
 struct IntegrandOps {
     template <typename R> static constexpr int tpb() { return sizeof(R) == 4 ? T32 : T64; }
-    static size_t smem(int prec, int nb, int npv)
+    static size_t smem(int prec, int nb, int npv, bool obs)
     {
-        return prec ? SmemLayout<P, float, T32>::bytes(nb, npv) : SmemLayout<P, double, T64>::bytes(nb, npv);
+        return prec ? SmemLayout<P, float, T32>::bytes(nb, npv, obs) : SmemLayout<P, double, T64>::bytes(nb, npv, obs);
     }
     static constexpr bool HS = P::HEAVY;   // the barrier variant exists for heavy processes only
     static constexpr bool HT = P::TC;      // and the tensor-core colour sum for P::TC processes

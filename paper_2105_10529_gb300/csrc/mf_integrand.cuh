@@ -22,6 +22,7 @@ constexpr int MAX_DIM = 18;
 constexpr int KIN_NEXT_MAX = 6;      // largest process (2 -> 4) for the global kinematics store
 constexpr int KIN_CAP_UNIT = 256;    // ring entries per region of the global kinematics store
 constexpr int MAX_BINS = 64;
+constexpr int MAX_OBS_BINS = 100;    // observable histogram: regular bins (plus under- and overflow)
 
 struct EwParams { double e2, sw2, cw2, mz, wz; };
 
@@ -49,9 +50,28 @@ struct KParams {
     uint8_t* kin_bins;
     int kin_ctas;
     const uint8_t* mask_in; // frozen cut masks (nullable)
+    // observable histogram (nobs = 0: off): transverse momentum of the first final-state
+    // particle in nobs uniform bins from obs_lo, obs_inv_w = nobs / (hi - lo); per CTA
+    // (blockIdx.x) a row of [nobs + 2][2] sums (sum w/N, sum (w/N)^2; bin 0 underflow,
+    // nobs + 1 overflow) in obs_partials
+    int nobs;
+    double obs_lo, obs_inv_w;
+    double* obs_partials;
     // per-event outputs (nullable; only the inspection kernel writes them)
     double* ev_u; double* ev_x; uint8_t* ev_bins; double* ev_w; uint8_t* ev_mask; double* ev_me2; double* ev_p;
 };
+
+// Observable bin of an event: 0 below obs_lo (and for a non-finite p_T), nobs + 1 at or
+// above the upper edge, else 1 + floor((p_T - obs_lo) obs_inv_w).  p_T of particle 2
+// (the first final-state particle; the top quark in the top-pair processes), in FP64.
+__device__ __forceinline__ int obs_bin(const KParams& kp, double px, double py)
+{
+    const double pt = sqrt(px * px + py * py);
+    if (!(pt >= kp.obs_lo)) return 0;
+    const double t = (pt - kp.obs_lo) * kp.obs_inv_w;
+    if (!(t < (double)kp.nobs)) return kp.nobs + 1;
+    return 1 + (int)t;
+}
 
 // ------------------------------------------------------------------ e+ e- -> mu+ mu-
 
@@ -321,7 +341,19 @@ struct SmemLayout {
     {
         return al(P::TC ? tc_off(nb, npv) + sizeof(TcCta) : red_off(nb, npv) + sizeof(double) * 2 * WARPS);
     }
-    static __host__ __device__ size_t bytes(int nb, int npv) { return slot_off(nb, npv) + (size_t)TPB * P::template slot_bytes<R>(); }
+    // observable histograms [NHIST][MAX_OBS_BINS + 2][2], then per-thread w/N and (heavy) bin buffers
+    static constexpr size_t OBS_ROW = 2 * (MAX_OBS_BINS + 2);
+    static __host__ __device__ size_t obs_off(int nb, int npv)
+    {
+        return al(slot_off(nb, npv) + (size_t)TPB * P::template slot_bytes<R>());
+    }
+    static __host__ __device__ size_t obs_w_off(int nb, int npv) { return obs_off(nb, npv) + sizeof(double) * NHIST * OBS_ROW; }
+    static __host__ __device__ size_t obs_b_off(int nb, int npv) { return obs_w_off(nb, npv) + sizeof(double) * TPB; }
+    // obs: with the observable region (kernels touch it only when kp.nobs > 0)
+    static __host__ __device__ size_t bytes(int nb, int npv, bool obs = false)
+    {
+        return obs ? al(obs_b_off(nb, npv) + sizeof(int16_t) * TPB) : obs_off(nb, npv);
+    }
 };
 
 // end of the kernel: two sums per CTA (warp trees, then warps in order), the
@@ -358,6 +390,20 @@ __device__ __forceinline__ void write_partials(const KParams& kp, double sw, dou
         double s = 0.0;
         for (int w = 0; w < NHIST; ++w) s += shist[w * D * nb + i];
         out[2 + i] = s;
+    }
+}
+
+// this CTA's observable row: the NHIST histograms summed in order
+template <int NHIST, size_t OBS_ROW>
+__device__ __forceinline__ void write_obs_partials(const KParams& kp, const double* sobs)
+{
+    if (kp.nobs <= 0) return;
+    const int n2 = 2 * (kp.nobs + 2);
+    double* row = kp.obs_partials + (size_t)blockIdx.x * n2;
+    for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+        double s = 0.0;
+        for (int w = 0; w < NHIST; ++w) s += sobs[w * OBS_ROW + i];
+        row[i] = s;
     }
 }
 
@@ -400,13 +446,19 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
     double* shist = reinterpret_cast<double*>(smem_raw + L::hist_off(nb, npv));
     double* svbuf = reinterpret_cast<double*>(smem_raw + L::vbuf_off(nb, npv));
     double* sred = reinterpret_cast<double*>(smem_raw + L::red_off(nb, npv));
+    double* sobs = reinterpret_cast<double*>(smem_raw + L::obs_off(nb, npv));
+    double* swbuf = reinterpret_cast<double*>(smem_raw + L::obs_w_off(nb, npv));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool obs = kp.nobs > 0;
 
     for (int i = tid; i < D * (nb + 1); i += TPB) sgrid[i] = kp.grid[i];
     for (int i = tid; i < L::NHIST * D * nb; i += TPB) shist[i] = 0.0;
+    if (obs)
+        for (int i = tid; i < L::NHIST * (int)L::OBS_ROW; i += TPB) sobs[i] = 0.0;
     __syncthreads();
 
     double* myhist = shist + warp * D * nb;
+    double* myobs = sobs + warp * L::OBS_ROW;
     double sw = 0.0, sw2 = 0.0;
     unsigned long long npass = 0, nnan = 0;
     const long long rounds = end > first ? (end - first + step - 1) / step : 0;
@@ -442,9 +494,27 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
                 myhist[d * nb + o.bins[d]] += s;
             }
         }
+        if (obs) {
+            // observable: the same leader scheme on the event's p_T bin (sum w/N and sum (w/N)^2)
+            swbuf[tid] = wn;
+            __syncwarp();
+            const int ob = valid ? obs_bin(kp, pm[2][1], pm[2][2]) : 0;
+            const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)ob);
+            if (lane == __ffs(peers) - 1) {
+                double s1 = 0.0, s2 = 0.0;
+                for (unsigned m = peers; m; m &= m - 1) {
+                    const int l = warp * 32 + __ffs(m) - 1;
+                    s1 += swbuf[l];
+                    s2 += svbuf[l];
+                }
+                myobs[2 * ob] += s1;
+                myobs[2 * ob + 1] += s2;
+            }
+        }
         __syncwarp();
     }
     write_partials<P, TPB, L::NHIST>(kp, sw, sw2, npass, nnan, sred, shist, out);
+    write_obs_partials<L::NHIST, L::OBS_ROW>(kp, sobs);
 }
 
 // Heavy processes (expensive matrix elements): kinematics first, then the
@@ -485,6 +555,10 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     double* kpref = kpm + P::NEXT * 4 * CAP;                                      // [CAP]
     uint8_t* kbins = reinterpret_cast<uint8_t*>(kpref + CAP);                     // [D][CAP]
     double* sred = reinterpret_cast<double*>(smem_raw + L::red_off(nb, npv));
+    double* sobs = reinterpret_cast<double*>(smem_raw + L::obs_off(nb, npv));
+    double* swbuf = reinterpret_cast<double*>(smem_raw + L::obs_w_off(nb, npv));
+    int16_t* sobin = reinterpret_cast<int16_t*>(smem_raw + L::obs_b_off(nb, npv));
+    const bool obs = kp.nobs > 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     void* slot = (void*)(smem_raw + L::slot_off(nb, npv) + (size_t)tid * P::template slot_bytes<R>());
     const double* gpdf = kp.pdf;
@@ -506,6 +580,8 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
 
     for (int i = tid; i < D * (nb + 1); i += TPB) sgrid[i] = kp.grid[i];
     for (int i = tid; i < D * nb; i += TPB) shist[i] = 0.0;
+    if (obs)
+        for (int i = tid; i < (int)L::OBS_ROW; i += TPB) sobs[i] = 0.0;
     if (tid == 0) { scount[0] = 0; scount[1] = 0; }
     TcCta* tc = nullptr;
     if constexpr (TC) {
@@ -607,11 +683,20 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             svbuf[tid] = v;
 #pragma unroll
             for (int d = 0; d < D; ++d) sbins[d * TPB + tid] = o.bins[d];
+            if (obs) {
+                swbuf[tid] = wn;
+                sobin[tid] = (int16_t)(owner ? obs_bin(kp, pm[2][1], pm[2][2]) : 0);
+            }
             __syncthreads();
             if (tid < D) {
                 double* h = shist + tid * nb;
                 const uint8_t* b = sbins + tid * TPB;
                 for (int t = 0; t < take; ++t) h[b[t]] += svbuf[t];   // the owners, in queue order
+            } else if (obs && tid == D) {
+                for (int t = 0; t < take; ++t) {                     // the observable, in queue order
+                    sobs[2 * sobin[t]] += swbuf[t];
+                    sobs[2 * sobin[t] + 1] += svbuf[t];
+                }
             }
             // the batch's entries leave the ring
             __syncthreads();
@@ -621,6 +706,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     }
     if constexpr (TC) tc_teardown(tc);
     write_partials<P, TPB, 1>(kp, sw, sw2, npass, nnan, sred, shist, out);
+    write_obs_partials<1, L::OBS_ROW>(kp, sobs);
 }
 
 // ------------------------------------------------------------------ the fused integrand kernel

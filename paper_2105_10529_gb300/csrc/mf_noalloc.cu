@@ -100,9 +100,10 @@ extern "C" int mf_vegas_pass_static(int process, const mf_config* cfg, double sq
     if (scratch_on_current_device(&scratch) != MF_OK) return MF_ERR_CUDA;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MF_ERR_CUDA;
-    const size_t sm = ops->smem(cfg->precision, nb, nx * nq);
+    const size_t sm = ops->smem(cfg->precision, nb, nx * nq, false);
     // allow this process's kernels the largest shared-memory size any argument set can need
-    if (ops->prepare(ops->smem(1, MAX_BINS, 8192), ops->smem(0, MAX_BINS, 8192)) != cudaSuccess) return MF_ERR_CUDA;
+    if (ops->prepare(ops->smem(1, MAX_BINS, 8192, false), ops->smem(0, MAX_BINS, 8192, false)) != cudaSuccess)
+        return MF_ERR_CUDA;
     int n_sm = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MF_ERR_CUDA;
     if (ops->occupancy(cfg->precision, sm, &per_sm) != cudaSuccess || per_sm < 1) return MF_ERR_CUDA;
