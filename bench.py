@@ -142,14 +142,18 @@ def run_batch(ctx, phys, IN, n_iter):
     ns = [int(n) for _, n in IN.BATCH_CHANNELS]
     names = {IN.GG_TT: "gg_tt", IN.UU_TT: "uu_tt", IN.GG_TTG: "gg_ttg", IN.UG_TTU: "ug_ttu", IN.GG_TTGG: "gg_ttgg"}
     choice = ctx.autotune_batch(procs, ns, phys.sqrt_s)
-    per_mode = {}
-    for mode in (0, 1):
-        ctx.set_batch_schedule(mode, *choice[1:])
+
+    def timed(sch):
+        ctx.set_batch_schedule(*sch)
         ctx.integrate_batch(procs, ns, phys.sqrt_s, n_iter)          # graph capture
         t0 = time.perf_counter()
         r = ctx.integrate_batch(procs, ns, phys.sqrt_s, n_iter)
-        per_mode[mode] = (time.perf_counter() - t0, r)
-    t_batch, (tot, chans) = per_mode[choice[0]]
+        return time.perf_counter() - t0, r
+
+    # the chosen schedule, and one representative schedule per mode
+    t_batch, (tot, chans) = timed(choice)
+    per_mode = {0: timed((0, 1, 4096, 4096, 0, 1)), 1: timed((1, 1, 4096, 4096, 0, 1)),
+                2: timed((2, 2, 4096, 4096, 0, 1))}
     ctx.set_batch_schedule(*choice)
     ctx.integrate_batch(procs, ns, phys.sqrt_s, n_iter)               # grids of the chosen schedule
     g = ctx.batch_grad(procs, ns, phys.sqrt_s, 1000)
@@ -165,10 +169,13 @@ def run_batch(ctx, phys, IN, n_iter):
             "events_per_s": ev / t_batch, "s_per_call": t_batch,
             "sequential_events_per_s": ev / t_seq, "speedup_vs_sequential": t_seq / t_batch,
             "sequential_s_by_channel": {names[p]: t for p, t in zip(procs, t_ch)},
-            "schedule": {"mode": ["one launch", "split"][choice[0]], "helicity_barrier": choice[1],
+            "schedule": {"mode": ["one launch", "split", "per-channel kernels"][choice[0]],
+                         "integrand_schedule": choice[1],
                          "tile_heavy": choice[2], "tile_light": choice[3], "ctas_per_sm": choice[4],
                          "helicity_split": choice[5]},
-            "events_per_s_by_mode": {"one launch": ev / per_mode[0][0], "split": ev / per_mode[1][0]},
+            "events_per_s_by_mode": {"one launch (0, 1, 4096, 4096)": ev / per_mode[0][0],
+                                     "split (1, 1, 4096, 4096)": ev / per_mode[1][0],
+                                     "per-channel kernels (2, 2, -, 4096)": ev / per_mode[2][0]},
             "sigma_pb": tot["sigma"], "error_pb": tot["error"],
             "channels": {names[p]: {"sigma_pb": c["sigma"], "error_pb": c["error"], "chi2dof": c["chi2dof"],
                                     "sequential_sigma_pb": q["sigma"]} for p, c, q in zip(procs, chans, seq)},

@@ -299,7 +299,10 @@ int mf_evaluate(struct mf_ctx *ctx, int process, const double *momenta_dev, long
  * launch for all channels; 1 = the g g -> t tbar g and t tbar g g channels
  * in the persistent launch on a high-priority stream and the cheaper
  * channels as their own integrand kernels on a forked low-priority stream,
- * which fill the SMs as the expensive work runs out.  All iterations
+ * which fill the SMs as the expensive work runs out; 2 = every channel as
+ * its own integrand kernel in the single-process launch configuration, the
+ * g g -> t tbar g(g) channels on the high-priority stream (in mode 2 these
+ * run a single-process pass's kernel, not persistent tiles).  All iterations
  * (launches, reductions, refinements) are captured once as a CUDA graph on a
  * private stream and replayed while the channel list, sizes, sqrt_s, n_iter,
  * couplings and schedule stay the same.  The schedule changes how sums are
@@ -333,14 +336,16 @@ int mf_batch_grad(struct mf_ctx *ctx, int n_ch, const int *processes, const long
                   const mf_cuts *cuts, unsigned int iteration, double *out_host);
 
 /* Sets the mf_integrate_batch schedule explicitly (no counterpart in the
- * paper): mode 0/1 (one launch / split, see mf_integrate_batch), sched 0/1
- * (helicity barrier off/on in the g g -> t tbar g(g) matrix elements),
+ * paper): mode 0/1/2 (one launch / split / per-channel kernels, see
+ * mf_integrate_batch), sched 0/1 (helicity barrier off/on in the
+ * g g -> t tbar g(g) matrix elements; in mode 2 also 2, the integrand
+ * schedule with the tensor-core colour sum, as mf_set_schedule),
  * tile_heavy and tile_light in [32, 2^26] events per work item for the
  * g g -> t tbar g(g) channels and for the others (in the split mode, the
  * other channels' kernels get one CTA per tile_light events), ctas_per_sm in
  * [0, 16] (0 = as many as fit; values above that are clamped), hsplit 1 or 2
  * (helicity split of the g g -> t tbar g(g) channels as mf_set_helicity_split;
- * 2 needs sched 1).  MF_ERR_ARG outside these ranges.  Defaults: 0, 1, 4096,
+ * 2 needs sched 1; modes 0 and 1 only).  MF_ERR_ARG outside these ranges.  Defaults: 0, 1, 4096,
  * 4096, 0, 1. */
 int mf_set_batch_schedule(struct mf_ctx *ctx, int mode, int sched, long long tile_heavy, long long tile_light,
                           int ctas_per_sm, int hsplit);
@@ -348,8 +353,9 @@ int mf_set_batch_schedule(struct mf_ctx *ctx, int mode, int sched, long long til
 /* Launch-schedule autotuner for mf_integrate_batch (no counterpart in the
  * paper).  Times one iteration of the given channels and sizes at uniform
  * grids for every mode {0, 1} x (helicity barrier, helicity split) {(0, 1),
- * (1, 1), (1, 2)} x tile_heavy {1024, 2048, 4096} x tile_light {2048, 4096}
- * (CTAs per SM as fit; 36 candidates) and keeps the fastest for later
+ * (1, 1), (1, 2)} x tile_heavy {1024, 2048, 4096} x tile_light {2048, 4096},
+ * and mode 2 x sched {1, 2} x tile_light {2048, 4096} (CTAs per SM as fit;
+ * 40 candidates) and keeps the fastest for later
  * mf_integrate_batch calls on this context.  choice_host [6] (nullable)
  * receives (mode, sched, tile_heavy, tile_light, ctas_per_sm, hsplit), the
  * arguments of mf_set_batch_schedule.  Arguments as mf_integrate_batch; the cuts are the

@@ -11,14 +11,19 @@
 // does not depend on which CTA ran which tile.  Items are handed out most
 // expensive channel first, so that the cheap tiles fill the end.
 //
-// Two schedules:
+// Three schedules:
 //   0  one persistent launch over every channel;
 //   1  split: the 2 -> 3 and 2 -> 4 gluon channels (255 registers a thread)
 //      in the persistent launch on a high-priority stream, the cheaper
 //      channels as their own integrand kernels (fewer registers, more
 //      resident warps) on a low-priority stream forked from it; their CTAs
 //      take the SMs that the persistent CTAs leave when the expensive work
-//      runs out.
+//      runs out;
+//   2  every channel as its own integrand kernel, in the launch
+//      configuration of a single-process pass (g g -> t tbar g g: 256-thread
+//      CTAs and, with sched 2, the tensor-core colour sum): the 2 -> 3 and
+//      2 -> 4 gluon channels one after the other on the high-priority stream,
+//      the others on the forked low-priority stream.
 #include <cuda_runtime.h>
 #include <algorithm>
 #include <cmath>
@@ -182,13 +187,15 @@ const void* batch_fn(const Schedule& sch)
     return sch.hsplit == 2 ? (const void*)batch_kernel<true, 2> : (const void*)batch_kernel<true, 1>;
 }
 
-// a cheaper channel of the split schedule: its own integrand kernel
+// a channel run as its own integrand kernel (schedules 1 and 2)
 struct SideLaunch {
     int ch;
     const ProcOps* ops;
     KParams kp;
     int nblk;
     size_t sm;
+    bool high;    // on the high-priority stream (schedule 2's expensive channels)
+    int sched;    // integrand schedule of the kernel
 };
 
 struct Plan {
@@ -232,10 +239,17 @@ int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, 
     size_t tile_doubles = 0;
     for (int i = 0; i < n_ch; ++i) {
         const ProcOps* ops = mf_proc_ops(procs[i]);
-        in_kernel[i] = sch.mode == 0 || heavy_channel(procs[i]);
+        in_kernel[i] = sch.mode == 0 || (sch.mode == 1 && heavy_channel(procs[i]));
         if (in_kernel[i]) {
             const long long te = heavy_channel(procs[i]) ? sch.tile_heavy : sch.tile_light;
             pl.rows[i] = (n_events[i] + te - 1) / te;
+        } else if (heavy_channel(procs[i])) {
+            // schedule 2: as many CTAs as fit, as in a single-process pass
+            int per_sm = 0;
+            const size_t sm = ops->smem(MF_MIXED, nb, npv, false);
+            MF_BCUDA(c, ops->occupancy(MF_MIXED, sm, &per_sm));
+            if (per_sm < 1) return mf_fail(c, MF_ERR_CUDA, "integrand kernel does not fit on an SM");
+            pl.rows[i] = std::min((long long)per_sm * c->n_sm, (long long)c->max_blocks);
         } else {
             int per_sm = 0;
             const size_t sm = ops->smem(MF_MIXED, nb, npv, false);
@@ -287,6 +301,8 @@ int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, 
             sl.kp = kp;
             sl.nblk = (int)pl.rows[i];
             sl.sm = ops->smem(MF_MIXED, nb, npv, false);
+            sl.high = heavy_channel(procs[i]);
+            sl.sched = sl.high ? sch.sched : 0;
             pl.side.push_back(sl);
         }
     }
@@ -327,7 +343,8 @@ int reset_batch(mf_ctx* c, const Plan& pl, cudaStream_t s)
 int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s, cudaStream_t low)
 {
     const int nb = c->cfg.n_bins;
-    const bool fork = !pl.side.empty();
+    bool fork = false;
+    for (const SideLaunch& sl : pl.side) fork |= !sl.high;
     if (fork) {
         MF_BCUDA(c, cudaEventRecord(c->ev_cap, s));
         MF_BCUDA(c, cudaStreamWaitEvent(low, c->ev_cap, 0));
@@ -342,7 +359,7 @@ int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s, c
     }
     for (SideLaunch& sl : pl.side) {
         sl.kp.iteration = (unsigned)it;
-        MF_BCUDA(c, sl.ops->integrand(MF_MIXED, false, pl.sch.sched, 1, sl.kp, sl.nblk, sl.sm, low));
+        MF_BCUDA(c, sl.ops->integrand(MF_MIXED, false, sl.sched, 1, sl.kp, sl.nblk, sl.sm, sl.high ? s : low));
     }
     if (fork) {
         MF_BCUDA(c, cudaEventRecord(c->ev_join, low));
@@ -359,11 +376,17 @@ int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s, c
     return MF_OK;
 }
 
-// The persistent kernels run at the stream's high priority and the side
-// kernels at the low one; set on the captured nodes explicitly and honoured
-// through cudaGraphInstantiateFlagUseNodePriority.
-int set_node_priorities(mf_ctx* c, cudaGraph_t g)
+// The persistent kernels (and schedule 2's expensive channels) run at the
+// stream's high priority and the other kernels at the low one; set on the
+// captured nodes explicitly and honoured through
+// cudaGraphInstantiateFlagUseNodePriority.
+int set_node_priorities(mf_ctx* c, cudaGraph_t g, const Plan& pl)
 {
+    // high: the persistent kernels and schedule 2's expensive channels
+    std::vector<const void*> hi_fns = { (const void*)batch_kernel<true, 1>, (const void*)batch_kernel<true, 2>,
+                                        (const void*)batch_kernel<false, 1> };
+    for (const SideLaunch& sl : pl.side)
+        if (sl.high) hi_fns.push_back(sl.ops->kernel(MF_MIXED, false, sl.sched, 1));
     int least = 0, greatest = 0;
     MF_BCUDA(c, cudaDeviceGetStreamPriorityRange(&least, &greatest));
     size_t n = 0;
@@ -376,8 +399,7 @@ int set_node_priorities(mf_ctx* c, cudaGraph_t g)
         if (ty != cudaGraphNodeTypeKernel) continue;
         cudaKernelNodeParams kp;
         MF_BCUDA(c, cudaGraphKernelNodeGetParams(nd, &kp));
-        const bool hi = kp.func == (void*)batch_kernel<true, 1> || kp.func == (void*)batch_kernel<true, 2> ||
-                        kp.func == (void*)batch_kernel<false, 1>;
+        const bool hi = std::find(hi_fns.begin(), hi_fns.end(), (const void*)kp.func) != hi_fns.end();
         cudaLaunchAttributeValue v;
         std::memset(&v, 0, sizeof(v));
         v.priority = hi ? greatest : least;
@@ -502,7 +524,7 @@ int mf_integrate_batch(mf_ctx* c, int n_ch, const int* processes, const long lon
         for (int it = 0; it < n_iter && erc == MF_OK; ++it)
             erc = enqueue_iteration(c, pl, it, n_iter, c->cap_stream, c->cap_low);
         cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
-        if (erc == MF_OK && ce == cudaSuccess) erc = set_node_priorities(c, g);
+        if (erc == MF_OK && ce == cudaSuccess) erc = set_node_priorities(c, g, pl);
         if (erc) { if (g) cudaGraphDestroy(g); return erc; }
         if (ce != cudaSuccess) return mf_fail(c, MF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
         ce = cudaGraphInstantiateWithFlags(&c->graph, g, cudaGraphInstantiateFlagUseNodePriority);
@@ -581,9 +603,9 @@ int mf_set_batch_schedule(mf_ctx* c, int mode, int sched, long long tile_heavy, 
                           int hsplit)
 {
     if (!c) return MF_ERR_ARG;
-    if ((mode != 0 && mode != 1) || (sched != 0 && sched != 1) || tile_heavy < 32 || tile_heavy > (1LL << 26) ||
-        tile_light < 32 || tile_light > (1LL << 26) || ctas_per_sm < 0 || ctas_per_sm > 16 ||
-        (hsplit != 1 && hsplit != 2) || (hsplit == 2 && sched != 1))
+    if (mode < 0 || mode > 2 || sched < 0 || sched > 2 || (sched == 2 && mode != 2) || tile_heavy < 32 ||
+        tile_heavy > (1LL << 26) || tile_light < 32 || tile_light > (1LL << 26) || ctas_per_sm < 0 ||
+        ctas_per_sm > 16 || (hsplit != 1 && hsplit != 2) || (hsplit == 2 && (sched != 1 || mode == 2)))
         return mf_fail(c, MF_ERR_ARG, "mf_set_batch_schedule: bad argument");
     c->b_hsplit = hsplit;
     c->b_mode = mode;
@@ -608,13 +630,16 @@ int mf_autotune_batch(mf_ctx* c, int n_ch, const int* processes, const long long
                 for (long long th : { 1024LL, 2048LL, 4096LL })
                     for (long long tl : { 2048LL, 4096LL })
                         cand.push_back(Schedule{ mode, sched, 0, th, tl, hs });
+    // every channel as its own kernel: FMA or tensor-core colour sum for the expensive ones
+    for (int sched = 1; sched <= 2; ++sched)
+        for (long long tl : { 2048LL, 4096LL }) cand.push_back(Schedule{ 2, sched, 0, 4096, tl, 1 });
     float best = 1e30f;
     Schedule pick = current_schedule(c);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     MF_BCUDA(c, cudaEventCreate(&e0));
     MF_BCUDA(c, cudaEventCreate(&e1));
     int rc = MF_OK;
-    bool warmed[2] = { false, false };
+    bool warmed[3] = { false, false, false };
     for (const Schedule& s : cand) {
         Plan pl;
         rc = make_plan(c, n_ch, processes, n_events, sqrt_s, nullptr, s, pl);

@@ -19,6 +19,8 @@ struct ProcOps {
                              cudaStream_t s);
     cudaError_t (*evaluate)(int prec, const double* mom, long long n, double* me2, double mt, double gs,
                             const EwParams& ew, int nblk, cudaStream_t s);
+    // the integrand kernel (function) that integrand() launches with these settings
+    const void* (*kernel)(int prec, bool write, int sched, int hsplit);
 };
 
 // Derivative kernels of one process, built in their own translation units.
@@ -105,42 +107,36 @@ struct IntegrandOps {
         return cudaOccupancyMaxActiveBlocksPerMultiprocessor(b, prec ? fn<float, false, false>() : fn<double, false, false>(),
                                                              prec ? T32 : T64, sm);
     }
+    // the kernel that a launch with these settings runs
     template <typename R, bool W>
-    static void launch(int sched, int hsplit, const KParams& kp, int nblk, size_t sm, cudaStream_t s)
+    static const void* pick(int sched, int hsplit)
     {
         constexpr int TPB = tpb<R>();
         if constexpr (HS && sizeof(R) == 4 && !W) {
             if (hsplit == 2 && sched >= 1) {
                 if constexpr (HT) {
-                    if (sched == 2) {
-                        integrand_kernel<P, float, TPB, false, true, true, 2><<<nblk, TPB, sm, s>>>(kp);
-                        return;
-                    }
+                    if (sched == 2) return (const void*)integrand_kernel<P, float, TPB, false, true, true, 2>;
                 }
-                integrand_kernel<P, float, TPB, false, true, false, 2><<<nblk, TPB, sm, s>>>(kp);
-                return;
+                return (const void*)integrand_kernel<P, float, TPB, false, true, false, 2>;
             }
         }
         if constexpr (HT && sizeof(R) == 4) {
-            if (sched == 2) {
-                integrand_kernel<P, float, TPB, W, true, true><<<nblk, TPB, sm, s>>>(kp);
-                return;
-            }
+            if (sched == 2) return (const void*)integrand_kernel<P, float, TPB, W, true, true>;
         }
-        if (sched && HS) integrand_kernel<P, R, TPB, W, HS><<<nblk, TPB, sm, s>>>(kp);
-        else integrand_kernel<P, R, TPB, W, false><<<nblk, TPB, sm, s>>>(kp);
+        if (sched && HS) return (const void*)integrand_kernel<P, R, TPB, W, HS>;
+        return (const void*)integrand_kernel<P, R, TPB, W, false>;
+    }
+    static const void* kernel(int prec, bool write, int sched, int hsplit)
+    {
+        if (prec) return write ? pick<float, true>(sched, hsplit) : pick<float, false>(sched, hsplit);
+        return write ? pick<double, true>(sched, hsplit) : pick<double, false>(sched, hsplit);
     }
     static cudaError_t integrand(int prec, bool write, int sched, int hsplit, const KParams& kp, int nblk, size_t sm,
                                  cudaStream_t s)
     {
-        if (prec) {
-            if (write) launch<float, true>(sched, hsplit, kp, nblk, sm, s);
-            else launch<float, false>(sched, hsplit, kp, nblk, sm, s);
-        } else {
-            if (write) launch<double, true>(sched, hsplit, kp, nblk, sm, s);
-            else launch<double, false>(sched, hsplit, kp, nblk, sm, s);
-        }
-        return cudaGetLastError();
+        KParams arg = kp;
+        void* args[1] = { &arg };
+        return cudaLaunchKernel(kernel(prec, write, sched, hsplit), dim3(nblk), dim3(prec ? T32 : T64), args, sm, s);
     }
 };
 
