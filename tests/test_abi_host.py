@@ -69,3 +69,27 @@ def test_generated_headers_are_current():
         assert open(os.path.join(OUT, f"me_{name}.cuh")).read() == src
         assert st["n_diag"] == {2: 3, 3: 16, 4: 123}[k]
         assert st["ncol"] == {2: 2, 3: 6, 4: 24}[k]
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the built CUDA library every entry point raises; nothing falls
+    back to a CPU path (checked in a fresh interpreter whose library path
+    points at an empty directory)."""
+    import subprocess
+    import sys
+    code = (
+        "import paper_2105_10529_gb300._lib as L\n"
+        f"L.LIB_PATH = {str(tmp_path / 'absent.so')!r}\n"
+        "from paper_2105_10529_gb300 import inputs as IN\n"
+        "from paper_2105_10529_gb300.api import Context, process_info\n"
+        "for f in (lambda: process_info(IN.GG_TT), lambda: Context(IN.Physics(), IN.make_pdf_grid())):\n"
+        "    try:\n"
+        "        f()\n"
+        "    except RuntimeError as e:\n"
+        "        assert 'no CPU fallback' in str(e), e\n"
+        "    else:\n"
+        "        raise SystemExit('no error without the library')\n"
+        "print('ok')\n")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "-c", code], cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0 and r.stdout.strip().endswith("ok"), r.stdout + r.stderr
