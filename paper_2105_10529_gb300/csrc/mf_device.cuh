@@ -142,6 +142,20 @@ __device__ __forceinline__ S rambo(S rs, const S (&m)[N], const double* u, S (&p
     if (!massive) return vol_massless;
     if (msum >= rs) return S(0.0);
     S xi = sqrt(1.0 - (msum / rs) * (msum / rs));
+    if constexpr (N == 2 && !is_dual<S>::value) {
+        // two equal masses: the massless energies are both sqrt(shat)/2, so this
+        // xi solves sum_i E_i(xi) = sqrt(shat) exactly, each massive energy is
+        // sqrt(shat)/2 and the weight factor reduces to xi (= beta)
+        if (m[0] == m[1]) {
+            const S h = 0.5 * rs;
+#pragma unroll
+            for (int i = 0; i < 2; ++i) {
+                p[i][1] = p[i][1] * xi; p[i][2] = p[i][2] * xi; p[i][3] = p[i][3] * xi;
+                p[i][0] = h;
+            }
+            return vol_massless * xi;
+        }
+    }
     S e2[N];
 #pragma unroll
     for (int i = 0; i < N; ++i) e2[i] = p[i][0] * p[i][0];

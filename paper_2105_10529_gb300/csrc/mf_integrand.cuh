@@ -270,9 +270,10 @@ __device__ __forceinline__ void kinematics_tops_t(const KParams& kp, const doubl
         lq = log(0.25 * ht * ht);
     }
     const int npv = kp.pdfg.nx * kp.pdfg.nq;
-    const S f1 = pdf_xf_log(spdf + P::FLAV1 * npv, kp.pdfg, lx1, lq) / x1;
-    const S f2 = pdf_xf_log(spdf + P::FLAV2 * npv, kp.pdfg, lx2, lq) / x2;
-    pref = f1 * f2 / (2.0 * shat) * wps * jp * jv * GEV2_TO_PB;
+    // f1 f2 / (2 shat) with f = (x f) / x: one division, by 2 shat x1 x2
+    const S xf1 = pdf_xf_log(spdf + P::FLAV1 * npv, kp.pdfg, lx1, lq);
+    const S xf2 = pdf_xf_log(spdf + P::FLAV2 * npv, kp.pdfg, lx2, lq);
+    pref = xf1 * xf2 / (2.0 * shat * (x1 * x2)) * wps * jp * jv * GEV2_TO_PB;
     o.me2 = 0.0;
     o.w = 0.0;
 }
