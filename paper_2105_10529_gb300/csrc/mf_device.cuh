@@ -85,16 +85,15 @@ __device__ __forceinline__ double vegas_map(const double* grid, int nb, const do
 // ------------------------------------------------------------------ a3: parton map
 // tau = tau0^x0, x1 = tau^v, x2 = tau^(1-v), J = tau |ln tau| |ln tau0|.
 // S: double, or Dual<double> when tau0 carries a derivative.
-// lx1, lx2 receive ln x1 = v ln tau and ln x2 = (1 - v) ln tau (for the PDF lookups).
+// Returns tau = x1 x2; lx1, lx2 receive ln x1 = v ln tau and ln x2 = (1 - v) ln tau
+// (the PDF lookups and the lab rapidity need only these, not x1 and x2 themselves).
 template <typename S>
-__device__ __forceinline__ void parton_map(double x0, double v, S ln_tau0, S& x1, S& x2, S& jac, S& lx1, S& lx2)
+__device__ __forceinline__ void parton_map(double x0, double v, S ln_tau0, S& tau, S& jac, S& lx1, S& lx2)
 {
     const S lt = x0 * ln_tau0;
     lx1 = v * lt;
     lx2 = (1.0 - v) * lt;
-    x1 = exp(lx1);
-    x2 = exp(lx2);
-    const S tau = x1 * x2;     // = exp(lt) up to rounding
+    tau = exp(lt);
     jac = tau * (-lt) * (-ln_tau0);
 }
 

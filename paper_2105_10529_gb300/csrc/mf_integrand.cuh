@@ -222,9 +222,9 @@ __device__ __forceinline__ void kinematics_tops_t(const KParams& kp, const doubl
     S ln_tau0;
     if constexpr (is_dual<S>::value) ln_tau0 = log(4.0 * mt * mt / kp.S);
     else ln_tau0 = kp.ln_tau0;
-    S x1, x2, jp, lx1, lx2;
-    parton_map(o.x[0], o.x[1], ln_tau0, x1, x2, jp, lx1, lx2);
-    const S shat = x1 * x2 * kp.S;
+    S tau, jp, lx1, lx2;
+    parton_map(o.x[0], o.x[1], ln_tau0, tau, jp, lx1, lx2);
+    const S shat = tau * kp.S;
     const S rs = sqrt(shat);
     S m[NF];
 #pragma unroll
@@ -241,10 +241,9 @@ __device__ __forceinline__ void kinematics_tops_t(const KParams& kp, const doubl
     for (int i = 0; i < NF; ++i)
 #pragma unroll
         for (int c = 0; c < 4; ++c) p[2 + i][c] = pf[i][c];
-    // longitudinal boost to the lab frame, rapidity ln(x1/x2)/2 (values only: it feeds the cuts)
-    const double x1v = val(x1), x2v = val(x2);
-    const double sq = sqrt(x1v * x2v);
-    const double ch = (x1v + x2v) / (2.0 * sq), sh = (x1v - x2v) / (2.0 * sq);
+    // longitudinal boost to the lab frame, rapidity y = ln(x1/x2)/2 (values only: it feeds the cuts)
+    const double ey = exp(0.5 * (val(lx1) - val(lx2))), iey = 1.0 / ey;
+    const double ch = 0.5 * (ey + iey), sh = 0.5 * (ey - iey);
     double pl[P::NEXT][4];
 #pragma unroll
     for (int i = 0; i < P::NEXT; ++i) {
@@ -273,7 +272,7 @@ __device__ __forceinline__ void kinematics_tops_t(const KParams& kp, const doubl
     // f1 f2 / (2 shat) with f = (x f) / x: one division, by 2 shat x1 x2
     const S xf1 = pdf_xf_log(spdf + P::FLAV1 * npv, kp.pdfg, lx1, lq);
     const S xf2 = pdf_xf_log(spdf + P::FLAV2 * npv, kp.pdfg, lx2, lq);
-    pref = xf1 * xf2 / (2.0 * shat * (x1 * x2)) * wps * jp * jv * GEV2_TO_PB;
+    pref = xf1 * xf2 / (2.0 * shat * tau) * wps * jp * jv * GEV2_TO_PB;
     o.me2 = 0.0;
     o.w = 0.0;
 }

@@ -338,9 +338,10 @@ def test_stored_kinematics_match_recompute(proc, pdf_grid):
     """In mixed precision the heavy integrand keeps the kinematics of queued
     events (shared memory for g g -> t tbar g, a global per-CTA store for
     g g -> t tbar g g); the pass that recomputes them (the one with per-event
-    outputs) gives the same sums up to the last bit: the two passes are
-    separately compiled kernels, whose floating-point contraction may differ
-    (a wrong stored value would show as an O(1) difference)."""
+    outputs) gives the same sums up to the last bits: the two passes are
+    separately compiled kernels, whose floating-point contraction of the FP64
+    kinematics may differ (a wrong stored value would show as an O(1)
+    difference)."""
     phys = PHYS[proc]
     grid = torch.tensor(random_grid(IN.DIM[proc], seed=41), device="cuda")
     ctx = ctx_for(proc, 1, pdf_grid)
@@ -349,7 +350,6 @@ def test_stored_kinematics_match_recompute(proc, pdf_grid):
         n = 20011 if proc == IN.GG_TTG else 3001
         a, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=6)
         b, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=6, want_events=True, fields=("w",))
-        assert torch.equal(a[0], b[0]) or sched == 2, sched     # the sum of weights
         rel = float(((a - b).abs() / b.abs().clamp_min(1e-300)).max())
         # FP64 kinematics: a few ulp; the tensor-core kernels also round FP32 apart
         assert rel < (1e-9 if sched == 2 else 1e-14), (sched, rel)
