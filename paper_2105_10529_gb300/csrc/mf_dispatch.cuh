@@ -7,7 +7,7 @@
 namespace mf {
 
 struct ProcOps {
-    int D, NEXT, npdf, tpb;
+    int D, NEXT, npdf;
     size_t (*smem)(int prec, int nb, int npv, bool obs);   // obs: room for the observable histogram
     cudaError_t (*prepare)(size_t smem_mixed, size_t smem_fp64);
     cudaError_t (*occupancy)(int prec, size_t smem, int* blocks_per_sm);

@@ -16,7 +16,7 @@ cudaError_t evaluate(int prec, const double* mom, long long n, double* me2, doub
     return cudaGetLastError();
 }
 
-const ProcOps kOps = { P::D, P::NEXT, P::NPDF, 256, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate, &I::kernel };
+const ProcOps kOps = { P::D, P::NEXT, P::NPDF, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate, &I::kernel };
 }  // namespace
 
 const ProcOps* ops_ug_ttu() { return &kOps; }
