@@ -21,6 +21,7 @@ import math
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
@@ -33,9 +34,9 @@ SM_MAX_MHZ = 2070.0
 FP64_PEAK_NOMINAL_TFLOPS = 1.25
 # DRAM bytes (read + write) per event of the mixed g g -> t tbar g g integrand with the
 # tensor-core colour sum (256-thread CTAs), from the dram__bytes capture in
-# profiles/launches_bench_gg_ttgg.txt (3.156 GB over 1e6 events; the traffic, evicted
+# profiles/integrand_gg_ttgg_mixed_1m_ncu.txt (2.803 GB over 1e6 events; the traffic, evicted
 # local-memory lines, grows with the number of events)
-DRAM_BYTES_PER_EVENT_P3_TC = 3156.3
+DRAM_BYTES_PER_EVENT_P3_TC = 2802.6
 
 
 def parse():
@@ -48,6 +49,8 @@ def parse():
     ap.add_argument("--fp64-events", type=int, default=200_000)
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched p p -> t tbar + jets leg")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the leg that runs the other single-process workloads at full size")
     ap.add_argument("--batch-iters", type=int, default=10)
     ap.add_argument("--sched", type=int, default=None,
                     help="integrand schedule (0 free warps, 1 CTA barrier per helicity, 2 = 1 + colour sum on the "
@@ -83,9 +86,8 @@ class ClockSampler:
 
     def __init__(self, index: int):
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"clocks_bench_{os.getpid()}.csv")
         try:
-            os.makedirs(os.path.dirname(self.path), exist_ok=True)
             q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
                  "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
                  "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -182,6 +184,63 @@ def run_batch(ctx, phys, IN, n_iter):
             "dsigma_dmt_pb_per_gev": float(g[-1, 1]), "dsigma_dmt_error": float(g[-1, 2]),
             "dsigma_dalphas_pb": float(g[-1, 3]),
             "timing": "host wall clock around the synchronous C-ABI call (graph launch, reductions, host results)"}
+
+
+def run_configs(pdf, IN, MF_FP64, MF_MIXED, stream):
+    """The other single-process workloads at their full sizes through
+    mf_integrate (host wall clock around the synchronous call, one warm-up
+    call first): e+e- -> mu+mu- in FP64 (1e5 x 5); g g -> t tbar and
+    g g -> t tbar g (1e7 x 10) in mixed precision and in FP64, the latter with
+    d sigma/d m_t from the extra derivative pass; and the per-event relative
+    error of the mixed weights against the FP64 GPU weights on 1e5 events at
+    the uniform grid."""
+    import numpy as np
+    import torch
+    from paper_2105_10529_gb300.api import Context, process_info
+    out = {}
+    names = {IN.EE_MUMU: "ee_mumu", IN.GG_TT: "gg_tt", IN.GG_TTG: "gg_ttg"}
+    for key, wl in IN.workloads().items():
+        p = wl.process
+        if p not in names:
+            continue
+        grads = p == IN.GG_TTG
+        precs = [MF_FP64] if p == IN.EE_MUMU else [MF_MIXED, MF_FP64]
+        entry = {"workload": wl.name, "events_per_iteration": wl.n_events, "iterations": wl.n_iter}
+        ws = {}
+        for prec in precs:
+            ctx = Context(wl.physics, pdf, precision=prec, stream=stream)
+            ctx.integrate(p, wl.physics.sqrt_s, min(wl.n_events, 100_000), 1)          # warm-up
+            t0 = time.perf_counter()
+            r = ctx.integrate(p, wl.physics.sqrt_s, wl.n_events, wl.n_iter, want_grads=grads)
+            dt = time.perf_counter() - t0
+            tag = "fp64" if prec == MF_FP64 else "mixed"
+            e = {"events_per_s": wl.n_events * wl.n_iter / dt, "s_per_call": dt, "sigma_pb": r["sigma"],
+                 "error_pb": r["error"], "chi2dof": r["chi2dof"], "pass_fraction": r["n_pass"] / max(r["n_events"], 1)}
+            if grads:
+                e.update(dsigma_dmt_pb_per_gev=r["dsigma_dmt"], dsigma_dmt_error=r["dsigma_dmt_error"],
+                         dsigma_dalphas_pb=r["dsigma_dalphas"],
+                         timing_note="includes one derivative pass of the same size at the final grid")
+            entry[tag] = e
+            if len(precs) > 1:
+                _, dim = process_info(p)
+                grid = torch.linspace(0, 1, wl.physics.n_bins + 1, dtype=torch.float64,
+                                      device="cuda").repeat(dim, 1).contiguous()
+                _, ev = ctx.vegas_pass(p, wl.physics.sqrt_s, grid, 100_000, iteration=10**6, want_events=True,
+                                       fields=("w",))
+                torch.cuda.synchronize()
+                ws[tag] = ev["w"].cpu().numpy()
+            ctx.close()
+        if "mixed" in entry and "fp64" in entry:
+            ok = ws["fp64"] != 0
+            rel = np.abs(ws["mixed"][ok] - ws["fp64"][ok]) / np.abs(ws["fp64"][ok])
+            entry["mixed_speedup"] = entry["mixed"]["events_per_s"] / entry["fp64"]["events_per_s"]
+            entry["stated_err"] = {"per_event_rel_max": float(rel.max()),
+                                   "per_event_rel_p999": float(np.quantile(rel, 0.999)),
+                                   "per_event_rel_median": float(np.median(rel)), "events": int(ok.sum()),
+                                   "sigma_rel_mixed_vs_fp64": abs(entry["mixed"]["sigma_pb"] - entry["fp64"]["sigma_pb"])
+                                   / abs(entry["fp64"]["sigma_pb"])}
+        out[names[p]] = entry
+    return out
 
 
 METRIC = "gg->ttbar gg weighted events/s, FP32-mixed vs FP64 GPU at stated err; % FP peak"
@@ -386,6 +445,11 @@ def run_ours(args):
     if not args.no_batch:
         batch = run_batch(ctx, phys, IN, args.batch_iters)
 
+    # ---- the other single-process workloads (e+e-, gg -> t tbar, gg -> t tbar g)
+    per_config = None
+    if not args.no_configs:
+        per_config = run_configs(pdf, IN, MF_FP64, MF_MIXED, stream)
+
     # ---- FP64 CPU oracle on the host cores (bounded sample)
     cpu = None
     if not args.no_cpu:
@@ -436,6 +500,8 @@ def run_ours(args):
         line["cpu_baseline"] = cpu
     if batch:
         line["batch"] = batch
+    if per_config:
+        line["per_config"] = per_config
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
