@@ -32,11 +32,11 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_NOMINAL_TFLOPS = 1.25
-# DRAM bytes (read + write) per event of the mixed g g -> t tbar g g integrand with the
-# tensor-core colour sum (256-thread CTAs), from the dram__bytes capture in
-# profiles/integrand_gg_ttgg_mixed_1m_ncu.txt (2.803 GB over 1e6 events; the traffic, evicted
-# local-memory lines, grows with the number of events)
-DRAM_BYTES_PER_EVENT_P3_TC = 2802.6
+# DRAM bytes (read + write) per event of the mixed g g -> t tbar g g integrand under the
+# default schedule (warp per event, tensor-core colour sum), from the dram__bytes counters of
+# the capture in profiles/integrand_gg_ttgg_mixed_1m_ncu.txt (over 1e6 events; the traffic,
+# evicted local-memory lines, grows with the number of events)
+DRAM_BYTES_PER_EVENT_P3 = None
 
 
 def parse():
@@ -54,7 +54,7 @@ def parse():
     ap.add_argument("--batch-iters", type=int, default=10)
     ap.add_argument("--sched", type=int, default=None,
                     help="integrand schedule (0 free warps, 1 CTA barrier per helicity, 2 = 1 + colour sum on the "
-                         "tensor cores; default 2)")
+                         "tensor cores, 3 = 2 with one warp per event and one lane per helicity; default 3)")
     ap.add_argument("--hsplit", type=int, default=None,
                     help="threads per event of the heavy integrand (1 or 2; default 1)")
     ap.add_argument("--only-timed", action="store_true",
@@ -155,7 +155,7 @@ def run_batch(ctx, phys, IN, n_iter):
     # the chosen schedule, and one representative schedule per mode
     t_batch, (tot, chans) = timed(choice)
     per_mode = {0: timed((0, 1, 4096, 4096, 0, 1)), 1: timed((1, 1, 4096, 4096, 0, 1)),
-                2: timed((2, 2, 4096, 4096, 0, 1))}
+                2: timed((2, 3, 4096, 4096, 0, 1))}
     ctx.set_batch_schedule(*choice)
     ctx.integrate_batch(procs, ns, phys.sqrt_s, n_iter)               # grids of the chosen schedule
     g = ctx.batch_grad(procs, ns, phys.sqrt_s, 1000)
@@ -177,7 +177,7 @@ def run_batch(ctx, phys, IN, n_iter):
                          "helicity_split": choice[5]},
             "events_per_s_by_mode": {"one launch (0, 1, 4096, 4096)": ev / per_mode[0][0],
                                      "split (1, 1, 4096, 4096)": ev / per_mode[1][0],
-                                     "per-channel kernels (2, 2, -, 4096)": ev / per_mode[2][0]},
+                                     "per-channel kernels (2, 3, -, 4096)": ev / per_mode[2][0]},
             "sigma_pb": tot["sigma"], "error_pb": tot["error"],
             "channels": {names[p]: {"sigma_pb": c["sigma"], "error_pb": c["error"], "chi2dof": c["chi2dof"],
                                     "sequential_sigma_pb": q["sigma"]} for p, c, q in zip(procs, chans, seq)},
@@ -471,16 +471,19 @@ def run_ours(args):
         "ms_per_step": 1e3 * t_total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
         "config": dict(workload_config(N, dim, nb), colour_sum=(
-            "tensor cores: tcgen05.mma kind::f16, two (128 events x 24) x (24 x 24) per helicity and 256-thread CTA, "
+            "tensor cores: tcgen05.mma kind::f16, two (128 rows x 24) x (24 x 24) per step and 256-thread CTA, "
             "bf16x2 split of "
-            "the colour flows, FP32 accumulation in TMEM") if (args.sched is None or args.sched == 2) else "FP32 FMA",
+            "the colour flows, FP32 accumulation in TMEM") if (args.sched is None or args.sched >= 2) else "FP32 FMA",
+                      schedule=("one warp per event, one lane per helicity of the parity-halved sum"
+                                if args.sched is None or args.sched == 3 else f"integrand schedule {args.sched}"),
                       helicity_split=args.hsplit or 1),
         # per step: the integrand and the end-of-pass reduction (mf_vegas_pass) and the refinement
         "gpu_launches": 3 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved_tflops / fp32_peak,
-                     "traffic": (DRAM_BYTES_PER_EVENT_P3_TC * N)
-                     if (args.sched is None or args.sched == 2) and (args.hsplit or 1) == 1 else None,
+                     "traffic": (DRAM_BYTES_PER_EVENT_P3 * N)
+                     if DRAM_BYTES_PER_EVENT_P3 is not None and (args.sched is None or args.sched == 3)
+                     and (args.hsplit or 1) == 1 else None,
                      "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of a 1e6-event ncu capture of the "
                                       "same kernel, scaled to the launch's events (spill lines; grows with events)",
                      "kernel": "integrand_kernel<gg_ttgg, float>",

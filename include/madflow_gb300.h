@@ -128,9 +128,10 @@ int mf_process_info(int process, int *n_ext, int *dim);
  * on ln-uniform nodes, layout [flavour][ix][iq] with flavours 0 gluon,
  * 1 u, 2 ubar (n_flav >= 1; the gluon processes read flavour 0), copied to
  * the device.  stream: a cudaStream_t or NULL.  On success *out owns device
- * buffers sized for every built process (about 80 MB on a 152-SM GPU:
- * per-CTA partial sums and the heavy integrand's kinematics store; the
- * batch calls add their own on first use); release with mf_destroy. */
+ * buffers sized for every built process (about 100 MB on a 152-SM GPU:
+ * per-CTA partial sums, the heavy integrand's kinematics store and the
+ * per-event records of schedule 3; the batch calls add their own on first
+ * use); release with mf_destroy. */
 int mf_create(struct mf_ctx **out, const mf_config *cfg, const double *pdf_grid_host, int n_flav, int nx, int nq,
               double x_min, double q2_min, double q2_max, void *stream);
 void mf_destroy(struct mf_ctx *ctx);
@@ -139,12 +140,20 @@ int mf_set_precision(struct mf_ctx *ctx, int precision);
 /* Integrand schedule for the heavy processes (gg -> t tbar g, gg -> t tbar g g):
  * 0 = warps run freely through the helicity sum, 1 = a CTA barrier after every
  * helicity keeps the CTA's warps on the same instructions,
- * 2 (the default) = as 1, and for g g -> t tbar g g in MF_MIXED the colour sum of every
+ * 2 = as 1, and for g g -> t tbar g g in MF_MIXED the colour sum of every
  * helicity (24 x 24 colour matrix, Sec. 2.2) runs on the tensor cores as one
  * (128 events x 24) x (24 x 24) contraction per 128 threads (tcgen05, bf16 split of the
  * colour-flow amplitudes, FP32 accumulation in tensor memory); elsewhere 2 acts
- * as 1.  Schedules 0 and 1 give identical results; 2 differs from them by FP32
- * rounding.  MF_ERR_ARG for other values. */
+ * as 1.  3 (the default) = the warp-per-event schedule of g g -> t tbar g g in MF_MIXED (no
+ * counterpart in the paper, whose kernels give one thread per event): one warp per
+ * event, its 32 lanes evaluating the 32 helicities of the parity-halved sum of
+ * Sec. 2.2 at once, the colour sum on the tensor cores as in 2, and the event's
+ * sum over its lanes by a fixed shuffle tree.  The warp shares one copy of the
+ * event's helicity-independent pieces, so the kernel needs far less shared memory
+ * and the SM's L1 keeps more of the matrix element's local memory.  Passes with
+ * per-event outputs, the helicity split and the other processes run 3 as 2.
+ * Schedules 0 and 1 give identical results; 2 and 3 differ from them and from
+ * each other by FP32 rounding.  MF_ERR_ARG for other values. */
 int mf_set_schedule(struct mf_ctx *ctx, int sched);
 /* Observable histogram (Sec. 2.1: the pipeline ends in histogram accumulation;
  * Sec. 3, Fig. 2: the leading-order cross section differential in p_T): the
@@ -339,7 +348,8 @@ int mf_batch_grad(struct mf_ctx *ctx, int n_ch, const int *processes, const long
  * paper): mode 0/1/2 (one launch / split / per-channel kernels, see
  * mf_integrate_batch), sched 0/1 (helicity barrier off/on in the
  * g g -> t tbar g(g) matrix elements; in mode 2 also 2, the integrand
- * schedule with the tensor-core colour sum, as mf_set_schedule),
+ * schedule with the tensor-core colour sum, and 3, the warp-per-event
+ * schedule, as mf_set_schedule),
  * tile_heavy and tile_light in [32, 2^26] events per work item for the
  * g g -> t tbar g(g) channels and for the others (in the split mode, the
  * other channels' kernels get one CTA per tile_light events), ctas_per_sm in
@@ -354,8 +364,8 @@ int mf_set_batch_schedule(struct mf_ctx *ctx, int mode, int sched, long long til
  * paper).  Times one iteration of the given channels and sizes at uniform
  * grids for every mode {0, 1} x (helicity barrier, helicity split) {(0, 1),
  * (1, 1), (1, 2)} x tile_heavy {1024, 2048, 4096} x tile_light {2048, 4096},
- * and mode 2 x sched {1, 2} x tile_light {2048, 4096} (CTAs per SM as fit;
- * 40 candidates) and keeps the fastest for later
+ * and mode 2 x sched {1, 2, 3} x tile_light {2048, 4096} (CTAs per SM as fit;
+ * 42 candidates) and keeps the fastest for later
  * mf_integrate_batch calls on this context.  choice_host [6] (nullable)
  * receives (mode, sched, tile_heavy, tile_light, ctas_per_sm, hsplit), the
  * arguments of mf_set_batch_schedule.  Arguments as mf_integrate_batch; the cuts are the

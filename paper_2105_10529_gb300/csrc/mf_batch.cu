@@ -603,7 +603,7 @@ int mf_set_batch_schedule(mf_ctx* c, int mode, int sched, long long tile_heavy, 
                           int hsplit)
 {
     if (!c) return MF_ERR_ARG;
-    if (mode < 0 || mode > 2 || sched < 0 || sched > 2 || (sched == 2 && mode != 2) || tile_heavy < 32 ||
+    if (mode < 0 || mode > 2 || sched < 0 || sched > 3 || (sched >= 2 && mode != 2) || tile_heavy < 32 ||
         tile_heavy > (1LL << 26) || tile_light < 32 || tile_light > (1LL << 26) || ctas_per_sm < 0 ||
         ctas_per_sm > 16 || (hsplit != 1 && hsplit != 2) || (hsplit == 2 && (sched != 1 || mode == 2)))
         return mf_fail(c, MF_ERR_ARG, "mf_set_batch_schedule: bad argument");
@@ -631,7 +631,7 @@ int mf_autotune_batch(mf_ctx* c, int n_ch, const int* processes, const long long
                     for (long long tl : { 2048LL, 4096LL })
                         cand.push_back(Schedule{ mode, sched, 0, th, tl, hs });
     // every channel as its own kernel: FMA or tensor-core colour sum for the expensive ones
-    for (int sched = 1; sched <= 2; ++sched)
+    for (int sched = 1; sched <= 3; ++sched)
         for (long long tl : { 2048LL, 4096LL }) cand.push_back(Schedule{ 2, sched, 0, 4096, tl, 1 });
     float best = 1e30f;
     Schedule pick = current_schedule(c);

@@ -214,6 +214,8 @@ int make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KPara
     kp.kin = c->d_kin;
     kp.kin_bins = c->d_kin_bins;
     kp.kin_ctas = c->kin_ctas;
+    kp.inv_rec = c->d_inv;
+    kp.inv_ctas = c->inv_ctas;
     return MF_OK;
 }
 
@@ -313,6 +315,10 @@ int mf_create(mf_ctx** out, const mf_config* cfg, const double* pdf_grid_host, i
             cudaSuccess ||
         cudaMalloc(&c->d_kin_bins, (size_t)c->kin_ctas * MAX_DIM * KIN_CAP_UNIT) != cudaSuccess)
         return bail(MF_ERR_CUDA);
+    // records of the warp-per-event schedule: one CTA per SM of LH_TPB queued events
+    c->inv_ctas = c->n_sm;
+    if (cudaMalloc(&c->d_inv, (size_t)c->inv_ctas * LH_INV_WORDS_MAX * LH_TPB * sizeof(float)) != cudaSuccess)
+        return bail(MF_ERR_CUDA);
     if (cudaMemcpy(c->d_pdf, pdf_grid_host, npdf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(MF_ERR_CUDA);
     for (int p : { MF_EE_MUMU, MF_GG_TT, MF_GG_TTG, MF_GG_TTGG, MF_UU_TT, MF_UG_TTU }) {
@@ -337,6 +343,7 @@ void mf_destroy(mf_ctx* c)
     cudaFree(c->d_err);
     cudaFree(c->d_kin);
     cudaFree(c->d_kin_bins);
+    cudaFree(c->d_inv);
     cudaFree(c->d_obs_partials);
     cudaFree(c->d_obs_iter);
     cudaFree(c->d_kps);
@@ -381,7 +388,7 @@ int mf_set_precision(mf_ctx* c, int precision)
 
 int mf_set_schedule(mf_ctx* c, int sched)
 {
-    if (!c || sched < 0 || sched > 2) return MF_ERR_ARG;
+    if (!c || sched < 0 || sched > 3) return MF_ERR_ARG;
     c->sched = sched;
     return MF_OK;
 }

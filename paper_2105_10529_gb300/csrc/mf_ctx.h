@@ -23,8 +23,10 @@ struct mf_ctx {
     double* d_kin = nullptr;         // kinematics of queued events (heavy integrand), per CTA
     uint8_t* d_kin_bins = nullptr;
     int kin_ctas = 0;
+    float* d_inv = nullptr;          // per-event records of the warp-per-event schedule, per CTA
+    int inv_ctas = 0;
     int max_blocks = 0;
-    int sched = 2;                   // integrand schedule (see mf_set_schedule)
+    int sched = 3;                   // integrand schedule (see mf_set_schedule)
     int hsplit = 1;                  // lanes per event in the heavy integrand (see mf_set_helicity_split)
     // observable histogram (mf_set_observable): n bins from obs_lo, obs_inv_w = n / (hi - lo)
     int obs_n = 0;

@@ -12,7 +12,9 @@ struct ProcOps {
     cudaError_t (*prepare)(size_t smem_mixed, size_t smem_fp64);
     cudaError_t (*occupancy)(int prec, size_t smem, int* blocks_per_sm);
     // sched: 0 free-running warps, 1 CTA barrier between helicities (heavy processes),
-    // 2 barrier and the colour sum on the tensor cores (processes with P::TC, mixed precision);
+    // 2 barrier and the colour sum on the tensor cores (processes with P::TC, mixed precision),
+    // 3 warp-per-event schedule with the tensor-core colour sum (P::TC, mixed precision, no
+    // per-event outputs, kp.inv_rec set for every CTA; otherwise as 2);
     // hsplit: 1, or 2 lanes per event each summing half the helicities (heavy processes,
     // mixed precision, sched >= 1, no per-event outputs; otherwise 1)
     cudaError_t (*integrand)(int prec, bool write, int sched, int hsplit, const KParams& kp, int nblk, size_t smem,
@@ -85,6 +87,10 @@ struct IntegrandOps {
     // helicity split variants (mixed precision, barrier schedule, no per-event outputs)
     static const void* fn_hs() { return (const void*)integrand_kernel<P, float, T32, false, HS, false, HS ? 2 : 1>; }
     static const void* fn_hs_tc() { return (const void*)integrand_kernel<P, float, T32, false, HT, HT, HT ? 2 : 1>; }
+    // warp-per-event schedule (P::TC processes with LH_TPB-thread mixed-precision CTAs)
+    static constexpr bool HL = HT && T32 == LH_TPB;
+    static const void* fn_lh() { return (const void*)integrand_kernel<P, float, T32, false, HL, HL, 1, HL>; }
+    static size_t smem_lh(int nb, int npv, bool obs) { return SmemLayout<P, float, T32, HL>::bytes(nb, npv, obs); }
     // the dynamic shared memory of every variant of one precision (sm32, sm64: bytes)
     static cudaError_t prepare(size_t sm32, size_t sm64)
     {
@@ -98,6 +104,20 @@ struct IntegrandOps {
         }
         for (const void* f : f64) {
             cudaError_t e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm64);
+            if (e != cudaSuccess) return e;
+        }
+        if constexpr (HL) {
+            // the warp-per-event kernel needs far less shared memory: ask for the smallest
+            // carveout that holds it, so that the rest of the SM's L1 serves its local memory
+            int dev = 0, smem_sm = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            if (e != cudaSuccess) return e;
+            const size_t need = smem_lh(MAX_BINS, 0, true) + 1024;
+            int pct = smem_sm > 0 ? (int)((need * 100 + (size_t)smem_sm - 1) / (size_t)smem_sm) : 100;
+            if (pct > 100) pct = 100;
+            e = cudaFuncSetAttribute(fn_lh(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm32);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(fn_lh(), cudaFuncAttributePreferredSharedMemoryCarveout, pct);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -115,13 +135,16 @@ struct IntegrandOps {
         if constexpr (HS && sizeof(R) == 4 && !W) {
             if (hsplit == 2 && sched >= 1) {
                 if constexpr (HT) {
-                    if (sched == 2) return (const void*)integrand_kernel<P, float, TPB, false, true, true, 2>;
+                    if (sched >= 2) return (const void*)integrand_kernel<P, float, TPB, false, true, true, 2>;
                 }
                 return (const void*)integrand_kernel<P, float, TPB, false, true, false, 2>;
             }
         }
+        if constexpr (HL && sizeof(R) == 4 && !W) {
+            if (sched == 3 && hsplit == 1) return fn_lh();
+        }
         if constexpr (HT && sizeof(R) == 4) {
-            if (sched == 2) return (const void*)integrand_kernel<P, float, TPB, W, true, true>;
+            if (sched >= 2) return (const void*)integrand_kernel<P, float, TPB, W, true, true>;
         }
         if (sched && HS) return (const void*)integrand_kernel<P, R, TPB, W, HS>;
         return (const void*)integrand_kernel<P, R, TPB, W, false>;
@@ -136,7 +159,13 @@ struct IntegrandOps {
     {
         KParams arg = kp;
         void* args[1] = { &arg };
-        return cudaLaunchKernel(kernel(prec, write, sched, hsplit), dim3(nblk), dim3(prec ? T32 : T64), args, sm, s);
+        if (sched == 3 && (kp.inv_rec == nullptr || nblk > kp.inv_ctas)) sched = 2;   // no record region: as 2
+        const void* f = kernel(prec, write, sched, hsplit);
+        if constexpr (HL) {
+            // the warp-per-event kernel runs with its own, smaller dynamic shared memory
+            if (f == fn_lh()) sm = smem_lh(kp.nb, kp.pdfg.nx * kp.pdfg.nq, kp.nobs > 0);
+        }
+        return cudaLaunchKernel(f, dim3(nblk), dim3(prec ? T32 : T64), args, sm, s);
     }
 };
 

@@ -21,6 +21,7 @@
 // propagator denominators, the spinor normalisations omega) are computed
 // per event in FP64 and passed in as R.
 #pragma once
+#include <cstdint>
 #include "mf_dual.cuh"
 
 namespace mf {
@@ -116,6 +117,45 @@ template <typename R> __device__ __forceinline__ void jadd_c(volatile cx<R>& j, 
 {
     vset(j.r, vget(j.r) + (cr * a.r - ci * a.i)); vset(j.i, vget(j.i) + (cr * a.i + ci * a.r));
 }
+
+// Wide shared-memory accesses of the warp-per-event helicity body (float only; the
+// record's momenta 16-byte and the colour-flow accumulators 8-byte aligned): one
+// instruction where the scalar forms above take four or two.  Like ldv they are
+// issued at every use (volatile asm: never merged or hoisted), in program order.
+__device__ __forceinline__ uint32_t smem_addr(const volatile void* p)
+{
+    return (uint32_t)__cvta_generic_to_shared((const void*)p);
+}
+// o = x (four floats)
+__device__ __forceinline__ void ldv4(const float (&x)[4], float (&o)[4])
+{
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(o[0]), "=f"(o[1]), "=f"(o[2]), "=f"(o[3]) : "r"(smem_addr(x)));
+}
+// o = x - y (four floats each)
+__device__ __forceinline__ void ldv4_diff(const float (&x)[4], const float (&y)[4], float (&o)[4])
+{
+    float a[4], b[4];
+    ldv4(x, a);
+    ldv4(y, b);
+    for (int m = 0; m < 4; ++m) o[m] = a[m] - b[m];
+}
+__device__ __forceinline__ void jzero64(volatile cx<float>& j)
+{
+    asm volatile("st.shared.v2.f32 [%0], {%1, %1};" :: "r"(smem_addr(&j)), "f"(0.0f));
+}
+// j += (dr, di) with one 64-bit load and one 64-bit store
+__device__ __forceinline__ void jadd64(volatile cx<float>& j, float dr, float di)
+{
+    const uint32_t a = smem_addr(&j);
+    float r, i;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(r), "=f"(i) : "r"(a));
+    asm volatile("st.shared.v2.f32 [%0], {%1, %2};" :: "r"(a), "f"(r + dr), "f"(i + di));
+}
+__device__ __forceinline__ void jadd64_p(volatile cx<float>& j, cx<float> a) { jadd64(j, a.r, a.i); }
+__device__ __forceinline__ void jadd64_m(volatile cx<float>& j, cx<float> a) { jadd64(j, -a.r, -a.i); }
+__device__ __forceinline__ void jadd64_pi(volatile cx<float>& j, cx<float> a) { jadd64(j, -a.i, a.r); }
+__device__ __forceinline__ void jadd64_mi(volatile cx<float>& j, cx<float> a) { jadd64(j, a.i, -a.r); }
 
 template <typename R> __device__ __forceinline__ FermionBasis<R> load_basis(const FermionBasis<R>& f)
 {

@@ -10,6 +10,7 @@
 // histograms updated by one leader lane per distinct bin in lane order,
 // warps combined in index order, CTAs combined in index order.
 #pragma once
+#include <cstddef>
 #include <cstdint>
 #include "mf_device.cuh"
 #include "mf_helas.cuh"
@@ -23,6 +24,8 @@ constexpr int KIN_NEXT_MAX = 6;      // largest process (2 -> 4) for the global 
 constexpr int KIN_CAP_UNIT = 256;    // ring entries per region of the global kinematics store
 constexpr int MAX_BINS = 64;
 constexpr int MAX_OBS_BINS = 100;    // observable histogram: regular bins (plus under- and overflow)
+constexpr int LH_INV_WORDS_MAX = 136;   // words of a warp-per-event record (g g -> t tbar g g: 134)
+constexpr int LH_TPB = 256;             // threads per CTA of the warp-per-event schedule
 
 struct EwParams { double e2, sw2, cw2, mz, wz; };
 
@@ -50,6 +53,10 @@ struct KParams {
     uint8_t* kin_bins;
     int kin_ctas;
     const uint8_t* mask_in; // frozen cut masks (nullable)
+    // helicity-independent records of the warp-per-event schedule (nullable): inv_ctas
+    // regions of [LH_INV_WORDS_MAX][256] floats, field-major, one region per CTA
+    float* inv_rec;
+    int inv_ctas;
     // observable histogram (nobs = 0: off): transverse momentum of the first final-state
     // particle in nobs uniform bins from obs_lo, obs_inv_w = nobs / (hi - lo); per CTA
     // (blockIdx.x) a row of [nobs + 2][2] sums (sum w/N, sum (w/N)^2; bin 0 underflow,
@@ -308,13 +315,26 @@ __device__ __forceinline__ void event_tops(const KParams& kp, const double* sgri
 // Light processes keep one histogram per warp (updated by bin leaders);
 // heavy ones keep one per CTA, filled by one thread per dimension in event
 // order after every round.
-template <class P, typename R, int TPB>
+// LH (warp-per-event schedule): dynamic shared memory starts with one colour-flow
+// row per thread (2 NCOL + 2 words: 8-byte aligned, and for 8-byte accesses an
+// even word stride of 2 mod 32 per half-warp is conflict-free), followed by one
+// record per warp (16-byte aligned); both offsets are compile-time constants of the
+// helicity body
+template <class P, bool LH> struct LhRows { static constexpr int words() { return 0; } };
+template <class P> struct LhRows<P, true> { static constexpr int words() { return 2 * P::Me::NCOL + 2; } };
+
+template <class P, typename R, int TPB, bool LH = false>
 struct SmemLayout {
     static constexpr int WARPS = TPB / 32;
     static constexpr int D = P::D;
     static constexpr int NHIST = P::HEAVY ? 1 : WARPS;
-    static __host__ __device__ size_t al(size_t x) { return (x + 15) & ~(size_t)15; }
-    static __host__ __device__ size_t grid_off() { return 0; }
+    static constexpr __host__ __device__ size_t al(size_t x) { return (x + 15) & ~(size_t)15; }
+    // LH: the rows [TPB][LH_JROW] words, then the records [WARPS], LH_REC_STRIDE bytes apart, at LH_REC_OFF
+    static constexpr int LH_JROW = LhRows<P, LH>::words();
+    static constexpr int LH_REC_OFF = TPB * LH_JROW * (int)sizeof(R);
+    static constexpr int LH_REC_STRIDE = (int)al(P::template slot_bytes<R>());
+    static constexpr size_t lh_bytes() { return LH ? al((size_t)LH_REC_OFF + (size_t)WARPS * LH_REC_STRIDE) : 0; }
+    static __host__ __device__ size_t grid_off() { return lh_bytes(); }
     static __host__ __device__ size_t pdf_off(int nb) { return al(grid_off() + sizeof(double) * D * (nb + 1)); }
     static __host__ __device__ size_t hist_off(int nb, int npv) { return al(pdf_off(nb)); }
     static __host__ __device__ size_t vbuf_off(int nb, int npv) { return al(hist_off(nb, npv) + sizeof(double) * NHIST * D * nb); }
@@ -343,10 +363,8 @@ struct SmemLayout {
     }
     // observable histograms [NHIST][MAX_OBS_BINS + 2][2], then per-thread w/N and (heavy) bin buffers
     static constexpr size_t OBS_ROW = 2 * (MAX_OBS_BINS + 2);
-    static __host__ __device__ size_t obs_off(int nb, int npv)
-    {
-        return al(slot_off(nb, npv) + (size_t)TPB * P::template slot_bytes<R>());
-    }
+    static __host__ __device__ size_t slot_region() { return LH ? 0 : (size_t)TPB * P::template slot_bytes<R>(); }
+    static __host__ __device__ size_t obs_off(int nb, int npv) { return al(slot_off(nb, npv) + slot_region()); }
     static __host__ __device__ size_t obs_w_off(int nb, int npv) { return obs_off(nb, npv) + sizeof(double) * NHIST * OBS_ROW; }
     static __host__ __device__ size_t obs_b_off(int nb, int npv) { return obs_w_off(nb, npv) + sizeof(double) * TPB; }
     // obs: with the observable region (kernels touch it only when kp.nobs > 0)
@@ -517,6 +535,57 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
     write_obs_partials<L::NHIST, L::OBS_ROW>(kp, sobs);
 }
 
+// |M|^2 of the batch's events under the warp-per-event schedule (every thread of
+// the CTA calls it; see integrand_heavy).  smem_raw: the kernel's dynamic shared
+// memory in the LH layout of SmemLayout, sme: [TPB] doubles of scratch, take:
+// events in the batch, mine/pm: this thread's batch entry and its momenta.
+// Returns this thread's event's |M|^2 (meaningful where mine).
+template <class P, typename R, int TPB>
+__device__ __forceinline__ double lh_batch_me2(const KParams& kp, unsigned char* smem_raw, TcCta* tc, double* sme,
+                                               int take, bool mine, const double (&pm)[P::NEXT][4])
+{
+    using ME = typename P::Me;
+    using Inv = typename ME::template Inv<R>;
+    using L = SmemLayout<P, R, TPB, true>;
+    constexpr int WARPS = TPB / 32, NW = ME::INV_WORDS, JROW = L::LH_JROW, REC_OFF = L::LH_REC_OFF;
+    constexpr int REC_STRIDE = L::LH_REC_STRIDE;
+    static_assert(ME::NHEL / 2 == 32, "one lane per helicity of the parity-halved sum");
+    static_assert(NW <= LH_INV_WORDS_MAX && sizeof(R) == 4 && offsetof(Inv, jamp) == NW * sizeof(R),
+                  "record layout: the helicity-independent words precede the colour flows");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // this CTA's records, field-major: word f of entry j at grec[f TPB + j]
+    float* grec = kp.inv_rec + (size_t)blockIdx.x * LH_INV_WORDS_MAX * TPB;
+    if (mine) {
+        Inv rec;
+        ME::template inv<R>(pm, kp.mt, rec);
+        const float* wsrc = reinterpret_cast<const float*>(&rec);
+#pragma unroll
+        for (int f = 0; f < NW; ++f) grec[f * TPB + tid] = wsrc[f];
+    }
+    __syncthreads();
+    float* wwords = reinterpret_cast<float*>(smem_raw + REC_OFF + (size_t)warp * REC_STRIDE);
+    const volatile float* jrow = reinterpret_cast<const volatile float*>(smem_raw) + (size_t)tid * JROW;
+    const int nsub = (take + WARPS - 1) / WARPS;
+    for (int sub = 0; sub < nsub; ++sub) {
+        const int j = sub * WARPS + warp;
+        const int jj = j < take ? j : 0;          // a warp without an event repeats entry 0 and discards it
+        for (int f = lane; f < NW; f += 32) wwords[f] = grec[f * TPB + jj];
+        __syncwarp();
+        ME::template hel_j<R, JROW, REC_OFF, REC_STRIDE>(1 + 2 * lane);
+        float mh = tc_colour_sum<ME::NCOL>(tc, jrow);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) mh += __shfl_xor_sync(0xffffffffu, mh, off);
+        if (lane == 0 && j < take) sme[j] = (double)mh;
+        __syncwarp();
+    }
+    __syncthreads();
+    const float acc = 2.0f * (float)sme[tid < take ? tid : 0];
+    double gk = 1.0;
+    for (int i = 0; i < ME::NGLUON; ++i) gk = gk * (kp.gs * kp.gs);
+    __syncthreads();   // sme is reused by the caller
+    return (double)acc / ME::COLOUR_DEN * gk * ME::AVG * ME::SYM;
+}
+
 // Heavy processes (expensive matrix elements): kinematics first, then the
 // events that pass the cuts are queued in event order and their matrix
 // elements are evaluated TPB at a time, so no lane idles through a matrix
@@ -530,15 +599,25 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
 // TPB / 2 events per round (step is a multiple of TPB / HS), a batch holds
 // TPB / 2 events, and every warp still evaluates one helicity at a time (the
 // halves live in different warps, so the helicity stays warp-uniform).
-template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false, int HS = 1>
+// LH: warp-per-event schedule (tensor-core processes, no per-event outputs).  A
+// batch first computes every queued event's helicity-independent pieces, one
+// event per thread, into this CTA's region of kp.inv_rec; then warp w takes
+// the batch's events w, w + WARPS, ..., copies the event's record into its
+// shared-memory record and lane l evaluates helicity 1 + 2 l of the
+// parity-halved sum (32 helicities, 32 lanes), with the colour sum of all 256
+// rows on the tensor cores and the event's sum over its lanes by a fixed
+// shuffle tree.  The per-event record is shared by the warp, so shared memory
+// holds 8 records instead of 256 per-thread slots and leaves the rest to L1.
+template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false, int HS = 1, bool LH = false>
 __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char* smem_raw, long long first,
                                                 long long step, long long end, double* out)
 {
     static_assert(HS == 1 || (HS == 2 && SYNC && !WRITE), "helicity split: pairs of lanes, barrier schedule");
     static_assert(!TC || (P::TC && SYNC && (TPB == 128 || TPB == 256) && sizeof(R) == 4),
                   "tensor-core colour sum: float, barrier schedule, one TMEM lane per thread");
+    static_assert(!LH || (TC && HS == 1 && !WRITE && TPB == LH_TPB), "warp-per-event: tensor cores, no split or outputs");
     constexpr int D = P::D, WARPS = TPB / 32;
-    using L = SmemLayout<P, R, TPB>;
+    using L = SmemLayout<P, R, TPB, LH>;
     const int nb = kp.nb;
     const int npv = kp.pdfg.nx * kp.pdfg.nq;
     double* sgrid = reinterpret_cast<double*>(smem_raw + L::grid_off());
@@ -658,8 +737,13 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
                 kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
             }
             double me;
-            if constexpr (TC) me = P::Me::template me2<R, SYNC, true>(pm, kp.mt, kp.gs, slot, tc, hpart, HS);
-            else me = P::Me::template me2<R, SYNC>(pm, kp.mt, kp.gs, slot, nullptr, hpart, HS);
+            if constexpr (LH) {
+                me = lh_batch_me2<P, R, TPB>(kp, smem_raw, tc, svbuf, take, mine, pm);
+            } else if constexpr (TC) {
+                me = P::Me::template me2<R, SYNC, true>(pm, kp.mt, kp.gs, slot, tc, hpart, HS);
+            } else {
+                me = P::Me::template me2<R, SYNC>(pm, kp.mt, kp.gs, slot, nullptr, hpart, HS);
+            }
             if constexpr (HS == 2) {
                 // the owner adds the second half, evaluated in another warp
                 svbuf[tid] = me;
@@ -711,7 +795,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
 
 // ------------------------------------------------------------------ the fused integrand kernel
 
-template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false, int HS = 1>
+template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false, int HS = 1, bool LH = false>
 __global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -719,7 +803,15 @@ __global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
     if constexpr (P::HEAVY) {
         constexpr int EPB = TPB / HS;   // events per CTA and round
         const long long first = (long long)blockIdx.x * EPB, step = (long long)gridDim.x * EPB;
-        integrand_heavy<P, R, TPB, WRITE, SYNC, TC, HS>(kp, smem_raw, first, step, kp.n_events, out);
+        if constexpr (LH) {
+            // the host launches this schedule only with a record region for every CTA
+            if (kp.inv_rec == nullptr || (int)blockIdx.x >= kp.inv_ctas) {
+                if (threadIdx.x == 0 && kp.dev_err) atomicExch(kp.dev_err, 1u);
+                for (int i = threadIdx.x; i < 2 + P::D * kp.nb; i += TPB) out[i] = 0.0;
+                return;
+            }
+        }
+        integrand_heavy<P, R, TPB, WRITE, SYNC, TC, HS, LH>(kp, smem_raw, first, step, kp.n_events, out);
     } else {
         const long long first = (long long)blockIdx.x * TPB, step = (long long)gridDim.x * TPB;
         integrand_light<P, R, TPB, WRITE>(kp, smem_raw, first, step, kp.n_events, out);

@@ -27,6 +27,7 @@ four-gluon vertex -i g^2 (f f)(g g - g g) in three colour structures.
 from __future__ import annotations
 
 import itertools
+import re
 import math
 from fractions import Fraction
 from functools import reduce
@@ -475,6 +476,26 @@ def _emit_single(em: "Emitter", kind, data, poly, widx, full):
     _emit_amp_jamps(em, em.tree_var[key][t - 1], poly, widx)
 
 
+_K4 = re.compile(r"const R (\w+)\[4\] = \{ldv\(v\.K\[(\d+)\]\[0\]\), ldv\(v\.K\[\2\]\[1\]\), "
+                 r"ldv\(v\.K\[\2\]\[2\]\), ldv\(v\.K\[\2\]\[3\]\)\};")
+_Q4 = re.compile(r"const R (\w+)\[4\] = \{ldv\(v\.p3\[0\]\) - ldv\(v\.K\[(\d+)\]\[0\]\), "
+                 r"ldv\(v\.p3\[1\]\) - ldv\(v\.K\[\2\]\[1\]\), ldv\(v\.p3\[2\]\) - ldv\(v\.K\[\2\]\[2\]\), "
+                 r"ldv\(v\.p3\[3\]\) - ldv\(v\.K\[\2\]\[3\]\)\};")
+
+
+def _wide_access(line: str) -> str:
+    """One line of the warp-per-event helicity body with its shared-memory
+    accesses widened: momentum 4-vectors of the record in one 16-byte load,
+    colour-flow updates as one 8-byte load and store (same arithmetic)."""
+    line = _K4.sub(lambda m: f"R {m.group(1)}[4]; ldv4(v.K[{m.group(2)}], {m.group(1)});", line)
+    line = _Q4.sub(lambda m: f"R {m.group(1)}[4]; ldv4_diff(v.p3, v.K[{m.group(2)}], {m.group(1)});", line)
+    line = line.replace("{ vset(jamp[c].r, R(0)); vset(jamp[c].i, R(0)); }", "jzero64(jamp[c]);")
+    for f in ("jadd_mi(", "jadd_pi(", "jadd_p(", "jadd_m("):
+        line = line.replace(f, f.replace("jadd_", "jadd64_"))
+    assert "jadd_" not in line and "ldv(v.K" not in line, line
+    return line
+
+
 def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]:
     """CUDA source for the averaged |M|^2 of g g -> t tbar + (k-2) g."""
     words = list(itertools.permutations(range(k)))
@@ -623,6 +644,18 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot,")
     src.append("                                                void* cta = nullptr, int hpart = 0, int hparts = 1);")
     src.append("  template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }")
+    if tc:
+        src.append("  // warp-per-event schedule: the helicity-independent words of Inv (everything before jamp),")
+        src.append("  // filled for one event by one thread (inv), then read by the 32 lanes of a warp, each")
+        src.append("  // evaluating one of the 32 helicities of the parity-halved sum (hel_j, colour flows in")
+        src.append("  // caller storage, no colour sum)")
+        src.append(f"  static constexpr int INV_WORDS = {n_words - 2 * ncol};")
+        src.append("  template <typename R>")
+        src.append("  __device__ static void inv(const typename Widen<R>::type (&p)[NEXT][4], typename Widen<R>::type mt, Inv<R>& v);")
+        src.append("  // hel_j reads the warp's record at REC_OFF + (threadIdx.x / 32) REC_STRIDE bytes and keeps the")
+        src.append("  // thread's colour flows at threadIdx.x JROW words, both from the start of dynamic shared memory")
+        src.append("  template <typename R, int JROW, int REC_OFF, int REC_STRIDE>")
+        src.append("  __device__ static void hel_j(int ih);")
     src.append("};")
     src.append("")
     src.append("// one helicity configuration: amplitudes, colour flows and (CSUM) the colour sum;")
@@ -688,6 +721,54 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("{")
     src.append(f"    return me2_{name}_impl<R, SYNC, TC>(&p[0][0], mt, gs, slot, cta, hpart, hparts);")
     src.append("}")
+    if tc:
+        src.append("")
+        src.append("// the prologue of me2 alone: the event's helicity-independent pieces into v")
+        src.append("template <typename R>")
+        src.append(f"__device__ __forceinline__ void inv_{name}(const typename Widen<R>::type* pflat, typename Widen<R>::type mt,")
+        src.append(f"                                       Me_{name}::Inv<R>& v)")
+        src.append("{")
+        src.append("    using S = typename Widen<R>::type;")
+        src.append(f"    constexpr int NEXT = Me_{name}::NEXT;")
+        src.append("    S p[NEXT][4];")
+        src.append("    for (int i = 0; i < NEXT; ++i)")
+        src.append("        for (int c = 0; c < 4; ++c) p[i][c] = pflat[4 * i + c];")
+        for l in pro:
+            src.append("    " + l)
+        src.append("}")
+        src.append("")
+        src.append("// one helicity's colour-flow amplitudes (the same as hel_" + name + ", without the colour sum);")
+        src.append("// the record and the colour-flow row sit at fixed offsets of dynamic shared memory, so that")
+        src.append("// both addresses are shared-space offsets derived from threadIdx.x")
+        src.append("// (R = float: the record's momenta are read 16 bytes and the colour flows")
+        src.append("// updated 8 bytes at a time; REC_STRIDE and JROW keep them aligned)")
+        src.append("template <typename R, int JROW, int REC_OFF, int REC_STRIDE>")
+        src.append(f"__device__ __noinline__ void hel_{name}_j(int ih)")
+        src.append("{")
+        src.append(f"    constexpr int NCOL = Me_{name}::NCOL;")
+        src.append("    static_assert(sizeof(R) == 4 && REC_OFF % 16 == 0 && REC_STRIDE % 16 == 0 && JROW % 2 == 0,")
+        src.append("                  \"aligned float records and colour-flow rows\");")
+        src.append("    extern __shared__ __align__(128) unsigned char mf_lh_smem[];")
+        src.append(f"    const Me_{name}::Inv<R>& v = *reinterpret_cast<const Me_{name}::Inv<R>*>(")
+        src.append("        mf_lh_smem + REC_OFF + (threadIdx.x >> 5) * REC_STRIDE);")
+        src.append("    volatile cx<R>* jamp = reinterpret_cast<volatile cx<R>*>(mf_lh_smem + threadIdx.x * (JROW * sizeof(R)));")
+        src.append("#define HEL(i) ((ih >> (i)) & 1 ? 1 : -1)")
+        assert body[1].startswith("volatile cx<R>* jamp =")
+        for l in body[2:]:
+            src.append("    " + _wide_access(l))
+        src.append("#undef HEL")
+        src.append("}")
+        src.append("")
+        src.append("template <typename R>")
+        src.append(f"__device__ void Me_{name}::inv(const typename Widen<R>::type (&p)[NEXT][4], typename Widen<R>::type mt, Inv<R>& v)")
+        src.append("{")
+        src.append(f"    inv_{name}<R>(&p[0][0], mt, v);")
+        src.append("}")
+        src.append("template <typename R, int JROW, int REC_OFF, int REC_STRIDE>")
+        src.append(f"__device__ void Me_{name}::hel_j(int ih)")
+        src.append("{")
+        src.append(f"    hel_{name}_j<R, JROW, REC_OFF, REC_STRIDE>(ih);")
+        src.append("}")
     src.append("}  // namespace mf")
     stats = dict(n_diag=n_diag, n_amp=len(diags), ncol=ncol, counts=dict(em.counts), colour_den=den)
     stats["flops_per_helicity"] = helicity_flops(em, ncol, CI)

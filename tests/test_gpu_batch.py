@@ -125,17 +125,20 @@ def test_batch_helicity_split(ctx, mode):
     ctx.set_batch_schedule(mode, 1, TILE, 3 * TILE, 0)
 
 
-def test_batch_per_channel_kernels_with_tensor_cores(ctx, pdf_grid):
-    """Schedule 2 with the tensor-core colour sum: each channel equals a
-    single-process mf_integrate on the default schedule (the same kernels and
-    launch configuration), and the result is stable under graph replay."""
+@pytest.mark.parametrize("sched", [2, 3])
+def test_batch_per_channel_kernels_with_tensor_cores(sched, ctx, pdf_grid):
+    """Mode 2 with the tensor-core colour sum (integrand schedule 2) and with the
+    warp-per-event schedule (3): each channel equals a single-process
+    mf_integrate on the same integrand schedule (the same kernels and launch
+    configuration), and the result is stable under graph replay."""
     from paper_2105_10529_gb300.api import Context
-    ctx.set_batch_schedule(2, 2, TILE, 3 * TILE, 0)
+    ctx.set_batch_schedule(2, sched, TILE, 3 * TILE, 0)
     tot, chans = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 2)
     tot2, chans2 = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 2)
     assert [c["sigma"] for c in chans] == [c["sigma"] for c in chans2]
     for i, (p, n) in enumerate(zip(CHANNELS, N_EV)):
         single = Context(dataclasses.replace(PHYS, channel=PHYS.channel + i), pdf_grid, precision=1)
+        single.set_schedule(sched)
         r = single.integrate(p, PHYS.sqrt_s, n, 2)
         single.close()
         assert chans[i]["sigma"] == pytest.approx(r["sigma"], rel=1e-9), p
@@ -160,7 +163,7 @@ def test_batch_graph_cache_invalidation(ctx):
 
 def test_batch_autotune(ctx):
     choice = ctx.autotune_batch(CHANNELS, [40000, 10000, 10000, 8000, 4000], PHYS.sqrt_s)
-    assert choice[0] in (0, 1, 2) and choice[1] in (0, 1, 2) and choice[2] in (1024, 2048, 4096)
+    assert choice[0] in (0, 1, 2) and choice[1] in (0, 1, 2, 3) and choice[2] in (1024, 2048, 4096)
     assert choice[1] < 2 or choice[0] == 2
     assert choice[3] in (2048, 4096) and choice[4] == 0 and choice[5] in (1, 2)
     assert choice[5] == 1 or choice[1] == 1
@@ -182,7 +185,7 @@ def test_batch_bad_arguments(ctx, pdf_grid):
     assert e.value.code == 1
     for bad in [(1, 2, 1024, 4096, 0), (1, 1, 16, 4096, 0), (1, 1, 1024, 16, 0),
                 (1, 1, 1024, 4096, -1), (1, 1, 1024, 4096, 0, 3), (1, 0, 1024, 4096, 0, 2), (3, 1, 1024, 4096, 0),
-                (0, 2, 1024, 4096, 0), (2, 1, 1024, 4096, 0, 2)]:
+                (0, 2, 1024, 4096, 0), (2, 1, 1024, 4096, 0, 2), (1, 3, 1024, 4096, 0), (2, 4, 1024, 4096, 0)]:
         with pytest.raises(MfError):
             ctx.set_batch_schedule(*bad)
     f64 = Context(PHYS, pdf_grid, precision=0)

@@ -116,13 +116,14 @@ def test_observable_leaves_the_integral_unchanged(pdf_grid):
 
 
 def test_observable_heavy_schedules_agree(pdf_grid):
-    """g g -> t tbar g g mixed: the barrier schedule, the tensor-core colour sum
-    and the helicity split fill the same histogram up to FP32 rounding."""
+    """g g -> t tbar g g mixed: the barrier schedule, the tensor-core colour sum,
+    the helicity split and the warp-per-event schedule fill the same histogram
+    up to FP32 rounding."""
     proc, n = IN.GG_TTGG, 60013
     ctx = ctx_for(proc, 1, pdf_grid)
     ctx.set_observable(16, 0.0, 480.0)
     out = []
-    for sched, hs in ((1, 1), (2, 1), (1, 2), (2, 2)):
+    for sched, hs in ((1, 1), (2, 1), (1, 2), (2, 2), (3, 1)):
         ctx.set_schedule(sched)
         ctx.set_helicity_split(hs)
         r = ctx.integrate(proc, PHYS[proc].sqrt_s, n, 1)

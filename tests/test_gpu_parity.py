@@ -186,7 +186,7 @@ def test_bad_arguments(pdf_grid):
     with pytest.raises(MfError):
         ctx.integrate(17, 13000.0, 1000, 2)
     with pytest.raises(MfError):
-        ctx.set_schedule(3)
+        ctx.set_schedule(4)
     ctx.device_status()
     ctx.close()
 
@@ -345,14 +345,16 @@ def test_stored_kinematics_match_recompute(proc, pdf_grid):
     phys = PHYS[proc]
     grid = torch.tensor(random_grid(IN.DIM[proc], seed=41), device="cuda")
     ctx = ctx_for(proc, 1, pdf_grid)
-    for sched in (0, 1, 2):
+    for sched in (0, 1, 2, 3):
         ctx.set_schedule(sched)
         n = 20011 if proc == IN.GG_TTG else 3001
         a, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=6)
         b, _ = ctx.vegas_pass(proc, phys.sqrt_s, grid, n, iteration=6, want_events=True, fields=("w",))
         rel = float(((a - b).abs() / b.abs().clamp_min(1e-300)).max())
-        # FP64 kinematics: a few ulp; the tensor-core kernels also round FP32 apart
-        assert rel < (1e-9 if sched == 2 else 1e-14), (sched, rel)
+        # FP64 kinematics: a few ulp; the tensor-core kernels also round FP32 apart; schedule 3
+        # (g g -> t tbar g g) adds the helicities in another order than the pass with outputs
+        tol = 1e-14 if sched < 2 else (1e-6 if sched == 3 and proc == IN.GG_TTGG else 1e-9)
+        assert rel < tol, (sched, rel)
     ctx.close()
 
 
