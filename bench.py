@@ -36,7 +36,7 @@ FP64_PEAK_NOMINAL_TFLOPS = 1.25
 # default schedule (warp per event, tensor-core colour sum), from the dram__bytes counters of
 # the capture in profiles/integrand_gg_ttgg_mixed_1m_ncu.txt (over 1e6 events; the traffic,
 # evicted local-memory lines, grows with the number of events)
-DRAM_BYTES_PER_EVENT_P3 = None
+DRAM_BYTES_PER_EVENT_P3 = 3809.2
 
 
 def parse():
