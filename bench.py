@@ -395,6 +395,10 @@ def run_ours(args):
     achieved_tflops = flops_launch / kern_avg_s / 1e12
     pk, pk_kind = peaks()
     fp32_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    # the FMA pipes' measured throughput (a microbenchmark of independent FMA chains)
+    from paper_2105_10529_gb300.api import measure_fma_peak
+    fma32 = measure_fma_peak(MF_MIXED, stream)
+    fma64 = measure_fma_peak(MF_FP64, stream)
 
     # ---- FP64 GPU path on a bounded sample and the per-event error of the mixed path
     n64 = args.fp64_events
@@ -488,9 +492,11 @@ def run_ours(args):
                                       "same kernel, scaled to the launch's events (spill lines; grows with events)",
                      "kernel": "integrand_kernel<gg_ttgg, float>",
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz (nominal units and max clock)",
-                     "flops_per_event_me": fl_me, "pass_fraction": pass_frac, "kernel_ms_avg": kern_avg_s * 1e3},
+                     "flops_per_event_me": fl_me, "pass_fraction": pass_frac, "kernel_ms_avg": kern_avg_s * 1e3,
+                     "measured_fma_peak_tflops": fma32, "frac_of_measured_fma_peak": achieved_tflops / fma32},
         "fp64_gpu": {"value": fp64_value, "unit": "events/s", "events": n64,
                      "achieved_tflops": fp64_tflops, "peak_nominal_tflops": FP64_PEAK_NOMINAL_TFLOPS,
+                     "measured_fma_peak_tflops": fma64, "frac_of_measured_fma_peak": fp64_tflops / fma64,
                      "mixed_speedup": value / fp64_value},
         "stated_err": {"per_event_rel_max": float(rel.max()), "per_event_rel_p999": float(np.quantile(rel, 0.999)),
                        "per_event_rel_median": float(np.median(rel)), "sigma_rel_mixed_vs_fp64": sig_rel,

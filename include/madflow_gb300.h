@@ -373,6 +373,17 @@ int mf_set_batch_schedule(struct mf_ctx *ctx, int mode, int sched, long long til
 int mf_autotune_batch(struct mf_ctx *ctx, int n_ch, const int *processes, const long long *n_events, double sqrt_s,
                       int *choice_host);
 
+/* FMA throughput of the current device (no counterpart in the paper): the ALU
+ * peak that the matrix-element kernels, bound by the FMA pipes, are measured
+ * against.  precision MF_MIXED measures FP32, MF_FP64 FP64: 8 CTAs of 256
+ * threads per SM, each thread running 8 independent multiply-add chains,
+ * timed with CUDA events on stream (cudaStream_t or NULL), best of 3 launches
+ * of about 8 ms after one warm-up.  *tflops_host (host, caller-owned): the
+ * rate in TFLOP/s (an FMA counts 2).  The result depends on the SM clock at
+ * the time of the call.  Needs no context; synchronises the stream.
+ * MF_ERR_ARG for a null pointer or another precision. */
+int mf_measure_fma_peak(int precision, void *stream, double *tflops_host);
+
 #ifdef __cplusplus
 }
 #endif

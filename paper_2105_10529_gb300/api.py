@@ -269,6 +269,18 @@ class Context:
         return out
 
 
+def measure_fma_peak(precision: int, stream=None) -> float:
+    """FMA throughput of the current device in TFLOP/s (mf_measure_fma_peak):
+    FP32 for MF_MIXED, FP64 for MF_FP64."""
+    torch = _torch()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    out = C.c_double(0.0)
+    rc = _lib.lib().mf_measure_fma_peak(int(precision), C.c_void_p(s.cuda_stream), C.byref(out))
+    if rc:
+        raise MfError(rc, "mf_measure_fma_peak failed")
+    return float(out.value)
+
+
 def integrate(process: int, sqrt_s: float, n_events: int, n_iter: int, physics: Optional[IN.Physics] = None,
               precision: int = _lib.MF_MIXED):
     """One-shot integrate(process, sqrt_s, n_events, n_iter) -> sigma, error (Sec. 2.1)."""
