@@ -243,6 +243,49 @@ def run_configs(pdf, IN, MF_FP64, MF_MIXED, stream):
     return out
 
 
+def run_derivatives(ctx, phys, IN, grid, stream):
+    """Rates of the derivative and evaluate calls (mixed precision, CUDA events
+    on the stream, one warm-up call each): the m_t-derivative pass of the
+    estimator (mf_vegas_pass_grad) for g g -> t tbar g and g g -> t tbar g g at
+    their full pass sizes and the adapted g g -> t tbar g g grid, and
+    mf_evaluate of g g -> t tbar g g momenta with and without d|M|^2/dp."""
+    import torch
+    from paper_2105_10529_gb300.api import process_info
+
+    def timed(fn):
+        fn()                                       # warm-up
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        res = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / 1e3, res
+
+    out = {}
+    dev = grid.device
+    for proc, n, name in ((IN.GG_TTG, 10_000_000, "gg_ttg"), (IN.GG_TTGG, 4_000_000, "gg_ttgg")):
+        _, dim = process_info(proc)
+        g = grid if proc == IN.GG_TTGG else torch.linspace(0, 1, phys.n_bins + 1, dtype=torch.float64,
+                                                           device=dev).repeat(dim, 1).contiguous()
+        t, r = timed(lambda: ctx.vegas_pass_grad(proc, phys.sqrt_s, g, n, iteration=77))
+        r = r.cpu().tolist()
+        out[f"dsigma_dmt_pass_{name}"] = {"events": n, "events_per_s": n / t, "s": t, "sigma_hat_pb": r[0],
+                                          "dsigma_dmt_pb_per_gev": r[1], "dsigma_dalphas_pb": r[3]}
+    n_ev = 100_000
+    _, ev = ctx.vegas_pass(IN.GG_TTGG, phys.sqrt_s, grid, n_ev, ev_offset=5 * 10**8, iteration=78,
+                           want_events=True, fields=("momenta",))
+    mom = ev["momenta"]
+    t, _ = timed(lambda: ctx.evaluate(IN.GG_TTGG, mom))
+    out["evaluate_gg_ttgg"] = {"points": n_ev, "points_per_s": n_ev / t, "s": t}
+    n_g = 20_000
+    mg = mom[:n_g].contiguous()
+    t, _ = timed(lambda: ctx.evaluate_grad(IN.GG_TTGG, mg))
+    out["evaluate_with_dme2_dp_gg_ttgg"] = {"points": n_g, "points_per_s": n_g / t, "s": t,
+                                            "note": "forward mode: one tangent evaluation per momentum component (24)"}
+    return out
+
+
 METRIC = "gg->ttbar gg weighted events/s, FP32-mixed vs FP64 GPU at stated err; % FP peak"
 
 
@@ -454,6 +497,14 @@ def run_ours(args):
     if not args.no_configs:
         per_config = run_configs(pdf, IN, MF_FP64, MF_MIXED, stream)
 
+    # ---- derivative and evaluate calls
+    derivs = None
+    if not args.no_configs:
+        try:
+            derivs = run_derivatives(ctx, phys, IN, grid, stream)
+        except Exception as exc:            # reported in the line, never fatal to it
+            derivs = {"error": f"{type(exc).__name__}: {exc}"}
+
     # ---- FP64 CPU oracle on the host cores (bounded sample)
     cpu = None
     if not args.no_cpu:
@@ -511,6 +562,8 @@ def run_ours(args):
         line["batch"] = batch
     if per_config:
         line["per_config"] = per_config
+    if derivs:
+        line["derivatives"] = derivs
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist
