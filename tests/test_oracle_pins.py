@@ -501,6 +501,56 @@ def test_ug_ttu_ward_and_lorentz():
         assert abs(O.me2_ug_ttu(MT, GS, boost(p, (0.2, 0.3, -0.4))) * 96 / m2 - 1) < 1e-12
 
 
+def gell_mann_textbook():
+    """T^a = lambda_a / 2 from the textbook Gell-Mann matrices, written out here
+    (independent of the oracle's own generator)."""
+    lam = np.zeros((8, 3, 3), dtype=complex)
+    lam[0][0, 1] = lam[0][1, 0] = 1
+    lam[1][0, 1], lam[1][1, 0] = -1j, 1j
+    lam[2][0, 0], lam[2][1, 1] = 1, -1
+    lam[3][0, 2] = lam[3][2, 0] = 1
+    lam[4][0, 2], lam[4][2, 0] = -1j, 1j
+    lam[5][1, 2] = lam[5][2, 1] = 1
+    lam[6][1, 2], lam[6][2, 1] = -1j, 1j
+    lam[7][0, 0] = lam[7][1, 1] = 1 / math.sqrt(3)
+    lam[7][2, 2] = -2 / math.sqrt(3)
+    return lam / 2
+
+
+@pytest.mark.parametrize("k", [2, 3, 4])
+def test_explicit_colour_sum_equals_colour_matrix_contraction(k):
+    """The third route to the colour sum: for every gluon colour assignment
+    (8^k of them) and quark colours i, j, the full amplitude is
+    M = sum over orderings sigma of (T^a_sigma1 ... T^a_sigmak)_ij A_sigma with the
+    oracle's colour-ordered partial amplitudes A_sigma; sum |M|^2 over colours,
+    spins and polarisations equals the oracle's colour-matrix contraction
+    (or_me2_bg) to 1e-12."""
+    rng = np.random.default_rng(80 + k)
+    p = event_momenta(rng, [MT, MT] + [0.0] * (k - 2), 2200.0)
+    gp, kg = gluon_setup(p, k)
+    T = gell_mann_textbook()
+    perms = list(itertools.permutations(range(k)))
+    letters = "abcdefgh"[:k]
+    # S[sigma][a_1 .. a_k, i, j] = (T^{a_sigma(1)} ... T^{a_sigma(k)})_ij, axes in gluon order
+    chain = ",".join(f"{letters[q]}{'ijklmnop'[q]}{'ijklmnop'[q + 1]}" for q in range(k))
+    strings = []
+    for perm in perms:
+        pos_axes = "".join(letters[q] for q in range(k))         # position q carries gluon perm[q]
+        prod = np.einsum(f"{chain}->{pos_axes}i{'ijklmnop'[k]}", *([T] * k))
+        order = [perm.index(g) for g in range(k)]                # the axis of gluon g
+        strings.append(np.transpose(prod, order + [k, k + 1]))
+    total = 0.0
+    for pols in itertools.product((0, 1), repeat=k):
+        eps = np.array([lin_pol(gp[i], pols[i]) for i in range(k)], dtype=complex)
+        for s3 in (0, 1):
+            for s4 in (0, 1):
+                A = [O.bg_partial(kg, eps, p[2], p[3], MT, GS, s3, s4, perm) for perm in perms]
+                M = sum(a * st for a, st in zip(A, strings))
+                total += float(np.sum(np.abs(M) ** 2))
+    ref = O.me2_bg(k, p, 2, MT, GS)
+    assert abs(total / ref - 1) < 1e-12, (total, ref)
+
+
 # ------------------------------------------------------------------ colour
 
 def test_gellmann_algebra():
