@@ -373,6 +373,35 @@ def test_ee_mumu_z_peak_breit_wigner():
     assert abs(sig / ref - 1) < 1e-12
 
 
+@pytest.mark.parametrize("rs", [20.0, 60.0, 91.19, 130.0, 250.0])
+def test_ee_mumu_vector_axial_form(rs):
+    """Away from the Z peak the photon-Z interference matters, and the two tests
+    above are blind to its sign.  The textbook vector/axial form of the same
+    process: (1/4) sum |M|^2 = e^4 [F1 (1 + c^2) + 2 F2 c] with, for Q_e = Q_mu = -1,
+    v = T3 - 2 Q sW^2, a = T3, chi' = s / (4 sW^2 cW^2 (s - MZ^2 + i MZ GZ)),
+    F1 = 1 + 2 v^2 Re chi' + (v^2 + a^2)^2 |chi'|^2, F2 = 2 a^2 Re chi' + 4 v^2 a^2 |chi'|^2;
+    it gives A_FB = 3 F2 / (4 F1) (the standard vector/axial-vector form of the gamma/Z cross section)."""
+    ph = IN.Physics(sqrt_s=rs)
+    a_em = 1 / ph.alpha_em_inv
+    mz = ph.mz
+    mw2 = mz * mz / 2 + math.sqrt(mz ** 4 / 4 - math.pi * a_em * mz * mz / (math.sqrt(2) * ph.gf))
+    sw2 = 1 - mw2 / mz ** 2; cw2 = 1 - sw2
+    Q, T3 = -1.0, -0.5
+    v, a = T3 - 2 * Q * sw2, T3
+    s = rs * rs
+    chi = s / (4 * sw2 * cw2 * (s - mz * mz + 1j * mz * ph.wz))
+    F1 = Q ** 4 + 2 * Q * Q * v * v * chi.real + (v * v + a * a) ** 2 * abs(chi) ** 2
+    F2 = 2 * Q * Q * a * a * chi.real + 4 * v * v * a * a * abs(chi) ** 2
+    e4 = (4 * math.pi * a_em) ** 2
+    for c in [-0.97, -0.5, 0.0, 0.3, 0.8, 0.99]:
+        ref = e4 * (F1 * (1 + c * c) + 2 * F2 * c)
+        assert abs(O.me2_ee_mumu_closed(ph, ee_momenta(rs, c)) / ref - 1) < 1e-12, c
+    xg, wg = np.polynomial.legendre.leggauss(20)
+    fwd = sum(w * O.me2_ee_mumu_closed(ph, ee_momenta(rs, 0.5 + 0.5 * x)) for x, w in zip(xg, wg)) * 0.5
+    bwd = sum(w * O.me2_ee_mumu_closed(ph, ee_momenta(rs, -0.5 + 0.5 * x)) for x, w in zip(xg, wg)) * 0.5
+    assert abs((fwd - bwd) / (fwd + bwd) - 0.75 * F2 / F1) < 1e-13
+
+
 def test_gg_tt_recursion_equals_combridge():
     rng = np.random.default_rng(21)
     for rs in [360.0, 500.0, 2000.0, 8000.0]:
