@@ -580,6 +580,47 @@ def test_explicit_colour_sum_equals_colour_matrix_contraction(k):
     assert abs(total / ref - 1) < 1e-12, (total, ref)
 
 
+def _collinear_ug_config(E1, E2, x, lam, phi, th, ph):
+    """u(p1) g(p2) -> t(p3) tbar(p4) u(p5) with p5 = (1 - x) p1 + k_T, |k_T| = lam E1
+    at azimuth phi; the t tbar pair has the fixed direction (th, ph) in its rest frame."""
+    p1 = np.array([E1, 0.0, 0.0, E1]); p2 = np.array([E2, 0.0, 0.0, -E2])
+    kt, pz = lam * E1, (1 - x) * E1
+    p5 = np.array([math.hypot(kt, pz), kt * math.cos(phi), kt * math.sin(phi), pz])
+    Q = p1 + p2 - p5
+    M = math.sqrt(Q[0] ** 2 - Q[1:] @ Q[1:])
+    pst = math.sqrt(M * M / 4 - MT * MT)
+    n = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+    b = Q[1:] / Q[0]
+    out = []
+    for sgn in (1.0, -1.0):
+        q = np.concatenate([[M / 2], sgn * pst * n])
+        out.append(boost(q[None, :], b)[0] if b @ b > 0 else q)
+    return p1, p2, out[0], out[1], p5
+
+
+@pytest.mark.parametrize("x, th, ph", [(0.6, 1.1, 0.4), (0.3, 2.3, -1.0)])
+def test_ug_ttu_initial_state_collinear_limit(x, th, ph):
+    """Absolute normalisation of u g -> t tbar u (which the Ward and Lorentz pins
+    cannot fix): when the final u becomes collinear to the incoming u, the
+    spin- and colour-averaged |M|^2, averaged over the azimuth of k_T, factorises
+    onto g g -> t tbar (pinned to Combridge's closed form) with the q -> g
+    splitting function:  |M|^2 -> (1/x) (g_s^2 / p1.p5) C_F (1 + (1-x)^2)/x |M_gg|^2(x p1, p2).
+    The corrections fall like k_T^2."""
+    E1, E2 = 1000.0, 700.0
+    p1, p2, h3, h4, _ = _collinear_ug_config(E1, E2, x, 0.0, 0.0, th, ph)
+    gg = O.me2_gg_tt_closed(MT, GS, np.array([x * p1, p2, h3, h4]))
+    dev = []
+    for lam in (1e-2, 1e-3, 1e-4):
+        r = []
+        for j in range(8):                       # 8 azimuths average the cos 2 phi correlation exactly
+            p1, p2, p3, p4, p5 = _collinear_ug_config(E1, E2, x, lam, 2 * math.pi * j / 8, th, ph)
+            lim = (1 / x) * (GS * GS / mdot(p1, p5)) * (4 / 3) * (1 + (1 - x) ** 2) / x * gg
+            r.append(O.me2_ug_ttu(MT, GS, np.array([p1, p2, p3, p4, p5])) / lim)
+        dev.append(abs(np.mean(r) - 1))
+    assert dev[1] < 1e-4 and dev[2] < 1e-6, dev
+    assert dev[1] < 0.03 * dev[0] and dev[2] < 0.03 * dev[1], dev      # quadratic in k_T
+
+
 # ------------------------------------------------------------------ colour
 
 def test_gellmann_algebra():
