@@ -621,6 +621,75 @@ def test_ug_ttu_initial_state_collinear_limit(x, th, ph):
     assert dev[1] < 0.03 * dev[0] and dev[2] < 0.03 * dev[1], dev      # quadratic in k_T
 
 
+def _tt_pair(Q, th, ph):
+    """t and tbar with total momentum Q, back to back along (th, ph) in their rest frame."""
+    M = math.sqrt(Q[0] ** 2 - Q[1:] @ Q[1:])
+    pst = math.sqrt(M * M / 4 - MT * MT)
+    n = np.array([math.sin(th) * math.cos(ph), math.sin(th) * math.sin(ph), math.cos(th)])
+    pair = np.array([np.concatenate([[M / 2], pst * n]), np.concatenate([[M / 2], -pst * n])])
+    return boost(pair, Q[1:] / Q[0])
+
+
+def _p_gg(x):
+    """Unregularised g -> g splitting function, azimuth-averaged, in 4 dimensions."""
+    return 2 * 3.0 * (x / (1 - x) + (1 - x) / x + x * (1 - x))
+
+
+def test_gg_ttg_initial_state_collinear_limit():
+    """Absolute normalisation of g g -> t tbar g: with the final gluon along the
+    incoming gluon p1, the azimuth-averaged averaged |M|^2 tends to
+    (1/x) (g_s^2 / p1.p5) P_gg(x) |M|^2(g g -> t tbar) at (x p1, p2), the 2 -> 2
+    result being Combridge's closed form; corrections fall like k_T^2."""
+    E1, E2, x, th, ph = 1000.0, 700.0, 0.6, 1.1, 0.4
+    p1 = np.array([E1, 0.0, 0.0, E1]); p2 = np.array([E2, 0.0, 0.0, -E2])
+    h3, h4 = _tt_pair(x * p1 + p2, th, ph)
+    born = O.me2_gg_tt_closed(MT, GS, np.array([x * p1, p2, h3, h4]))
+    dev = []
+    for lam in (1e-2, 1e-3, 1e-4):
+        r = []
+        for j in range(8):
+            phi = 2 * math.pi * j / 8
+            kt, pz = lam * E1, (1 - x) * E1
+            p5 = np.array([math.hypot(kt, pz), kt * math.cos(phi), kt * math.sin(phi), pz])
+            p3, p4 = _tt_pair(p1 + p2 - p5, th, ph)
+            full = O.me2_bg(3, np.array([p1, p2, p3, p4, p5]), 2, MT, GS) / 256
+            r.append(full / ((1 / x) * (GS * GS / mdot(p1, p5)) * _p_gg(x) * born))
+        dev.append(abs(np.mean(r) - 1))
+    assert dev[1] < 1e-5 and dev[2] < 1e-7, dev
+    assert dev[1] < 0.03 * dev[0] and dev[2] < 0.03 * dev[1], dev
+
+
+def test_gg_ttgg_final_state_collinear_limit():
+    """Absolute normalisation of g g -> t tbar g g (identical-gluon factor 1/2
+    included): with the two final gluons collinear, momentum fractions z and
+    1 - z of P, the azimuth-averaged averaged |M|^2 tends to
+    (1/2) (g_s^2 / p5.p6) P_gg(z) |M|^2(g g -> t tbar g) at P, the latter pinned by
+    the previous test; corrections fall like k_T^2."""
+    E1, E2, th, ph, z, EP = 1000.0, 700.0, 1.1, 0.4, 0.35, 600.0
+    p1 = np.array([E1, 0.0, 0.0, E1]); p2 = np.array([E2, 0.0, 0.0, -E2])
+    nP = np.array([math.sin(0.9) * math.cos(2.0), math.sin(0.9) * math.sin(2.0), math.cos(0.9)])
+    v1 = np.cross(nP, [0.0, 0.0, 1.0]); v1 /= np.linalg.norm(v1)
+    v2 = np.cross(nP, v1)
+    P = np.concatenate([[EP], EP * nP])
+    h3, h4 = _tt_pair(p1 + p2 - P, th, ph)
+    born = O.me2_bg(3, np.array([p1, p2, h3, h4, P]), 2, MT, GS) / 256
+    dev = []
+    for lam in (1e-2, 1e-3, 1e-4):
+        r = []
+        for j in range(8):
+            phi = 2 * math.pi * j / 8
+            vt = math.cos(phi) * v1 + math.sin(phi) * v2
+            a = z * EP * nP + lam * EP * vt
+            b = (1 - z) * EP * nP - lam * EP * vt
+            p5 = np.concatenate([[np.linalg.norm(a)], a]); p6 = np.concatenate([[np.linalg.norm(b)], b])
+            p3, p4 = _tt_pair(p1 + p2 - p5 - p6, th, ph)
+            full = O.me2_bg(4, np.array([p1, p2, p3, p4, p5, p6]), 2, MT, GS) / 256 * 0.5
+            r.append(full / (0.5 * (GS * GS / mdot(p5, p6)) * _p_gg(z) * born))
+        dev.append(abs(np.mean(r) - 1))
+    assert dev[1] < 1e-4 and dev[2] < 1e-6, dev
+    assert dev[1] < 0.03 * dev[0] and dev[2] < 0.03 * dev[1], dev
+
+
 # ------------------------------------------------------------------ colour
 
 def test_gellmann_algebra():
