@@ -269,10 +269,11 @@ def test_cuts_argument(pdf_grid):
 
 def test_full_size_pass_sampled_against_oracle(pdf_grid, opdf):
     """The benchmark's workload at full size: one mixed-precision pass of
-    4e6 g g -> t tbar g g events in the launch configuration the benchmark
-    times (default schedule, as many CTAs as fit), with per-event outputs; a
-    seeded sample of events is recomputed one by one by the oracle, and the
-    pass sums equal the sums of the per-event weights."""
+    4e6 g g -> t tbar g g events, as many CTAs as fit, with per-event outputs
+    (which run the tensor-core schedule 2; test_gpu_warp_per_event ties the
+    benchmark's schedule 3 to it at the same size); a seeded sample of events is
+    recomputed one by one by the oracle, and the pass sums equal the sums of
+    the per-event weights."""
     proc = IN.GG_TTGG
     phys = IN.Physics(seed=3)            # the benchmark's physics
     n = 4_000_000
@@ -389,9 +390,9 @@ def test_helicity_split_pass(proc, pdf_grid, opdf):
 
 
 def test_helicity_split_integrate(pdf_grid):
-    """Iterated VEGAS of g g -> t tbar g g with the helicity split on the
-    default (tensor-core) schedule agrees with no split to rounding; the pass
-    with per-event outputs ignores the split."""
+    """Iterated VEGAS of g g -> t tbar g g with the helicity split (which runs the
+    tensor-core schedule 2 under the default schedule 3) agrees with no split to
+    rounding; the pass with per-event outputs ignores the split."""
     proc = IN.GG_TTGG
     phys = PHYS[proc]
     ctx = ctx_for(proc, 1, pdf_grid)
