@@ -188,9 +188,9 @@ int mf_get_observable(struct mf_ctx *ctx, double *hist_host, double *err_host, d
  * other one of the helicities the matrix element evaluates (Sec. 2.2's
  * helicity sum split in two), and the pair adds its halves; a CTA then
  * holds half as many events at a time.  Applies to
- * g g -> t tbar g and g g -> t tbar g g in MF_MIXED under schedules 1 and 2,
- * in mf_vegas_pass without per-event outputs and in mf_integrate; elsewhere
- * it acts as 1.  Results differ from parts = 1 by FP32 rounding only.
+ * g g -> t tbar g and g g -> t tbar g g in MF_MIXED under schedules 1, 2 and 3
+ * (with 3 it runs schedule 2's kernel), in mf_vegas_pass without per-event
+ * outputs and in mf_integrate; elsewhere it acts as 1.  Results differ from parts = 1 by FP32 rounding only.
  * MF_ERR_ARG for other values. */
 int mf_set_helicity_split(struct mf_ctx *ctx, int parts);
 
