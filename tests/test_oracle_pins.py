@@ -260,6 +260,48 @@ def test_rambo_massive_three_body_volume_by_quadrature():
     assert abs(mc - vol) < 4 * err, (mc, vol, err)
 
 
+def _phi2(ss, ma, mb):
+    """Two-body phase-space volume sqrt(lambda(s, ma^2, mb^2)) / (8 pi s)."""
+    lam = ss * ss + ma ** 4 + mb ** 4 - 2 * ss * ma * ma - 2 * ss * mb * mb - 2 * ma * ma * mb * mb
+    return math.sqrt(max(lam, 0.0)) / (8 * math.pi * ss)
+
+
+def _phi_recursive(ss, masses, order=120):
+    """n-body phase-space volume by the recursion
+    Phi_n(s; m1, rest) = int dq / (2 pi) Phi_2(s; m1, sqrt q) Phi_{n-1}(q; rest),
+    Gauss-Legendre in q over its kinematic range at every level."""
+    if len(masses) == 2:
+        return _phi2(ss, masses[0], masses[1])
+    m1, rest = masses[0], masses[1:]
+    lo, hi = sum(rest) ** 2, (math.sqrt(ss) - m1) ** 2
+    xg, wg = np.polynomial.legendre.leggauss(order)
+    qs = 0.5 * (hi - lo) * (xg + 1) + lo
+    return sum(0.5 * (hi - lo) * w / (2 * math.pi) * _phi2(ss, m1, math.sqrt(q)) * _phi_recursive(q, rest, order)
+               for q, w in zip(qs, wg))
+
+
+@pytest.mark.parametrize("n", [4, 5])
+def test_rambo_massless_weight_equals_recursive_volume(n):
+    """Massless RAMBO has a constant weight; for 4 and 5 particles (where a slip in
+    the factorials or powers of the volume would first show) it equals the
+    phase-space volume built recursively from two-body volumes."""
+    rs = 700.0
+    ref = _phi_recursive(rs * rs, [0.0] * n, order=40)
+    _, w = O.rambo(n, rs, [0.0] * n, np.random.default_rng(6).random(4 * n))
+    assert abs(w / ref - 1) < 1e-12, (w, ref)
+
+
+def test_rambo_massive_four_body_volume_by_quadrature():
+    """The g g -> t tbar g g phase space: <RAMBO weight> over the uniforms equals
+    Phi_4(s; m, m, 0, 0) from the two-body recursion (nested quadrature)."""
+    rs, m = 900.0, MT
+    vol = _phi_recursive(rs * rs, [m, m, 0.0, 0.0], order=60)
+    rng = np.random.default_rng(7)
+    ws = np.array([O.rambo(4, rs, [m, m, 0.0, 0.0], rng.random(16))[1] for _ in range(40000)])
+    mc, err = ws.mean(), ws.std() / math.sqrt(len(ws))
+    assert abs(mc - vol) < 4 * err and err < 0.01 * vol, (mc, vol, err)
+
+
 # ------------------------------------------------------------------ a5, a6
 
 def test_cuts_hand_built():
