@@ -390,6 +390,29 @@ def test_pdf_bicubic_exact_on_quadratics_and_nodes():
     assert noisy.xf(0, x, 1e9) == noisy.xf(0, x, 1e8)
 
 
+def test_pdf_bicubic_exact_on_linear_fields_in_every_cell():
+    """A field linear in (ln x, ln Q^2) has exact central and one-sided node
+    differences, so the Hermite interpolation reproduces it in every cell,
+    the edge cells of both directions included (the quadratic test above
+    stays inside, where only the central differences act)."""
+    nx, nq = 100, 50
+    lx = np.linspace(math.log(1e-6), 0.0, nx)
+    lq = np.linspace(0.0, math.log(1e8), nq)
+    LX, LQ = np.meshgrid(lx, lq, indexing="ij")
+    f = lambda a, b: 40.0 + 1.3 * a - 0.7 * b
+    pdf = O.Pdf(np.stack([f(LX, LQ)] * 3))
+    rng = np.random.default_rng(10)
+    cells_x = [0, 1, nx - 3, nx - 2]
+    cells_q = [0, 1, nq - 3, nq - 2]
+    for i in cells_x:
+        for j in cells_q:
+            for _ in range(4):
+                a = lx[i] + rng.random() * (lx[i + 1] - lx[i])
+                b = lq[j] + rng.random() * (lq[j + 1] - lq[j])
+                v = pdf.xf(0, math.exp(a), math.exp(b))
+                assert abs(v - f(a, b)) < 1e-12 * abs(f(a, b)), (i, j, v, f(a, b))
+
+
 def test_pdf_grid_momentum_sum():
     """Without noise the gluon grid carries momentum fraction 1/2 at Q^2 = 1."""
     g = IN.make_pdf_grid(noise=0.0)
