@@ -74,31 +74,35 @@ typedef struct {
 
 int or_proc_info_get(int proc, or_proc_info *out);
 
-/* a1: Philox4x32-10 and the per-event uniform stream */
+/* Philox4x32-10 (Salmon et al., SC'11) and the per-event uniform stream: the random
+ * numbers that start the paper's event pipeline (Sec. 2.1) */
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
 double or_u01(uint32_t a, uint32_t b);
 void or_uniforms(uint64_t seed, uint64_t event, uint32_t iteration, uint32_t channel,
                  int dim, double *u);
 
-/* a2, a12-a14: VEGAS */
+/* VEGAS (Lepage 1978; the paper's integrator, Sec. 1): map, grid refinement and the
+ * combination of iterations */
 void or_vegas_init(double *grid, int dim, int nb);
 double or_vegas_map(const double *grid, int dim, int nb, const double *u, double *x, uint8_t *bins);
 void or_vegas_refine(const double *hist, double *grid, int dim, int nb, double alpha);
 void or_vegas_combine(int n_iter, const double *I, const double *var,
                       double *mean, double *err, double *chi2dof);
 
-/* a3: parton-luminosity map */
+/* parton-luminosity map from two uniforms to x1, x2 (a choice of this library; the
+ * paper does not give one) */
 void or_parton_map(double x0, double v, double tau0, double *x1, double *x2, double *jac);
 
-/* a4: RAMBO (massive), output momenta (E,px,py,pz) in the partonic rest frame */
+/* RAMBO (Kleiss, Stirling, Ellis 1986) with the massive rescaling; output momenta
+ * (E,px,py,pz) in the partonic rest frame */
 int or_rambo(int n, double sqrt_shat, const double *masses, const double *u, double *p, double *weight);
 double or_rambo_massless_volume(int n, double shat);
 
-/* a5-a6: cuts and factorisation scale */
+/* fiducial cuts and factorisation scale (Sec. 2.1: phase space with cuts) */
 int or_cuts(int proc, const or_params *P, const double *plab /* n_ext x 4 */);
 double or_muf2(int proc, const or_params *P, const double *p /* n_ext x 4 */);
 
-/* a7: log-bicubic PDF.  grid: n_flav x nx x nq values of x f(x,Q^2) on
+/* log-bicubic PDF interpolation (the PDF stage of Sec. 1, LHAPDF6 scheme).  grid: n_flav x nx x nq values of x f(x,Q^2) on
  * ln-uniform nodes x in [x_min,1], Q^2 in [q2_min,q2_max]. */
 typedef struct {
     const double *xf; int n_flav, nx, nq;
@@ -106,7 +110,7 @@ typedef struct {
 } or_pdf;
 double or_pdf_xf(const or_pdf *pdf, int flav, double x, double q2);
 
-/* a8-a10: squared matrix elements, spin/colour averaged, including the
+/* squared matrix elements (Sec. 2.2), spin/colour averaged, including the
  * identical-particle factor; momenta n_ext x 4, incoming first. */
 double or_me2(int proc, const or_params *P, const double *p);
 double or_me2_ee_mumu_closed(const or_params *P, const double *p);
@@ -131,7 +135,7 @@ double or_me2_uu_tt_diagram(double mt, double gs, const double *p);
  * spins and colours of |M|^2, which gauge invariance sets to zero (Ward test) */
 double or_amp2_ug_ttu_ward(double mt, double gs, const double *p);
 
-/* the whole per-event integrand, a1..a11 */
+/* the whole per-event integrand (Sec. 2.1): random numbers to event weight */
 typedef struct {
     double u[32], x[32];
     uint8_t bins[32];

@@ -1,5 +1,6 @@
 /*
- * Oracle: the per-event integrand (a1-a11) and the VEGAS passes (a12-a14).
+ * Oracle: the per-event integrand (Sec. 2.1: random numbers to event weight) and the
+ * VEGAS passes (sums, per-bin histograms, refinement, combination).
  * TEST INFRASTRUCTURE ONLY (see mf_oracle.h).
  *
  * The event pipeline runs in the order of Sec. 2.1 of the paper: random

@@ -18,7 +18,7 @@
 #define M_PI 3.14159265358979323846
 #endif
 
-/* a3: tau = tau0^x0, x1 = tau^v, x2 = tau^(1-v); dx1 dx2 = tau |ln tau| |ln tau0| dx0 dv. */
+/* Parton-luminosity map: tau = tau0^x0, x1 = tau^v, x2 = tau^(1-v); dx1 dx2 = tau |ln tau| |ln tau0| dx0 dv. */
 void or_parton_map(double x0, double v, double tau0, double *x1, double *x2, double *jac)
 {
     double lt0 = log(tau0);
@@ -39,7 +39,7 @@ double or_rambo_massless_volume(int n, double shat)
            / (factorial(n - 1) * factorial(n - 2));
 }
 
-/* a4: RAMBO.  Four uniforms per particle give an isotropic massless momentum
+/* RAMBO (Kleiss, Stirling, Ellis 1986).  Four uniforms per particle give an isotropic massless momentum
  * with energy -ln(u3 u4); a conformal transformation (boost + scale) brings
  * the sum to (sqrt(shat), 0); masses are then restored by a common rescaling
  * xi of the three-momenta found by Newton's method, with the massive weight
@@ -108,7 +108,7 @@ int or_rambo(int n, double sqrt_shat, const double *masses, const double *u, dou
 
 static double pt2_of(const double *p) { return p[1] * p[1] + p[2] * p[2]; }
 
-/* a5: fiducial cuts on the final light partons in the lab frame:
+/* Fiducial cuts on the final light partons in the lab frame:
  * pT > pt_min, |eta| < eta_max (tested as |pz| < pT sinh(eta_max)), and
  * Delta R > dr_min between final gluons.  Returns 1 when the event passes. */
 int or_cuts(int proc, const or_params *P, const double *plab)
@@ -137,7 +137,7 @@ int or_cuts(int proc, const or_params *P, const double *plab)
     return 1;
 }
 
-/* a6: mu_F = m_t for the 2 -> 2 top channels, H_T/2 with H_T the sum of the
+/* Factorisation scale: mu_F = m_t for the 2 -> 2 top channels, H_T/2 with H_T the sum of the
  * final-state transverse masses otherwise; returns mu_F^2. */
 double or_muf2(int proc, const or_params *P, const double *p)
 {
@@ -172,7 +172,7 @@ static double hermite(double f0, double f1, double d0, double d1, double h, doub
     return h00 * f0 + h10 * h * d0 + h01 * f1 + h11 * h * d1;
 }
 
-/* a7: x f(x, Q^2) by cubic Hermite in ln x along every Q^2 row that the
+/* PDF: x f(x, Q^2) by cubic Hermite in ln x along every Q^2 row that the
  * Q^2 step needs, then cubic Hermite in ln Q^2 over those row values.
  * ln Q^2 outside the grid is clamped to its edge. */
 double or_pdf_xf(const or_pdf *pdf, int flav, double x, double q2)

@@ -1,5 +1,5 @@
 /*
- * Oracle: squared matrix elements (steps a8-a10).
+ * Oracle: squared matrix elements (Sec. 2.2: wavefunctions, amplitudes, colour sum).
  * TEST INFRASTRUCTURE ONLY (see mf_oracle.h).
  *
  * Sec. 2.2 of the paper: the squared amplitude is the sum over external

@@ -1,5 +1,6 @@
 /*
- * Oracle: random numbers (step a1) and the VEGAS integrator (steps a2, a12-a14).
+ * Oracle: random numbers (Philox) and the VEGAS integrator (map, per-bin sums,
+ * refinement and the combination of iterations).
  * TEST INFRASTRUCTURE ONLY (see mf_oracle.h).
  *
  * The paper's integrator (Sec. 1, the VegasFlow library; Sec. 2.1, where the
