@@ -187,6 +187,27 @@ def test_vegas_refine_scale_invariance_and_mirror_symmetry():
     assert np.all(np.diff(a, axis=1) > 0)      # edges stay ordered
 
 
+def test_vegas_combine_worked_example_and_invariances():
+    """Weighted mean of iterations with weights 1/V_k.  By hand for I = (1, 2),
+    V = (1, 4): mean (1 + 2/4)/(1 + 1/4) = 1.2, error (1 + 1/4)^(-1/2), chi^2 =
+    0.2^2/1 + 0.8^2/4 = 0.2 on one degree of freedom.  The result does not depend
+    on the order of the iterations, scales with I when the errors scale alike,
+    and equal iterations give chi^2 = 0 (up to rounding)."""
+    m, err, chi2 = O.vegas_combine([1.0, 2.0], [1.0, 4.0])
+    assert abs(m - 1.2) < 1e-15 and abs(err - 1 / math.sqrt(1.25)) < 1e-15 and abs(chi2 - 0.2) < 1e-15
+    rng = np.random.default_rng(11)
+    I = rng.normal(5.0, 0.3, 7); V = rng.uniform(0.01, 0.2, 7)
+    a = O.vegas_combine(list(I), list(V))
+    perm = rng.permutation(7)
+    b = O.vegas_combine(list(I[perm]), list(V[perm]))
+    assert np.allclose(a, b, rtol=1e-13, atol=0)
+    c = O.vegas_combine(list(3.0 * I), list(9.0 * V))
+    assert abs(c[0] - 3 * a[0]) < 1e-13 * abs(a[0]) and abs(c[1] - 3 * a[1]) < 1e-13 * a[1]
+    assert abs(c[2] - a[2]) < 1e-12 * max(a[2], 1.0)
+    d = O.vegas_combine([2.5] * 4, [0.1, 0.2, 0.3, 0.4])
+    assert abs(d[0] - 2.5) < 4 * np.spacing(2.5) and d[2] < 1e-25      # zero up to rounding
+
+
 def test_vegas_integrates_peaked_function():
     """VEGAS map + refine + combine on a separable Gaussian peak in 3-D with a
     known integral; the result must lie within 4 sigma and the error must
