@@ -490,12 +490,18 @@ def run_ours(args):
     # with uneven sizes in one persistent launch per iteration (graph-replayed)
     batch = None
     if not args.no_batch:
-        batch = run_batch(ctx, phys, IN, args.batch_iters)
+        try:
+            batch = run_batch(ctx, phys, IN, args.batch_iters)
+        except Exception as exc:            # reported in the line, never fatal to it
+            batch = {"error": f"{type(exc).__name__}: {exc}"}
 
     # ---- the other single-process workloads (e+e-, gg -> t tbar, gg -> t tbar g)
     per_config = None
     if not args.no_configs:
-        per_config = run_configs(pdf, IN, MF_FP64, MF_MIXED, stream)
+        try:
+            per_config = run_configs(pdf, IN, MF_FP64, MF_MIXED, stream)
+        except Exception as exc:            # reported in the line, never fatal to it
+            per_config = {"error": f"{type(exc).__name__}: {exc}"}
 
     # ---- derivative and evaluate calls
     derivs = None
@@ -508,17 +514,20 @@ def run_ours(args):
     # ---- FP64 CPU oracle on the host cores (bounded sample)
     cpu = None
     if not args.no_cpu:
-        import oracle as O
-        cores = os.cpu_count() or 1
-        n_cpu = max(200, 1500 * cores)
-        opdf = O.Pdf(pdf)
-        gnp = grid.cpu().numpy()
-        O.vegas_pass(proc, phys, opdf, gnp, 64, iteration=0, n_threads=cores)
-        t0 = time.perf_counter()
-        O.vegas_pass(proc, phys, opdf, gnp, n_cpu, iteration=7, n_threads=cores)
-        dt = time.perf_counter() - t0
-        cpu = {"value": n_cpu / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
-               "sample": f"{n_cpu} events of one iteration at the adapted grid ({dt:.1f} s)"}
+        try:
+            import oracle as O
+            cores = os.cpu_count() or 1
+            n_cpu = max(200, 1500 * cores)
+            opdf = O.Pdf(pdf)
+            gnp = grid.cpu().numpy()
+            O.vegas_pass(proc, phys, opdf, gnp, 64, iteration=0, n_threads=cores)
+            t0 = time.perf_counter()
+            O.vegas_pass(proc, phys, opdf, gnp, n_cpu, iteration=7, n_threads=cores)
+            dt = time.perf_counter() - t0
+            cpu = {"value": n_cpu / dt, "unit": "events/s", "cores": cores, "kind": "oracle",
+                   "sample": f"{n_cpu} events of one iteration at the adapted grid ({dt:.1f} s)"}
+        except Exception as exc:            # reported in the line, never fatal to it
+            cpu = {"error": f"{type(exc).__name__}: {exc}", "kind": "oracle"}
 
     line = {
         "metric": METRIC,
