@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline leg")
     ap.add_argument("--no-batch", action="store_true", help="skip the batched p p -> t tbar + jets leg")
     ap.add_argument("--no-configs", action="store_true",
-                    help="skip the leg that runs the other single-process workloads at full size")
+                    help="skip the legs that run the other single-process workloads at full size and time "
+                         "the derivative and evaluate calls")
     ap.add_argument("--batch-iters", type=int, default=10)
     ap.add_argument("--sched", type=int, default=None,
                     help="integrand schedule (0 free warps, 1 CTA barrier per helicity, 2 = 1 + colour sum on the "
