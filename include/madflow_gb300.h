@@ -227,7 +227,12 @@ int mf_integrate(struct mf_ctx *ctx, int process, double sqrt_s, const mf_cuts *
  * sums_dev: [2 + dim n_bins] receives sum w, sum w^2 and the histogram
  * of w^2 (w includes the 1/n_events of the estimator).  mask_in_dev
  * (nullable, [n_events]) freezes the cut masks.  ev (nullable) requests the
- * per-event outputs.  Does not synchronise. */
+ * per-event outputs (device arrays, caller-owned; a NULL member is skipped):
+ * u, x [n_events][dim], bins [n_events][dim], w, mask, me2 [n_events],
+ * momenta [n_events][n_ext][4] in the partonic rest frame.  Under schedule 3
+ * and the helicity split the pass with outputs runs the very kernel that runs
+ * without them (the stores are a run-time choice), so its outputs are those
+ * of the timed configuration.  Does not synchronise. */
 int mf_vegas_pass(struct mf_ctx *ctx, int process, double sqrt_s, const double *grid_dev, long long n_events,
                   long long ev_offset, unsigned int iteration, const unsigned char *mask_in_dev, double *sums_dev,
                   const mf_event_arrays *ev);
@@ -249,6 +254,10 @@ int mf_vegas_refine(struct mf_ctx *ctx, int dim, int n_bins, double alpha, const
  * Inputs: cfg (host), pdf_dev [n_flav][nx][nq] and grid_dev [dim][n_bins+1]
  * (device, caller-owned, same meaning as for mf_create / mf_vegas_pass).
  * Output: sums_dev [2 + dim n_bins] (device): sum w, sum w^2, histogram.
+ * Kernel: integrand schedule 0 (one event per thread, colour sum on the FMA
+ * pipes) whatever the precision; for g g -> t tbar g g in MF_MIXED its sums
+ * therefore differ from a context's default schedule 3 by FP32 rounding
+ * (about 1e-6 relative) and it runs slower.
  * Scratch: a fixed 4 MiB array inside the library (the per-CTA partial
  * sums and two counters), held by every GPU that loads the library until the
  * process exits.  The first call on a device looks up that array's device
@@ -330,6 +339,23 @@ int mf_evaluate(struct mf_ctx *ctx, int process, const double *momenta_dev, long
 int mf_integrate_batch(struct mf_ctx *ctx, int n_ch, const int *processes, const long long *n_events, double sqrt_s,
                        const mf_cuts *cuts, int n_iter, int want_grads, struct mf_result *per_ch_host,
                        struct mf_result *total_host, double *grids_host);
+
+/* One pass of a batch of channels at caller grids, with optional per-event
+ * outputs: the inspection call of mf_integrate_batch, as mf_vegas_pass is of
+ * mf_integrate (no counterpart in the paper).  Runs the kernels of the
+ * current batch schedule (mf_set_batch_schedule; the persistent kernel in
+ * modes 0 and 1) once, without refinement, on events [0, n_events[i]) of
+ * Philox iteration `iteration` and channel cfg.channel + i, at the
+ * configuration's cuts.  grids_dev (device) [n_ch][18][n_bins+1]: each
+ * channel's grid in its first dim rows; sums_dev (device)
+ * [n_ch][2 + 18 n_bins]: each channel's pass sums as mf_vegas_pass (first
+ * 2 + dim n_bins entries written).  ev_host (host, nullable) [n_ch]: per
+ * channel the per-event device arrays of mf_vegas_pass (NULL members
+ * skipped), written by the same kernels that run without them.
+ * Other arguments and errors as mf_integrate_batch.  Orders itself after
+ * work already queued on the context's stream; synchronises. */
+int mf_batch_pass(struct mf_ctx *ctx, int n_ch, const int *processes, const long long *n_events, double sqrt_s,
+                  const double *grids_dev, unsigned int iteration, double *sums_dev, const mf_event_arrays *ev_host);
 
 /* d sigma_total / d m_t of a batch: one derivative pass per channel (as
  * mf_vegas_pass_grad, mixed precision) at the final grids left by the last

@@ -91,6 +91,8 @@ def lib():
                                              C.POINTER(MfResult), dp]),
             "mf_batch_grad": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double,
                                         C.POINTER(MfCuts), C.c_uint, dp]),
+            "mf_batch_pass": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double, vp, C.c_uint,
+                                        vp, C.POINTER(MfEventArrays)]),
             "mf_set_batch_schedule": (C.c_int, [vp, C.c_int, C.c_int, i64, i64, C.c_int, C.c_int]),
             "mf_autotune_batch": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double,
                                             C.POINTER(C.c_int)]),
@@ -108,5 +110,5 @@ def exported_symbols():
     return ["mf_default_config", "mf_process_info", "mf_create", "mf_destroy", "mf_last_error",
             "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_set_helicity_split", "mf_set_observable", "mf_get_observable", "mf_device_status", "mf_selftest_wait", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
             "mf_vegas_pass_static", "mf_set_couplings", "mf_vegas_pass_grad",
-            "mf_integrate_batch", "mf_batch_grad", "mf_set_batch_schedule", "mf_autotune_batch",
+            "mf_integrate_batch", "mf_batch_pass", "mf_batch_grad", "mf_set_batch_schedule", "mf_autotune_batch",
             "mf_measure_fma_peak"]

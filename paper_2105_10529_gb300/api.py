@@ -171,6 +171,39 @@ class Context:
                 chans[i]["grid"] = grids[i, :process_info(p)[1]].copy()
         return d(tot), chans
 
+    def batch_pass(self, processes, n_events, sqrt_s: float, grids, iteration: int = 0, want_events: bool = False,
+                   fields=None):
+        """One pass of a batch at caller grids (mf_batch_pass): grids [n_ch][18][n_bins+1] (device
+        tensor; each channel's first dim rows used).  Returns (sums [n_ch][2 + 18 n_bins], list of
+        per-channel event dicts or None)."""
+        torch = _torch()
+        n_ch = len(processes)
+        dev = torch.device("cuda", torch.cuda.current_device())
+        nb = self.cfg.n_bins
+        grids = grids.to(device=dev, dtype=torch.float64).contiguous()
+        assert tuple(grids.shape) == (n_ch, 18, nb + 1)
+        sums = torch.zeros((n_ch, 2 + 18 * nb), dtype=torch.float64, device=dev)
+        procs = (C.c_int * n_ch)(*[int(p) for p in processes])
+        ns = (C.c_longlong * n_ch)(*[int(n) for n in n_events])
+        evs, arr = None, None
+        if want_events:
+            fields = fields or ("u", "x", "bins", "w", "mask", "me2", "momenta")
+            evs, arr = [], (MfEventArrays * n_ch)()
+            for i, p in enumerate(processes):
+                n_ext, dim = process_info(p)
+                n = int(n_events[i])
+                shapes = dict(u=((n, dim), torch.float64), x=((n, dim), torch.float64),
+                              bins=((n, dim), torch.uint8), w=((n,), torch.float64), mask=((n,), torch.uint8),
+                              me2=((n,), torch.float64), momenta=((n, n_ext, 4), torch.float64))
+                e = {f: torch.empty(*shapes[f][0], dtype=shapes[f][1], device=dev) for f in fields}
+                evs.append(e)
+                arr[i] = MfEventArrays(**{f: C.c_void_p(e[f].data_ptr()) if f in e else None
+                                          for f, _ in MfEventArrays._fields_})
+        rc = _lib.lib().mf_batch_pass(self.ptr, n_ch, procs, ns, sqrt_s, C.c_void_p(grids.data_ptr()), iteration,
+                                      C.c_void_p(sums.data_ptr()), arr)
+        _check(self.ptr, rc)
+        return sums, evs
+
     def batch_grad(self, processes, n_events, sqrt_s: float, iteration: int, cuts=None):
         """Derivative passes at the grids of the last integrate_batch: array [n_ch + 1, 4] of
         (sigma_hat, d sigma_hat/d m_t, its MC error, d sigma_hat/d alpha_s); last row = sum."""

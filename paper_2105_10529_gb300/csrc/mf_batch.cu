@@ -200,6 +200,7 @@ struct SideLaunch {
 
 struct Plan {
     int n_ch = 0;
+    int slot_ch[MAX_CH];           // channel of each slot of the persistent launch
     int proc[MAX_CH];
     long long n[MAX_CH];
     int dim[MAX_CH];
@@ -288,6 +289,7 @@ int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, 
         kp.partials = pl.out[i];
         if (in_kernel[i]) {
             const int s = pl.bp.n_slot++;
+            pl.slot_ch[s] = i;
             pl.bp.proc[s] = procs[i];
             pl.bp.tile_begin[s] = tb;
             pl.bp.tile_events[s] = heavy_channel(procs[i]) ? sch.tile_heavy : sch.tile_light;
@@ -340,8 +342,11 @@ int reset_batch(mf_ctx* c, const Plan& pl, cudaStream_t s)
 
 // one iteration: the persistent launch (and, split, the side kernels on the
 // forked low-priority stream), then per channel the row reduction and refinement
-int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s, cudaStream_t low)
+int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s, cudaStream_t low,
+                      long long philox_it = -1)
 {
+    // Philox iteration of the pass: the iteration index unless given apart
+    const unsigned pit = philox_it >= 0 ? (unsigned)philox_it : (unsigned)it;
     const int nb = c->cfg.n_bins;
     bool fork = false;
     for (const SideLaunch& sl : pl.side) fork |= !sl.high;
@@ -351,14 +356,14 @@ int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s, c
     }
     if (pl.bp.n_slot > 0) {
         MF_BCUDA(c, cudaMemsetAsync(pl.bp.tile_counter, 0, sizeof(unsigned long long), s));
-        pl.bp.iteration = (unsigned)it;
+        pl.bp.iteration = pit;
         if (!pl.sch.sched) batch_kernel<false, 1><<<pl.nblk, BATCH_TPB, pl.sm, s>>>(pl.bp);
         else if (pl.sch.hsplit == 2) batch_kernel<true, 2><<<pl.nblk, BATCH_TPB, pl.sm, s>>>(pl.bp);
         else batch_kernel<true, 1><<<pl.nblk, BATCH_TPB, pl.sm, s>>>(pl.bp);
         MF_BCUDA(c, cudaGetLastError());
     }
     for (SideLaunch& sl : pl.side) {
-        sl.kp.iteration = (unsigned)it;
+        sl.kp.iteration = pit;
         MF_BCUDA(c, sl.ops->integrand(MF_MIXED, false, sl.sched, 1, sl.kp, sl.nblk, sl.sm, sl.high ? s : low));
     }
     if (fork) {
@@ -582,6 +587,49 @@ int mf_integrate_batch(mf_ctx* c, int n_ch, const int* processes, const long lon
     total_host->n_pass = np;
     total_host->n_nan = nn;
     total_host->n_iter = n_iter;
+    return MF_OK;
+}
+
+int mf_batch_pass(mf_ctx* c, int n_ch, const int* processes, const long long* n_events, double sqrt_s,
+                  const double* grids_dev, unsigned int iteration, double* sums_dev, const mf_event_arrays* ev_host)
+{
+    if (!c) return MF_ERR_ARG;
+    if (!grids_dev || !sums_dev || !(sqrt_s > 0.0)) return mf_fail(c, MF_ERR_ARG, "mf_batch_pass: bad argument");
+    Plan pl;
+    int rc = make_plan(c, n_ch, processes, n_events, sqrt_s, nullptr, current_schedule(c), pl);
+    if (rc) return rc;
+    const int nb = c->cfg.n_bins;
+    // per-event outputs: every kernel of the plan writes the channel's arrays at run time
+    auto attach = [&](KParams& kp, int ch) {
+        if (!ev_host) return;
+        const mf_event_arrays& e = ev_host[ch];
+        kp.ev_u = e.u; kp.ev_x = e.x; kp.ev_bins = e.bins; kp.ev_w = e.w;
+        kp.ev_mask = e.mask; kp.ev_me2 = e.me2; kp.ev_p = e.momenta;
+        kp.ev_out = (e.u || e.x || e.bins || e.w || e.mask || e.me2 || e.momenta) ? 1 : 0;
+    };
+    for (int s = 0; s < pl.bp.n_slot; ++s) attach(pl.slot_kp[(size_t)s], pl.slot_ch[s]);
+    for (SideLaunch& sl : pl.side) attach(sl.kp, sl.ch);
+    MF_BCUDA(c, cudaEventRecord(c->ev_user, c->stream));
+    MF_BCUDA(c, cudaStreamWaitEvent(c->cap_stream, c->ev_user, 0));
+    cudaStream_t s = c->cap_stream;
+    // the caller's grids into the batch grid slots, then the slot parameters and the counters
+    for (int i = 0; i < n_ch; ++i)
+        MF_BCUDA(c, cudaMemcpyAsync(c->d_bgrids + (size_t)i * MAX_DIM * (MAX_BINS + 1),
+                                    grids_dev + (size_t)i * MAX_DIM * (nb + 1),
+                                    sizeof(double) * pl.dim[i] * (nb + 1), cudaMemcpyDeviceToDevice, s));
+    if (!pl.slot_kp.empty())
+        MF_BCUDA(c, cudaMemcpyAsync(c->d_kps, pl.slot_kp.data(), sizeof(KParams) * pl.slot_kp.size(),
+                                    cudaMemcpyHostToDevice, s));
+    MF_BCUDA(c, cudaMemsetAsync(c->d_bcount, 0, sizeof(unsigned long long) * 2 * MAX_CH, s));
+    // one pass without refinement (statistics slot 0), random numbers of Philox iteration `iteration`
+    rc = enqueue_iteration(c, pl, 0, 1, s, c->cap_low, (long long)iteration);
+    if (rc) return rc;
+    const size_t row = 2 + (size_t)MAX_DIM * nb;
+    for (int i = 0; i < n_ch; ++i)
+        MF_BCUDA(c, cudaMemcpyAsync(sums_dev + (size_t)i * row, c->d_bsums + (size_t)i * (2 + MAX_DIM * MAX_BINS),
+                                    sizeof(double) * (2 + (size_t)pl.dim[i] * nb), cudaMemcpyDeviceToDevice, s));
+    // the pageable parameter upload and the outputs complete before returning
+    MF_BCUDA(c, cudaStreamSynchronize(s));
     return MF_OK;
 }
 

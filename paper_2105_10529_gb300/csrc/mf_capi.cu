@@ -464,6 +464,7 @@ int mf_vegas_pass(mf_ctx* c, int process, double sqrt_s, const double* grid_dev,
     if (ev) {
         kp.ev_u = ev->u; kp.ev_x = ev->x; kp.ev_bins = ev->bins; kp.ev_w = ev->w;
         kp.ev_mask = ev->mask; kp.ev_me2 = ev->me2; kp.ev_p = ev->momenta;
+        kp.ev_out = 1;
     }
     const size_t sm = ops->smem(c->cfg.precision, c->cfg.n_bins, c->nx * c->nq, false);
     int nblk = 0;

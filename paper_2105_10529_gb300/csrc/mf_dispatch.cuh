@@ -13,10 +13,13 @@ struct ProcOps {
     cudaError_t (*occupancy)(int prec, size_t smem, int* blocks_per_sm);
     // sched: 0 free-running warps, 1 CTA barrier between helicities (heavy processes),
     // 2 barrier and the colour sum on the tensor cores (processes with P::TC, mixed precision),
-    // 3 warp-per-event schedule with the tensor-core colour sum (P::TC, mixed precision, no
-    // per-event outputs, kp.inv_rec set for every CTA; otherwise as 2);
+    // 3 warp-per-event schedule with the tensor-core colour sum (P::TC, mixed precision,
+    // kp.inv_rec set for every CTA; otherwise as 2);
     // hsplit: 1, or 2 lanes per event each summing half the helicities (heavy processes,
-    // mixed precision, sched >= 1, no per-event outputs; otherwise 1)
+    // mixed precision, sched >= 1; otherwise 1).
+    // write: per-event outputs.  Schedule 3 and the helicity split run the same kernel with
+    // and without them (kp.ev_out selects the stores at run time); the other schedules have
+    // a separately compiled kernel with the stores
     cudaError_t (*integrand)(int prec, bool write, int sched, int hsplit, const KParams& kp, int nblk, size_t smem,
                              cudaStream_t s);
     cudaError_t (*evaluate)(int prec, const double* mom, long long n, double* me2, double mt, double gs,
@@ -132,7 +135,7 @@ struct IntegrandOps {
     static const void* pick(int sched, int hsplit)
     {
         constexpr int TPB = tpb<R>();
-        if constexpr (HS && sizeof(R) == 4 && !W) {
+        if constexpr (HS && sizeof(R) == 4) {
             if (hsplit == 2 && sched >= 1) {
                 if constexpr (HT) {
                     if (sched >= 2) return (const void*)integrand_kernel<P, float, TPB, false, true, true, 2>;
@@ -140,7 +143,7 @@ struct IntegrandOps {
                 return (const void*)integrand_kernel<P, float, TPB, false, true, false, 2>;
             }
         }
-        if constexpr (HL && sizeof(R) == 4 && !W) {
+        if constexpr (HL && sizeof(R) == 4) {
             if (sched == 3 && hsplit == 1) return fn_lh();
         }
         if constexpr (HT && sizeof(R) == 4) {

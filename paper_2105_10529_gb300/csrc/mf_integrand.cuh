@@ -64,8 +64,12 @@ struct KParams {
     int nobs;
     double obs_lo, obs_inv_w;
     double* obs_partials;
-    // per-event outputs (nullable; only the inspection kernel writes them)
+    // per-event outputs (nullable).  ev_out != 0 asks every integrand kernel to write the
+    // non-null ones: the kernels that a pass without outputs runs write them as well (a
+    // run-time branch per event, outside the helicity body), so that the kernel a
+    // benchmark times is the kernel whose events a parity test reads
     double* ev_u; double* ev_x; uint8_t* ev_bins; double* ev_w; uint8_t* ev_mask; double* ev_me2; double* ev_p;
+    int ev_out;
 };
 
 // Observable bin of an event: 0 below obs_lo (and for a non-finite p_T), nobs + 1 at or
@@ -477,6 +481,7 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
 
     double* myhist = shist + warp * D * nb;
     double* myobs = sobs + warp * L::OBS_ROW;
+    const bool wr = WRITE || kp.ev_out != 0;   // per-event outputs
     double sw = 0.0, sw2 = 0.0;
     unsigned long long npass = 0, nnan = 0;
     const long long rounds = end > first ? (end - first + step - 1) / step : 0;
@@ -494,7 +499,7 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
             else event_tops<P, R>(kp, sgrid, spdf, ev, o, pm, nullptr);
             if (!isfinite(o.w)) { o.w = 0.0; ++nnan; }
             npass += o.mask ? 1 : 0;
-            if constexpr (WRITE) { write_event<D>(kp, e, o, true); write_momenta<P::NEXT>(kp, e, pm); }
+            if (wr) { write_event<D>(kp, e, o, true); write_momenta<P::NEXT>(kp, e, pm); }
         }
         const double wn = o.w * kp.inv_n;
         const double v = wn * wn;
@@ -638,6 +643,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     double* swbuf = reinterpret_cast<double*>(smem_raw + L::obs_w_off(nb, npv));
     int16_t* sobin = reinterpret_cast<int16_t*>(smem_raw + L::obs_b_off(nb, npv));
     const bool obs = kp.nobs > 0;
+    const bool wr = WRITE || kp.ev_out != 0;   // per-event outputs
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     void* slot = (void*)(smem_raw + L::slot_off(nb, npv) + (size_t)tid * P::template slot_bytes<R>());
     const double* gpdf = kp.pdf;
@@ -684,7 +690,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
                 kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
                 pass = o.mask ? 1 : 0;
                 npass += pass;
-                if constexpr (WRITE) {
+                if (wr) {
                     write_event<D>(kp, e, o, true);
                     if (!pass) write_momenta<P::NEXT>(kp, e, pm);
                 }
@@ -753,7 +759,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             }
             double w = owner ? pref * me : 0.0;
             if (!isfinite(w)) { w = 0.0; if (owner) ++nnan; }
-            if constexpr (WRITE) {
+            if (wr) {
                 if (owner) {
                     o.me2 = me; o.w = w;
                     write_event<D>(kp, e, o, false);

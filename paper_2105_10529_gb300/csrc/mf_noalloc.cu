@@ -14,6 +14,7 @@
 // process exits.  Nothing here allocates: no cudaMalloc, no cudaFree, no
 // library routine that allocates.
 #include <cuda_runtime.h>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 
@@ -35,8 +36,9 @@ constexpr size_t kScratchDoubles = 512 * 1024;
 static __device__ __align__(256) double g_pass_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
-// per-device state, filled by the first call on that device
-double* g_scratch_ptr[kMaxDevices] = {};
+// per-device state, filled by the first call on that device (host threads may race
+// on the first call; every one of them stores the same address)
+std::atomic<double*> g_scratch_ptr[kMaxDevices] = {};
 
 const ProcOps* ops_for(int p)
 {
@@ -66,12 +68,14 @@ int scratch_on_current_device(double** out)
 {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return MF_ERR_CUDA;
-    if (!g_scratch_ptr[dev]) {
+    double* ptr = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!ptr) {
         void* p = nullptr;
         if (cudaGetSymbolAddress(&p, g_pass_scratch) != cudaSuccess || !p) return MF_ERR_CUDA;
-        g_scratch_ptr[dev] = static_cast<double*>(p);
+        ptr = static_cast<double*>(p);
+        g_scratch_ptr[dev].store(ptr, std::memory_order_release);
     }
-    *out = g_scratch_ptr[dev];
+    *out = ptr;
     return MF_OK;
 }
 
@@ -101,8 +105,10 @@ extern "C" int mf_vegas_pass_static(int process, const mf_config* cfg, double sq
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return MF_ERR_CUDA;
     const size_t sm = ops->smem(cfg->precision, nb, nx * nq, false);
-    // allow this process's kernels the largest shared-memory size any argument set can need
-    if (ops->prepare(ops->smem(1, MAX_BINS, 8192, false), ops->smem(0, MAX_BINS, 8192, false)) != cudaSuccess)
+    // allow this process's kernels the largest shared-memory size any argument set can need,
+    // the observable region included: the same sizes mf_create sets, so a call here never
+    // lowers the limit that a context's passes with the observable histogram rely on
+    if (ops->prepare(ops->smem(1, MAX_BINS, 8192, true), ops->smem(0, MAX_BINS, 8192, true)) != cudaSuccess)
         return MF_ERR_CUDA;
     int n_sm = 0, per_sm = 0;
     if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return MF_ERR_CUDA;
@@ -126,7 +132,8 @@ extern "C" int mf_vegas_pass_static(int process, const mf_config* cfg, double sq
         kp.ln_tau0 = std::log(tau0);
     }
     kp.pt_min2 = cfg->pt_min > 0.0 ? cfg->pt_min * cfg->pt_min : 0.0;
-    kp.sinh_eta = cfg->eta_max > 0.0 ? std::sinh(cfg->eta_max) : 0.0;
+    // an infinite eta_max disables the cut, as in a context's passes
+    kp.sinh_eta = cfg->eta_max > 0.0 && std::isfinite(cfg->eta_max) ? std::sinh(cfg->eta_max) : 0.0;
     kp.dr_min2 = cfg->dr_min > 0.0 ? cfg->dr_min * cfg->dr_min : 0.0;
     {
         const double a = 1.0 / cfg->alpha_em_inv, mz2 = cfg->mz * cfg->mz;
@@ -163,6 +170,8 @@ extern "C" int mf_vegas_pass_static(int process, const mf_config* cfg, double sq
     cudaStream_t s = (cudaStream_t)stream;
     // the counters start at zero on every call; the partials are fully overwritten by the kernel
     if (cudaMemsetAsync(scratch, 0, 2 * sizeof(double), s) != cudaSuccess) return MF_ERR_CUDA;
+    // schedule 0: one event per thread with the FMA colour sum (the warp-per-event schedule
+    // needs a per-CTA record region that only a context owns)
     if (ops->integrand(cfg->precision, false, 0, 1, kp, (int)nblk, sm, s) != cudaSuccess) return MF_ERR_CUDA;
     finish_pass_kernel<<<1, 1024, ncol * sizeof(double), s>>>(kp.partials, (int)nblk, D, nb, n_events, cfg->alpha, 0,
                                                               nullptr, nullptr, sums_dev);

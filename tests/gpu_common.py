@@ -112,3 +112,27 @@ def assert_fp_parity(err, prec, what=""):
     assert err.max() < 1e-10, (what, err.max(), int(np.argmax(err)))
     if err.size >= 100:
         assert np.median(err) < 1e-14, (what, np.median(err))
+
+
+def check_events_against_oracle(proc, phys, opdf, grid, ev, iteration, prec, first=0, events=None, what=""):
+    """Per-event parity of a pass's outputs (a dict of device tensors with
+    some of bins, mask, w, me2) against the oracle's events: bins bit-exact,
+    masks bit-exact away from a cut threshold, w and |M|^2 within the
+    precision's per-event bound.  events: the indices of the pass to check
+    (default: all); first: the pass's event offset."""
+    n = int(next(iter(ev.values())).shape[0])
+    idx = np.arange(n) if events is None else np.asarray(events)
+    ref = oracle_events(proc, phys, opdf, grid, 0, iteration=iteration, events=[first + int(i) for i in idx])
+    if "bins" in ev:
+        assert np.array_equal(ev["bins"].cpu().numpy()[idx], ref["bins"]), what
+    same = np.ones(len(idx), dtype=bool)
+    if "mask" in ev:
+        mk = ev["mask"].cpu().numpy()[idx].astype(int)
+        for i in np.nonzero(mk != ref["mask"])[0]:
+            assert cut_margin(proc, phys, ref["plab"][i]) < 1e-9, (what, "mask flip far from a threshold", int(idx[i]))
+        same = mk == ref["mask"]
+    for f in ("w", "me2"):
+        if f in ev:
+            v = ev[f].cpu().numpy()[idx]
+            assert_fp_parity(rel_err(v[same], ref[f][same]), prec, f"{what} {f}")
+    return ref

@@ -62,6 +62,38 @@ def test_batch_one_iteration_matches_oracle(ctx, opdf, mode):
     assert tot["n_events"] == sum(N_EV)
 
 
+# (mode, barrier schedule, helicity split): the persistent kernel with and without the barrier and
+# the split, the split mode (heavy channels persistent, the others as their own kernels), and the
+# per-channel kernels with the warp-per-event schedule
+@pytest.mark.parametrize("mode,sched,hsplit", [(0, 0, 1), (0, 1, 2), (1, 1, 1), (2, 3, 1)])
+def test_batch_pass_events_match_oracle(ctx, opdf, mode, sched, hsplit):
+    """One batch pass at non-uniform caller grids with per-event outputs,
+    written by the batch's own kernels (the persistent kernel in modes 0 and
+    1): every channel's events against the oracle's, bins bit-exact and w,
+    |M|^2 within the mixed-precision bound, and the channel's pass sums equal
+    to the sums of its per-event weights and to the pass without outputs."""
+    from tests.gpu_common import check_events_against_oracle, random_grid
+    n_ev = [3001, 2003, 1201, 601, 151]
+    nb = PHYS.n_bins
+    grids = np.zeros((len(CHANNELS), 18, nb + 1))
+    for i, p in enumerate(CHANNELS):
+        grids[i, :IN.DIM[p]] = random_grid(IN.DIM[p], nb, seed=90 + i)
+    gt = torch.tensor(grids, device="cuda")
+    ctx.set_batch_schedule(mode, sched, 256, 512, 0, hsplit)
+    plain, _ = ctx.batch_pass(CHANNELS, n_ev, PHYS.sqrt_s, gt, iteration=6)
+    sums, evs = ctx.batch_pass(CHANNELS, n_ev, PHYS.sqrt_s, gt, iteration=6, want_events=True,
+                               fields=("bins", "mask", "w", "me2"))
+    ctx.device_status()
+    assert torch.equal(plain, sums)
+    for i, (p, n) in enumerate(zip(CHANNELS, n_ev)):
+        ph = dataclasses.replace(PHYS, channel=PHYS.channel + i)
+        w = evs[i]["w"].cpu().numpy()
+        s0 = float(sums[i, 0])
+        assert abs(s0 - w.sum() / n) <= 1e-12 * abs(w.sum() / n) + 1e-300, p
+        check_events_against_oracle(p, ph, opdf, grids[i, :IN.DIM[p]], evs[i], 6, 1,
+                                    what=f"batch mode {mode} sched {sched} split {hsplit} process {p}")
+
+
 @pytest.mark.parametrize("mode", [0, 1, 2])
 def test_batch_iterations_match_single_process(ctx, pdf_grid, mode):
     """Three iterations with refinement: each channel equals mf_integrate of

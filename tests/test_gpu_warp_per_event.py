@@ -9,7 +9,7 @@ import pytest
 
 import oracle as O
 from paper_2105_10529_gb300 import inputs as IN
-from tests.gpu_common import PHYS, oracle_events, random_grid
+from tests.gpu_common import PHYS, check_events_against_oracle, oracle_events, random_grid
 
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
@@ -45,7 +45,9 @@ def pass_pair(ctx, phys, grid, n, iteration, offset=0):
 def test_pass_matches_schedule_2_and_oracle(n, pdf_grid, opdf):
     """Small and ragged passes (a single event, fewer events than warps, a
     partial last batch in every CTA): every entry of the pass sums within
-    1e-6 of schedule 2, the sum of weights within 1e-5 of the oracle's."""
+    1e-6 of schedule 2, the sum of weights within 1e-5 of the oracle's, and
+    event by event (the same kernel writing its per-event outputs) the
+    bins bit-exact and |M|^2 and w within 1e-5 of the oracle."""
     phys = PHYS[PROC]
     g = random_grid(IN.DIM[PROC], seed=61)
     grid = torch.tensor(g, device="cuda")
@@ -58,6 +60,13 @@ def test_pass_matches_schedule_2_and_oracle(n, pdf_grid, opdf):
         assert float(b[0]) == 0.0
     else:
         assert float(b[0]) == pytest.approx(ref_sum, rel=1e-5)
+    # schedule 3 with per-event outputs: the same kernel, so the same sums bit for bit
+    ctx.set_schedule(3)
+    c, ev = ctx.vegas_pass(PROC, phys.sqrt_s, grid, n, iteration=4, want_events=True,
+                           fields=("bins", "mask", "w", "me2"))
+    ctx.device_status()
+    assert torch.equal(c, b)
+    check_events_against_oracle(PROC, phys, opdf, g, ev, 4, 1, what=f"schedule 3, n={n}")
     ctx.close()
 
 
@@ -107,16 +116,23 @@ def test_integrate_and_observable(pdf_grid):
 
 
 def test_per_event_outputs_and_other_processes_fall_back(pdf_grid):
-    """Per-event outputs, the helicity split and processes without the
-    tensor-core colour sum run schedule 3 as schedule 2; 4 is rejected."""
+    """Per-event outputs run schedule 3 itself (|M|^2 within FP32 rounding of
+    schedule 2, the sums equal to those of the pass without outputs); the
+    helicity split and processes without the tensor-core colour sum run
+    schedule 3 as schedule 2; 4 is rejected."""
     phys = PHYS[PROC]
     grid = torch.tensor(random_grid(IN.DIM[PROC], seed=63), device="cuda")
     ctx = ctx_for(pdf_grid)
     ctx.set_schedule(2)
     _, e2 = ctx.vegas_pass(PROC, phys.sqrt_s, grid, 300, iteration=1, want_events=True, fields=("me2",))
     ctx.set_schedule(3)
-    _, e3 = ctx.vegas_pass(PROC, phys.sqrt_s, grid, 300, iteration=1, want_events=True, fields=("me2",))
-    assert torch.equal(e2["me2"], e3["me2"])
+    s3, e3 = ctx.vegas_pass(PROC, phys.sqrt_s, grid, 300, iteration=1, want_events=True, fields=("me2",))
+    s3n, _ = ctx.vegas_pass(PROC, phys.sqrt_s, grid, 300, iteration=1)
+    assert torch.equal(s3, s3n)
+    m2, m3 = e2["me2"].cpu().numpy(), e3["me2"].cpu().numpy()
+    assert np.array_equal(m2 == 0, m3 == 0)
+    nz = m2 != 0
+    assert np.all(np.abs(m3[nz] - m2[nz]) <= 1e-6 * np.abs(m2[nz]))
     ctx.set_helicity_split(2)
     s3, _ = ctx.vegas_pass(PROC, phys.sqrt_s, grid, 700, iteration=1)
     ctx.set_schedule(2)

@@ -66,3 +66,33 @@ def test_static_scratch_pass_rejects_bad_sizes():
     cfg = make_config(phys, 1)
     assert _static_pass(L, cfg, IN.GG_TTGG, phys, pdf_t, grid_t, 0, 0, 0, out) == 1   # no events
     assert _static_pass(L, cfg, 17, phys, pdf_t, grid_t, 100, 0, 0, out) == 1         # unknown process
+
+
+@pytest.mark.parametrize("proc,prec", [(IN.GG_TTGG, 1), (IN.GG_TTG, 0)])
+def test_static_pass_leaves_context_observable_working(proc, prec):
+    """A call of the allocation-free pass must not lower the shared-memory
+    limit of the process's kernels below what a context's passes with the
+    p_T histogram need: a context created before it still integrates with the
+    histogram on, and gives the same result as before the call."""
+    from paper_2105_10529_gb300 import _lib
+    from paper_2105_10529_gb300.api import Context, make_config, process_info
+    from tests.gpu_common import PHYS, random_grid
+    L = _lib.lib()
+    phys = PHYS[proc]
+    _, dim = process_info(proc)
+    pdf = IN.make_pdf_grid()
+    ctx = Context(phys, pdf, precision=prec)
+    ctx.set_observable(20, 0.0, 800.0)
+    before = ctx.integrate(proc, phys.sqrt_s, 4000, 2)
+    h_before = ctx.observable()[0]
+    pdf_t = torch.tensor(pdf, device="cuda")
+    grid_t = torch.tensor(random_grid(dim, seed=77), device="cuda")
+    out = torch.zeros(2 + dim * phys.n_bins, dtype=torch.float64, device="cuda")
+    assert _static_pass(L, make_config(phys, prec), proc, phys, pdf_t, grid_t, 3000, 0, 1, out) == 0
+    torch.cuda.synchronize()
+    after = ctx.integrate(proc, phys.sqrt_s, 4000, 2)
+    ctx.device_status()
+    assert after["status"] == 0
+    assert after["sigma"] == before["sigma"]
+    assert np.array_equal(ctx.observable()[0], h_before)
+    ctx.close()
