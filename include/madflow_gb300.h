@@ -218,9 +218,25 @@ int mf_set_pdf(struct mf_ctx *ctx, const double *pdf_grid_host);
  * out->dsigma_dalphas (as mf_vegas_pass_grad; MF_ERR_UNSUPPORTED where that
  * has no kernel).  iter_host (nullable): [n_iter][2] estimate and variance
  * per iteration; grid_host (nullable): [dim][n_bins+1] final grid.
- * Synchronises the stream. */
+ * The iterations (integrand, end-of-pass reduction and refinement, and the
+ * observable's reduction) are captured once as a CUDA graph on a private
+ * stream, ordered after the work queued on the context's stream, and the
+ * graph is replayed while the process, sizes, cuts, couplings, schedule and
+ * observable stay the same.  Synchronises. */
 int mf_integrate(struct mf_ctx *ctx, int process, double sqrt_s, const mf_cuts *cuts, long long n_events, int n_iter,
                  int want_grads, mf_result *out_host, double *iter_host, double *grid_host);
+
+/* integrate from a caller grid (no counterpart in the paper: it resumes an
+ * adaptation, e.g. one started by mf_vegas_pass / mf_vegas_refine): as
+ * mf_integrate, but the first iteration uses grid_in_host [dim][n_bins+1]
+ * (host, caller-owned, copied) instead of the uniform grid, and iteration j
+ * draws its random numbers from Philox iteration first_iteration + j (the
+ * derivative pass from first_iteration + n_iter).  MF_ERR_ARG when
+ * grid_in_host is NULL.  Like mf_integrate, its iterations are captured once
+ * as a CUDA graph and replayed.  Synchronises. */
+int mf_integrate_grid(struct mf_ctx *ctx, int process, double sqrt_s, const mf_cuts *cuts, long long n_events,
+                      int n_iter, unsigned int first_iteration, const double *grid_in_host, int want_grads,
+                      mf_result *out_host, double *iter_host, double *grid_host);
 
 /* One VEGAS pass over events [ev_offset, ev_offset + n_events) of Philox
  * iteration `iteration` at a caller grid (grid_dev: [dim][n_bins+1]).

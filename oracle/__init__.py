@@ -35,7 +35,7 @@ class OrEvent(C.Structure):
     _fields_ = [("u", C.c_double * 32), ("x", C.c_double * 32), ("bins", C.c_uint8 * 32),
                 ("jac_vegas", C.c_double), ("x1", C.c_double), ("x2", C.c_double),
                 ("shat", C.c_double), ("jac_parton", C.c_double), ("w_ps", C.c_double),
-                ("p", C.c_double * 24), ("plab", C.c_double * 24), ("mask", C.c_int),
+                ("p", C.c_double * 28), ("plab", C.c_double * 28), ("mask", C.c_int),
                 ("muf2", C.c_double), ("f1", C.c_double), ("f2", C.c_double),
                 ("me2", C.c_double), ("w", C.c_double)]
 
@@ -88,6 +88,8 @@ def lib():
             "or_proc_info_get": (C.c_int, [C.c_int, C.POINTER(OrProcInfo)]),
             "or_event": (C.c_int, [C.c_int, C.POINTER(OrParams), C.POINTER(OrPdf), _D, C.c_uint64,
                                    C.c_uint32, _I, C.POINTER(OrEvent)]),
+            "or_events": (C.c_int, [C.c_int, C.POINTER(OrParams), C.POINTER(OrPdf), _D, C.POINTER(C.c_uint64),
+                                    C.c_int64, C.c_uint32, C.POINTER(OrEvent), C.c_int]),
             "or_pass": (C.c_int, [C.c_int, C.POINTER(OrParams), C.POINTER(OrPdf), _D, C.c_int64, C.c_uint32,
                                   _U8, _U8, _D, _D, _D, C.POINTER(C.c_int64), C.c_int]),
             "or_integrate": (C.c_int, [C.c_int, C.POINTER(OrParams), C.POINTER(OrPdf), C.c_int64, C.c_int,
@@ -281,6 +283,18 @@ def event(proc: int, phys, pdf: Pdf, grid: np.ndarray, ev: int, iteration: int =
     if rc:
         raise ValueError("or_event failed")
     return o
+
+
+def events(proc: int, phys, pdf: Pdf, grid: np.ndarray, idx, iteration: int = 0, n_threads: int = 0):
+    """event() for every index in idx, computed in parallel; a list of OrEvent."""
+    P = params(phys); g = _f64(grid)
+    ev = np.ascontiguousarray(np.asarray(idx, dtype=np.uint64))
+    out = (OrEvent * max(len(ev), 1))()
+    rc = lib().or_events(proc, C.byref(P), C.byref(pdf.c), _dp(g), ev.ctypes.data_as(C.POINTER(C.c_uint64)),
+                         len(ev), iteration, out, n_threads)
+    if rc:
+        raise ValueError("or_events failed")
+    return [out[i] for i in range(len(ev))]
 
 
 def vegas_pass(proc: int, phys, pdf: Pdf, grid: np.ndarray, n: int, iteration: int = 0,

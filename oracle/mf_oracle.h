@@ -23,9 +23,11 @@
  *   pdf bicubic ............. pinned (exact on quadratics, node values)
  *   me2 e+e- -> mu+mu- ...... closed form; pinned (QED limit, total sigma)
  *   me2 q qbar -> t tbar .... closed form; pinned (sigma-hat closed form)
- *   me2 gg -> t tbar (+g..) . Berends-Giele; pinned (Combridge closed form,
- *                             Ward identity, Lorentz invariance, Bose symmetry,
- *                             massless MHV ratios)
+ *   me2 gg -> t tbar (+g..) . Berends-Giele, up to three final gluons; pinned
+ *                             (Combridge closed form, Ward identity, Lorentz
+ *                             invariance, Bose symmetry, massless MHV ratios,
+ *                             collinear factorisation chains k -> k - 1,
+ *                             explicit colour sums)
  *   me2 u g -> t tbar u ..... explicit Feynman diagrams, explicit colour;
  *                             pinned (Ward identity, Lorentz invariance; the
  *                             same diagram machinery reproduces the u ubar ->
@@ -43,7 +45,7 @@ extern "C" {
 #endif
 
 /* Process numbering (same meaning as the library's enum, defined here on its own). */
-enum { OR_EE_MUMU = 0, OR_GG_TT = 1, OR_UU_TT = 2, OR_GG_TTG = 3, OR_UG_TTU = 4, OR_GG_TTGG = 5 };
+enum { OR_EE_MUMU = 0, OR_GG_TT = 1, OR_UU_TT = 2, OR_GG_TTG = 3, OR_UG_TTU = 4, OR_GG_TTGG = 5, OR_GG_TTGGG = 6 };
 
 typedef struct {
     double sqrt_s;        /* collider (or e+e-) energy, GeV                        */
@@ -123,7 +125,8 @@ void or_bg_partial(int k, const double *kg, const double *eps, const double *p3,
                    double m, double gs, int s3, int s4, const int *perm, double *amp_re_im);
 double or_me2_bg(int k, const double *p_all, int n_in_gluons, double m, double gs);
 /* colour matrix C[s][t] = sum_colours conj((T^s)_ij) (T^t)_ij over orderings of k gluons
- * (orderings enumerated lexicographically), by brute force over Gell-Mann matrices. */
+ * (orderings enumerated lexicographically), by brute force over Gell-Mann matrices;
+ * k <= 5 (120 orderings). */
 void or_colour_matrix(int k, double *C);
 /* Gell-Mann generators T^a = lambda^a/2, a=0..7: 3x3 complex as re,im pairs */
 void or_gellmann_T(int a, double *T);
@@ -140,8 +143,8 @@ typedef struct {
     double u[32], x[32];
     uint8_t bins[32];
     double jac_vegas, x1, x2, shat, jac_parton, w_ps;
-    double p[6][4];     /* partonic rest frame */
-    double plab[6][4];  /* lab frame */
+    double p[7][4];     /* partonic rest frame */
+    double plab[7][4];  /* lab frame */
     int mask;
     double muf2, f1, f2, me2;
     double w;           /* event weight f*J (pb), before the 1/N of the estimator */
@@ -149,6 +152,9 @@ typedef struct {
 
 int or_event(int proc, const or_params *P, const or_pdf *pdf, const double *grid,
              uint64_t event, uint32_t iteration, const int *mask_override, or_event_out *o);
+/* or_event for n listed events, threads over events (n_threads <= 0: all) */
+int or_events(int proc, const or_params *P, const or_pdf *pdf, const double *grid, const uint64_t *events,
+              int64_t n, uint32_t iteration, or_event_out *out, int n_threads);
 
 /* one VEGAS pass over events [0,n) at fixed grid: sums of w and w^2 (w includes 1/n)
  * and the histogram hist[d][b] += w^2.  mask_in (nullable) freezes cut masks,

@@ -29,6 +29,7 @@ static void final_masses(int proc, const or_params *P, double *m, int *n)
     case OR_GG_TT: case OR_UU_TT: m[0] = P->mt; m[1] = P->mt; *n = 2; break;
     case OR_GG_TTG: case OR_UG_TTU: m[0] = P->mt; m[1] = P->mt; m[2] = 0.0; *n = 3; break;
     case OR_GG_TTGG: m[0] = P->mt; m[1] = P->mt; m[2] = 0.0; m[3] = 0.0; *n = 4; break;
+    case OR_GG_TTGGG: m[0] = P->mt; m[1] = P->mt; m[2] = m[3] = m[4] = 0.0; *n = 5; break;
     default: *n = 2; m[0] = m[1] = 0.0;
     }
 }
@@ -72,7 +73,7 @@ int or_event(int proc, const or_params *P, const or_pdf *pdf, const double *grid
     }
 
     double S = P->sqrt_s * P->sqrt_s;
-    double m[4]; int nf;
+    double m[5]; int nf;
     final_masses(proc, P, m, &nf);
     double msum = 0.0;
     for (int i = 0; i < nf; ++i) msum += m[i];
@@ -80,7 +81,7 @@ int or_event(int proc, const or_params *P, const or_pdf *pdf, const double *grid
     or_parton_map(o->x[0], o->x[1], tau0, &o->x1, &o->x2, &o->jac_parton);
     o->shat = o->x1 * o->x2 * S;
     double rs = sqrt(o->shat);
-    double pf[4 * 4];
+    double pf[5 * 4];
     if (or_rambo(nf, rs, m, o->x + 2, pf, &o->w_ps)) { o->w = 0.0; return 0; }
     double half = 0.5 * rs;
     double pin[2][4] = { { half, 0, 0, half }, { half, 0, 0, -half } };
@@ -107,6 +108,19 @@ int or_event(int proc, const or_params *P, const or_pdf *pdf, const double *grid
     o->me2 = or_me2(proc, P, &o->p[0][0]);
     o->w = o->f1 * o->f2 * o->me2 / (2.0 * o->shat) * o->w_ps * o->jac_parton * o->jac_vegas * GEV2_TO_PB;
     return 0;
+}
+
+/* or_event for a list of events, in parallel over events (independent calls). */
+int or_events(int proc, const or_params *P, const or_pdf *pdf, const double *grid, const uint64_t *events,
+              int64_t n, uint32_t iteration, or_event_out *out, int n_threads)
+{
+    int rc = 0;
+#ifdef _OPENMP
+    if (n_threads <= 0) n_threads = omp_get_max_threads();
+#pragma omp parallel for schedule(dynamic, 1) num_threads(n_threads) reduction(| : rc)
+#endif
+    for (int64_t i = 0; i < n; ++i) rc |= or_event(proc, P, pdf, grid, events[i], iteration, NULL, out + i);
+    return rc;
 }
 
 /*

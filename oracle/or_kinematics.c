@@ -110,12 +110,14 @@ static double pt2_of(const double *p) { return p[1] * p[1] + p[2] * p[2]; }
 
 /* Fiducial cuts on the final light partons in the lab frame:
  * pT > pt_min, |eta| < eta_max (tested as |pz| < pT sinh(eta_max)), and
- * Delta R > dr_min between final gluons.  Returns 1 when the event passes. */
+ * Delta R > dr_min between every pair of final gluons.  Returns 1 when the
+ * event passes. */
 int or_cuts(int proc, const or_params *P, const double *plab)
 {
-    int light[2], nl = 0;
+    int light[3], nl = 0;
     if (proc == OR_GG_TTG || proc == OR_UG_TTU) { light[0] = 4; nl = 1; }
     else if (proc == OR_GG_TTGG) { light[0] = 4; light[1] = 5; nl = 2; }
+    else if (proc == OR_GG_TTGGG) { light[0] = 4; light[1] = 5; light[2] = 6; nl = 3; }
     else return 1;
     double sh = P->eta_max > 0.0 ? sinh(P->eta_max) : 0.0;
     for (int j = 0; j < nl; ++j) {
@@ -124,15 +126,18 @@ int or_cuts(int proc, const or_params *P, const double *plab)
         if (P->pt_min > 0.0 && !(pt2 > P->pt_min * P->pt_min)) return 0;
         if (P->eta_max > 0.0 && !(fabs(p[3]) < sqrt(pt2) * sh)) return 0;
     }
-    if (proc == OR_GG_TTGG && P->dr_min > 0.0) {
-        const double *a = plab + 16, *b = plab + 20;
-        double pta = sqrt(pt2_of(a)), ptb = sqrt(pt2_of(b));
-        double ea = asinh(a[3] / pta), eb = asinh(b[3] / ptb);
-        double dphi = atan2(a[2], a[1]) - atan2(b[2], b[1]);
-        if (dphi > M_PI) dphi -= 2.0 * M_PI;
-        if (dphi < -M_PI) dphi += 2.0 * M_PI;
-        double dr2 = (ea - eb) * (ea - eb) + dphi * dphi;
-        if (!(dr2 > P->dr_min * P->dr_min)) return 0;
+    if ((proc == OR_GG_TTGG || proc == OR_GG_TTGGG) && P->dr_min > 0.0) {
+        for (int i = 0; i < nl; ++i)
+            for (int j = i + 1; j < nl; ++j) {
+                const double *a = plab + 4 * light[i], *b = plab + 4 * light[j];
+                double pta = sqrt(pt2_of(a)), ptb = sqrt(pt2_of(b));
+                double ea = asinh(a[3] / pta), eb = asinh(b[3] / ptb);
+                double dphi = atan2(a[2], a[1]) - atan2(b[2], b[1]);
+                if (dphi > M_PI) dphi -= 2.0 * M_PI;
+                if (dphi < -M_PI) dphi += 2.0 * M_PI;
+                double dr2 = (ea - eb) * (ea - eb) + dphi * dphi;
+                if (!(dr2 > P->dr_min * P->dr_min)) return 0;
+            }
     }
     return 1;
 }
@@ -143,7 +148,7 @@ double or_muf2(int proc, const or_params *P, const double *p)
 {
     if (proc == OR_GG_TT || proc == OR_UU_TT) return P->mt * P->mt;
     if (proc == OR_EE_MUMU) return 0.0;
-    int n_ext = proc == OR_GG_TTGG ? 6 : 5;
+    int n_ext = proc == OR_GG_TTGGG ? 7 : (proc == OR_GG_TTGG ? 6 : 5);
     double ht = 0.0;
     for (int i = 2; i < n_ext; ++i) {
         double m = (i == 2 || i == 3) ? P->mt : 0.0;

@@ -32,7 +32,11 @@
 #include "mf_oracle.h"
 #include <complex.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #ifndef M_PI
 #define M_PI 3.14159265358979323846
@@ -273,34 +277,56 @@ static int perms(int k, int out[][8])
 }
 
 /* C[s][t] = sum over gluon colours a_1..a_k and quark indices i,j of
- * conj((T^{a_s1} ... T^{a_sk})_ij) (T^{a_t1} ... T^{a_tk})_ij, by brute force. */
+ * conj((T^{a_s1} ... T^{a_sk})_ij) (T^{a_t1} ... T^{a_tk})_ij, by brute force.
+ * The 8^k colour assignments are split over threads, each adding into its own
+ * matrix; the per-thread matrices are then added in thread order. */
+#define MAXPERM 120
 void or_colour_matrix(int k, double *C)
 {
     static int P[40320][8];
     int np = perms(k, P);
     cplx T[8][3][3];
     for (int a = 0; a < 8; ++a) gellmann(a, T[a]);
-    static cplx S[24][3][3];
     for (int i = 0; i < np * np; ++i) C[i] = 0.0;
     int n_assign = 1;
     for (int i = 0; i < k; ++i) n_assign *= 8;
-    for (int as = 0; as < n_assign; ++as) {
-        int col[8], r = as;
-        for (int i = 0; i < k; ++i) { col[i] = r % 8; r /= 8; }
-        for (int s = 0; s < np; ++s) {
-            cplx M[3][3];
-            memcpy(M, T[col[P[s][0]]], sizeof(M));
-            for (int i = 1; i < k; ++i) mat3_mul(M, T[col[P[s][i]]], M);
-            memcpy(S[s], M, sizeof(M));
-        }
-        for (int s = 0; s < np; ++s)
-            for (int t = 0; t < np; ++t) {
-                cplx acc = 0;
-                for (int i = 0; i < 3; ++i)
-                    for (int j = 0; j < 3; ++j) acc += conj(S[s][i][j]) * S[t][i][j];
-                C[s * np + t] += creal(acc);
+    int nthr = 1;
+#ifdef _OPENMP
+    nthr = omp_get_max_threads();
+    if (nthr > 64) nthr = 64;
+#endif
+    double *part = calloc((size_t)nthr * np * np, sizeof(double));
+#pragma omp parallel num_threads(nthr)
+    {
+        int tid = 0;
+#ifdef _OPENMP
+        tid = omp_get_thread_num();
+#endif
+        double *Cp = part + (size_t)tid * np * np;
+        cplx (*S)[3][3] = malloc(sizeof(cplx[3][3]) * MAXPERM);
+#pragma omp for schedule(static)
+        for (int as = 0; as < n_assign; ++as) {
+            int col[8], r = as;
+            for (int i = 0; i < k; ++i) { col[i] = r % 8; r /= 8; }
+            for (int s = 0; s < np; ++s) {
+                cplx M[3][3];
+                memcpy(M, T[col[P[s][0]]], sizeof(M));
+                for (int i = 1; i < k; ++i) mat3_mul(M, T[col[P[s][i]]], M);
+                memcpy(S[s], M, sizeof(M));
             }
+            for (int s = 0; s < np; ++s)
+                for (int t = 0; t < np; ++t) {
+                    cplx acc = 0;
+                    for (int i = 0; i < 3; ++i)
+                        for (int j = 0; j < 3; ++j) acc += conj(S[s][i][j]) * S[t][i][j];
+                    Cp[s * np + t] += creal(acc);
+                }
+        }
+        free(S);
     }
+    for (int t = 0; t < nthr; ++t)
+        for (int i = 0; i < np * np; ++i) C[i] += part[(size_t)t * np * np + i];
+    free(part);
 }
 
 /* ---------------------------------------------------------------- Berends-Giele */
@@ -400,15 +426,24 @@ void or_bg_partial(int k, const double *kg, const double *eps, const double *p3,
  * (outgoing ones with a minus sign). */
 double or_me2_bg(int k, const double *p_all, int n_in_gluons, double m, double gs)
 {
-    static double Cm[7][24 * 24];
-    static int c_ready[7] = {0};
+    static double *Cm[7];
+    static volatile int c_ready[7] = {0};
+    if (k < 1 || k > 5) return 0.0;
     if (!c_ready[k]) {
 #pragma omp critical(or_colour_init)
         {
-            if (!c_ready[k]) { or_colour_matrix(k, Cm[k]); c_ready[k] = 1; }
+            if (!c_ready[k]) {
+                int n = 1;
+                for (int i = 2; i <= k; ++i) n *= i;
+                double *c = malloc(sizeof(double) * n * n);
+                or_colour_matrix(k, c);
+                Cm[k] = c;
+                __sync_synchronize();
+                c_ready[k] = 1;
+            }
         }
     }
-    int P[24][8];
+    int P[MAXPERM][8];
     int np = perms(k, P);
     double kg[MAXG * 4];
     const double *p3 = p_all + 4 * n_in_gluons, *p4 = p_all + 4 * (n_in_gluons + 1);
@@ -429,7 +464,7 @@ double or_me2_bg(int k, const double *p_all, int n_in_gluons, double m, double g
         }
         for (int s3 = 0; s3 < 2; ++s3)
             for (int s4 = 0; s4 < 2; ++s4) {
-                cplx A[24];
+                cplx A[MAXPERM];
                 for (int s = 0; s < np; ++s) {
                     double a[2];
                     or_bg_partial(k, kg, eps, p3, p4, m, gs, s3, s4, P[s], a);
@@ -648,6 +683,7 @@ int or_proc_info_get(int proc, or_proc_info *o)
     case OR_GG_TTG:  *o = (or_proc_info){ 5, 3, 14, 32, 3, 1.0 / 256.0, 1.0 }; return 0;
     case OR_UG_TTU:  *o = (or_proc_info){ 5, 3, 14, 32, 3, 1.0 / 96.0, 1.0 }; return 0;
     case OR_GG_TTGG: *o = (or_proc_info){ 6, 4, 18, 64, 4, 1.0 / 256.0, 0.5 }; return 0;
+    case OR_GG_TTGGG: *o = (or_proc_info){ 7, 5, 22, 128, 5, 1.0 / 256.0, 1.0 / 6.0 }; return 0;
     }
     return 1;
 }
@@ -662,6 +698,7 @@ double or_me2(int proc, const or_params *P, const double *p)
     case OR_GG_TTG:  return or_me2_bg(3, p, 2, P->mt, gs) / 256.0;
     case OR_UG_TTU:  return or_me2_ug_ttu(P->mt, gs, p);
     case OR_GG_TTGG: return or_me2_bg(4, p, 2, P->mt, gs) / 256.0 * 0.5;
+    case OR_GG_TTGGG: return or_me2_bg(5, p, 2, P->mt, gs) / 256.0 / 6.0;
     }
     return 0.0;
 }

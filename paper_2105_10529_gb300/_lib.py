@@ -78,6 +78,8 @@ def lib():
             "mf_selftest_wait": (C.c_int, [vp, C.c_uint]),
             "mf_integrate": (C.c_int, [vp, C.c_int, C.c_double, C.POINTER(MfCuts), i64, C.c_int, C.c_int,
                                        C.POINTER(MfResult), dp, dp]),
+            "mf_integrate_grid": (C.c_int, [vp, C.c_int, C.c_double, C.POINTER(MfCuts), i64, C.c_int, C.c_uint, dp,
+                                            C.c_int, C.POINTER(MfResult), dp, dp]),
             "mf_vegas_pass": (C.c_int, [vp, C.c_int, C.c_double, vp, i64, i64, C.c_uint, vp, vp,
                                         C.POINTER(MfEventArrays)]),
             "mf_vegas_refine": (C.c_int, [vp, C.c_int, C.c_int, C.c_double, vp, vp]),
@@ -108,7 +110,7 @@ def lib():
 
 def exported_symbols():
     return ["mf_default_config", "mf_process_info", "mf_create", "mf_destroy", "mf_last_error",
-            "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_set_helicity_split", "mf_set_observable", "mf_get_observable", "mf_device_status", "mf_selftest_wait", "mf_integrate", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
+            "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_set_helicity_split", "mf_set_observable", "mf_get_observable", "mf_device_status", "mf_selftest_wait", "mf_integrate", "mf_integrate_grid", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
             "mf_vegas_pass_static", "mf_set_couplings", "mf_vegas_pass_grad",
             "mf_integrate_batch", "mf_batch_pass", "mf_batch_grad", "mf_set_batch_schedule", "mf_autotune_batch",
             "mf_measure_fma_peak"]

@@ -150,6 +150,23 @@ class Context:
         _check(self.ptr, rc)
         return out
 
+    def integrate_grid(self, process: int, sqrt_s: float, n_events: int, n_iter: int, grid, first_iteration: int = 0,
+                       want_grads: bool = False, cuts=None):
+        """mf_integrate_grid: iterations from a host grid [dim][n_bins+1], Philox iterations from
+        first_iteration on; returns the integrate() dict with the final grid."""
+        res = MfResult()
+        it = np.zeros((n_iter, 2))
+        g_in = np.ascontiguousarray(grid, dtype=np.float64)
+        g_out = np.zeros_like(g_in)
+        dp = C.POINTER(C.c_double)
+        rc = _lib.lib().mf_integrate_grid(self.ptr, process, sqrt_s, _cuts(cuts), n_events, n_iter, first_iteration,
+                                          g_in.ctypes.data_as(dp), int(want_grads), C.byref(res),
+                                          it.ctypes.data_as(dp), g_out.ctypes.data_as(dp))
+        out = _result(res)
+        out.update(per_iter=it, grid=g_out, status=rc)
+        _check(self.ptr, rc)
+        return out
+
     def integrate_batch(self, processes, n_events, sqrt_s: float, n_iter: int, want_grids: bool = False,
                         want_grads: bool = False, cuts=None):
         """Several channels in one persistent launch per iteration (mf_integrate_batch).

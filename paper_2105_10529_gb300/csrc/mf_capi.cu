@@ -353,6 +353,10 @@ void mf_destroy(mf_ctx* c)
     cudaFree(c->d_bsums);
     cudaFree(c->d_bcount);
     if (c->graph) cudaGraphExecDestroy(c->graph);
+    if (c->int_stream) cudaStreamSynchronize(c->int_stream);
+    if (c->int_graph) cudaGraphExecDestroy(c->int_graph);
+    if (c->int_ev) cudaEventDestroy(c->int_ev);
+    if (c->int_stream) cudaStreamDestroy(c->int_stream);
     if (c->ev_user) cudaEventDestroy(c->ev_user);
     if (c->ev_cap) cudaEventDestroy(c->ev_cap);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
@@ -490,10 +494,28 @@ int mf_vegas_refine(mf_ctx* c, int dim, int n_bins, double alpha, const double* 
     return MF_OK;
 }
 
-int mf_integrate(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, long long n_events, int n_iter,
-                 int want_grads, mf_result* out, double* iter_host, double* grid_host)
+}  // extern "C"
+
+namespace {
+
+// the launch parameters that a captured iteration graph bakes in
+std::string integrate_key(const KParams& kp, int prec, int sched, int hsplit, int nblk, size_t sm, int n_iter,
+                          unsigned first_it, int obs_n)
 {
-    if (!c) return MF_ERR_ARG;
+    KParams k = kp;
+    k.iteration = 0;
+    std::string key(reinterpret_cast<const char*>(&k), sizeof(k));
+    const long long tail[8] = { prec, sched, hsplit, nblk, (long long)sm, n_iter, (long long)first_it, obs_n };
+    key.append(reinterpret_cast<const char*>(tail), sizeof(tail));
+    return key;
+}
+
+// n_iter VEGAS iterations (Philox iterations first_it, first_it + 1, ...) from the grid
+// grid_in_host (nullable: uniform); see mf_integrate and mf_integrate_grid
+int integrate_impl(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, long long n_events, int n_iter,
+                   unsigned first_it, const double* grid_in_host, int want_grads, mf_result* out, double* iter_host,
+                   double* grid_host)
+{
     const ProcOps* ops = proc_ops(process);
     if (!ops) return fail(c, MF_ERR_ARG, "unknown process");
     if (!out || n_events < 2 || n_iter < 1 || n_iter > MAX_ITER || !(sqrt_s > 0.0))
@@ -525,52 +547,83 @@ int mf_integrate(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, lon
     int nblk = 0;
     rc = pick_blocks(c, ops, sm, c->cfg.precision, &nblk);
     if (rc) return rc;
-    std::vector<double> g0((size_t)D * (nb + 1));
-    for (int d = 0; d < D; ++d)
-        for (int i = 0; i <= nb; ++i) g0[(size_t)d * (nb + 1) + i] = (double)i / (double)nb;
-    MF_CUDA(c, cudaMemcpyAsync(c->d_grid, g0.data(), g0.size() * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-    MF_CUDA(c, cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), c->stream));
-    const int ncol = 2 + D * nb;
-    for (int it = 0; it < n_iter; ++it) {
-        kp.iteration = (uint32_t)it;
-        MF_CUDA(c, ops->integrand(c->cfg.precision, false, c->sched, c->hsplit, kp, nblk, sm, c->stream));
-        finish_pass_kernel<<<1, 1024, ncol * sizeof(double), c->stream>>>(
-            c->d_partials, nblk, D, nb, n_events, c->cfg.alpha, it < n_iter - 1, c->d_grid, c->d_iter + 2 * it, nullptr);
-        MF_CUDA(c, cudaGetLastError());
-        if (obs) {
-            obs_reduce_kernel<<<1, 128, 0, c->stream>>>(c->d_obs_partials, nblk, nobs2, n_events,
-                                                        c->d_obs_iter + (size_t)it * 2 * nobs2);
-            MF_CUDA(c, cudaGetLastError());
-        }
+    // private stream for capture and replay, ordered after the caller's stream
+    if (!c->int_stream) {
+        MF_CUDA(c, cudaStreamCreateWithFlags(&c->int_stream, cudaStreamNonBlocking));
+        MF_CUDA(c, cudaEventCreateWithFlags(&c->int_ev, cudaEventDisableTiming));
     }
+    cudaStream_t s = c->int_stream;
+    MF_CUDA(c, cudaEventRecord(c->int_ev, c->stream));
+    MF_CUDA(c, cudaStreamWaitEvent(s, c->int_ev, 0));
+    std::vector<double> g0((size_t)D * (nb + 1));
+    if (grid_in_host) {
+        std::memcpy(g0.data(), grid_in_host, g0.size() * sizeof(double));
+    } else {
+        for (int d = 0; d < D; ++d)
+            for (int i = 0; i <= nb; ++i) g0[(size_t)d * (nb + 1) + i] = (double)i / (double)nb;
+    }
+    MF_CUDA(c, cudaMemcpyAsync(c->d_grid, g0.data(), g0.size() * sizeof(double), cudaMemcpyHostToDevice, s));
+    MF_CUDA(c, cudaMemsetAsync(c->d_counters, 0, 2 * sizeof(unsigned long long), s));
+    const int ncol = 2 + D * nb;
+    // the iterations: captured once, replayed while the parameters stay the same
+    const std::string key = integrate_key(kp, c->cfg.precision, c->sched, c->hsplit, nblk, sm, n_iter, first_it,
+                                          obs ? c->obs_n : 0);
+    if (!c->int_graph || c->int_key != key) {
+        if (c->int_graph) { cudaGraphExecDestroy(c->int_graph); c->int_graph = nullptr; c->int_key.clear(); }
+        cudaGraph_t g = nullptr;
+        MF_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        int erc = MF_OK;
+        for (int it = 0; it < n_iter && erc == MF_OK; ++it) {
+            kp.iteration = first_it + (uint32_t)it;
+            if (ops->integrand(c->cfg.precision, false, c->sched, c->hsplit, kp, nblk, sm, s) != cudaSuccess) {
+                erc = fail(c, MF_ERR_CUDA, "integrand launch");
+                break;
+            }
+            finish_pass_kernel<<<1, 1024, ncol * sizeof(double), s>>>(c->d_partials, nblk, D, nb, n_events, c->cfg.alpha,
+                                                                     it < n_iter - 1, c->d_grid, c->d_iter + 2 * it,
+                                                                     nullptr);
+            if (obs)
+                obs_reduce_kernel<<<1, 128, 0, s>>>(c->d_obs_partials, nblk, nobs2, n_events,
+                                                    c->d_obs_iter + (size_t)it * 2 * nobs2);
+        }
+        cudaError_t ce = cudaStreamEndCapture(s, &g);
+        if (erc) { if (g) cudaGraphDestroy(g); return erc; }
+        if (ce != cudaSuccess) return fail(c, MF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
+        ce = cudaGraphInstantiateWithFlags(&c->int_graph, g, 0);
+        cudaGraphDestroy(g);
+        if (ce != cudaSuccess) {
+            c->int_graph = nullptr;
+            return fail(c, MF_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        }
+        c->int_key = key;
+    }
+    MF_CUDA(c, cudaGraphLaunch(c->int_graph, s));
     if (want_grads) {
-        // one derivative pass at the final grid on fresh random numbers (Philox iteration n_iter)
+        // one derivative pass at the final grid on fresh random numbers (Philox iteration first_it + n_iter)
         KParams kg = kp;
-        kg.iteration = (uint32_t)n_iter;
+        kg.iteration = first_it + (uint32_t)n_iter;
         kg.mask_in = nullptr;
         const long long want = (n_events + 127) / 128, cap = (long long)c->n_sm * 8;
         const int gblk = (int)(want < cap ? want : cap);
-        MF_CUDA(c, gops->grad(c->cfg.precision, kg, gblk, c->d_partials, gops->k_as, c->cfg.alpha_s, c->stream));
-        finish_pass_kernel<<<1, 32, 4 * sizeof(double), c->stream>>>(c->d_partials, gblk, 1, 2, n_events, 0.0, 0,
-                                                                     nullptr, nullptr, c->d_sums);
+        MF_CUDA(c, gops->grad(c->cfg.precision, kg, gblk, c->d_partials, gops->k_as, c->cfg.alpha_s, s));
+        finish_pass_kernel<<<1, 32, 4 * sizeof(double), s>>>(c->d_partials, gblk, 1, 2, n_events, 0.0, 0, nullptr,
+                                                             nullptr, c->d_sums);
         MF_CUDA(c, cudaGetLastError());
     }
     double gsum[4] = { 0.0, 0.0, 0.0, 0.0 };
-    if (want_grads)
-        MF_CUDA(c, cudaMemcpyAsync(gsum, c->d_sums, sizeof(gsum), cudaMemcpyDeviceToHost, c->stream));
+    if (want_grads) MF_CUDA(c, cudaMemcpyAsync(gsum, c->d_sums, sizeof(gsum), cudaMemcpyDeviceToHost, s));
     std::vector<double> iters((size_t)2 * n_iter);
     unsigned long long cnt[2];
-    MF_CUDA(c, cudaMemcpyAsync(iters.data(), c->d_iter, iters.size() * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-    MF_CUDA(c, cudaMemcpyAsync(cnt, c->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, c->stream));
+    MF_CUDA(c, cudaMemcpyAsync(iters.data(), c->d_iter, iters.size() * sizeof(double), cudaMemcpyDeviceToHost, s));
+    MF_CUDA(c, cudaMemcpyAsync(cnt, c->d_counters, sizeof(cnt), cudaMemcpyDeviceToHost, s));
     if (grid_host)
-        MF_CUDA(c, cudaMemcpyAsync(grid_host, c->d_grid, (size_t)D * (nb + 1) * sizeof(double), cudaMemcpyDeviceToHost,
-                                   c->stream));
+        MF_CUDA(c, cudaMemcpyAsync(grid_host, c->d_grid, (size_t)D * (nb + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
     if (obs) {
         c->obs_iter_host.resize((size_t)n_iter * 2 * nobs2);
         MF_CUDA(c, cudaMemcpyAsync(c->obs_iter_host.data(), c->d_obs_iter, c->obs_iter_host.size() * sizeof(double),
-                                   cudaMemcpyDeviceToHost, c->stream));
+                                   cudaMemcpyDeviceToHost, s));
     }
-    MF_CUDA(c, cudaStreamSynchronize(c->stream));
+    MF_CUDA(c, cudaStreamSynchronize(s));
     if (take_device_error(c)) return fail(c, MF_ERR_TIMEOUT, "a bounded device wait ran out");
     double sw = 0.0, swi = 0.0;
     for (int k = 0; k < n_iter; ++k) {
@@ -615,6 +668,28 @@ int mf_integrate(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, lon
     if (cnt[1] > (unsigned long long)(n_events * (long long)n_iter) / 1000)
         return fail(c, MF_ERR_NUMERIC, "more than 0.1% of the event weights were not finite");
     return MF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int mf_integrate(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, long long n_events, int n_iter,
+                 int want_grads, mf_result* out, double* iter_host, double* grid_host)
+{
+    if (!c) return MF_ERR_ARG;
+    return integrate_impl(c, process, sqrt_s, cuts, n_events, n_iter, 0u, nullptr, want_grads, out, iter_host,
+                          grid_host);
+}
+
+int mf_integrate_grid(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, long long n_events, int n_iter,
+                      unsigned int first_iteration, const double* grid_in_host, int want_grads, mf_result* out,
+                      double* iter_host, double* grid_host)
+{
+    if (!c) return MF_ERR_ARG;
+    if (!grid_in_host) return fail(c, MF_ERR_ARG, "mf_integrate_grid: no starting grid");
+    return integrate_impl(c, process, sqrt_s, cuts, n_events, n_iter, first_iteration, grid_in_host, want_grads,
+                          out, iter_host, grid_host);
 }
 
 int mf_set_couplings(mf_ctx* c, double mt, double alpha_s)

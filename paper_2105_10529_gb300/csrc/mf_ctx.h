@@ -54,6 +54,12 @@ struct mf_ctx {
     int b_hsplit = 1;                    // tuned: lanes per event of the 2 -> 3 and 2 -> 4 gluon channels
     cudaGraphExec_t graph = nullptr;
     std::string graph_key;
+    // mf_integrate: its iterations captured as one CUDA graph on a private stream, replayed
+    // while the launch parameters (int_key) stay the same
+    cudaStream_t int_stream = nullptr;
+    cudaEvent_t int_ev = nullptr;
+    cudaGraphExec_t int_graph = nullptr;
+    std::string int_key;
     int b_last_nch = 0;                  // channel list of the grids in d_bgrids
     int b_last_proc[mf::MAX_CH] = {};
 };

@@ -146,12 +146,18 @@ __device__ __forceinline__ S rambo(S rs, const S (&m)[N], const double* u, S (&p
         // xi solves sum_i E_i(xi) = sqrt(shat) exactly, each massive energy is
         // sqrt(shat)/2 and the weight factor reduces to xi (= beta)
         if (m[0] == m[1]) {
+            // The massless momenta leave the conformal map back to back with |k| = sqrt(shat)/2
+            // only up to rounding amplified by the map's boost (about gamma^2 eps); the massive
+            // pair is built from their half difference d, rescaled to length xi sqrt(shat)/2
+            // with a first-order correction of |d| (its deviation is ~1e-10 at most, so the
+            // neglected second order is far below rounding): exactly back to back, on its
+            // mass shell to rounding
             const S h = 0.5 * rs;
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                p[i][1] = p[i][1] * xi; p[i][2] = p[i][2] * xi; p[i][3] = p[i][3] * xi;
-                p[i][0] = h;
-            }
+            const S d1 = 0.5 * (p[0][1] - p[1][1]), d2 = 0.5 * (p[0][2] - p[1][2]), d3 = 0.5 * (p[0][3] - p[1][3]);
+            const S dd = d1 * d1 + d2 * d2 + d3 * d3;
+            const S c = xi * (1.5 - 0.5 * dd / (h * h));
+            p[0][0] = h; p[0][1] = c * d1; p[0][2] = c * d2; p[0][3] = c * d3;
+            p[1][0] = h; p[1][1] = -(c * d1); p[1][2] = -(c * d2); p[1][3] = -(c * d3);
             return vol_massless * xi;
         }
     }

@@ -33,7 +33,7 @@ PDF_Q2_MAX = 1e8
 PDF_NOISE_SEED = 0x5DF
 
 # process ids (same numbering in the C ABI and in the oracle)
-EE_MUMU, GG_TT, UU_TT, GG_TTG, UG_TTU, GG_TTGG = 0, 1, 2, 3, 4, 5
+EE_MUMU, GG_TT, UU_TT, GG_TTG, UG_TTU, GG_TTGG, GG_TTGGG = 0, 1, 2, 3, 4, 5, 6
 PROCESS_NAMES = {
     EE_MUMU: "e+e- -> mu+mu-",
     GG_TT: "g g -> t tbar",
@@ -41,9 +41,10 @@ PROCESS_NAMES = {
     GG_TTG: "g g -> t tbar g",
     UG_TTU: "u g -> t tbar u",
     GG_TTGG: "g g -> t tbar g g",
+    GG_TTGGG: "g g -> t tbar g g g",
 }
-N_EXT = {EE_MUMU: 4, GG_TT: 4, UU_TT: 4, GG_TTG: 5, UG_TTU: 5, GG_TTGG: 6}
-DIM = {EE_MUMU: 2, GG_TT: 10, UU_TT: 10, GG_TTG: 14, UG_TTU: 14, GG_TTGG: 18}
+N_EXT = {EE_MUMU: 4, GG_TT: 4, UU_TT: 4, GG_TTG: 5, UG_TTU: 5, GG_TTGG: 6, GG_TTGGG: 7}
+DIM = {EE_MUMU: 2, GG_TT: 10, UU_TT: 10, GG_TTG: 14, UG_TTU: 14, GG_TTGG: 18, GG_TTGGG: 22}
 
 
 def _beta(a: float, b: float) -> float:
@@ -111,6 +112,9 @@ def workloads():
         "gg_tt": Workload("gg -> t tbar, 13 TeV, 1e7 x 10", GG_TT, 10_000_000, 10, Physics(seed=1)),
         "gg_ttg": Workload("gg -> t tbar g, 13 TeV, 1e7 x 10", GG_TTG, 10_000_000, 10, Physics(seed=2)),
         "gg_ttgg": Workload("gg -> t tbar g g, 13 TeV, 4e6 x 10", GG_TTGG, 4_000_000, 10, Physics(seed=3)),
+        # the multi-leg extension: three final gluons (pT > 30 GeV, |eta| < 2.5 and Delta R > 0.4
+        # between every pair, as for two)
+        "gg_ttggg": Workload("gg -> t tbar g g g, 13 TeV, 1e6 x 10", GG_TTGGG, 1_000_000, 10, Physics(seed=6)),
     }
 
 

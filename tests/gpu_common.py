@@ -33,11 +33,10 @@ def random_grid(dim, nb=50, seed=0):
 def oracle_events(proc, phys, pdf, grid, n, iteration=0, first=0, events=None):
     """Oracle per-event outputs for events first..first+n-1 (or the given list)."""
     idx = list(range(first, first + n)) if events is None else list(events)
-    out = dict(u=[], x=[], bins=[], w=[], mask=[], me2=[], p=[], plab=[])
+    out = dict(u=[], x=[], bins=[], w=[], mask=[], me2=[], p=[], plab=[], x12=[])
     dim = IN.DIM[proc]
     n_ext = IN.N_EXT[proc]
-    for e in idx:
-        o = O.event(proc, phys, pdf, grid, e, iteration)
+    for o in O.events(proc, phys, pdf, grid, idx, iteration):
         out["u"].append(np.array(o.u[:dim]))
         out["x"].append(np.array(o.x[:dim]))
         out["bins"].append(np.array(o.bins[:dim], dtype=np.uint8))
@@ -46,6 +45,7 @@ def oracle_events(proc, phys, pdf, grid, n, iteration=0, first=0, events=None):
         out["me2"].append(o.me2)
         out["p"].append(np.array(o.p[:4 * n_ext]).reshape(n_ext, 4))
         out["plab"].append(np.array(o.plab[:4 * n_ext]).reshape(n_ext, 4))
+        out["x12"].append((o.x1, o.x2))
     return {k: np.array(v) for k, v in out.items()}
 
 
@@ -94,24 +94,19 @@ def rel_err(a, b):
     return np.where((a == 0) & (b == 0), 0.0, np.abs(a - b) / den)
 
 
-def assert_fp_parity(err, prec, what=""):
+def assert_fp_parity(err, prec, what="", bound=None):
     """Per-event floating-point parity.  Mixed path: every event within 1e-5.
-    FP64 path: at least 99.5% of events within 1e-12 (median below 1e-14) and
-    every event within 1e-10; the tail are events whose weight is ill-conditioned (x -> 1 where
-    the PDF falls like (1-x)^5, forward t-channel tops at high energy), where
-    last-bit differences of exp/log between libm and CUDA or between the two
-    matrix-element algorithms are amplified."""
+    FP64 path: every event within its own bound (default 1e-12; the callers pass
+    fp64_event_bounds, which exceed 1e-12 only where the event is
+    ill-conditioned: a final particle along a beam, a PDF value near x = 1,
+    a large RAMBO boost), and the median below 1e-14."""
     err = np.asarray(err, float)
     if err.size == 0:
         return
     if prec == 1:
         assert err.max() < 1e-5, (what, err.max(), int(np.argmax(err)))
         return
-    frac_bad = float(np.mean(err > 1e-12))
-    assert frac_bad <= 5e-3 or int(np.sum(err > 1e-12)) <= 1, (what, frac_bad, err.max())
-    assert err.max() < 1e-10, (what, err.max(), int(np.argmax(err)))
-    if err.size >= 100:
-        assert np.median(err) < 1e-14, (what, np.median(err))
+    assert_fp64_bounded(err, np.full(err.shape, 1e-12) if bound is None else bound, what)
 
 
 def check_events_against_oracle(proc, phys, opdf, grid, ev, iteration, prec, first=0, events=None, what=""):
@@ -131,8 +126,91 @@ def check_events_against_oracle(proc, phys, opdf, grid, ev, iteration, prec, fir
         for i in np.nonzero(mk != ref["mask"])[0]:
             assert cut_margin(proc, phys, ref["plab"][i]) < 1e-9, (what, "mask flip far from a threshold", int(idx[i]))
         same = mk == ref["mask"]
+    bounds = dict(zip(("me2", "w"), fp64_event_bounds(proc, phys, opdf, ref))) if prec == 0 else {}
     for f in ("w", "me2"):
         if f in ev:
             v = ev[f].cpu().numpy()[idx]
-            assert_fp_parity(rel_err(v[same], ref[f][same]), prec, f"{what} {f}")
+            assert_fp_parity(rel_err(v[same], ref[f][same]), prec, f"{what} {f}",
+                             bounds[f][same] if prec == 0 else None)
     return ref
+
+
+EPS = np.finfo(float).eps
+# process -> (PDF flavours of the two incoming partons, masses of the final particles)
+_FLAV = {IN.GG_TT: (0, 0), IN.GG_TTG: (0, 0), IN.GG_TTGG: (0, 0), IN.GG_TTGGG: (0, 0), IN.UU_TT: (1, 2),
+         IN.UG_TTU: (1, 0)}
+
+
+def me_condition(proc, phys, p):
+    """Condition number of |M|^2 at momenta p [n_ext, 4] (partonic frame): a
+    final particle i nearly along a beam makes p_beam . p_i = E (E_i - |p_z,i|)
+    cancel, amplifying the relative rounding of its momentum by
+    2 E_i^2 / (m_i^2 + pT_i^2); the largest such factor (at least 1)."""
+    if proc == IN.EE_MUMU:
+        return 1.0
+    k = 1.0
+    for i in range(2, p.shape[0]):
+        m = phys.mt if i in (2, 3) else 0.0
+        pt2 = p[i][1] ** 2 + p[i][2] ** 2
+        k = max(k, 2.0 * p[i][0] ** 2 / max(m * m + pt2, 1e-300))
+    return k
+
+
+def pdf_condition(opdf, flav, x, q2):
+    """|d ln(x f) / d ln x| + 1 of the interpolated PDF (central difference in
+    ln x): how much a relative rounding of ln x (the two paths form it
+    differently) grows in the PDF value.  Large where the interpolant nears a
+    zero, in the last x cell toward x = 1."""
+    if x >= 1.0 or x <= 0.0:
+        return 1.0
+    h = 1e-6
+    lx = math.log(x)
+    f0 = opdf.xf(flav, x, q2)
+    fp = opdf.xf(flav, min(math.exp(lx + h), 1.0), q2)
+    fm = opdf.xf(flav, math.exp(lx - h), q2)
+    if f0 == 0.0:
+        return 1e300
+    return abs((fp - fm) / (2 * h) / f0) + 1.0
+
+
+def fp64_event_bounds(proc, phys, opdf, ref):
+    """Per-event bounds for the FP64 path against the oracle, from the
+    conditioning of each event (64 eps times the condition numbers, and never
+    below 1e-12):
+      |M|^2 : 64 eps me_condition;
+      w     : that, plus the weight factor's 64 eps sum_i pdf_condition(x_i) (1 + |ln x_i|)
+              and the RAMBO map's 8 gamma^2 eps.
+    Returns (bound_me2 [n], bound_w [n])."""
+    n = len(ref["w"])
+    b_me = np.empty(n); b_w = np.empty(n)
+    gam = np.ones(n) if proc == IN.EE_MUMU else rambo_gamma(ref["x"], IN.N_EXT[proc] - 2)
+    for e in range(n):
+        km = me_condition(proc, phys, ref["p"][e])
+        b_me[e] = max(1e-12, 64 * EPS * km)
+        bw = b_me[e] + 8 * gam[e] ** 2 * EPS
+        if proc in _FLAV:
+            x1, x2 = ref["x12"][e]
+            p = ref["p"][e]
+            if proc in (IN.GG_TT, IN.UU_TT):
+                q2 = phys.mt ** 2
+            else:
+                ht = sum(math.sqrt((phys.mt ** 2 if i in (2, 3) else 0.0) + p[i][1] ** 2 + p[i][2] ** 2)
+                         for i in range(2, p.shape[0]))
+                q2 = 0.25 * ht * ht
+            f1, f2 = _FLAV[proc]
+            bw += 64 * EPS * (pdf_condition(opdf, f1, x1, q2) * (1 + abs(math.log(x1)))
+                              + pdf_condition(opdf, f2, x2, q2) * (1 + abs(math.log(x2))))
+        b_w[e] = max(1e-12, bw)
+    return b_me, b_w
+
+
+def assert_fp64_bounded(err, bound, what=""):
+    """FP64 per-event parity: every event within its own conditioning bound,
+    and the bulk far below 1e-12 (median under 1e-14 for 100 events or more)."""
+    err = np.asarray(err, float); bound = np.asarray(bound, float)
+    if err.size == 0:
+        return
+    bad = np.nonzero(err > bound)[0]
+    assert bad.size == 0, (what, [(int(i), float(err[i]), float(bound[i])) for i in bad[:5]])
+    if err.size >= 100:
+        assert np.median(err) < 1e-14, (what, np.median(err))
