@@ -278,9 +278,35 @@ static int perms(int k, int out[][8])
 
 /* C[s][t] = sum over gluon colours a_1..a_k and quark indices i,j of
  * conj((T^{a_s1} ... T^{a_sk})_ij) (T^{a_t1} ... T^{a_tk})_ij, by brute force.
- * The 8^k colour assignments are split over threads, each adding into its own
- * matrix; the per-thread matrices are then added in thread order. */
+ * Up to four gluons the 8^k colour assignments are summed one after the other;
+ * for five (32768 assignments, 120 x 120 entries) they are split into 64 fixed
+ * consecutive chunks, each summed in order (the chunks over threads), and the
+ * chunk sums added in chunk order: the result does not depend on the number of
+ * threads. */
 #define MAXPERM 120
+static void colour_chunk(int k, int np, int (*P)[8], cplx T[8][3][3], int a0, int a1, double *Cp)
+{
+    cplx (*S)[3][3] = malloc(sizeof(cplx[3][3]) * MAXPERM);
+    for (int as = a0; as < a1; ++as) {
+        int col[8], r = as;
+        for (int i = 0; i < k; ++i) { col[i] = r % 8; r /= 8; }
+        for (int s = 0; s < np; ++s) {
+            cplx M[3][3];
+            memcpy(M, T[col[P[s][0]]], sizeof(M));
+            for (int i = 1; i < k; ++i) mat3_mul(M, T[col[P[s][i]]], M);
+            memcpy(S[s], M, sizeof(M));
+        }
+        for (int s = 0; s < np; ++s)
+            for (int t = 0; t < np; ++t) {
+                cplx acc = 0;
+                for (int i = 0; i < 3; ++i)
+                    for (int j = 0; j < 3; ++j) acc += conj(S[s][i][j]) * S[t][i][j];
+                Cp[s * np + t] += creal(acc);
+            }
+    }
+    free(S);
+}
+
 void or_colour_matrix(int k, double *C)
 {
     static int P[40320][8];
@@ -290,42 +316,18 @@ void or_colour_matrix(int k, double *C)
     for (int i = 0; i < np * np; ++i) C[i] = 0.0;
     int n_assign = 1;
     for (int i = 0; i < k; ++i) n_assign *= 8;
-    int nthr = 1;
-#ifdef _OPENMP
-    nthr = omp_get_max_threads();
-    if (nthr > 64) nthr = 64;
-#endif
-    double *part = calloc((size_t)nthr * np * np, sizeof(double));
-#pragma omp parallel num_threads(nthr)
-    {
-        int tid = 0;
-#ifdef _OPENMP
-        tid = omp_get_thread_num();
-#endif
-        double *Cp = part + (size_t)tid * np * np;
-        cplx (*S)[3][3] = malloc(sizeof(cplx[3][3]) * MAXPERM);
-#pragma omp for schedule(static)
-        for (int as = 0; as < n_assign; ++as) {
-            int col[8], r = as;
-            for (int i = 0; i < k; ++i) { col[i] = r % 8; r /= 8; }
-            for (int s = 0; s < np; ++s) {
-                cplx M[3][3];
-                memcpy(M, T[col[P[s][0]]], sizeof(M));
-                for (int i = 1; i < k; ++i) mat3_mul(M, T[col[P[s][i]]], M);
-                memcpy(S[s], M, sizeof(M));
-            }
-            for (int s = 0; s < np; ++s)
-                for (int t = 0; t < np; ++t) {
-                    cplx acc = 0;
-                    for (int i = 0; i < 3; ++i)
-                        for (int j = 0; j < 3; ++j) acc += conj(S[s][i][j]) * S[t][i][j];
-                    Cp[s * np + t] += creal(acc);
-                }
-        }
-        free(S);
+    if (k <= 4) {
+        colour_chunk(k, np, P, T, 0, n_assign, C);
+        return;
     }
-    for (int t = 0; t < nthr; ++t)
-        for (int i = 0; i < np * np; ++i) C[i] += part[(size_t)t * np * np + i];
+    enum { NCHUNK = 64 };
+    double *part = calloc((size_t)NCHUNK * np * np, sizeof(double));
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int c = 0; c < NCHUNK; ++c)
+        colour_chunk(k, np, P, T, (int)((long)n_assign * c / NCHUNK), (int)((long)n_assign * (c + 1) / NCHUNK),
+                     part + (size_t)c * np * np);
+    for (int c = 0; c < NCHUNK; ++c)
+        for (int i = 0; i < np * np; ++i) C[i] += part[(size_t)c * np * np + i];
     free(part);
 }
 

@@ -27,9 +27,10 @@ PHYSICS = {
     IN.GG_TTG: IN.Physics(seed=14),
     IN.UG_TTU: IN.Physics(seed=15, channel=3),
     IN.GG_TTGG: IN.Physics(seed=16),
+    IN.GG_TTGGG: IN.Physics(seed=17),
 }
 ITERATION = 5
-N_FIRST = {IN.EE_MUMU: 8, IN.GG_TT: 8, IN.UU_TT: 8, IN.GG_TTG: 8, IN.UG_TTU: 8, IN.GG_TTGG: 4}
+N_FIRST = {IN.EE_MUMU: 8, IN.GG_TT: 8, IN.UU_TT: 8, IN.GG_TTG: 8, IN.UG_TTU: 8, IN.GG_TTGG: 4, IN.GG_TTGGG: 6}
 HIGH_EVENT = (1 << 32) + 3          # the Philox counter's second word in use
 U_STORED = 4                        # uniforms stored per event (the first dimensions, at most D)
 

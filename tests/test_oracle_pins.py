@@ -373,6 +373,32 @@ def test_cuts_hand_built():
     assert abs(sh - 6.0502044810397875) < 1e-15
 
 
+def test_cuts_hand_built_three_gluons():
+    """g g -> t tbar g g g: pT and eta on each gluon, Delta R on each of the
+    three pairs (the failing pair placed first, second and last)."""
+    ph = IN.Physics()
+
+    def ev(glu):
+        p = np.zeros((7, 4))
+        p[:4, 0] = 1.0
+        for i, (pt, pz, phi) in enumerate(glu):
+            p[4 + i] = [math.hypot(pt, pz), pt * math.cos(phi), pt * math.sin(phi), pz]
+        return p
+
+    good = [(50, 0, 0.0), (60, 0, 1.0), (70, 0, 2.0)]
+    assert O.cuts(IN.GG_TTGGG, ph, ev(good)) == 1
+    assert O.cuts(IN.GG_TTGGG, ph, ev([(50, 0, 0.0), (60, 0, 1.0), (29, 0, 2.0)])) == 0       # pT of the third
+    assert O.cuts(IN.GG_TTGGG, ph, ev([(50, 0, 0.0), (60, 0, 1.0), (70, 70 * math.sinh(2.6), 2.0)])) == 0
+    assert O.cuts(IN.GG_TTGGG, ph, ev([(50, 0, 0.0), (60, 0, 0.3), (70, 0, 2.0)])) == 0       # pair (1, 2)
+    assert O.cuts(IN.GG_TTGGG, ph, ev([(50, 0, 0.0), (60, 0, 1.0), (70, 0, 1.3)])) == 0       # pair (2, 3)
+    assert O.cuts(IN.GG_TTGGG, ph, ev([(50, 0, 0.0), (60, 0, 2.0), (70, 0, 0.3)])) == 0       # pair (1, 3)
+    assert O.cuts(IN.GG_TTGGG, ph, ev([(50, 0, 0.0), (60, 0, 2.0), (70, 0, 0.45)])) == 1
+    q = ev(good)
+    q[2, 1:] = [30.0, 40.0, 5.0]
+    ht = math.sqrt(MT ** 2 + 2500) + MT + 50 + 60 + 70
+    assert abs(O.muf2(IN.GG_TTGGG, ph, q) - ht * ht / 4) < 1e-9
+
+
 def test_factorisation_scale():
     ph = IN.Physics()
     p = np.zeros((6, 4))
@@ -559,13 +585,13 @@ def gluon_setup(p, k):
     return gp, kg
 
 
-@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_ward_identity_every_partial_amplitude(k):
     rng = np.random.default_rng(30 + k)
     masses = [MT, MT] + [0.0] * (k - 2)
     p = event_momenta(rng, masses, 2500.0)
     gp, kg = gluon_setup(p, k)
-    for pols in [(0,) * k, tuple(rng.integers(0, 2, k))]:
+    for pols in ([(0,) * k, tuple(rng.integers(0, 2, k))] if k < 5 else [tuple(rng.integers(0, 2, k))]):
         eps = np.array([lin_pol(gp[i], pols[i]) for i in range(k)], dtype=complex)
         perms = list(itertools.permutations(range(k)))
         spins = [(0, 0), (0, 1), (1, 0)]
@@ -579,7 +605,7 @@ def test_ward_identity_every_partial_amplitude(k):
                     assert abs(a) < 1e-13 * scale * gp[j][0]   # eps -> k scales A by ~E_j
 
 
-@pytest.mark.parametrize("k", [3, 4])
+@pytest.mark.parametrize("k", [3, 4, 5])
 def test_lorentz_invariance(k):
     rng = np.random.default_rng(40 + k)
     p = event_momenta(rng, [MT, MT] + [0.0] * (k - 2), 2000.0)
@@ -597,6 +623,19 @@ def test_bose_symmetry_gg_ttgg():
     assert abs(O.me2_bg(4, q, 2, MT, GS) / m0 - 1) < 1e-12
     q = p.copy(); q[[0, 1]] = q[[1, 0]]
     assert abs(O.me2_bg(4, q, 2, MT, GS) / m0 - 1) < 1e-12
+
+
+def test_bose_symmetry_gg_ttggg():
+    """Every permutation of the three final gluons, and the two initial
+    gluons swapped, leave |M|^2 unchanged."""
+    rng = np.random.default_rng(51)
+    p = event_momenta(rng, [MT, MT, 0.0, 0.0, 0.0], 3000.0)
+    m0 = O.me2_bg(5, p, 2, MT, GS)
+    for perm in itertools.permutations([4, 5, 6]):
+        q = p.copy(); q[[4, 5, 6]] = p[list(perm)]
+        assert abs(O.me2_bg(5, q, 2, MT, GS) / m0 - 1) < 1e-12, perm
+    q = p.copy(); q[[0, 1]] = q[[1, 0]]
+    assert abs(O.me2_bg(5, q, 2, MT, GS) / m0 - 1) < 1e-12
 
 
 @pytest.mark.parametrize("k", [2, 3])
@@ -686,6 +725,41 @@ def test_explicit_colour_sum_equals_colour_matrix_contraction(k):
                 total += float(np.sum(np.abs(M) ** 2))
     ref = O.me2_bg(k, p, 2, MT, GS)
     assert abs(total / ref - 1) < 1e-12, (total, ref)
+
+
+def test_explicit_colour_sum_five_gluons():
+    """The explicit colour route at five gluons (8^5 gluon and 3 x 3 quark
+    colour assignments), for the oracle's partial amplitudes of two
+    polarisation and spin configurations: sum over colours of
+    |sum_sigma (T^a_sigma1 ... T^a_sigma5)_ij A_sigma|^2 equals A^dagger C A
+    with the oracle's brute-force colour matrix C, to 1e-12."""
+    k = 5
+    rng = np.random.default_rng(85)
+    p = event_momenta(rng, [MT, MT] + [0.0] * (k - 2), 2200.0)
+    gp, kg = gluon_setup(p, k)
+    T = gell_mann_textbook()
+    perms = list(itertools.permutations(range(k)))
+    Cm = O.colour_matrix(k)
+    configs = [((0, 1, 0, 1, 1), 0, 1), ((1, 1, 0, 0, 1), 1, 1)]
+    As = []
+    for pols, s3, s4 in configs:
+        eps = np.array([lin_pol(gp[i], pols[i]) for i in range(k)], dtype=complex)
+        As.append(np.array([O.bg_partial(kg, eps, p[2], p[3], MT, GS, s3, s4, perm) for perm in perms]))
+    # M_c[a_0 .. a_4, i, j] = sum_sigma A_c[sigma] (T^{a_sigma(1)} ... T^{a_sigma(5)})_ij, the string of
+    # every ordering built as a chain product over its positions, its colour axes then put in gluon order
+    M = [np.zeros((8,) * k + (3, 3), dtype=complex) for _ in configs]
+    for si, perm in enumerate(perms):
+        prod = T
+        for q in range(1, k):
+            prod = np.einsum("...ij,bjk->...bik", prod, T)
+        order = [perm.index(g) for g in range(k)]          # the position axis that carries gluon g
+        prod = np.transpose(prod, order + [k, k + 1])
+        for c in range(len(configs)):
+            M[c] += As[c][si] * prod
+    total = [float(np.sum(np.abs(M[c]) ** 2)) for c in range(len(configs))]
+    for c in range(len(configs)):
+        ref = float(np.real(np.conj(As[c]) @ Cm @ As[c]))
+        assert abs(total[c] / ref - 1) < 1e-12, (c, total[c], ref)
 
 
 def _collinear_ug_config(E1, E2, x, lam, phi, th, ph):
@@ -798,6 +872,39 @@ def test_gg_ttgg_final_state_collinear_limit():
     assert dev[1] < 0.03 * dev[0] and dev[2] < 0.03 * dev[1], dev
 
 
+def test_gg_ttggg_final_state_collinear_limit():
+    """Absolute normalisation of g g -> t tbar g g g (identical-gluon factor
+    1/6 included): with two of the final gluons collinear, momentum fractions z
+    and 1 - z of P, the azimuth-averaged averaged |M|^2 tends to
+    (1/3) (g_s^2 / p6.p7) P_gg(z) |M|^2(g g -> t tbar g g) at (p5, P), the latter
+    pinned by the previous tests (its 1/2 included); corrections fall like k_T^2."""
+    E1, E2, th, ph, z, EP = 1100.0, 800.0, 1.1, 0.4, 0.35, 500.0
+    p1 = np.array([E1, 0.0, 0.0, E1]); p2 = np.array([E2, 0.0, 0.0, -E2])
+    n5 = np.array([math.sin(2.1) * math.cos(-0.7), math.sin(2.1) * math.sin(-0.7), math.cos(2.1)])
+    p5 = np.concatenate([[300.0], 300.0 * n5])
+    nP = np.array([math.sin(0.9) * math.cos(2.0), math.sin(0.9) * math.sin(2.0), math.cos(0.9)])
+    v1 = np.cross(nP, [0.0, 0.0, 1.0]); v1 /= np.linalg.norm(v1)
+    v2 = np.cross(nP, v1)
+    P = np.concatenate([[EP], EP * nP])
+    h3, h4 = _tt_pair(p1 + p2 - p5 - P, th, ph)
+    born = O.me2_bg(4, np.array([p1, p2, h3, h4, p5, P]), 2, MT, GS) / 256 * 0.5
+    dev = []
+    for lam in (1e-2, 1e-3, 1e-4):
+        r = []
+        for j in range(8):
+            phi = 2 * math.pi * j / 8
+            vt = math.cos(phi) * v1 + math.sin(phi) * v2
+            a = z * EP * nP + lam * EP * vt
+            b = (1 - z) * EP * nP - lam * EP * vt
+            p6 = np.concatenate([[np.linalg.norm(a)], a]); p7 = np.concatenate([[np.linalg.norm(b)], b])
+            p3, p4 = _tt_pair(p1 + p2 - p5 - p6 - p7, th, ph)
+            full = O.me2(IN.GG_TTGGG, IN.Physics(), np.array([p1, p2, p3, p4, p5, p6, p7]))
+            r.append(full / ((1.0 / 3.0) * (GS * GS / mdot(p6, p7)) * _p_gg(z) * born))
+        dev.append(abs(np.mean(r) - 1))
+    assert dev[1] < 1e-4 and dev[2] < 1e-6, dev
+    assert dev[1] < 0.03 * dev[0] and dev[2] < 0.03 * dev[1], dev
+
+
 # ------------------------------------------------------------------ colour
 
 def test_gellmann_algebra():
@@ -813,7 +920,7 @@ def test_gellmann_algebra():
     assert abs(f(3, 4, 7) - math.sqrt(3) / 2) < 1e-15
 
 
-@pytest.mark.parametrize("k", [2, 3, 4])
+@pytest.mark.parametrize("k", [2, 3, 4, 5])
 def test_colour_matrix_casimir_and_symmetry(k):
     Cm = O.colour_matrix(k)
     CF, N = 4 / 3, 3
@@ -827,3 +934,17 @@ def test_colour_matrix_casimir_and_symmetry(k):
         vals = set(np.round(Cm.ravel() * 54).astype(int))
         assert vals <= {512, 80, 71, 62, 8, -1, -10, -28, -64}
         assert np.allclose(Cm * 54, np.round(Cm * 54), atol=1e-10)
+    if k == 5:
+        # entries are integers over 324 = 4 * 81 (each string product of five T's carries 1/2^5,
+        # the traces of the closed indices powers of 1/3); the diagonal 4096/324 = N C_F^5
+        assert np.allclose(Cm * 324, np.round(Cm * 324), atol=1e-9)
+        assert abs(Cm[0, 0] * 324 - 4096) < 1e-9
+        # the colour matrix depends only on the relative ordering: C[pi s, pi t] = C[s, t]
+        perms = list(itertools.permutations(range(k)))
+        index = {q: i for i, q in enumerate(perms)}
+        rng = np.random.default_rng(5)
+        for _ in range(20):
+            pi = rng.permutation(k)
+            a, b = rng.integers(0, len(perms), 2)
+            pa = tuple(pi[g] for g in perms[a]); pb = tuple(pi[g] for g in perms[b])
+            assert abs(Cm[index[pa], index[pb]] - Cm[a, b]) < 1e-12
