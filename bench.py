@@ -55,6 +55,8 @@ def parse():
                     help="skip the legs that run the other single-process workloads at full size and time "
                          "the derivative and evaluate calls")
     ap.add_argument("--batch-iters", type=int, default=10)
+    ap.add_argument("--ttggg-events", type=int, default=400_000,
+                    help="events of the timed mixed-precision g g -> t tbar g g g pass")
     ap.add_argument("--sched", type=int, default=None,
                     help="integrand schedule (0 free warps, 1 CTA barrier per helicity, 2 = 1 + colour sum on the "
                          "tensor cores, 3 = 2 with one warp per event and one lane per helicity; default 3)")
@@ -286,6 +288,121 @@ def run_derivatives(ctx, phys, IN, grid, stream):
     t, _ = timed(lambda: ctx.evaluate_grad(IN.GG_TTGG, mg))
     out["evaluate_with_dme2_dp_gg_ttgg"] = {"points": n_g, "points_per_s": n_g / t, "s": t,
                                             "note": "forward mode: one tangent evaluation per momentum component (24)"}
+    return out
+
+
+def run_helicity(pdf, IN, MF_FP64, MF_MIXED, stream):
+    """Helicity measurement (mf_helicity_profile, FP64) on events that pass the
+    cuts at the uniform grid, per top process: configurations in all, exactly
+    zero ones (skipped by the integrand), the mean share of |M|^2 carried by the
+    largest configuration and the mean number of configurations that carry
+    99%; and the light-quark channels' pass time (mixed, 4e6 events, CUDA
+    events) with the filtered helicity loops."""
+    import numpy as np
+    import torch
+    from paper_2105_10529_gb300.api import Context, process_info
+    out = {}
+    names = {IN.GG_TT: "gg_tt", IN.UU_TT: "uu_tt", IN.GG_TTG: "gg_ttg", IN.UG_TTU: "ug_ttu", IN.GG_TTGG: "gg_ttgg"}
+    for p, name in names.items():
+        phys = IN.Physics(seed=11)
+        _, dim = process_info(p)
+        grid = torch.linspace(0, 1, phys.n_bins + 1, dtype=torch.float64, device="cuda").repeat(dim, 1).contiguous()
+        ctx = Context(phys, pdf, precision=MF_FP64, stream=stream)
+        _, ev = ctx.vegas_pass(p, phys.sqrt_s, grid, 4000, iteration=5, want_events=True, fields=("mask", "momenta"))
+        mom = ev["momenta"][ev["mask"].bool()][:2000].contiguous()
+        prof = ctx.helicity_profile(p, mom).cpu().numpy()
+        ctx.close()
+        tot = prof.sum(1, keepdims=True)
+        share = prof / tot
+        srt = -np.sort(-share, axis=1)
+        n99 = (np.cumsum(srt, axis=1) < 0.99).sum(1) + 1
+        entry = {"configurations": int(prof.shape[1]), "exactly_zero": int(np.all(prof == 0.0, axis=0).sum()),
+                 "mean_largest_share": float(srt[:, 0].mean()), "mean_configs_for_99pct": float(n99.mean()),
+                 "mean_smallest_nonzero_share": float(np.where(share > 0, share, np.inf).min(1).mean()),
+                 "events": int(prof.shape[0])}
+        if p in (IN.UU_TT, IN.UG_TTU):
+            ctx = Context(phys, pdf, precision=MF_MIXED, stream=stream)
+            ctx.vegas_pass(p, phys.sqrt_s, grid, 400_000, iteration=0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            torch.cuda.synchronize()
+            e0.record(stream)
+            ctx.vegas_pass(p, phys.sqrt_s, grid, 4_000_000, iteration=1)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            entry["mixed_pass_ms_4e6_filtered"] = e0.elapsed_time(e1)
+            ctx.close()
+        out[name] = entry
+    return out
+
+
+def run_ttggg(pdf, IN, MF_FP64, MF_MIXED, stream, n_mixed, fma32):
+    """g g -> t tbar g g g (the multi-leg extension: 5 gluons, 120 colour orderings,
+    warp-level Berends-Giele recursion): one mixed-precision pass of n_mixed events
+    and one FP64 pass, CUDA events on the stream after a warm-up pass, at the grid
+    after two refined iterations; the algorithmic FLOPs of the recursion per event
+    that passes the cuts (64 helicity configurations); the per-event error of the
+    mixed weights against the FP64 CPU oracle on a sample; sigma from 2 iterations."""
+    import numpy as np
+    import torch
+    from paper_2105_10529_gb300.api import Context, process_info
+    from paper_2105_10529_gb300.gen import bg_tables
+    p = IN.GG_TTGGG
+    phys = IN.workloads()["gg_ttggg"].physics
+    _, dim = process_info(p)
+    hel = bg_tables.helicity_flops(5)
+    fl_event = 64 * hel["total"]
+    out = {"workload": "g g -> t tbar g g g LO, 13 TeV, pT(g)>30, |eta(g)|<2.5, dR(g,g)>0.4 for every pair",
+           "flops_per_passing_event": fl_event, "flops_basis": "bg_tables.helicity_flops(5) x 64 helicities",
+           "flops_split_per_helicity": {k: v for k, v in hel.items() if k not in ("counts",)}}
+    ctx = Context(phys, pdf, precision=MF_MIXED, stream=stream)
+    r = ctx.integrate(p, phys.sqrt_s, 100_000, 2, want_grid=True)
+    grid = torch.tensor(r["grid"], device="cuda")
+    _, ev = ctx.vegas_pass(p, phys.sqrt_s, grid, 50_000, iteration=50, want_events=True, fields=("mask", "w"))
+    pass_frac = float(ev["mask"].float().mean().item())
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ctx.vegas_pass(p, phys.sqrt_s, grid, 100_000, iteration=51)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    s32, _ = ctx.vegas_pass(p, phys.sqrt_s, grid, n_mixed, iteration=52)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t32 = e0.elapsed_time(e1) / 1e3
+    ach = fl_event * n_mixed * pass_frac / t32 / 1e12
+    out["mixed"] = {"events": n_mixed, "events_per_s": n_mixed / t32, "kernel_ms": t32 * 1e3, "pass_fraction": pass_frac,
+                    "achieved_tflops": ach, "frac_of_fp32_peak": ach / (SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ / 1e6),
+                    "frac_of_measured_fma_peak": ach / fma32, "sigma_2_iterations_pb": r["sigma"],
+                    "error_pb": r["error"]}
+    ctx.close()
+    n64 = max(2000, n_mixed // 50)
+    ctx64 = Context(phys, pdf, precision=MF_FP64, stream=stream)
+    ctx64.vegas_pass(p, phys.sqrt_s, grid, 2000, iteration=53)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx64.vegas_pass(p, phys.sqrt_s, grid, n64, iteration=54)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t64 = e0.elapsed_time(e1) / 1e3
+    out["fp64"] = {"events": n64, "events_per_s": n64 / t64, "mixed_speedup": (n_mixed / t32) / (n64 / t64)}
+    ctx64.close()
+    # per-event error of the mixed path against the FP64 CPU oracle
+    try:
+        import oracle as O
+        n_or = 400
+        ctx = Context(phys, pdf, precision=MF_MIXED, stream=stream)
+        _, evm = ctx.vegas_pass(p, phys.sqrt_s, grid, n_or, iteration=55, want_events=True, fields=("w",))
+        torch.cuda.synchronize()
+        ctx.close()
+        t0 = time.perf_counter()
+        evs = O.events(p, phys, O.Pdf(pdf), grid.cpu().numpy(), range(n_or), 55, n_threads=os.cpu_count() or 1)
+        t_or = time.perf_counter() - t0
+        w_or = np.array([e.w for e in evs]); w_mx = evm["w"].cpu().numpy()
+        sel = w_or != 0
+        rel = np.abs(w_mx[sel] - w_or[sel]) / np.abs(w_or[sel])
+        out["stated_err"] = {"per_event_rel_max": float(rel.max()), "per_event_rel_median": float(np.median(rel)),
+                             "events": int(sel.sum()), "reference": "FP64 CPU oracle"}
+        out["cpu_oracle_events_per_s"] = n_or / t_or
+    except Exception as exc:                 # reported in the line, never fatal to it
+        out["stated_err"] = {"error": f"{type(exc).__name__}: {exc}"}
     return out
 
 
@@ -550,6 +667,22 @@ def run_ours(args):
         except Exception as exc:            # reported in the line, never fatal to it
             derivs = {"error": f"{type(exc).__name__}: {exc}"}
 
+    # ---- g g -> t tbar g g g (the five-gluon process)
+    ttggg = None
+    if not args.no_configs:
+        try:
+            ttggg = run_ttggg(pdf, IN, MF_FP64, MF_MIXED, stream, args.ttggg_events, fma32)
+        except Exception as exc:            # reported in the line, never fatal to it
+            ttggg = {"error": f"{type(exc).__name__}: {exc}"}
+
+    # ---- helicity profile measurement and the filtered light-quark passes
+    helicity = None
+    if not args.no_configs:
+        try:
+            helicity = run_helicity(pdf, IN, MF_FP64, MF_MIXED, stream)
+        except Exception as exc:            # reported in the line, never fatal to it
+            helicity = {"error": f"{type(exc).__name__}: {exc}"}
+
     # ---- FP64 CPU oracle on the host cores (bounded sample)
     cpu = None
     if not args.no_cpu:
@@ -610,6 +743,10 @@ def run_ours(args):
         line["per_config"] = per_config
     if derivs:
         line["derivatives"] = derivs
+    if helicity:
+        line["helicity"] = helicity
+    if ttggg:
+        line["gg_ttggg"] = ttggg
     print(json.dumps(line), flush=True)
     if world > 1:
         import torch.distributed as dist

@@ -43,8 +43,12 @@ extern "C" {
  *   MF_UU_TT    u(1) ubar(2) -> t(3) tbar(4)
  *   MF_GG_TTG   g(1) g(2) -> t(3) tbar(4) g(5)
  *   MF_UG_TTU   u(1) g(2) -> t(3) tbar(4) u(5)
- *   MF_GG_TTGG  g(1) g(2) -> t(3) tbar(4) g(5) g(6)                          */
-enum mf_process { MF_EE_MUMU = 0, MF_GG_TT = 1, MF_UU_TT = 2, MF_GG_TTG = 3, MF_UG_TTU = 4, MF_GG_TTGG = 5 };
+ *   MF_GG_TTGG  g(1) g(2) -> t(3) tbar(4) g(5) g(6)
+ *   MF_GG_TTGGG g(1) g(2) -> t(3) tbar(4) g(5) g(6) g(7)  (the multi-leg
+ *               extension of Sec. 4: its matrix element is a warp-level
+ *               Berends-Giele recursion; no derivatives, not in batches)      */
+enum mf_process { MF_EE_MUMU = 0, MF_GG_TT = 1, MF_UU_TT = 2, MF_GG_TTG = 3, MF_UG_TTU = 4, MF_GG_TTGG = 5,
+                  MF_GG_TTGGG = 6 };
 
 /* Arithmetic of the matrix element: MF_FP64 everywhere in FP64; MF_MIXED
  * evaluates wavefunctions, vertices and the colour sum in FP32 and keeps
@@ -97,7 +101,8 @@ typedef struct mf_result {
 } mf_result;
 
 /* Fiducial cuts on the final light partons (Sec. 1: phase space with cuts):
- * pT > pt_min [GeV], |eta| < eta_max, Delta R between light partons > dr_min.
+ * pT > pt_min [GeV], |eta| < eta_max, Delta R between every pair of final
+ * gluons > dr_min.
  * A value <= 0 (or an infinite eta_max) disables that cut. */
 typedef struct mf_cuts {
     double pt_min, eta_max, dr_min;
@@ -258,7 +263,7 @@ int mf_vegas_pass(struct mf_ctx *ctx, int process, double sqrt_s, const double *
  * written by mf_vegas_pass (several ranks' sums may be combined first: the
  * refinement depends only on the shape of each dimension's histogram),
  * grid_dev [dim][n_bins+1] updated in place; a dimension whose histogram is
- * all zero keeps its edges.  dim <= 18, 2 <= n_bins <= 64, alpha >= 0.
+ * all zero keeps its edges.  dim <= 22, 2 <= n_bins <= 64, alpha >= 0.
  * Does not synchronise. */
 int mf_vegas_refine(struct mf_ctx *ctx, int dim, int n_bins, double alpha, const double *sums_dev, double *grid_dev);
 
@@ -316,6 +321,20 @@ int mf_vegas_pass_grad(struct mf_ctx *ctx, int process, double sqrt_s, const dou
  * Device pointers, caller-owned.  Does not synchronise. */
 int mf_evaluate(struct mf_ctx *ctx, int process, const double *momenta_dev, long long n, double *me2_dev,
                 double *dme2_dp_dev);
+
+/* Helicity profile (the measurement behind the helicity filtering; the
+ * paper's generated matrix element sums helicities in a loop, Sec. 2.2):
+ * for n phase-space points momenta_dev [n][n_ext][4] (as mf_evaluate), out_dev
+ * [n][2^n_ext] receives the averaged |M_h|^2 of every helicity configuration
+ * h (bit i of h: helicity of external particle i, set = +1), so that each row
+ * adds up to mf_evaluate's |M|^2.  The configurations that helicity
+ * conservation on a massless fermion line forbids come out exactly zero; the
+ * integrand and mf_evaluate skip them (e+ e- -> mu+ mu-: 12 of 16, u ubar ->
+ * t tbar: 8 of 16, u g -> t tbar u: 16 of 32).  For the gluon processes
+ * the parity mirror h ^ (2^n_ext - 1) has the same value (the integrand
+ * evaluates one of each pair and doubles it).  In the context's precision;
+ * device pointers, caller-owned; n = 0 is a no-op.  Does not synchronise. */
+int mf_helicity_profile(struct mf_ctx *ctx, int process, const double *momenta_dev, long long n, double *out_dev);
 
 /* Batched channels: several partonic subprocesses of one hadronic process
  * (p p -> t tbar + jets), each integrated on its own VEGAS grid, the sum

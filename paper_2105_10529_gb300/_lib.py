@@ -11,7 +11,7 @@ import os
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmadflow_gb300.so")
 
-MF_EE_MUMU, MF_GG_TT, MF_UU_TT, MF_GG_TTG, MF_UG_TTU, MF_GG_TTGG = 0, 1, 2, 3, 4, 5
+MF_EE_MUMU, MF_GG_TT, MF_UU_TT, MF_GG_TTG, MF_UG_TTU, MF_GG_TTGG, MF_GG_TTGGG = 0, 1, 2, 3, 4, 5, 6
 MF_FP64, MF_MIXED = 0, 1
 STATUS = {0: "MF_OK", 1: "MF_ERR_ARG", 2: "MF_ERR_CUDA", 3: "MF_ERR_TIMEOUT", 4: "MF_ERR_NUMERIC",
           5: "MF_ERR_UNSUPPORTED"}
@@ -84,6 +84,7 @@ def lib():
                                         C.POINTER(MfEventArrays)]),
             "mf_vegas_refine": (C.c_int, [vp, C.c_int, C.c_int, C.c_double, vp, vp]),
             "mf_evaluate": (C.c_int, [vp, C.c_int, vp, i64, vp, vp]),
+            "mf_helicity_profile": (C.c_int, [vp, C.c_int, vp, i64, vp]),
             "mf_set_couplings": (C.c_int, [vp, C.c_double, C.c_double]),
             "mf_vegas_pass_grad": (C.c_int, [vp, C.c_int, C.c_double, vp, i64, i64, C.c_uint, vp, vp]),
             "mf_vegas_pass_static": (C.c_int, [C.c_int, C.POINTER(MfConfig), C.c_double, vp, C.c_int, C.c_int, C.c_int,
@@ -110,7 +111,7 @@ def lib():
 
 def exported_symbols():
     return ["mf_default_config", "mf_process_info", "mf_create", "mf_destroy", "mf_last_error",
-            "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_set_helicity_split", "mf_set_observable", "mf_get_observable", "mf_device_status", "mf_selftest_wait", "mf_integrate", "mf_integrate_grid", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate",
+            "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_set_helicity_split", "mf_set_observable", "mf_get_observable", "mf_device_status", "mf_selftest_wait", "mf_integrate", "mf_integrate_grid", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate", "mf_helicity_profile",
             "mf_vegas_pass_static", "mf_set_couplings", "mf_vegas_pass_grad",
             "mf_integrate_batch", "mf_batch_pass", "mf_batch_grad", "mf_set_batch_schedule", "mf_autotune_batch",
             "mf_measure_fma_peak"]

@@ -308,6 +308,16 @@ class Context:
         _check(self.ptr, rc)
         return me, dme
 
+    def helicity_profile(self, process: int, momenta):
+        """Per-helicity averaged |M_h|^2 [n, 2^n_ext] of momenta [n, n_ext, 4] (mf_helicity_profile)."""
+        torch = _torch()
+        mom = momenta.to(dtype=torch.float64).contiguous()
+        n, n_ext = mom.shape[0], mom.shape[1]
+        out = torch.empty((n, 1 << n_ext), dtype=torch.float64, device=mom.device)
+        rc = _lib.lib().mf_helicity_profile(self.ptr, process, C.c_void_p(mom.data_ptr()), n, C.c_void_p(out.data_ptr()))
+        _check(self.ptr, rc)
+        return out
+
     def evaluate(self, process: int, momenta):
         """Averaged |M|^2 of momenta [n, n_ext, 4] (float64, on the device)."""
         torch = _torch()

@@ -40,6 +40,10 @@ struct Me_gg_ttg {
                                                 typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot,
                                                 void* cta = nullptr, int hpart = 0, int hparts = 1);
   template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }
+  // per-helicity averaged |M_h|^2 of all NHEL configurations into out[NHEL] (diagnostic)
+  template <typename R>
+  __device__ static void hel_profile(const typename Widen<R>::type (&p)[NEXT][4], typename Widen<R>::type mt,
+                                     typename Widen<R>::type gs, double* out);
 };
 
 // one helicity configuration: amplitudes, colour flows and (CSUM) the colour sum;
@@ -249,5 +253,80 @@ __device__ typename Widen<R>::type Me_gg_ttg::me2(const typename Widen<R>::type 
     typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta, int hpart, int hparts)
 {
     return me2_gg_ttg_impl<R, SYNC, TC>(&p[0][0], mt, gs, slot, cta, hpart, hparts);
+}
+
+// the prologue of me2 alone: the event's helicity-independent pieces into v
+template <typename R>
+__device__ __forceinline__ void inv_gg_ttg(const typename Widen<R>::type* pflat, typename Widen<R>::type mt,
+                                       Me_gg_ttg::Inv<R>& v)
+{
+    using S = typename Widen<R>::type;
+    constexpr int NEXT = Me_gg_ttg::NEXT;
+    S p[NEXT][4];
+    for (int i = 0; i < NEXT; ++i)
+        for (int c = 0; c < 4; ++c) p[i][c] = pflat[4 * i + c];
+    // gluon momenta, incoming convention: gluons 0,1 incoming, the rest outgoing
+    const S kd1[4] = {p[0][0], p[0][1], p[0][2], p[0][3]};
+    const S kd2[4] = {p[1][0], p[1][1], p[1][2], p[1][3]};
+    const S kd4[4] = {-p[4][0], -p[4][1], -p[4][2], -p[4][3]};
+    const S kd3[4] = {kd1[0] + kd2[0], kd1[1] + kd2[1], kd1[2] + kd2[2], kd1[3] + kd2[3]};
+    const S kd5[4] = {kd1[0] + kd4[0], kd1[1] + kd4[1], kd1[2] + kd4[2], kd1[3] + kd4[3]};
+    const S kd6[4] = {kd2[0] + kd4[0], kd2[1] + kd4[1], kd2[2] + kd4[2], kd2[3] + kd4[3]};
+    const S kd7[4] = {kd1[0] + kd2[0] + kd4[0], kd1[1] + kd2[1] + kd4[1], kd1[2] + kd2[2] + kd4[2], kd1[3] + kd2[3] + kd4[3]};
+    for (int c = 0; c < 4; ++c) v.K[0][c] = R(kd1[c]);
+    for (int c = 0; c < 4; ++c) v.K[1][c] = R(kd2[c]);
+    for (int c = 0; c < 4; ++c) v.K[2][c] = R(kd3[c]);
+    for (int c = 0; c < 4; ++c) v.K[3][c] = R(kd4[c]);
+    for (int c = 0; c < 4; ++c) v.K[4][c] = R(kd5[c]);
+    for (int c = 0; c < 4; ++c) v.K[5][c] = R(kd6[c]);
+    for (int c = 0; c < 4; ++c) v.K[6][c] = R(kd7[c]);
+    for (int c = 0; c < 4; ++c) v.p3[c] = R(p[2][c]);
+    v.iG[0] = R(1.0 / mdot(kd3, kd3));
+    v.iG[1] = R(1.0 / mdot(kd5, kd5));
+    v.iG[2] = R(1.0 / mdot(kd6, kd6));
+    v.iG[3] = R(1.0 / mdot(kd7, kd7));
+    { const S q[4] = {p[2][0] - kd1[0], p[2][1] - kd1[1], p[2][2] - kd1[2], p[2][3] - kd1[3]};
+      v.iQ[0] = R(1.0 / (mdot(q, q) - mt * mt)); }
+    { const S q[4] = {p[2][0] - kd2[0], p[2][1] - kd2[1], p[2][2] - kd2[2], p[2][3] - kd2[3]};
+      v.iQ[1] = R(1.0 / (mdot(q, q) - mt * mt)); }
+    { const S q[4] = {p[2][0] - kd3[0], p[2][1] - kd3[1], p[2][2] - kd3[2], p[2][3] - kd3[3]};
+      v.iQ[2] = R(1.0 / (mdot(q, q) - mt * mt)); }
+    { const S q[4] = {p[2][0] - kd4[0], p[2][1] - kd4[1], p[2][2] - kd4[2], p[2][3] - kd4[3]};
+      v.iQ[3] = R(1.0 / (mdot(q, q) - mt * mt)); }
+    { const S q[4] = {p[2][0] - kd5[0], p[2][1] - kd5[1], p[2][2] - kd5[2], p[2][3] - kd5[3]};
+      v.iQ[4] = R(1.0 / (mdot(q, q) - mt * mt)); }
+    { const S q[4] = {p[2][0] - kd6[0], p[2][1] - kd6[1], p[2][2] - kd6[2], p[2][3] - kd6[3]};
+      v.iQ[5] = R(1.0 / (mdot(q, q) - mt * mt)); }
+    { S a[3], b[3]; gluon_basis(p[0], a, b);
+      for (int j = 0; j < 3; ++j) { v.e1[0][j] = R(a[j]); v.e2[0][j] = R(b[j]); } }
+    { S a[3], b[3]; gluon_basis(p[1], a, b);
+      for (int j = 0; j < 3; ++j) { v.e1[1][j] = R(a[j]); v.e2[1][j] = R(b[j]); } }
+    { S a[3], b[3]; gluon_basis(p[4], a, b);
+      for (int j = 0; j < 3; ++j) { v.e1[2][j] = R(a[j]); v.e2[2][j] = R(b[j]); } }
+    v.fb3 = fermion_basis<R>(p[2], mt);
+    v.fb4 = fermion_basis<R>(p[3], mt);
+    v.mt = R(mt);
+}
+
+// Helicity profile: the averaged |M_h|^2 of every one of the NHEL helicity configurations
+// (ih bit i: helicity of external particle i, set = +1), parity mirrors included, so that
+// out[ih] sums to me2 and out[ih] = out[ih ^ (NHEL - 1)] tests the parity halving of me2
+template <typename R>
+__device__ void hel_profile_gg_ttg(const typename Widen<R>::type* pflat, typename Widen<R>::type mt,
+                                   typename Widen<R>::type gs, Me_gg_ttg::Inv<R>& v, double* out)
+{
+    using S = typename Widen<R>::type;
+    inv_gg_ttg<R>(pflat, mt, v);
+    S gk = S(1.0);
+    for (int i = 0; i < Me_gg_ttg::NGLUON; ++i) gk = gk * (gs * gs);
+    for (int ih = 0; ih < Me_gg_ttg::NHEL; ++ih)
+        out[ih] = val(S(hel_gg_ttg<R>(v, ih)) / Me_gg_ttg::COLOUR_DEN * gk * Me_gg_ttg::AVG * Me_gg_ttg::SYM);
+}
+template <typename R>
+__device__ void Me_gg_ttg::hel_profile(const typename Widen<R>::type (&p)[NEXT][4], typename Widen<R>::type mt,
+                                  typename Widen<R>::type gs, double* out)
+{
+    Me_gg_ttg::Inv<R> v;
+    hel_profile_gg_ttg<R>(&p[0][0], mt, gs, v, out);
 }
 }  // namespace mf

@@ -43,6 +43,10 @@ struct Me_gg_ttgg {
                                                 typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot,
                                                 void* cta = nullptr, int hpart = 0, int hparts = 1);
   template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }
+  // per-helicity averaged |M_h|^2 of all NHEL configurations into out[NHEL] (diagnostic)
+  template <typename R>
+  __device__ static void hel_profile(const typename Widen<R>::type (&p)[NEXT][4], typename Widen<R>::type mt,
+                                     typename Widen<R>::type gs, double* out);
   // warp-per-event schedule: the helicity-independent words of Inv (everything before jamp),
   // filled for one event by one thread (inv), then read by the 32 lanes of a warp, each
   // evaluating one of the 32 helicities of the parity-halved sum (hel_j, colour flows in
@@ -1454,6 +1458,28 @@ __device__ __forceinline__ void inv_gg_ttgg(const typename Widen<R>::type* pflat
     v.fb3 = fermion_basis<R>(p[2], mt);
     v.fb4 = fermion_basis<R>(p[3], mt);
     v.mt = R(mt);
+}
+
+// Helicity profile: the averaged |M_h|^2 of every one of the NHEL helicity configurations
+// (ih bit i: helicity of external particle i, set = +1), parity mirrors included, so that
+// out[ih] sums to me2 and out[ih] = out[ih ^ (NHEL - 1)] tests the parity halving of me2
+template <typename R>
+__device__ void hel_profile_gg_ttgg(const typename Widen<R>::type* pflat, typename Widen<R>::type mt,
+                                   typename Widen<R>::type gs, Me_gg_ttgg::Inv<R>& v, double* out)
+{
+    using S = typename Widen<R>::type;
+    inv_gg_ttgg<R>(pflat, mt, v);
+    S gk = S(1.0);
+    for (int i = 0; i < Me_gg_ttgg::NGLUON; ++i) gk = gk * (gs * gs);
+    for (int ih = 0; ih < Me_gg_ttgg::NHEL; ++ih)
+        out[ih] = val(S(hel_gg_ttgg<R>(v, ih)) / Me_gg_ttgg::COLOUR_DEN * gk * Me_gg_ttgg::AVG * Me_gg_ttgg::SYM);
+}
+template <typename R>
+__device__ void Me_gg_ttgg::hel_profile(const typename Widen<R>::type (&p)[NEXT][4], typename Widen<R>::type mt,
+                                  typename Widen<R>::type gs, double* out)
+{
+    Me_gg_ttgg::Inv<R> v;
+    hel_profile_gg_ttgg<R>(&p[0][0], mt, gs, v, out);
 }
 
 // one helicity's colour-flow amplitudes (the same as hel_gg_ttgg, without the colour sum);

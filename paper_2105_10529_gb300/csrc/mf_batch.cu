@@ -226,7 +226,8 @@ int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, 
     std::vector<int> order(n_ch);
     for (int i = 0; i < n_ch; ++i) {
         const ProcOps* ops = mf_proc_ops(procs[i]);
-        if (!ops || procs[i] == MF_EE_MUMU) return mf_fail(c, MF_ERR_ARG, "batch: channels must be hadronic top processes");
+        if (!ops || procs[i] == MF_EE_MUMU || procs[i] == MF_GG_TTGGG)
+            return mf_fail(c, MF_ERR_ARG, "batch: channels must be the hadronic top processes up to g g -> t tbar g g");
         if (n_events[i] < 2) return mf_fail(c, MF_ERR_ARG, "batch: every channel needs at least 2 events");
         pl.proc[i] = procs[i];
         pl.n[i] = n_events[i];
@@ -549,7 +550,7 @@ int mf_integrate_batch(mf_ctx* c, int n_ch, const int* processes, const long lon
     const int nb = c->cfg.n_bins;
     if (grids_host)
         for (int i = 0; i < n_ch; ++i)
-            MF_BCUDA(c, cudaMemcpyAsync(grids_host + (size_t)i * MAX_DIM * (nb + 1),
+            MF_BCUDA(c, cudaMemcpyAsync(grids_host + (size_t)i * BATCH_DIM * (nb + 1),
                                         c->d_bgrids + (size_t)i * MAX_DIM * (MAX_BINS + 1),
                                         sizeof(double) * pl.dim[i] * (nb + 1), cudaMemcpyDeviceToHost, c->cap_stream));
     MF_BCUDA(c, cudaStreamSynchronize(c->cap_stream));
@@ -615,7 +616,7 @@ int mf_batch_pass(mf_ctx* c, int n_ch, const int* processes, const long long* n_
     // the caller's grids into the batch grid slots, then the slot parameters and the counters
     for (int i = 0; i < n_ch; ++i)
         MF_BCUDA(c, cudaMemcpyAsync(c->d_bgrids + (size_t)i * MAX_DIM * (MAX_BINS + 1),
-                                    grids_dev + (size_t)i * MAX_DIM * (nb + 1),
+                                    grids_dev + (size_t)i * BATCH_DIM * (nb + 1),
                                     sizeof(double) * pl.dim[i] * (nb + 1), cudaMemcpyDeviceToDevice, s));
     if (!pl.slot_kp.empty())
         MF_BCUDA(c, cudaMemcpyAsync(c->d_kps, pl.slot_kp.data(), sizeof(KParams) * pl.slot_kp.size(),
@@ -624,7 +625,7 @@ int mf_batch_pass(mf_ctx* c, int n_ch, const int* processes, const long long* n_
     // one pass without refinement (statistics slot 0), random numbers of Philox iteration `iteration`
     rc = enqueue_iteration(c, pl, 0, 1, s, c->cap_low, (long long)iteration);
     if (rc) return rc;
-    const size_t row = 2 + (size_t)MAX_DIM * nb;
+    const size_t row = 2 + (size_t)BATCH_DIM * nb;
     for (int i = 0; i < n_ch; ++i)
         MF_BCUDA(c, cudaMemcpyAsync(sums_dev + (size_t)i * row, c->d_bsums + (size_t)i * (2 + MAX_DIM * MAX_BINS),
                                     sizeof(double) * (2 + (size_t)pl.dim[i] * nb), cudaMemcpyDeviceToDevice, s));

@@ -7,6 +7,9 @@
 namespace mf {
 
 constexpr int MAX_CH = 8;
+// rows per channel of the batch calls' caller-side grid and sum layouts ([n_ch][18][n_bins+1],
+// [n_ch][2 + 18 n_bins]): the largest dimension of the batch's processes (g g -> t tbar g g)
+constexpr int BATCH_DIM = 18;
 
 // The work list of one persistent launch: slots (channels) in the order
 // their tiles are handed out, most expensive events first.

@@ -123,6 +123,7 @@ const ProcOps* proc_ops(int p)
     case MF_GG_TTGG: return ops_gg_ttgg();
     case MF_UU_TT: return ops_uu_tt();
     case MF_UG_TTU: return ops_ug_ttu();
+    case MF_GG_TTGGG: return ops_gg_ttggg();
     default: return nullptr;
     }
 }
@@ -321,7 +322,7 @@ int mf_create(mf_ctx** out, const mf_config* cfg, const double* pdf_grid_host, i
         return bail(MF_ERR_CUDA);
     if (cudaMemcpy(c->d_pdf, pdf_grid_host, npdf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(MF_ERR_CUDA);
-    for (int p : { MF_EE_MUMU, MF_GG_TT, MF_GG_TTG, MF_GG_TTGG, MF_UU_TT, MF_UG_TTU }) {
+    for (int p : { MF_EE_MUMU, MF_GG_TT, MF_GG_TTG, MF_GG_TTGG, MF_UU_TT, MF_UG_TTU, MF_GG_TTGGG }) {
         const ProcOps* o = proc_ops(p);
         if (o->prepare(o->smem(1, MAX_BINS, nx * nq, true), o->smem(0, MAX_BINS, nx * nq, true)) != cudaSuccess)
             return bail(MF_ERR_CUDA);
@@ -727,6 +728,22 @@ int mf_vegas_pass_grad(mf_ctx* c, int process, double sqrt_s, const double* grid
     finish_pass_kernel<<<1, 32, 4 * sizeof(double), c->stream>>>(c->d_partials, nblk, 1, 2, n_events, 0.0, 0, nullptr,
                                                                  nullptr, out_dev);
     MF_CUDA(c, cudaGetLastError());
+    return MF_OK;
+}
+
+int mf_helicity_profile(mf_ctx* c, int process, const double* momenta_dev, long long n, double* out_dev)
+{
+    if (!c) return MF_ERR_ARG;
+    const ProcOps* ops = proc_ops(process);
+    if (!ops || !ops->profile) return fail(c, MF_ERR_ARG, "unknown process");
+    if (n == 0) return MF_OK;
+    if (!momenta_dev || !out_dev || n < 0) return fail(c, MF_ERR_ARG, "mf_helicity_profile: bad argument");
+    KParams kp;
+    int rc = make_params(c, process, ops, 1.0e4, kp);
+    if (rc) return rc;
+    const long long nb = (n + 63) / 64, cap = (long long)c->n_sm * 16;
+    const int nblk = (int)(nb < cap ? nb : cap);
+    MF_CUDA(c, ops->profile(c->cfg.precision, momenta_dev, n, out_dev, kp.mt, kp.gs, kp.ew, nblk, c->stream));
     return MF_OK;
 }
 

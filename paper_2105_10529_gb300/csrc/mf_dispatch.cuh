@@ -26,7 +26,21 @@ struct ProcOps {
                             const EwParams& ew, int nblk, cudaStream_t s);
     // the integrand kernel (function) that integrand() launches with these settings
     const void* (*kernel)(int prec, bool write, int sched, int hsplit);
+    // per-helicity |M_h|^2 of caller momenta, out [n][nhel] (helicity profile)
+    cudaError_t (*profile)(int prec, const double* mom, long long n, double* out, double mt, double gs,
+                           const EwParams& ew, int nblk, cudaStream_t s);
+    int nhel;
 };
+
+// helicity-profile launch of a matrix element with a hel_profile member
+template <class ME>
+cudaError_t profile_launch(int prec, const double* mom, long long n, double* out, double mt, double gs, const EwParams&,
+                           int nblk, cudaStream_t s)
+{
+    if (prec) helicity_profile_kernel<ME, float><<<nblk, 64, 0, s>>>(mom, n, out, mt, gs);
+    else helicity_profile_kernel<ME, double><<<nblk, 64, 0, s>>>(mom, n, out, mt, gs);
+    return cudaGetLastError();
+}
 
 // Derivative kernels of one process, built in their own translation units.
 struct GradOpsTable {
@@ -71,6 +85,7 @@ const ProcOps* ops_gg_ttg();
 const ProcOps* ops_gg_ttgg();
 const ProcOps* ops_uu_tt();
 const ProcOps* ops_ug_ttu();
+const ProcOps* ops_gg_ttggg();
 
 // integrand launch helpers for a process trait P: T32 threads per CTA for the
 // mixed-precision kernels, T64 for the FP64 ones

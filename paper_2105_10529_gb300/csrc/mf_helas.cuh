@@ -441,14 +441,16 @@ __device__ __forceinline__ void gluon_basis(const S* p, S* e1, S* e2)
 }
 
 // Helicity eigenspinors and omega_+/- of a fermion of mass m (FP64);
-// omega_- = m / omega_+ avoids the cancellation in E - |p|.
+// omega_- = m / omega_+ avoids the cancellation in E - |p|, and is exactly 0 for a
+// massless fermion (E - |p| there is rounding), so that massless spinors have exact
+// chirality and helicity-violating amplitudes vanish exactly.
 template <typename R, typename S> __device__ __forceinline__ FermionBasis<R> fermion_basis(const S* p, S m)
 {
     FermionBasis<R> f;
     const S pa = sqrt(p[1] * p[1] + p[2] * p[2] + p[3] * p[3]);
     const S ppz = pa + p[3];
     const S omp = sqrt(p[0] + pa);
-    const S omm = val(m) > 0.0 ? m / omp : sqrt(fmax(p[0] - pa, 0.0));
+    const S omm = val(m) > 0.0 ? m / omp : S(0.0);
     f.om[0] = R(omp); f.om[1] = R(omm);
     if (val(ppz) > 1e-12 * (val(pa) + 1e-300)) {
         const S n = 1.0 / sqrt(2.0 * pa * ppz);

@@ -12,6 +12,7 @@
 #pragma once
 #include <cstddef>
 #include <cstdint>
+#include <type_traits>
 #include "mf_device.cuh"
 #include "mf_helas.cuh"
 #include "mf_tc.cuh"
@@ -19,8 +20,8 @@
 namespace mf {
 
 constexpr double GEV2_TO_PB = 0.3893793721e9;   // (hbar c)^2 in pb GeV^2
-constexpr int MAX_DIM = 18;
-constexpr int KIN_NEXT_MAX = 6;      // largest process (2 -> 4) for the global kinematics store
+constexpr int MAX_DIM = 22;
+constexpr int KIN_NEXT_MAX = 7;      // largest process (2 -> 5) for the global kinematics store
 constexpr int KIN_CAP_UNIT = 256;    // ring entries per region of the global kinematics store
 constexpr int MAX_BINS = 64;
 constexpr int MAX_OBS_BINS = 100;    // observable histogram: regular bins (plus under- and overflow)
@@ -107,27 +108,63 @@ struct MeEeMumu {
         const FermionBasis<R> f1 = fermion_basis<R>(p[0], 0.0), f2 = fermion_basis<R>(p[1], 0.0);
         const FermionBasis<R> f3 = fermion_basis<R>(p[2], 0.0), f4 = fermion_basis<R>(p[3], 0.0);
         R acc = R(0);
+        // helicity filtering: the massless e- e+ (and mu- mu+) annihilate into (come from) a
+        // vector current only with opposite helicity bits, 4 of the 16 configurations
 #pragma unroll 1
-        for (int ih = 0; ih < NHEL; ++ih) {
-            const int h1 = (ih & 1) ? 1 : -1, h2 = (ih & 2) ? 1 : -1, h3 = (ih & 4) ? 1 : -1, h4 = (ih & 8) ? 1 : -1;
-            W4<R> eL, eR, mL, mR;
-            ffv_cur_lr(ext_vbar(f2, h2), ext_u(f1, h1), eL, eR);
-            ffv_cur_lr(ext_ubar(f3, h3), ext_v(f4, h4), mL, mR);
-            cx<R> amp = cmul(A[0][0], cdot(eL, mL));
-            amp = cfma(A[0][1], cdot(eL, mR), amp);
-            amp = cfma(A[1][0], cdot(eR, mL), amp);
-            amp = cfma(A[1][1], cdot(eR, mR), amp);
-            acc += amp.r * amp.r + amp.i * amp.i;
-        }
+        for (int j = 0; j < NHEL_NZ; ++j) acc += hel<R>(hel_nz(j), A, f1, f2, f3, f4);
         return 0.25 * double(acc);
+    }
+    static constexpr int NHEL_NZ = 4;
+    __host__ __device__ static constexpr int hel_nz(int j)
+    {
+        return (j & 1) | ((~j & 1) << 1) | (((j >> 1) & 1) << 2) | ((~(j >> 1) & 1) << 3);
+    }
+    // one helicity configuration (ih bit i: helicity of particle i, set = +1), unaveraged
+    template <typename R>
+    __device__ static R hel(int ih, const cx<R> (&A)[2][2], const FermionBasis<R>& f1, const FermionBasis<R>& f2,
+                            const FermionBasis<R>& f3, const FermionBasis<R>& f4)
+    {
+        const int h1 = (ih & 1) ? 1 : -1, h2 = (ih & 2) ? 1 : -1, h3 = (ih & 4) ? 1 : -1, h4 = (ih & 8) ? 1 : -1;
+        W4<R> eL, eR, mL, mR;
+        ffv_cur_lr(ext_vbar(f2, h2), ext_u(f1, h1), eL, eR);
+        ffv_cur_lr(ext_ubar(f3, h3), ext_v(f4, h4), mL, mR);
+        cx<R> amp = cmul(A[0][0], cdot(eL, mL));
+        amp = cfma(A[0][1], cdot(eL, mR), amp);
+        amp = cfma(A[1][0], cdot(eR, mL), amp);
+        amp = cfma(A[1][1], cdot(eR, mR), amp);
+        return amp.r * amp.r + amp.i * amp.i;
+    }
+    // averaged |M_h|^2 of all 16 configurations (diagnostic; the filtered ones come out zero)
+    template <typename R>
+    __device__ static void hel_profile(const double (&p)[4][4], const EwParams& ew, double* out)
+    {
+        const double s = 2.0 * mdot(p[0], p[1]);
+        const double gL = -0.5 + ew.sw2, gR = ew.sw2;
+        const double dre = s - ew.mz * ew.mz, dim = ew.mz * ew.wz;
+        const double dd = dre * dre + dim * dim;
+        const double chr = s * dre / dd / (ew.sw2 * ew.cw2), chi = -s * dim / dd / (ew.sw2 * ew.cw2);
+        const double g[2] = { gL, gR };
+        cx<R> A[2][2];
+        for (int i = 0; i < 2; ++i)
+            for (int j = 0; j < 2; ++j)
+                A[i][j] = mkc(R(ew.e2 / s * (1.0 + g[i] * g[j] * chr)), R(ew.e2 / s * g[i] * g[j] * chi));
+        const FermionBasis<R> f1 = fermion_basis<R>(p[0], 0.0), f2 = fermion_basis<R>(p[1], 0.0);
+        const FermionBasis<R> f3 = fermion_basis<R>(p[2], 0.0), f4 = fermion_basis<R>(p[3], 0.0);
+        for (int ih = 0; ih < NHEL; ++ih) out[ih] = 0.25 * double(hel<R>(ih, A, f1, f2, f3, f4));
     }
 };
 
 // ------------------------------------------------------------------ process traits
 
+// matrix elements evaluated by a whole warp per event (the Berends-Giele recursion of
+// mf_bg.cuh) declare BG = true
+template <class ME, class = void> struct MeIsBg : std::false_type {};
+template <class ME> struct MeIsBg<ME, std::void_t<decltype(ME::BG)>> : std::bool_constant<ME::BG> {};
+
 struct ProcEe {
     static constexpr int NEXT = 4, NF = 2, D = 2, NPDF = 0;
     static constexpr bool HEAVY = false;
+    static constexpr bool BG = false;
     static constexpr bool TC = false;
     static constexpr bool STORE_KIN = false;
     template <typename R> static constexpr size_t slot_bytes() { return 0; }
@@ -143,9 +180,11 @@ struct ProcTops {
     static constexpr int NLIGHT = NF - 2;
     static constexpr int NPDF = 1;             // PDFs are read from the global grid (through L1)
     static constexpr int FLAV1 = F1, FLAV2 = F2;
-    // heavy matrix elements (2 -> 3 and more with a per-thread invariant slot): queue of
-    // the events that pass the cuts, one CTA-level histogram, shared-memory slots
-    static constexpr bool HEAVY = NEXT >= 5 && ME::template slot_bytes<float>() > 0;
+    // warp-level matrix element (one warp per event, state in the warp's shared memory)
+    static constexpr bool BG = MeIsBg<ME>::value;
+    // heavy matrix elements (2 -> 3 and more with a per-thread invariant slot, or warp-level):
+    // queue of the events that pass the cuts, one CTA-level histogram, shared-memory slots
+    static constexpr bool HEAVY = NEXT >= 5 && (ME::template slot_bytes<float>() > 0 || BG);
     // the colour sum can run on the tensor cores (heavy processes with a 24-flow basis)
     static constexpr bool TC = HEAVY && ME::TC_COLOUR;
     // the kinematics of queued events are kept in shared memory (where it fits: 2 -> 3),
@@ -200,19 +239,25 @@ __device__ __forceinline__ int cuts_tops(const KParams& kp, const double (&pl)[P
         // |eta| < eta_max  <=>  p_z^2 < p_T^2 sinh^2(eta_max)
         if (kp.sinh_eta > 0.0) ok &= (q[3] * q[3] < pt2 * sh2);
     }
-    if (P::NLIGHT == 2 && kp.dr_min2 > 0.0 && ok) {
-        const double* a = pl[4];
-        const double* b = pl[P::NLIGHT == 2 ? 5 : 4];
-        const double pta2 = a[1] * a[1] + a[2] * a[2], ptb2 = b[1] * b[1] + b[2] * b[2];
-        const double pa = sqrt(pta2 + a[3] * a[3]), pb = sqrt(ptb2 + b[3] * b[3]);
-        // eta = ln((|p| + p_z) / p_T), so eta_a - eta_b in one logarithm (|p| + p_z formed
-        // as p_T^2 / (|p| - p_z) for p_z < 0, without cancellation); the azimuthal
-        // difference in (-pi, pi] from one atan2 of the transverse cross and dot products
-        const double ua = a[3] >= 0.0 ? pa + a[3] : pta2 / (pa - a[3]);
-        const double ub = b[3] >= 0.0 ? pb + b[3] : ptb2 / (pb - b[3]);
-        const double deta = log(ua * sqrt(ptb2) / (ub * sqrt(pta2)));
-        const double dphi = atan2(a[1] * b[2] - a[2] * b[1], a[1] * b[1] + a[2] * b[2]);
-        ok &= (deta * deta + dphi * dphi > kp.dr_min2);
+    // Delta R between every pair of final gluons (gluon processes with two or more)
+    if (P::NLIGHT >= 2 && kp.dr_min2 > 0.0 && ok) {
+#pragma unroll
+        for (int ia = 0; ia < P::NLIGHT; ++ia)
+#pragma unroll
+            for (int ib = ia + 1; ib < P::NLIGHT; ++ib) {
+                const double* a = pl[4 + ia];
+                const double* b = pl[4 + ib];
+                const double pta2 = a[1] * a[1] + a[2] * a[2], ptb2 = b[1] * b[1] + b[2] * b[2];
+                const double pa = sqrt(pta2 + a[3] * a[3]), pb = sqrt(ptb2 + b[3] * b[3]);
+                // eta = ln((|p| + p_z) / p_T), so eta_a - eta_b in one logarithm (|p| + p_z formed
+                // as p_T^2 / (|p| - p_z) for p_z < 0, without cancellation); the azimuthal
+                // difference in (-pi, pi] from one atan2 of the transverse cross and dot products
+                const double ua = a[3] >= 0.0 ? pa + a[3] : pta2 / (pa - a[3]);
+                const double ub = b[3] >= 0.0 ? pb + b[3] : ptb2 / (pb - b[3]);
+                const double deta = log(ua * sqrt(ptb2) / (ub * sqrt(pta2)));
+                const double dphi = atan2(a[1] * b[2] - a[2] * b[1], a[1] * b[1] + a[2] * b[2]);
+                ok &= (deta * deta + dphi * dphi > kp.dr_min2);
+            }
     }
     return ok;
 }
@@ -338,7 +383,13 @@ struct SmemLayout {
     static constexpr int LH_REC_OFF = TPB * LH_JROW * (int)sizeof(R);
     static constexpr int LH_REC_STRIDE = (int)al(P::template slot_bytes<R>());
     static constexpr size_t lh_bytes() { return LH ? al((size_t)LH_REC_OFF + (size_t)WARPS * LH_REC_STRIDE) : 0; }
-    static __host__ __device__ size_t grid_off() { return lh_bytes(); }
+    // warp-level matrix elements: the colour matrix and one state per warp at the start
+    static constexpr __host__ __device__ size_t bg_bytes()
+    {
+        if constexpr (P::BG) return al(P::Me::template cta_bytes<R>(WARPS));
+        else return 0;
+    }
+    static __host__ __device__ size_t grid_off() { return lh_bytes() + bg_bytes(); }
     static __host__ __device__ size_t pdf_off(int nb) { return al(grid_off() + sizeof(double) * D * (nb + 1)); }
     static __host__ __device__ size_t hist_off(int nb, int npv) { return al(pdf_off(nb)); }
     static __host__ __device__ size_t vbuf_off(int nb, int npv) { return al(hist_off(nb, npv) + sizeof(double) * NHIST * D * nb); }
@@ -591,6 +642,38 @@ __device__ __forceinline__ double lh_batch_me2(const KParams& kp, unsigned char*
     return (double)acc / ME::COLOUR_DEN * gk * ME::AVG * ME::SYM;
 }
 
+// |M|^2 of the batch's events for a warp-level matrix element (P::BG; every thread of the
+// CTA calls it, see integrand_heavy): the queued events' FP64 momenta go to this CTA's
+// region of kp.inv_rec (field-major), then warp w evaluates events w, w + WARPS, ...
+// with its shared-memory state.  sme: [TPB] doubles of scratch; returns this thread's
+// event's |M|^2 (meaningful where mine).
+template <class P, typename R, int TPB>
+__device__ __forceinline__ double bg_batch_me2(const KParams& kp, unsigned char* smem_raw, double* sme, int take,
+                                               bool mine, const double (&pm)[P::NEXT][4])
+{
+    using ME = typename P::Me;
+    constexpr int WARPS = TPB / 32;
+    static_assert(P::NEXT * 4 * TPB <= LH_INV_WORDS_MAX * LH_TPB / 2, "momenta fit the CTA's record region");
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    double* grec = reinterpret_cast<double*>(kp.inv_rec + (size_t)blockIdx.x * LH_INV_WORDS_MAX * LH_TPB);
+    if (mine) {
+#pragma unroll
+        for (int f = 0; f < P::NEXT * 4; ++f) grec[(size_t)f * TPB + tid] = pm[f >> 2][f & 3];
+    }
+    __syncthreads();
+    const float* cs = reinterpret_cast<const float*>(smem_raw);
+    auto& w = *reinterpret_cast<typename ME::template Warp<R>*>(smem_raw + ME::colour_bytes() +
+                                                                (size_t)warp * ME::template warp_bytes<R>());
+    for (int j = warp; j < take; j += WARPS) {
+        const double v = ME::template warp_me2<R>(w, cs, grec + j, TPB, kp.mt, false, nullptr, 0.0);
+        if (lane == 0) sme[j] = v;
+    }
+    __syncthreads();
+    const double me = sme[tid < take ? tid : 0] * ME::norm(kp.gs);
+    __syncthreads();   // sme is reused by the caller
+    return me;
+}
+
 // Heavy processes (expensive matrix elements): kinematics first, then the
 // events that pass the cuts are queued in event order and their matrix
 // elements are evaluated TPB at a time, so no lane idles through a matrix
@@ -673,6 +756,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
         tc = reinterpret_cast<TcCta*>(smem_raw + L::tc_off(nb, npv));
         tc_setup<P::Me::NCOL>(tc, P::Me::colour54(), kp.dev_err);
     }
+    if constexpr (P::BG) P::Me::load_colour(reinterpret_cast<float*>(smem_raw));
     __syncthreads();
 
     double sw = 0.0, sw2 = 0.0;
@@ -743,7 +827,10 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
                 kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
             }
             double me;
-            if constexpr (LH) {
+            if constexpr (P::BG) {
+                static_assert(HS == 1 && !LH && !TC, "warp-level matrix element: its own schedule");
+                me = bg_batch_me2<P, R, TPB>(kp, smem_raw, svbuf, take, mine, pm);
+            } else if constexpr (LH) {
                 me = lh_batch_me2<P, R, TPB>(kp, smem_raw, tc, svbuf, take, mine, pm);
             } else if constexpr (TC) {
                 me = P::Me::template me2<R, SYNC, true>(pm, kp.mt, kp.gs, slot, tc, hpart, HS);
@@ -809,7 +896,7 @@ __global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
     if constexpr (P::HEAVY) {
         constexpr int EPB = TPB / HS;   // events per CTA and round
         const long long first = (long long)blockIdx.x * EPB, step = (long long)gridDim.x * EPB;
-        if constexpr (LH) {
+        if constexpr (LH || P::BG) {
             // the host launches this schedule only with a record region for every CTA
             if (kp.inv_rec == nullptr || (int)blockIdx.x >= kp.inv_ctas) {
                 if (threadIdx.x == 0 && kp.dev_err) atomicExch(kp.dev_err, 1u);
@@ -849,6 +936,34 @@ __global__ void __launch_bounds__(128) evaluate_ee_kernel(const double* __restri
         for (int i = 0; i < 4; ++i)
             for (int c = 0; c < 4; ++c) p[i][c] = mom[(e * 4 + i) * 4 + c];
         me2[e] = MeEeMumu::me2<R>(p, ew);
+    }
+}
+
+// ------------------------------------------------------------------ helicity profile
+
+// per-helicity averaged |M_h|^2 of caller momenta: out [n][ME::NHEL] (diagnostic of the
+// helicity sum: its entries add up to evaluate's |M|^2)
+template <class ME, typename R>
+__global__ void __launch_bounds__(64) helicity_profile_kernel(const double* __restrict__ mom, long long n,
+                                                              double* __restrict__ out, double mt, double gs)
+{
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double p[ME::NEXT][4];
+        for (int i = 0; i < ME::NEXT; ++i)
+            for (int c = 0; c < 4; ++c) p[i][c] = mom[(e * ME::NEXT + i) * 4 + c];
+        ME::template hel_profile<R>(p, mt, gs, out + e * ME::NHEL);
+    }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(64) helicity_profile_ee_kernel(const double* __restrict__ mom, long long n,
+                                                                 double* __restrict__ out, EwParams ew)
+{
+    for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+        double p[4][4];
+        for (int i = 0; i < 4; ++i)
+            for (int c = 0; c < 4; ++c) p[i][c] = mom[(e * 4 + i) * 4 + c];
+        MeEeMumu::hel_profile<R>(p, ew, out + e * MeEeMumu::NHEL);
     }
 }
 

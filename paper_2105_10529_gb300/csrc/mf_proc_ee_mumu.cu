@@ -14,7 +14,16 @@ cudaError_t evaluate(int prec, const double* mom, long long n, double* me2, doub
     return cudaGetLastError();
 }
 
-const ProcOps kOps = { P::D, P::NEXT, P::NPDF, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate, &I::kernel };
+cudaError_t profile(int prec, const double* mom, long long n, double* out, double, double, const EwParams& ew, int nblk,
+                    cudaStream_t s)
+{
+    if (prec) helicity_profile_ee_kernel<float><<<nblk, 64, 0, s>>>(mom, n, out, ew);
+    else helicity_profile_ee_kernel<double><<<nblk, 64, 0, s>>>(mom, n, out, ew);
+    return cudaGetLastError();
+}
+
+const ProcOps kOps = { P::D, P::NEXT, P::NPDF, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate, &I::kernel,
+                       &profile, MeEeMumu::NHEL };
 }  // namespace
 
 const ProcOps* ops_ee_mumu() { return &kOps; }

@@ -23,7 +23,8 @@ cudaError_t evaluate(int prec, const double* mom, long long n, double* me2, doub
     return cudaGetLastError();
 }
 
-const ProcOps kOps = { P::D, P::NEXT, P::NPDF, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate, &I::kernel };
+const ProcOps kOps = { P::D, P::NEXT, P::NPDF, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate, &I::kernel,
+                         &profile_launch<Me_gg_ttg>, Me_gg_ttg::NHEL };
 }  // namespace
 
 const ProcOps* ops_gg_ttg() { return &kOps; }

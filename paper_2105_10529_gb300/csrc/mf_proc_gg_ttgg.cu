@@ -26,7 +26,8 @@ cudaError_t evaluate(int prec, const double* mom, long long n, double* me2, doub
     return cudaGetLastError();
 }
 
-const ProcOps kOps = { P::D, P::NEXT, P::NPDF, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate, &I::kernel };
+const ProcOps kOps = { P::D, P::NEXT, P::NPDF, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate, &I::kernel,
+                         &profile_launch<Me_gg_ttgg>, Me_gg_ttgg::NHEL };
 }  // namespace
 
 const ProcOps* ops_gg_ttgg() { return &kOps; }

@@ -16,7 +16,8 @@ cudaError_t evaluate(int prec, const double* mom, long long n, double* me2, doub
     return cudaGetLastError();
 }
 
-const ProcOps kOps = { P::D, P::NEXT, P::NPDF, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate, &I::kernel };
+const ProcOps kOps = { P::D, P::NEXT, P::NPDF, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate, &I::kernel,
+                         &profile_launch<Me_uu_tt>, Me_uu_tt::NHEL };
 }  // namespace
 
 const ProcOps* ops_uu_tt() { return &kOps; }

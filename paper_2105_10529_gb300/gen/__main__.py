@@ -5,7 +5,7 @@
 import os
 from fractions import Fraction
 
-from . import qcd_diagrams, qq_processes
+from . import bg_tables, qcd_diagrams, qq_processes
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(os.path.dirname(HERE), "csrc", "generated")
@@ -23,7 +23,8 @@ def write_all(out_dir: str = OUT) -> list:
     items = [(f"me_{name}.cuh", lambda k=k, name=name, sym=sym: qcd_diagrams.generate_gluon_process(k, name, sym)[0])
              for k, name, sym in PROCESSES]
     items += [("me_uu_tt.cuh", lambda: qq_processes.generate_uu_tt()[0]),
-              ("me_ug_ttu.cuh", lambda: qq_processes.generate_ug_ttu()[0])]
+              ("me_ug_ttu.cuh", lambda: qq_processes.generate_ug_ttu()[0]),
+              ("bg_gg_ttggg.cuh", lambda: bg_tables.generate(5, "gg_ttggg")[0])]
     for fname, make in items:
         src = make()
         path = os.path.join(out_dir, fname)

@@ -644,6 +644,10 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot,")
     src.append("                                                void* cta = nullptr, int hpart = 0, int hparts = 1);")
     src.append("  template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }")
+    src.append("  // per-helicity averaged |M_h|^2 of all NHEL configurations into out[NHEL] (diagnostic)")
+    src.append("  template <typename R>")
+    src.append("  __device__ static void hel_profile(const typename Widen<R>::type (&p)[NEXT][4], typename Widen<R>::type mt,")
+    src.append("                                     typename Widen<R>::type gs, double* out);")
     if tc:
         src.append("  // warp-per-event schedule: the helicity-independent words of Inv (everything before jamp),")
         src.append("  // filled for one event by one thread (inv), then read by the 32 lanes of a warp, each")
@@ -721,21 +725,43 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("{")
     src.append(f"    return me2_{name}_impl<R, SYNC, TC>(&p[0][0], mt, gs, slot, cta, hpart, hparts);")
     src.append("}")
+    src.append("")
+    src.append("// the prologue of me2 alone: the event's helicity-independent pieces into v")
+    src.append("template <typename R>")
+    src.append(f"__device__ __forceinline__ void inv_{name}(const typename Widen<R>::type* pflat, typename Widen<R>::type mt,")
+    src.append(f"                                       Me_{name}::Inv<R>& v)")
+    src.append("{")
+    src.append("    using S = typename Widen<R>::type;")
+    src.append(f"    constexpr int NEXT = Me_{name}::NEXT;")
+    src.append("    S p[NEXT][4];")
+    src.append("    for (int i = 0; i < NEXT; ++i)")
+    src.append("        for (int c = 0; c < 4; ++c) p[i][c] = pflat[4 * i + c];")
+    for l in pro:
+        src.append("    " + l)
+    src.append("}")
+    src.append("")
+    src.append("// Helicity profile: the averaged |M_h|^2 of every one of the NHEL helicity configurations")
+    src.append("// (ih bit i: helicity of external particle i, set = +1), parity mirrors included, so that")
+    src.append("// out[ih] sums to me2 and out[ih] = out[ih ^ (NHEL - 1)] tests the parity halving of me2")
+    src.append("template <typename R>")
+    src.append(f"__device__ void hel_profile_{name}(const typename Widen<R>::type* pflat, typename Widen<R>::type mt,")
+    src.append(f"                                   typename Widen<R>::type gs, Me_{name}::Inv<R>& v, double* out)")
+    src.append("{")
+    src.append("    using S = typename Widen<R>::type;")
+    src.append(f"    inv_{name}<R>(pflat, mt, v);")
+    src.append("    S gk = S(1.0);")
+    src.append(f"    for (int i = 0; i < Me_{name}::NGLUON; ++i) gk = gk * (gs * gs);")
+    src.append(f"    for (int ih = 0; ih < Me_{name}::NHEL; ++ih)")
+    src.append(f"        out[ih] = val(S(hel_{name}<R>(v, ih)) / Me_{name}::COLOUR_DEN * gk * Me_{name}::AVG * Me_{name}::SYM);")
+    src.append("}")
+    src.append("template <typename R>")
+    src.append(f"__device__ void Me_{name}::hel_profile(const typename Widen<R>::type (&p)[NEXT][4], typename Widen<R>::type mt,")
+    src.append("                                  typename Widen<R>::type gs, double* out)")
+    src.append("{")
+    src.append(f"    Me_{name}::Inv<R> v;")
+    src.append(f"    hel_profile_{name}<R>(&p[0][0], mt, gs, v, out);")
+    src.append("}")
     if tc:
-        src.append("")
-        src.append("// the prologue of me2 alone: the event's helicity-independent pieces into v")
-        src.append("template <typename R>")
-        src.append(f"__device__ __forceinline__ void inv_{name}(const typename Widen<R>::type* pflat, typename Widen<R>::type mt,")
-        src.append(f"                                       Me_{name}::Inv<R>& v)")
-        src.append("{")
-        src.append("    using S = typename Widen<R>::type;")
-        src.append(f"    constexpr int NEXT = Me_{name}::NEXT;")
-        src.append("    S p[NEXT][4];")
-        src.append("    for (int i = 0; i < NEXT; ++i)")
-        src.append("        for (int c = 0; c < 4; ++c) p[i][c] = pflat[4 * i + c];")
-        for l in pro:
-            src.append("    " + l)
-        src.append("}")
         src.append("")
         src.append("// one helicity's colour-flow amplitudes (the same as hel_" + name + ", without the colour sum);")
         src.append("// the record and the colour-flow row sit at fixed offsets of dynamic shared memory, so that")

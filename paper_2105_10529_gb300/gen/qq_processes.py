@@ -79,11 +79,16 @@ namespace mf {
 
 
 def _struct(name: str, n_ext: int, n_hel: int, avg: str, k: int, prologue: List[str], body: List[str],
-            csum: List[str], comment: str) -> str:
+            csum: List[str], comment: str, hel_map: str, n_hel_nz: int) -> str:
+    """hel_map: C expression of the j-th helicity configuration (0 <= j < n_hel_nz) that helicity
+    conservation on the massless quark lines allows; the others vanish identically (exactly, with
+    the massless spinors' zero components) and are skipped."""
     s = [f"// {comment}"]
     s.append(f"struct Me_{name} {{")
     s.append(f"  static constexpr int NEXT = {n_ext};")
     s.append(f"  static constexpr int NHEL = {n_hel};")
+    s.append(f"  static constexpr int NHEL_NZ = {n_hel_nz};   // configurations allowed by helicity conservation")
+    s.append(f"  __host__ __device__ static constexpr int hel_nz(int j) {{ return {hel_map}; }}")
     s.append(f"  static constexpr int NGS = {k};   // powers of g in the amplitude")
     s.append(f"  static constexpr double AVG = {avg};")
     s.append("  static constexpr bool TC_COLOUR = false;")
@@ -99,8 +104,10 @@ def _struct(name: str, n_ext: int, n_hel: int, avg: str, k: int, prologue: List[
     for l in prologue:
         s.append("    " + l)
     s.append("    R acc = R(0);")
+    s.append("    // helicity filtering: only the configurations helicity conservation allows")
     s.append("#pragma unroll 1")
-    s.append("    for (int ih = 0; ih < NHEL; ++ih) {")
+    s.append("    for (int jh = 0; jh < NHEL_NZ; ++jh) {")
+    s.append("      const int ih = hel_nz(jh);")
     s.append("#define HEL(i) ((ih >> (i)) & 1 ? 1 : -1)")
     for l in body + csum:
         s.append("      " + l)
@@ -110,6 +117,25 @@ def _struct(name: str, n_ext: int, n_hel: int, avg: str, k: int, prologue: List[
     s.append("    S gk = S(1.0);")
     s.append("    for (int i = 0; i < NGS; ++i) gk = gk * gs;")
     s.append("    return S(acc) * gk * gk * AVG;")
+    s.append("  }")
+    s.append("  // Helicity profile: the averaged |M_h|^2 of every configuration ih (bit i: helicity of")
+    s.append("  // external particle i, set = +1), the filtered ones included (they come out zero)")
+    s.append("  template <typename R>")
+    s.append("  __device__ static void hel_profile(const typename Widen<R>::type (&p)[NEXT][4], typename Widen<R>::type mt,")
+    s.append("                                     typename Widen<R>::type gs, double* out)")
+    s.append("  {")
+    s.append("    using S = typename Widen<R>::type;")
+    for l in prologue:
+        s.append("    " + l)
+    s.append("    S gk = S(1.0);")
+    s.append("    for (int i = 0; i < NGS; ++i) gk = gk * gs;")
+    s.append("    for (int ih = 0; ih < NHEL; ++ih) {")
+    s.append("#define HEL(i) ((ih >> (i)) & 1 ? 1 : -1)")
+    for l in body + csum:
+        s.append("      " + l)
+    s.append("      out[ih] = val(S(me) * gk * gk * AVG);")
+    s.append("#undef HEL")
+    s.append("    }")
     s.append("  }")
     s.append("};")
     return "\n".join(s) + "\n"
@@ -129,8 +155,12 @@ def generate_uu_tt() -> Tuple[str, dict]:
         "const cx<R> a1 = ffv_amp(ext_ubar(f3, HEL(2)), ext_v(f4, HEL(3)), ju);",
     ]
     csum = _emit_colour_sum(Cm, ["a1"])
+    # the massless u and ubar annihilate into a vector current only with opposite helicity bits
+    # (u(+) is right-handed and pairs with vbar(-)): bit 1 = not bit 0
+    hel_map = "(j & 1) | ((~j & 1) << 1) | ((j >> 1) << 2)"
     src = HEADER + _struct("uu_tt", 4, 16, "1.0 / 36.0", 2, pro, body, csum,
-                           "u ubar -> t tbar: 1 diagram, colour factor (T^c)(T^c), 16 helicities") + "}  // namespace mf\n"
+                           "u ubar -> t tbar: 1 diagram, colour factor (T^c)(T^c), 16 helicities, 8 allowed",
+                           hel_map, 8) + "}  // namespace mf\n"
     return src, dict(n_diag=1, colour=Cm)
 
 
@@ -177,6 +207,9 @@ def generate_ug_ttu() -> Tuple[str, dict]:
         "const cx<R> a5 = vvv_amp(ju, g2, jt, KA, KB, KC);",
     ]
     csum = _emit_colour_sum(C, ["a1", "a2", "a3", "a4", "a5"])
+    # the massless u line keeps its helicity from p1 to p5: bit 4 = bit 0
+    hel_map = "(j & 15) | ((j & 1) << 4)"
     src = HEADER + _struct("ug_ttu", 5, 32, "1.0 / 96.0", 3, pro, body, csum,
-                           "u g -> t tbar u: 5 diagrams, diagram colour basis, 32 helicities") + "}  // namespace mf\n"
+                           "u g -> t tbar u: 5 diagrams, diagram colour basis, 32 helicities, 16 allowed",
+                           hel_map, 16) + "}  // namespace mf\n"
     return src, dict(n_diag=5, colour=C)

@@ -40,6 +40,7 @@ def test_default_config_and_process_info_without_gpu():
     assert process_info(_lib.MF_EE_MUMU) == (4, 2)
     assert process_info(_lib.MF_UU_TT) == (4, 10)
     assert process_info(_lib.MF_UG_TTU) == (5, 14)
+    assert process_info(_lib.MF_GG_TTGGG) == (7, 22)
     with pytest.raises(_lib.MfError):
         process_info(17)
 

@@ -90,7 +90,7 @@ def test_integrate_grid_resumes_the_pass_and_refine_loop(proc, prec, n, pdf_grid
     ref = np.array(per[W:])
     assert np.allclose(r["per_iter"], ref, rtol=1e-13, atol=0)
     assert np.array_equal(r["grid"], grid.cpu().numpy())
-    u = np.linspace(0, 1, nb + 1)[None, :].repeat(dim, 0)
+    u = (np.arange(nb + 1) / nb)[None, :].repeat(dim, 0)    # the uniform grid as the library forms it, i / n_bins
     a = ctx.integrate_grid(proc, phys.sqrt_s, n, K, u, first_iteration=0)
     b = ctx.integrate(proc, phys.sqrt_s, n, K, want_grid=True)
     assert a["sigma"] == b["sigma"] and np.array_equal(a["grid"], b["grid"])
