@@ -178,8 +178,9 @@ def fp64_event_bounds(proc, phys, opdf, ref):
     conditioning of each event (64 eps times the condition numbers, and never
     below 1e-12):
       |M|^2 : 64 eps me_condition;
-      w     : that, plus the weight factor's 64 eps sum_i pdf_condition(x_i) (1 + |ln x_i|)
-              and the RAMBO map's 8 gamma^2 eps.
+      w     : that, plus the weight factor's 64 eps sum_i pdf_condition(x_i) (1 + |ln tau|)
+              (ln x_i = v ln tau carries an absolute rounding of order eps |ln tau|,
+              tau = x1 x2) and the RAMBO map's 8 gamma^2 eps.
     Returns (bound_me2 [n], bound_w [n])."""
     n = len(ref["w"])
     b_me = np.empty(n); b_w = np.empty(n)
@@ -198,8 +199,8 @@ def fp64_event_bounds(proc, phys, opdf, ref):
                          for i in range(2, p.shape[0]))
                 q2 = 0.25 * ht * ht
             f1, f2 = _FLAV[proc]
-            bw += 64 * EPS * (pdf_condition(opdf, f1, x1, q2) * (1 + abs(math.log(x1)))
-                              + pdf_condition(opdf, f2, x2, q2) * (1 + abs(math.log(x2))))
+            ltau = 1 + abs(math.log(x1 * x2))
+            bw += 64 * EPS * ltau * (pdf_condition(opdf, f1, x1, q2) + pdf_condition(opdf, f2, x2, q2))
         b_w[e] = max(1e-12, bw)
     return b_me, b_w
 
