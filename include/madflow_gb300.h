@@ -316,9 +316,16 @@ int mf_vegas_pass_grad(struct mf_ctx *ctx, int process, double sqrt_s, const dou
  * (E, px, py, pz), incoming first; me2_dev: [n] (nullable when dme2_dp_dev
  * is given).  dme2_dp_dev (nullable): [n][n_ext][4] derivatives of |M|^2 with
  * respect to every momentum component, the components taken as independent
- * variables (forward mode, one tangent per component; top-pair processes
- * only, g g -> t tbar g g in MF_MIXED only, MF_ERR_UNSUPPORTED otherwise).
- * Device pointers, caller-owned.  Does not synchronise. */
+ * variables of the library's formula (top-pair processes only,
+ * MF_ERR_UNSUPPORTED otherwise).  For the gluon processes (g g -> t tbar plus
+ * 0 to 3 gluons, FP64 and MF_MIXED) a reverse sweep of the Berends-Giele
+ * recursion: per helicity the currents are recomputed, the adjoints run
+ * back through the colour sum, the closures, the recursion and the external
+ * states, and one tangent per component through the per-event invariants
+ * contracts them; me2_dev then holds that recursion's |M|^2 (equal to the
+ * value path's on shell, to rounding).  For u ubar -> t tbar and u g -> t
+ * tbar u one forward tangent per component.  Device pointers, caller-owned.
+ * Does not synchronise. */
 int mf_evaluate(struct mf_ctx *ctx, int process, const double *momenta_dev, long long n, double *me2_dev,
                 double *dme2_dp_dev);
 

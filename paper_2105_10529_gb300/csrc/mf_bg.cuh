@@ -144,4 +144,610 @@ __device__ __forceinline__ void bg_top_current(W& w, int c, int uoff, const uint
     w.U[uoff + c] = row_qprop(acc, q, w.mt, -w.iQ[msk]);
 }
 
+
+// ------------------------------------------------------------------ adjoints (reverse sweep)
+//
+// For a complex intermediate z the adjoint is zb = dL/dRe z + i dL/dIm z, L the real
+// colour- and helicity-summed |M|^2.  A holomorphic multilinear map w(x, y, ..)
+// passes xb += conj(dw/dx) wb; a real parameter s of w = s z gets
+// sb += Re(wb conj(z)).  Adjoints that several lanes add to (the currents of lower
+// levels, the per-event invariants) are accumulated with shared-memory atomics.
+
+template <typename R, int K, int NJ, int NU>
+struct BgAdj {
+    W4<R> Jb[NJ];                      // adjoints of the gluon currents (helicity being summed)
+    W4<R> Ub[NU];                      // adjoints of the top-line currents
+    W4<R> Vb;                          // adjoint of v(p_tbar)
+    // adjoints of the per-event invariants, summed over helicities
+    R Pb[1 << K][4], iP2b[1 << K], Qb[1 << K][4], iQb[1 << K];
+    R e1b[K][3], e2b[K][3];
+    cx<R> chi3b[2][2], chi4b[2][2];
+    R om3b[2], om4b[2];
+    R mtb;
+};
+
+template <typename R> __device__ __forceinline__ void atomic_add_cx(cx<R>* d, cx<R> v)
+{
+    atomicAdd(&d->r, v.r);
+    atomicAdd(&d->i, v.i);
+}
+template <typename R> __device__ __forceinline__ void atomic_add_w4(W4<R>& d, const W4<R>& v)
+{
+    for (int m = 0; m < 4; ++m) atomic_add_cx(&d.c[m], v.c[m]);
+}
+template <typename R> __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b)   // a conj(b)
+{
+    return mkc(a.r * b.r + a.i * b.i, a.i * b.r - a.r * b.i);
+}
+template <typename R> __device__ __forceinline__ R re_mulc(cx<R> a, cx<R> b)      // Re(a conj(b))
+{
+    return a.r * b.r + a.i * b.i;
+}
+__device__ __forceinline__ float metric(int mu) { return mu == 0 ? 1.0f : -1.0f; }
+
+// adjoint of vvv_cur(J1, J2, k1, k2, s) given ob: J1b, J2b (accumulated, per call), k1b, k2b
+template <typename R>
+__device__ __forceinline__ void vvv_cur_adj(const W4<R>& J1, const W4<R>& J2, const R* k1, const R* k2, R s,
+                                            const W4<R>& ob, W4<R>& J1b, W4<R>& J2b, R* k1b, R* k2b)
+{
+    R a[4], b[4], c[4];
+    for (int m = 0; m < 4; ++m) {
+        a[m] = k1[m] - k2[m];
+        b[m] = k1[m] + R(2) * k2[m];
+        c[m] = -(R(2) * k1[m] + k2[m]);
+    }
+    const cx<R> j12 = cdot(J1, J2), bj1 = rdot(b, J1), cj2 = rdot(c, J2);
+    cx<R> j12b = mkc(R(0), R(0)), bj1b = mkc(R(0), R(0)), cj2b = mkc(R(0), R(0));
+    for (int m = 0; m < 4; ++m) {
+        const cx<R> o = cscale(ob.c[m], s);
+        j12b = mkc(j12b.r + o.r * a[m], j12b.i + o.i * a[m]);
+        bj1b = cadd(bj1b, cmulc(o, J2.c[m]));
+        cj2b = cadd(cj2b, cmulc(o, J1.c[m]));
+        J2b.c[m] = cadd(J2b.c[m], cmulc(o, bj1));
+        J1b.c[m] = cadd(J1b.c[m], cmulc(o, cj2));
+        const R ab = re_mulc(o, j12);
+        k1b[m] += ab;
+        k2b[m] -= ab;
+    }
+    for (int m = 0; m < 4; ++m) {
+        const R eta = R(metric(m));
+        J1b.c[m] = cadd(J1b.c[m], cscale(cmulc(j12b, J2.c[m]), eta));
+        J2b.c[m] = cadd(J2b.c[m], cscale(cmulc(j12b, J1.c[m]), eta));
+        J1b.c[m] = cadd(J1b.c[m], cscale(bj1b, eta * b[m]));
+        J2b.c[m] = cadd(J2b.c[m], cscale(cj2b, eta * c[m]));
+        const R bb = eta * re_mulc(bj1b, J1.c[m]), cb = eta * re_mulc(cj2b, J2.c[m]);
+        k1b[m] += bb - R(2) * cb;
+        k2b[m] += R(2) * bb - cb;
+    }
+}
+
+// adjoint of v4_add(acc, J1, J2, J3, s) given ab (the adjoint of acc)
+template <typename R>
+__device__ __forceinline__ void v4_adj(const W4<R>& J1, const W4<R>& J2, const W4<R>& J3, R s, const W4<R>& ab,
+                                       W4<R>& J1b, W4<R>& J2b, W4<R>& J3b)
+{
+    const cx<R> d13 = cdot(J1, J3), d12 = cdot(J1, J2), d23 = cdot(J2, J3);
+    cx<R> d13b = mkc(R(0), R(0)), d12b = mkc(R(0), R(0)), d23b = mkc(R(0), R(0));
+    for (int m = 0; m < 4; ++m) {
+        d13b = cadd(d13b, cscale(cmulc(ab.c[m], J2.c[m]), R(2) * s));
+        d12b = cadd(d12b, cscale(cmulc(ab.c[m], J3.c[m]), -s));
+        d23b = cadd(d23b, cscale(cmulc(ab.c[m], J1.c[m]), -s));
+        J2b.c[m] = cadd(J2b.c[m], cscale(cmulc(ab.c[m], d13), R(2) * s));
+        J3b.c[m] = cadd(J3b.c[m], cscale(cmulc(ab.c[m], d12), -s));
+        J1b.c[m] = cadd(J1b.c[m], cscale(cmulc(ab.c[m], d23), -s));
+    }
+    for (int m = 0; m < 4; ++m) {
+        const R eta = R(metric(m));
+        J1b.c[m] = cadd(J1b.c[m], cscale(cadd(cmulc(d13b, J3.c[m]), cmulc(d12b, J2.c[m])), eta));
+        J3b.c[m] = cadd(J3b.c[m], cscale(cadd(cmulc(d13b, J1.c[m]), cmulc(d23b, J2.c[m])), eta));
+        J2b.c[m] = cadd(J2b.c[m], cscale(cadd(cmulc(d12b, J1.c[m]), cmulc(d23b, J3.c[m])), eta));
+    }
+}
+
+// adjoint of o = row_jslash(u, J) given ob: ub and Jb accumulated
+template <typename R>
+__device__ __forceinline__ void row_jslash_adj(const W4<R>& u, const W4<R>& J, const W4<R>& ob, W4<R>& ub, W4<R>& Jb)
+{
+    const M2<R> S = sig(J), Sb = sigbar(J);
+    // o_left = u_right Sigmabar, o_right = u_left Sigma (row times matrix, o_c = sum_r u_r M_rc)
+    ub.c[2] = cadd(ub.c[2], cadd(cmulc(ob.c[0], Sb.m00), cmulc(ob.c[1], Sb.m01)));
+    ub.c[3] = cadd(ub.c[3], cadd(cmulc(ob.c[0], Sb.m10), cmulc(ob.c[1], Sb.m11)));
+    ub.c[0] = cadd(ub.c[0], cadd(cmulc(ob.c[2], S.m00), cmulc(ob.c[3], S.m01)));
+    ub.c[1] = cadd(ub.c[1], cadd(cmulc(ob.c[2], S.m10), cmulc(ob.c[3], S.m11)));
+    // adjoints of the matrix entries
+    const cx<R> bb00 = cmulc(ob.c[0], u.c[2]), bb01 = cmulc(ob.c[1], u.c[2]);
+    const cx<R> bb10 = cmulc(ob.c[0], u.c[3]), bb11 = cmulc(ob.c[1], u.c[3]);
+    const cx<R> ss00 = cmulc(ob.c[2], u.c[0]), ss01 = cmulc(ob.c[3], u.c[0]);
+    const cx<R> ss10 = cmulc(ob.c[2], u.c[1]), ss11 = cmulc(ob.c[3], u.c[1]);
+    // Sigma: m00 = J0 - J3, m11 = J0 + J3, m01 = -J1 + i J2, m10 = -J1 - i J2;
+    // Sigmabar: m00 = J0 + J3, m11 = J0 - J3, m01 = J1 - i J2, m10 = J1 + i J2
+    Jb.c[0] = cadd(Jb.c[0], cadd(cadd(ss00, ss11), cadd(bb00, bb11)));
+    Jb.c[3] = cadd(Jb.c[3], cadd(csub(ss11, ss00), csub(bb00, bb11)));
+    Jb.c[1] = cadd(Jb.c[1], csub(cadd(bb01, bb10), cadd(ss01, ss10)));
+    // J2: conj(i) ss01 + conj(-i) ss10 + conj(-i) bb01 + conj(i) bb10 = -i (ss01 - ss10 - bb01 + bb10)
+    const cx<R> t = cadd(csub(ss01, ss10), csub(bb10, bb01));
+    Jb.c[2] = cadd(Jb.c[2], mkc(t.i, -t.r));
+}
+
+// adjoint of o = row_qprop(x, q, m, s) given ob: xb (accumulated), qb, mb, sb
+template <typename R>
+__device__ __forceinline__ void row_qprop_adj(const W4<R>& x, const R* q, R m, R s, const W4<R>& ob, W4<R>& xb,
+                                              R* qb, R& mb, R& sb)
+{
+    // inner = o / s: (m x_left + x_right Sb_q, x_left S_q + m x_right); Sb_q = q0 + q.sigma, S_q = q0 - q.sigma
+    const W4<R> inner = row_qprop(x, q, m, R(1));
+    for (int c = 0; c < 4; ++c) sb += re_mulc(ob.c[c], inner.c[c]);
+    W4<R> o;
+    for (int c = 0; c < 4; ++c) o.c[c] = cscale(ob.c[c], s);
+    // matrices as [[M00, M01], [M10, M11]] with row-vector products y_c = sum_r x_r M_rc
+    const cx<R> Sb00 = mkc(q[0] + q[3], R(0)), Sb11 = mkc(q[0] - q[3], R(0));
+    const cx<R> Sb01 = mkc(q[1], -q[2]), Sb10 = mkc(q[1], q[2]);
+    const cx<R> S00 = mkc(q[0] - q[3], R(0)), S11 = mkc(q[0] + q[3], R(0));
+    const cx<R> S01 = mkc(-q[1], q[2]), S10 = mkc(-q[1], -q[2]);
+    // x_left: m o_left + o_right S_q^dagger rows; x_right: o_left Sb_q^dagger rows + m o_right
+    xb.c[0] = cadd(xb.c[0], cadd(cscale(o.c[0], m), cadd(cmulc(o.c[2], S00), cmulc(o.c[3], S01))));
+    xb.c[1] = cadd(xb.c[1], cadd(cscale(o.c[1], m), cadd(cmulc(o.c[2], S10), cmulc(o.c[3], S11))));
+    xb.c[2] = cadd(xb.c[2], cadd(cadd(cmulc(o.c[0], Sb00), cmulc(o.c[1], Sb01)), cscale(o.c[2], m)));
+    xb.c[3] = cadd(xb.c[3], cadd(cadd(cmulc(o.c[0], Sb10), cmulc(o.c[1], Sb11)), cscale(o.c[3], m)));
+    for (int c = 0; c < 4; ++c) mb += re_mulc(o.c[c], x.c[c]);
+    // entry adjoints: Sb_rc from o_left_c and x_right_r, S_rc from o_right_c and x_left_r
+    const cx<R> b00 = cmulc(o.c[0], x.c[2]), b01 = cmulc(o.c[1], x.c[2]), b10 = cmulc(o.c[0], x.c[3]), b11 = cmulc(o.c[1], x.c[3]);
+    const cx<R> a00 = cmulc(o.c[2], x.c[0]), a01 = cmulc(o.c[3], x.c[0]), a10 = cmulc(o.c[2], x.c[1]), a11 = cmulc(o.c[3], x.c[1]);
+    // dq for a real q: Re(entry adjoint * conj(d entry / dq))
+    qb[0] += b00.r + b11.r + a00.r + a11.r;
+    qb[3] += b00.r - b11.r - a00.r + a11.r;
+    qb[1] += b01.r + b10.r - a01.r - a10.r;
+    qb[2] += -b01.i + b10.i + a01.i - a10.i;
+}
+
+// reverse of gluon current c of level M (its adjoint a.Jb[joff + c] complete)
+template <typename R, int M, int NV4, class W, class A>
+__device__ __forceinline__ void bg_gluon_current_adj(const W& w, A& a, int c, int joff, const uint8_t* mask,
+                                                     const uint16_t* v3, const uint8_t* v3m, const uint16_t* v4)
+{
+    const int msk = __ldg(mask + c);
+    const W4<R> Jo = w.J[joff + c], Jb = a.Jb[joff + c];
+    const R ip = w.iP2[msk];
+    // J = ip acc: accb = ip Jb; ipb = Re sum Jb conj(acc) = Re sum Jb conj(J) / ip
+    W4<R> accb;
+    R ipb = R(0);
+    for (int m = 0; m < 4; ++m) { accb.c[m] = cscale(Jb.c[m], ip); ipb += re_mulc(Jb.c[m], Jo.c[m]); }
+    atomicAdd(&a.iP2b[msk], ipb / ip);
+#pragma unroll
+    for (int j = 0; j < M - 1; ++j) {
+        const uint16_t ra = __ldg(v3 + (c * (M - 1) + j) * 2), rb = __ldg(v3 + (c * (M - 1) + j) * 2 + 1);
+        const int ma = __ldg(v3m + (c * (M - 1) + j) * 2), mb = __ldg(v3m + (c * (M - 1) + j) * 2 + 1);
+        const R k1[4] = { w.P[ma][0], w.P[ma][1], w.P[ma][2], w.P[ma][3] };
+        const R k2[4] = { w.P[mb][0], w.P[mb][1], w.P[mb][2], w.P[mb][3] };
+        W4<R> J1b = w4_zero<R>(), J2b = w4_zero<R>();
+        R k1b[4] = { R(0), R(0), R(0), R(0) }, k2b[4] = { R(0), R(0), R(0), R(0) };
+        vvv_cur_adj(w.J[ref_id(ra)], w.J[ref_id(rb)], k1, k2, -(ref_sign<R>(ra) * ref_sign<R>(rb)), accb, J1b, J2b,
+                    k1b, k2b);
+        atomic_add_w4(a.Jb[ref_id(ra)], J1b);
+        atomic_add_w4(a.Jb[ref_id(rb)], J2b);
+        for (int m = 0; m < 4; ++m) { atomicAdd(&a.Pb[ma][m], k1b[m]); atomicAdd(&a.Pb[mb][m], k2b[m]); }
+    }
+#pragma unroll
+    for (int j = 0; j < NV4; ++j) {
+        const uint16_t ra = __ldg(v4 + (c * NV4 + j) * 3), rb = __ldg(v4 + (c * NV4 + j) * 3 + 1);
+        const uint16_t rc = __ldg(v4 + (c * NV4 + j) * 3 + 2);
+        W4<R> J1b = w4_zero<R>(), J2b = w4_zero<R>(), J3b = w4_zero<R>();
+        v4_adj(w.J[ref_id(ra)], w.J[ref_id(rb)], w.J[ref_id(rc)], ref_sign<R>(ra) * ref_sign<R>(rb) * ref_sign<R>(rc),
+               accb, J1b, J2b, J3b);
+        atomic_add_w4(a.Jb[ref_id(ra)], J1b);
+        atomic_add_w4(a.Jb[ref_id(rb)], J2b);
+        atomic_add_w4(a.Jb[ref_id(rc)], J3b);
+    }
+}
+
+// reverse of top-line current c of level M (its adjoint a.Ub[uoff + c] complete); the
+// sum before the propagator is recomputed from the stored currents
+template <typename R, int M, class W, class A>
+__device__ __forceinline__ void bg_top_current_adj(const W& w, A& a, int c, int uoff, const uint8_t* mask,
+                                                   const uint16_t* terms)
+{
+    W4<R> x = w4_zero<R>();
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const int ui = __ldg(terms + (c * M + j) * 2);
+        const uint16_t r = __ldg(terms + (c * M + j) * 2 + 1);
+        w4_axpy(x, ref_sign<R>(r), row_jslash(w.U[ui], w.J[ref_id(r)]));
+    }
+    const int msk = __ldg(mask + c);
+    const R q[4] = { w.Q[msk][0], w.Q[msk][1], w.Q[msk][2], w.Q[msk][3] };
+    const R s = -w.iQ[msk];
+    W4<R> xb = w4_zero<R>();
+    R qb[4] = { R(0), R(0), R(0), R(0) }, mb = R(0), sb = R(0);
+    row_qprop_adj(x, q, w.mt, s, a.Ub[uoff + c], xb, qb, mb, sb);
+    for (int m = 0; m < 4; ++m) atomicAdd(&a.Qb[msk][m], qb[m]);
+    atomicAdd(&a.iQb[msk], -sb);
+    atomicAdd(&a.mtb, mb);
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+        const int ui = __ldg(terms + (c * M + j) * 2);
+        const uint16_t r = __ldg(terms + (c * M + j) * 2 + 1);
+        W4<R> ob;
+        const R sg = ref_sign<R>(r);
+        for (int m = 0; m < 4; ++m) ob.c[m] = cscale(xb.c[m], sg);
+        W4<R> ub = w4_zero<R>(), Jb = w4_zero<R>();
+        row_jslash_adj(w.U[ui], w.J[ref_id(r)], ob, ub, Jb);
+        atomic_add_w4(a.Ub[ui], ub);
+        atomic_add_w4(a.Jb[ref_id(r)], Jb);
+    }
+}
+
+
+// ------------------------------------------------------------------ one event, one warp
+
+// The per-event invariants (FP64 arithmetic, stored as R) of the K gluons (incoming
+// convention: gluons 0 and 1 incoming, the rest outgoing with minus their momenta), the
+// top and the antitop: subset momenta and inverse denominators, one subset per lane,
+// polarisation and spinor bases.  Particle order of p: g, g, t, tbar, g, ...
+template <int K, typename R, class W>
+__device__ __forceinline__ void bg_event_invariants(W& w, const double (&p)[K + 2][4], double mt, int lane)
+{
+    const int msk = lane;
+    if (msk >= 1 && msk < (1 << K)) {
+        double P[4] = { 0.0, 0.0, 0.0, 0.0 };
+        for (int i = 0; i < K; ++i)
+            if (msk >> i & 1) {
+                const int e = i < 2 ? i : i + 2;
+                const double sg = i < 2 ? 1.0 : -1.0;
+                for (int c = 0; c < 4; ++c) P[c] += sg * p[e][c];
+            }
+        double q[4];
+        for (int c = 0; c < 4; ++c) { w.P[msk][c] = R(P[c]); q[c] = p[2][c] - P[c]; w.Q[msk][c] = R(q[c]); }
+        w.iP2[msk] = __popc(msk) >= 2 ? R(1.0 / mdot(P, P)) : R(0);
+        w.iQ[msk] = R(1.0 / (mdot(q, q) - mt * mt));
+    }
+    if (lane < K) {
+        double a[3], b[3];
+        gluon_basis(p[lane < 2 ? lane : lane + 2], a, b);
+        for (int j = 0; j < 3; ++j) { w.e1[lane][j] = R(a[j]); w.e2[lane][j] = R(b[j]); }
+    }
+    if (lane == K) w.fb3 = fermion_basis<R>(p[2], mt);
+    if (lane == K + 1) w.fb4 = fermion_basis<R>(p[3], mt);
+    if (lane == K + 2) w.mt = R(mt);
+}
+
+// external states of helicity configuration ih (bit i: helicity of external particle i)
+template <int K, typename R, class W>
+__device__ __forceinline__ void bg_external_states(W& w, int ih, int lane)
+{
+#define HEL(i) ((ih >> (i)) & 1 ? 1 : -1)
+    if (lane < K) w.J[lane] = ext_gluon(w.e1[lane], w.e2[lane], HEL(lane < 2 ? lane : lane + 2), lane >= 2);
+    else if (lane == K) w.U[0] = ext_ubar(w.fb3, HEL(2));
+    else if (lane == K + 1) w.V = ext_v(w.fb4, HEL(3));
+#undef HEL
+}
+
+// partial amplitudes: the top line closed on v(p_tbar), lanes over the orderings
+template <class G, typename R, class W>
+__device__ __forceinline__ void bg_closures(W& w, int lane)
+{
+    const uint16_t* cl = G::closure();
+    for (int s = lane; s < G::NPERM; s += 32) {
+        cx<R> a = mkc(R(0), R(0));
+#pragma unroll
+        for (int j = 0; j < G::K; ++j) {
+            const int ui = __ldg(cl + (s * G::K + j) * 2);
+            const uint16_t r = __ldg(cl + (s * G::K + j) * 2 + 1);
+            const cx<R> t = ffv_amp(w.U[ui], w.V, w.J[ref_id(r)]);
+            const R sg = ref_sign<R>(r);
+            a.r = fma(sg, t.r, a.r);
+            a.i = fma(sg, t.i, a.i);
+        }
+        w.A[s] = a;
+    }
+}
+
+// the colour sum of the helicity: every lane's rows sigma = lane, lane + 32, ... of
+// sum_tau C A_tau (C scaled to integers, rows CROW floats apart in shared memory); with
+// yout the rows' complex sums are kept (the adjoint of the partial amplitudes is 2 y).
+// Returns the warp's sum (all lanes).
+template <class G, typename R, class W>
+__device__ __forceinline__ R bg_colour_sum(W& w, const float* cs, int crow, int lane, cx<R>* yout)
+{
+    R part = R(0);
+    for (int s = lane; s < G::NPERM; s += 32) {
+        const float* row = cs + s * crow;
+        R yr = R(0), yi = R(0);
+#pragma unroll 8
+        for (int t = 0; t < G::NPERM; ++t) {
+            const R c = R(row[t]);
+            yr = fma(c, w.A[t].r, yr);
+            yi = fma(c, w.A[t].i, yi);
+        }
+        part = fma(w.A[s].r, yr, fma(w.A[s].i, yi, part));
+        if (yout) yout[s] = mkc(yr, yi);
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    return part;
+}
+
+// Sum over helicities of sum_{sigma tau} A*_sigma C_{sigma tau} A_tau / COLOUR_DEN for one
+// event, by the whole warp (couplings and averages not applied).  pev: the event's FP64
+// momenta, component 4 i + c of particle i at pev[(4 i + c) stride].  all_hel: every
+// configuration (else one of each parity pair, doubled); hel_out (nullable, all_hel):
+// each configuration's value times hel_scale, written by lane 0.
+template <class G, typename R, class W>
+__device__ double bg_warp_me2(W& w, const float* cs, int crow, const double* pev, int stride, double mt, bool all_hel,
+                              double* hel_out, double hel_scale)
+{
+    constexpr int K = G::K, NEXT = K + 2, NHEL = 1 << NEXT;
+    const int lane = threadIdx.x & 31;
+    double p[NEXT][4];
+    for (int f = 0; f < NEXT * 4; ++f) p[f >> 2][f & 3] = pev[(size_t)f * stride];
+    bg_event_invariants<K, R>(w, p, mt, lane);
+    __syncwarp();
+    R total = R(0);
+    const int h0 = all_hel ? 0 : 1, hstep = all_hel ? 1 : 2;
+#pragma unroll 1
+    for (int ih = h0; ih < NHEL; ih += hstep) {
+        bg_external_states<K, R>(w, ih, lane);
+        __syncwarp();
+        G::template forward<R>(w, lane);
+        bg_closures<G, R>(w, lane);
+        __syncwarp();
+        const R part = bg_colour_sum<G, R>(w, cs, crow, lane, (cx<R>*)nullptr);
+        if (hel_out && lane == 0) hel_out[ih] = double(part) * hel_scale;
+        total += part;
+        __syncwarp();
+    }
+    return double(total) * (all_hel ? 1.0 : 2.0) / G::COLOUR_DEN;
+}
+
+
+// The value of bg_warp_me2 (parity-halved helicity sum, doubled) and its derivatives by a
+// reverse sweep.  For every helicity the warp recomputes the currents forward (nothing is
+// kept from one helicity to the next), seeds the adjoints of the partial amplitudes with
+// the colour sum (dL/dA*_sigma = 2 sum_tau C A_tau, doubled for the parity mirror), and
+// runs the closures, the recursion levels and the external states backwards, summing the
+// adjoints of the per-event invariants over helicities.  Then lane j < 4 (K + 2) carries
+// the tangent of momentum component j (and, with dir, lane 4 (K + 2) the tangent along
+// dir[0 .. 4 (K + 2) - 1] for the momenta and dir[4 (K + 2)] for m_t) through the
+// invariants' FP64 arithmetic and contracts it with their adjoints: dout[j] (lane j) is
+// the derivative of the returned value along that direction, the momentum components
+// taken as independent variables of this formula.  a: the warp's adjoint state.
+template <class G, typename R, class W, class A>
+__device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const double* pev, int stride, double mt,
+                               double* dout, const double* dir)
+{
+    constexpr int K = G::K, NEXT = K + 2, NHEL = 1 << NEXT, NM = 1 << K;
+    constexpr int ROWS = (G::NPERM + 31) / 32;
+    using D = Dual<double>;
+    const int lane = threadIdx.x & 31;
+    double p[NEXT][4];
+    for (int f = 0; f < NEXT * 4; ++f) p[f >> 2][f & 3] = pev[(size_t)f * stride];
+    bg_event_invariants<K, R>(w, p, mt, lane);
+    // the invariants' adjoints start at zero
+    for (int i = lane; i < NM; i += 32) {
+        for (int c = 0; c < 4; ++c) { a.Pb[i][c] = R(0); a.Qb[i][c] = R(0); }
+        a.iP2b[i] = R(0); a.iQb[i] = R(0);
+    }
+    if (lane < K)
+        for (int j = 0; j < 3; ++j) { a.e1b[lane][j] = R(0); a.e2b[lane][j] = R(0); }
+    if (lane == K) {
+        for (int x = 0; x < 4; ++x) { a.chi3b[x >> 1][x & 1] = mkc(R(0), R(0)); a.chi4b[x >> 1][x & 1] = mkc(R(0), R(0)); }
+        a.om3b[0] = a.om3b[1] = a.om4b[0] = a.om4b[1] = R(0);
+        a.mtb = R(0);
+    }
+    __syncwarp();
+    R total = R(0);
+#pragma unroll 1
+    for (int ih = 1; ih < NHEL; ih += 2) {
+        bg_external_states<K, R>(w, ih, lane);
+        for (int i = lane; i < G::NJ; i += 32) a.Jb[i] = w4_zero<R>();
+        for (int i = lane; i < G::NU; i += 32) a.Ub[i] = w4_zero<R>();
+        if (lane == 0) a.Vb = w4_zero<R>();
+        __syncwarp();
+        G::template forward<R>(w, lane);
+        bg_closures<G, R>(w, lane);
+        __syncwarp();
+        cx<R> y[ROWS];
+        R part = R(0);
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            const int sg = lane + 32 * r;
+            if (sg < G::NPERM) {
+                const float* row = cs + sg * crow;
+                R yr = R(0), yi = R(0);
+                for (int t = 0; t < G::NPERM; ++t) {
+                    const R c = R(row[t]);
+                    yr = fma(c, w.A[t].r, yr);
+                    yi = fma(c, w.A[t].i, yi);
+                }
+                part = fma(w.A[sg].r, yr, fma(w.A[sg].i, yi, part));
+                y[r] = mkc(yr, yi);
+            }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+        total += part;
+        __syncwarp();
+        // the partial amplitudes' adjoints replace them: 2 (C A)_sigma, times 2 for the parity mirror
+#pragma unroll
+        for (int r = 0; r < ROWS; ++r) {
+            const int sg = lane + 32 * r;
+            if (sg < G::NPERM) w.A[sg] = cscale(y[r], R(4));
+        }
+        __syncwarp();
+        // closures backwards: A_sigma = sum_j sg_j (U_j Jslash_j) . v
+        {
+            const uint16_t* cl = G::closure();
+            W4<R> vb = w4_zero<R>();
+            for (int sgm = lane; sgm < G::NPERM; sgm += 32) {
+                const cx<R> ab = w.A[sgm];
+#pragma unroll
+                for (int j = 0; j < K; ++j) {
+                    const int ui = __ldg(cl + (sgm * K + j) * 2);
+                    const uint16_t r = __ldg(cl + (sgm * K + j) * 2 + 1);
+                    const R sgn = ref_sign<R>(r);
+                    const W4<R> t = row_jslash(w.U[ui], w.J[ref_id(r)]);
+                    W4<R> tb;
+                    for (int c = 0; c < 4; ++c) {
+                        vb.c[c] = cadd(vb.c[c], cscale(cmulc(ab, t.c[c]), sgn));
+                        tb.c[c] = cscale(cmulc(ab, w.V.c[c]), sgn);
+                    }
+                    W4<R> ub = w4_zero<R>(), jb = w4_zero<R>();
+                    row_jslash_adj(w.U[ui], w.J[ref_id(r)], tb, ub, jb);
+                    atomic_add_w4(a.Ub[ui], ub);
+                    atomic_add_w4(a.Jb[ref_id(r)], jb);
+                }
+            }
+            atomic_add_w4(a.Vb, vb);
+        }
+        __syncwarp();
+        G::template reverse<R>(w, a, lane);
+        // external states backwards into the polarisation and spinor pieces (one lane each)
+#define HEL(i) ((ih >> (i)) & 1 ? 1 : -1)
+        if (lane < K) {
+            const R l = HEL(lane < 2 ? lane : lane + 2) > 0 ? R(1) : R(-1), so = lane >= 2 ? R(1) : R(-1);
+            for (int j = 0; j < 3; ++j) {
+                a.e1b[lane][j] += -l * a.Jb[lane].c[j + 1].r;
+                a.e2b[lane][j] += so * a.Jb[lane].c[j + 1].i;
+            }
+        } else if (lane == K) {
+            // ubar = (conj(chi_l) om_l, conj(chi_l) om_-l)
+            const int l = HEL(2) > 0 ? 0 : 1;
+            const W4<R>& ub = a.Ub[0];
+            const R wl = w.fb3.om[l], wml = w.fb3.om[1 - l];
+            for (int b = 0; b < 2; ++b) {
+                a.chi3b[l][b] = cadd(a.chi3b[l][b], cadd(cscale(conjc(ub.c[b]), wl), cscale(conjc(ub.c[2 + b]), wml)));
+                a.om3b[l] += ub.c[b].r * w.fb3.chi[l][b].r - ub.c[b].i * w.fb3.chi[l][b].i;
+                a.om3b[1 - l] += ub.c[2 + b].r * w.fb3.chi[l][b].r - ub.c[2 + b].i * w.fb3.chi[l][b].i;
+            }
+        } else if (lane == K + 1) {
+            // v = (chi_-l (-s om_l), chi_-l (s om_-l))
+            const int l = HEL(3) > 0 ? 0 : 1;
+            const R sl = HEL(3) > 0 ? R(1) : R(-1);
+            const W4<R>& vb = a.Vb;
+            const R wl = w.fb4.om[l], wml = w.fb4.om[1 - l];
+            for (int b = 0; b < 2; ++b) {
+                a.chi4b[1 - l][b] = cadd(a.chi4b[1 - l][b], cadd(cscale(vb.c[b], -sl * wl), cscale(vb.c[2 + b], sl * wml)));
+                a.om4b[l] += -sl * re_mulc(vb.c[b], w.fb4.chi[1 - l][b]);
+                a.om4b[1 - l] += sl * re_mulc(vb.c[2 + b], w.fb4.chi[1 - l][b]);
+            }
+        }
+#undef HEL
+        __syncwarp();
+    }
+    // tangents through the invariants
+    const int nd = NEXT * 4 + (dir ? 1 : 0);
+    if (lane < nd && dout) {
+        D pd[NEXT][4];
+        D mtd(mt, 0.0);
+        for (int i = 0; i < NEXT; ++i)
+            for (int c = 0; c < 4; ++c)
+                pd[i][c] = D(p[i][c], lane < NEXT * 4 ? ((4 * i + c) == lane ? 1.0 : 0.0) : dir[4 * i + c]);
+        if (lane == NEXT * 4) mtd = D(mt, dir[NEXT * 4]);
+        double g = 0.0;
+        for (int msk = 1; msk < NM; ++msk) {
+            D P[4] = { D(0.0), D(0.0), D(0.0), D(0.0) };
+            for (int i = 0; i < K; ++i)
+                if (msk >> i & 1) {
+                    const int e = i < 2 ? i : i + 2;
+                    for (int c = 0; c < 4; ++c) P[c] = i < 2 ? P[c] + pd[e][c] : P[c] - pd[e][c];
+                }
+            D q[4];
+            for (int c = 0; c < 4; ++c) {
+                q[c] = pd[2][c] - P[c];
+                g += P[c].d * double(a.Pb[msk][c]) + q[c].d * double(a.Qb[msk][c]);
+            }
+            if (__popc(msk) >= 2) g += (1.0 / mdot(P, P)).d * double(a.iP2b[msk]);
+            g += (1.0 / (mdot(q, q) - mtd * mtd)).d * double(a.iQb[msk]);
+        }
+        for (int gl = 0; gl < K; ++gl) {
+            D e1[3], e2[3];
+            gluon_basis(pd[gl < 2 ? gl : gl + 2], e1, e2);
+            for (int j = 0; j < 3; ++j) g += e1[j].d * double(a.e1b[gl][j]) + e2[j].d * double(a.e2b[gl][j]);
+        }
+        {
+            const FermionBasis<D> f3 = fermion_basis<D>(pd[2], mtd), f4 = fermion_basis<D>(pd[3], mtd);
+            for (int x = 0; x < 2; ++x)
+                for (int b = 0; b < 2; ++b) {
+                    g += f3.chi[x][b].r.d * double(a.chi3b[x][b].r) + f3.chi[x][b].i.d * double(a.chi3b[x][b].i);
+                    g += f4.chi[x][b].r.d * double(a.chi4b[x][b].r) + f4.chi[x][b].i.d * double(a.chi4b[x][b].i);
+                }
+            for (int x = 0; x < 2; ++x) g += f3.om[x].d * double(a.om3b[x]) + f4.om[x].d * double(a.om4b[x]);
+        }
+        g += mtd.d * double(a.mtb);
+        dout[lane] = g / G::COLOUR_DEN;
+    }
+    return double(total) * 2.0 / G::COLOUR_DEN;
+}
+
+// state of a warp for the derivative: forward currents and their adjoints
+template <class G, typename R>
+struct BgGradWarp {
+    BgWarp<R, G::K, G::NJ, G::NU, G::NPERM> w;
+    BgAdj<R, G::K, G::NJ, G::NU> a;
+};
+
+// mf_evaluate with derivatives for a gluon process of the recursion: one warp per point,
+// WARPS warps per CTA; the colour matrix and the warps' states in dynamic shared memory.
+// me2 [n] and dme2 [n][K + 2][4]: averaged |M|^2 (norm: couplings, averages, symmetry)
+// and its derivatives with respect to every momentum component
+template <class G, typename R>
+__global__ void __launch_bounds__(128) bg_evaluate_grad_kernel(const double* __restrict__ mom, long long n,
+                                                               double* __restrict__ me2, double* __restrict__ dme2,
+                                                               double mt, double norm)
+{
+    constexpr int NEXT = G::K + 2, CROW = G::NPERM + 1;
+    extern __shared__ __align__(128) unsigned char mf_bgg_smem[];
+    float* cs = reinterpret_cast<float*>(mf_bgg_smem);
+    for (int i = threadIdx.x; i < G::NPERM * G::NPERM; i += blockDim.x)
+        cs[(i / G::NPERM) * CROW + i % G::NPERM] = __ldg(G::colour() + i);
+    __syncthreads();
+    const size_t cbytes = ((sizeof(float) * G::NPERM * CROW) + 127) & ~(size_t)127;
+    const size_t wbytes = (sizeof(BgGradWarp<G, R>) + 15) & ~(size_t)15;
+    const int warp = threadIdx.x >> 5, nw = blockDim.x >> 5, lane = threadIdx.x & 31;
+    auto& st = *reinterpret_cast<BgGradWarp<G, R>*>(mf_bgg_smem + cbytes + warp * wbytes);
+    for (long long e = (long long)blockIdx.x * nw + warp; e < n; e += (long long)gridDim.x * nw) {
+        double dbuf[32];   // lane j keeps the derivative along component j
+        const double v = bg_warp_grad<G, R>(st.w, st.a, cs, CROW, mom + e * NEXT * 4, 1, mt, dbuf, nullptr);
+        if (lane < NEXT * 4 && dme2) dme2[e * NEXT * 4 + lane] = dbuf[lane] * norm;
+        if (lane == 0 && me2) me2[e] = v * norm;
+    }
+}
+
+template <class G, typename R>
+inline size_t bg_grad_smem(int warps)
+{
+    const size_t cbytes = ((sizeof(float) * G::NPERM * (G::NPERM + 1)) + 127) & ~(size_t)127;
+    const size_t wbytes = (sizeof(BgGradWarp<G, R>) + 15) & ~(size_t)15;
+    return cbytes + (size_t)warps * wbytes;
+}
+
+
+// host launcher of bg_evaluate_grad_kernel for a gluon process with tables G and
+// symmetry factor 1/SYM_DEN: |M|^2 averaged over the initial spins and colours (1/256)
+template <class G, int SYM_DEN>
+struct BgEvalGrad {
+    static constexpr int WARPS = 4;
+    static cudaError_t launch(int prec, const double* mom, long long n, double* me2, double* dme2, double mt, double gs,
+                              int, cudaStream_t s)
+    {
+        static bool attr = false;
+        const size_t s32 = bg_grad_smem<G, float>(WARPS), s64 = bg_grad_smem<G, double>(WARPS);
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute((const void*)bg_evaluate_grad_kernel<G, float>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute((const void*)bg_evaluate_grad_kernel<G, double>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        double norm = 1.0 / (256.0 * SYM_DEN);
+        for (int i = 0; i < G::K; ++i) norm *= gs * gs;
+        const long long want = (n + WARPS - 1) / WARPS;
+        const int nblk = (int)(want < 8192 ? want : 8192);
+        if (prec) bg_evaluate_grad_kernel<G, float><<<nblk, 32 * WARPS, s32, s>>>(mom, n, me2, dme2, mt, norm);
+        else bg_evaluate_grad_kernel<G, double><<<nblk, 32 * WARPS, s64, s>>>(mom, n, me2, dme2, mt, norm);
+        return cudaGetLastError();
+    }
+};
+
 }  // namespace mf

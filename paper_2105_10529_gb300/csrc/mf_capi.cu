@@ -136,6 +136,7 @@ const GradOpsTable* grad_ops(int p)
     case MF_GG_TTGG: return grad_gg_ttgg();
     case MF_UU_TT: return grad_uu_tt();
     case MF_UG_TTU: return grad_ug_ttu();
+    case MF_GG_TTGGG: return grad_gg_ttggg();
     default: return nullptr;
     }
 }
@@ -524,7 +525,7 @@ int integrate_impl(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, l
     const GradOpsTable* gops = nullptr;
     if (want_grads) {
         gops = grad_ops(process);
-        if (!gops) return fail(c, MF_ERR_UNSUPPORTED, "no derivative pass for this process");
+        if (!gops || !gops->has_pass) return fail(c, MF_ERR_UNSUPPORTED, "no derivative pass for this process");
         if (c->cfg.precision == MF_FP64 && !gops->has_fp64)
             return fail(c, MF_ERR_UNSUPPORTED, "FP64 derivative of this process not built; use MF_MIXED");
     }
@@ -707,7 +708,7 @@ int mf_vegas_pass_grad(mf_ctx* c, int process, double sqrt_s, const double* grid
     if (!c) return MF_ERR_ARG;
     const ProcOps* ops = proc_ops(process);
     const GradOpsTable* g = grad_ops(process);
-    if (!ops || !g) return fail(c, MF_ERR_UNSUPPORTED, "no derivative pass for this process");
+    if (!ops || !g || !g->has_pass) return fail(c, MF_ERR_UNSUPPORTED, "no derivative pass for this process");
     if (c->cfg.precision == MF_FP64 && !g->has_fp64)
         return fail(c, MF_ERR_UNSUPPORTED, "FP64 derivative of this process not built; use MF_MIXED");
     if (!grid_dev || !out_dev || n_events < 1 || ev_offset < 0 || !(sqrt_s > 0.0))
@@ -756,7 +757,7 @@ int mf_evaluate(mf_ctx* c, int process, const double* momenta_dev, long long n, 
         // |M|^2 and its momentum derivatives in one kernel (forward mode, one tangent per component)
         const GradOpsTable* g = grad_ops(process);
         if (!g) return fail(c, MF_ERR_UNSUPPORTED, "no derivative for this process");
-        if (c->cfg.precision == MF_FP64 && !g->has_fp64)
+        if (c->cfg.precision == MF_FP64 && !g->has_fp64_evaluate)
             return fail(c, MF_ERR_UNSUPPORTED, "FP64 derivative of this process not built; use MF_MIXED");
         if (n == 0) return MF_OK;
         if (!momenta_dev || n < 0) return fail(c, MF_ERR_ARG, "mf_evaluate: bad argument");

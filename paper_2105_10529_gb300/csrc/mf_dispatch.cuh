@@ -49,7 +49,9 @@ struct GradOpsTable {
     cudaError_t (*evaluate_grad)(int prec, const double* mom, long long n, double* me2, double* dme2, double mt,
                                  double gs, int nblk, cudaStream_t s);
     int k_as;          // power of alpha_s in |M|^2
-    bool has_fp64;     // FP64 (Dual<double>) derivative built
+    bool has_fp64;     // FP64 (Dual<double>) derivative pass built
+    bool has_fp64_evaluate;   // FP64 d|M|^2/dp built (evaluate_grad)
+    bool has_pass = true;     // the derivative pass of the integrand (grad) exists
 };
 
 const GradOpsTable* grad_gg_tt();
@@ -57,6 +59,7 @@ const GradOpsTable* grad_gg_ttg();
 const GradOpsTable* grad_gg_ttgg();
 const GradOpsTable* grad_uu_tt();
 const GradOpsTable* grad_ug_ttu();
+const GradOpsTable* grad_gg_ttggg();
 
 template <class P, class ME, bool FP64>
 struct GradOps {

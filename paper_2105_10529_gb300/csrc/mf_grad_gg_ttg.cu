@@ -1,13 +1,17 @@
-// Derivative kernels of the process gg_ttg (forward mode), in a translation
+// Derivative kernels of the process gg_ttg (the m_t derivative pass in forward mode, d|M|^2/dp
+// by the reverse sweep), in a translation
 // unit of their own so that they compile in parallel with the value kernels.
 #include "mf_dispatch.cuh"
 #include "generated/me_gg_ttg.cuh"
+#include "generated/bg_gg_ttg.cuh"
 
 namespace mf {
 namespace {
 using P = ProcTops<Me_gg_ttg>;
 using G = GradOps<P, Me_gg_ttg, true>;
-const GradOpsTable kGrad = { &G::grad, &G::evaluate_grad, 3, true };
+// d|M|^2/dp by the reverse sweep of the Berends-Giele recursion (FP64 and mixed)
+using E = BgEvalGrad<BgGen_gg_ttg, 1>;
+const GradOpsTable kGrad = { &G::grad, &E::launch, 3, true, true };
 }  // namespace
 
 const GradOpsTable* grad_gg_ttg() { return &kGrad; }

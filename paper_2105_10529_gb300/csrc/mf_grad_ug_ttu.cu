@@ -7,7 +7,7 @@ namespace mf {
 namespace {
 using P = ProcTops<Me_ug_ttu, 1, 0>;
 using G = GradOps<P, Me_ug_ttu, true>;
-const GradOpsTable kGrad = { &G::grad, &G::evaluate_grad, 3, true };
+const GradOpsTable kGrad = { &G::grad, &G::evaluate_grad, 3, true, true };
 }  // namespace
 
 const GradOpsTable* grad_ug_ttu() { return &kGrad; }

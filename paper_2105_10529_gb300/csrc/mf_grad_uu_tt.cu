@@ -7,7 +7,7 @@ namespace mf {
 namespace {
 using P = ProcTops<Me_uu_tt, 1, 2>;
 using G = GradOps<P, Me_uu_tt, true>;
-const GradOpsTable kGrad = { &G::grad, &G::evaluate_grad, 2, true };
+const GradOpsTable kGrad = { &G::grad, &G::evaluate_grad, 2, true, true };
 }  // namespace
 
 const GradOpsTable* grad_uu_tt() { return &kGrad; }

@@ -25,6 +25,9 @@ def write_all(out_dir: str = OUT) -> list:
     items += [("me_uu_tt.cuh", lambda: qq_processes.generate_uu_tt()[0]),
               ("me_ug_ttu.cuh", lambda: qq_processes.generate_ug_ttu()[0]),
               ("bg_gg_ttggg.cuh", lambda: bg_tables.generate(5, "gg_ttggg")[0])]
+    # the recursion's tables of the lighter gluon processes (their derivatives run the reverse sweep)
+    items += [(f"bg_{name}.cuh", lambda k=k, name=name: bg_tables.generate(k, name)[0])
+              for k, name in ((2, "gg_tt"), (3, "gg_ttg"), (4, "gg_ttgg"))]
     for fname, make in items:
         src = make()
         path = os.path.join(out_dir, fname)

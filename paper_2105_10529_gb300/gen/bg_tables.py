@@ -125,6 +125,7 @@ def generate(k: int, name: str) -> Tuple[str, dict]:
     L.append(f"// {t['nj_total']} stored gluon currents, {t['nu_total']} top-line currents.")
     L.append("#pragma once")
     L.append("#include <cstdint>")
+    L.append('#include "mf_bg.cuh"')
     L.append("namespace mf {")
     L.append(f"namespace bg_{name} {{")
     L.append(f"constexpr int K = {k};")
@@ -154,6 +155,60 @@ def generate(k: int, name: str) -> Tuple[str, dict]:
     L.append(f"// C_{{sigma tau}} times COLOUR_DEN (integers), orderings lexicographic")
     L.append(_arr("colour", "float", [n * n], _flat(t["colour"])))
     L.append(f"}}  // namespace bg_{name}")
+    L.append("")
+    # the level drivers: one warp, lanes over the currents of a level (gluon level m with
+    # top-line level m - 1), __syncwarp between levels
+    def gl(m):
+        nv4 = (m - 1) * (m - 2) // 2
+        v4 = f"&T::j{m}_v4[0][0][0]" if nv4 else "nullptr"
+        return (f"bg_gluon_current<R, {m}, {nv4}>(w, t, T::JOFF{m}, T::j{m}_mask, &T::j{m}_v3[0][0][0], "
+                f"&T::j{m}_v3m[0][0][0], {v4})")
+
+    def gl_adj(m):
+        nv4 = (m - 1) * (m - 2) // 2
+        v4 = f"&T::j{m}_v4[0][0][0]" if nv4 else "nullptr"
+        return (f"bg_gluon_current_adj<R, {m}, {nv4}>(w, a, t, T::JOFF{m}, T::j{m}_mask, &T::j{m}_v3[0][0][0], "
+                f"&T::j{m}_v3m[0][0][0], {v4})")
+
+    def tl(m, adj=False):
+        f = "bg_top_current_adj" if adj else "bg_top_current"
+        extra = "a, " if adj else ""
+        return f"{f}<R, {m}>(w, {extra}t - T::NJ{m + 1 if not adj else m + 1}, T::UOFF{m}, T::u{m}_mask, &T::u{m}_terms[0][0][0])"
+
+    L.append(f"// level drivers of the recursion of {name} (see mf_bg.cuh)")
+    L.append(f"struct BgGen_{name} {{")
+    L.append(f"    static constexpr int K = {k}, NPERM = {n}, NJ = {t['nj_total']}, NU = {t['nu_total']};")
+    L.append(f"    static constexpr double COLOUR_DEN = {t['colour_den']}.0;")
+    L.append(f"    __device__ static const float* colour() {{ return bg_{name}::colour; }}")
+    L.append(f"    __device__ static const uint16_t* closure() {{ return &bg_{name}::closure[0][0][0]; }}")
+    L.append("    // gluon currents of 2 .. K gluons and top-line currents of 1 .. K-1 gluons from the")
+    L.append("    // external states in w.J[0 .. K-1] and w.U[0]")
+    L.append("    template <typename R, class W> __device__ static void forward(W& w, int lane)")
+    L.append("    {")
+    L.append(f"        namespace T = bg_{name};")
+    for m in range(2, k + 1):
+        # gluon level m with top-line level m - 1
+        L.append(f"        for (int t = lane; t < T::NJ{m} + T::NU{m - 1}; t += 32) {{")
+        L.append(f"            if (t < T::NJ{m}) {gl(m)};")
+        L.append(f"            else {tl(m - 1).replace(f't - T::NJ{m}', f't - T::NJ{m}')};")
+        L.append("        }")
+        L.append("        __syncwarp();")
+    L.append("    }")
+    L.append("    // the reverse sweep: adjoints of the currents (a.Jb, a.Ub, a.Vb from the closures)")
+    L.append("    // and of the per-event invariants, level by level downwards: top-line level m with")
+    L.append("    // gluon level m + 1 (each pushes only to lower levels)")
+    L.append("    template <typename R, class W, class A> __device__ static void reverse(const W& w, A& a, int lane)")
+    L.append("    {")
+    L.append(f"        namespace T = bg_{name};")
+    for m in range(k - 1, 0, -1):
+        L.append(f"        for (int t = lane; t < T::NJ{m + 1} + T::NU{m}; t += 32) {{")
+        L.append(f"            if (t < T::NJ{m + 1}) {gl_adj(m + 1)};")
+        L.append(f"            else bg_top_current_adj<R, {m}>(w, a, t - T::NJ{m + 1}, T::UOFF{m}, T::u{m}_mask, "
+                 f"&T::u{m}_terms[0][0][0]);")
+        L.append("        }")
+        L.append("        __syncwarp();")
+    L.append("    }")
+    L.append("};")
     L.append("}  // namespace mf")
     return "\n".join(L) + "\n", t
 

@@ -142,17 +142,20 @@ _FLAV = {IN.GG_TT: (0, 0), IN.GG_TTG: (0, 0), IN.GG_TTGG: (0, 0), IN.GG_TTGGG: (
 
 
 def me_condition(proc, phys, p):
-    """Condition number of |M|^2 at momenta p [n_ext, 4] (partonic frame): a
-    final particle i nearly along a beam makes p_beam . p_i = E (E_i - |p_z,i|)
-    cancel, amplifying the relative rounding of its momentum by
-    2 E_i^2 / (m_i^2 + pT_i^2); the largest such factor (at least 1)."""
-    if proc == IN.EE_MUMU:
-        return 1.0
+    """Condition number of |M|^2 at momenta p [n_ext, 4] (partonic frame): the
+    matrix element depends on the momenta through Minkowski products p_i . p_j,
+    which cancel for two nearly collinear momenta (a final particle along a
+    beam, a gluon along a top); the relative rounding of the momenta reaches
+    p_i . p_j amplified by (E_i E_j + |p_i| |p_j|) / |p_i . p_j|.  The largest such
+    factor over all pairs (at least 1)."""
     k = 1.0
-    for i in range(2, p.shape[0]):
-        m = phys.mt if i in (2, 3) else 0.0
-        pt2 = p[i][1] ** 2 + p[i][2] ** 2
-        k = max(k, 2.0 * p[i][0] ** 2 / max(m * m + pt2, 1e-300))
+    n = p.shape[0]
+    for i in range(n):
+        for j in range(i + 1, n):
+            a, b = p[i], p[j]
+            dot = a[0] * b[0] - a[1] * b[1] - a[2] * b[2] - a[3] * b[3]
+            mag = a[0] * b[0] + math.sqrt(a[1] ** 2 + a[2] ** 2 + a[3] ** 2) * math.sqrt(b[1] ** 2 + b[2] ** 2 + b[3] ** 2)
+            k = max(k, mag / max(abs(dot), 1e-300))
     return k
 
 
@@ -173,11 +176,31 @@ def pdf_condition(opdf, flav, x, q2):
     return abs((fp - fm) / (2 * h) / f0) + 1.0
 
 
-def fp64_event_bounds(proc, phys, opdf, ref):
+def momentum_inconsistency(proc, phys, p):
+    """How far momenta p [n_ext, 4] (partonic frame) are from the constraints every
+    |M|^2 formula assumes: the largest mass-shell residual |p_i^2 - m_i^2| / E_i^2 and
+    the momentum-conservation residual relative to sqrt(shat).  Both sides' RAMBO
+    momenta carry these at rounding level, amplified where the conformal map is
+    ill-conditioned, and different formulas for |M|^2 (closed form, recursion,
+    diagrams) respond to them differently."""
+    n_ext = p.shape[0]
+    masses = [0.0] * n_ext
+    if proc != IN.EE_MUMU:
+        masses[2] = masses[3] = phys.mt
+    sh = max(abs(p[i][0] ** 2 - p[i][1] ** 2 - p[i][2] ** 2 - p[i][3] ** 2 - masses[i] ** 2) / p[i][0] ** 2
+             for i in range(n_ext))
+    cons = np.abs(p[0] + p[1] - p[2:].sum(0)).max() / (p[0][0] + p[1][0])
+    return max(sh, cons)
+
+
+def fp64_event_bounds(proc, phys, opdf, ref, p_gpu=None):
     """Per-event bounds for the FP64 path against the oracle, from the
     conditioning of each event (64 eps times the condition numbers, and never
     below 1e-12):
-      |M|^2 : 64 eps me_condition;
+      |M|^2 : 64 eps me_condition, plus 16 me_condition times the inputs'
+              disagreement: the larger momentum_inconsistency of the two sides'
+              momenta (the oracle's, and the GPU's p_gpu [n, n_ext, 4] where
+              given) and their largest difference relative to the largest component;
       w     : that, plus the weight factor's 64 eps sum_i pdf_condition(x_i) (1 + |ln tau|)
               (ln x_i = v ln tau carries an absolute rounding of order eps |ln tau|,
               tau = x1 x2) and the RAMBO map's 8 gamma^2 eps.
@@ -187,7 +210,11 @@ def fp64_event_bounds(proc, phys, opdf, ref):
     gam = np.ones(n) if proc == IN.EE_MUMU else rambo_gamma(ref["x"], IN.N_EXT[proc] - 2)
     for e in range(n):
         km = me_condition(proc, phys, ref["p"][e])
-        b_me[e] = max(1e-12, 64 * EPS * km)
+        inc = momentum_inconsistency(proc, phys, ref["p"][e])
+        if p_gpu is not None:
+            inc = max(inc, momentum_inconsistency(proc, phys, p_gpu[e]))
+            inc += float(np.abs(p_gpu[e] - ref["p"][e]).max() / np.abs(ref["p"][e]).max())
+        b_me[e] = max(1e-12, 64 * EPS * km) + 16 * km * inc
         bw = b_me[e] + 8 * gam[e] ** 2 * EPS
         if proc in _FLAV:
             x1, x2 = ref["x12"][e]

@@ -95,8 +95,31 @@ def boost_direction(p):
     return d
 
 
-@pytest.mark.parametrize("proc,prec", [(IN.GG_TT, 0), (IN.GG_TTG, 0), (IN.GG_TTGG, 1)])
+def rotation_direction(p):
+    """Infinitesimal rotation about z of every momentum: dp_x = -p_y, dp_y = p_x."""
+    d = np.zeros_like(p)
+    d[..., 1] = -p[..., 2]
+    d[..., 2] = p[..., 1]
+    return d
+
+
+def boost_x_direction(p):
+    """Infinitesimal boost along x: dE = p_x, dp_x = E."""
+    d = np.zeros_like(p)
+    d[..., 0] = p[..., 1]
+    d[..., 1] = p[..., 0]
+    return d
+
+
+@pytest.mark.parametrize("proc,prec", [(IN.GG_TT, 0), (IN.GG_TTG, 0), (IN.GG_TTGG, 0), (IN.GG_TTGG, 1),
+                                       (IN.GG_TTGGG, 0), (IN.GG_TTGGG, 1), (IN.UG_TTU, 1)])
 def test_evaluate_gradient(proc, prec, pdf_grid):
+    """d|M|^2/dp of mf_evaluate (the reverse sweep of the Berends-Giele recursion
+    for the gluon processes, forward tangents for u g -> t tbar u): every
+    component against fourth-order differences of the same formula (the value
+    the derivative call returns, in FP64), the value itself against mf_evaluate
+    (the same |M|^2 on shell), and zero along the Lorentz generators (two boosts,
+    one rotation), the directions in which |M|^2 does not change."""
     phys = PHYS[proc]
     rng = np.random.default_rng(50 + proc)
     n_ext = IN.N_EXT[proc]
@@ -110,23 +133,47 @@ def test_evaluate_gradient(proc, prec, pdf_grid):
     ctx = ctx_for(proc, prec, pdf_grid)
     ctx64 = ctx_for(proc, 0, pdf_grid)
     me, g = ctx.evaluate_grad(proc, torch.tensor(P, device="cuda"))
-    g = g.cpu().numpy()
+    me, g = me.cpu().numpy(), g.cpu().numpy()
+    plain = ctx64.evaluate(proc, torch.tensor(P, device="cuda")).cpu().numpy()
+    assert np.all(np.abs(me - plain) <= (1e-11 if prec == 0 else 1e-5) * np.abs(plain)), (me, plain)
     for e in range(len(P)):
-        for (i, c) in [(2, 0), (2, 3), (3, 1), (0, 0), (n_ext - 1, 2)]:
-            # fourth-order central difference (error O(h^4))
+        for (i, c) in [(2, 0), (2, 3), (3, 1), (0, 0), (1, 3), (n_ext - 1, 2)]:
+            # fourth-order central difference (error O(h^4)) of the FP64 value of the same formula
             h = 1e-4 * abs(P[e, i, 0])
             q = np.repeat(P[e:e + 1], 4, axis=0)
             for r, k in enumerate((2, 1, -1, -2)):
                 q[r, i, c] += k * h
-            v = ctx64.evaluate(proc, torch.tensor(q, device="cuda")).cpu().numpy()
+            v = ctx64.evaluate_grad(proc, torch.tensor(q, device="cuda"))[0].cpu().numpy()
             fd = (-v[0] + 8 * v[1] - 8 * v[2] + v[3]) / (12 * h)
             scale = np.abs(g[e]).max() * abs(P[e, i, 0])
             assert abs(g[e, i, c] - fd) * abs(P[e, i, 0]) < (1e-7 if prec == 0 else 3e-5) * scale, (e, i, c, g[e, i, c], fd)
-        # |M|^2 is boost invariant: no derivative along the boost generator
-        d = boost_direction(P[e])
-        along = float(np.sum(g[e] * d))
-        assert abs(along) < (1e-9 if prec == 0 else 1e-4) * float(np.sum(np.abs(g[e] * d))), along
+        # |M|^2 is Lorentz invariant: no derivative along the boost and rotation generators
+        for gen in (boost_direction, boost_x_direction, rotation_direction):
+            d = gen(P[e])
+            along = float(np.sum(g[e] * d))
+            assert abs(along) < (1e-9 if prec == 0 else 1e-4) * float(np.sum(np.abs(g[e] * d))), (gen.__name__, along)
     ctx.close(); ctx64.close()
+
+
+@pytest.mark.parametrize("proc", [IN.GG_TT, IN.GG_TTG, IN.GG_TTGG, IN.GG_TTGGG])
+def test_mixed_evaluate_gradient_matches_fp64(proc, pdf_grid):
+    """The mixed-precision reverse sweep against the FP64 one: every component of
+    d|M|^2/dp within 1e-5 of the event's largest component."""
+    phys = PHYS[proc]
+    rng = np.random.default_rng(70 + proc)
+    nf = IN.N_EXT[proc] - 2
+    moms = []
+    for rs in (600.0, 1500.0, 4000.0):
+        for _ in range(4):
+            pf, _ = O.rambo(nf, rs, [phys.mt, phys.mt] + [0.0] * (nf - 2), rng.random(4 * nf))
+            moms.append(np.vstack([[[rs / 2, 0, 0, rs / 2], [rs / 2, 0, 0, -rs / 2]], pf]))
+    P = torch.tensor(np.array(moms), device="cuda")
+    _, g64 = ctx_for(proc, 0, pdf_grid).evaluate_grad(proc, P)
+    _, g32 = ctx_for(proc, 1, pdf_grid).evaluate_grad(proc, P)
+    g64, g32 = g64.cpu().numpy(), g32.cpu().numpy()
+    for e in range(len(moms)):
+        scale = np.abs(g64[e]).max()
+        assert np.abs(g32[e] - g64[e]).max() <= 1e-5 * scale, (e, float(np.abs(g32[e] - g64[e]).max() / scale))
 
 
 def test_gg_tt_pathwise_derivative_matches_quadrature(pdf_grid):

@@ -59,7 +59,7 @@ def test_event_parity(proc, prec, pdf_grid, opdf):
     for i in flips:
         assert cut_margin(proc, phys, ref["plab"][i]) < 1e-9, f"mask flip far from threshold at event {i}"
     same = mk == ref["mask"]
-    b_me, b_w = fp64_event_bounds(proc, phys, opdf, ref) if prec == 0 else (None, None)
+    b_me, b_w = fp64_event_bounds(proc, phys, opdf, ref, ev["momenta"].cpu().numpy()) if prec == 0 else (None, None)
     w = ev["w"].cpu().numpy()
     assert_fp_parity(rel_err(w[same], ref["w"][same]), prec, "w", b_w[same] if prec == 0 else None)
     me = ev["me2"].cpu().numpy()
