@@ -471,7 +471,7 @@ int batch_grads(mf_ctx* c, int n_ch, const int* processes, const long long* n_ev
         kp.inv_n = 1.0 / (double)n_events[i];
         kp.grid = c->d_bgrids + (size_t)i * MAX_DIM * (MAX_BINS + 1);
         kp.mask_in = nullptr;
-        const long long want = (n_events[i] + 127) / 128, cap = (long long)c->n_sm * 8;
+        const long long want = (n_events[i] + 127) / 128, cap = (long long)c->n_sm * g->ctas_per_sm;
         const int nblk = (int)(want < cap ? want : cap);
         // the single-process partials buffer: this call is ordered after the caller's
         // stream and synchronises before returning, so nothing else uses it meanwhile

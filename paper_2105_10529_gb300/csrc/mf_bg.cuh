@@ -512,7 +512,7 @@ __device__ double bg_warp_me2(W& w, const float* cs, int crow, const double* pev
 // taken as independent variables of this formula.  a: the warp's adjoint state.
 template <class G, typename R, class W, class A>
 __device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const double* pev, int stride, double mt,
-                               double* dout, const double* dir)
+                               double* dout, const double* dir, bool only_dir = false)
 {
     constexpr int K = G::K, NEXT = K + 2, NHEL = 1 << NEXT, NM = 1 << K;
     constexpr int ROWS = (G::NPERM + 31) / 32;
@@ -633,15 +633,16 @@ __device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const doub
 #undef HEL
         __syncwarp();
     }
-    // tangents through the invariants
-    const int nd = NEXT * 4 + (dir ? 1 : 0);
+    // tangents through the invariants (only_dir: lane 0 carries dir alone)
+    const int nd = only_dir ? 1 : NEXT * 4 + (dir ? 1 : 0);
     if (lane < nd && dout) {
+        const int td = only_dir ? NEXT * 4 : lane;   // the direction this lane carries
         D pd[NEXT][4];
         D mtd(mt, 0.0);
         for (int i = 0; i < NEXT; ++i)
             for (int c = 0; c < 4; ++c)
-                pd[i][c] = D(p[i][c], lane < NEXT * 4 ? ((4 * i + c) == lane ? 1.0 : 0.0) : dir[4 * i + c]);
-        if (lane == NEXT * 4) mtd = D(mt, dir[NEXT * 4]);
+                pd[i][c] = D(p[i][c], td < NEXT * 4 ? ((4 * i + c) == td ? 1.0 : 0.0) : dir[4 * i + c]);
+        if (td == NEXT * 4) mtd = D(mt, dir[NEXT * 4]);
         double g = 0.0;
         for (int msk = 1; msk < NM; ++msk) {
             D P[4] = { D(0.0), D(0.0), D(0.0), D(0.0) };

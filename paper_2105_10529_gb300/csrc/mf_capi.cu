@@ -605,7 +605,7 @@ int integrate_impl(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, l
         KParams kg = kp;
         kg.iteration = first_it + (uint32_t)n_iter;
         kg.mask_in = nullptr;
-        const long long want = (n_events + 127) / 128, cap = (long long)c->n_sm * 8;
+        const long long want = (n_events + 127) / 128, cap = (long long)c->n_sm * gops->ctas_per_sm;
         const int gblk = (int)(want < cap ? want : cap);
         MF_CUDA(c, gops->grad(c->cfg.precision, kg, gblk, c->d_partials, gops->k_as, c->cfg.alpha_s, s));
         finish_pass_kernel<<<1, 32, 4 * sizeof(double), s>>>(c->d_partials, gblk, 1, 2, n_events, 0.0, 0, nullptr,
@@ -723,7 +723,7 @@ int mf_vegas_pass_grad(mf_ctx* c, int process, double sqrt_s, const double* grid
     kp.grid = grid_dev;
     kp.mask_in = mask_in_dev;
     long long want = (n_events + 127) / 128;
-    const long long cap = (long long)c->n_sm * 8;
+    const long long cap = (long long)c->n_sm * g->ctas_per_sm;
     const int nblk = (int)(want < cap ? want : cap);
     MF_CUDA(c, g->grad(c->cfg.precision, kp, nblk, c->d_partials, g->k_as, c->cfg.alpha_s, c->stream));
     finish_pass_kernel<<<1, 32, 4 * sizeof(double), c->stream>>>(c->d_partials, nblk, 1, 2, n_events, 0.0, 0, nullptr,

@@ -52,6 +52,32 @@ struct GradOpsTable {
     bool has_fp64;     // FP64 (Dual<double>) derivative pass built
     bool has_fp64_evaluate;   // FP64 d|M|^2/dp built (evaluate_grad)
     bool has_pass = true;     // the derivative pass of the integrand (grad) exists
+    int ctas_per_sm = 8;      // the largest grid the derivative pass takes: this many CTAs per SM
+};
+
+// The derivative pass by the reverse sweep (gluon processes with the recursion's tables G):
+// two 128-thread CTAs per SM at most (their staging shares the per-SM record regions)
+template <class P, class G, int SYM_DEN>
+struct BgGradPass {
+    static cudaError_t grad(int prec, const KParams& kp, int nblk, double* partials, int k_as, double alpha_s,
+                            cudaStream_t s)
+    {
+        if (kp.inv_rec == nullptr || nblk > 2 * kp.inv_ctas) return cudaErrorInvalidValue;
+        static bool attr = false;
+        const size_t s32 = bg_grad_pass_smem<P, G, float>(MAX_BINS), s64 = bg_grad_pass_smem<P, G, double>(MAX_BINS);
+        if (!attr) {
+            cudaError_t e = cudaFuncSetAttribute((const void*)bg_grad_kernel<P, G, float, SYM_DEN>,
+                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32);
+            if (e == cudaSuccess)
+                e = cudaFuncSetAttribute((const void*)bg_grad_kernel<P, G, double, SYM_DEN>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        if (prec) bg_grad_kernel<P, G, float, SYM_DEN><<<nblk, 128, bg_grad_pass_smem<P, G, float>(kp.nb), s>>>(kp, partials, k_as, alpha_s);
+        else bg_grad_kernel<P, G, double, SYM_DEN><<<nblk, 128, bg_grad_pass_smem<P, G, double>(kp.nb), s>>>(kp, partials, k_as, alpha_s);
+        return cudaGetLastError();
+    }
 };
 
 const GradOpsTable* grad_gg_tt();

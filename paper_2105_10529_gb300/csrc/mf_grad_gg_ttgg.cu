@@ -1,5 +1,5 @@
-// Derivative kernels of the process gg_ttgg (the m_t derivative pass in forward mode, d|M|^2/dp
-// by the reverse sweep), in a translation
+// Derivative kernels of the process gg_ttgg (the m_t derivative pass and d|M|^2/dp by the
+// reverse sweep), in a translation
 // unit of their own so that they compile in parallel with the value kernels.
 #include "mf_dispatch.cuh"
 #include "generated/me_gg_ttgg.cuh"
@@ -8,10 +8,11 @@
 namespace mf {
 namespace {
 using P = ProcTops<Me_gg_ttgg>;
-using G = GradOps<P, Me_gg_ttgg, false>;
 // d|M|^2/dp by the reverse sweep of the Berends-Giele recursion (FP64 and mixed)
 using E = BgEvalGrad<BgGen_gg_ttgg, 2>;
-const GradOpsTable kGrad = { &G::grad, &E::launch, 4, false, true };
+// the m_t derivative pass by the reverse sweep as well (FP64 and mixed)
+using B = BgGradPass<P, BgGen_gg_ttgg, 2>;
+const GradOpsTable kGrad = { &B::grad, &E::launch, 4, true, true, true, 2 };
 }  // namespace
 
 const GradOpsTable* grad_gg_ttgg() { return &kGrad; }

@@ -13,6 +13,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <type_traits>
+#include "mf_bg.cuh"
 #include "mf_device.cuh"
 #include "mf_helas.cuh"
 #include "mf_tc.cuh"
@@ -1016,6 +1017,115 @@ __global__ void __launch_bounds__(128) grad_kernel(KParams kp, double* partials,
         for (int w = 0; w < WARPS; ++w) v += sred[4 * w + tid];
         partials[(size_t)blockIdx.x * 4 + tid] = v;
     }
+}
+
+// Derivative pass of a gluon process with the reverse sweep (G: the recursion's tables,
+// SYM_DEN its identical-gluon factor): each thread carries one event's kinematics with
+// the m_t tangent (Dual<double>: the parton map, RAMBO's mass rescaling, the scale and the
+// PDFs), the events that pass are staged with their momenta and tangents in this CTA's
+// region of kp.inv_rec, and warp w evaluates events w, w + 4, ... of the round: |M|^2 and
+// its derivative along (dp/dm_t, dm_t = 1) by one reverse sweep (bg_warp_grad).  Per CTA
+// the same four sums as grad_kernel, reduced deterministically.
+template <class P, class G, typename R, int SYM_DEN>
+__global__ void __launch_bounds__(128) bg_grad_kernel(KParams kp, double* partials, int k_as, double alpha_s)
+{
+    using S = Dual<double>;
+    constexpr int D = P::D, NEXT = P::NEXT, NW = NEXT * 4, TPB = 128, WARPS = TPB / 32, CROW = G::NPERM + 1;
+    static_assert((2 * NW + 2) * TPB <= LH_INV_WORDS_MAX * LH_TPB / 4, "staging fits half a record region");
+    extern __shared__ __align__(128) unsigned char mf_bgp_smem[];
+    const size_t cbytes = ((sizeof(float) * G::NPERM * CROW) + 127) & ~(size_t)127;
+    const size_t wbytes = (sizeof(BgGradWarp<G, R>) + 15) & ~(size_t)15;
+    float* cs = reinterpret_cast<float*>(mf_bgp_smem);
+    double* sgrid = reinterpret_cast<double*>(mf_bgp_smem + cbytes + WARPS * wbytes);
+    double* sres = sgrid + D * (kp.nb + 1);            // [TPB][2]: |M|^2 and its derivative
+    double* sdir = sres + 2 * TPB;                      // [WARPS][NW + 1]: a warp's direction
+    double* sred = sdir + WARPS * (NW + 1);             // [WARPS][4]
+    int* smask = reinterpret_cast<int*>(sred + 4 * WARPS);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (kp.inv_rec == nullptr || (int)(blockIdx.x >> 1) >= kp.inv_ctas) {
+        // the host launches at most two CTAs per region; a larger grid is an error, not a skip
+        if (tid == 0 && kp.dev_err) atomicExch(kp.dev_err, 1u);
+        if (tid < 4) partials[(size_t)blockIdx.x * 4 + tid] = 0.0;
+        return;
+    }
+    // two CTAs share one region of the record buffer, each taking half of it
+    double* grec = reinterpret_cast<double*>(kp.inv_rec + (size_t)(blockIdx.x >> 1) * LH_INV_WORDS_MAX * LH_TPB) +
+                   (blockIdx.x & 1) * (LH_INV_WORDS_MAX * LH_TPB / 4);
+    for (int i = tid; i < G::NPERM * G::NPERM; i += TPB) cs[(i / G::NPERM) * CROW + i % G::NPERM] = __ldg(G::colour() + i);
+    for (int i = tid; i < D * (kp.nb + 1); i += TPB) sgrid[i] = kp.grid[i];
+    __syncthreads();
+    auto& st = *reinterpret_cast<BgGradWarp<G, R>*>(mf_bgp_smem + cbytes + warp * wbytes);
+    double norm = 1.0 / (256.0 * SYM_DEN);
+    for (int i = 0; i < G::K; ++i) norm *= kp.gs * kp.gs;
+    double acc[4] = { 0.0, 0.0, 0.0, 0.0 };
+    const long long n = kp.n_events;
+    const S mt(kp.mt, 1.0);
+    for (long long base = (long long)blockIdx.x * TPB; base < n; base += (long long)gridDim.x * TPB) {
+        const long long e = base + tid;
+        int pass = 0;
+        S pref = S(0.0);
+        if (e < n) {
+            EventOut<D> o;
+            S pm[NEXT][4];
+            kinematics_tops_t<P, S>(kp, sgrid, kp.pdf, (unsigned long long)(kp.ev_offset + e), mt, o, pm, pref);
+            pass = o.mask;
+            if (pass) {
+#pragma unroll
+                for (int f = 0; f < NW; ++f) {
+                    grec[(size_t)f * TPB + tid] = pm[f >> 2][f & 3].v;
+                    grec[(size_t)(NW + f) * TPB + tid] = pm[f >> 2][f & 3].d;
+                }
+            }
+        }
+        smask[tid] = pass;
+        __syncthreads();
+        for (int j = warp; j < TPB; j += WARPS) {
+            if (!smask[j]) continue;                    // the same j for the whole warp
+            for (int f = lane; f < NW; f += 32) sdir[warp * (NW + 1) + f] = grec[(size_t)(NW + f) * TPB + j];
+            if (lane == 0) sdir[warp * (NW + 1) + NW] = 1.0;
+            __syncwarp();
+            double dme = 0.0;
+            const double v = bg_warp_grad<G, R>(st.w, st.a, cs, CROW, grec + j, TPB, kp.mt, &dme,
+                                                sdir + warp * (NW + 1), true);
+            if (lane == 0) { sres[2 * j] = v * norm; sres[2 * j + 1] = dme * norm; }
+            __syncwarp();
+        }
+        __syncthreads();
+        if (pass) {
+            const double me = sres[2 * tid], dme = sres[2 * tid + 1];
+            const double w = pref.v * me, dw = pref.d * me + pref.v * dme;
+            if (isfinite(w) && isfinite(dw)) {
+                const double wn = w * kp.inv_n, dn = dw * kp.inv_n;
+                acc[0] += wn;
+                acc[1] += dn;
+                acc[2] += dn * dn;
+                acc[3] += k_as * wn / alpha_s;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        double v = acc[k];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0) sred[4 * warp + k] = v;
+    }
+    __syncthreads();
+    if (tid < 4) {
+        double v = 0.0;
+        for (int w = 0; w < WARPS; ++w) v += sred[4 * w + tid];
+        partials[(size_t)blockIdx.x * 4 + tid] = v;
+    }
+}
+
+template <class P, class G, typename R>
+inline size_t bg_grad_pass_smem(int nb)
+{
+    constexpr int NW = P::NEXT * 4;
+    const size_t cbytes = ((sizeof(float) * G::NPERM * (G::NPERM + 1)) + 127) & ~(size_t)127;
+    const size_t wbytes = (sizeof(BgGradWarp<G, R>) + 15) & ~(size_t)15;
+    return cbytes + 4 * wbytes + sizeof(double) * (P::D * (nb + 1) + 2 * 128 + 4 * (NW + 1) + 16) + sizeof(int) * 128;
 }
 
 // d|M|^2 / d p for every momentum component (the components treated as

@@ -87,9 +87,9 @@ const ProcOps kOps = { P::D, P::NEXT, P::NPDF, &smem, &prepare, &occupancy, &int
 const ProcOps* ops_gg_ttggg() { return &kOps; }
 
 namespace {
-cudaError_t no_grad_pass(int, const KParams&, int, double*, int, double, cudaStream_t) { return cudaErrorNotSupported; }
-// d|M|^2/dp by the reverse sweep; no m_t derivative pass of the integrand
-const GradOpsTable kGrad = { &no_grad_pass, &BgEvalGrad<BgGen_gg_ttggg, 6>::launch, 5, false, true, false };
+// d|M|^2/dp and the m_t derivative pass by the reverse sweep (FP64 and mixed)
+const GradOpsTable kGrad = { &BgGradPass<P, BgGen_gg_ttggg, 6>::grad, &BgEvalGrad<BgGen_gg_ttggg, 6>::launch, 5, true,
+                             true, true, 2 };
 }  // namespace
 const GradOpsTable* grad_gg_ttggg() { return &kGrad; }
 }  // namespace mf

@@ -15,7 +15,7 @@ from tests.gpu_common import PHYS, random_grid
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-K_AS = {IN.GG_TT: 2, IN.GG_TTG: 3, IN.GG_TTGG: 4}
+K_AS = {IN.GG_TT: 2, IN.GG_TTG: 3, IN.GG_TTGG: 4, IN.GG_TTGGG: 5}
 
 
 @pytest.fixture(scope="module")
@@ -25,7 +25,7 @@ def pdf_grid():
 
 def ctx_for(proc, prec, pdf_grid):
     from paper_2105_10529_gb300.api import Context
-    return Context(PHYS[proc], pdf_grid, precision=prec)
+    return Context(PHYS.get(proc, IN.Physics(seed=6)), pdf_grid, precision=prec)
 
 
 def gpu_fd(ctx, proc, phys, grid, n, mask, h, it):
@@ -38,11 +38,12 @@ def gpu_fd(ctx, proc, phys, grid, n, mask, h, it):
     return (vals[0] - vals[1]) / (2 * h)
 
 
-@pytest.mark.parametrize("proc,prec", [(IN.GG_TT, 0), (IN.GG_TTG, 0), (IN.GG_TT, 1), (IN.GG_TTG, 1), (IN.GG_TTGG, 1)])
+@pytest.mark.parametrize("proc,prec", [(IN.GG_TT, 0), (IN.GG_TTG, 0), (IN.GG_TT, 1), (IN.GG_TTG, 1), (IN.GG_TTGG, 0),
+                                       (IN.GG_TTGG, 1), (IN.GG_TTGGG, 0), (IN.GG_TTGGG, 1)])
 def test_mt_and_alphas_derivatives(proc, prec, pdf_grid):
-    phys = PHYS[proc]
+    phys = PHYS.get(proc, IN.Physics(seed=6))
     grid = torch.tensor(random_grid(IN.DIM[proc], seed=20 + proc), device="cuda")
-    n = {IN.GG_TT: 20000, IN.GG_TTG: 4000, IN.GG_TTGG: 1000}[proc]
+    n = {IN.GG_TT: 20000, IN.GG_TTG: 4000, IN.GG_TTGG: 1000, IN.GG_TTGGG: 300}[proc]
     it = 6
     ctx = ctx_for(proc, prec, pdf_grid)
     d = ctx.vegas_pass_grad(proc, phys.sqrt_s, grid, n, iteration=it).cpu().numpy()
@@ -58,12 +59,15 @@ def test_mt_and_alphas_derivatives(proc, prec, pdf_grid):
     ctx.close(); ctx64.close()
 
 
-@pytest.mark.parametrize("proc", [IN.GG_TT, IN.GG_TTG])
+@pytest.mark.parametrize("proc", [IN.GG_TT, IN.GG_TTG, IN.GG_TTGG, IN.GG_TTGGG])
 def test_mt_derivative_matches_oracle_fd(proc, pdf_grid):
-    phys = PHYS[proc]
+    """The FP64 derivative pass (forward tangents for g g -> t tbar (g), the
+    reverse sweep for g g -> t tbar g g (g)) against central differences of the
+    oracle's pass with the masks frozen, to 1e-4."""
+    phys = PHYS.get(proc, IN.Physics(seed=6))
     gnp = random_grid(IN.DIM[proc], seed=30 + proc)
     grid = torch.tensor(gnp, device="cuda")
-    n = 3000 if proc == IN.GG_TT else 600
+    n = {IN.GG_TT: 3000, IN.GG_TTG: 600, IN.GG_TTGG: 200, IN.GG_TTGGG: 48}[proc]
     it = 2
     ctx = ctx_for(proc, 0, pdf_grid)
     d = ctx.vegas_pass_grad(proc, phys.sqrt_s, grid, n, iteration=it).cpu().numpy()
@@ -77,11 +81,11 @@ def test_mt_derivative_matches_oracle_fd(proc, pdf_grid):
     ctx.close()
 
 
-@pytest.mark.parametrize("proc", [IN.GG_TT, IN.GG_TTG])
+@pytest.mark.parametrize("proc", [IN.GG_TT, IN.GG_TTG, IN.GG_TTGG, IN.GG_TTGGG])
 def test_mixed_derivative_matches_fp64(proc, pdf_grid):
-    phys = PHYS[proc]
+    phys = PHYS.get(proc, IN.Physics(seed=6))
     grid = torch.tensor(random_grid(IN.DIM[proc], seed=40 + proc), device="cuda")
-    n = 20000
+    n = {IN.GG_TTGG: 4000, IN.GG_TTGGG: 1000}.get(proc, 20000)
     a = ctx_for(proc, 0, pdf_grid).vegas_pass_grad(proc, phys.sqrt_s, grid, n, iteration=3).cpu().numpy()
     b = ctx_for(proc, 1, pdf_grid).vegas_pass_grad(proc, phys.sqrt_s, grid, n, iteration=3).cpu().numpy()
     assert abs(b[1] / a[1] - 1) < 1e-5

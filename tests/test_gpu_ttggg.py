@@ -138,11 +138,9 @@ def test_full_size_pass_sampled_against_oracle(pdf_grid, opdf):
     ctx.close()
 
 
-def test_not_in_batches_and_no_derivative(pdf_grid):
+def test_not_in_batches(pdf_grid):
     from paper_2105_10529_gb300._lib import MfError
     ctx = ctx_for(1, pdf_grid)
     with pytest.raises(MfError):
         ctx.integrate_batch([IN.GG_TT, PROC], [1000, 1000], PHYS.sqrt_s, 1)
-    with pytest.raises(MfError):
-        ctx.integrate(PROC, PHYS.sqrt_s, 1000, 1, want_grads=True)
     ctx.close()
