@@ -65,7 +65,7 @@ def parse():
     ap.add_argument("--only-timed", action="store_true",
                     help="run only the warm-up and timed mixed-precision steps (for profiler captures)")
     ap.add_argument("--process", default="gg_ttgg",
-                    choices=["gg_tt", "uu_tt", "gg_ttg", "ug_ttu", "gg_ttgg"],
+                    choices=["gg_tt", "uu_tt", "gg_ttg", "ug_ttu", "gg_ttgg", "gg_ttggg"],
                     help="process of the timed steps with --only-timed (the benchmark line is gg_ttgg)")
     return ap.parse_args()
 
@@ -188,7 +188,37 @@ def run_batch(ctx, phys, IN, n_iter):
                                     "sequential_sigma_pb": q["sigma"]} for p, c, q in zip(procs, chans, seq)},
             "dsigma_dmt_pb_per_gev": float(g[-1, 1]), "dsigma_dmt_error": float(g[-1, 2]),
             "dsigma_dalphas_pb": float(g[-1, 3]),
-            "timing": "host wall clock around the synchronous C-ABI call (graph launch, reductions, host results)"}
+            "timing": "host wall clock around the synchronous C-ABI call (graph launch, reductions, host results)",
+            "small_channels": run_small_batch(ctx, phys, IN)}
+
+
+def run_small_batch(ctx, phys, IN, n_iter=5, reps=5):
+    """Many small, uneven channels (eight channels of 5e3 .. 6e4 events, five iterations):
+    where launch gaps and per-kernel tails dominate, one graph-replayed batch call against
+    the same channels one mf_integrate call after another (each itself graph-replayed);
+    best of reps calls each, after warm-up calls, autotuned batch schedule."""
+    procs = [IN.GG_TT, IN.UU_TT, IN.GG_TTG, IN.UG_TTU, IN.GG_TTGG, IN.GG_TT, IN.UG_TTU, IN.GG_TTG]
+    ns = [60000, 20000, 30000, 10000, 5000, 40000, 15000, 8000]
+    choice = ctx.autotune_batch(procs, ns, phys.sqrt_s)
+    ctx.set_batch_schedule(*choice)
+    ctx.integrate_batch(procs, ns, phys.sqrt_s, n_iter)
+    t_b = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        ctx.integrate_batch(procs, ns, phys.sqrt_s, n_iter)
+        t_b.append(time.perf_counter() - t0)
+    for p, n in zip(procs, ns):
+        ctx.integrate(p, phys.sqrt_s, n, n_iter)
+    t_s = []
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        for p, n in zip(procs, ns):
+            ctx.integrate(p, phys.sqrt_s, n, n_iter)
+        t_s.append(time.perf_counter() - t0)
+    ev = sum(ns) * n_iter
+    return {"channels": len(procs), "events_per_iteration": ns, "iterations": n_iter,
+            "batch_events_per_s": ev / min(t_b), "sequential_events_per_s": ev / min(t_s),
+            "speedup_vs_sequential": min(t_s) / min(t_b), "schedule": list(choice)}
 
 
 def run_configs(pdf, IN, MF_FP64, MF_MIXED, stream):
@@ -287,7 +317,7 @@ def run_derivatives(ctx, phys, IN, grid, stream):
     mg = mom[:n_g].contiguous()
     t, _ = timed(lambda: ctx.evaluate_grad(IN.GG_TTGG, mg))
     out["evaluate_with_dme2_dp_gg_ttgg"] = {"points": n_g, "points_per_s": n_g / t, "s": t,
-                                            "note": "forward mode: one tangent evaluation per momentum component (24)"}
+                                            "note": "reverse sweep of the Berends-Giele recursion per helicity, tangents through the invariants"}
     return out
 
 
@@ -469,7 +499,7 @@ def run_ours(args):
     proc = IN.GG_TTGG
     if args.only_timed:
         proc = {"gg_tt": IN.GG_TT, "uu_tt": IN.UU_TT, "gg_ttg": IN.GG_TTG, "ug_ttu": IN.UG_TTU,
-                "gg_ttgg": IN.GG_TTGG}[args.process]
+                "gg_ttgg": IN.GG_TTGG, "gg_ttggg": IN.GG_TTGGG}[args.process]
     phys = IN.Physics(seed=3)
     pdf = IN.make_pdf_grid()
     n_ext, dim = process_info(proc)

@@ -398,7 +398,8 @@ __device__ __forceinline__ void bg_event_invariants(W& w, const double (&p)[K + 
         double q[4];
         for (int c = 0; c < 4; ++c) { w.P[msk][c] = R(P[c]); q[c] = p[2][c] - P[c]; w.Q[msk][c] = R(q[c]); }
         w.iP2[msk] = __popc(msk) >= 2 ? R(1.0 / mdot(P, P)) : R(0);
-        w.iQ[msk] = R(1.0 / (mdot(q, q) - mt * mt));
+        // every gluon absorbed leaves q = -p_tbar, on its mass shell: no propagator there
+        w.iQ[msk] = msk != (1 << K) - 1 ? R(1.0 / (mdot(q, q) - mt * mt)) : R(0);
     }
     if (lane < K) {
         double a[3], b[3];
@@ -657,7 +658,7 @@ __device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const doub
                 g += P[c].d * double(a.Pb[msk][c]) + q[c].d * double(a.Qb[msk][c]);
             }
             if (__popc(msk) >= 2) g += (1.0 / mdot(P, P)).d * double(a.iP2b[msk]);
-            g += (1.0 / (mdot(q, q) - mtd * mtd)).d * double(a.iQb[msk]);
+            if (msk != NM - 1) g += (1.0 / (mdot(q, q) - mtd * mtd)).d * double(a.iQb[msk]);
         }
         for (int gl = 0; gl < K; ++gl) {
             D e1[3], e2[3];

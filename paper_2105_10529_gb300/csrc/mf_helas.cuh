@@ -426,9 +426,39 @@ template <typename S> __device__ __forceinline__ S mdot(const S* a, const S* b)
 }
 
 // Transverse basis of a massless momentum p (e1, e2 spatial parts, scaled by 1/sqrt 2).
+// For a Dual momentum the values are those of the plain basis and the tangents those of
+// the parallel-transported basis, de = -(e . dn) n with n = p/|p|: the helicity-summed
+// |M|^2 does not depend on the choice of transverse basis, and the transported one is
+// smooth where the plain one is not (a momentum along the z axis, whose azimuth is
+// undefined).
+template <typename S>
+__device__ __forceinline__ void gluon_basis(const S* p, S* e1, S* e2);
+
+template <typename T>
+__device__ __forceinline__ void gluon_basis_dual(const Dual<T>* p, Dual<T>* e1, Dual<T>* e2)
+{
+    const T pv[4] = { p[0].v, p[1].v, p[2].v, p[3].v };
+    T a[3], b[3];
+    gluon_basis(pv, a, b);
+    const T pa = sqrt(pv[1] * pv[1] + pv[2] * pv[2] + pv[3] * pv[3]);
+    const T n[3] = { pv[1] / pa, pv[2] / pa, pv[3] / pa };
+    const T ndp = n[0] * p[1].d + n[1] * p[2].d + n[2] * p[3].d;
+    const T dn[3] = { (p[1].d - n[0] * ndp) / pa, (p[2].d - n[1] * ndp) / pa, (p[3].d - n[2] * ndp) / pa };
+    const T ca = a[0] * dn[0] + a[1] * dn[1] + a[2] * dn[2];
+    const T cb = b[0] * dn[0] + b[1] * dn[1] + b[2] * dn[2];
+    for (int j = 0; j < 3; ++j) {
+        e1[j] = Dual<T>(a[j], -ca * n[j]);
+        e2[j] = Dual<T>(b[j], -cb * n[j]);
+    }
+}
+
 template <typename S>
 __device__ __forceinline__ void gluon_basis(const S* p, S* e1, S* e2)
 {
+    if constexpr (is_dual<S>::value) {
+        gluon_basis_dual(p, e1, e2);
+        return;
+    }
     const double r2 = 0.70710678118654752440;
     const S pt2 = p[1] * p[1] + p[2] * p[2];
     const S pa = sqrt(pt2 + p[3] * p[3]);

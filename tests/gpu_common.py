@@ -15,6 +15,7 @@ PHYS = {
     IN.GG_TTGG: IN.Physics(seed=3),
     IN.UU_TT: IN.Physics(seed=4, channel=1),
     IN.UG_TTU: IN.Physics(seed=5, channel=3),
+    IN.GG_TTGGG: IN.Physics(seed=6),
 }
 
 
