@@ -467,6 +467,45 @@ __device__ __forceinline__ R bg_colour_sum(W& w, const float* cs, int crow, int 
     return part;
 }
 
+// The same colour sum from the upper triangle of the symmetric C:
+//   sum_{s t} A*_s C_st A_t = sum_s Re A*_s (C_ss A_s + 2 sum_{t > s} C_st A_t),
+// half the multiply-adds.  The rows are paired as (s, N - 1 - s), so every lane walks N - 1
+// entries of the triangle in one loop (the two rows one after the other).
+template <class G, typename R, class W>
+__device__ __forceinline__ R bg_colour_sum_sym(W& w, const float* cs, int crow, int lane)
+{
+    constexpr int N = G::NPERM, NPAIR = (N + 1) / 2;
+    R part = R(0);
+    // Re A*_s (C_ss A_s + 2 y) for row s with its upper-triangle sum y
+    auto row_term = [&](int sr, R yr, R yi) {
+        const R d = R(cs[sr * crow + sr]);
+        part = fma(w.A[sr].r, fma(d, w.A[sr].r, R(2) * yr), fma(w.A[sr].i, fma(d, w.A[sr].i, R(2) * yi), part));
+    };
+    for (int pr = lane; pr < NPAIR; pr += 32) {
+        const int s1 = pr, s2 = N - 1 - pr;
+        const int n1 = N - 1 - s1;                       // entries right of the diagonal in row s1
+        const int len = s2 > s1 ? N - 1 : n1;            // both rows, or the middle row of an odd N
+        R yr = R(0), yi = R(0);
+        int srow = s1, t = s1 + 1;
+        for (int k = 0; k < len; ++k) {
+            if (k == n1) {                               // row s1 done: its term, then row s2
+                row_term(srow, yr, yi);
+                yr = R(0); yi = R(0);
+                srow = s2; t = s2 + 1;
+            }
+            const R c = R(cs[srow * crow + t]);
+            yr = fma(c, w.A[t].r, yr);
+            yi = fma(c, w.A[t].i, yi);
+            ++t;
+        }
+        row_term(srow, yr, yi);
+        if (s2 > s1 && srow == s1) row_term(s2, R(0), R(0));   // row N - 1: the diagonal alone
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    return part;
+}
+
 // Sum over helicities of sum_{sigma tau} A*_sigma C_{sigma tau} A_tau / COLOUR_DEN for one
 // event, by the whole warp (couplings and averages not applied).  pev: the event's FP64
 // momenta, component 4 i + c of particle i at pev[(4 i + c) stride].  all_hel: every
@@ -491,7 +530,7 @@ __device__ double bg_warp_me2(W& w, const float* cs, int crow, const double* pev
         G::template forward<R>(w, lane);
         bg_closures<G, R>(w, lane);
         __syncwarp();
-        const R part = bg_colour_sum<G, R>(w, cs, crow, lane, (cx<R>*)nullptr);
+        const R part = bg_colour_sum_sym<G, R>(w, cs, crow, lane);
         if (hel_out && lane == 0) hel_out[ih] = double(part) * hel_scale;
         total += part;
         __syncwarp();
@@ -645,25 +684,51 @@ __device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const doub
                 pd[i][c] = D(p[i][c], td < NEXT * 4 ? ((4 * i + c) == td ? 1.0 : 0.0) : dir[4 * i + c]);
         if (td == NEXT * 4) mtd = D(mt, dir[NEXT * 4]);
         double g = 0.0;
-        for (int msk = 1; msk < NM; ++msk) {
-            D P[4] = { D(0.0), D(0.0), D(0.0), D(0.0) };
-            for (int i = 0; i < K; ++i)
-                if (msk >> i & 1) {
-                    const int e = i < 2 ? i : i + 2;
-                    for (int c = 0; c < 4; ++c) P[c] = i < 2 ? P[c] + pd[e][c] : P[c] - pd[e][c];
+        {
+            // the subset invariants in the working precision R, with explicit derivatives:
+            // dP = sum of +-dp, d(1/P^2) = -2 (P.dP) / P^4, dQ = dp_t - dP,
+            // d(1/(Q^2 - m^2)) = -2 (Q.dQ - m dm) / (Q^2 - m^2)^2, the inverses from the
+            // FP64-computed values kept in w
+            R gr = R(0);
+            const R dmt = R(mtd.d);
+            for (int msk = 1; msk < NM; ++msk) {
+                R dP[4] = { R(0), R(0), R(0), R(0) };
+                for (int i = 0; i < K; ++i)
+                    if (msk >> i & 1) {
+                        const int e = i < 2 ? i : i + 2;
+                        for (int c = 0; c < 4; ++c) dP[c] = i < 2 ? dP[c] + R(pd[e][c].d) : dP[c] - R(pd[e][c].d);
+                    }
+                R dQ[4];
+                for (int c = 0; c < 4; ++c) {
+                    dQ[c] = R(pd[2][c].d) - dP[c];
+                    gr = fma(dP[c], a.Pb[msk][c], fma(dQ[c], a.Qb[msk][c], gr));
                 }
-            D q[4];
-            for (int c = 0; c < 4; ++c) {
-                q[c] = pd[2][c] - P[c];
-                g += P[c].d * double(a.Pb[msk][c]) + q[c].d * double(a.Qb[msk][c]);
+                if (__popc(msk) >= 2) {
+                    const R ip = w.iP2[msk];
+                    gr = fma(R(-2) * mdot(w.P[msk], dP) * ip * ip, a.iP2b[msk], gr);
+                }
+                if (msk != NM - 1) {
+                    const R iq = w.iQ[msk];
+                    gr = fma(R(-2) * (mdot(w.Q[msk], dQ) - w.mt * dmt) * iq * iq, a.iQb[msk], gr);
+                }
             }
-            if (__popc(msk) >= 2) g += (1.0 / mdot(P, P)).d * double(a.iP2b[msk]);
-            if (msk != NM - 1) g += (1.0 / (mdot(q, q) - mtd * mtd)).d * double(a.iQb[msk]);
+            g = double(gr);
         }
         for (int gl = 0; gl < K; ++gl) {
-            D e1[3], e2[3];
-            gluon_basis(pd[gl < 2 ? gl : gl + 2], e1, e2);
-            for (int j = 0; j < 3; ++j) g += e1[j].d * double(a.e1b[gl][j]) + e2[j].d * double(a.e2b[gl][j]);
+            // parallel-transported basis tangent: de = -(e . dn) n (see gluon_basis)
+            const D* q = pd[gl < 2 ? gl : gl + 2];
+            const double pa = sqrt(q[1].v * q[1].v + q[2].v * q[2].v + q[3].v * q[3].v);
+            const double n[3] = { q[1].v / pa, q[2].v / pa, q[3].v / pa };
+            const double ndp = n[0] * q[1].d + n[1] * q[2].d + n[2] * q[3].d;
+            const double dn[3] = { (q[1].d - n[0] * ndp) / pa, (q[2].d - n[1] * ndp) / pa, (q[3].d - n[2] * ndp) / pa };
+            double c1 = 0.0, c2 = 0.0, b1 = 0.0, b2 = 0.0;
+            for (int j = 0; j < 3; ++j) {
+                c1 += double(w.e1[gl][j]) * dn[j];
+                c2 += double(w.e2[gl][j]) * dn[j];
+                b1 += n[j] * double(a.e1b[gl][j]);
+                b2 += n[j] * double(a.e2b[gl][j]);
+            }
+            g -= c1 * b1 + c2 * b2;
         }
         {
             const FermionBasis<D> f3 = fermion_basis<D>(pd[2], mtd), f4 = fermion_basis<D>(pd[3], mtd);
