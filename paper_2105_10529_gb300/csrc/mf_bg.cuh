@@ -780,40 +780,53 @@ __global__ void __launch_bounds__(128) bg_evaluate_grad_kernel(const double* __r
 }
 
 template <class G, typename R>
-inline size_t bg_grad_smem(int warps)
+constexpr size_t bg_grad_smem_bytes(int warps)
 {
-    const size_t cbytes = ((sizeof(float) * G::NPERM * (G::NPERM + 1)) + 127) & ~(size_t)127;
-    const size_t wbytes = (sizeof(BgGradWarp<G, R>) + 15) & ~(size_t)15;
-    return cbytes + (size_t)warps * wbytes;
+    return (((sizeof(float) * G::NPERM * (G::NPERM + 1)) + 127) & ~(size_t)127) +
+           (size_t)warps * ((sizeof(BgGradWarp<G, R>) + 15) & ~(size_t)15);
 }
+template <class G, typename R>
+inline size_t bg_grad_smem(int warps) { return bg_grad_smem_bytes<G, R>(warps); }
 
 
 // host launcher of bg_evaluate_grad_kernel for a gluon process with tables G and
 // symmetry factor 1/SYM_DEN: |M|^2 averaged over the initial spins and colours (1/256)
+// largest number of warps (1 .. 4) whose states and the colour matrix fit 227 KB of shared memory
+template <class G, typename R>
+constexpr int bg_grad_warps()
+{
+    constexpr size_t cap = 227 * 1024;
+    int w = 4;
+    while (w > 1 && bg_grad_smem_bytes<G, R>(w) > cap) --w;
+    return w;
+}
+
 template <class G, int SYM_DEN>
 struct BgEvalGrad {
-    static constexpr int WARPS = 4;
-    static cudaError_t launch(int prec, const double* mom, long long n, double* me2, double* dme2, double mt, double gs,
-                              int, cudaStream_t s)
+    template <typename R>
+    static cudaError_t run(const double* mom, long long n, double* me2, double* dme2, double mt, double norm,
+                           cudaStream_t s)
     {
-        static bool attr = false;
-        const size_t s32 = bg_grad_smem<G, float>(WARPS), s64 = bg_grad_smem<G, double>(WARPS);
+        constexpr int W = bg_grad_warps<G, R>();
+        const size_t sm = bg_grad_smem<G, R>(W);
+        static bool attr = false;   // per precision
         if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute((const void*)bg_evaluate_grad_kernel<G, float>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute((const void*)bg_evaluate_grad_kernel<G, double>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64);
+            const cudaError_t e = cudaFuncSetAttribute((const void*)bg_evaluate_grad_kernel<G, R>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
             if (e != cudaSuccess) return e;
             attr = true;
         }
+        const long long want = (n + W - 1) / W;
+        const int nblk = (int)(want < 8192 ? want : 8192);
+        bg_evaluate_grad_kernel<G, R><<<nblk, 32 * W, sm, s>>>(mom, n, me2, dme2, mt, norm);
+        return cudaGetLastError();
+    }
+    static cudaError_t launch(int prec, const double* mom, long long n, double* me2, double* dme2, double mt, double gs,
+                              int, cudaStream_t s)
+    {
         double norm = 1.0 / (256.0 * SYM_DEN);
         for (int i = 0; i < G::K; ++i) norm *= gs * gs;
-        const long long want = (n + WARPS - 1) / WARPS;
-        const int nblk = (int)(want < 8192 ? want : 8192);
-        if (prec) bg_evaluate_grad_kernel<G, float><<<nblk, 32 * WARPS, s32, s>>>(mom, n, me2, dme2, mt, norm);
-        else bg_evaluate_grad_kernel<G, double><<<nblk, 32 * WARPS, s64, s>>>(mom, n, me2, dme2, mt, norm);
-        return cudaGetLastError();
+        return prec ? run<float>(mom, n, me2, dme2, mt, norm, s) : run<double>(mom, n, me2, dme2, mt, norm, s);
     }
 };
 

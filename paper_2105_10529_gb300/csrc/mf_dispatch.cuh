@@ -59,24 +59,27 @@ struct GradOpsTable {
 // two 128-thread CTAs per SM at most (their staging shares the per-SM record regions)
 template <class P, class G, int SYM_DEN>
 struct BgGradPass {
+    template <typename R>
+    static cudaError_t run(const KParams& kp, int nblk, double* partials, int k_as, double alpha_s, cudaStream_t s)
+    {
+        constexpr int MW = bg_grad_pass_warps<P, G, R>();
+        static bool attr = false;   // per precision
+        if (!attr) {
+            const cudaError_t e = cudaFuncSetAttribute((const void*)bg_grad_kernel<P, G, R, SYM_DEN, MW>,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                       (int)bg_grad_pass_smem<P, G, R>(MAX_BINS, MW));
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        bg_grad_kernel<P, G, R, SYM_DEN, MW><<<nblk, 128, bg_grad_pass_smem<P, G, R>(kp.nb, MW), s>>>(kp, partials, k_as,
+                                                                                                      alpha_s);
+        return cudaGetLastError();
+    }
     static cudaError_t grad(int prec, const KParams& kp, int nblk, double* partials, int k_as, double alpha_s,
                             cudaStream_t s)
     {
         if (kp.inv_rec == nullptr || nblk > 2 * kp.inv_ctas) return cudaErrorInvalidValue;
-        static bool attr = false;
-        const size_t s32 = bg_grad_pass_smem<P, G, float>(MAX_BINS), s64 = bg_grad_pass_smem<P, G, double>(MAX_BINS);
-        if (!attr) {
-            cudaError_t e = cudaFuncSetAttribute((const void*)bg_grad_kernel<P, G, float, SYM_DEN>,
-                                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s32);
-            if (e == cudaSuccess)
-                e = cudaFuncSetAttribute((const void*)bg_grad_kernel<P, G, double, SYM_DEN>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s64);
-            if (e != cudaSuccess) return e;
-            attr = true;
-        }
-        if (prec) bg_grad_kernel<P, G, float, SYM_DEN><<<nblk, 128, bg_grad_pass_smem<P, G, float>(kp.nb), s>>>(kp, partials, k_as, alpha_s);
-        else bg_grad_kernel<P, G, double, SYM_DEN><<<nblk, 128, bg_grad_pass_smem<P, G, double>(kp.nb), s>>>(kp, partials, k_as, alpha_s);
-        return cudaGetLastError();
+        return prec ? run<float>(kp, nblk, partials, k_as, alpha_s, s) : run<double>(kp, nblk, partials, k_as, alpha_s, s);
     }
 };
 

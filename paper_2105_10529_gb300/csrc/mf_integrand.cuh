@@ -1026,9 +1026,11 @@ __global__ void __launch_bounds__(128) grad_kernel(KParams kp, double* partials,
 // region of kp.inv_rec, and warp w evaluates events w, w + 4, ... of the round: |M|^2 and
 // its derivative along (dp/dm_t, dm_t = 1) by one reverse sweep (bg_warp_grad).  Per CTA
 // the same four sums as grad_kernel, reduced deterministically.
-template <class P, class G, typename R, int SYM_DEN>
+template <class P, class G, typename R, int SYM_DEN, int MW>
 __global__ void __launch_bounds__(128) bg_grad_kernel(KParams kp, double* partials, int k_as, double alpha_s)
 {
+    // MW: the warps with a recursion state (as many as fit the shared memory); every warp
+    // runs the kinematics, warps w < MW the matrix elements
     using S = Dual<double>;
     constexpr int D = P::D, NEXT = P::NEXT, NW = NEXT * 4, TPB = 128, WARPS = TPB / 32, CROW = G::NPERM + 1;
     static_assert((2 * NW + 2) * TPB <= LH_INV_WORDS_MAX * LH_TPB / 4, "staging fits half a record region");
@@ -1036,7 +1038,7 @@ __global__ void __launch_bounds__(128) bg_grad_kernel(KParams kp, double* partia
     const size_t cbytes = ((sizeof(float) * G::NPERM * CROW) + 127) & ~(size_t)127;
     const size_t wbytes = (sizeof(BgGradWarp<G, R>) + 15) & ~(size_t)15;
     float* cs = reinterpret_cast<float*>(mf_bgp_smem);
-    double* sgrid = reinterpret_cast<double*>(mf_bgp_smem + cbytes + WARPS * wbytes);
+    double* sgrid = reinterpret_cast<double*>(mf_bgp_smem + cbytes + MW * wbytes);
     double* sres = sgrid + D * (kp.nb + 1);            // [TPB][2]: |M|^2 and its derivative
     double* sdir = sres + 2 * TPB;                      // [WARPS][NW + 1]: a warp's direction
     double* sred = sdir + WARPS * (NW + 1);             // [WARPS][4]
@@ -1054,7 +1056,7 @@ __global__ void __launch_bounds__(128) bg_grad_kernel(KParams kp, double* partia
     for (int i = tid; i < G::NPERM * G::NPERM; i += TPB) cs[(i / G::NPERM) * CROW + i % G::NPERM] = __ldg(G::colour() + i);
     for (int i = tid; i < D * (kp.nb + 1); i += TPB) sgrid[i] = kp.grid[i];
     __syncthreads();
-    auto& st = *reinterpret_cast<BgGradWarp<G, R>*>(mf_bgp_smem + cbytes + warp * wbytes);
+    auto& st = *reinterpret_cast<BgGradWarp<G, R>*>(mf_bgp_smem + cbytes + (warp < MW ? warp : 0) * wbytes);
     double norm = 1.0 / (256.0 * SYM_DEN);
     for (int i = 0; i < G::K; ++i) norm *= kp.gs * kp.gs;
     double acc[4] = { 0.0, 0.0, 0.0, 0.0 };
@@ -1079,7 +1081,7 @@ __global__ void __launch_bounds__(128) bg_grad_kernel(KParams kp, double* partia
         }
         smask[tid] = pass;
         __syncthreads();
-        for (int j = warp; j < TPB; j += WARPS) {
+        for (int j = warp; warp < MW && j < TPB; j += MW) {
             if (!smask[j]) continue;                    // the same j for the whole warp
             for (int f = lane; f < NW; f += 32) sdir[warp * (NW + 1) + f] = grec[(size_t)(NW + f) * TPB + j];
             if (lane == 0) sdir[warp * (NW + 1) + NW] = 1.0;
@@ -1120,12 +1122,18 @@ __global__ void __launch_bounds__(128) bg_grad_kernel(KParams kp, double* partia
 }
 
 template <class P, class G, typename R>
-inline size_t bg_grad_pass_smem(int nb)
+constexpr size_t bg_grad_pass_smem(int nb, int mw)
 {
-    constexpr int NW = P::NEXT * 4;
-    const size_t cbytes = ((sizeof(float) * G::NPERM * (G::NPERM + 1)) + 127) & ~(size_t)127;
-    const size_t wbytes = (sizeof(BgGradWarp<G, R>) + 15) & ~(size_t)15;
-    return cbytes + 4 * wbytes + sizeof(double) * (P::D * (nb + 1) + 2 * 128 + 4 * (NW + 1) + 16) + sizeof(int) * 128;
+    return bg_grad_smem_bytes<G, R>(mw) +
+           sizeof(double) * (P::D * (nb + 1) + 2 * 128 + 4 * (P::NEXT * 4 + 1) + 16) + sizeof(int) * 128;
+}
+// recursion warps of the derivative pass: as many (1 .. 4) as fit 227 KB with a 64-bin grid
+template <class P, class G, typename R>
+constexpr int bg_grad_pass_warps()
+{
+    int w = 4;
+    while (w > 1 && bg_grad_pass_smem<P, G, R>(MAX_BINS, w) > 227 * 1024) --w;
+    return w;
 }
 
 // d|M|^2 / d p for every momentum component (the components treated as
