@@ -36,7 +36,7 @@ FP64_PEAK_NOMINAL_TFLOPS = 1.25
 # default schedule (warp per event, tensor-core colour sum), from the dram__bytes counters of
 # the capture in profiles/integrand_gg_ttgg_mixed_1m_ncu.txt (over 1e6 events; the traffic,
 # evicted local-memory lines, grows with the number of events)
-DRAM_BYTES_PER_EVENT_P3 = 3809.2
+DRAM_BYTES_PER_EVENT_P3 = 4235.4
 
 
 def parse():
@@ -402,6 +402,25 @@ def run_ttggg(pdf, IN, MF_FP64, MF_MIXED, stream, n_mixed, fma32):
                     "achieved_tflops": ach, "frac_of_fp32_peak": ach / (SM_COUNT * FP32_LANES_PER_SM * 2 * SM_MAX_MHZ / 1e6),
                     "frac_of_measured_fma_peak": ach / fma32, "sigma_2_iterations_pb": r["sigma"],
                     "error_pb": r["error"]}
+    # helicity sampling: pass time and per-event weight variance against the full sum on the
+    # same events; the time to a given error scales as time x variance
+    _, evf = ctx.vegas_pass(p, phys.sqrt_s, grid, 50_000, iteration=56, want_events=True, fields=("w",))
+    var_full = float(evf["w"].var().item())
+    samp = {}
+    for ns in (8, 1):
+        ctx.set_helicity_sampling(ns, 1)
+        _, evs_ = ctx.vegas_pass(p, phys.sqrt_s, grid, 50_000, iteration=56, want_events=True, fields=("w",))
+        var_s = float(evs_["w"].var().item())
+        torch.cuda.synchronize()
+        e0.record(stream)
+        ctx.vegas_pass(p, phys.sqrt_s, grid, n_mixed, iteration=52)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts = e0.elapsed_time(e1) / 1e3
+        samp[str(ns)] = {"events_per_s": n_mixed / ts, "speedup": t32 / ts, "weight_variance_ratio": var_s / var_full,
+                         "time_to_equal_error_gain": (t32 / ts) / (var_s / var_full)}
+    ctx.set_helicity_sampling(0)
+    out["mixed"]["helicity_sampling"] = {"configurations_of_64": samp, "variance_sample_events": 50_000}
     ctx.close()
     n64 = max(2000, n_mixed // 50)
     ctx64 = Context(phys, pdf, precision=MF_FP64, stream=stream)

@@ -199,6 +199,27 @@ int mf_get_observable(struct mf_ctx *ctx, double *hist_host, double *err_host, d
  * MF_ERR_ARG for other values. */
 int mf_set_helicity_split(struct mf_ctx *ctx, int parts);
 
+/* Helicity sampling (the paper's matrix element sums every helicity
+ * configuration, Sec. 2.2; sampling them is a variance-for-cost trade of the
+ * Monte Carlo that keeps its expectation): n_samples = 0 (the default) sums
+ * them all; n_samples = 1, 2, 4, ..., 32 makes each event of g g -> t tbar g g g
+ * evaluate n_samples of the 64 parity-halved configurations instead, one drawn
+ * uniformly from each of n_samples equal strata of consecutive configurations
+ * (configuration 2j + 1, j = 0 .. 63, stands for the pair {2j + 1, 126 - 2j}),
+ * weighted by the stratum size 64 / n_samples.  The per-event |M|^2 is then an
+ * unbiased estimate of the summed one, and the cross section's expectation is
+ * unchanged while its variance grows.  The draws are reproducible: stratum s
+ * of event e takes bits [s b, (s + 1) b) (b = log2(64 / n_samples)) of
+ * Philox4x32-10 (Salmon et al. 2011) at counter (e lo, e hi, iteration,
+ * channel << 8 | 0xFF), a counter block no VEGAS dimension uses, with the key
+ * (seed lo ^ 0x68656C69 ^ stream, seed hi); `stream` selects independent draws
+ * over the same events.  n_samples = 64 is the full sum.  Applies to
+ * mf_integrate, mf_integrate_grid and mf_vegas_pass (its per-event |M|^2 is
+ * the estimate); mf_evaluate, mf_helicity_profile, the derivative calls, the
+ * batch calls and mf_vegas_pass_static always sum every configuration, and
+ * so do the other processes.  MF_ERR_ARG for other values. */
+int mf_set_helicity_sampling(struct mf_ctx *ctx, int n_samples, unsigned int stream);
+
 /* Synchronises the context's stream and reports whether a bounded device-side
  * wait ran out since the last check (MF_ERR_TIMEOUT; the flag is cleared) or
  * not (MF_OK).  mf_integrate makes the same check before returning. */

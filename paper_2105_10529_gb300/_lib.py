@@ -72,6 +72,7 @@ def lib():
             "mf_set_pdf": (C.c_int, [vp, dp]),
             "mf_set_schedule": (C.c_int, [vp, C.c_int]),
             "mf_set_helicity_split": (C.c_int, [vp, C.c_int]),
+            "mf_set_helicity_sampling": (C.c_int, [vp, C.c_int, C.c_uint]),
             "mf_set_observable": (C.c_int, [vp, C.POINTER(MfObs)]),
             "mf_get_observable": (C.c_int, [vp, dp, dp, dp]),
             "mf_device_status": (C.c_int, [vp]),
@@ -111,7 +112,7 @@ def lib():
 
 def exported_symbols():
     return ["mf_default_config", "mf_process_info", "mf_create", "mf_destroy", "mf_last_error",
-            "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_set_helicity_split", "mf_set_observable", "mf_get_observable", "mf_device_status", "mf_selftest_wait", "mf_integrate", "mf_integrate_grid", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate", "mf_helicity_profile",
+            "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_set_helicity_split", "mf_set_helicity_sampling", "mf_set_observable", "mf_get_observable", "mf_device_status", "mf_selftest_wait", "mf_integrate", "mf_integrate_grid", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate", "mf_helicity_profile",
             "mf_vegas_pass_static", "mf_set_couplings", "mf_vegas_pass_grad",
             "mf_integrate_batch", "mf_batch_pass", "mf_batch_grad", "mf_set_batch_schedule", "mf_autotune_batch",
             "mf_measure_fma_peak"]

@@ -102,6 +102,11 @@ class Context:
         """Threads per event of the heavy integrand (1 or 2), as mf_set_helicity_split."""
         _check(self.ptr, _lib.lib().mf_set_helicity_split(self.ptr, parts))
 
+    def set_helicity_sampling(self, n_samples: int, stream: int = 0):
+        """Helicity configurations sampled per event of g g -> t tbar g g g (0: the full sum), and
+        the stream of the draws, as mf_set_helicity_sampling."""
+        _check(self.ptr, _lib.lib().mf_set_helicity_sampling(self.ptr, int(n_samples), int(stream) & 0xFFFFFFFF))
+
     def set_observable(self, n_bins: int = 0, lo: float = 0.0, hi: float = 0.0):
         """p_T histogram of the first final-state particle for the next integrate calls
         (n_bins = 0 disables), as mf_set_observable."""

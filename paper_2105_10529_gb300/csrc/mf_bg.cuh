@@ -511,20 +511,40 @@ __device__ __forceinline__ R bg_colour_sum_sym(W& w, const float* cs, int crow, 
 // momenta, component 4 i + c of particle i at pev[(4 i + c) stride].  all_hel: every
 // configuration (else one of each parity pair, doubled); hel_out (nullable, all_hel):
 // each configuration's value times hel_scale, written by lane 0.
+//
+// Helicity sampling (nsamp > 0, a power of two dividing NHEL / 2): instead of every
+// configuration of the parity-halved sum, the warp evaluates nsamp of them, one drawn
+// uniformly from each of nsamp strata of NHEL / (2 nsamp) consecutive configurations with the
+// bits of rnd (four random words of the event), each weighted by the stratum size: an
+// unbiased estimate of the helicity sum (nsamp = NHEL / 2 is the full sum itself).
 template <class G, typename R, class W>
 __device__ double bg_warp_me2(W& w, const float* cs, int crow, const double* pev, int stride, double mt, bool all_hel,
-                              double* hel_out, double hel_scale)
+                              double* hel_out, double hel_scale, int nsamp = 0, uint4 rnd = uint4{ 0u, 0u, 0u, 0u })
 {
-    constexpr int K = G::K, NEXT = K + 2, NHEL = 1 << NEXT;
+    constexpr int K = G::K, NEXT = K + 2, NHEL = 1 << NEXT, HALF = NHEL / 2;
     const int lane = threadIdx.x & 31;
     double p[NEXT][4];
     for (int f = 0; f < NEXT * 4; ++f) p[f >> 2][f & 3] = pev[(size_t)f * stride];
     bg_event_invariants<K, R>(w, p, mt, lane);
     __syncwarp();
     R total = R(0);
+    const bool sample = nsamp > 0 && !all_hel;
     const int h0 = all_hel ? 0 : 1, hstep = all_hel ? 1 : 2;
+    const int nloop = sample ? nsamp : (all_hel ? NHEL : HALF);
+    const int ssize = sample ? HALF / nsamp : 1;          // configurations per stratum
+    const int sbits = sample ? __ffs(ssize) - 1 : 0;      // random bits per draw
 #pragma unroll 1
-    for (int ih = h0; ih < NHEL; ih += hstep) {
+    for (int it = 0; it < nloop; ++it) {
+        int ih;
+        if (sample) {
+            // draw it: bits [it sbits, (it + 1) sbits) of the 128 random bits
+            const int b0 = it * sbits;
+            const uint32_t wd = b0 < 32 ? rnd.x : (b0 < 64 ? rnd.y : (b0 < 96 ? rnd.z : rnd.w));
+            const int r = sbits ? (int)((wd >> (b0 & 31)) & ((1u << sbits) - 1u)) : 0;
+            ih = 1 + 2 * (it * ssize + r);
+        } else {
+            ih = h0 + hstep * it;
+        }
         bg_external_states<K, R>(w, ih, lane);
         __syncwarp();
         G::template forward<R>(w, lane);
@@ -535,7 +555,7 @@ __device__ double bg_warp_me2(W& w, const float* cs, int crow, const double* pev
         total += part;
         __syncwarp();
     }
-    return double(total) * (all_hel ? 1.0 : 2.0) / G::COLOUR_DEN;
+    return double(total) * (all_hel ? 1.0 : 2.0) * double(ssize) / G::COLOUR_DEN;
 }
 
 

@@ -218,6 +218,11 @@ int make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KPara
     kp.kin_ctas = c->kin_ctas;
     kp.inv_rec = c->d_inv;
     kp.inv_ctas = c->inv_ctas;
+    // sampling as many configurations as the sum has is the sum itself
+    if (c->hel_samples > 0 && c->hel_samples < ops->hel_sample_max) {
+        kp.hel_samples = c->hel_samples;
+        kp.hel_stream = c->hel_stream;
+    }
     return MF_OK;
 }
 
@@ -437,6 +442,14 @@ int mf_set_helicity_split(mf_ctx* c, int parts)
 {
     if (!c || (parts != 1 && parts != 2)) return MF_ERR_ARG;
     c->hsplit = parts;
+    return MF_OK;
+}
+
+int mf_set_helicity_sampling(mf_ctx* c, int n_samples, unsigned int stream)
+{
+    if (!c || n_samples < 0 || n_samples > 64 || (n_samples & (n_samples - 1))) return MF_ERR_ARG;
+    c->hel_samples = n_samples;
+    c->hel_stream = stream;
     return MF_OK;
 }
 

@@ -28,6 +28,8 @@ struct mf_ctx {
     int max_blocks = 0;
     int sched = 3;                   // integrand schedule (see mf_set_schedule)
     int hsplit = 1;                  // lanes per event in the heavy integrand (see mf_set_helicity_split)
+    int hel_samples = 0;             // sampled helicity configurations per event (mf_set_helicity_sampling)
+    uint32_t hel_stream = 0;         // stream of the helicity draws
     // observable histogram (mf_set_observable): n bins from obs_lo, obs_inv_w = n / (hi - lo)
     int obs_n = 0;
     double obs_lo = 0.0, obs_hi = 0.0, obs_inv_w = 0.0;

@@ -30,6 +30,9 @@ struct ProcOps {
     cudaError_t (*profile)(int prec, const double* mom, long long n, double* out, double mt, double gs,
                            const EwParams& ew, int nblk, cudaStream_t s);
     int nhel;
+    // helicity sampling in the integrand (mf_set_helicity_sampling): the size of the helicity sum
+    // it samples from (the parity-halved configurations), 0 where the integrand does not sample
+    int hel_sample_max;
 };
 
 // helicity-profile launch of a matrix element with a hel_profile member

@@ -72,7 +72,19 @@ struct KParams {
     // benchmark times is the kernel whose events a parity test reads
     double* ev_u; double* ev_x; uint8_t* ev_bins; double* ev_w; uint8_t* ev_mask; double* ev_me2; double* ev_p;
     int ev_out;
+    // helicity sampling of the warp-level matrix elements (0: the full helicity sum): configurations
+    // per event, drawn from a Philox stream of its own (counter block 0xFF, key offset by hel_stream)
+    int hel_samples;
+    uint32_t hel_stream;
 };
+
+// the four random words of an event's helicity draws: counter (event lo, event hi, iteration,
+// channel << 8 | 0xFF), a block no VEGAS dimension uses, under the seed key offset by the stream
+__device__ __forceinline__ uint4 helicity_draw_words(const KParams& kp, unsigned long long ev)
+{
+    const uint4 c = make_uint4((uint32_t)ev, (uint32_t)(ev >> 32), kp.iteration, (kp.channel << 8) | 0xFFu);
+    return philox4x32_10(c, make_uint2(kp.key.x ^ 0x68656C69u ^ kp.hel_stream, kp.key.y));
+}
 
 // Observable bin of an event: 0 below obs_lo (and for a non-finite p_T), nobs + 1 at or
 // above the upper edge, else 1 + floor((p_T - obs_lo) obs_inv_w).  p_T of particle 2
@@ -650,23 +662,27 @@ __device__ __forceinline__ double lh_batch_me2(const KParams& kp, unsigned char*
 // event's |M|^2 (meaningful where mine).
 template <class P, typename R, int TPB>
 __device__ __forceinline__ double bg_batch_me2(const KParams& kp, unsigned char* smem_raw, double* sme, int take,
-                                               bool mine, const double (&pm)[P::NEXT][4])
+                                               bool mine, const double (&pm)[P::NEXT][4], unsigned long long ev)
 {
     using ME = typename P::Me;
     constexpr int WARPS = TPB / 32;
-    static_assert(P::NEXT * 4 * TPB <= LH_INV_WORDS_MAX * LH_TPB / 2, "momenta fit the CTA's record region");
+    static_assert((P::NEXT * 4 + 1) * TPB <= LH_INV_WORDS_MAX * LH_TPB / 2, "momenta fit the CTA's record region");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     double* grec = reinterpret_cast<double*>(kp.inv_rec + (size_t)blockIdx.x * LH_INV_WORDS_MAX * LH_TPB);
     if (mine) {
 #pragma unroll
         for (int f = 0; f < P::NEXT * 4; ++f) grec[(size_t)f * TPB + tid] = pm[f >> 2][f & 3];
+        grec[(size_t)P::NEXT * 4 * TPB + tid] = __longlong_as_double((long long)ev);   // the event number
     }
     __syncthreads();
     const float* cs = reinterpret_cast<const float*>(smem_raw);
     auto& w = *reinterpret_cast<typename ME::template Warp<R>*>(smem_raw + ME::colour_bytes() +
                                                                 (size_t)warp * ME::template warp_bytes<R>());
     for (int j = warp; j < take; j += WARPS) {
-        const double v = ME::template warp_me2<R>(w, cs, grec + j, TPB, kp.mt, false, nullptr, 0.0);
+        uint4 rnd = make_uint4(0u, 0u, 0u, 0u);
+        if (kp.hel_samples > 0)
+            rnd = helicity_draw_words(kp, (unsigned long long)__double_as_longlong(grec[(size_t)P::NEXT * 4 * TPB + j]));
+        const double v = ME::template warp_me2<R>(w, cs, grec + j, TPB, kp.mt, false, nullptr, 0.0, kp.hel_samples, rnd);
         if (lane == 0) sme[j] = v;
     }
     __syncthreads();
@@ -830,7 +846,8 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             double me;
             if constexpr (P::BG) {
                 static_assert(HS == 1 && !LH && !TC, "warp-level matrix element: its own schedule");
-                me = bg_batch_me2<P, R, TPB>(kp, smem_raw, svbuf, take, mine, pm);
+                me = bg_batch_me2<P, R, TPB>(kp, smem_raw, svbuf, take, mine, pm,
+                                             (unsigned long long)(kp.ev_offset + e));
             } else if constexpr (LH) {
                 me = lh_batch_me2<P, R, TPB>(kp, smem_raw, tc, svbuf, take, mine, pm);
             } else if constexpr (TC) {

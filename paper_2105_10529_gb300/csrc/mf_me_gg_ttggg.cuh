@@ -41,9 +41,10 @@ struct Me_gg_ttggg {
     // event, by the whole warp (bg_warp_me2; couplings and averages: norm())
     template <typename R>
     __device__ static double warp_me2(Warp<R>& w, const float* cs, const double* pev, int stride, double mt,
-                                      bool all_hel, double* hel_out, double hel_scale)
+                                      bool all_hel, double* hel_out, double hel_scale, int nsamp = 0,
+                                      uint4 rnd = uint4{ 0u, 0u, 0u, 0u })
     {
-        return bg_warp_me2<BgGen_gg_ttggg, R>(w, cs, CROW, pev, stride, mt, all_hel, hel_out, hel_scale);
+        return bg_warp_me2<BgGen_gg_ttggg, R>(w, cs, CROW, pev, stride, mt, all_hel, hel_out, hel_scale, nsamp, rnd);
     }
     // couplings, averages and symmetry factor that turn warp_me2 into the averaged |M|^2
     __host__ __device__ static double norm(double gs)

@@ -81,7 +81,7 @@ cudaError_t profile(int prec, const double* mom, long long n, double* out, doubl
 }
 
 const ProcOps kOps = { P::D, P::NEXT, P::NPDF, &smem, &prepare, &occupancy, &integrand, &evaluate, &kernel,
-                       &profile, ME::NHEL };
+                       &profile, ME::NHEL, ME::NHEL / 2 };
 }  // namespace
 
 const ProcOps* ops_gg_ttggg() { return &kOps; }

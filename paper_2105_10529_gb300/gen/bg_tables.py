@@ -228,7 +228,8 @@ BG_FLOPS = dict(
 def helicity_flops(k: int) -> dict:
     """Algorithmic FLOPs of one helicity configuration of the recursion: the
     gluon currents, the top line, the closures and the colour sum
-    sum_{sigma tau} A*_sigma C_{sigma tau} A_tau (two real quadratic forms)."""
+    sum_{sigma tau} A*_sigma C_{sigma tau} A_tau (two real quadratic forms of the
+    symmetric C, counted over its upper triangle: one multiply-add per pair and form)."""
     t = build(k)
     n_v3 = sum(lv["n"] * (m - 1) for m, lv in t["levels"].items())
     n_v4 = sum(lv["n"] * (m - 1) * (m - 2) // 2 for m, lv in t["levels"].items())
@@ -239,7 +240,7 @@ def helicity_flops(k: int) -> dict:
     n = len(t["perms"])
     f = dict(v3=n_v3 * BG_FLOPS["v3"], v4=n_v4 * BG_FLOPS["v4"], scale=n_cur * BG_FLOPS["scale"],
              top=n_top * BG_FLOPS["top_term"] + n_prop * BG_FLOPS["top_prop"], closure=n_clo * BG_FLOPS["closure"],
-             colour=n * n * 2 * 2 + n * 4)
+             colour=n * (n + 1) * 2 + n * 4)
     f["total"] = sum(f.values())
     f["counts"] = dict(v3=n_v3, v4=n_v4, currents=n_cur, top_terms=n_top, top_props=n_prop, closure_terms=n_clo)
     return f
