@@ -42,14 +42,15 @@ struct BgGen_gg_tt {
         __syncwarp();
     }
     // the reverse sweep: adjoints of the currents (a.Jb, a.Ub, a.Vb from the closures)
-    // and of the per-event invariants, level by level downwards: top-line level m with
-    // gluon level m + 1 (each pushes only to lower levels)
-    template <typename R, class W, class A> __device__ static void reverse(const W& w, A& a, int lane)
+    // and of the per-event invariants (into the lane's registers gi), level by level
+    // downwards: top-line level m with gluon level m + 1 (each pushes only to lower levels)
+    template <typename R, class W, class A, class I>
+    __device__ static void reverse(const W& w, A& a, I& gi, int lane)
     {
         namespace T = bg_gg_tt;
         for (int t = lane; t < T::NJ2 + T::NU1; t += 32) {
-            if (t < T::NJ2) bg_gluon_current_adj<R, 2, 0>(w, a, t, T::JOFF2, T::j2_mask, &T::j2_v3[0][0][0], &T::j2_v3m[0][0][0], nullptr);
-            else bg_top_current_adj<R, 1>(w, a, t - T::NJ2, T::UOFF1, T::u1_mask, &T::u1_terms[0][0][0]);
+            if (t < T::NJ2) bg_gluon_current_adj<R, 2, 0>(w, a, gi, t, T::JOFF2, T::j2_mask, &T::j2_v3[0][0][0], &T::j2_v3m[0][0][0], nullptr);
+            else bg_top_current_adj<R, 1>(w, a, gi, t - T::NJ2, T::UOFF1, T::u1_mask, &T::u1_terms[0][0][0]);
         }
         __syncwarp();
     }

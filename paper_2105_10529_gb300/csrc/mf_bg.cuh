@@ -59,6 +59,12 @@ template <typename R> __device__ __forceinline__ void w4_cxpy(W4<R>& y, cx<R> a,
     for (int m = 0; m < 4; ++m) y.c[m] = cfma(a, x.c[m], y.c[m]);
 }
 template <typename R> __device__ __forceinline__ R ref_sign(uint16_t r) { return (r & 0x8000u) ? R(-1) : R(1); }
+// butterfly step of a warp sum, for plain and dual numbers
+template <typename T> __device__ __forceinline__ T shfl_xor_r(T v, int off) { return __shfl_xor_sync(0xffffffffu, v, off); }
+template <typename T> __device__ __forceinline__ Dual<T> shfl_xor_r(const Dual<T>& v, int off)
+{
+    return Dual<T>(__shfl_xor_sync(0xffffffffu, v.v, off), __shfl_xor_sync(0xffffffffu, v.d, off));
+}
 __device__ __forceinline__ int ref_id(uint16_t r) { return (int)(r & 0x7FFFu); }
 
 // row spinor times Jslash: (a, b) Jslash = (b Sigmabar(J), a Sigma(J))
@@ -151,20 +157,56 @@ __device__ __forceinline__ void bg_top_current(W& w, int c, int uoff, const uint
 // colour- and helicity-summed |M|^2.  A holomorphic multilinear map w(x, y, ..)
 // passes xb += conj(dw/dx) wb; a real parameter s of w = s z gets
 // sb += Re(wb conj(z)).  Adjoints that several lanes add to (the currents of lower
-// levels, the per-event invariants) are accumulated with shared-memory atomics.
+// levels) are accumulated with shared-memory atomics; those of the per-event invariants
+// in each lane's registers (BgInvAcc).
 
 template <typename R, int K, int NJ, int NU>
 struct BgAdj {
     W4<R> Jb[NJ];                      // adjoints of the gluon currents (helicity being summed)
     W4<R> Ub[NU];                      // adjoints of the top-line currents
     W4<R> Vb;                          // adjoint of v(p_tbar)
-    // adjoints of the per-event invariants, summed over helicities
-    R Pb[1 << K][4], iP2b[1 << K], Qb[1 << K][4], iQb[1 << K];
+    // adjoints of the polarisation and spinor pieces, summed over helicities (one lane each)
     R e1b[K][3], e2b[K][3];
     cx<R> chi3b[2][2], chi4b[2][2];
     R om3b[2], om4b[2];
-    R mtb;
 };
+
+// The adjoints of the subset invariants (P_S, 1/P_S^2, Q_S = p_t - P_S, 1/(Q_S^2 - m_t^2) and
+// the propagators' m_t) pushed on at once to the external momenta and m_t, in the lane's
+// registers: gp[e][c] = dL/dp_e^c and gmt = dL/dm_t through the invariants, summed over
+// the lane's terms and helicities (the warp adds its lanes up once per event).  This keeps
+// the many currents that share a subset from updating one shared word.
+template <typename R, int K>
+struct BgInvAcc {
+    R gp[K + 2][4];
+    R gmt;
+};
+template <typename R, int K> __device__ __forceinline__ void inv_acc_zero(BgInvAcc<R, K>& g)
+{
+#pragma unroll
+    for (int e = 0; e < K + 2; ++e)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) g.gp[e][c] = R(0);
+    g.gmt = R(0);
+}
+// b: the adjoint of P_S (S = msk; gluon i enters P_S with + if incoming, i < 2, else -)
+template <typename R, int K> __device__ __forceinline__ void inv_acc_P(BgInvAcc<R, K>& g, int msk, const R* b)
+{
+#pragma unroll
+    for (int i = 0; i < K; ++i) {
+        const R s = (msk >> i & 1) ? (i < 2 ? R(1) : R(-1)) : R(0);
+#pragma unroll
+        for (int c = 0; c < 4; ++c) g.gp[i < 2 ? i : i + 2][c] = fma(s, b[c], g.gp[i < 2 ? i : i + 2][c]);
+    }
+}
+// b: the adjoint of Q_S = p_t - P_S
+template <typename R, int K> __device__ __forceinline__ void inv_acc_Q(BgInvAcc<R, K>& g, int msk, const R* b)
+{
+    R nb[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) { g.gp[2][c] += b[c]; nb[c] = -b[c]; }
+    inv_acc_P(g, msk, nb);
+}
 
 template <typename R> __device__ __forceinline__ void atomic_add_cx(cx<R>* d, cx<R> v)
 {
@@ -301,8 +343,8 @@ __device__ __forceinline__ void row_qprop_adj(const W4<R>& x, const R* q, R m, R
 }
 
 // reverse of gluon current c of level M (its adjoint a.Jb[joff + c] complete)
-template <typename R, int M, int NV4, class W, class A>
-__device__ __forceinline__ void bg_gluon_current_adj(const W& w, A& a, int c, int joff, const uint8_t* mask,
+template <typename R, int M, int NV4, class W, class A, class I>
+__device__ __forceinline__ void bg_gluon_current_adj(const W& w, A& a, I& gi, int c, int joff, const uint8_t* mask,
                                                      const uint16_t* v3, const uint8_t* v3m, const uint16_t* v4)
 {
     const int msk = __ldg(mask + c);
@@ -312,7 +354,13 @@ __device__ __forceinline__ void bg_gluon_current_adj(const W& w, A& a, int c, in
     W4<R> accb;
     R ipb = R(0);
     for (int m = 0; m < 4; ++m) { accb.c[m] = cscale(Jb.c[m], ip); ipb += re_mulc(Jb.c[m], Jo.c[m]); }
-    atomicAdd(&a.iP2b[msk], ipb / ip);
+    {
+        // d(1/P^2) = -2 (P.dP) / P^4: the adjoint of P from that of 1/P^2 (ipb / ip)
+        const R f = R(-2) * (ipb / ip) * ip * ip;
+        R pb[4];
+        for (int m = 0; m < 4; ++m) pb[m] = f * R(metric(m)) * w.P[msk][m];
+        inv_acc_P(gi, msk, pb);
+    }
 #pragma unroll
     for (int j = 0; j < M - 1; ++j) {
         const uint16_t ra = __ldg(v3 + (c * (M - 1) + j) * 2), rb = __ldg(v3 + (c * (M - 1) + j) * 2 + 1);
@@ -325,7 +373,8 @@ __device__ __forceinline__ void bg_gluon_current_adj(const W& w, A& a, int c, in
                     k1b, k2b);
         atomic_add_w4(a.Jb[ref_id(ra)], J1b);
         atomic_add_w4(a.Jb[ref_id(rb)], J2b);
-        for (int m = 0; m < 4; ++m) { atomicAdd(&a.Pb[ma][m], k1b[m]); atomicAdd(&a.Pb[mb][m], k2b[m]); }
+        inv_acc_P(gi, ma, k1b);
+        inv_acc_P(gi, mb, k2b);
     }
 #pragma unroll
     for (int j = 0; j < NV4; ++j) {
@@ -342,8 +391,8 @@ __device__ __forceinline__ void bg_gluon_current_adj(const W& w, A& a, int c, in
 
 // reverse of top-line current c of level M (its adjoint a.Ub[uoff + c] complete); the
 // sum before the propagator is recomputed from the stored currents
-template <typename R, int M, class W, class A>
-__device__ __forceinline__ void bg_top_current_adj(const W& w, A& a, int c, int uoff, const uint8_t* mask,
+template <typename R, int M, class W, class A, class I>
+__device__ __forceinline__ void bg_top_current_adj(const W& w, A& a, I& gi, int c, int uoff, const uint8_t* mask,
                                                    const uint16_t* terms)
 {
     W4<R> x = w4_zero<R>();
@@ -359,9 +408,13 @@ __device__ __forceinline__ void bg_top_current_adj(const W& w, A& a, int c, int 
     W4<R> xb = w4_zero<R>();
     R qb[4] = { R(0), R(0), R(0), R(0) }, mb = R(0), sb = R(0);
     row_qprop_adj(x, q, w.mt, s, a.Ub[uoff + c], xb, qb, mb, sb);
-    for (int m = 0; m < 4; ++m) atomicAdd(&a.Qb[msk][m], qb[m]);
-    atomicAdd(&a.iQb[msk], -sb);
-    atomicAdd(&a.mtb, mb);
+    {
+        // s = -1/(Q^2 - m^2): d(1/(Q^2 - m^2)) = -2 (Q.dQ - m dm) / (Q^2 - m^2)^2
+        const R iq = w.iQ[msk], f = R(-2) * (-sb) * iq * iq;
+        for (int m = 0; m < 4; ++m) qb[m] += f * R(metric(m)) * q[m];
+        inv_acc_Q(gi, msk, qb);
+        gi.gmt += mb - f * w.mt;
+    }
 #pragma unroll
     for (int j = 0; j < M; ++j) {
         const int ui = __ldg(terms + (c * M + j) * 2);
@@ -383,26 +436,29 @@ __device__ __forceinline__ void bg_top_current_adj(const W& w, A& a, int c, int 
 // convention: gluons 0 and 1 incoming, the rest outgoing with minus their momenta), the
 // top and the antitop: subset momenta and inverse denominators, one subset per lane,
 // polarisation and spinor bases.  Particle order of p: g, g, t, tbar, g, ...
-template <int K, typename R, class W>
-__device__ __forceinline__ void bg_event_invariants(W& w, const double (&p)[K + 2][4], double mt, int lane)
+//
+// S: the momenta's scalar, double, or Dual<double> for a forward-mode derivative (the
+// invariants of R = Dual<float> or Dual<double> then carry their tangents).
+template <int K, typename R, class W, typename S>
+__device__ __forceinline__ void bg_event_invariants(W& w, const S (&p)[K + 2][4], S mt, int lane)
 {
     const int msk = lane;
     if (msk >= 1 && msk < (1 << K)) {
-        double P[4] = { 0.0, 0.0, 0.0, 0.0 };
+        S P[4] = { S(0.0), S(0.0), S(0.0), S(0.0) };
         for (int i = 0; i < K; ++i)
             if (msk >> i & 1) {
                 const int e = i < 2 ? i : i + 2;
                 const double sg = i < 2 ? 1.0 : -1.0;
                 for (int c = 0; c < 4; ++c) P[c] += sg * p[e][c];
             }
-        double q[4];
+        S q[4];
         for (int c = 0; c < 4; ++c) { w.P[msk][c] = R(P[c]); q[c] = p[2][c] - P[c]; w.Q[msk][c] = R(q[c]); }
         w.iP2[msk] = __popc(msk) >= 2 ? R(1.0 / mdot(P, P)) : R(0);
         // every gluon absorbed leaves q = -p_tbar, on its mass shell: no propagator there
         w.iQ[msk] = msk != (1 << K) - 1 ? R(1.0 / (mdot(q, q) - mt * mt)) : R(0);
     }
     if (lane < K) {
-        double a[3], b[3];
+        S a[3], b[3];
         gluon_basis(p[lane < 2 ? lane : lane + 2], a, b);
         for (int j = 0; j < 3; ++j) { w.e1[lane][j] = R(a[j]); w.e2[lane][j] = R(b[j]); }
     }
@@ -463,7 +519,7 @@ __device__ __forceinline__ R bg_colour_sum(W& w, const float* cs, int crow, int 
         if (yout) yout[s] = mkc(yr, yi);
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    for (int off = 16; off > 0; off >>= 1) part += shfl_xor_r(part, off);
     return part;
 }
 
@@ -502,7 +558,7 @@ __device__ __forceinline__ R bg_colour_sum_sym(W& w, const float* cs, int crow, 
         if (s2 > s1 && srow == s1) row_term(s2, R(0), R(0));   // row N - 1: the diagonal alone
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) part += __shfl_xor_sync(0xffffffffu, part, off);
+    for (int off = 16; off > 0; off >>= 1) part += shfl_xor_r(part, off);
     return part;
 }
 
@@ -558,6 +614,40 @@ __device__ double bg_warp_me2(W& w, const float* cs, int crow, const double* pev
     return double(total) * (all_hel ? 1.0 : 2.0) * double(ssize) / G::COLOUR_DEN;
 }
 
+// One directional derivative of bg_warp_me2's parity-halved sum by forward mode: the whole
+// recursion in dual numbers D = Dual<R> (value and tangent of every current, closure and
+// colour sum), the FP64 momenta pev seeded with the tangents dev (same layout) and m_t with
+// dmt.  One pass per helicity, nothing stored, no reverse sweep: the cheap way to a single
+// direction (the m_t derivative of a pass); the full gradient takes bg_warp_grad.  w: the
+// warp's state in dual numbers.  Returns the value (as bg_warp_me2) and writes the
+// derivative to *dout (every lane).
+template <class G, typename R, class W>
+__device__ double bg_warp_me2_dir(W& w, const float* cs, int crow, const double* pev, const double* dev, int stride,
+                                  double mt, double dmt, double* dout)
+{
+    constexpr int K = G::K, NEXT = K + 2, NHEL = 1 << NEXT;
+    using D = Dual<R>;
+    using S = Dual<double>;
+    const int lane = threadIdx.x & 31;
+    S p[NEXT][4];
+    for (int f = 0; f < NEXT * 4; ++f) p[f >> 2][f & 3] = S(pev[(size_t)f * stride], dev[(size_t)f * stride]);
+    bg_event_invariants<K, D>(w, p, S(mt, dmt), lane);
+    __syncwarp();
+    D total = D(0);
+#pragma unroll 1
+    for (int ih = 1; ih < NHEL; ih += 2) {
+        bg_external_states<K, D>(w, ih, lane);
+        __syncwarp();
+        G::template forward<D>(w, lane);
+        bg_closures<G, D>(w, lane);
+        __syncwarp();
+        total += bg_colour_sum_sym<G, D>(w, cs, crow, lane);
+        __syncwarp();
+    }
+    *dout = double(total.d) * 2.0 / G::COLOUR_DEN;
+    return double(total.v) * 2.0 / G::COLOUR_DEN;
+}
+
 
 // The value of bg_warp_me2 (parity-halved helicity sum, doubled) and its derivatives by a
 // reverse sweep.  For every helicity the warp recomputes the currents forward (nothing is
@@ -581,17 +671,14 @@ __device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const doub
     double p[NEXT][4];
     for (int f = 0; f < NEXT * 4; ++f) p[f >> 2][f & 3] = pev[(size_t)f * stride];
     bg_event_invariants<K, R>(w, p, mt, lane);
-    // the invariants' adjoints start at zero
-    for (int i = lane; i < NM; i += 32) {
-        for (int c = 0; c < 4; ++c) { a.Pb[i][c] = R(0); a.Qb[i][c] = R(0); }
-        a.iP2b[i] = R(0); a.iQb[i] = R(0);
-    }
+    // the invariants' adjoints start at zero (registers), and those of the bases (shared)
+    BgInvAcc<R, K> gi;
+    inv_acc_zero(gi);
     if (lane < K)
         for (int j = 0; j < 3; ++j) { a.e1b[lane][j] = R(0); a.e2b[lane][j] = R(0); }
     if (lane == K) {
         for (int x = 0; x < 4; ++x) { a.chi3b[x >> 1][x & 1] = mkc(R(0), R(0)); a.chi4b[x >> 1][x & 1] = mkc(R(0), R(0)); }
         a.om3b[0] = a.om3b[1] = a.om4b[0] = a.om4b[1] = R(0);
-        a.mtb = R(0);
     }
     __syncwarp();
     R total = R(0);
@@ -659,7 +746,7 @@ __device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const doub
             atomic_add_w4(a.Vb, vb);
         }
         __syncwarp();
-        G::template reverse<R>(w, a, lane);
+        G::template reverse<R>(w, a, gi, lane);
         // external states backwards into the polarisation and spinor pieces (one lane each)
 #define HEL(i) ((ih >> (i)) & 1 ? 1 : -1)
         if (lane < K) {
@@ -693,6 +780,13 @@ __device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const doub
 #undef HEL
         __syncwarp();
     }
+    // the lanes' invariant adjoints added up (every lane gets the sums)
+#pragma unroll
+    for (int f = 0; f < NEXT * 4; ++f)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) gi.gp[f >> 2][f & 3] += __shfl_xor_sync(0xffffffffu, gi.gp[f >> 2][f & 3], off);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) gi.gmt += __shfl_xor_sync(0xffffffffu, gi.gmt, off);
     // tangents through the invariants (only_dir: lane 0 carries dir alone)
     const int nd = only_dir ? 1 : NEXT * 4 + (dir ? 1 : 0);
     if (lane < nd && dout) {
@@ -705,33 +799,12 @@ __device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const doub
         if (td == NEXT * 4) mtd = D(mt, dir[NEXT * 4]);
         double g = 0.0;
         {
-            // the subset invariants in the working precision R, with explicit derivatives:
-            // dP = sum of +-dp, d(1/P^2) = -2 (P.dP) / P^4, dQ = dp_t - dP,
-            // d(1/(Q^2 - m^2)) = -2 (Q.dQ - m dm) / (Q^2 - m^2)^2, the inverses from the
-            // FP64-computed values kept in w
+            // through the subset invariants and the propagators' mass: the adjoints gp, gmt
+            // (working precision R) contracted with the direction
             R gr = R(0);
-            const R dmt = R(mtd.d);
-            for (int msk = 1; msk < NM; ++msk) {
-                R dP[4] = { R(0), R(0), R(0), R(0) };
-                for (int i = 0; i < K; ++i)
-                    if (msk >> i & 1) {
-                        const int e = i < 2 ? i : i + 2;
-                        for (int c = 0; c < 4; ++c) dP[c] = i < 2 ? dP[c] + R(pd[e][c].d) : dP[c] - R(pd[e][c].d);
-                    }
-                R dQ[4];
-                for (int c = 0; c < 4; ++c) {
-                    dQ[c] = R(pd[2][c].d) - dP[c];
-                    gr = fma(dP[c], a.Pb[msk][c], fma(dQ[c], a.Qb[msk][c], gr));
-                }
-                if (__popc(msk) >= 2) {
-                    const R ip = w.iP2[msk];
-                    gr = fma(R(-2) * mdot(w.P[msk], dP) * ip * ip, a.iP2b[msk], gr);
-                }
-                if (msk != NM - 1) {
-                    const R iq = w.iQ[msk];
-                    gr = fma(R(-2) * (mdot(w.Q[msk], dQ) - w.mt * dmt) * iq * iq, a.iQb[msk], gr);
-                }
-            }
+#pragma unroll
+            for (int f = 0; f < NEXT * 4; ++f) gr = fma(gi.gp[f >> 2][f & 3], R(pd[f >> 2][f & 3].d), gr);
+            gr = fma(gi.gmt, R(mtd.d), gr);
             g = double(gr);
         }
         for (int gl = 0; gl < K; ++gl) {
@@ -759,11 +832,14 @@ __device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const doub
                 }
             for (int x = 0; x < 2; ++x) g += f3.om[x].d * double(a.om3b[x]) + f4.om[x].d * double(a.om4b[x]);
         }
-        g += mtd.d * double(a.mtb);
         dout[lane] = g / G::COLOUR_DEN;
     }
     return double(total) * 2.0 / G::COLOUR_DEN;
 }
+
+// state of a warp for one forward-mode direction (bg_warp_me2_dir)
+template <class G, typename R>
+using BgDirWarp = BgWarp<Dual<R>, G::K, G::NJ, G::NU, G::NPERM>;
 
 // state of a warp for the derivative: forward currents and their adjoints
 template <class G, typename R>

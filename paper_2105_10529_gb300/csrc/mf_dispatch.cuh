@@ -58,7 +58,7 @@ struct GradOpsTable {
     int ctas_per_sm = 8;      // the largest grid the derivative pass takes: this many CTAs per SM
 };
 
-// The derivative pass by the reverse sweep (gluon processes with the recursion's tables G):
+// The derivative pass by forward mode through the recursion (gluon processes with its tables G):
 // two 128-thread CTAs per SM at most (their staging shares the per-SM record regions)
 template <class P, class G, int SYM_DEN>
 struct BgGradPass {

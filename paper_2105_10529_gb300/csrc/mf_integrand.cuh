@@ -1036,13 +1036,14 @@ __global__ void __launch_bounds__(128) grad_kernel(KParams kp, double* partials,
     }
 }
 
-// Derivative pass of a gluon process with the reverse sweep (G: the recursion's tables,
-// SYM_DEN its identical-gluon factor): each thread carries one event's kinematics with
-// the m_t tangent (Dual<double>: the parton map, RAMBO's mass rescaling, the scale and the
-// PDFs), the events that pass are staged with their momenta and tangents in this CTA's
-// region of kp.inv_rec, and warp w evaluates events w, w + 4, ... of the round: |M|^2 and
-// its derivative along (dp/dm_t, dm_t = 1) by one reverse sweep (bg_warp_grad).  Per CTA
-// the same four sums as grad_kernel, reduced deterministically.
+// Derivative pass of a gluon process through the recursion (G: its tables, SYM_DEN the
+// identical-gluon factor): each thread carries one event's kinematics with the m_t tangent
+// (Dual<double>: the parton map, RAMBO's mass rescaling, the scale and the PDFs), the
+// events that pass are staged with their momenta and tangents in this CTA's region of
+// kp.inv_rec, and warp w < MW evaluates events w, w + MW, ... of the round: |M|^2 and its
+// derivative along (dp/dm_t, dm_t = 1) in forward mode (bg_warp_me2_dir: one direction,
+// so no reverse sweep).  Per CTA the same four sums as grad_kernel, reduced
+// deterministically.
 template <class P, class G, typename R, int SYM_DEN, int MW>
 __global__ void __launch_bounds__(128) bg_grad_kernel(KParams kp, double* partials, int k_as, double alpha_s)
 {
@@ -1053,12 +1054,11 @@ __global__ void __launch_bounds__(128) bg_grad_kernel(KParams kp, double* partia
     static_assert((2 * NW + 2) * TPB <= LH_INV_WORDS_MAX * LH_TPB / 4, "staging fits half a record region");
     extern __shared__ __align__(128) unsigned char mf_bgp_smem[];
     const size_t cbytes = ((sizeof(float) * G::NPERM * CROW) + 127) & ~(size_t)127;
-    const size_t wbytes = (sizeof(BgGradWarp<G, R>) + 15) & ~(size_t)15;
+    const size_t wbytes = (sizeof(BgDirWarp<G, R>) + 15) & ~(size_t)15;
     float* cs = reinterpret_cast<float*>(mf_bgp_smem);
     double* sgrid = reinterpret_cast<double*>(mf_bgp_smem + cbytes + MW * wbytes);
     double* sres = sgrid + D * (kp.nb + 1);            // [TPB][2]: |M|^2 and its derivative
-    double* sdir = sres + 2 * TPB;                      // [WARPS][NW + 1]: a warp's direction
-    double* sred = sdir + WARPS * (NW + 1);             // [WARPS][4]
+    double* sred = sres + 2 * TPB;                      // [WARPS][4]
     int* smask = reinterpret_cast<int*>(sred + 4 * WARPS);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     if (kp.inv_rec == nullptr || (int)(blockIdx.x >> 1) >= kp.inv_ctas) {
@@ -1073,7 +1073,7 @@ __global__ void __launch_bounds__(128) bg_grad_kernel(KParams kp, double* partia
     for (int i = tid; i < G::NPERM * G::NPERM; i += TPB) cs[(i / G::NPERM) * CROW + i % G::NPERM] = __ldg(G::colour() + i);
     for (int i = tid; i < D * (kp.nb + 1); i += TPB) sgrid[i] = kp.grid[i];
     __syncthreads();
-    auto& st = *reinterpret_cast<BgGradWarp<G, R>*>(mf_bgp_smem + cbytes + (warp < MW ? warp : 0) * wbytes);
+    auto& st = *reinterpret_cast<BgDirWarp<G, R>*>(mf_bgp_smem + cbytes + (warp < MW ? warp : 0) * wbytes);
     double norm = 1.0 / (256.0 * SYM_DEN);
     for (int i = 0; i < G::K; ++i) norm *= kp.gs * kp.gs;
     double acc[4] = { 0.0, 0.0, 0.0, 0.0 };
@@ -1100,12 +1100,10 @@ __global__ void __launch_bounds__(128) bg_grad_kernel(KParams kp, double* partia
         __syncthreads();
         for (int j = warp; warp < MW && j < TPB; j += MW) {
             if (!smask[j]) continue;                    // the same j for the whole warp
-            for (int f = lane; f < NW; f += 32) sdir[warp * (NW + 1) + f] = grec[(size_t)(NW + f) * TPB + j];
-            if (lane == 0) sdir[warp * (NW + 1) + NW] = 1.0;
-            __syncwarp();
+            // forward mode along (dp/dm_t, dm_t = 1): the staged momenta and their tangents
             double dme = 0.0;
-            const double v = bg_warp_grad<G, R>(st.w, st.a, cs, CROW, grec + j, TPB, kp.mt, &dme,
-                                                sdir + warp * (NW + 1), true);
+            const double v = bg_warp_me2_dir<G, R>(st, cs, CROW, grec + j, grec + (size_t)NW * TPB + j, TPB, kp.mt, 1.0,
+                                                   &dme);
             if (lane == 0) { sres[2 * j] = v * norm; sres[2 * j + 1] = dme * norm; }
             __syncwarp();
         }
@@ -1141,8 +1139,9 @@ __global__ void __launch_bounds__(128) bg_grad_kernel(KParams kp, double* partia
 template <class P, class G, typename R>
 constexpr size_t bg_grad_pass_smem(int nb, int mw)
 {
-    return bg_grad_smem_bytes<G, R>(mw) +
-           sizeof(double) * (P::D * (nb + 1) + 2 * 128 + 4 * (P::NEXT * 4 + 1) + 16) + sizeof(int) * 128;
+    return (((sizeof(float) * G::NPERM * (G::NPERM + 1)) + 127) & ~(size_t)127) +
+           (size_t)mw * ((sizeof(BgDirWarp<G, R>) + 15) & ~(size_t)15) +
+           sizeof(double) * (P::D * (nb + 1) + 2 * 128 + 16) + sizeof(int) * 128;
 }
 // recursion warps of the derivative pass: as many (1 .. 4) as fit 227 KB with a 64-bin grid
 template <class P, class G, typename R>

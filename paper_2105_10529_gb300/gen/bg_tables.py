@@ -167,7 +167,7 @@ def generate(k: int, name: str) -> Tuple[str, dict]:
     def gl_adj(m):
         nv4 = (m - 1) * (m - 2) // 2
         v4 = f"&T::j{m}_v4[0][0][0]" if nv4 else "nullptr"
-        return (f"bg_gluon_current_adj<R, {m}, {nv4}>(w, a, t, T::JOFF{m}, T::j{m}_mask, &T::j{m}_v3[0][0][0], "
+        return (f"bg_gluon_current_adj<R, {m}, {nv4}>(w, a, gi, t, T::JOFF{m}, T::j{m}_mask, &T::j{m}_v3[0][0][0], "
                 f"&T::j{m}_v3m[0][0][0], {v4})")
 
     def tl(m, adj=False):
@@ -195,15 +195,16 @@ def generate(k: int, name: str) -> Tuple[str, dict]:
         L.append("        __syncwarp();")
     L.append("    }")
     L.append("    // the reverse sweep: adjoints of the currents (a.Jb, a.Ub, a.Vb from the closures)")
-    L.append("    // and of the per-event invariants, level by level downwards: top-line level m with")
-    L.append("    // gluon level m + 1 (each pushes only to lower levels)")
-    L.append("    template <typename R, class W, class A> __device__ static void reverse(const W& w, A& a, int lane)")
+    L.append("    // and of the per-event invariants (into the lane's registers gi), level by level")
+    L.append("    // downwards: top-line level m with gluon level m + 1 (each pushes only to lower levels)")
+    L.append("    template <typename R, class W, class A, class I>")
+    L.append("    __device__ static void reverse(const W& w, A& a, I& gi, int lane)")
     L.append("    {")
     L.append(f"        namespace T = bg_{name};")
     for m in range(k - 1, 0, -1):
         L.append(f"        for (int t = lane; t < T::NJ{m + 1} + T::NU{m}; t += 32) {{")
         L.append(f"            if (t < T::NJ{m + 1}) {gl_adj(m + 1)};")
-        L.append(f"            else bg_top_current_adj<R, {m}>(w, a, t - T::NJ{m + 1}, T::UOFF{m}, T::u{m}_mask, "
+        L.append(f"            else bg_top_current_adj<R, {m}>(w, a, gi, t - T::NJ{m + 1}, T::UOFF{m}, T::u{m}_mask, "
                  f"&T::u{m}_terms[0][0][0]);")
         L.append("        }")
         L.append("        __syncwarp();")
