@@ -246,9 +246,11 @@ int mf_set_pdf(struct mf_ctx *ctx, const double *pdf_grid_host);
  * per iteration; grid_host (nullable): [dim][n_bins+1] final grid.
  * The iterations (integrand, end-of-pass reduction and refinement, and the
  * observable's reduction) are captured once as a CUDA graph on a private
- * stream, ordered after the work queued on the context's stream, and the
- * graph is replayed while the process, sizes, cuts, couplings, schedule and
- * observable stay the same.  Synchronises. */
+ * stream, ordered after the work queued on the context's stream; a later
+ * call with the same process, sizes, cuts, couplings, schedule and
+ * observable replays it.  The context keeps the graphs of its 16 most
+ * recently used parameter sets, so channels integrated in turn are each
+ * replayed.  Synchronises. */
 int mf_integrate(struct mf_ctx *ctx, int process, double sqrt_s, const mf_cuts *cuts, long long n_events, int n_iter,
                  int want_grads, mf_result *out_host, double *iter_host, double *grid_host);
 
@@ -454,7 +456,8 @@ int mf_set_batch_schedule(struct mf_ctx *ctx, int mode, int sched, long long til
  * grids for every mode {0, 1} x (helicity barrier, helicity split) {(0, 1),
  * (1, 1), (1, 2)} x tile_heavy {1024, 2048, 4096} x tile_light {2048, 4096},
  * and mode 2 x sched {1, 2, 3} x tile_light {2048, 4096} (CTAs per SM as fit;
- * 42 candidates) and keeps the fastest for later
+ * 42 candidates; each run once untimed first, so that no candidate pays for
+ * its kernels' first launch) and keeps the fastest for later
  * mf_integrate_batch calls on this context.  choice_host [6] (nullable)
  * receives (mode, sched, tile_heavy, tile_light, ctas_per_sm, hsplit), the
  * arguments of mf_set_batch_schedule.  Arguments as mf_integrate_batch; the cuts are the

@@ -688,17 +688,15 @@ int mf_autotune_batch(mf_ctx* c, int n_ch, const int* processes, const long long
     MF_BCUDA(c, cudaEventCreate(&e0));
     MF_BCUDA(c, cudaEventCreate(&e1));
     int rc = MF_OK;
-    bool warmed[3] = { false, false, false };
     for (const Schedule& s : cand) {
         Plan pl;
         rc = make_plan(c, n_ch, processes, n_events, sqrt_s, nullptr, s, pl);
         if (rc) break;
-        if (!warmed[s.mode]) {
-            rc = reset_batch(c, pl, c->cap_stream);
-            if (!rc) rc = enqueue_iteration(c, pl, 0, 1, c->cap_stream, c->cap_low);
-            if (rc) break;
-            warmed[s.mode] = true;
-        }
+        // an untimed run of every candidate first: its kernels' first launch in the process
+        // (module loading, attributes) must not count against it
+        rc = reset_batch(c, pl, c->cap_stream);
+        if (!rc) rc = enqueue_iteration(c, pl, 0, 1, c->cap_stream, c->cap_low);
+        if (rc) break;
         rc = reset_batch(c, pl, c->cap_stream);
         if (rc) break;
         if (cudaEventRecord(e0, c->cap_stream) != cudaSuccess) { rc = mf_fail(c, MF_ERR_CUDA, "autotune timing"); break; }

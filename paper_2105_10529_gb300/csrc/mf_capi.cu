@@ -361,7 +361,7 @@ void mf_destroy(mf_ctx* c)
     cudaFree(c->d_bcount);
     if (c->graph) cudaGraphExecDestroy(c->graph);
     if (c->int_stream) cudaStreamSynchronize(c->int_stream);
-    if (c->int_graph) cudaGraphExecDestroy(c->int_graph);
+    for (auto& kg : c->int_graphs) cudaGraphExecDestroy(kg.second);
     if (c->int_ev) cudaEventDestroy(c->int_ev);
     if (c->int_stream) cudaStreamDestroy(c->int_stream);
     if (c->ev_user) cudaEventDestroy(c->ev_user);
@@ -583,8 +583,21 @@ int integrate_impl(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, l
     // the iterations: captured once, replayed while the parameters stay the same
     const std::string key = integrate_key(kp, c->cfg.precision, c->sched, c->hsplit, nblk, sm, n_iter, first_it,
                                           obs ? c->obs_n : 0);
-    if (!c->int_graph || c->int_key != key) {
-        if (c->int_graph) { cudaGraphExecDestroy(c->int_graph); c->int_graph = nullptr; c->int_key.clear(); }
+    cudaGraphExec_t exec = nullptr;
+    for (size_t i = 0; i < c->int_graphs.size(); ++i)
+        if (c->int_graphs[i].first == key) {
+            // a hit moves to the most recently used end
+            auto kg = c->int_graphs[i];
+            c->int_graphs.erase(c->int_graphs.begin() + (long)i);
+            c->int_graphs.push_back(kg);
+            exec = kg.second;
+            break;
+        }
+    if (!exec) {
+        if (c->int_graphs.size() >= mf_ctx::INT_GRAPHS) {
+            cudaGraphExecDestroy(c->int_graphs.front().second);
+            c->int_graphs.erase(c->int_graphs.begin());
+        }
         cudaGraph_t g = nullptr;
         MF_CUDA(c, cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         int erc = MF_OK;
@@ -604,15 +617,12 @@ int integrate_impl(mf_ctx* c, int process, double sqrt_s, const mf_cuts* cuts, l
         cudaError_t ce = cudaStreamEndCapture(s, &g);
         if (erc) { if (g) cudaGraphDestroy(g); return erc; }
         if (ce != cudaSuccess) return fail(c, MF_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(ce));
-        ce = cudaGraphInstantiateWithFlags(&c->int_graph, g, 0);
+        ce = cudaGraphInstantiateWithFlags(&exec, g, 0);
         cudaGraphDestroy(g);
-        if (ce != cudaSuccess) {
-            c->int_graph = nullptr;
-            return fail(c, MF_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
-        }
-        c->int_key = key;
+        if (ce != cudaSuccess) return fail(c, MF_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(ce));
+        c->int_graphs.emplace_back(key, exec);
     }
-    MF_CUDA(c, cudaGraphLaunch(c->int_graph, s));
+    MF_CUDA(c, cudaGraphLaunch(exec, s));
     if (want_grads) {
         // one derivative pass at the final grid on fresh random numbers (Philox iteration first_it + n_iter)
         KParams kg = kp;

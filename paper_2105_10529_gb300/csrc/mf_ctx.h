@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <string>
+#include <utility>
+#include <vector>
 
 #include "mf_batch.cuh"
 #include "mf_dispatch.cuh"
@@ -56,12 +58,13 @@ struct mf_ctx {
     int b_hsplit = 1;                    // tuned: lanes per event of the 2 -> 3 and 2 -> 4 gluon channels
     cudaGraphExec_t graph = nullptr;
     std::string graph_key;
-    // mf_integrate: its iterations captured as one CUDA graph on a private stream, replayed
-    // while the launch parameters (int_key) stay the same
+    // mf_integrate: its iterations captured as CUDA graphs on a private stream, one per set of
+    // launch parameters (the key), the INT_GRAPHS most recently used kept for replay (a caller
+    // that integrates several channels in turn replays each one's graph)
+    static constexpr size_t INT_GRAPHS = 16;
     cudaStream_t int_stream = nullptr;
     cudaEvent_t int_ev = nullptr;
-    cudaGraphExec_t int_graph = nullptr;
-    std::string int_key;
+    std::vector<std::pair<std::string, cudaGraphExec_t>> int_graphs;   // least recently used first
     int b_last_nch = 0;                  // channel list of the grids in d_bgrids
     int b_last_proc[mf::MAX_CH] = {};
 };

@@ -101,3 +101,24 @@ def test_integrate_grid_resumes_the_pass_and_refine_loop(proc, prec, n, pdf_grid
     assert _lib.lib().mf_integrate_grid(ctx.ptr, proc, phys.sqrt_s, None, n, 2, 0, None, 0, C.byref(res),
                                         None, None) == 1
     ctx.close()
+
+
+def test_graphs_of_several_channels_are_kept(pdf_grid):
+    """Channels integrated in turn on one context each replay their own graph:
+    every result equals the first call's, also after more parameter sets than
+    the context keeps (the evicted one is captured afresh)."""
+    phys = PHYS[IN.GG_TT]
+    ctx = ctx_for(IN.GG_TT, 1, pdf_grid)
+    runs = [(IN.GG_TT, 20_000), (IN.UU_TT, 20_000), (IN.GG_TTG, 10_000), (IN.GG_TTGG, 3000)]
+    first = {r: ctx.integrate(r[0], phys.sqrt_s, r[1], 3, want_grid=True) for r in runs}
+    for _ in range(2):
+        for r in runs:
+            x = ctx.integrate(r[0], phys.sqrt_s, r[1], 3, want_grid=True)
+            assert x["sigma"] == first[r]["sigma"] and np.array_equal(x["grid"], first[r]["grid"]), r
+    # 20 more parameter sets push the first ones out
+    for k in range(20):
+        ctx.integrate(IN.GG_TT, phys.sqrt_s, 1000 + k, 1)
+    for r in runs:
+        x = ctx.integrate(r[0], phys.sqrt_s, r[1], 3, want_grid=True)
+        assert x["sigma"] == first[r]["sigma"] and np.array_equal(x["grid"], first[r]["grid"]), r
+    ctx.close()
