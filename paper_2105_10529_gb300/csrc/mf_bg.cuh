@@ -164,7 +164,6 @@ template <typename R, int K, int NJ, int NU>
 struct BgAdj {
     W4<R> Jb[NJ];                      // adjoints of the gluon currents (helicity being summed)
     W4<R> Ub[NU];                      // adjoints of the top-line currents
-    W4<R> Vb;                          // adjoint of v(p_tbar)
     // adjoints of the polarisation and spinor pieces, summed over helicities (one lane each)
     R e1b[K][3], e2b[K][3];
     cx<R> chi3b[2][2], chi4b[2][2];
@@ -176,10 +175,16 @@ struct BgAdj {
 // registers: gp[e][c] = dL/dp_e^c and gmt = dL/dm_t through the invariants, summed over
 // the lane's terms and helicities (the warp adds its lanes up once per event).  This keeps
 // the many currents that share a subset from updating one shared word.
+//
+// The same registers hold the lane's part of the adjoints of the warp's most shared
+// currents, the K external gluons (hJ) and ubar(p_t) (hU0): nearly every current and
+// ordering reaches them, so they are added up over the warp once per helicity instead.
 template <typename R, int K>
 struct BgInvAcc {
     R gp[K + 2][4];
     R gmt;
+    W4<R> hJ[K];
+    W4<R> hU0;
 };
 template <typename R, int K> __device__ __forceinline__ void inv_acc_zero(BgInvAcc<R, K>& g)
 {
@@ -188,6 +193,12 @@ template <typename R, int K> __device__ __forceinline__ void inv_acc_zero(BgInvA
 #pragma unroll
         for (int c = 0; c < 4; ++c) g.gp[e][c] = R(0);
     g.gmt = R(0);
+}
+template <typename R, int K> __device__ __forceinline__ void hub_zero(BgInvAcc<R, K>& g)
+{
+#pragma unroll
+    for (int i = 0; i < K; ++i) g.hJ[i] = w4_zero<R>();
+    g.hU0 = w4_zero<R>();
 }
 // b: the adjoint of P_S (S = msk; gluon i enters P_S with + if incoming, i < 2, else -)
 template <typename R, int K> __device__ __forceinline__ void inv_acc_P(BgInvAcc<R, K>& g, int msk, const R* b)
@@ -216,6 +227,40 @@ template <typename R> __device__ __forceinline__ void atomic_add_cx(cx<R>* d, cx
 template <typename R> __device__ __forceinline__ void atomic_add_w4(W4<R>& d, const W4<R>& v)
 {
     for (int m = 0; m < 4; ++m) atomic_add_cx(&d.c[m], v.c[m]);
+}
+template <typename R> __device__ __forceinline__ void w4_add(W4<R>& d, const W4<R>& v)
+{
+    for (int m = 0; m < 4; ++m) { d.c[m].r += v.c[m].r; d.c[m].i += v.c[m].i; }
+}
+// v summed over the warp (every lane gets the sum)
+template <typename R> __device__ __forceinline__ void w4_warp_sum(W4<R>& v)
+{
+#pragma unroll
+    for (int m = 0; m < 4; ++m)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            v.c[m].r += __shfl_xor_sync(0xffffffffu, v.c[m].r, off);
+            v.c[m].i += __shfl_xor_sync(0xffffffffu, v.c[m].i, off);
+        }
+}
+// add v to the adjoint of gluon current id / top-line current ui: the lane's registers for
+// the external gluons and ubar, a shared-memory atomic for the others
+template <typename R, int K, class A>
+__device__ __forceinline__ void adj_add_J(A& a, BgInvAcc<R, K>& g, int id, const W4<R>& v)
+{
+    if (id < K) {
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+            if (i == id) w4_add(g.hJ[i], v);
+    } else {
+        atomic_add_w4(a.Jb[id], v);
+    }
+}
+template <typename R, int K, class A>
+__device__ __forceinline__ void adj_add_U(A& a, BgInvAcc<R, K>& g, int ui, const W4<R>& v)
+{
+    if (ui == 0) w4_add(g.hU0, v);
+    else atomic_add_w4(a.Ub[ui], v);
 }
 template <typename R> __device__ __forceinline__ cx<R> cmulc(cx<R> a, cx<R> b)   // a conj(b)
 {
@@ -371,8 +416,8 @@ __device__ __forceinline__ void bg_gluon_current_adj(const W& w, A& a, I& gi, in
         R k1b[4] = { R(0), R(0), R(0), R(0) }, k2b[4] = { R(0), R(0), R(0), R(0) };
         vvv_cur_adj(w.J[ref_id(ra)], w.J[ref_id(rb)], k1, k2, -(ref_sign<R>(ra) * ref_sign<R>(rb)), accb, J1b, J2b,
                     k1b, k2b);
-        atomic_add_w4(a.Jb[ref_id(ra)], J1b);
-        atomic_add_w4(a.Jb[ref_id(rb)], J2b);
+        adj_add_J(a, gi, ref_id(ra), J1b);
+        adj_add_J(a, gi, ref_id(rb), J2b);
         inv_acc_P(gi, ma, k1b);
         inv_acc_P(gi, mb, k2b);
     }
@@ -383,9 +428,9 @@ __device__ __forceinline__ void bg_gluon_current_adj(const W& w, A& a, I& gi, in
         W4<R> J1b = w4_zero<R>(), J2b = w4_zero<R>(), J3b = w4_zero<R>();
         v4_adj(w.J[ref_id(ra)], w.J[ref_id(rb)], w.J[ref_id(rc)], ref_sign<R>(ra) * ref_sign<R>(rb) * ref_sign<R>(rc),
                accb, J1b, J2b, J3b);
-        atomic_add_w4(a.Jb[ref_id(ra)], J1b);
-        atomic_add_w4(a.Jb[ref_id(rb)], J2b);
-        atomic_add_w4(a.Jb[ref_id(rc)], J3b);
+        adj_add_J(a, gi, ref_id(ra), J1b);
+        adj_add_J(a, gi, ref_id(rb), J2b);
+        adj_add_J(a, gi, ref_id(rc), J3b);
     }
 }
 
@@ -424,8 +469,8 @@ __device__ __forceinline__ void bg_top_current_adj(const W& w, A& a, I& gi, int 
         for (int m = 0; m < 4; ++m) ob.c[m] = cscale(xb.c[m], sg);
         W4<R> ub = w4_zero<R>(), Jb = w4_zero<R>();
         row_jslash_adj(w.U[ui], w.J[ref_id(r)], ob, ub, Jb);
-        atomic_add_w4(a.Ub[ui], ub);
-        atomic_add_w4(a.Jb[ref_id(r)], Jb);
+        adj_add_U(a, gi, ui, ub);
+        adj_add_J(a, gi, ref_id(r), Jb);
     }
 }
 
@@ -687,7 +732,7 @@ __device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const doub
         bg_external_states<K, R>(w, ih, lane);
         for (int i = lane; i < G::NJ; i += 32) a.Jb[i] = w4_zero<R>();
         for (int i = lane; i < G::NU; i += 32) a.Ub[i] = w4_zero<R>();
-        if (lane == 0) a.Vb = w4_zero<R>();
+        hub_zero(gi);
         __syncwarp();
         G::template forward<R>(w, lane);
         bg_closures<G, R>(w, lane);
@@ -721,9 +766,9 @@ __device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const doub
         }
         __syncwarp();
         // closures backwards: A_sigma = sum_j sg_j (U_j Jslash_j) . v
+        W4<R> vb = w4_zero<R>();      // the lane's part of v's adjoint
         {
             const uint16_t* cl = G::closure();
-            W4<R> vb = w4_zero<R>();
             for (int sgm = lane; sgm < G::NPERM; sgm += 32) {
                 const cx<R> ab = w.A[sgm];
 #pragma unroll
@@ -739,26 +784,34 @@ __device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const doub
                     }
                     W4<R> ub = w4_zero<R>(), jb = w4_zero<R>();
                     row_jslash_adj(w.U[ui], w.J[ref_id(r)], tb, ub, jb);
-                    atomic_add_w4(a.Ub[ui], ub);
-                    atomic_add_w4(a.Jb[ref_id(r)], jb);
+                    adj_add_U(a, gi, ui, ub);
+                    adj_add_J(a, gi, ref_id(r), jb);
                 }
             }
-            atomic_add_w4(a.Vb, vb);
         }
         __syncwarp();
         G::template reverse<R>(w, a, gi, lane);
+        // the register-held adjoints of v, ubar and the external gluons summed over the warp
+        w4_warp_sum(vb);
+        w4_warp_sum(gi.hU0);
+#pragma unroll
+        for (int i = 0; i < K; ++i) w4_warp_sum(gi.hJ[i]);
+        W4<R> jb_ext = gi.hJ[0];
+#pragma unroll
+        for (int i = 1; i < K; ++i)
+            if (i == lane) jb_ext = gi.hJ[i];
         // external states backwards into the polarisation and spinor pieces (one lane each)
 #define HEL(i) ((ih >> (i)) & 1 ? 1 : -1)
         if (lane < K) {
             const R l = HEL(lane < 2 ? lane : lane + 2) > 0 ? R(1) : R(-1), so = lane >= 2 ? R(1) : R(-1);
             for (int j = 0; j < 3; ++j) {
-                a.e1b[lane][j] += -l * a.Jb[lane].c[j + 1].r;
-                a.e2b[lane][j] += so * a.Jb[lane].c[j + 1].i;
+                a.e1b[lane][j] += -l * jb_ext.c[j + 1].r;
+                a.e2b[lane][j] += so * jb_ext.c[j + 1].i;
             }
         } else if (lane == K) {
             // ubar = (conj(chi_l) om_l, conj(chi_l) om_-l)
             const int l = HEL(2) > 0 ? 0 : 1;
-            const W4<R>& ub = a.Ub[0];
+            const W4<R>& ub = gi.hU0;
             const R wl = w.fb3.om[l], wml = w.fb3.om[1 - l];
             for (int b = 0; b < 2; ++b) {
                 a.chi3b[l][b] = cadd(a.chi3b[l][b], cadd(cscale(conjc(ub.c[b]), wl), cscale(conjc(ub.c[2 + b]), wml)));
@@ -769,7 +822,6 @@ __device__ double bg_warp_grad(W& w, A& a, const float* cs, int crow, const doub
             // v = (chi_-l (-s om_l), chi_-l (s om_-l))
             const int l = HEL(3) > 0 ? 0 : 1;
             const R sl = HEL(3) > 0 ? R(1) : R(-1);
-            const W4<R>& vb = a.Vb;
             const R wl = w.fb4.om[l], wml = w.fb4.om[1 - l];
             for (int b = 0; b < 2; ++b) {
                 a.chi4b[1 - l][b] = cadd(a.chi4b[1 - l][b], cadd(cscale(vb.c[b], -sl * wl), cscale(vb.c[2 + b], sl * wml)));
