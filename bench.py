@@ -304,9 +304,13 @@ def run_derivatives(ctx, phys, IN, grid, stream):
         g = grid if proc == IN.GG_TTGG else torch.linspace(0, 1, phys.n_bins + 1, dtype=torch.float64,
                                                            device=dev).repeat(dim, 1).contiguous()
         t, r = timed(lambda: ctx.vegas_pass_grad(proc, phys.sqrt_s, g, n, iteration=77))
+        tv, _ = timed(lambda: ctx.vegas_pass(proc, phys.sqrt_s, g, n, iteration=77))
         r = r.cpu().tolist()
-        out[f"dsigma_dmt_pass_{name}"] = {"events": n, "events_per_s": n / t, "s": t, "sigma_hat_pb": r[0],
-                                          "dsigma_dmt_pb_per_gev": r[1], "dsigma_dalphas_pb": r[3]}
+        out[f"dsigma_dmt_pass_{name}"] = {
+            "events": n, "events_per_s": n / t, "s": t, "over_value_pass": t / tv, "sigma_hat_pb": r[0],
+            "dsigma_dmt_pb_per_gev": r[1], "dsigma_dalphas_pb": r[3],
+            "method": ("forward mode through the Berends-Giele recursion (dual numbers), kinematics with the m_t "
+                       "tangent" if proc == IN.GG_TTGG else "forward tangents through the generated diagrams")}
     n_ev = 100_000
     _, ev = ctx.vegas_pass(IN.GG_TTGG, phys.sqrt_s, grid, n_ev, ev_offset=5 * 10**8, iteration=78,
                            want_events=True, fields=("momenta",))
@@ -316,7 +320,8 @@ def run_derivatives(ctx, phys, IN, grid, stream):
     n_g = 20_000
     mg = mom[:n_g].contiguous()
     t, _ = timed(lambda: ctx.evaluate_grad(IN.GG_TTGG, mg))
-    out["evaluate_with_dme2_dp_gg_ttgg"] = {"points": n_g, "points_per_s": n_g / t, "s": t,
+    tv, _ = timed(lambda: ctx.evaluate(IN.GG_TTGG, mg))
+    out["evaluate_with_dme2_dp_gg_ttgg"] = {"points": n_g, "points_per_s": n_g / t, "s": t, "over_value": t / tv,
                                             "note": "reverse sweep of the Berends-Giele recursion per helicity, tangents through the invariants"}
     return out
 
@@ -421,6 +426,38 @@ def run_ttggg(pdf, IN, MF_FP64, MF_MIXED, stream, n_mixed, fma32):
                          "time_to_equal_error_gain": (t32 / ts) / (var_s / var_full)}
     ctx.set_helicity_sampling(0)
     out["mixed"]["helicity_sampling"] = {"configurations_of_64": samp, "variance_sample_events": 50_000}
+    # derivatives: the m_t pass (forward mode through the recursion) and d|M|^2/dp (reverse sweep)
+    n_d = max(4000, n_mixed // 10)
+    ctx.vegas_pass_grad(p, phys.sqrt_s, grid, 2000, iteration=57)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.vegas_pass_grad(p, phys.sqrt_s, grid, n_d, iteration=58)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    td = e0.elapsed_time(e1) / 1e3
+    e0.record(stream)
+    ctx.vegas_pass(p, phys.sqrt_s, grid, n_d, iteration=58)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tvd = e0.elapsed_time(e1) / 1e3
+    _, evm = ctx.vegas_pass(p, phys.sqrt_s, grid, 4 * 4000, iteration=59, want_events=True, fields=("mask", "momenta"))
+    mom = evm["momenta"][evm["mask"].bool()][:4000].contiguous()
+    ctx.evaluate_grad(p, mom)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.evaluate_grad(p, mom)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    tg = e0.elapsed_time(e1) / 1e3
+    e0.record(stream)
+    ctx.evaluate(p, mom)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    te = e0.elapsed_time(e1) / 1e3
+    out["derivatives"] = {"dsigma_dmt_pass": {"events": n_d, "events_per_s": n_d / td, "over_value_pass": td / tvd,
+                                              "method": "forward mode through the recursion (dual numbers)"},
+                          "evaluate_with_dme2_dp": {"points": int(mom.shape[0]), "points_per_s": mom.shape[0] / tg,
+                                                    "over_value": tg / te, "method": "reverse sweep per helicity"}}
     ctx.close()
     n64 = max(2000, n_mixed // 50)
     ctx64 = Context(phys, pdf, precision=MF_FP64, stream=stream)
