@@ -559,11 +559,27 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
         for (int d = 0; d < D; ++d) o.bins[d] = 0;
         if (valid) {
             const unsigned long long ev = (unsigned long long)(kp.ev_offset + e);
-            if constexpr (P::NPDF == 0) event_ee<R>(kp, sgrid, ev, o, pm);
-            else event_tops<P, R>(kp, sgrid, spdf, ev, o, pm, nullptr);
+            if constexpr (P::NPDF == 0) {
+                event_ee<R>(kp, sgrid, ev, o, pm);
+            } else {
+                double pref;
+                kinematics_tops<P>(kp, sgrid, spdf, ev, o, pm, pref);
+                // the per-event kinematics go out before the matrix element, so that the
+                // uniforms and mapped points need not stay live across it (the same kernel
+                // serves passes with and without outputs)
+                if (wr) { write_event<D>(kp, e, o, true); write_momenta<P::NEXT>(kp, e, pm); }
+                // matrix element only for events that pass; the warp skips it when no lane needs it
+                if (__any_sync(__activemask(), o.mask)) {
+                    if (o.mask) o.me2 = P::Me::template me2<R>(pm, kp.mt, kp.gs, nullptr);
+                }
+                if (o.mask) o.w = pref * o.me2;
+            }
             if (!isfinite(o.w)) { o.w = 0.0; ++nnan; }
             npass += o.mask ? 1 : 0;
-            if (wr) { write_event<D>(kp, e, o, true); write_momenta<P::NEXT>(kp, e, pm); }
+            if (wr) {
+                if constexpr (P::NPDF == 0) { write_event<D>(kp, e, o, true); write_momenta<P::NEXT>(kp, e, pm); }
+                else write_event<D>(kp, e, o, false);
+            }
         }
         const double wn = o.w * kp.inv_n;
         const double v = wn * wn;
@@ -906,8 +922,12 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
 
 // ------------------------------------------------------------------ the fused integrand kernel
 
+// Light processes in mixed precision ask for two CTAs per SM (at most 128 registers a thread for
+// 256-thread CTAs): their kernels are bound by the FP64 pipe's latency, which more warps hide.
+template <class P, typename R> constexpr int integrand_min_ctas() { return (!P::HEAVY && sizeof(R) == 4) ? 2 : 1; }
+
 template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false, int HS = 1, bool LH = false>
-__global__ void __launch_bounds__(TPB) integrand_kernel(KParams kp)
+__global__ void __launch_bounds__(TPB, integrand_min_ctas<P, R>()) integrand_kernel(KParams kp)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];
     double* out = kp.partials + (size_t)blockIdx.x * (2 + P::D * kp.nb);
