@@ -64,6 +64,10 @@ def parse():
                     help="threads per event of the heavy integrand (1 or 2; default 1)")
     ap.add_argument("--only-timed", action="store_true",
                     help="run only the warm-up and timed mixed-precision steps (for profiler captures)")
+    ap.add_argument("--only-grad", action="store_true",
+                    help="run only the derivative calls of --process in mixed precision (for profiler captures): "
+                         "d|M|^2/dp of --events points from one pass, then the m_t pass of --events events, each "
+                         "once untimed and once timed")
     ap.add_argument("--process", default="gg_ttgg",
                     choices=["gg_tt", "uu_tt", "gg_ttg", "ug_ttu", "gg_ttgg", "gg_ttggg"],
                     help="process of the timed steps with --only-timed (the benchmark line is gg_ttgg)")
@@ -839,10 +843,45 @@ def run_ours(args):
         dist.barrier()
 
 
+def run_only_grad(args):
+    """The derivative calls alone: d|M|^2/dp (reverse sweep) and the m_t pass of one process."""
+    import torch
+    from paper_2105_10529_gb300 import inputs as IN
+    from paper_2105_10529_gb300.api import Context, process_info
+    from paper_2105_10529_gb300._lib import MF_MIXED
+    proc = {"gg_tt": IN.GG_TT, "uu_tt": IN.UU_TT, "gg_ttg": IN.GG_TTG, "ug_ttu": IN.UG_TTU,
+            "gg_ttgg": IN.GG_TTGG, "gg_ttggg": IN.GG_TTGGG}[args.process]
+    phys = IN.Physics(seed=3)
+    _, dim = process_info(proc)
+    stream = torch.cuda.current_stream()
+    ctx = Context(phys, IN.make_pdf_grid(), precision=MF_MIXED, stream=stream)
+    grid = torch.linspace(0, 1, phys.n_bins + 1, dtype=torch.float64, device="cuda").repeat(dim, 1).contiguous()
+    n = args.events
+    _, ev = ctx.vegas_pass(proc, phys.sqrt_s, grid, 4 * n, iteration=0, want_events=True, fields=("mask", "momenta"))
+    mom = ev["momenta"][ev["mask"].bool()][:n].contiguous()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out = {"only_grad": True, "process": args.process}
+    for name, fn in (("evaluate_with_dme2_dp", lambda: ctx.evaluate_grad(proc, mom)),
+                     ("dsigma_dmt_pass", lambda: ctx.vegas_pass_grad(proc, phys.sqrt_s, grid, n, iteration=1))):
+        fn()
+        torch.cuda.synchronize()
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3
+        units = int(mom.shape[0]) if name.startswith("evaluate") else n
+        out[name] = {"units": units, "per_s": units / t, "ms": t * 1e3}
+    ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_grad:
+        run_only_grad(args)
     else:
         run_ours(args)
 
