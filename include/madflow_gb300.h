@@ -380,12 +380,14 @@ int mf_helicity_profile(struct mf_ctx *ctx, int process, const double *momenta_d
  * tile order, so the result does not depend on which CTA ran which tile.
  * Schedule (mf_set_batch_schedule, mf_autotune_batch): 0 = one persistent
  * launch for all channels; 1 = the g g -> t tbar g and t tbar g g channels
- * in the persistent launch on a high-priority stream and the cheaper
- * channels as their own integrand kernels on a forked low-priority stream,
- * which fill the SMs as the expensive work runs out; 2 = every channel as
- * its own integrand kernel in the single-process launch configuration, the
- * g g -> t tbar g(g) channels on the high-priority stream (in mode 2 these
- * run a single-process pass's kernel, not persistent tiles).  All iterations
+ * in the persistent launch at high priority and the cheaper channels as
+ * their own integrand kernels at low priority, which fill the SMs as the
+ * expensive work runs out; 2 = every channel as
+ * its own integrand kernel, the g g -> t tbar g(g) ones at high priority (in
+ * mode 2 these run a single-process pass's kernel, not persistent tiles).
+ * Every channel that runs as its own kernel has its own stream, forked from
+ * the iteration's start and joined before its reductions, so that the
+ * channels overlap on the GPU.  All iterations
  * (launches, reductions, refinements) are captured once as a CUDA graph on a
  * private stream and replayed while the channel list, sizes, sqrt_s, n_iter,
  * couplings and schedule stay the same.  The schedule changes how sums are
@@ -442,8 +444,10 @@ int mf_batch_grad(struct mf_ctx *ctx, int n_ch, const int *processes, const long
  * schedule with the tensor-core colour sum, and 3, the warp-per-event
  * schedule, as mf_set_schedule),
  * tile_heavy and tile_light in [32, 2^26] events per work item for the
- * g g -> t tbar g(g) channels and for the others (in the split mode, the
- * other channels' kernels get one CTA per tile_light events), ctas_per_sm in
+ * g g -> t tbar g(g) channels and for the others (in modes 1 and 2 the cheaper
+ * channels' kernels get one CTA per tile_light events; in mode 2 the
+ * g g -> t tbar g(g) kernels at most one CTA per tile_heavy events, up to as
+ * many as fit), ctas_per_sm in
  * [0, 16] (0 = as many as fit; values above that are clamped), hsplit 1 or 2
  * (helicity split of the g g -> t tbar g(g) channels as mf_set_helicity_split;
  * 2 needs sched 1; modes 0 and 1 only).  MF_ERR_ARG outside these ranges.  Defaults: 0, 1, 4096,
@@ -455,9 +459,10 @@ int mf_set_batch_schedule(struct mf_ctx *ctx, int mode, int sched, long long til
  * paper).  Times one iteration of the given channels and sizes at uniform
  * grids for every mode {0, 1} x (helicity barrier, helicity split) {(0, 1),
  * (1, 1), (1, 2)} x tile_heavy {1024, 2048, 4096} x tile_light {2048, 4096},
- * and mode 2 x sched {1, 2, 3} x tile_light {2048, 4096} (CTAs per SM as fit;
- * 42 candidates; each run once untimed first, so that no candidate pays for
- * its kernels' first launch) and keeps the fastest for later
+ * and mode 2 x sched {1, 2, 3} x tile_heavy {512, 4096} x tile_light
+ * {256, 2048, 4096} (CTAs per SM as fit; 54 candidates; each run once
+ * untimed first, so that no candidate pays for its kernels' first launch)
+ * and keeps the fastest for later
  * mf_integrate_batch calls on this context.  choice_host [6] (nullable)
  * receives (mode, sched, tile_heavy, tile_light, ctas_per_sm, hsplit), the
  * arguments of mf_set_batch_schedule.  Arguments as mf_integrate_batch; the cuts are the

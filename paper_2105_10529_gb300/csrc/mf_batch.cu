@@ -150,10 +150,12 @@ int ensure_batch_buffers(mf_ctx* c, size_t tile_doubles)
         int least = 0, greatest = 0;
         MF_BCUDA(c, cudaDeviceGetStreamPriorityRange(&least, &greatest));
         MF_BCUDA(c, cudaStreamCreateWithPriority(&c->cap_stream, cudaStreamNonBlocking, greatest));
-        MF_BCUDA(c, cudaStreamCreateWithPriority(&c->cap_low, cudaStreamNonBlocking, least));
+        for (int k = 0; k < MAX_CH; ++k) {
+            MF_BCUDA(c, cudaStreamCreateWithPriority(&c->cap_side[k], cudaStreamNonBlocking, least));
+            MF_BCUDA(c, cudaEventCreateWithFlags(&c->ev_side[k], cudaEventDisableTiming));
+        }
         MF_BCUDA(c, cudaEventCreateWithFlags(&c->ev_user, cudaEventDisableTiming));
         MF_BCUDA(c, cudaEventCreateWithFlags(&c->ev_cap, cudaEventDisableTiming));
-        MF_BCUDA(c, cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming));
         MF_BCUDA(c, cudaMalloc(&c->d_kps, sizeof(KParams) * MAX_CH));
         MF_BCUDA(c, cudaMalloc(&c->d_bgrids, sizeof(double) * MAX_CH * MAX_DIM * (MAX_BINS + 1)));
         MF_BCUDA(c, cudaMalloc(&c->d_biter, sizeof(double) * MAX_CH * 1000 * 2));
@@ -246,12 +248,15 @@ int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, 
             const long long te = heavy_channel(procs[i]) ? sch.tile_heavy : sch.tile_light;
             pl.rows[i] = (n_events[i] + te - 1) / te;
         } else if (heavy_channel(procs[i])) {
-            // schedule 2: as many CTAs as fit, as in a single-process pass
+            // schedule 2: as many CTAs as fit, as in a single-process pass, but no more than one
+            // per tile_heavy events: a small channel then leaves SMs to the others (its warps are
+            // latency-bound with a few events each anyway)
             int per_sm = 0;
             const size_t sm = ops->smem(MF_MIXED, nb, npv, false);
             MF_BCUDA(c, ops->occupancy(MF_MIXED, sm, &per_sm));
             if (per_sm < 1) return mf_fail(c, MF_ERR_CUDA, "integrand kernel does not fit on an SM");
-            pl.rows[i] = std::min((long long)per_sm * c->n_sm, (long long)c->max_blocks);
+            const long long want = (n_events[i] + sch.tile_heavy - 1) / sch.tile_heavy;
+            pl.rows[i] = std::max(1LL, std::min({ want, (long long)per_sm * c->n_sm, (long long)c->max_blocks }));
         } else {
             int per_sm = 0;
             const size_t sm = ops->smem(MF_MIXED, nb, npv, false);
@@ -341,20 +346,15 @@ int reset_batch(mf_ctx* c, const Plan& pl, cudaStream_t s)
     return MF_OK;
 }
 
-// one iteration: the persistent launch (and, split, the side kernels on the
-// forked low-priority stream), then per channel the row reduction and refinement
-int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s, cudaStream_t low,
-                      long long philox_it = -1)
+// one iteration: the persistent launch on s and the side kernels, each channel's on its own
+// stream forked from s and joined back, then per channel the row reduction and refinement
+int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s, long long philox_it = -1)
 {
     // Philox iteration of the pass: the iteration index unless given apart
     const unsigned pit = philox_it >= 0 ? (unsigned)philox_it : (unsigned)it;
     const int nb = c->cfg.n_bins;
-    bool fork = false;
-    for (const SideLaunch& sl : pl.side) fork |= !sl.high;
-    if (fork) {
-        MF_BCUDA(c, cudaEventRecord(c->ev_cap, s));
-        MF_BCUDA(c, cudaStreamWaitEvent(low, c->ev_cap, 0));
-    }
+    const bool fork = !pl.side.empty();
+    if (fork) MF_BCUDA(c, cudaEventRecord(c->ev_cap, s));
     if (pl.bp.n_slot > 0) {
         MF_BCUDA(c, cudaMemsetAsync(pl.bp.tile_counter, 0, sizeof(unsigned long long), s));
         pl.bp.iteration = pit;
@@ -363,14 +363,15 @@ int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s, c
         else batch_kernel<true, 1><<<pl.nblk, BATCH_TPB, pl.sm, s>>>(pl.bp);
         MF_BCUDA(c, cudaGetLastError());
     }
-    for (SideLaunch& sl : pl.side) {
+    for (size_t k = 0; k < pl.side.size(); ++k) {
+        SideLaunch& sl = pl.side[k];
+        cudaStream_t ss = c->cap_side[k];
         sl.kp.iteration = pit;
-        MF_BCUDA(c, sl.ops->integrand(MF_MIXED, false, sl.sched, 1, sl.kp, sl.nblk, sl.sm, sl.high ? s : low));
+        MF_BCUDA(c, cudaStreamWaitEvent(ss, c->ev_cap, 0));
+        MF_BCUDA(c, sl.ops->integrand(MF_MIXED, false, sl.sched, 1, sl.kp, sl.nblk, sl.sm, ss));
+        MF_BCUDA(c, cudaEventRecord(c->ev_side[k], ss));
     }
-    if (fork) {
-        MF_BCUDA(c, cudaEventRecord(c->ev_join, low));
-        MF_BCUDA(c, cudaStreamWaitEvent(s, c->ev_join, 0));
-    }
+    for (size_t k = 0; k < pl.side.size(); ++k) MF_BCUDA(c, cudaStreamWaitEvent(s, c->ev_side[k], 0));
     for (int i = 0; i < pl.n_ch; ++i) {
         const int ncol = 2 + pl.dim[i] * nb;
         finish_pass_kernel<<<1, 1024, ncol * sizeof(double), s>>>(
@@ -528,7 +529,7 @@ int mf_integrate_batch(mf_ctx* c, int n_ch, const int* processes, const long lon
         MF_BCUDA(c, cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal));
         int erc = MF_OK;
         for (int it = 0; it < n_iter && erc == MF_OK; ++it)
-            erc = enqueue_iteration(c, pl, it, n_iter, c->cap_stream, c->cap_low);
+            erc = enqueue_iteration(c, pl, it, n_iter, c->cap_stream);
         cudaError_t ce = cudaStreamEndCapture(c->cap_stream, &g);
         if (erc == MF_OK && ce == cudaSuccess) erc = set_node_priorities(c, g, pl);
         if (erc) { if (g) cudaGraphDestroy(g); return erc; }
@@ -623,7 +624,7 @@ int mf_batch_pass(mf_ctx* c, int n_ch, const int* processes, const long long* n_
                                     cudaMemcpyHostToDevice, s));
     MF_BCUDA(c, cudaMemsetAsync(c->d_bcount, 0, sizeof(unsigned long long) * 2 * MAX_CH, s));
     // one pass without refinement (statistics slot 0), random numbers of Philox iteration `iteration`
-    rc = enqueue_iteration(c, pl, 0, 1, s, c->cap_low, (long long)iteration);
+    rc = enqueue_iteration(c, pl, 0, 1, s, (long long)iteration);
     if (rc) return rc;
     const size_t row = 2 + (size_t)BATCH_DIM * nb;
     for (int i = 0; i < n_ch; ++i)
@@ -680,8 +681,11 @@ int mf_autotune_batch(mf_ctx* c, int n_ch, const int* processes, const long long
                     for (long long tl : { 2048LL, 4096LL })
                         cand.push_back(Schedule{ mode, sched, 0, th, tl, hs });
     // every channel as its own kernel: FMA or tensor-core colour sum for the expensive ones
+    // (tile_heavy caps the CTAs of an expensive channel's kernel, tile_light sets a cheap one's:
+    // small tiles spread a small channel over many SMs, or over few)
     for (int sched = 1; sched <= 3; ++sched)
-        for (long long tl : { 2048LL, 4096LL }) cand.push_back(Schedule{ 2, sched, 0, 4096, tl, 1 });
+        for (long long th : { 512LL, 4096LL })
+            for (long long tl : { 256LL, 2048LL, 4096LL }) cand.push_back(Schedule{ 2, sched, 0, th, tl, 1 });
     float best = 1e30f;
     Schedule pick = current_schedule(c);
     cudaEvent_t e0 = nullptr, e1 = nullptr;
@@ -695,12 +699,12 @@ int mf_autotune_batch(mf_ctx* c, int n_ch, const int* processes, const long long
         // an untimed run of every candidate first: its kernels' first launch in the process
         // (module loading, attributes) must not count against it
         rc = reset_batch(c, pl, c->cap_stream);
-        if (!rc) rc = enqueue_iteration(c, pl, 0, 1, c->cap_stream, c->cap_low);
+        if (!rc) rc = enqueue_iteration(c, pl, 0, 1, c->cap_stream);
         if (rc) break;
         rc = reset_batch(c, pl, c->cap_stream);
         if (rc) break;
         if (cudaEventRecord(e0, c->cap_stream) != cudaSuccess) { rc = mf_fail(c, MF_ERR_CUDA, "autotune timing"); break; }
-        rc = enqueue_iteration(c, pl, 0, 1, c->cap_stream, c->cap_low);
+        rc = enqueue_iteration(c, pl, 0, 1, c->cap_stream);
         if (rc) break;
         if (cudaEventRecord(e1, c->cap_stream) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
             rc = mf_fail(c, MF_ERR_CUDA, "autotune timing");

@@ -366,9 +366,11 @@ void mf_destroy(mf_ctx* c)
     if (c->int_stream) cudaStreamDestroy(c->int_stream);
     if (c->ev_user) cudaEventDestroy(c->ev_user);
     if (c->ev_cap) cudaEventDestroy(c->ev_cap);
-    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    for (int k = 0; k < mf::MAX_CH; ++k) {
+        if (c->ev_side[k]) cudaEventDestroy(c->ev_side[k]);
+        if (c->cap_side[k]) cudaStreamDestroy(c->cap_side[k]);
+    }
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
-    if (c->cap_low) cudaStreamDestroy(c->cap_low);
     delete c;
 }
 

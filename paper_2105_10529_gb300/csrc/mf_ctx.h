@@ -42,8 +42,11 @@ struct mf_ctx {
     std::string err;
     // batched channels: workspace, tuned schedule and the cached CUDA graph
     cudaStream_t cap_stream = nullptr;   // private stream for graph capture and replay (high priority)
-    cudaStream_t cap_low = nullptr;      // forked low-priority stream of the split schedule
-    cudaEvent_t ev_user = nullptr, ev_cap = nullptr, ev_join = nullptr;
+    // the channels that run as their own integrand kernels: one forked stream each, so that
+    // they overlap (node priorities decide who goes first), joined back by their events
+    cudaStream_t cap_side[mf::MAX_CH] = {};
+    cudaEvent_t ev_side[mf::MAX_CH] = {};
+    cudaEvent_t ev_user = nullptr, ev_cap = nullptr;
     mf::KParams* d_kps = nullptr;        // [MAX_CH]
     double* d_tiles = nullptr;           // tile partial sums of all channels
     size_t tiles_cap = 0;                // doubles
