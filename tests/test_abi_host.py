@@ -45,6 +45,16 @@ def test_default_config_and_process_info_without_gpu():
         process_info(17)
 
 
+def test_setters_reject_a_null_context_without_gpu():
+    """The context setters check their arguments before touching the device: a null context is
+    MF_ERR_ARG (1) for every one of them."""
+    from paper_2105_10529_gb300 import _lib
+    L = _lib.lib()
+    assert L.mf_set_helicity_sampling(None, 4, 0) == 1
+    assert L.mf_set_helicity_split(None, 1) == 1
+    assert L.mf_set_precision(None, 1) == 1
+
+
 def test_oracle_and_cuda_path_share_no_code():
     cuda_dir = os.path.join(ROOT, "paper_2105_10529_gb300")
     oracle_dir = os.path.join(ROOT, "oracle")
