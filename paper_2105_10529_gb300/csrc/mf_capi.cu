@@ -401,7 +401,7 @@ int mf_set_precision(mf_ctx* c, int precision)
 
 int mf_set_schedule(mf_ctx* c, int sched)
 {
-    if (!c || sched < 0 || sched > 3) return MF_ERR_ARG;
+    if (!c || sched < 0 || sched > 4) return MF_ERR_ARG;
     c->sched = sched;
     return MF_OK;
 }

@@ -1,6 +1,7 @@
 // Per-process launch table shared by the process translation units and the
 // C ABI (host side only).
 #pragma once
+#include <algorithm>
 #include <cuda_runtime.h>
 #include "mf_integrand.cuh"
 
@@ -15,6 +16,8 @@ struct ProcOps {
     // 2 barrier and the colour sum on the tensor cores (processes with P::TC, mixed precision),
     // 3 warp-per-event schedule with the tensor-core colour sum (P::TC, mixed precision,
     // kp.inv_rec set for every CTA; otherwise as 2);
+    // 4 the helicity-recycled recursion with one warp per event (matrix elements with
+    // RcTraits; otherwise as 3);
     // hsplit: 1, or 2 lanes per event each summing half the helicities (heavy processes,
     // mixed precision, sched >= 1; otherwise 1).
     // write: per-event outputs.  Schedule 3 and the helicity split run the same kernel with
@@ -122,6 +125,10 @@ const ProcOps* ops_uu_tt();
 const ProcOps* ops_ug_ttu();
 const ProcOps* ops_gg_ttggg();
 
+// whether a warp-per-event process (HL) has the helicity-recycled schedule
+template <class P, bool HL> struct ProcHasRc : std::false_type {};
+template <class P> struct ProcHasRc<P, true> : HasRc<typename P::Me> {};
+
 // integrand launch helpers for a process trait P: T32 threads per CTA for the
 // mixed-precision kernels, T64 for the FP64 ones
 template <class P, int T32, int T64 = T32>
@@ -144,6 +151,18 @@ struct IntegrandOps {
     static constexpr bool HL = HT && T32 == LH_TPB;
     static const void* fn_lh() { return (const void*)integrand_kernel<P, float, T32, false, HL, HL, 1, HL>; }
     static size_t smem_lh(int nb, int npv, bool obs) { return SmemLayout<P, float, T32, HL>::bytes(nb, npv, obs); }
+    // the helicity-recycled warp-per-event schedule (matrix elements with RcTraits, mf_rc.cuh)
+    static constexpr bool HR = ProcHasRc<P, HL>::value;
+    static const void* fn_rc()
+    {
+        if constexpr (HR) return (const void*)integrand_kernel<P, float, T32, false, true, true, 1, 2>;
+        else return fn_lh();
+    }
+    static size_t smem_rc(int nb, int npv, bool obs)
+    {
+        if constexpr (HR) return SmemLayout<P, float, T32, 2>::bytes(nb, npv, obs);
+        else return smem_lh(nb, npv, obs);
+    }
     // the dynamic shared memory of every variant of one precision (sm32, sm64: bytes)
     static cudaError_t prepare(size_t sm32, size_t sm64)
     {
@@ -173,6 +192,13 @@ struct IntegrandOps {
             if (e == cudaSuccess) e = cudaFuncSetAttribute(fn_lh(), cudaFuncAttributePreferredSharedMemoryCarveout, pct);
             if (e != cudaSuccess) return e;
         }
+        if constexpr (HR) {
+            // the recycled schedule keeps its store in shared memory: its own limit
+            const size_t need = smem_rc(MAX_BINS, 0, true);
+            cudaError_t e = cudaFuncSetAttribute(fn_rc(), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 (int)std::max(need, sm32));
+            if (e != cudaSuccess) return e;
+        }
         return cudaSuccess;
     }
     static cudaError_t occupancy(int prec, size_t sm, int* b)
@@ -193,8 +219,11 @@ struct IntegrandOps {
                 return (const void*)integrand_kernel<P, float, TPB, false, true, false, 2>;
             }
         }
+        if constexpr (HR && sizeof(R) == 4) {
+            if (sched == 4 && hsplit == 1) return fn_rc();
+        }
         if constexpr (HL && sizeof(R) == 4) {
-            if (sched == 3 && hsplit == 1) return fn_lh();
+            if (sched >= 3 && hsplit == 1) return fn_lh();
         }
         if constexpr (HT && sizeof(R) == 4) {
             if (sched >= 2) return (const void*)integrand_kernel<P, float, TPB, W, true, true>;
@@ -212,11 +241,14 @@ struct IntegrandOps {
     {
         KParams arg = kp;
         void* args[1] = { &arg };
-        if (sched == 3 && (kp.inv_rec == nullptr || nblk > kp.inv_ctas)) sched = 2;   // no record region: as 2
+        if (sched >= 3 && (kp.inv_rec == nullptr || nblk > kp.inv_ctas)) sched = 2;   // no record region: as 2
         const void* f = kernel(prec, write, sched, hsplit);
         if constexpr (HL) {
             // the warp-per-event kernel runs with its own, smaller dynamic shared memory
             if (f == fn_lh()) sm = smem_lh(kp.nb, kp.pdfg.nx * kp.pdfg.nq, kp.nobs > 0);
+            if constexpr (HR) {
+                if (f == fn_rc()) sm = smem_rc(kp.nb, kp.pdfg.nx * kp.pdfg.nq, kp.nobs > 0);
+            }
         }
         return cudaLaunchKernel(f, dim3(nblk), dim3(prec ? T32 : T64), args, sm, s);
     }

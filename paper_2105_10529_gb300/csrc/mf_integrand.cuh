@@ -29,6 +29,14 @@ constexpr int MAX_OBS_BINS = 100;    // observable histogram: regular bins (plus
 constexpr int LH_INV_WORDS_MAX = 136;   // words of a warp-per-event record (g g -> t tbar g g: 134)
 constexpr int LH_TPB = 256;             // threads per CTA of the warp-per-event schedule
 
+// The warp-per-event schedules (template argument LH of the heavy integrand): 1, the
+// Feynman-diagram helicity body with one lane per configuration (schedule 3); 2, the
+// helicity-recycled recursion of mf_rc.cuh (schedule 4), for the matrix elements that
+// specialise RcTraits there: warp_bytes(), the shared memory of one warp's store, and
+// extra_bytes(), the CTA's tables after the warps' regions.
+template <class ME> struct RcTraits;
+template <class ME> struct HasRc : std::false_type {};
+
 struct EwParams { double e2, sw2, cw2, mz, wz; };
 
 struct KParams {
@@ -384,18 +392,33 @@ __device__ __forceinline__ void event_tops(const KParams& kp, const double* sgri
 // helicity body
 template <class P, bool LH> struct LhRows { static constexpr int words() { return 0; } };
 template <class P> struct LhRows<P, true> { static constexpr int words() { return 2 * P::Me::NCOL + 2; } };
+// a warp's region (its record, or with LH = 2 its store) and the CTA's extra bytes after them
+template <class P, typename R, int LH> struct LhRegion {
+    static constexpr size_t stride() { return (P::template slot_bytes<R>() + 15) & ~(size_t)15; }
+    static constexpr size_t extra() { return 0; }
+};
+template <class P, typename R> struct LhRegion<P, R, 2> {
+    static constexpr size_t stride() { return (RcTraits<typename P::Me>::warp_bytes() + 15) & ~(size_t)15; }
+    static constexpr size_t extra() { return RcTraits<typename P::Me>::extra_bytes(); }
+};
 
-template <class P, typename R, int TPB, bool LH = false>
+template <class P, typename R, int TPB, int LH = 0>
 struct SmemLayout {
     static constexpr int WARPS = TPB / 32;
     static constexpr int D = P::D;
     static constexpr int NHIST = P::HEAVY ? 1 : WARPS;
     static constexpr __host__ __device__ size_t al(size_t x) { return (x + 15) & ~(size_t)15; }
-    // LH: the rows [TPB][LH_JROW] words, then the records [WARPS], LH_REC_STRIDE bytes apart, at LH_REC_OFF
-    static constexpr int LH_JROW = LhRows<P, LH>::words();
+    // LH: the rows [TPB][LH_JROW] words (LH = 1; with LH = 2 the rows live in tensor memory),
+    // then the warps' regions [WARPS], LH_REC_STRIDE bytes apart, at LH_REC_OFF, then the
+    // CTA's extra tables (LH = 2) at LH_EXTRA_OFF
+    static constexpr int LH_JROW = LhRows<P, LH == 1>::words();
     static constexpr int LH_REC_OFF = TPB * LH_JROW * (int)sizeof(R);
-    static constexpr int LH_REC_STRIDE = (int)al(P::template slot_bytes<R>());
-    static constexpr size_t lh_bytes() { return LH ? al((size_t)LH_REC_OFF + (size_t)WARPS * LH_REC_STRIDE) : 0; }
+    static constexpr int LH_REC_STRIDE = LH ? (int)LhRegion<P, R, LH>::stride() : 0;
+    static constexpr int LH_EXTRA_OFF = LH_REC_OFF + WARPS * LH_REC_STRIDE;
+    static constexpr size_t lh_bytes()
+    {
+        return LH ? al((size_t)LH_EXTRA_OFF + LhRegion<P, R, LH>::extra()) : 0;
+    }
     // warp-level matrix elements: the colour matrix and one state per warp at the start
     static constexpr __host__ __device__ size_t bg_bytes()
     {
@@ -707,6 +730,13 @@ __device__ __forceinline__ double bg_batch_me2(const KParams& kp, unsigned char*
     return me;
 }
 
+// the helicity-recycled schedule (LH = 2), defined in mf_rc.cuh: the CTA's set-up after
+// tc_setup, and |M|^2 of a batch (as lh_batch_me2)
+template <class P, int TPB> __device__ void rc_cta_setup(unsigned char* smem_raw, TcCta* tc);
+template <class P, int TPB>
+__device__ double rc_batch_me2(const KParams& kp, unsigned char* smem_raw, TcCta* tc, double* sme, int take, bool mine,
+                               const double (&pm)[P::NEXT][4]);
+
 // Heavy processes (expensive matrix elements): kinematics first, then the
 // events that pass the cuts are queued in event order and their matrix
 // elements are evaluated TPB at a time, so no lane idles through a matrix
@@ -729,7 +759,7 @@ __device__ __forceinline__ double bg_batch_me2(const KParams& kp, unsigned char*
 // rows on the tensor cores and the event's sum over its lanes by a fixed
 // shuffle tree.  The per-event record is shared by the warp, so shared memory
 // holds 8 records instead of 256 per-thread slots and leaves the rest to L1.
-template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false, int HS = 1, bool LH = false>
+template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false, int HS = 1, int LH = 0>
 __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char* smem_raw, long long first,
                                                 long long step, long long end, double* out)
 {
@@ -787,7 +817,8 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     TcCta* tc = nullptr;
     if constexpr (TC) {
         tc = reinterpret_cast<TcCta*>(smem_raw + L::tc_off(nb, npv));
-        tc_setup<P::Me::NCOL>(tc, P::Me::colour54(), kp.dev_err);
+        tc_setup<P::Me::NCOL>(tc, P::Me::colour54(), kp.dev_err, LH == 2 ? TC_RC_COLS : TC_COLS);
+        if constexpr (LH == 2) rc_cta_setup<P, TPB>(smem_raw, tc);
     }
     if constexpr (P::BG) P::Me::load_colour(reinterpret_cast<float*>(smem_raw));
     __syncthreads();
@@ -864,7 +895,9 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
                 static_assert(HS == 1 && !LH && !TC, "warp-level matrix element: its own schedule");
                 me = bg_batch_me2<P, R, TPB>(kp, smem_raw, svbuf, take, mine, pm,
                                              (unsigned long long)(kp.ev_offset + e));
-            } else if constexpr (LH) {
+            } else if constexpr (LH == 2) {
+                me = rc_batch_me2<P, TPB>(kp, smem_raw, tc, svbuf, take, mine, pm);
+            } else if constexpr (LH == 1) {
                 me = lh_batch_me2<P, R, TPB>(kp, smem_raw, tc, svbuf, take, mine, pm);
             } else if constexpr (TC) {
                 me = P::Me::template me2<R, SYNC, true>(pm, kp.mt, kp.gs, slot, tc, hpart, HS);
@@ -915,7 +948,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             __syncthreads();
         }
     }
-    if constexpr (TC) tc_teardown(tc);
+    if constexpr (TC) tc_teardown(tc, LH == 2 ? TC_RC_COLS : TC_COLS);
     write_partials<P, TPB, 1>(kp, sw, sw2, npass, nnan, sred, shist, out);
     write_obs_partials<1, L::OBS_ROW>(kp, sobs);
 }
@@ -926,7 +959,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
 // 256-thread CTAs): their kernels are bound by the FP64 pipe's latency, which more warps hide.
 template <class P, typename R> constexpr int integrand_min_ctas() { return (!P::HEAVY && sizeof(R) == 4) ? 2 : 1; }
 
-template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false, int HS = 1, bool LH = false>
+template <class P, typename R, int TPB, bool WRITE, bool SYNC, bool TC = false, int HS = 1, int LH = 0>
 __global__ void __launch_bounds__(TPB, integrand_min_ctas<P, R>()) integrand_kernel(KParams kp)
 {
     extern __shared__ __align__(128) unsigned char smem_raw[];

@@ -2,6 +2,7 @@
 // matrix-element evaluation, instantiated in their own translation unit.
 #include "mf_dispatch.cuh"
 #include "generated/me_gg_ttgg.cuh"
+#include "mf_rc.cuh"
 
 namespace mf {
 namespace {

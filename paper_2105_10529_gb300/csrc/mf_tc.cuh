@@ -192,9 +192,10 @@ __device__ __forceinline__ float bf16_value(uint32_t bits)
 
 // Set-up by the whole CTA (every thread calls), once per CTA: B = 54 C from
 // c54 [ncol][ncol] (row-major, symmetric), the mbarrier and the TMEM
-// allocation (warp 0), after which the CTA relinquishes the allocation permit.
+// allocation of cols columns per group (warp 0), after which the CTA
+// relinquishes the allocation permit.
 template <int NCOL>
-__device__ __forceinline__ void tc_setup(TcCta* tc, const short* c54, unsigned* err)
+__device__ __forceinline__ void tc_setup(TcCta* tc, const short* c54, unsigned* err, uint32_t cols = TC_COLS)
 {
     static_assert(NCOL <= TC_N && NCOL <= TC_K, "colour basis larger than the padded contraction");
     for (int idx = threadIdx.x; idx < TC_N * TC_K; idx += blockDim.x) {
@@ -211,7 +212,7 @@ __device__ __forceinline__ void tc_setup(TcCta* tc, const short* c54, unsigned* 
     // generic-proxy writes of B become visible to the tensor core (async proxy)
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     if (threadIdx.x < 32) {
-        tc_alloc(&tc->tmem, TC_COLS * tc_groups());
+        tc_alloc(&tc->tmem, cols * tc_groups());
         // give up the right to allocate again: while a CTA holds it, no further
         // CTA of the kernel is placed on the SM
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
@@ -222,12 +223,12 @@ __device__ __forceinline__ void tc_setup(TcCta* tc, const short* c54, unsigned* 
 }
 
 // Release by the whole CTA (every thread calls) once no thread uses TMEM any more.
-__device__ __forceinline__ void tc_teardown(TcCta* tc)
+__device__ __forceinline__ void tc_teardown(TcCta* tc, uint32_t cols = TC_COLS)
 {
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (threadIdx.x < 32) tc_dealloc(tc->tmem, TC_COLS * tc_groups());
+    if (threadIdx.x < 32) tc_dealloc(tc->tmem, cols * tc_groups());
 }
 
 // TMEM address of this thread's lane at column 0 of its group's columns: a
@@ -332,4 +333,145 @@ __device__ __forceinline__ float tc_colour_sum(TcCta* tc, const volatile float* 
     return acc;
 }
 
+// ------------------------------------------------------------------ amplitudes produced in TMEM
+//
+// The helicity-recycled recursion (mf_rc.cuh) forms a configuration's colour-flow
+// amplitudes two at a time and writes them straight into its TMEM lane, so no row of
+// shared memory holds them: per group of 128 threads TC_RC_COLS columns, the A pieces
+// and D as above and, from column TC_U, the FP32 u = 2 J - J1 - J2 of every flow
+// (flows 2c, 2c + 1 at columns TC_U + 4c + 0..3 as re, re, im, im).
+constexpr uint32_t TC_RC_COLS = 256;
+constexpr uint32_t TC_U = 128;
+
+__device__ __forceinline__ uint32_t tc_rc_lane(const TcCta* tc)
+{
+    const uint32_t warp = threadIdx.x >> 5;
+    return tc->tmem + (((warp & 3u) * 32u) << 16) + (warp >> 2) * TC_RC_COLS;
+}
+__device__ __forceinline__ void tc_st1(uint32_t taddr, uint32_t v)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x1.b32 [%0], {%1};" ::"r"(taddr), "r"(v) : "memory");
+}
+__device__ __forceinline__ void tc_st4(uint32_t taddr, uint32_t v0, uint32_t v1, uint32_t v2, uint32_t v3)
+{
+    asm volatile("tcgen05.st.sync.aligned.32x32b.x4.b32 [%0], {%1, %2, %3, %4};" ::"r"(taddr), "r"(v0), "r"(v1),
+                 "r"(v2), "r"(v3)
+                 : "memory");
+}
+
+// Once per CTA after tc_setup (every thread calls): the A columns of the padding flows
+// k = NCOL .. TC_K - 1 are zero (the amplitudes only ever write the first NCOL / 2 columns).
+template <int NCOL>
+__device__ __forceinline__ void tc_rc_zero_pad(const TcCta* tc)
+{
+    static_assert(NCOL % 2 == 0 && NCOL <= TC_K, "pairs of flows");
+    const uint32_t lb = tc_rc_lane(tc);
+#pragma unroll
+    for (uint32_t c = NCOL / 2; c < TC_K / 2; ++c) {
+        tc_st1(lb + TC_A_RE1 + c, 0u);
+        tc_st1(lb + TC_A_RE2 + c, 0u);
+        tc_st1(lb + TC_A_IM1 + c, 0u);
+        tc_st1(lb + TC_A_IM2 + c, 0u);
+    }
+    tc_wait_st();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+}
+
+// Flows 2c and 2c + 1 of this thread's configuration (warp-uniform call): their bf16
+// pieces into column c of the four A regions, u into its four columns.
+__device__ __forceinline__ void tc_rc_put_pair(uint32_t lane_base, int c, float re0, float im0, float re1, float im1)
+{
+    const uint32_t r1 = bf16x2_bits(re0, re1);
+    const float rh0 = __uint_as_float(r1 << 16), rh1 = __uint_as_float(r1 & 0xFFFF0000u);
+    const uint32_t r2 = bf16x2_bits(re0 - rh0, re1 - rh1);
+    const float rl0 = __uint_as_float(r2 << 16), rl1 = __uint_as_float(r2 & 0xFFFF0000u);
+    const uint32_t i1 = bf16x2_bits(im0, im1);
+    const float ih0 = __uint_as_float(i1 << 16), ih1 = __uint_as_float(i1 & 0xFFFF0000u);
+    const uint32_t i2 = bf16x2_bits(im0 - ih0, im1 - ih1);
+    const float il0 = __uint_as_float(i2 << 16), il1 = __uint_as_float(i2 & 0xFFFF0000u);
+    tc_st1(lane_base + TC_A_RE1 + c, r1);
+    tc_st1(lane_base + TC_A_RE2 + c, r2);
+    tc_st1(lane_base + TC_A_IM1 + c, i1);
+    tc_st1(lane_base + TC_A_IM2 + c, i2);
+    tc_st4(lane_base + TC_U + 4 * c, __float_as_uint(fmaf(2.0f, re0, -(rh0 + rl0))),
+           __float_as_uint(fmaf(2.0f, re1, -(rh1 + rl1))), __float_as_uint(fmaf(2.0f, im0, -(ih0 + il0))),
+           __float_as_uint(fmaf(2.0f, im1, -(ih1 + il1))));
+}
+
+// The colour sum of the amplitudes that tc_rc_put_pair left in every thread's lane,
+// scaled by 54 (as tc_colour_sum; every thread of the CTA calls, once per round).
+template <int NCOL>
+__device__ __forceinline__ float tc_rc_colour_sum(TcCta* tc)
+{
+    static_assert(NCOL <= 32 && NCOL % 2 == 0, "one x16 load of u per 16 flows");
+    const int tid = threadIdx.x;
+    const uint32_t lane_base = tc_rc_lane(tc);
+    const uint32_t parity = tc->phase & 1u;
+    tc_wait_st();
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    if (tc->dead) {
+        __syncthreads();
+        return 0.0f;
+    }
+    if (tid == 0) {
+        tc->phase = parity ^ 1u;
+        constexpr uint32_t idesc = tc_idesc(128, TC_N);
+        const uint32_t b0 = smem_u32(tc->B);
+        const uint32_t groups = tc_groups();
+        for (uint32_t g = 0; g < groups; ++g) {
+            const uint32_t base = tc->tmem + g * TC_RC_COLS;
+#pragma unroll
+            for (int part = 0; part < 2; ++part) {
+                const uint32_t d = base + (part ? TC_D_IM : TC_D_RE);
+                const uint32_t a1 = base + (part ? TC_A_IM1 : TC_A_RE1);
+                const uint32_t a2 = base + (part ? TC_A_IM2 : TC_A_RE2);
+#pragma unroll
+                for (int ks = 0; ks < 2; ++ks) {
+                    const uint64_t bd = tc_smem_desc(b0 + (uint32_t)ks * 1024u, 512u, 128u);
+                    tc_mma_ts(d, a1 + 8u * ks, bd, idesc, ks > 0 ? 1u : 0u);
+                    tc_mma_ts(d, a2 + 8u * ks, bd, idesc, 1u);
+                }
+            }
+        }
+        tc_commit(&tc->mbar);
+    }
+    if (!mbar_wait(&tc->mbar, parity)) {
+        tc->dead = 1u;
+        if (tc->err) atomicExch(tc->err, 1u);
+    }
+    tc_fence_after();
+    float acc = 0.0f;
+    // flows 16 h .. 16 h + 15: D (re, im) and the u columns of pairs 8 h .. 8 h + 7
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        if (16 * half >= NCOL) break;
+        uint32_t dre[16], dim[16], uu[32];
+        tc_ld16x2(lane_base + TC_D_RE + 16 * half, dre, lane_base + TC_D_IM + 16 * half, dim);
+        uint32_t u0[16], u1[16];
+        tc_ld16x2(lane_base + TC_U + 32 * half, u0, lane_base + TC_U + 32 * half + 16, u1);
+#pragma unroll
+        for (int i = 0; i < 16; ++i) { uu[i] = u0[i]; uu[16 + i] = u1[i]; }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int k = 16 * half + 2 * c + e;
+                if (k < NCOL) {
+                    acc = fmaf(__uint_as_float(uu[4 * c + e]), __uint_as_float(dre[2 * c + e]), acc);
+                    acc = fmaf(__uint_as_float(uu[4 * c + 2 + e]), __uint_as_float(dim[2 * c + e]), acc);
+                }
+            }
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    return acc;
+}
+
 }  // namespace mf
+

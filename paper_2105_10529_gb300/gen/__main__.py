@@ -5,7 +5,7 @@
 import os
 from fractions import Fraction
 
-from . import bg_tables, qcd_diagrams, qq_processes
+from . import bg_tables, qcd_diagrams, qq_processes, rc_tables
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 OUT = os.path.join(os.path.dirname(HERE), "csrc", "generated")
@@ -28,6 +28,8 @@ def write_all(out_dir: str = OUT) -> list:
     # the recursion's tables of the lighter gluon processes (their derivatives run the reverse sweep)
     items += [(f"bg_{name}.cuh", lambda k=k, name=name: bg_tables.generate(k, name)[0])
               for k, name in ((2, "gg_tt"), (3, "gg_ttg"), (4, "gg_ttgg"))]
+    # the helicity-recycled recursion of g g -> t tbar g g (warp-per-event schedule 4)
+    items += [("rc_gg_ttgg.cuh", lambda: rc_tables.generate("gg_ttgg")[0])]
     for fname, make in items:
         src = make()
         path = os.path.join(out_dir, fname)

@@ -226,7 +226,7 @@ def test_bad_arguments(pdf_grid):
     with pytest.raises(MfError):
         ctx.integrate(17, 13000.0, 1000, 2)
     with pytest.raises(MfError):
-        ctx.set_schedule(4)
+        ctx.set_schedule(5)
     ctx.device_status()
     ctx.close()
 

@@ -119,7 +119,7 @@ def test_per_event_outputs_and_other_processes_fall_back(pdf_grid):
     """Per-event outputs run schedule 3 itself (|M|^2 within FP32 rounding of
     schedule 2, the sums equal to those of the pass without outputs); the
     helicity split and processes without the tensor-core colour sum run
-    schedule 3 as schedule 2; 4 is rejected."""
+    schedule 3 as schedule 2; 5 is rejected."""
     phys = PHYS[PROC]
     grid = torch.tensor(random_grid(IN.DIM[PROC], seed=63), device="cuda")
     ctx = ctx_for(pdf_grid)
@@ -148,5 +148,5 @@ def test_per_event_outputs_and_other_processes_fall_back(pdf_grid):
     ctx.device_status()
     from paper_2105_10529_gb300._lib import MfError
     with pytest.raises(MfError):
-        ctx.set_schedule(4)
+        ctx.set_schedule(5)
     ctx.close()
