@@ -26,7 +26,7 @@ constexpr int KIN_NEXT_MAX = 7;      // largest process (2 -> 5) for the global 
 constexpr int KIN_CAP_UNIT = 256;    // ring entries per region of the global kinematics store
 constexpr int MAX_BINS = 64;
 constexpr int MAX_OBS_BINS = 100;    // observable histogram: regular bins (plus under- and overflow)
-constexpr int LH_INV_WORDS_MAX = 136;   // words of a warp-per-event record (g g -> t tbar g g: 134)
+constexpr int LH_INV_WORDS_MAX = 144;   // words of a warp-per-event record (g g -> t tbar g g: 134; recycled: 144)
 constexpr int LH_TPB = 256;             // threads per CTA of the warp-per-event schedule
 
 // The warp-per-event schedules (template argument LH of the heavy integrand): 1, the

@@ -21,8 +21,9 @@
 //
 // The amplitudes go straight into tensor memory for the colour sum (mf_tc.cuh,
 // tc_rc_put_pair and tc_rc_colour_sum).  Conventions and routines are those of
-// mf_helas.cuh and mf_bg.cuh; the invariants (subset momenta and inverse propagator
-// denominators in FP64, stored as FP32) are those of bg_event_invariants.
+// mf_helas.cuh and mf_bg.cuh.  The per-event invariants (subset momenta and inverse
+// propagator denominators formed in FP64, stored as FP32) are computed one event per
+// thread, like the records of the diagram schedule, and each warp copies its event's.
 #pragma once
 #include <cstdint>
 #include "mf_bg.cuh"
@@ -35,54 +36,118 @@ namespace mf {
 
 namespace rcT = rc_gg_ttgg;
 
-// one warp's shared-memory state: the store first (16-byte aligned slots), then the
-// per-event invariants in the field names of bg_event_invariants
-struct RcWarp {
-    W4<float> W[rcT::NSLOT];
-    float P[16][4];
+// the per-event invariants of one event (FP32 words): the incoming-convention momentum of
+// every non-empty gluon subset m (gluons 0, 1 incoming, the rest outgoing with minus their
+// momenta) at P[m - 1], p_t, 1 / P^2 of the subsets of two or more gluons, 1 / ((p_t - P)^2
+// - m_t^2) of the subsets short of all four, the gluons' transverse bases, the spinor
+// pieces of t and tbar and m_t
+struct RcRec {
+    float P[15][4];
+    float pt[4];
     float iP2[16];
-    float Q[16][4];
     float iQ[16];
     float e1[4][3], e2[4][3];
     FermionBasis<float> fb3, fb4;
     float mt;
+    float pad[3];
+};
+constexpr int RC_REC_WORDS = (int)(sizeof(RcRec) / sizeof(float));
+static_assert(RC_REC_WORDS * sizeof(float) == sizeof(RcRec) && RC_REC_WORDS <= LH_INV_WORDS_MAX, "record words");
+
+// one warp's shared-memory state: the store, each slot's four complex components split
+// into two 16-byte halves in two arrays (so that eight lanes reading eight consecutive
+// slots touch 128 consecutive bytes, free of bank conflicts), then its event's record
+struct RcWarp {
+    float4 Wlo[rcT::NSLOT];
+    float4 Whi[rcT::NSLOT];
+    RcRec r;
 };
 
-// the combination offset of lane l for a lane-bit mask m: the bits of l selected by m,
-// packed (a table of 32 x 32 bytes in shared memory, filled once per CTA)
-constexpr int RC_OFFTAB_BYTES = 32 * 32;
-__device__ __forceinline__ void rc_fill_offtab(uint8_t* tab)
+// the record of one event (one thread, FP64 arithmetic); p: g g t tbar g g
+__device__ __forceinline__ void rc_record(const double (&p)[6][4], double mt, RcRec& r)
 {
-    for (int i = threadIdx.x; i < RC_OFFTAB_BYTES; i += blockDim.x) {
-        const int m = i >> 5, l = i & 31;
-        int r = 0, j = 0;
-        for (int b = 0; b < 5; ++b)
-            if ((m >> b) & 1) r |= ((l >> b) & 1) << j++;
-        tab[i] = (uint8_t)r;
+    double K[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) K[i][c] = i < 2 ? p[i][c] : -p[i + 2][c];
+    double P[16][4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) P[0][c] = 0.0;
+#pragma unroll
+    for (int m = 1; m < 16; ++m) {
+        const int low = __ffs(m) - 1;
+#pragma unroll
+        for (int c = 0; c < 4; ++c) {
+            P[m][c] = P[m & (m - 1)][c] + K[low][c];
+            r.P[m - 1][c] = (float)P[m][c];
+        }
+        r.iP2[m] = __popc(m) >= 2 ? (float)(1.0 / mdot(P[m], P[m])) : 0.0f;
+        double q[4];
+#pragma unroll
+        for (int c = 0; c < 4; ++c) q[c] = p[2][c] - P[m][c];
+        r.iQ[m] = m != 15 ? (float)(1.0 / (mdot(q, q) - mt * mt)) : 0.0f;
     }
+    r.iP2[0] = 0.0f;
+    r.iQ[0] = 0.0f;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) r.pt[c] = (float)p[2][c];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        double a[3], b[3];
+        gluon_basis(p[i < 2 ? i : i + 2], a, b);
+#pragma unroll
+        for (int j = 0; j < 3; ++j) { r.e1[i][j] = (float)a[j]; r.e2[i][j] = (float)b[j]; }
+    }
+    r.fb3 = fermion_basis<float>(p[2], mt);
+    r.fb4 = fermion_basis<float>(p[3], mt);
+    r.mt = (float)mt;
+    r.pad[0] = r.pad[1] = r.pad[2] = 0.0f;
 }
 
-__device__ __forceinline__ W4<float> rc_ld(const W4<float>* p)
+// the per-lane words of the five contractions of every ordering (rc_gg_ttgg::lane_terms),
+// copied into shared memory once per CTA
+constexpr int RC_TERM_BYTES = rcT::TERM_WORDS * (int)sizeof(uint32_t);
+
+__device__ __forceinline__ W4<float> rc_ld(const RcWarp& w, int i)
 {
-    const float4 a = reinterpret_cast<const float4*>(p)[0], b = reinterpret_cast<const float4*>(p)[1];
-    W4<float> w;
-    w.c[0] = mkc(a.x, a.y); w.c[1] = mkc(a.z, a.w); w.c[2] = mkc(b.x, b.y); w.c[3] = mkc(b.z, b.w);
-    return w;
+    const float4 a = w.Wlo[i], b = w.Whi[i];
+    W4<float> o;
+    o.c[0] = mkc(a.x, a.y); o.c[1] = mkc(a.z, a.w); o.c[2] = mkc(b.x, b.y); o.c[3] = mkc(b.z, b.w);
+    return o;
 }
-__device__ __forceinline__ void rc_st(W4<float>* p, const W4<float>& w)
+__device__ __forceinline__ void rc_st(RcWarp& w, int i, const W4<float>& v)
 {
-    reinterpret_cast<float4*>(p)[0] = make_float4(w.c[0].r, w.c[0].i, w.c[1].r, w.c[1].i);
-    reinterpret_cast<float4*>(p)[1] = make_float4(w.c[2].r, w.c[2].i, w.c[3].r, w.c[3].i);
+    w.Wlo[i] = make_float4(v.c[0].r, v.c[0].i, v.c[1].r, v.c[1].i);
+    w.Whi[i] = make_float4(v.c[2].r, v.c[2].i, v.c[3].r, v.c[3].i);
+}
+
+// one lane's task of a step: NQ 16-byte words of 16-bit fields (low half first)
+template <int NQ> struct RcTask {
+    uint32_t q[4 * NQ];
+    __device__ __forceinline__ int f(int i) const { return (int)((q[i >> 1] >> (16 * (i & 1))) & 0xFFFFu); }
+};
+template <int NQ> __device__ __forceinline__ RcTask<NQ> rc_task(const uint32_t* tab, int step, int lane)
+{
+    RcTask<NQ> t;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) {
+        const uint4 v = __ldg(reinterpret_cast<const uint4*>(tab) + ((size_t)step * NQ + q) * 32 + lane);
+        t.q[4 * q] = v.x; t.q[4 * q + 1] = v.y; t.q[4 * q + 2] = v.z; t.q[4 * q + 3] = v.w;
+    }
+    return t;
 }
 __device__ __forceinline__ void rc_mom(const RcWarp& w, int m, float (&k)[4])
 {
-    const float4 v = *reinterpret_cast<const float4*>(&w.P[m][0]);
+    const float4 v = *reinterpret_cast<const float4*>(&w.r.P[m - 1][0]);
     k[0] = v.x; k[1] = v.y; k[2] = v.z; k[3] = v.w;
 }
+// p_t - P of subset m (the momentum of the top line after absorbing it), in FP32
 __device__ __forceinline__ void rc_qmom(const RcWarp& w, int m, float (&q)[4])
 {
-    const float4 v = *reinterpret_cast<const float4*>(&w.Q[m][0]);
-    q[0] = v.x; q[1] = v.y; q[2] = v.z; q[3] = v.w;
+    const float4 v = *reinterpret_cast<const float4*>(&w.r.P[m - 1][0]);
+    const float4 t = *reinterpret_cast<const float4*>(&w.r.pt[0]);
+    q[0] = t.x - v.x; q[1] = t.y - v.y; q[2] = t.z - v.z; q[3] = t.w - v.w;
 }
 __device__ __forceinline__ float rc_sign(unsigned bits, int b) { return (bits >> b) & 1u ? -1.0f : 1.0f; }
 
@@ -107,127 +172,127 @@ __device__ __forceinline__ void w4_acc(W4<float>& acc, const W4<float>& x)
 }
 
 // ---------------------------------------------------------------- the routines of phase 1
-// t: this lane's task, the fields of rc_tables.TASK_FIELDS (slot indices into w.W)
+// t: this lane's task, the fields of rc_tables.TASK_FIELDS (slot indices of the store)
 
-__device__ __forceinline__ void rc_task_ext(RcWarp& w, const uint16_t* t)
+template <class T> __device__ __forceinline__ void rc_task_ext(RcWarp& w, const T& t)
 {
-    const int code = __ldg(t + 1), hel = __ldg(t + 2) ? 1 : -1;
+    const int code = t.f(1), hel = t.f(2) ? 1 : -1;
     W4<float> o;
-    if (code < 4) o = ext_gluon(w.e1[code], w.e2[code], hel, code >= 2);
-    else if (code == 4) o = ext_ubar(w.fb3, hel);
-    else o = ext_v(w.fb4, hel);
-    rc_st(&w.W[__ldg(t)], o);
+    if (code < 4) o = ext_gluon(w.r.e1[code], w.r.e2[code], hel, code >= 2);
+    else if (code == 4) o = ext_ubar(w.r.fb3, hel);
+    else o = ext_v(w.r.fb4, hel);
+    rc_st(w, t.f(0), o);
 }
 
-__device__ __forceinline__ void rc_task_j2(RcWarp& w, const uint16_t* t)
+template <class T> __device__ __forceinline__ void rc_task_j2(RcWarp& w, const T& t)
 {
     float ka[4], kb[4];
-    rc_mom(w, __ldg(t + 4), ka);
-    rc_mom(w, __ldg(t + 5), kb);
-    const W4<float> o = vvv_cur(rc_ld(&w.W[__ldg(t + 1)]), rc_ld(&w.W[__ldg(t + 2)]), ka, kb, -w.iP2[__ldg(t + 6)]);
-    rc_st(&w.W[__ldg(t)], o);
+    rc_mom(w, t.f(4), ka);
+    rc_mom(w, t.f(5), kb);
+    const W4<float> o = vvv_cur(rc_ld(w, t.f(1)), rc_ld(w, t.f(2)), ka, kb, -w.r.iP2[t.f(6)]);
+    rc_st(w, t.f(0), o);
 }
 
 // J(x y z) = [ - V3(J(x), J(y z)) - V3(J(x y), J(z)) + V4(J(x), J(y), J(z)) ] / P^2
-__device__ __forceinline__ void rc_task_j3(RcWarp& w, const uint16_t* t)
+template <class T> __device__ __forceinline__ void rc_task_j3(RcWarp& w, const T& t)
 {
-    const unsigned sg = __ldg(t + 6);
-    const W4<float> x = rc_ld(&w.W[__ldg(t + 1)]), y = rc_ld(&w.W[__ldg(t + 2)]), z = rc_ld(&w.W[__ldg(t + 3)]);
+    const unsigned sg = t.f(6);
+    const W4<float> x = rc_ld(w, t.f(1)), y = rc_ld(w, t.f(2)), z = rc_ld(w, t.f(3));
     float k1[4], k2[4];
-    rc_mom(w, __ldg(t + 7), k1);
-    rc_mom(w, __ldg(t + 8), k2);
-    W4<float> acc = vvv_cur(x, rc_ld(&w.W[__ldg(t + 5)]), k1, k2, -rc_sign(sg, 0));
-    rc_mom(w, __ldg(t + 9), k1);
-    rc_mom(w, __ldg(t + 10), k2);
-    w4_acc(acc, vvv_cur(rc_ld(&w.W[__ldg(t + 4)]), z, k1, k2, -rc_sign(sg, 1)));
+    rc_mom(w, t.f(7), k1);
+    rc_mom(w, t.f(8), k2);
+    W4<float> acc = vvv_cur(x, rc_ld(w, t.f(5)), k1, k2, -rc_sign(sg, 0));
+    rc_mom(w, t.f(9), k1);
+    rc_mom(w, t.f(10), k2);
+    w4_acc(acc, vvv_cur(rc_ld(w, t.f(4)), z, k1, k2, -rc_sign(sg, 1)));
     v4_add(acc, x, y, z, 1.0f);
-    const float ip = w.iP2[__ldg(t + 11)];
+    const float ip = w.r.iP2[t.f(11)];
     W4<float> o;
 #pragma unroll
     for (int m = 0; m < 4; ++m) o.c[m] = cscale(acc.c[m], ip);
-    rc_st(&w.W[__ldg(t)], o);
+    rc_st(w, t.f(0), o);
 }
 
 // J(w x y z): three V3 splits (w | x y z), (w x | y z), (w x y | z) and three V4 splits
 // (w, x, y z), (w, x y, z), (w x, y, z)
-__device__ __forceinline__ void rc_task_j4(RcWarp& w, const uint16_t* t)
+template <class T> __device__ __forceinline__ void rc_task_j4(RcWarp& w, const T& t)
 {
-    const unsigned sg = __ldg(t + 10);
+    const unsigned sg = t.f(10);
     float k1[4], k2[4];
     W4<float> acc;
     {
-        rc_mom(w, __ldg(t + 11), k1);
-        rc_mom(w, __ldg(t + 12), k2);
-        acc = vvv_cur(rc_ld(&w.W[__ldg(t + 1)]), rc_ld(&w.W[__ldg(t + 9)]), k1, k2, -rc_sign(sg, 0));
+        rc_mom(w, t.f(11), k1);
+        rc_mom(w, t.f(12), k2);
+        acc = vvv_cur(rc_ld(w, t.f(1)), rc_ld(w, t.f(9)), k1, k2, -rc_sign(sg, 0));
     }
     {
-        rc_mom(w, __ldg(t + 13), k1);
-        rc_mom(w, __ldg(t + 14), k2);
-        w4_acc(acc, vvv_cur(rc_ld(&w.W[__ldg(t + 5)]), rc_ld(&w.W[__ldg(t + 7)]), k1, k2, -rc_sign(sg, 1)));
+        rc_mom(w, t.f(13), k1);
+        rc_mom(w, t.f(14), k2);
+        w4_acc(acc, vvv_cur(rc_ld(w, t.f(5)), rc_ld(w, t.f(7)), k1, k2, -rc_sign(sg, 1)));
     }
     {
-        rc_mom(w, __ldg(t + 15), k1);
-        rc_mom(w, __ldg(t + 16), k2);
-        w4_acc(acc, vvv_cur(rc_ld(&w.W[__ldg(t + 8)]), rc_ld(&w.W[__ldg(t + 4)]), k1, k2, -rc_sign(sg, 2)));
+        rc_mom(w, t.f(15), k1);
+        rc_mom(w, t.f(16), k2);
+        w4_acc(acc, vvv_cur(rc_ld(w, t.f(8)), rc_ld(w, t.f(4)), k1, k2, -rc_sign(sg, 2)));
     }
-    v4_add(acc, rc_ld(&w.W[__ldg(t + 1)]), rc_ld(&w.W[__ldg(t + 2)]), rc_ld(&w.W[__ldg(t + 7)]), rc_sign(sg, 3));
-    v4_add(acc, rc_ld(&w.W[__ldg(t + 1)]), rc_ld(&w.W[__ldg(t + 6)]), rc_ld(&w.W[__ldg(t + 4)]), rc_sign(sg, 4));
-    v4_add(acc, rc_ld(&w.W[__ldg(t + 5)]), rc_ld(&w.W[__ldg(t + 3)]), rc_ld(&w.W[__ldg(t + 4)]), rc_sign(sg, 5));
-    const float ip = w.iP2[__ldg(t + 17)];
+    v4_add(acc, rc_ld(w, t.f(1)), rc_ld(w, t.f(2)), rc_ld(w, t.f(7)), rc_sign(sg, 3));
+    v4_add(acc, rc_ld(w, t.f(1)), rc_ld(w, t.f(6)), rc_ld(w, t.f(4)), rc_sign(sg, 4));
+    v4_add(acc, rc_ld(w, t.f(5)), rc_ld(w, t.f(3)), rc_ld(w, t.f(4)), rc_sign(sg, 5));
+    const float ip = w.r.iP2[t.f(17)];
     W4<float> o;
 #pragma unroll
     for (int m = 0; m < 4; ++m) o.c[m] = cscale(acc.c[m], ip);
-    rc_st(&w.W[__ldg(t)], o);
+    rc_st(w, t.f(0), o);
 }
 
 // U1(a) = - ubar Jslash(a) (qslash + m) / (q^2 - m^2), q = p_t - K_a
-__device__ __forceinline__ void rc_task_u1(RcWarp& w, const uint16_t* t)
+template <class T> __device__ __forceinline__ void rc_task_u1(RcWarp& w, const T& t)
 {
-    const int qm = __ldg(t + 3);
+    const int qm = t.f(3);
     float q[4];
     rc_qmom(w, qm, q);
-    rc_st(&w.W[__ldg(t)], ffv_row(rc_ld(&w.W[__ldg(t + 1)]), rc_ld(&w.W[__ldg(t + 2)]), q, w.mt, -w.iQ[qm]));
+    rc_st(w, t.f(0), ffv_row(rc_ld(w, t.f(1)), rc_ld(w, t.f(2)), q, w.r.mt, -w.r.iQ[qm]));
 }
 
 // Vr1(d) = - (qslash + m) Jslash(d) v / (q^2 - m^2), q = p_t - (every gluon but d)
-__device__ __forceinline__ void rc_task_vr1(RcWarp& w, const uint16_t* t)
+template <class T> __device__ __forceinline__ void rc_task_vr1(RcWarp& w, const T& t)
 {
-    const int qm = __ldg(t + 3);
+    const int qm = t.f(3);
     float q[4];
     rc_qmom(w, qm, q);
-    rc_st(&w.W[__ldg(t)], ffv_col(rc_ld(&w.W[__ldg(t + 1)]), rc_ld(&w.W[__ldg(t + 2)]), q, w.mt, -w.iQ[qm]));
+    rc_st(w, t.f(0), ffv_col(rc_ld(w, t.f(1)), rc_ld(w, t.f(2)), q, w.r.mt, -w.r.iQ[qm]));
 }
 
 // U2(a b) = - [ ubar Jslash(J(a b)) + U1(a) Jslash(b) ] (qslash + m) / (q^2 - m^2)
-__device__ __forceinline__ void rc_task_u2(RcWarp& w, const uint16_t* t)
+template <class T> __device__ __forceinline__ void rc_task_u2(RcWarp& w, const T& t)
 {
-    W4<float> acc = row_jslash(rc_ld(&w.W[__ldg(t + 4)]), rc_ld(&w.W[__ldg(t + 5)]));
-    w4_fma(acc, rc_sign(__ldg(t + 3), 0), row_jslash(rc_ld(&w.W[__ldg(t + 1)]), rc_ld(&w.W[__ldg(t + 2)])));
-    const int qm = __ldg(t + 6);
+    W4<float> acc = row_jslash(rc_ld(w, t.f(4)), rc_ld(w, t.f(5)));
+    w4_fma(acc, rc_sign(t.f(3), 0), row_jslash(rc_ld(w, t.f(1)), rc_ld(w, t.f(2))));
+    const int qm = t.f(6);
     float q[4];
     rc_qmom(w, qm, q);
-    rc_st(&w.W[__ldg(t)], row_qprop(acc, q, w.mt, -w.iQ[qm]));
+    rc_st(w, t.f(0), row_qprop(acc, q, w.r.mt, -w.r.iQ[qm]));
 }
 
 // W2(c d) = Jslash(J(c d)) v + Jslash(c) Vr1(d)   (no propagator at its left end)
-__device__ __forceinline__ void rc_task_w2(RcWarp& w, const uint16_t* t)
+template <class T> __device__ __forceinline__ void rc_task_w2(RcWarp& w, const T& t)
 {
-    W4<float> acc = col_jslash(rc_ld(&w.W[__ldg(t + 4)]), rc_ld(&w.W[__ldg(t + 5)]));
-    w4_fma(acc, rc_sign(__ldg(t + 2), 0), col_jslash(rc_ld(&w.W[__ldg(t + 1)]), rc_ld(&w.W[__ldg(t + 3)])));
-    rc_st(&w.W[__ldg(t)], acc);
+    W4<float> acc = col_jslash(rc_ld(w, t.f(4)), rc_ld(w, t.f(5)));
+    w4_fma(acc, rc_sign(t.f(2), 0), col_jslash(rc_ld(w, t.f(1)), rc_ld(w, t.f(3))));
+    rc_st(w, t.f(0), acc);
 }
 
 // X = row gamma^mu col
-__device__ __forceinline__ void rc_task_x(RcWarp& w, const uint16_t* t)
+template <class T> __device__ __forceinline__ void rc_task_x(RcWarp& w, const T& t)
 {
-    rc_st(&w.W[__ldg(t)], ffv_cur(rc_ld(&w.W[__ldg(t + 1)]), rc_ld(&w.W[__ldg(t + 2)]), 1.0f));
+    rc_st(w, t.f(0), ffv_cur(rc_ld(w, t.f(1)), rc_ld(w, t.f(2)), 1.0f));
 }
 
-// the steps of one routine: lane takes task [step][lane] (out = 0xFFFF: none)
-#define MF_RC_STEPS(TYPE, FN)                                                            \
-    for (int s_ = 0; s_ < rcT::STEPS_##TYPE; ++s_) {                                    \
-        const uint16_t* t_ = &rcT::task_##TYPE[s_][lane][0];                            \
-        if (__ldg(t_) != 0xFFFFu) FN(w, t_);                                            \
+// the steps of one routine: lane takes task [step][lane] (field 0 = 0xFFFF: none)
+#define MF_RC_STEPS(TYPE, FN)                                                                              \
+    for (int s_ = 0; s_ < rcT::STEPS_##TYPE; ++s_) {                                                      \
+        const auto t_ = rc_task<rcT::NQ_##TYPE>(&rcT::task_##TYPE[0][0][0][0], s_, lane);                  \
+        if (t_.f(0) != 0xFFFF) FN(w, t_);                                                                  \
     }
 
 // Phase 1: every current of the event's store, stage by stage (a __syncwarp between
@@ -264,25 +329,24 @@ __device__ __forceinline__ cx<float> rc_rowcol(const W4<float>& a, const W4<floa
 
 // Phase 2: lane l's 24 partial amplitudes of configuration ih = 1 + 2 l, two orderings
 // at a time into its TMEM lane (bf16 pieces of the A operand and the FP32 u of the
-// colour sum).  offtab: rc_fill_offtab's table; lane_base: tc_rc_lane.
-__device__ __forceinline__ void rc_amplitudes(const RcWarp& w, const uint8_t* offtab, int lane, uint32_t lane_base)
+// colour sum).  terms: the per-lane words in shared memory; lane_base: tc_rc_lane.
+__device__ __forceinline__ void rc_amplitudes(const RcWarp& w, const uint32_t* terms, int lane, uint32_t lane_base)
 {
+    const uint32_t* lt = terms + lane;
 #pragma unroll 1
     for (int pc = 0; pc < rcT::NPERM / 2; ++pc) {
         float re[2], im[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            const uint16_t* tr = &rcT::terms[2 * pc + h][0][0];
             cx<float> acc = mkc(0.0f, 0.0f);
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
-                const int sa = tr[6 * k + 1] + offtab[tr[6 * k + 2] * 32 + lane];
-                const int sb = tr[6 * k + 3] + offtab[tr[6 * k + 4] * 32 + lane];
-                const W4<float> x = rc_ld(&w.W[sa]), y = rc_ld(&w.W[sb]);
+                const uint32_t word = lt[((2 * pc + h) * 5 + k) * 32];
+                const W4<float> x = rc_ld(w, (int)(word & 0xFFFu)), y = rc_ld(w, (int)((word >> 12) & 0xFFFu));
                 const cx<float> v = k == 0 ? rc_rowcol(x, y) : cdot(x, y);
-                const float s = tr[6 * k + 5] ? -1.0f : 1.0f;
-                acc.r = fmaf(s, v.r, acc.r);
-                acc.i = fmaf(s, v.i, acc.i);
+                const float sg = (word >> 24) ? -1.0f : 1.0f;
+                acc.r = fmaf(sg, v.r, acc.r);
+                acc.i = fmaf(sg, v.i, acc.i);
             }
             re[h] = acc.r;
             im[h] = acc.i;
@@ -295,18 +359,20 @@ __device__ __forceinline__ void rc_amplitudes(const RcWarp& w, const uint8_t* of
 
 template <> struct RcTraits<Me_gg_ttgg> {
     static constexpr size_t warp_bytes() { return sizeof(RcWarp); }
-    static constexpr size_t extra_bytes() { return RC_OFFTAB_BYTES; }
+    static constexpr size_t extra_bytes() { return RC_TERM_BYTES; }
 };
 template <> struct HasRc<Me_gg_ttgg> : std::true_type {};
 
 // after tc_setup (every thread of the CTA calls): the zero padding of the A operand and
-// the combination-offset table
+// the per-lane contraction words in shared memory
 template <class P, int TPB>
 __device__ void rc_cta_setup(unsigned char* smem_raw, TcCta* tc)
 {
     using L = SmemLayout<P, float, TPB, 2>;
+    static_assert(L::LH_EXTRA_OFF % 16 == 0, "aligned table");
     tc_rc_zero_pad<P::Me::NCOL>(tc);
-    rc_fill_offtab(smem_raw + L::LH_EXTRA_OFF);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(smem_raw + L::LH_EXTRA_OFF);
+    for (int i = threadIdx.x; i < rcT::TERM_WORDS; i += TPB) dst[i] = __ldg(&rcT::lane_terms[0][0][0] + i);
     __syncthreads();
 }
 
@@ -325,28 +391,29 @@ __device__ double rc_batch_me2(const KParams& kp, unsigned char* smem_raw, TcCta
     using L = SmemLayout<P, float, TPB, 2>;
     constexpr int WARPS = TPB / 32, NEXT = P::NEXT;
     static_assert(NEXT == 6 && ME::NCOL == rcT::NPERM && TPB == LH_TPB, "g g -> t tbar g g, one TMEM lane per thread");
-    static_assert(NEXT * 4 * TPB <= LH_INV_WORDS_MAX * LH_TPB / 2, "momenta fit the CTA's record region");
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    double* grec = reinterpret_cast<double*>(kp.inv_rec + (size_t)blockIdx.x * LH_INV_WORDS_MAX * LH_TPB);
+    // this CTA's records, field-major: word f of entry j at grec[f TPB + j]
+    float* grec = kp.inv_rec + (size_t)blockIdx.x * LH_INV_WORDS_MAX * TPB;
     if (mine) {
+        RcRec rec;
+        rc_record(pm, kp.mt, rec);
+        const float* wsrc = reinterpret_cast<const float*>(&rec);
 #pragma unroll
-        for (int f = 0; f < NEXT * 4; ++f) grec[(size_t)f * TPB + tid] = pm[f >> 2][f & 3];
+        for (int f = 0; f < RC_REC_WORDS; ++f) grec[(size_t)f * TPB + tid] = wsrc[f];
     }
     __syncthreads();
     RcWarp& w = *reinterpret_cast<RcWarp*>(smem_raw + L::LH_REC_OFF + (size_t)warp * L::LH_REC_STRIDE);
-    const uint8_t* offtab = smem_raw + L::LH_EXTRA_OFF;
+    const uint32_t* terms = reinterpret_cast<const uint32_t*>(smem_raw + L::LH_EXTRA_OFF);
     const uint32_t lb = tc_rc_lane(tc);
     const int nsub = (take + WARPS - 1) / WARPS;
     for (int sub = 0; sub < nsub; ++sub) {
         const int j = sub * WARPS + warp;
         const int jj = j < take ? j : 0;
-        double p[NEXT][4];
-#pragma unroll
-        for (int f = 0; f < NEXT * 4; ++f) p[f >> 2][f & 3] = grec[(size_t)f * TPB + jj];
-        bg_event_invariants<4, float>(w, p, kp.mt, lane);
+        float* wwords = reinterpret_cast<float*>(&w.r);
+        for (int f = lane; f < RC_REC_WORDS; f += 32) wwords[f] = grec[(size_t)f * TPB + jj];
         __syncwarp();
         rc_currents<true>(w, lane);
-        rc_amplitudes(w, offtab, lane, lb);
+        rc_amplitudes(w, terms, lane, lb);
         float mh = tc_rc_colour_sum<ME::NCOL>(tc);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) mh += __shfl_xor_sync(0xffffffffu, mh, off);

@@ -208,6 +208,7 @@ def build() -> dict:
     # phase 2: five contractions per ordering (lexicographic orderings = colour-flow order)
     perms = list(itertools.permutations(range(K)))
     terms = []
+    lane_words = []   # [ordering][term][lane]: slot of operand A | slot of B << 12 | sign << 24
     for (a, b, c_, d) in perms:
         j3a, j4, j2, j3b = J((a, b, c_)), J((a, b, c_, d)), J((b, c_)), J((b, c_, d))
         row = []
@@ -216,6 +217,15 @@ def build() -> dict:
             ox, oy = objs[x], objs[y]
             row.append([kind, ox.base, ox.lane_mask, oy.base, oy.lane_mask, 1 if sg < 0 else 0])
         terms.append(row)
+        lw = []
+        for kind, ba, ma, bb, mb, neg in row:
+            words = []
+            for lane in range(32):
+                sa, sb = ba + _pext(lane, ma), bb + _pext(lane, mb)
+                assert sa < 4096 and sb < 4096
+                words.append(sa | (sb << 12) | (neg << 24))
+            lw.append(words)
+        lane_words.append(lw)
 
     Cm = col.colour_matrix_words(perms)
     den = 1
@@ -223,8 +233,17 @@ def build() -> dict:
         for v in r:
             den = den * v.denominator // math.gcd(den, v.denominator)
     CI = [[int(v * den) for v in r] for r in Cm]
-    return dict(objs=objs, order=order, nslot=nslot, tasks=tasks, terms=terms, perms=perms, colour=CI,
-                colour_den=den)
+    return dict(objs=objs, order=order, nslot=nslot, tasks=tasks, terms=terms, lane_words=lane_words, perms=perms,
+                colour=CI, colour_den=den)
+
+
+def _pext(lane: int, mask: int) -> int:
+    r, j = 0, 0
+    for b in range(5):
+        if (mask >> b) & 1:
+            r |= ((lane >> b) & 1) << j
+            j += 1
+    return r
 
 
 # fields per task of each routine (uint16 each), and the order of the steps
@@ -278,25 +297,34 @@ def generate(name: str = "gg_ttgg") -> Tuple[str, dict]:
     L.append(f"constexpr int NSLOT = {t['nslot']};")
     L.append(f"constexpr int NPERM = {len(t['perms'])};")
     L.append(f"constexpr double COLOUR_DEN = {t['colour_den']}.0;")
+    L.append("// the tasks of a routine: [step][q][lane] 16-byte words, word q holding fields 8q .. 8q + 7 of")
+    L.append("// the lane's task (uint16 each, low half first); field 0 = 0xFFFF: no task")
     for k, v in t["tasks"].items():
         nf = TASK_FIELDS[k]
+        nq = (nf + 7) // 8
         steps = (len(v) + 31) // 32
         flat = []
         for s in range(steps):
+            rows = []
             for lane in range(32):
                 i = s * 32 + lane
-                row = v[i] if i < len(v) else [0xFFFF] + [0] * (nf - 1)   # out = 0xFFFF: no task
+                row = v[i] if i < len(v) else [0xFFFF] + [0] * (nf - 1)
                 assert len(row) == nf, (k, row)
-                flat.extend(row)
-        L.append(f"constexpr int N_{k} = {len(v)}, STEPS_{k} = {steps}, NF_{k} = {nf};")
-        L.append(_arr(f"task_{k}", "uint16_t", [steps, 32, nf], flat))
+                rows.append(row + [0] * (8 * nq - nf))
+            for q in range(nq):
+                for lane in range(32):
+                    f = rows[lane][8 * q: 8 * q + 8]
+                    flat.extend(f[2 * i] | (f[2 * i + 1] << 16) for i in range(4))
+        L.append(f"constexpr int N_{k} = {len(v)}, STEPS_{k} = {steps}, NF_{k} = {nf}, NQ_{k} = {nq};")
+        L.append(_arr(f"task_{k}", "uint32_t", [steps, nq, 32, 4], flat))
     flat = []
-    for row in t["terms"]:
-        for term in row:
-            flat.extend(term)
-    L.append("// per ordering, five contractions: kind (0: row . col, 1: Minkowski), slot base and lane mask of")
-    L.append("// the two operands, sign (1: minus)")
-    L.append(_arr("terms", "uint16_t", [len(t["terms"]), 5, 6], flat, space="__constant__"))
+    for lw in t["lane_words"]:
+        for words in lw:
+            flat.extend(words)
+    L.append("// per ordering, its five contractions (the first a row . col product, the others Minkowski")
+    L.append("// products) for every lane: slot of operand A | slot of B << 12 | sign << 24 (1: minus)")
+    L.append(f"constexpr int TERM_WORDS = {len(flat)};")
+    L.append(_arr("lane_terms", "uint32_t", [len(t["lane_words"]), 5, 32], flat))
     L.append(f"}}  // namespace rc_{name}")
     L.append("}  // namespace mf")
     return "\n".join(L) + "\n", t
