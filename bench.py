@@ -32,11 +32,14 @@ SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_NOMINAL_TFLOPS = 1.25
-# DRAM bytes (read + write) per event of the mixed g g -> t tbar g g integrand under the
-# default schedule (warp per event, tensor-core colour sum), from the dram__bytes counters of
-# the capture in profiles/integrand_gg_ttgg_mixed_1m_ncu.txt (over 1e6 events; the traffic,
-# evicted local-memory lines, grows with the number of events)
+# DRAM bytes (read + write) per event of the mixed g g -> t tbar g g integrand, from the
+# dram__bytes counters of 1e6-event ncu captures: schedule 3 (diagram helicity body, one lane
+# per helicity; profiles/integrand_gg_ttgg_mixed_1m_ncu.txt: evicted local-memory lines, which
+# grow with the number of events) and schedule 4, the default (helicity-recycled recursion;
+# profiles/integrand_gg_ttgg_recycled_1m_ncu.txt: no spills, the per-CTA records and sums)
 DRAM_BYTES_PER_EVENT_P3 = 4235.4
+DRAM_BYTES_PER_EVENT_P4 = 22.8
+DEFAULT_SCHED = 4
 
 
 def parse():
@@ -59,7 +62,8 @@ def parse():
                     help="events of the timed mixed-precision g g -> t tbar g g g pass")
     ap.add_argument("--sched", type=int, default=None,
                     help="integrand schedule (0 free warps, 1 CTA barrier per helicity, 2 = 1 + colour sum on the "
-                         "tensor cores, 3 = 2 with one warp per event and one lane per helicity; default 3)")
+                         "tensor cores, 3 = 2 with one warp per event and one lane per helicity, 4 = one warp per "
+                         "event with the helicity-recycled recursion (g g -> t tbar g g; else as 3); default 4)")
     ap.add_argument("--hsplit", type=int, default=None,
                     help="threads per event of the heavy integrand (1 or 2; default 1)")
     ap.add_argument("--only-timed", action="store_true",
@@ -136,9 +140,14 @@ class ClockSampler:
         return out
 
 
-def flops_per_event_me(process: int) -> float:
+def flops_per_event_me(process: int, sched: int = DEFAULT_SCHED) -> float:
+    """Algorithmic FLOPs of the matrix element per event passing the cuts, of the method the
+    schedule runs: the helicity-recycled recursion (g g -> t tbar g g, schedule 4) or the
+    Feynman-diagram helicity body (parity-halved helicity sum)."""
     from fractions import Fraction
-    from paper_2105_10529_gb300.gen import qcd_diagrams as Q
+    from paper_2105_10529_gb300.gen import qcd_diagrams as Q, rc_tables as RT
+    if process == 5 and sched == 4:
+        return float(RT.flops_per_event(RT.build())["total"])
     k = {1: 2, 3: 3, 5: 4}[process]
     _, st = Q.generate_gluon_process(k, "x", Fraction(1))
     return float(st["flops_me"])
@@ -639,7 +648,9 @@ def run_ours(args):
     # per-step estimate of the last iteration and the pass rate
     cnt = np.zeros(2, dtype=np.uint64)
     # dominant kernel: the fused integrand (pass) -- algorithmic FLOPs per launch
-    fl_me = flops_per_event_me(proc)
+    sched_eff = DEFAULT_SCHED if args.sched is None else args.sched
+    fl_me = flops_per_event_me(proc, sched_eff if (args.hsplit or 1) == 1 else 2)
+    fl_diagram = flops_per_event_me(proc, 3)
     # pass fraction from one extra inspection pass of the final grid
     sums_chk, evs = ctx.vegas_pass(proc, phys.sqrt_s, grid, 200_000, ev_offset=10**9, iteration=999,
                                    want_events=True, fields=("mask",))
@@ -800,21 +811,28 @@ def run_ours(args):
             "tensor cores: tcgen05.mma kind::f16, two (128 rows x 24) x (24 x 24) per step and 256-thread CTA, "
             "bf16x2 split of "
             "the colour flows, FP32 accumulation in TMEM") if (args.sched is None or args.sched >= 2) else "FP32 FMA",
-                      schedule=("one warp per event, one lane per helicity of the parity-halved sum"
-                                if args.sched is None or args.sched == 3 else f"integrand schedule {args.sched}"),
+                      schedule=("one warp per event: helicity-recycled Berends-Giele currents (lanes over "
+                                "current x helicity-combination tasks), five contractions per colour ordering and "
+                                "configuration, amplitudes written to tensor memory"
+                                if sched_eff == 4 and (args.hsplit or 1) == 1 else
+                                "one warp per event, one lane per helicity of the parity-halved sum"
+                                if sched_eff == 3 else f"integrand schedule {args.sched}"),
                       helicity_split=args.hsplit or 1),
         # per step: the integrand and the end-of-pass reduction (mf_vegas_pass) and the refinement
         "gpu_launches": 3 * args.steps,
         "roofline": {"bound": "alu", "achieved": achieved_tflops, "peak": fp32_peak, "unit": "TFLOP/s",
                      "frac": achieved_tflops / fp32_peak,
-                     "traffic": (DRAM_BYTES_PER_EVENT_P3 * N)
-                     if DRAM_BYTES_PER_EVENT_P3 is not None and (args.sched is None or args.sched == 3)
-                     and (args.hsplit or 1) == 1 else None,
+                     "traffic": ({3: DRAM_BYTES_PER_EVENT_P3, 4: DRAM_BYTES_PER_EVENT_P4}[sched_eff] * N)
+                     if sched_eff in (3, 4) and (args.hsplit or 1) == 1 else None,
                      "traffic_basis": "dram__bytes_read.sum + dram__bytes_write.sum of a 1e6-event ncu capture of the "
-                                      "same kernel, scaled to the launch's events (spill lines; grows with events)",
+                                      "same kernel, scaled to the launch's events",
                      "kernel": "integrand_kernel<gg_ttgg, float>",
                      "peak_basis": f"{SM_COUNT} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 x {SM_MAX_MHZ:.0f} MHz (nominal units and max clock)",
                      "flops_per_event_me": fl_me, "pass_fraction": pass_frac, "kernel_ms_avg": kern_avg_s * 1e3,
+                     # context: the same events at the Feynman-diagram helicity body's count (898 kFLOP per
+                     # event), i.e. the rate of diagram arithmetic this kernel replaces
+                     "diagram_equivalent_tflops": fl_diagram * N * pass_frac / kern_avg_s / 1e12,
+                     "diagram_equivalent_frac": fl_diagram * N * pass_frac / kern_avg_s / 1e12 / fp32_peak,
                      "measured_fma_peak_tflops": fma32, "frac_of_measured_fma_peak": achieved_tflops / fma32},
         "fp64_gpu": {"value": fp64_value, "unit": "events/s", "events": n64,
                      "achieved_tflops": fp64_tflops, "peak_nominal_tflops": FP64_PEAK_NOMINAL_TFLOPS,

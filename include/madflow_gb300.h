@@ -135,8 +135,8 @@ int mf_process_info(int process, int *n_ext, int *dim);
  * the device.  stream: a cudaStream_t or NULL.  On success *out owns device
  * buffers sized for every built process (about 100 MB on a 152-SM GPU:
  * per-CTA partial sums, the heavy integrand's kinematics store and the
- * per-event records of schedule 3; the batch calls add their own on first
- * use); release with mf_destroy. */
+ * per-event records of schedules 3 and 4; the batch calls add their own on
+ * first use); release with mf_destroy. */
 int mf_create(struct mf_ctx **out, const mf_config *cfg, const double *pdf_grid_host, int n_flav, int nx, int nq,
               double x_min, double q2_min, double q2_max, void *stream);
 void mf_destroy(struct mf_ctx *ctx);
@@ -149,15 +149,23 @@ int mf_set_precision(struct mf_ctx *ctx, int precision);
  * helicity (24 x 24 colour matrix, Sec. 2.2) runs on the tensor cores as one
  * (128 events x 24) x (24 x 24) contraction per 128 threads (tcgen05, bf16 split of the
  * colour-flow amplitudes, FP32 accumulation in tensor memory); elsewhere 2 acts
- * as 1.  3 (the default) = the warp-per-event schedule of g g -> t tbar g g in MF_MIXED (no
+ * as 1.  3 = the warp-per-event schedule of g g -> t tbar g g in MF_MIXED (no
  * counterpart in the paper, whose kernels give one thread per event): one warp per
  * event, its 32 lanes evaluating the 32 helicities of the parity-halved sum of
  * Sec. 2.2 at once, the colour sum on the tensor cores as in 2, and the event's
  * sum over its lanes by a fixed shuffle tree.  The warp shares one copy of the
  * event's helicity-independent pieces, so the kernel needs far less shared memory
- * and the SM's L1 keeps more of the matrix element's local memory.  Passes with
- * per-event outputs, the helicity split and the other processes run 3 as 2.
- * Schedules 0 and 1 give identical results; 2 and 3 differ from them and from
+ * and the SM's L1 keeps more of the matrix element's local memory.  The helicity
+ * split and the other processes run 3 as 2.
+ * 4 (the default) = for g g -> t tbar g g in MF_MIXED, one warp per event with the
+ * helicity-recycled Berends-Giele recursion (the same |M|^2 as Sec. 2.2's helicity
+ * loop, re-associated; no counterpart in the paper): every off-shell current is
+ * evaluated once per combination of the helicities it depends on, the colour-ordered
+ * partial amplitudes of the 32 configurations follow from five complex contractions
+ * each, and the colour sum runs on the tensor cores as in 3.  It needs the context's
+ * record region (one CTA per SM); the helicity split runs it as 2 and the other
+ * processes as 3.
+ * Schedules 0 and 1 give identical results; 2, 3 and 4 differ from them and from
  * each other by FP32 rounding.  MF_ERR_ARG for other values. */
 int mf_set_schedule(struct mf_ctx *ctx, int sched);
 /* Observable histogram (Sec. 2.1: the pipeline ends in histogram accumulation;
@@ -273,8 +281,8 @@ int mf_integrate_grid(struct mf_ctx *ctx, int process, double sqrt_s, const mf_c
  * (nullable, [n_events]) freezes the cut masks.  ev (nullable) requests the
  * per-event outputs (device arrays, caller-owned; a NULL member is skipped):
  * u, x [n_events][dim], bins [n_events][dim], w, mask, me2 [n_events],
- * momenta [n_events][n_ext][4] in the partonic rest frame.  Under schedule 3
- * and the helicity split the pass with outputs runs the very kernel that runs
+ * momenta [n_events][n_ext][4] in the partonic rest frame.  Under schedules 3
+ * and 4 and the helicity split the pass with outputs runs the very kernel that runs
  * without them (the stores are a run-time choice), so its outputs are those
  * of the timed configuration.  Does not synchronise. */
 int mf_vegas_pass(struct mf_ctx *ctx, int process, double sqrt_s, const double *grid_dev, long long n_events,
@@ -300,8 +308,8 @@ int mf_vegas_refine(struct mf_ctx *ctx, int dim, int n_bins, double alpha, const
  * Output: sums_dev [2 + dim n_bins] (device): sum w, sum w^2, histogram.
  * Kernel: integrand schedule 0 (one event per thread, colour sum on the FMA
  * pipes) whatever the precision; for g g -> t tbar g g in MF_MIXED its sums
- * therefore differ from a context's default schedule 3 by FP32 rounding
- * (about 1e-6 relative) and it runs slower.
+ * therefore differ from a context's default schedule 4 by FP32 rounding
+ * (a few 1e-6 relative) and it runs slower.
  * Scratch: a fixed 4 MiB array inside the library (the per-CTA partial
  * sums and two counters), held by every GPU that loads the library until the
  * process exits.  The first call on a device looks up that array's device
@@ -441,8 +449,8 @@ int mf_batch_grad(struct mf_ctx *ctx, int n_ch, const int *processes, const long
  * paper): mode 0/1/2 (one launch / split / per-channel kernels, see
  * mf_integrate_batch), sched 0/1 (helicity barrier off/on in the
  * g g -> t tbar g(g) matrix elements; in mode 2 also 2, the integrand
- * schedule with the tensor-core colour sum, and 3, the warp-per-event
- * schedule, as mf_set_schedule),
+ * schedule with the tensor-core colour sum, 3, the warp-per-event
+ * schedule, and 4, the helicity-recycled recursion, as mf_set_schedule),
  * tile_heavy and tile_light in [32, 2^26] events per work item for the
  * g g -> t tbar g(g) channels and for the others (in modes 1 and 2 the cheaper
  * channels' kernels get one CTA per tile_light events; in mode 2 the

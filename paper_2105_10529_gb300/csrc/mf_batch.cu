@@ -653,7 +653,7 @@ int mf_set_batch_schedule(mf_ctx* c, int mode, int sched, long long tile_heavy, 
                           int hsplit)
 {
     if (!c) return MF_ERR_ARG;
-    if (mode < 0 || mode > 2 || sched < 0 || sched > 3 || (sched >= 2 && mode != 2) || tile_heavy < 32 ||
+    if (mode < 0 || mode > 2 || sched < 0 || sched > 4 || (sched >= 2 && mode != 2) || tile_heavy < 32 ||
         tile_heavy > (1LL << 26) || tile_light < 32 || tile_light > (1LL << 26) || ctas_per_sm < 0 ||
         ctas_per_sm > 16 || (hsplit != 1 && hsplit != 2) || (hsplit == 2 && (sched != 1 || mode == 2)))
         return mf_fail(c, MF_ERR_ARG, "mf_set_batch_schedule: bad argument");
@@ -683,7 +683,7 @@ int mf_autotune_batch(mf_ctx* c, int n_ch, const int* processes, const long long
     // every channel as its own kernel: FMA or tensor-core colour sum for the expensive ones
     // (tile_heavy caps the CTAs of an expensive channel's kernel, tile_light sets a cheap one's:
     // small tiles spread a small channel over many SMs, or over few)
-    for (int sched = 1; sched <= 3; ++sched)
+    for (int sched = 1; sched <= 4; ++sched)
         for (long long th : { 512LL, 4096LL })
             for (long long tl : { 256LL, 2048LL, 4096LL }) cand.push_back(Schedule{ 2, sched, 0, th, tl, 1 });
     float best = 1e30f;

@@ -240,6 +240,10 @@ int pick_blocks(mf_ctx* c, const ProcOps* ops, size_t sm, int prec, int* nblk)
     int per_sm = 0;
     MF_CUDA(c, ops->occupancy(prec, sm, &per_sm));
     if (per_sm < 1) return fail(c, MF_ERR_CUDA, "integrand kernel does not fit on an SM");
+    if (ops->sched_ctas) {
+        const int k = ops->sched_ctas(prec, c->sched, c->hsplit);
+        if (k > 0) per_sm = k;
+    }
     int n = per_sm * c->n_sm;
     if (n > c->max_blocks) n = c->max_blocks;
     *nblk = n;

@@ -28,7 +28,7 @@ struct mf_ctx {
     float* d_inv = nullptr;          // per-event records of the warp-per-event schedule, per CTA
     int inv_ctas = 0;
     int max_blocks = 0;
-    int sched = 3;                   // integrand schedule (see mf_set_schedule)
+    int sched = 4;                   // integrand schedule (see mf_set_schedule)
     int hsplit = 1;                  // lanes per event in the heavy integrand (see mf_set_helicity_split)
     int hel_samples = 0;             // sampled helicity configurations per event (mf_set_helicity_sampling)
     uint32_t hel_stream = 0;         // stream of the helicity draws

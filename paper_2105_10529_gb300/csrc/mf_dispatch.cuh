@@ -36,6 +36,9 @@ struct ProcOps {
     // helicity sampling in the integrand (mf_set_helicity_sampling): the size of the helicity sum
     // it samples from (the parity-halved configurations), 0 where the integrand does not sample
     int hel_sample_max;
+    // CTAs per SM of the kernel that integrand() launches with these settings when it is not
+    // the occupancy of the default kernel (null, or 0: the occupancy applies)
+    int (*sched_ctas)(int prec, int sched, int hsplit) = nullptr;
 };
 
 // helicity-profile launch of a matrix element with a hel_profile member
@@ -151,17 +154,24 @@ struct IntegrandOps {
     static constexpr bool HL = HT && T32 == LH_TPB;
     static const void* fn_lh() { return (const void*)integrand_kernel<P, float, T32, false, HL, HL, 1, HL>; }
     static size_t smem_lh(int nb, int npv, bool obs) { return SmemLayout<P, float, T32, HL>::bytes(nb, npv, obs); }
-    // the helicity-recycled warp-per-event schedule (matrix elements with RcTraits, mf_rc.cuh)
+    // the helicity-recycled warp-per-event schedule (matrix elements with RcTraits, mf_rc.cuh):
+    // RC_CTAS CTAs of RC_TPB threads per SM (one of 256: two CTAs of 128, whose FP64
+    // kinematics and matrix elements could overlap, ran 10% slower with twice as many batches)
     static constexpr bool HR = ProcHasRc<P, HL>::value;
+    static constexpr int RC_TPB = 256, RC_CTAS = 1;
     static const void* fn_rc()
     {
-        if constexpr (HR) return (const void*)integrand_kernel<P, float, T32, false, true, true, 1, 2>;
+        if constexpr (HR) return (const void*)integrand_kernel<P, float, RC_TPB, false, true, true, 1, 2>;
         else return fn_lh();
     }
     static size_t smem_rc(int nb, int npv, bool obs)
     {
-        if constexpr (HR) return SmemLayout<P, float, T32, 2>::bytes(nb, npv, obs);
+        if constexpr (HR) return SmemLayout<P, float, RC_TPB, 2>::bytes(nb, npv, obs);
         else return smem_lh(nb, npv, obs);
+    }
+    static int sched_ctas(int prec, int sched, int hsplit)
+    {
+        return (HR && prec && sched == 4 && hsplit == 1) ? RC_CTAS : 0;
     }
     // the dynamic shared memory of every variant of one precision (sm32, sm64: bytes)
     static cudaError_t prepare(size_t sm32, size_t sm64)
@@ -193,10 +203,20 @@ struct IntegrandOps {
             if (e != cudaSuccess) return e;
         }
         if constexpr (HR) {
-            // the recycled schedule keeps its store in shared memory: its own limit
+            // the recycled schedule keeps its store in shared memory: its own limit, and the
+            // smallest carveout that holds its CTAs, so that L1 keeps the rest (the task tables,
+            // the PDF grid and the records are read through it; a carveout of 100% left L1
+            // 28 KB and cost 9%)
+            int dev = 0, smem_sm = 0;
+            cudaError_t e = cudaGetDevice(&dev);
+            if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+            if (e != cudaSuccess) return e;
             const size_t need = smem_rc(MAX_BINS, 0, true);
-            cudaError_t e = cudaFuncSetAttribute(fn_rc(), cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 (int)std::max(need, sm32));
+            const size_t per_sm = (need + 1024) * RC_CTAS;
+            int pct = smem_sm > 0 ? (int)((per_sm * 100 + (size_t)smem_sm - 1) / (size_t)smem_sm) : 100;
+            if (pct > 100) pct = 100;
+            e = cudaFuncSetAttribute(fn_rc(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+            if (e == cudaSuccess) e = cudaFuncSetAttribute(fn_rc(), cudaFuncAttributePreferredSharedMemoryCarveout, pct);
             if (e != cudaSuccess) return e;
         }
         return cudaSuccess;
@@ -241,16 +261,25 @@ struct IntegrandOps {
     {
         KParams arg = kp;
         void* args[1] = { &arg };
-        if (sched >= 3 && (kp.inv_rec == nullptr || nblk > kp.inv_ctas)) sched = 2;   // no record region: as 2
+        // no record region for every CTA: as schedule 2
+        if (sched == 4 && sched_ctas(prec, sched, hsplit) > 0) {
+            if (kp.inv_rec == nullptr || (long long)nblk * RC_TPB > (long long)kp.inv_ctas * LH_TPB) sched = 2;
+        } else if (sched >= 3 && (kp.inv_rec == nullptr || nblk > kp.inv_ctas)) {
+            sched = 2;
+        }
         const void* f = kernel(prec, write, sched, hsplit);
+        int threads = prec ? T32 : T64;
         if constexpr (HL) {
             // the warp-per-event kernel runs with its own, smaller dynamic shared memory
             if (f == fn_lh()) sm = smem_lh(kp.nb, kp.pdfg.nx * kp.pdfg.nq, kp.nobs > 0);
             if constexpr (HR) {
-                if (f == fn_rc()) sm = smem_rc(kp.nb, kp.pdfg.nx * kp.pdfg.nq, kp.nobs > 0);
+                if (f == fn_rc()) {
+                    sm = smem_rc(kp.nb, kp.pdfg.nx * kp.pdfg.nq, kp.nobs > 0);
+                    threads = RC_TPB;
+                }
             }
         }
-        return cudaLaunchKernel(f, dim3(nblk), dim3(prec ? T32 : T64), args, sm, s);
+        return cudaLaunchKernel(f, dim3(nblk), dim3(threads), args, sm, s);
     }
 };
 

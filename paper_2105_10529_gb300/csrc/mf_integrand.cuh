@@ -33,7 +33,7 @@ constexpr int LH_TPB = 256;             // threads per CTA of the warp-per-event
 // Feynman-diagram helicity body with one lane per configuration (schedule 3); 2, the
 // helicity-recycled recursion of mf_rc.cuh (schedule 4), for the matrix elements that
 // specialise RcTraits there: warp_bytes(), the shared memory of one warp's store, and
-// extra_bytes(), the CTA's tables after the warps' regions.
+// extra_bytes(tpb), the tables of a CTA of tpb threads after the warps' regions.
 template <class ME> struct RcTraits;
 template <class ME> struct HasRc : std::false_type {};
 
@@ -393,13 +393,13 @@ __device__ __forceinline__ void event_tops(const KParams& kp, const double* sgri
 template <class P, bool LH> struct LhRows { static constexpr int words() { return 0; } };
 template <class P> struct LhRows<P, true> { static constexpr int words() { return 2 * P::Me::NCOL + 2; } };
 // a warp's region (its record, or with LH = 2 its store) and the CTA's extra bytes after them
-template <class P, typename R, int LH> struct LhRegion {
+template <class P, typename R, int LH, int TPB> struct LhRegion {
     static constexpr size_t stride() { return (P::template slot_bytes<R>() + 15) & ~(size_t)15; }
     static constexpr size_t extra() { return 0; }
 };
-template <class P, typename R> struct LhRegion<P, R, 2> {
+template <class P, typename R, int TPB> struct LhRegion<P, R, 2, TPB> {
     static constexpr size_t stride() { return (RcTraits<typename P::Me>::warp_bytes() + 15) & ~(size_t)15; }
-    static constexpr size_t extra() { return RcTraits<typename P::Me>::extra_bytes(); }
+    static constexpr size_t extra() { return RcTraits<typename P::Me>::extra_bytes(TPB); }
 };
 
 template <class P, typename R, int TPB, int LH = 0>
@@ -413,11 +413,11 @@ struct SmemLayout {
     // CTA's extra tables (LH = 2) at LH_EXTRA_OFF
     static constexpr int LH_JROW = LhRows<P, LH == 1>::words();
     static constexpr int LH_REC_OFF = TPB * LH_JROW * (int)sizeof(R);
-    static constexpr int LH_REC_STRIDE = LH ? (int)LhRegion<P, R, LH>::stride() : 0;
+    static constexpr int LH_REC_STRIDE = LH ? (int)LhRegion<P, R, LH, TPB>::stride() : 0;
     static constexpr int LH_EXTRA_OFF = LH_REC_OFF + WARPS * LH_REC_STRIDE;
     static constexpr size_t lh_bytes()
     {
-        return LH ? al((size_t)LH_EXTRA_OFF + LhRegion<P, R, LH>::extra()) : 0;
+        return LH ? al((size_t)LH_EXTRA_OFF + LhRegion<P, R, LH, TPB>::extra()) : 0;
     }
     // warp-level matrix elements: the colour matrix and one state per warp at the start
     static constexpr __host__ __device__ size_t bg_bytes()
@@ -766,7 +766,8 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     static_assert(HS == 1 || (HS == 2 && SYNC && !WRITE), "helicity split: pairs of lanes, barrier schedule");
     static_assert(!TC || (P::TC && SYNC && (TPB == 128 || TPB == 256) && sizeof(R) == 4),
                   "tensor-core colour sum: float, barrier schedule, one TMEM lane per thread");
-    static_assert(!LH || (TC && HS == 1 && !WRITE && TPB == LH_TPB), "warp-per-event: tensor cores, no split or outputs");
+    static_assert(!LH || (TC && HS == 1 && !WRITE && (TPB == LH_TPB || (LH == 2 && TPB == 128))),
+                  "warp-per-event: tensor cores, no split or outputs");
     constexpr int D = P::D, WARPS = TPB / 32;
     using L = SmemLayout<P, R, TPB, LH>;
     const int nb = kp.nb;
@@ -968,8 +969,11 @@ __global__ void __launch_bounds__(TPB, integrand_min_ctas<P, R>()) integrand_ker
         constexpr int EPB = TPB / HS;   // events per CTA and round
         const long long first = (long long)blockIdx.x * EPB, step = (long long)gridDim.x * EPB;
         if constexpr (LH || P::BG) {
-            // the host launches this schedule only with a record region for every CTA
-            if (kp.inv_rec == nullptr || (int)blockIdx.x >= kp.inv_ctas) {
+            // the host launches this schedule only with a record region for every CTA (the
+            // recycled schedule's CTAs of TPB threads take TPB / LH_TPB of a region each)
+            const bool room = LH == 2 ? (long long)blockIdx.x * TPB < (long long)kp.inv_ctas * LH_TPB
+                                      : (int)blockIdx.x < kp.inv_ctas;
+            if (kp.inv_rec == nullptr || !room) {
                 if (threadIdx.x == 0 && kp.dev_err) atomicExch(kp.dev_err, 1u);
                 for (int i = threadIdx.x; i < 2 + P::D * kp.nb; i += TPB) out[i] = 0.0;
                 return;

@@ -28,7 +28,7 @@ cudaError_t evaluate(int prec, const double* mom, long long n, double* me2, doub
 }
 
 const ProcOps kOps = { P::D, P::NEXT, P::NPDF, &I::smem, &I::prepare, &I::occupancy, &I::integrand, &evaluate, &I::kernel,
-                         &profile_launch<Me_gg_ttgg>, Me_gg_ttgg::NHEL };
+                         &profile_launch<Me_gg_ttgg>, Me_gg_ttgg::NHEL, 0, &I::sched_ctas };
 }  // namespace
 
 const ProcOps* ops_gg_ttgg() { return &kOps; }

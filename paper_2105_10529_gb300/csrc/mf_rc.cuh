@@ -329,7 +329,9 @@ __device__ __forceinline__ cx<float> rc_rowcol(const W4<float>& a, const W4<floa
 
 // Phase 2: lane l's 24 partial amplitudes of configuration ih = 1 + 2 l, two orderings
 // at a time into its TMEM lane (bf16 pieces of the A operand and the FP32 u of the
-// colour sum).  terms: the per-lane words in shared memory; lane_base: tc_rc_lane.
+// colour sum).  terms: the per-lane words, in shared memory (GLOBAL false) or the
+// generated table itself (read through the L1 cache); lane_base: tc_rc_lane.
+template <bool GLOBAL>
 __device__ __forceinline__ void rc_amplitudes(const RcWarp& w, const uint32_t* terms, int lane, uint32_t lane_base)
 {
     const uint32_t* lt = terms + lane;
@@ -341,7 +343,7 @@ __device__ __forceinline__ void rc_amplitudes(const RcWarp& w, const uint32_t* t
             cx<float> acc = mkc(0.0f, 0.0f);
 #pragma unroll
             for (int k = 0; k < 5; ++k) {
-                const uint32_t word = lt[((2 * pc + h) * 5 + k) * 32];
+                const uint32_t word = GLOBAL ? __ldg(lt + ((2 * pc + h) * 5 + k) * 32) : lt[((2 * pc + h) * 5 + k) * 32];
                 const W4<float> x = rc_ld(w, (int)(word & 0xFFFu)), y = rc_ld(w, (int)((word >> 12) & 0xFFFu));
                 const cx<float> v = k == 0 ? rc_rowcol(x, y) : cdot(x, y);
                 const float sg = (word >> 24) ? -1.0f : 1.0f;
@@ -359,7 +361,9 @@ __device__ __forceinline__ void rc_amplitudes(const RcWarp& w, const uint32_t* t
 
 template <> struct RcTraits<Me_gg_ttgg> {
     static constexpr size_t warp_bytes() { return sizeof(RcWarp); }
-    static constexpr size_t extra_bytes() { return RC_TERM_BYTES; }
+    // CTAs of 256 threads keep the contraction words in shared memory; CTAs of 128 threads
+    // (two per SM) read them through the L1 cache and leave the room to the second CTA
+    static constexpr size_t extra_bytes(int tpb) { return tpb == 256 ? RC_TERM_BYTES : 0; }
 };
 template <> struct HasRc<Me_gg_ttgg> : std::true_type {};
 
@@ -371,8 +375,10 @@ __device__ void rc_cta_setup(unsigned char* smem_raw, TcCta* tc)
     using L = SmemLayout<P, float, TPB, 2>;
     static_assert(L::LH_EXTRA_OFF % 16 == 0, "aligned table");
     tc_rc_zero_pad<P::Me::NCOL>(tc);
-    uint32_t* dst = reinterpret_cast<uint32_t*>(smem_raw + L::LH_EXTRA_OFF);
-    for (int i = threadIdx.x; i < rcT::TERM_WORDS; i += TPB) dst[i] = __ldg(&rcT::lane_terms[0][0][0] + i);
+    if constexpr (RcTraits<typename P::Me>::extra_bytes(TPB) > 0) {
+        uint32_t* dst = reinterpret_cast<uint32_t*>(smem_raw + L::LH_EXTRA_OFF);
+        for (int i = threadIdx.x; i < rcT::TERM_WORDS; i += TPB) dst[i] = __ldg(&rcT::lane_terms[0][0][0] + i);
+    }
     __syncthreads();
 }
 
@@ -390,7 +396,9 @@ __device__ double rc_batch_me2(const KParams& kp, unsigned char* smem_raw, TcCta
     using ME = typename P::Me;
     using L = SmemLayout<P, float, TPB, 2>;
     constexpr int WARPS = TPB / 32, NEXT = P::NEXT;
-    static_assert(NEXT == 6 && ME::NCOL == rcT::NPERM && TPB == LH_TPB, "g g -> t tbar g g, one TMEM lane per thread");
+    static_assert(NEXT == 6 && ME::NCOL == rcT::NPERM && (TPB == 128 || TPB == 256),
+                  "g g -> t tbar g g, one TMEM lane per thread");
+    constexpr bool GLOBAL_TERMS = RcTraits<ME>::extra_bytes(TPB) == 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // this CTA's records, field-major: word f of entry j at grec[f TPB + j]
     float* grec = kp.inv_rec + (size_t)blockIdx.x * LH_INV_WORDS_MAX * TPB;
@@ -403,7 +411,8 @@ __device__ double rc_batch_me2(const KParams& kp, unsigned char* smem_raw, TcCta
     }
     __syncthreads();
     RcWarp& w = *reinterpret_cast<RcWarp*>(smem_raw + L::LH_REC_OFF + (size_t)warp * L::LH_REC_STRIDE);
-    const uint32_t* terms = reinterpret_cast<const uint32_t*>(smem_raw + L::LH_EXTRA_OFF);
+    const uint32_t* terms = GLOBAL_TERMS ? &rcT::lane_terms[0][0][0]
+                                         : reinterpret_cast<const uint32_t*>(smem_raw + L::LH_EXTRA_OFF);
     const uint32_t lb = tc_rc_lane(tc);
     const int nsub = (take + WARPS - 1) / WARPS;
     for (int sub = 0; sub < nsub; ++sub) {
@@ -413,7 +422,7 @@ __device__ double rc_batch_me2(const KParams& kp, unsigned char* smem_raw, TcCta
         for (int f = lane; f < RC_REC_WORDS; f += 32) wwords[f] = grec[(size_t)f * TPB + jj];
         __syncwarp();
         rc_currents<true>(w, lane);
-        rc_amplitudes(w, terms, lane, lb);
+        rc_amplitudes<GLOBAL_TERMS>(w, terms, lane, lb);
         float mh = tc_rc_colour_sum<ME::NCOL>(tc);
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) mh += __shfl_xor_sync(0xffffffffu, mh, off);

@@ -266,13 +266,16 @@ RC_FLOPS = dict(
 
 
 def flops_per_event(t: dict) -> dict:
-    """Algorithmic FLOPs per event: every task once, the contractions of every
-    ordering for each of the 32 configurations, and the colour sum (two real
-    quadratic forms of the 24 x 24 colour matrix per configuration)."""
+    """Algorithmic FLOPs per event passing the cuts: every task once, the five
+    contractions of every ordering for each of the 32 configurations, and the
+    colour sum of each configuration counted as the diagram code counts it (the
+    two real quadratic forms of the symmetric colour matrix over its upper
+    triangle, one multiply-add per nonzero entry and form, and the final products)."""
     f = {k: len(v) * RC_FLOPS[k] for k, v in t["tasks"].items()}
     n = len(t["perms"])
     f["terms"] = 32 * n * 5 * RC_FLOPS["TERM"]
-    f["colour"] = 32 * (2 * 2 * n * n)
+    nz = sum(1 for i in range(n) for j in range(i, n) if t["colour"][i][j] != 0)
+    f["colour"] = 32 * (2 * 2 * nz + 4 * n)
     f["total"] = sum(f.values())
     return f
 

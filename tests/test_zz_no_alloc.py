@@ -36,6 +36,7 @@ def test_static_scratch_pass_matches_context_pass(proc, prec):
     pdf_t = torch.tensor(pdf, device="cuda")
     cfg = make_config(phys, prec)
     ctx = Context(phys, pdf, precision=prec)
+    ctx.set_schedule(0)     # the allocation-free pass runs schedule 0 (one event per thread)
     n = 20_000 if proc == IN.GG_TTGG else 200_000
     for call, (seed, offset, it) in enumerate([(proc, 0, 2), (proc + 10, 12345, 5)]):
         grid_t = torch.tensor(random_grid(dim, seed=seed), device="cuda")
