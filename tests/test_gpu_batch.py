@@ -64,8 +64,8 @@ def test_batch_one_iteration_matches_oracle(ctx, opdf, mode):
 
 # (mode, barrier schedule, helicity split): the persistent kernel with and without the barrier and
 # the split, the split mode (heavy channels persistent, the others as their own kernels), and the
-# per-channel kernels with the warp-per-event schedule
-@pytest.mark.parametrize("mode,sched,hsplit", [(0, 0, 1), (0, 1, 2), (1, 1, 1), (2, 3, 1)])
+# per-channel kernels with the warp-per-event schedules (diagrams, helicity-recycled recursion)
+@pytest.mark.parametrize("mode,sched,hsplit", [(0, 0, 1), (0, 1, 2), (1, 1, 1), (2, 3, 1), (2, 4, 1)])
 def test_batch_pass_events_match_oracle(ctx, opdf, mode, sched, hsplit):
     """One batch pass at non-uniform caller grids with per-event outputs,
     written by the batch's own kernels (the persistent kernel in modes 0 and
@@ -157,10 +157,11 @@ def test_batch_helicity_split(ctx, mode):
     ctx.set_batch_schedule(mode, 1, TILE, 3 * TILE, 0)
 
 
-@pytest.mark.parametrize("sched", [2, 3])
+@pytest.mark.parametrize("sched", [2, 3, 4])
 def test_batch_per_channel_kernels_with_tensor_cores(sched, ctx, pdf_grid):
-    """Mode 2 with the tensor-core colour sum (integrand schedule 2) and with the
-    warp-per-event schedule (3): each channel equals a single-process
+    """Mode 2 with the tensor-core colour sum (integrand schedule 2), with the
+    warp-per-event schedule (3) and with the helicity-recycled recursion (4):
+    each channel equals a single-process
     mf_integrate on the same integrand schedule (the same kernels and launch
     configuration), and the result is stable under graph replay."""
     from paper_2105_10529_gb300.api import Context
@@ -197,7 +198,7 @@ def test_batch_autotune(ctx):
     choice = ctx.autotune_batch(CHANNELS, [40000, 10000, 10000, 8000, 4000], PHYS.sqrt_s)
     # the candidates: modes 0/1 with heavy tiles 1024/2048/4096 and light tiles 2048/4096; mode 2
     # with heavy tiles 512/4096 and light tiles 256/2048/4096
-    assert choice[0] in (0, 1, 2) and choice[1] in (0, 1, 2, 3)
+    assert choice[0] in (0, 1, 2) and choice[1] in (0, 1, 2, 3, 4)
     assert choice[2] in ((512, 4096) if choice[0] == 2 else (1024, 2048, 4096))
     assert choice[1] < 2 or choice[0] == 2
     assert choice[3] in ((256, 2048, 4096) if choice[0] == 2 else (2048, 4096))
@@ -221,7 +222,7 @@ def test_batch_bad_arguments(ctx, pdf_grid):
     assert e.value.code == 1
     for bad in [(1, 2, 1024, 4096, 0), (1, 1, 16, 4096, 0), (1, 1, 1024, 16, 0),
                 (1, 1, 1024, 4096, -1), (1, 1, 1024, 4096, 0, 3), (1, 0, 1024, 4096, 0, 2), (3, 1, 1024, 4096, 0),
-                (0, 2, 1024, 4096, 0), (2, 1, 1024, 4096, 0, 2), (1, 3, 1024, 4096, 0), (2, 4, 1024, 4096, 0)]:
+                (0, 2, 1024, 4096, 0), (2, 1, 1024, 4096, 0, 2), (1, 3, 1024, 4096, 0), (2, 5, 1024, 4096, 0)]:
         with pytest.raises(MfError):
             ctx.set_batch_schedule(*bad)
     f64 = Context(PHYS, pdf_grid, precision=0)
