@@ -328,6 +328,11 @@ def generate(name: str = "gg_ttgg") -> Tuple[str, dict]:
     L.append("// products) for every lane: slot of operand A | slot of B << 12 | sign << 24 (1: minus)")
     L.append(f"constexpr int TERM_WORDS = {len(flat)};")
     L.append(_arr("lane_terms", "uint32_t", [len(t["lane_words"]), 5, 32], flat))
+    n = len(t["perms"])
+    L.append("// the colour matrix C_{sigma tau} times COLOUR_DEN, orderings lexicographic (the per-lane")
+    L.append("// colour sum of the derivative pass reads it as constant operands)")
+    L.append(_arr("colour", "float", [n * n], [t["colour"][i][j] for i in range(n) for j in range(n)],
+                  space="__constant__"))
     L.append(f"}}  // namespace rc_{name}")
     L.append("}  // namespace mf")
     return "\n".join(L) + "\n", t
