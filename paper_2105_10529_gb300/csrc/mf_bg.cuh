@@ -28,11 +28,39 @@
 
 namespace mf {
 
+// An array of N four-component wavefunctions in shared memory, each split into 16-byte
+// chunks kept in NCH separate arrays: lanes reading different entries then fall into
+// different 16-byte bank groups eight entries apart (with whole 32- or 64-byte entries, two
+// or four apart), which removes most bank conflicts of the lanes' scattered reads.  Entries
+// are read by value (a[i]) and written with set().
+template <typename R, int N> struct W4Arr {
+    static constexpr int NCH = (int)(sizeof(W4<R>) / 16);
+    static_assert(NCH * 16 == (int)sizeof(W4<R>), "16-byte chunks");
+    float4 ch[NCH][N];
+    __device__ __forceinline__ W4<R> operator[](int i) const
+    {
+        W4<R> o;
+        float* f = reinterpret_cast<float*>(&o);
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) {
+            const float4 v = ch[k][i];
+            f[4 * k] = v.x; f[4 * k + 1] = v.y; f[4 * k + 2] = v.z; f[4 * k + 3] = v.w;
+        }
+        return o;
+    }
+    __device__ __forceinline__ void set(int i, const W4<R>& v)
+    {
+        const float* f = reinterpret_cast<const float*>(&v);
+#pragma unroll
+        for (int k = 0; k < NCH; ++k) ch[k][i] = make_float4(f[4 * k], f[4 * k + 1], f[4 * k + 2], f[4 * k + 3]);
+    }
+};
+
 // one warp's shared-memory state for an event with K gluons (T: the table namespace)
 template <typename R, int K, int NJ, int NU, int NPERM>
 struct BgWarp {
-    W4<R> J[NJ];          // gluon currents (the first K: the polarisations)
-    W4<R> U[NU];          // top-line row spinors (U[0]: ubar(p_t))
+    W4Arr<R, NJ> J;       // gluon currents (the first K: the polarisations)
+    W4Arr<R, NU> U;       // top-line row spinors (U[0]: ubar(p_t))
     W4<R> V;              // v(p_tbar)
     cx<R> A[NPERM];       // partial amplitudes of the helicity being summed
     R P[1 << K][4];       // momentum of every gluon subset (incoming convention)
@@ -131,7 +159,7 @@ __device__ __forceinline__ void bg_gluon_current(W& w, int c, int joff, const ui
     const R ip = w.iP2[__ldg(mask + c)];
     W4<R> o;
     for (int m = 0; m < 4; ++m) o.c[m] = cscale(acc.c[m], ip);
-    w.J[joff + c] = o;
+    w.J.set(joff + c, o);
 }
 
 // top-line current c of level M: sum over the split points, then the propagator
@@ -147,7 +175,7 @@ __device__ __forceinline__ void bg_top_current(W& w, int c, int uoff, const uint
     }
     const int msk = __ldg(mask + c);
     const R q[4] = { w.Q[msk][0], w.Q[msk][1], w.Q[msk][2], w.Q[msk][3] };
-    w.U[uoff + c] = row_qprop(acc, q, w.mt, -w.iQ[msk]);
+    w.U.set(uoff + c, row_qprop(acc, q, w.mt, -w.iQ[msk]));
 }
 
 
@@ -517,8 +545,8 @@ template <int K, typename R, class W>
 __device__ __forceinline__ void bg_external_states(W& w, int ih, int lane)
 {
 #define HEL(i) ((ih >> (i)) & 1 ? 1 : -1)
-    if (lane < K) w.J[lane] = ext_gluon(w.e1[lane], w.e2[lane], HEL(lane < 2 ? lane : lane + 2), lane >= 2);
-    else if (lane == K) w.U[0] = ext_ubar(w.fb3, HEL(2));
+    if (lane < K) w.J.set(lane, ext_gluon(w.e1[lane], w.e2[lane], HEL(lane < 2 ? lane : lane + 2), lane >= 2));
+    else if (lane == K) w.U.set(0, ext_ubar(w.fb3, HEL(2)));
     else if (lane == K + 1) w.V = ext_v(w.fb4, HEL(3));
 #undef HEL
 }
