@@ -818,8 +818,13 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     TcCta* tc = nullptr;
     if constexpr (TC) {
         tc = reinterpret_cast<TcCta*>(smem_raw + L::tc_off(nb, npv));
-        tc_setup<P::Me::NCOL>(tc, P::Me::colour54(), kp.dev_err, LH == 2 ? TC_RC_COLS : TC_COLS);
-        if constexpr (LH == 2) rc_cta_setup<P, TPB>(smem_raw, tc);
+        if constexpr (LH == 2) {
+            // the recursion orders its colour flows differently: its own copy of 54 C
+            tc_setup<P::Me::NCOL>(tc, RcTraits<typename P::Me>::colour54(), kp.dev_err, TC_RC_COLS);
+            rc_cta_setup<P, TPB>(smem_raw, tc);
+        } else {
+            tc_setup<P::Me::NCOL>(tc, P::Me::colour54(), kp.dev_err, TC_COLS);
+        }
     }
     if constexpr (P::BG) P::Me::load_colour(reinterpret_cast<float*>(smem_raw));
     __syncthreads();

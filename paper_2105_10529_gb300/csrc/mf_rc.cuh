@@ -350,22 +350,37 @@ template <typename R> __device__ __forceinline__ cx<R> rc_rowcol(const W4<R>& a,
     return cfma(a.c[3], b.c[3], s);
 }
 
-// Phase 2: the partial amplitudes of orderings 2 pc and 2 pc + 1 for lane l's configuration
-// ih = 1 + 2 l, five contractions each.  lt: the per-lane words (rc_gg_ttgg::lane_terms) at
-// this lane, in shared memory (GLOBAL false) or the generated table itself (read through the
-// L1 cache).
-template <typename R, bool GLOBAL>
-__device__ __forceinline__ void rc_amp_pair(const RcWarpT<R>& w, const uint32_t* lt, int pc, cx<R> (&a)[2])
+// Phase 2: the partial amplitudes of orderings 2 pc and 2 pc + 1 (an ordering and its
+// reverse) for lane l's configuration ih = 1 + 2 l, five contractions each.  lt: the per-lane
+// words (rc_gg_ttgg::lane_terms) at this lane, in shared memory (GLOBAL false) or the
+// generated table itself (read through the L1 cache).  The third term of every ordering is
+// X(ubar, v) . J(sigma), X(ubar, v) the lane's jq (loaded once per event), and the pair's two
+// third terms contract the same slots (the generator checks it): computed once.
+template <typename R> __device__ __forceinline__ W4<R> rc_jq(const RcWarpT<R>& w, const uint32_t* lt, bool global)
 {
+    const uint32_t word = global ? __ldg(lt + 2 * 32) : lt[2 * 32];
+    return rc_ld(w, (int)(word & 0xFFFu));
+}
+template <typename R, bool GLOBAL>
+__device__ __forceinline__ void rc_amp_pair(const RcWarpT<R>& w, const uint32_t* lt, int pc, const W4<R>& jq,
+                                            cx<R> (&a)[2])
+{
+    cx<R> v3 = mkc(R(0.0f), R(0.0f));
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         cx<R> acc = mkc(R(0.0f), R(0.0f));
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             const uint32_t word = GLOBAL ? __ldg(lt + ((2 * pc + h) * 5 + k) * 32) : lt[((2 * pc + h) * 5 + k) * 32];
-            const W4<R> x = rc_ld(w, (int)(word & 0xFFFu)), y = rc_ld(w, (int)((word >> 12) & 0xFFFu));
-            const cx<R> v = k == 0 ? rc_rowcol(x, y) : cdot(x, y);
-            const R sg = R((word >> 24) ? -1.0f : 1.0f);
+            cx<R> v;
+            if (k == 2) {
+                if (h == 0) v3 = cdot(jq, rc_ld(w, (int)((word >> 12) & 0xFFFu)));
+                v = v3;
+            } else {
+                const W4<R> x = rc_ld(w, (int)(word & 0xFFFu)), y = rc_ld(w, (int)((word >> 12) & 0xFFFu));
+                v = k == 0 ? rc_rowcol(x, y) : cdot(x, y);
+            }
+            const R sg = R(((word >> 24) & 1u) ? -1.0f : 1.0f);
             acc.r = fma(sg, v.r, acc.r);
             acc.i = fma(sg, v.i, acc.i);
         }
@@ -379,10 +394,11 @@ template <bool GLOBAL>
 __device__ __forceinline__ void rc_amplitudes(const RcWarp& w, const uint32_t* terms, int lane, uint32_t lane_base)
 {
     const uint32_t* lt = terms + lane;
+    const W4<float> jq = rc_jq(w, lt, GLOBAL);
 #pragma unroll 1
     for (int pc = 0; pc < rcT::NPERM / 2; ++pc) {
         cx<float> a[2];
-        rc_amp_pair<float, GLOBAL>(w, lt, pc, a);
+        rc_amp_pair<float, GLOBAL>(w, lt, pc, jq, a);
         tc_rc_put_pair(lane_base, pc, a[0].r, a[0].i, a[1].r, a[1].i);
     }
 }
@@ -390,6 +406,8 @@ __device__ __forceinline__ void rc_amplitudes(const RcWarp& w, const uint32_t* t
 // ---------------------------------------------------------------- the integrand's schedule 4
 
 template <> struct RcTraits<Me_gg_ttgg> {
+    // the colour matrix times 54 in the recursion's flow order (orderings paired with their reverses)
+    __device__ static const short* colour54() { return rcT::colour54; }
     static constexpr size_t warp_bytes() { return sizeof(RcWarp); }
     // CTAs of 256 threads keep the contraction words in shared memory; CTAs of 128 threads
     // (two per SM) read them through the L1 cache and leave the room to the second CTA
@@ -575,10 +593,11 @@ __global__ void __launch_bounds__(RC_GRAD_TPB, 1) rc_grad_kernel(KParams kp, dou
             for (int f = lane; f < NW; f += 32) wwords[f] = grec[(size_t)f * TPB + j];
             __syncwarp();
             rc_currents<R, false>(w, lane);
+            const W4<R> jq = rc_jq(w, lt, true);
 #pragma unroll 1
             for (int pc = 0; pc < rcT::NPERM / 2; ++pc) {
                 cx<R> a[2];
-                rc_amp_pair<R, true>(w, lt, pc, a);
+                rc_amp_pair<R, true>(w, lt, pc, jq, a);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     float* q = row + 4 * (2 * pc + h);

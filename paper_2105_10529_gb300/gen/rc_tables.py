@@ -206,9 +206,16 @@ def build() -> dict:
                 tasks["X"].append([out, S(row, full), S(colm, full)])
 
     # phase 2: five contractions per ordering (lexicographic orderings = colour-flow order)
-    perms = list(itertools.permutations(range(K)))
+    # the orderings in pairs (sigma, reverse sigma), the flows of the colour basis in that order:
+    # the third terms X(ubar, v) . J(sigma) of a pair contract the same two slots (J of the reversed
+    # sequence is the stored current with its sign), so the pair computes the product once (bit 25
+    # of the second's word: reuse the first's value, with the second's sign)
+    perms = []
+    for s_ in itertools.permutations(range(K)):
+        if s_ not in perms:
+            perms += [s_, tuple(reversed(s_))]
     terms = []
-    lane_words = []   # [ordering][term][lane]: slot of operand A | slot of B << 12 | sign << 24
+    lane_words = []   # [ordering][term][lane]: slot of operand A | slot of B << 12 | sign << 24 | reuse << 25
     for (a, b, c_, d) in perms:
         j3a, j4, j2, j3b = J((a, b, c_)), J((a, b, c_, d)), J((b, c_)), J((b, c_, d))
         row = []
@@ -217,13 +224,17 @@ def build() -> dict:
             ox, oy = objs[x], objs[y]
             row.append([kind, ox.base, ox.lane_mask, oy.base, oy.lane_mask, 1 if sg < 0 else 0])
         terms.append(row)
+        second = len(terms) % 2 == 0          # the second ordering of its pair
+        if second:
+            prev = terms[-2][2]
+            assert (prev[1], prev[2], prev[3], prev[4]) == tuple(row[2][1:5]), "a pair shares its J4 term"
         lw = []
-        for kind, ba, ma, bb, mb, neg in row:
+        for k, (kind, ba, ma, bb, mb, neg) in enumerate(row):
             words = []
             for lane in range(32):
                 sa, sb = ba + _pext(lane, ma), bb + _pext(lane, mb)
                 assert sa < 4096 and sb < 4096
-                words.append(sa | (sb << 12) | (neg << 24))
+                words.append(sa | (sb << 12) | (neg << 24) | ((1 << 25) if (second and k == 2) else 0))
             lw.append(words)
         lane_words.append(lw)
 
@@ -266,14 +277,15 @@ RC_FLOPS = dict(
 
 
 def flops_per_event(t: dict) -> dict:
-    """Algorithmic FLOPs per event passing the cuts: every task once, the five
+    """Algorithmic FLOPs per event passing the cuts: every task once, the
     contractions of every ordering for each of the 32 configurations, and the
     colour sum of each configuration counted as the diagram code counts it (the
     two real quadratic forms of the symmetric colour matrix over its upper
     triangle, one multiply-add per nonzero entry and form, and the final products)."""
     f = {k: len(v) * RC_FLOPS[k] for k, v in t["tasks"].items()}
     n = len(t["perms"])
-    f["terms"] = 32 * n * 5 * RC_FLOPS["TERM"]
+    # five contractions per ordering, the third shared by an ordering and its reverse
+    f["terms"] = 32 * (n * 5 - n // 2) * RC_FLOPS["TERM"]
     nz = sum(1 for i in range(n) for j in range(i, n) if t["colour"][i][j] != 0)
     f["colour"] = 32 * (2 * 2 * nz + 4 * n)
     f["total"] = sum(f.values())
@@ -324,14 +336,18 @@ def generate(name: str = "gg_ttgg") -> Tuple[str, dict]:
     for lw in t["lane_words"]:
         for words in lw:
             flat.extend(words)
-    L.append("// per ordering, its five contractions (the first a row . col product, the others Minkowski")
-    L.append("// products) for every lane: slot of operand A | slot of B << 12 | sign << 24 (1: minus)")
+    L.append("// per ordering (in pairs sigma, reverse sigma), its five contractions (the first a row . col")
+    L.append("// product, the others Minkowski products) for every lane: slot of operand A | slot of B << 12 |")
+    L.append("// sign << 24 (1: minus) | reuse << 25 (the pair's second: the third term's value is the first's)")
     L.append(f"constexpr int TERM_WORDS = {len(flat)};")
     L.append(_arr("lane_terms", "uint32_t", [len(t["lane_words"]), 5, 32], flat))
     n = len(t["perms"])
-    L.append("// the colour matrix C_{sigma tau} times COLOUR_DEN, orderings lexicographic (the per-lane")
-    L.append("// colour sum of the derivative pass reads it as constant operands)")
+    L.append("// the colour matrix C_{sigma tau} times COLOUR_DEN, the orderings in the pairs above (the per-lane")
+    L.append("// colour sum of the derivative pass reads it as constant operands, the tensor cores as shorts)")
     L.append(_arr("colour", "float", [n * n], [t["colour"][i][j] for i in range(n) for j in range(n)],
+                  space="__constant__"))
+    assert t["colour_den"] == 54
+    L.append(_arr("colour54", "short", [n * n], [t["colour"][i][j] for i in range(n) for j in range(n)],
                   space="__constant__"))
     L.append(f"}}  // namespace rc_{name}")
     L.append("}  // namespace mf")
