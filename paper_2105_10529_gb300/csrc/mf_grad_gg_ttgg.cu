@@ -5,6 +5,7 @@
 #include "generated/me_gg_ttgg.cuh"
 #include "generated/bg_gg_ttgg.cuh"
 #include "mf_rc.cuh"
+#include "mf_rc_grad.cuh"
 
 namespace mf {
 namespace {
@@ -33,7 +34,30 @@ struct RcGradPass {
         return cudaGetLastError();
     }
 };
-const GradOpsTable kGrad = { &RcGradPass<2>::grad, &E::launch, 4, true, true, true, 2 };
+// d|M|^2/dp: mixed precision by the reverse sweep of the recycled recursion (rc_evaluate_grad_kernel),
+// FP64 by the reverse sweep of the plain recursion
+struct RcEvalGrad {
+    static cudaError_t launch(int prec, const double* mom, long long n, double* me2, double* dme2, double mt,
+                              double gs, int nb, cudaStream_t s)
+    {
+        if (!prec) return E::launch(prec, mom, n, me2, dme2, mt, gs, nb, s);
+        double norm = 1.0 / (256.0 * 2);
+        for (int i = 0; i < 4; ++i) norm *= gs * gs;
+        const size_t sm = (size_t)RCE_WARPS * rce_warp_bytes();
+        static bool attr = false;
+        if (!attr) {
+            const cudaError_t e = cudaFuncSetAttribute((const void*)rc_evaluate_grad_kernel,
+                                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            if (e != cudaSuccess) return e;
+            attr = true;
+        }
+        const long long want = (n + RCE_WARPS - 1) / RCE_WARPS;
+        const int nblk = (int)(want < 8192 ? want : 8192);
+        rc_evaluate_grad_kernel<<<nblk, 32 * RCE_WARPS, sm, s>>>(mom, n, me2, dme2, mt, norm);
+        return cudaGetLastError();
+    }
+};
+const GradOpsTable kGrad = { &RcGradPass<2>::grad, &RcEvalGrad::launch, 4, true, true, true, 2 };
 }  // namespace
 
 const GradOpsTable* grad_gg_ttgg() { return &kGrad; }

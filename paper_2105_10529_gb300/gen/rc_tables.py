@@ -341,6 +341,10 @@ def generate(name: str = "gg_ttgg") -> Tuple[str, dict]:
     L.append("// sign << 24 (1: minus) | reuse << 25 (the pair's second: the third term's value is the first's)")
     L.append(f"constexpr int TERM_WORDS = {len(flat)};")
     L.append(_arr("lane_terms", "uint32_t", [len(t["lane_words"]), 5, 32], flat))
+    L.append("// the lane masks of the two operands of every contraction (mask A | mask B << 5): the lanes")
+    L.append("// whose bits agree on a mask read the same slot (the reverse sweep sums over them)")
+    L.append(_arr("term_masks", "uint16_t", [len(t["terms"]), 5],
+                  [row[k][2] | (row[k][4] << 5) for row in t["terms"] for k in range(5)], space="__constant__"))
     n = len(t["perms"])
     L.append("// the colour matrix C_{sigma tau} times COLOUR_DEN, the orderings in the pairs above (the per-lane")
     L.append("// colour sum of the derivative pass reads it as constant operands, the tensor cores as shorts)")
