@@ -322,20 +322,22 @@ def run_derivatives(ctx, phys, IN, grid, stream):
         out[f"dsigma_dmt_pass_{name}"] = {
             "events": n, "events_per_s": n / t, "s": t, "over_value_pass": t / tv, "sigma_hat_pb": r[0],
             "dsigma_dmt_pb_per_gev": r[1], "dsigma_dalphas_pb": r[3],
-            "method": ("forward mode through the Berends-Giele recursion (dual numbers), kinematics with the m_t "
-                       "tangent" if proc == IN.GG_TTGG else "forward tangents through the generated diagrams")}
+            "method": ("forward mode through the helicity-recycled recursion (dual numbers), kinematics with the "
+                       "m_t tangent" if proc == IN.GG_TTGG else "forward tangents through the generated diagrams")}
     n_ev = 100_000
     _, ev = ctx.vegas_pass(IN.GG_TTGG, phys.sqrt_s, grid, n_ev, ev_offset=5 * 10**8, iteration=78,
                            want_events=True, fields=("momenta",))
     mom = ev["momenta"]
     t, _ = timed(lambda: ctx.evaluate(IN.GG_TTGG, mom))
     out["evaluate_gg_ttgg"] = {"points": n_ev, "points_per_s": n_ev / t, "s": t}
-    n_g = 20_000
+    n_g = 100_000
     mg = mom[:n_g].contiguous()
     t, _ = timed(lambda: ctx.evaluate_grad(IN.GG_TTGG, mg))
     tv, _ = timed(lambda: ctx.evaluate(IN.GG_TTGG, mg))
     out["evaluate_with_dme2_dp_gg_ttgg"] = {"points": n_g, "points_per_s": n_g / t, "s": t, "over_value": t / tv,
-                                            "note": "reverse sweep of the Berends-Giele recursion per helicity, tangents through the invariants"}
+                                            "note": "reverse sweep of the helicity-recycled recursion, tangents "
+                                                    "through the invariants; over_value against the diagram "
+                                                    "evaluate kernel"}
     return out
 
 
