@@ -489,6 +489,21 @@ int mf_autotune_batch(struct mf_ctx *ctx, int n_ch, const int *processes, const 
  * MF_ERR_ARG for a null pointer or another precision. */
 int mf_measure_fma_peak(int precision, void *stream, double *tflops_host);
 
+/* Self-test of the double-float arithmetic (a value as the unevaluated sum of
+ * two floats, about 48 bits) in which the mixed-precision path computes its
+ * kinematics (Sec. 2.1: phase space, parton map, PDFs; no counterpart in the
+ * paper, whose kinematics run in FP64).  y_dev[i] = f(x_dev[i]) for
+ * i < n, the argument rounded to the nearest double-float and the result
+ * converted to double; f one of MF_DF_EXP (e^x, |x| < 87), MF_DF_LOG (ln x,
+ * x > 0), MF_DF_SQRT, MF_DF_SINPI (sin(pi x)), MF_DF_COSPI (cos(pi x)),
+ * MF_DF_RECIP (1/x), MF_DF_SQUARE (x x).  x_dev, y_dev: device arrays of n
+ * doubles, caller-owned.  Runs on stream (cudaStream_t or NULL) and
+ * synchronises it.  Needs no context.  MF_ERR_ARG for another f, n < 0 or a
+ * null array with n > 0; MF_ERR_CUDA on a launch failure. */
+enum { MF_DF_EXP = 0, MF_DF_LOG = 1, MF_DF_SQRT = 2, MF_DF_SINPI = 3, MF_DF_COSPI = 4, MF_DF_RECIP = 5,
+       MF_DF_SQUARE = 6 };
+int mf_selftest_df(int fn, const double *x_dev, long long n, double *y_dev, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -101,6 +101,7 @@ def lib():
             "mf_autotune_batch": (C.c_int, [vp, C.c_int, C.POINTER(C.c_int), C.POINTER(i64), C.c_double,
                                             C.POINTER(C.c_int)]),
             "mf_measure_fma_peak": (C.c_int, [C.c_int, vp, dp]),
+            "mf_selftest_df": (C.c_int, [C.c_int, vp, i64, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -115,4 +116,4 @@ def exported_symbols():
             "mf_set_precision", "mf_set_pdf", "mf_set_schedule", "mf_set_helicity_split", "mf_set_helicity_sampling", "mf_set_observable", "mf_get_observable", "mf_device_status", "mf_selftest_wait", "mf_integrate", "mf_integrate_grid", "mf_vegas_pass", "mf_vegas_refine", "mf_evaluate", "mf_helicity_profile",
             "mf_vegas_pass_static", "mf_set_couplings", "mf_vegas_pass_grad",
             "mf_integrate_batch", "mf_batch_pass", "mf_batch_grad", "mf_set_batch_schedule", "mf_autotune_batch",
-            "mf_measure_fma_peak"]
+            "mf_measure_fma_peak", "mf_selftest_df"]

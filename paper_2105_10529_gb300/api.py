@@ -346,6 +346,25 @@ def measure_fma_peak(precision: int, stream=None) -> float:
     return float(out.value)
 
 
+DF_FUNCTIONS = {"exp": 0, "log": 1, "sqrt": 2, "sinpi": 3, "cospi": 4, "recip": 5, "square": 6}
+
+
+def selftest_df(fn: str, x):
+    """The double-float function fn (a key of DF_FUNCTIONS) of the mixed-precision kinematics
+    at the points x (a float64 CUDA tensor), as doubles (mf_selftest_df)."""
+    torch = _torch()
+    if x.dtype != torch.float64 or not x.is_cuda:
+        raise ValueError("x: a float64 CUDA tensor")
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    s = torch.cuda.current_stream()
+    rc = _lib.lib().mf_selftest_df(DF_FUNCTIONS[fn], C.c_void_p(x.data_ptr()), x.numel(), C.c_void_p(y.data_ptr()),
+                                   C.c_void_p(s.cuda_stream))
+    if rc:
+        raise MfError(rc, "mf_selftest_df failed")
+    return y
+
+
 def integrate(process: int, sqrt_s: float, n_events: int, n_iter: int, physics: Optional[IN.Physics] = None,
               precision: int = _lib.MF_MIXED):
     """One-shot integrate(process, sqrt_s, n_events, n_iter) -> sigma, error (Sec. 2.1)."""

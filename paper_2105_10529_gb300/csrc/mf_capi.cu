@@ -209,7 +209,9 @@ int make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KPara
     kp.pdfg.ihx = 1.0 / kp.pdfg.hx;
     kp.pdfg.ihq = 1.0 / kp.pdfg.hq;
     kp.pdf = c->d_pdf;
+    kp.pdf_df = c->d_pdf_df;
     kp.ln_muf2_fixed = std::log(g.mt * g.mt);
+    fill_kin_df(kp.kd, kp.S, kp.ln_tau0, kp.mt, kp.vol_const, kp.ln_muf2_fixed, kp.pdfg);
     kp.partials = c->d_partials;
     kp.counters = c->d_counters;
     kp.dev_err = c->d_err;
@@ -313,6 +315,7 @@ int mf_create(mf_ctx** out, const mf_config* cfg, const double* pdf_grid_host, i
     const size_t npdf = (size_t)n_flav * nx * nq;
     const size_t ncol = 2 + (size_t)MAX_DIM * MAX_BINS;
     if (cudaMalloc(&c->d_pdf, npdf * sizeof(double)) != cudaSuccess ||
+        cudaMalloc(&c->d_pdf_df, npdf * sizeof(Df)) != cudaSuccess ||
         cudaMalloc(&c->d_grid, (size_t)MAX_DIM * (MAX_BINS + 1) * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->d_partials, (size_t)c->max_blocks * ncol * sizeof(double)) != cudaSuccess ||
         cudaMalloc(&c->d_iter, (size_t)MAX_ITER * 2 * sizeof(double)) != cudaSuccess ||
@@ -332,6 +335,11 @@ int mf_create(mf_ctx** out, const mf_config* cfg, const double* pdf_grid_host, i
         return bail(MF_ERR_CUDA);
     if (cudaMemcpy(c->d_pdf, pdf_grid_host, npdf * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess)
         return bail(MF_ERR_CUDA);
+    {
+        const std::vector<Df> pdf_df = split_df(pdf_grid_host, npdf);
+        if (cudaMemcpy(c->d_pdf_df, pdf_df.data(), npdf * sizeof(Df), cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(MF_ERR_CUDA);
+    }
     for (int p : { MF_EE_MUMU, MF_GG_TT, MF_GG_TTG, MF_GG_TTGG, MF_UU_TT, MF_UG_TTU, MF_GG_TTGGG }) {
         const ProcOps* o = proc_ops(p);
         if (o->prepare(o->smem(1, MAX_BINS, nx * nq, true), o->smem(0, MAX_BINS, nx * nq, true)) != cudaSuccess)
@@ -346,6 +354,7 @@ void mf_destroy(mf_ctx* c)
     if (!c) return;
     if (c->cap_stream) cudaStreamSynchronize(c->cap_stream);
     cudaFree(c->d_pdf);
+    cudaFree(c->d_pdf_df);
     cudaFree(c->d_grid);
     cudaFree(c->d_partials);
     cudaFree(c->d_iter);
@@ -462,8 +471,11 @@ int mf_set_helicity_sampling(mf_ctx* c, int n_samples, unsigned int stream)
 int mf_set_pdf(mf_ctx* c, const double* pdf_grid_host)
 {
     if (!c || !pdf_grid_host) return MF_ERR_ARG;
-    MF_CUDA(c, cudaMemcpyAsync(c->d_pdf, pdf_grid_host, (size_t)c->n_flav * c->nx * c->nq * sizeof(double),
-                               cudaMemcpyHostToDevice, c->stream));
+    const size_t npdf = (size_t)c->n_flav * c->nx * c->nq;
+    MF_CUDA(c, cudaMemcpyAsync(c->d_pdf, pdf_grid_host, npdf * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    // the double-float copy from pageable memory: the call returns once the host buffer is staged
+    const std::vector<Df> pdf_df = split_df(pdf_grid_host, npdf);
+    MF_CUDA(c, cudaMemcpyAsync(c->d_pdf_df, pdf_df.data(), npdf * sizeof(Df), cudaMemcpyHostToDevice, c->stream));
     return MF_OK;
 }
 

@@ -16,6 +16,7 @@ struct mf_ctx {
     int n_flav = 0, nx = 0, nq = 0;
     double x_min = 0, q2_min = 0, q2_max = 0;
     double* d_pdf = nullptr;
+    mf::Df* d_pdf_df = nullptr;   // its double-float copy (the mixed-precision kinematics)
     double* d_grid = nullptr;        // [MAX_DIM][MAX_BINS+1]
     double* d_partials = nullptr;    // [max_blocks][2 + MAX_DIM MAX_BINS]
     double* d_iter = nullptr;        // [MAX_ITER][2]

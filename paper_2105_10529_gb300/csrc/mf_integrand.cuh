@@ -16,6 +16,7 @@
 #include "mf_bg.cuh"
 #include "mf_device.cuh"
 #include "mf_helas.cuh"
+#include "mf_kin_df.cuh"
 #include "mf_tc.cuh"
 
 namespace mf {
@@ -84,6 +85,10 @@ struct KParams {
     // per event, drawn from a Philox stream of its own (counter block 0xFF, key offset by hel_stream)
     int hel_samples;
     uint32_t hel_stream;
+    // the mixed-precision path's kinematics in double-float: the constants above as double-floats
+    // (fill_kin_df) and the PDF grid's double-float copy (nullable: then converted per node)
+    KinDf kd;
+    const Df* pdf_df;
 };
 
 // the four random words of an event's helicity draws: counter (event lo, event hi, iteration,
@@ -362,6 +367,124 @@ __device__ __forceinline__ void kinematics_tops(const KParams& kp, const double*
     kinematics_tops_t<P, double>(kp, sgrid, spdf, ev, kp.mt, o, p, pref);
 }
 
+// The same kinematics in double-float (the mixed-precision path).  The VEGAS bins, the cut
+// decisions and the PDF cells are those of the FP64 kinematics (bins exactly; the cuts on the
+// lab-frame light-parton momenta converted to FP64); the momenta and the weight factor carry
+// about 48 bits.  outs: also the FP64 uniforms and mapped points of the per-event outputs.
+// sgdf: the VEGAS grid [D][nb+1] in double-float (null: sgrid's edges are converted).
+template <class P>
+__device__ __forceinline__ void kinematics_tops_df(const KParams& kp, const double* sgrid, const Df* sgdf,
+                                                   unsigned long long ev, EventOut<P::D>& o, Df (&p)[P::NEXT][4],
+                                                   Df& pref, bool outs)
+{
+    constexpr int NF = P::NF, D = P::D;
+    const KinDf& K = kp.kd;
+    unsigned long long kw[D];
+    event_words<D>(ev, kp.iteration, kp.channel, kp.key, kw);
+    Df x[D];
+    const Df jv = vegas_map_df<D>(sgdf, sgrid, kp.nb, kw, x, o.bins);
+    if (outs) {
+        uint8_t b64[D];
+        event_uniforms<D>(ev, kp.iteration, kp.channel, kp.key, o.u);
+        (void)vegas_map<D>(sgrid, kp.nb, o.u, o.x, b64);
+    }
+    // parton map: tau = tau0^x0, ln x1 = x1' ln tau, ln x2 = (1 - x1') ln tau
+    const Df lt = x[0] * K.ln_tau0;
+    const Df lx1 = x[1] * lt, lx2 = df_add(-x[1], 1.0f) * lt;
+    const Df tau = exp(lt);
+    const Df jp = tau * (-lt) * (-K.ln_tau0);
+    const Df shat = tau * K.S;
+    const Df rs = sqrt(shat);
+    Df vol = K.vol_const;
+#pragma unroll
+    for (int i = 0; i < NF - 2; ++i) vol = vol * shat;
+    Df pf[NF][4];
+    const Df wps = rambo_df<NF>(rs, K.mt, x + 2, pf, vol);
+    const Df h = df_scale(rs, 0.5f), z(0.0f, 0.0f);
+    p[0][0] = h; p[0][1] = z; p[0][2] = z; p[0][3] = h;
+    p[1][0] = h; p[1][1] = z; p[1][2] = z; p[1][3] = -h;
+#pragma unroll
+    for (int i = 0; i < NF; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) p[2 + i][c] = pf[i][c];
+    // the light partons in the lab frame (rapidity ln(x1/x2)/2), as doubles for the cuts
+    double pl[P::NEXT][4];
+#pragma unroll
+    for (int i = 0; i < P::NEXT; ++i)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) pl[i][c] = 0.0;
+    if constexpr (P::NLIGHT > 0) {
+        const Df ey = exp(df_scale(lx1 - lx2, 0.5f)), iey = df_div(Df(1.0f, 0.0f), ey);
+        const Df ch = df_scale(ey + iey, 0.5f), sh = df_scale(ey - iey, 0.5f);
+#pragma unroll
+        for (int i = 4; i < P::NEXT; ++i) {
+            pl[i][0] = (double)(ch * p[i][0] + sh * p[i][3]);
+            pl[i][1] = (double)p[i][1];
+            pl[i][2] = (double)p[i][2];
+            pl[i][3] = (double)(ch * p[i][3] + sh * p[i][0]);
+        }
+    }
+    o.mask = kp.mask_in ? (int)kp.mask_in[ev - kp.ev_offset] : cuts_tops<P>(kp, pl);
+    if (wps.hi <= 0.0f) o.mask = 0;
+    // factorisation scale: m_t for 2 -> 2, H_T / 2 otherwise (as ln mu_F^2)
+    Df lq;
+    if constexpr (NF == 2) {
+        lq = K.ln_muf2_fixed;
+    } else {
+        const Df mt2 = K.mt * K.mt;
+        Df ht(0.0f, 0.0f);
+#pragma unroll
+        for (int i = 2; i < P::NEXT; ++i) {
+            const Df pt2 = p[i][1] * p[i][1] + p[i][2] * p[i][2];
+            ht = ht + sqrt(i < 4 ? mt2 + pt2 : pt2);
+        }
+        lq = log(df_scale(ht * ht, 0.25f));
+    }
+    const int npv = kp.pdfg.nx * kp.pdfg.nq;
+    const Df* gdf = kp.pdf_df;
+    const Df xf1 = pdf_xf_df(kp.pdf + P::FLAV1 * npv, gdf ? gdf + P::FLAV1 * npv : nullptr, kp.pdfg, K, lx1, lq);
+    const Df xf2 = pdf_xf_df(kp.pdf + P::FLAV2 * npv, gdf ? gdf + P::FLAV2 * npv : nullptr, kp.pdfg, K, lx2, lq);
+    // the PDFs enter last and apart, so that two small ones do not meet in a product below
+    // the double-float range
+    pref = wps * jp * jv * GEV2_TO_PB / (df_scale(shat, 2.0f) * tau) * xf1 * xf2;
+    o.me2 = 0.0;
+    o.w = 0.0;
+}
+
+// the same, out of line: the heavy processes' kernels call it, so that its register demand
+// does not shape the allocation of their matrix-element loops (inlined, it left spills there)
+template <class P>
+__device__ __noinline__ void kinematics_tops_df_call(const KParams& kp, const double* sgrid, const Df* sgdf,
+                                                     unsigned long long ev, EventOut<P::D>& o, Df (&p)[P::NEXT][4],
+                                                     Df& pref, bool outs)
+{
+    kinematics_tops_df<P>(kp, sgrid, sgdf, ev, o, p, pref, outs);
+}
+
+// One event's kinematics in the arithmetic of its path: FP64 for the FP64 matrix elements,
+// double-float for the mixed-precision ones.  M: the type of the momenta handed on (double, or
+// Df for a matrix element that takes double-float momenta).  sgdf: the double-float VEGAS grid
+// (mixed precision; null where the kernel keeps none).  outs: the per-event outputs' uniforms and points are wanted.
+template <class P, typename R, typename M>
+__device__ __forceinline__ void kinematics_path(const KParams& kp, const double* sgrid, const Df* sgdf,
+                                                unsigned long long ev, EventOut<P::D>& o, M (&p)[P::NEXT][4],
+                                                double& pref, bool outs)
+{
+    if constexpr (sizeof(R) == 4) {
+        Df pd[P::NEXT][4], pr;
+        if constexpr (P::HEAVY) kinematics_tops_df_call<P>(kp, sgrid, sgdf, ev, o, pd, pr, outs);
+        else kinematics_tops_df<P>(kp, sgrid, sgdf, ev, o, pd, pr, outs);
+        pref = (double)pr;
+#pragma unroll
+        for (int i = 0; i < P::NEXT; ++i)
+#pragma unroll
+            for (int c = 0; c < 4; ++c) p[i][c] = M(pd[i][c]);
+    } else {
+        static_assert(std::is_same<M, double>::value, "the FP64 path hands on FP64 momenta");
+        kinematics_tops<P>(kp, sgrid, kp.pdf, ev, o, p, pref);
+    }
+}
+
 template <class P, typename R>
 __device__ __forceinline__ void event_tops(const KParams& kp, const double* sgrid, const double* spdf,
                                            unsigned long long ev, EventOut<P::D>& o, double (&p)[P::NEXT][4],
@@ -379,7 +502,7 @@ __device__ __forceinline__ void event_tops(const KParams& kp, const double* sgri
 // ------------------------------------------------------------------ shared-memory layout
 
 // Byte offsets of the kernel's dynamic shared memory:
-//   grid [D][nb+1] | histograms | value buffer |
+//   grid [D][nb+1] (and in double-float, mixed precision) | histograms | value buffer |
 //   bins buffer (heavy) | event queue and counts (heavy) | block-sum scratch |
 //   tensor-core colour-sum state (TC processes) | per-thread slots (heavy)
 // Light processes keep one histogram per warp (updated by bin leaders);
@@ -426,7 +549,12 @@ struct SmemLayout {
         else return 0;
     }
     static __host__ __device__ size_t grid_off() { return lh_bytes() + bg_bytes(); }
-    static __host__ __device__ size_t pdf_off(int nb) { return al(grid_off() + sizeof(double) * D * (nb + 1)); }
+    // the mixed-precision kinematics keep a double-float copy of the grid after the FP64 one,
+    // except for the 2 -> 3 processes, whose two CTAs per SM it would not leave room for
+    // (they convert the edges they read)
+    static constexpr bool GDF = sizeof(R) == 4 && P::NPDF > 0 && !P::STORE_KIN;
+    static __host__ __device__ size_t gdf_off(int nb) { return al(grid_off() + sizeof(double) * D * (nb + 1)); }
+    static __host__ __device__ size_t pdf_off(int nb) { return al(gdf_off(nb) + (GDF ? sizeof(Df) * D * (nb + 1) : 0)); }
     static __host__ __device__ size_t hist_off(int nb, int npv) { return al(pdf_off(nb)); }
     static __host__ __device__ size_t vbuf_off(int nb, int npv) { return al(hist_off(nb, npv) + sizeof(double) * NHIST * D * nb); }
     static __host__ __device__ size_t bbuf_off(int nb, int npv) { return al(vbuf_off(nb, npv) + sizeof(double) * TPB); }
@@ -531,13 +659,36 @@ __device__ __forceinline__ void write_event(const KParams& kp, long long e, cons
     if (kp.ev_me2) kp.ev_me2[e] = o.me2;
 }
 
-template <int NEXT>
-__device__ __forceinline__ void write_momenta(const KParams& kp, long long e, const double (&pm)[NEXT][4])
+template <int NEXT, typename M>
+__device__ __forceinline__ void write_momenta(const KParams& kp, long long e, const M (&pm)[NEXT][4])
 {
     if (kp.ev_p)
         for (int i = 0; i < NEXT; ++i)
-            for (int c = 0; c < 4; ++c) kp.ev_p[(e * NEXT + i) * 4 + c] = pm[i][c];
+            for (int c = 0; c < 4; ++c) kp.ev_p[(e * NEXT + i) * 4 + c] = (double)pm[i][c];
 }
+
+// the VEGAS grid into shared memory (every thread of the CTA calls; the caller synchronises):
+// its FP64 edges, and for the mixed-precision kinematics their double-float copy
+template <class L>
+__device__ __forceinline__ void stage_grid(const KParams& kp, unsigned char* smem_raw, double* sgrid)
+{
+    const int n = L::D * (kp.nb + 1);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) sgrid[i] = kp.grid[i];
+    if constexpr (L::GDF) {
+        Df* sgdf = reinterpret_cast<Df*>(smem_raw + L::gdf_off(kp.nb));
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sgdf[i] = Df(kp.grid[i]);
+    }
+}
+template <class L> __device__ __forceinline__ const Df* grid_df(const KParams& kp, const unsigned char* smem_raw)
+{
+    return L::GDF ? reinterpret_cast<const Df*>(smem_raw + L::gdf_off(kp.nb)) : nullptr;
+}
+
+// queued events' momenta: FP64 words, or a double-float's two floats in one 8-byte word
+__device__ __forceinline__ void kin_st(double* a, int i, double v) { a[i] = v; }
+__device__ __forceinline__ void kin_st(double* a, int i, const Df& v) { reinterpret_cast<Df*>(a)[i] = v; }
+__device__ __forceinline__ void kin_ld(const double* a, int i, double& v) { v = a[i]; }
+__device__ __forceinline__ void kin_ld(const double* a, int i, Df& v) { v = reinterpret_cast<const Df*>(a)[i]; }
 
 // Light processes (cheap matrix elements): one event per thread per round,
 // per-warp histograms updated by bin leaders.
@@ -551,7 +702,6 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
     const int nb = kp.nb;
     const int npv = kp.pdfg.nx * kp.pdfg.nq;
     double* sgrid = reinterpret_cast<double*>(smem_raw + L::grid_off());
-    const double* spdf = kp.pdf;
     double* shist = reinterpret_cast<double*>(smem_raw + L::hist_off(nb, npv));
     double* svbuf = reinterpret_cast<double*>(smem_raw + L::vbuf_off(nb, npv));
     double* sred = reinterpret_cast<double*>(smem_raw + L::red_off(nb, npv));
@@ -559,8 +709,9 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
     double* swbuf = reinterpret_cast<double*>(smem_raw + L::obs_w_off(nb, npv));
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const bool obs = kp.nobs > 0;
+    const Df* sgdf = grid_df<L>(kp, smem_raw);
 
-    for (int i = tid; i < D * (nb + 1); i += TPB) sgrid[i] = kp.grid[i];
+    stage_grid<L>(kp, smem_raw, sgrid);
     for (int i = tid; i < L::NHIST * D * nb; i += TPB) shist[i] = 0.0;
     if (obs)
         for (int i = tid; i < L::NHIST * (int)L::OBS_ROW; i += TPB) sobs[i] = 0.0;
@@ -586,7 +737,7 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
                 event_ee<R>(kp, sgrid, ev, o, pm);
             } else {
                 double pref;
-                kinematics_tops<P>(kp, sgrid, spdf, ev, o, pm, pref);
+                kinematics_path<P, R>(kp, sgrid, sgdf, ev, o, pm, pref, wr);
                 // the per-event kinematics go out before the matrix element, so that the
                 // uniforms and mapped points need not stay live across it (the same kernel
                 // serves passes with and without outputs)
@@ -731,11 +882,11 @@ __device__ __forceinline__ double bg_batch_me2(const KParams& kp, unsigned char*
 }
 
 // the helicity-recycled schedule (LH = 2), defined in mf_rc.cuh: the CTA's set-up after
-// tc_setup, and |M|^2 of a batch (as lh_batch_me2)
+// tc_setup, and |M|^2 of a batch (as lh_batch_me2; the momenta in double-float)
 template <class P, int TPB> __device__ void rc_cta_setup(unsigned char* smem_raw, TcCta* tc);
 template <class P, int TPB>
 __device__ double rc_batch_me2(const KParams& kp, unsigned char* smem_raw, TcCta* tc, double* sme, int take, bool mine,
-                               const double (&pm)[P::NEXT][4]);
+                               const Df (&pm)[P::NEXT][4]);
 
 // Heavy processes (expensive matrix elements): kinematics first, then the
 // events that pass the cuts are queued in event order and their matrix
@@ -793,7 +944,10 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     const bool wr = WRITE || kp.ev_out != 0;   // per-event outputs
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     void* slot = (void*)(smem_raw + L::slot_off(nb, npv) + (size_t)tid * P::template slot_bytes<R>());
-    const double* gpdf = kp.pdf;
+    const Df* sgdf = grid_df<L>(kp, smem_raw);
+    // the momenta handed to the matrix element: double-float for the recycled schedule, whose
+    // records take them in that arithmetic, else FP64
+    using KM = std::conditional_t<LH == 2, Df, double>;
     // batches read back the kinematics stored when the events were queued: in shared
     // memory (L::KIN), else for mixed precision in this CTA's global region (kp.kin)
     constexpr bool GKIN = !L::KIN && !WRITE && sizeof(R) == 4 && CAP <= KIN_CAP_UNIT * 2;
@@ -810,7 +964,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
         }
     }
 
-    for (int i = tid; i < D * (nb + 1); i += TPB) sgrid[i] = kp.grid[i];
+    stage_grid<L>(kp, smem_raw, sgrid);
     for (int i = tid; i < D * nb; i += TPB) shist[i] = 0.0;
     if (obs)
         for (int i = tid; i < (int)L::OBS_ROW; i += TPB) sobs[i] = 0.0;
@@ -839,9 +993,10 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             const long long e = first + r * step + tid;
             int pass = 0;
             EventOut<D> o;
-            double pm[P::NEXT][4], pref = 0.0;
+            KM pm[P::NEXT][4];
+            double pref = 0.0;
             if (tid < EPB && e < end) {
-                kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
+                kinematics_path<P, R>(kp, sgrid, sgdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref, wr);
                 pass = o.mask ? 1 : 0;
                 npass += pass;
                 if (wr) {
@@ -862,7 +1017,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
 #pragma unroll
                     for (int i = 0; i < P::NEXT; ++i)
 #pragma unroll
-                        for (int c = 0; c < 4; ++c) kpm[(i * 4 + c) * CAP + pos] = pm[i][c];
+                        for (int c = 0; c < 4; ++c) kin_st(kpm, (i * 4 + c) * CAP + pos, pm[i][c]);
                     kpref[pos] = pref;
 #pragma unroll
                     for (int d = 0; d < D; ++d) kbins[d * CAP + pos] = o.bins[d];
@@ -884,17 +1039,18 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             const int li = squeue[pos];
             const long long e = first + (long long)(li / EPB) * step + (li % EPB);
             EventOut<D> o;
-            double pm[P::NEXT][4], pref;
+            KM pm[P::NEXT][4];
+            double pref;
             if (MAYREUSE && reuse) {
 #pragma unroll
                 for (int i = 0; i < P::NEXT; ++i)
 #pragma unroll
-                    for (int c = 0; c < 4; ++c) pm[i][c] = kpm[(i * 4 + c) * CAP + pos];
+                    for (int c = 0; c < 4; ++c) kin_ld(kpm, (i * 4 + c) * CAP + pos, pm[i][c]);
                 pref = kpref[pos];
 #pragma unroll
                 for (int d = 0; d < D; ++d) o.bins[d] = kbins[d * CAP + pos];
             } else {
-                kinematics_tops<P>(kp, sgrid, gpdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref);
+                kinematics_path<P, R>(kp, sgrid, sgdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref, false);
             }
             double me;
             if constexpr (P::BG) {
@@ -935,7 +1091,7 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             for (int d = 0; d < D; ++d) sbins[d * TPB + tid] = o.bins[d];
             if (obs) {
                 swbuf[tid] = wn;
-                sobin[tid] = (int16_t)(owner ? obs_bin(kp, pm[2][1], pm[2][2]) : 0);
+                sobin[tid] = (int16_t)(owner ? obs_bin(kp, (double)pm[2][1], (double)pm[2][2]) : 0);
             }
             __syncthreads();
             if (tid < D) {

@@ -67,8 +67,8 @@ template <typename R> struct RcWarpT {
 };
 using RcWarp = RcWarpT<float>;
 
-// the record of one event (one thread, FP64 arithmetic, S = double or Dual<double> with
-// the m_t tangent); p: g g t tbar g g
+// the record of one event (one thread; S = Df, double-float for the value path, or double
+// or Dual<double> with the m_t tangent for the FP64 and derivative paths); p: g g t tbar g g
 template <typename R, typename S>
 __device__ __forceinline__ void rc_record(const S (&p)[6][4], S mt, RcRecT<R>& r)
 {
@@ -431,7 +431,8 @@ __device__ void rc_cta_setup(unsigned char* smem_raw, TcCta* tc)
 }
 
 // |M|^2 of a batch of queued events (every thread of the CTA calls; as lh_batch_me2): the
-// events' FP64 momenta go to this CTA's region of kp.inv_rec, then warp w evaluates events
+// events' records, formed from their double-float momenta, go to this CTA's region of
+// kp.inv_rec, then warp w evaluates events
 // w, w + WARPS, ... (a warp without an event in a round repeats entry 0 and discards it,
 // so that every warp takes part in the CTA barriers of each round): the invariants one
 // subset per lane, the recycled currents, each lane's amplitudes into its TMEM lane, the
@@ -439,7 +440,7 @@ __device__ void rc_cta_setup(unsigned char* smem_raw, TcCta* tc)
 // fixed shuffle tree.  Returns this thread's event's |M|^2 (meaningful where mine).
 template <class P, int TPB>
 __device__ double rc_batch_me2(const KParams& kp, unsigned char* smem_raw, TcCta* tc, double* sme, int take, bool mine,
-                               const double (&pm)[P::NEXT][4])
+                               const Df (&pm)[P::NEXT][4])
 {
     using ME = typename P::Me;
     using L = SmemLayout<P, float, TPB, 2>;
@@ -452,7 +453,7 @@ __device__ double rc_batch_me2(const KParams& kp, unsigned char* smem_raw, TcCta
     float* grec = kp.inv_rec + (size_t)blockIdx.x * LH_INV_WORDS_MAX * TPB;
     if (mine) {
         RcRec rec;
-        rc_record(pm, kp.mt, rec);
+        rc_record(pm, kp.kd.mt, rec);
         const float* wsrc = reinterpret_cast<const float*>(&rec);
 #pragma unroll
         for (int f = 0; f < RC_REC_WORDS; ++f) grec[(size_t)f * TPB + tid] = wsrc[f];
