@@ -36,9 +36,11 @@ FP64_PEAK_NOMINAL_TFLOPS = 1.25
 # dram__bytes counters of 1e6-event ncu captures: schedule 3 (diagram helicity body, one lane
 # per helicity; profiles/integrand_gg_ttgg_mixed_1m_ncu.txt: evicted local-memory lines, which
 # grow with the number of events) and schedule 4, the default (helicity-recycled recursion;
-# profiles/integrand_gg_ttgg_recycled_1m_ncu.txt: no spills, the per-CTA records and sums)
+# profiles/integrand_gg_ttgg_recycled_1m_ncu.txt: no spills; the per-CTA records and sums, and
+# the out-of-line double-float kinematics' results passed through the stack, partly evicted
+# from L2)
 DRAM_BYTES_PER_EVENT_P3 = 4235.4
-DRAM_BYTES_PER_EVENT_P4 = 22.8
+DRAM_BYTES_PER_EVENT_P4 = 111.3
 DEFAULT_SCHED = 4
 
 
