@@ -34,14 +34,14 @@ struct Me_gg_ttgg {
   // slot: this thread's Inv<R> in shared memory, or null for a private local copy
   // SYNC: a CTA barrier after every helicity (every thread of the CTA must call)
   // R: float or double (or Dual of them for derivatives); the momenta, masses and
-  // the result use the matching FP64 scalar S = Widen<R>::type
+  // the result use the scalar S of the momenta: the matching FP64 scalar Widen<R>::type,
+  // or Df (double-float) where the mixed-precision kinematics hand theirs on
   // TC: colour sum on the tensor cores (float, SYNC, CTAs of 128 or 256 threads; cta: the CTA's TcCta)
   // hpart, hparts: helicity split, this call sums every hparts-th evaluated helicity
   // from the hpart-th on (the caller adds the hparts partial sums)
-  template <typename R, bool SYNC = false, bool TC = false>
-  __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],
-                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot,
-                                                void* cta = nullptr, int hpart = 0, int hparts = 1);
+  template <typename R, bool SYNC = false, bool TC = false, typename S = typename Widen<R>::type>
+  __device__ static S me2(const S (&p)[NEXT][4], typename NoDeduce<S>::type mt, typename NoDeduce<S>::type gs,
+                         void* slot, void* cta = nullptr, int hpart = 0, int hparts = 1);
   template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }
   // per-helicity averaged |M_h|^2 of all NHEL configurations into out[NHEL] (diagnostic)
   template <typename R>
@@ -1242,11 +1242,10 @@ __device__ __noinline__ R hel_gg_ttgg(const Me_gg_ttgg::Inv<R>& v, int ih)
 #undef HEL
 }
 
-template <typename R, bool SYNC, bool TC>
-__device__ __noinline__ typename Widen<R>::type me2_gg_ttgg_impl(const typename Widen<R>::type* pflat,
-    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta, int hpart, int hparts)
+template <typename R, bool SYNC, bool TC, typename S>
+__device__ __noinline__ S me2_gg_ttgg_impl(const S* pflat, S mt, S gs, void* slot, void* cta, int hpart,
+                                       int hparts)
 {
-    using S = typename Widen<R>::type;
     constexpr int NEXT = Me_gg_ttgg::NEXT, NHEL = Me_gg_ttgg::NHEL, NGLUON = Me_gg_ttgg::NGLUON;
     constexpr double COLOUR_DEN = Me_gg_ttgg::COLOUR_DEN, AVG = Me_gg_ttgg::AVG, SYM = Me_gg_ttgg::SYM;
     S p[NEXT][4];
@@ -1359,11 +1358,11 @@ __device__ __noinline__ typename Widen<R>::type me2_gg_ttgg_impl(const typename 
     return S(acc) / COLOUR_DEN * gk * AVG * SYM;
 }
 
-template <typename R, bool SYNC, bool TC>
-__device__ typename Widen<R>::type Me_gg_ttgg::me2(const typename Widen<R>::type (&p)[NEXT][4],
-    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta, int hpart, int hparts)
+template <typename R, bool SYNC, bool TC, typename S>
+__device__ S Me_gg_ttgg::me2(const S (&p)[NEXT][4], typename NoDeduce<S>::type mt,
+    typename NoDeduce<S>::type gs, void* slot, void* cta, int hpart, int hparts)
 {
-    return me2_gg_ttgg_impl<R, SYNC, TC>(&p[0][0], mt, gs, slot, cta, hpart, hparts);
+    return me2_gg_ttgg_impl<R, SYNC, TC, S>(&p[0][0], mt, gs, slot, cta, hpart, hparts);
 }
 
 // the prologue of me2 alone: the event's helicity-independent pieces into v

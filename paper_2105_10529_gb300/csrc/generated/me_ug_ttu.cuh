@@ -13,13 +13,12 @@ struct Me_ug_ttu {
   static constexpr bool TC_COLOUR = false;
   template <typename R> struct Inv { float unused; };
   template <typename R> static constexpr size_t slot_bytes() { return 0; }
-  // averaged |M|^2 (S = Widen<R>::type carries the FP64 momenta and the result)
-  template <typename R, bool SYNC = false, bool TC = false>
-  __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],
-                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void*,
-                                                void* = nullptr, int = 0, int = 1)
+  // averaged |M|^2 (S, the scalar of the momenta, carries them and the result: the FP64
+  // scalar Widen<R>::type, or Df where the mixed-precision kinematics hand theirs on)
+  template <typename R, bool SYNC = false, bool TC = false, typename S = typename Widen<R>::type>
+  __device__ static S me2(const S (&p)[NEXT][4], typename NoDeduce<S>::type mt, typename NoDeduce<S>::type gs,
+                         void*, void* = nullptr, int = 0, int = 1)
   {
-    using S = typename Widen<R>::type;
     // momenta of the internal lines
     const S qtt[4] = {p[2][0] + p[3][0], p[2][1] + p[3][1], p[2][2] + p[3][2], p[2][3] + p[3][3]};
     const S qu[4] = {p[0][0] - p[4][0], p[0][1] - p[4][1], p[0][2] - p[4][2], p[0][3] - p[4][3]};

@@ -211,7 +211,7 @@ int make_params(mf_ctx* c, int process, const ProcOps* ops, double sqrt_s, KPara
     kp.pdf = c->d_pdf;
     kp.pdf_df = c->d_pdf_df;
     kp.ln_muf2_fixed = std::log(g.mt * g.mt);
-    fill_kin_df(kp.kd, kp.S, kp.ln_tau0, kp.mt, kp.vol_const, kp.ln_muf2_fixed, kp.pdfg);
+    fill_kin_df(kp.kd, kp.S, kp.ln_tau0, kp.mt, kp.gs, kp.vol_const, kp.ln_muf2_fixed, kp.pdfg);
     kp.partials = c->d_partials;
     kp.counters = c->d_counters;
     kp.dev_err = c->d_err;

@@ -45,6 +45,8 @@ template <typename T> struct is_dual<Dual<T>> { static constexpr bool value = tr
 // double, Dual<double> for Dual<float> and Dual<double>
 template <typename R> struct Widen { using type = double; };
 template <typename T> struct Widen<Dual<T>> { using type = Dual<double>; };
+// a parameter of type T that takes no part in template argument deduction
+template <typename T> struct NoDeduce { using type = T; };
 
 // value part of a scalar
 template <typename T> __host__ __device__ __forceinline__ T val(T x) { return x; }

@@ -689,6 +689,17 @@ __device__ __forceinline__ void kin_st(double* a, int i, double v) { a[i] = v; }
 __device__ __forceinline__ void kin_st(double* a, int i, const Df& v) { reinterpret_cast<Df*>(a)[i] = v; }
 __device__ __forceinline__ void kin_ld(const double* a, int i, double& v) { v = a[i]; }
 __device__ __forceinline__ void kin_ld(const double* a, int i, Df& v) { v = reinterpret_cast<const Df*>(a)[i]; }
+// the top mass and the strong coupling in the scalar K of the momenta (double or Df)
+template <typename K> __device__ __forceinline__ K kin_mt(const KParams& kp)
+{
+    if constexpr (std::is_same<K, Df>::value) return kp.kd.mt;
+    else return kp.mt;
+}
+template <typename K> __device__ __forceinline__ K kin_gs(const KParams& kp)
+{
+    if constexpr (std::is_same<K, Df>::value) return kp.kd.gs;
+    else return kp.gs;
+}
 
 // Light processes (cheap matrix elements): one event per thread per round,
 // per-warp histograms updated by bin leaders.
@@ -722,12 +733,14 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
     const bool wr = WRITE || kp.ev_out != 0;   // per-event outputs
     double sw = 0.0, sw2 = 0.0;
     unsigned long long npass = 0, nnan = 0;
+    // the momenta: double-float from the mixed-precision kinematics, FP64 otherwise
+    using KM = std::conditional_t<sizeof(R) == 4 && P::NPDF != 0, Df, double>;
     const long long rounds = end > first ? (end - first + step - 1) / step : 0;
     for (long long r = 0; r < rounds; ++r) {
         const long long e = first + r * step + tid;
         const bool valid = e < end;
         EventOut<D> o;
-        double pm[P::NEXT][4];
+        KM pm[P::NEXT][4];
         o.w = 0.0; o.me2 = 0.0; o.mask = 0;
 #pragma unroll
         for (int d = 0; d < D; ++d) o.bins[d] = 0;
@@ -744,7 +757,7 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
                 if (wr) { write_event<D>(kp, e, o, true); write_momenta<P::NEXT>(kp, e, pm); }
                 // matrix element only for events that pass; the warp skips it when no lane needs it
                 if (__any_sync(__activemask(), o.mask)) {
-                    if (o.mask) o.me2 = P::Me::template me2<R>(pm, kp.mt, kp.gs, nullptr);
+                    if (o.mask) o.me2 = (double)P::Me::template me2<R>(pm, kin_mt<KM>(kp), kin_gs<KM>(kp), nullptr);
                 }
                 if (o.mask) o.w = pref * o.me2;
             }
@@ -775,7 +788,7 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
             // observable: the same leader scheme on the event's p_T bin (sum w/N and sum (w/N)^2)
             swbuf[tid] = wn;
             __syncwarp();
-            const int ob = valid ? obs_bin(kp, pm[2][1], pm[2][2]) : 0;
+            const int ob = valid ? obs_bin(kp, (double)pm[2][1], (double)pm[2][2]) : 0;
             const unsigned peers = __match_any_sync(0xffffffffu, (unsigned)ob);
             if (lane == __ffs(peers) - 1) {
                 double s1 = 0.0, s2 = 0.0;
@@ -945,9 +958,10 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     void* slot = (void*)(smem_raw + L::slot_off(nb, npv) + (size_t)tid * P::template slot_bytes<R>());
     const Df* sgdf = grid_df<L>(kp, smem_raw);
-    // the momenta handed to the matrix element: double-float for the recycled schedule, whose
-    // records take them in that arithmetic, else FP64
-    using KM = std::conditional_t<LH == 2, Df, double>;
+    // the momenta handed to the matrix element: double-float where the mixed-precision matrix
+    // element takes them in that arithmetic (the recycled schedule's records, the generated
+    // prologues of the per-thread schedules), else FP64
+    using KM = std::conditional_t<LH == 2 || (sizeof(R) == 4 && LH == 0 && !P::BG), Df, double>;
     // batches read back the kinematics stored when the events were queued: in shared
     // memory (L::KIN), else for mixed precision in this CTA's global region (kp.kin)
     constexpr bool GKIN = !L::KIN && !WRITE && sizeof(R) == 4 && CAP <= KIN_CAP_UNIT * 2;
@@ -1062,9 +1076,9 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             } else if constexpr (LH == 1) {
                 me = lh_batch_me2<P, R, TPB>(kp, smem_raw, tc, svbuf, take, mine, pm);
             } else if constexpr (TC) {
-                me = P::Me::template me2<R, SYNC, true>(pm, kp.mt, kp.gs, slot, tc, hpart, HS);
+                me = (double)P::Me::template me2<R, SYNC, true>(pm, kin_mt<KM>(kp), kin_gs<KM>(kp), slot, tc, hpart, HS);
             } else {
-                me = P::Me::template me2<R, SYNC>(pm, kp.mt, kp.gs, slot, nullptr, hpart, HS);
+                me = (double)P::Me::template me2<R, SYNC>(pm, kin_mt<KM>(kp), kin_gs<KM>(kp), slot, nullptr, hpart, HS);
             }
             if constexpr (HS == 2) {
                 // the owner adds the second half, evaluated in another warp

@@ -15,14 +15,14 @@ namespace mf {
 // double-float copies of a pass's kinematic constants, filled by the host next to their FP64
 // values (fill_kin_df)
 struct KinDf {
-    Df S, ln_tau0, mt, vol_const, ln_muf2_fixed;
+    Df S, ln_tau0, mt, gs, vol_const, ln_muf2_fixed;
     Df lx0, hx, ihx, lq0, lq1, hq, ihq;   // the PDF grid's geometry
 };
 
-inline void fill_kin_df(KinDf& k, double S, double ln_tau0, double mt, double vol_const, double ln_muf2_fixed,
-                        const PdfGeom& g)
+inline void fill_kin_df(KinDf& k, double S, double ln_tau0, double mt, double gs, double vol_const,
+                        double ln_muf2_fixed, const PdfGeom& g)
 {
-    k.S = Df(S); k.ln_tau0 = Df(ln_tau0); k.mt = Df(mt); k.vol_const = Df(vol_const);
+    k.S = Df(S); k.ln_tau0 = Df(ln_tau0); k.mt = Df(mt); k.gs = Df(gs); k.vol_const = Df(vol_const);
     k.ln_muf2_fixed = Df(ln_muf2_fixed);
     k.lx0 = Df(g.lx0); k.hx = Df(g.hx); k.ihx = Df(g.ihx);
     k.lq0 = Df(g.lq0); k.lq1 = Df(g.lq1); k.hq = Df(g.hq); k.ihq = Df(g.ihq);

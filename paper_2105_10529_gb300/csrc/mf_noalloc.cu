@@ -163,7 +163,7 @@ extern "C" int mf_vegas_pass_static(int process, const mf_config* cfg, double sq
     kp.pdf = pdf_dev;
     kp.pdf_df = nullptr;   // no copy without an allocation: the mixed kinematics convert each node
     kp.ln_muf2_fixed = std::log(cfg->mt * cfg->mt);
-    fill_kin_df(kp.kd, kp.S, kp.ln_tau0, kp.mt, kp.vol_const, kp.ln_muf2_fixed, kp.pdfg);
+    fill_kin_df(kp.kd, kp.S, kp.ln_tau0, kp.mt, kp.gs, kp.vol_const, kp.ln_muf2_fixed, kp.pdfg);
     kp.grid = grid_dev;
     // layout of the shared scratch: [0..1] counters, then the partial sums
     kp.counters = reinterpret_cast<unsigned long long*>(scratch);

@@ -635,14 +635,14 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("  // slot: this thread's Inv<R> in shared memory, or null for a private local copy")
     src.append("  // SYNC: a CTA barrier after every helicity (every thread of the CTA must call)")
     src.append("  // R: float or double (or Dual of them for derivatives); the momenta, masses and")
-    src.append("  // the result use the matching FP64 scalar S = Widen<R>::type")
+    src.append("  // the result use the scalar S of the momenta: the matching FP64 scalar Widen<R>::type,")
+    src.append("  // or Df (double-float) where the mixed-precision kinematics hand theirs on")
     src.append("  // TC: colour sum on the tensor cores (float, SYNC, CTAs of 128 or 256 threads; cta: the CTA's TcCta)")
     src.append("  // hpart, hparts: helicity split, this call sums every hparts-th evaluated helicity")
     src.append("  // from the hpart-th on (the caller adds the hparts partial sums)")
-    src.append("  template <typename R, bool SYNC = false, bool TC = false>")
-    src.append("  __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],")
-    src.append("                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot,")
-    src.append("                                                void* cta = nullptr, int hpart = 0, int hparts = 1);")
+    src.append("  template <typename R, bool SYNC = false, bool TC = false, typename S = typename Widen<R>::type>")
+    src.append("  __device__ static S me2(const S (&p)[NEXT][4], typename NoDeduce<S>::type mt, typename NoDeduce<S>::type gs,")
+    src.append("                         void* slot, void* cta = nullptr, int hpart = 0, int hparts = 1);")
     src.append("  template <typename R> static constexpr size_t slot_bytes() { return sizeof(Inv<R>); }")
     src.append("  // per-helicity averaged |M_h|^2 of all NHEL configurations into out[NHEL] (diagnostic)")
     src.append("  template <typename R>")
@@ -677,11 +677,10 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("#undef HEL")
     src.append("}")
     src.append("")
-    src.append("template <typename R, bool SYNC, bool TC>")
-    src.append(f"__device__ __noinline__ typename Widen<R>::type me2_{name}_impl(const typename Widen<R>::type* pflat,")
-    src.append("    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta, int hpart, int hparts)")
+    src.append("template <typename R, bool SYNC, bool TC, typename S>")
+    src.append(f"__device__ __noinline__ S me2_{name}_impl(const S* pflat, S mt, S gs, void* slot, void* cta, int hpart,")
+    src.append("                                       int hparts)")
     src.append("{")
-    src.append("    using S = typename Widen<R>::type;")
     src.append(f"    constexpr int NEXT = Me_{name}::NEXT, NHEL = Me_{name}::NHEL, NGLUON = Me_{name}::NGLUON;")
     src.append(f"    constexpr double COLOUR_DEN = Me_{name}::COLOUR_DEN, AVG = Me_{name}::AVG, SYM = Me_{name}::SYM;")
     src.append("    S p[NEXT][4];")
@@ -719,11 +718,11 @@ def generate_gluon_process(k: int, name: str, sym: Fraction) -> Tuple[str, dict]
     src.append("    return S(acc) / COLOUR_DEN * gk * AVG * SYM;")
     src.append("}")
     src.append("")
-    src.append("template <typename R, bool SYNC, bool TC>")
-    src.append(f"__device__ typename Widen<R>::type Me_{name}::me2(const typename Widen<R>::type (&p)[NEXT][4],")
-    src.append("    typename Widen<R>::type mt, typename Widen<R>::type gs, void* slot, void* cta, int hpart, int hparts)")
+    src.append("template <typename R, bool SYNC, bool TC, typename S>")
+    src.append(f"__device__ S Me_{name}::me2(const S (&p)[NEXT][4], typename NoDeduce<S>::type mt,")
+    src.append("    typename NoDeduce<S>::type gs, void* slot, void* cta, int hpart, int hparts)")
     src.append("{")
-    src.append(f"    return me2_{name}_impl<R, SYNC, TC>(&p[0][0], mt, gs, slot, cta, hpart, hparts);")
+    src.append(f"    return me2_{name}_impl<R, SYNC, TC, S>(&p[0][0], mt, gs, slot, cta, hpart, hparts);")
     src.append("}")
     src.append("")
     src.append("// the prologue of me2 alone: the event's helicity-independent pieces into v")

@@ -94,13 +94,12 @@ def _struct(name: str, n_ext: int, n_hel: int, avg: str, k: int, prologue: List[
     s.append("  static constexpr bool TC_COLOUR = false;")
     s.append("  template <typename R> struct Inv { float unused; };")
     s.append("  template <typename R> static constexpr size_t slot_bytes() { return 0; }")
-    s.append("  // averaged |M|^2 (S = Widen<R>::type carries the FP64 momenta and the result)")
-    s.append("  template <typename R, bool SYNC = false, bool TC = false>")
-    s.append("  __device__ static typename Widen<R>::type me2(const typename Widen<R>::type (&p)[NEXT][4],")
-    s.append("                                                typename Widen<R>::type mt, typename Widen<R>::type gs, void*,")
-    s.append("                                                void* = nullptr, int = 0, int = 1)")
+    s.append("  // averaged |M|^2 (S, the scalar of the momenta, carries them and the result: the FP64")
+    s.append("  // scalar Widen<R>::type, or Df where the mixed-precision kinematics hand theirs on)")
+    s.append("  template <typename R, bool SYNC = false, bool TC = false, typename S = typename Widen<R>::type>")
+    s.append("  __device__ static S me2(const S (&p)[NEXT][4], typename NoDeduce<S>::type mt, typename NoDeduce<S>::type gs,")
+    s.append("                         void*, void* = nullptr, int = 0, int = 1)")
     s.append("  {")
-    s.append("    using S = typename Widen<R>::type;")
     for l in prologue:
         s.append("    " + l)
     s.append("    R acc = R(0);")
