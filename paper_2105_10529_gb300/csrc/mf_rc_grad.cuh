@@ -2,7 +2,7 @@
 // (mf_rc.cuh), one warp per point, mixed precision: the derivative of the matrix element of
 // Sec. 2.2 with respect to every momentum component (the momenta as independent variables).
 //
-// Forward: the record (FP64 arithmetic), the recycled currents and each lane's 24 partial
+// Forward: the record (double-float arithmetic), the recycled currents and each lane's 24 partial
 // amplitudes, as the value kernel.  Backward, with a second store of the same layout for the
 // adjoints (zb = dL/dRe z + i dL/dIm z of L, the helicity-summed colour sum):
 //  * the colour sum: Abar = 2 (C A), doubled for the parity mirrors;
@@ -407,14 +407,19 @@ __global__ void __launch_bounds__(32 * RCE_WARPS, 1) rc_evaluate_grad_kernel(con
     RcEvalWarp& st = *reinterpret_cast<RcEvalWarp*>(mf_rce_smem + (size_t)warp * rce_warp_bytes());
     const uint32_t* lt = &rcT::lane_terms[0][0][0] + lane;
     float* row = st.rows[lane];
+    const Df mt_df(mt);
     for (long long e = (long long)blockIdx.x * RCE_WARPS + warp; e < n; e += (long long)gridDim.x * RCE_WARPS) {
         double p[NEXT][4];
 #pragma unroll
         for (int f = 0; f < NEXT * 4; ++f) p[f >> 2][f & 3] = mom[e * NEXT * 4 + f];
         {
-            // every lane forms the record, each stores its share of the words
+            // every lane forms the record (in double-float arithmetic, as the integrand's), each
+            // stores its share of the words
+            Df pdf[NEXT][4];
+#pragma unroll
+            for (int f = 0; f < NEXT * 4; ++f) pdf[f >> 2][f & 3] = Df(p[f >> 2][f & 3]);
             RcRec rec;
-            rc_record<float>(p, mt, rec);
+            rc_record<float>(pdf, mt_df, rec);
             const float* ws = reinterpret_cast<const float*>(&rec);
             float* wd = reinterpret_cast<float*>(&st.w.r);
             for (int f = lane; f < RC_REC_WORDS; f += 32) wd[f] = ws[f];
