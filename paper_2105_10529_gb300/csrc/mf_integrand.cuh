@@ -502,7 +502,7 @@ __device__ __forceinline__ void event_tops(const KParams& kp, const double* sgri
 // ------------------------------------------------------------------ shared-memory layout
 
 // Byte offsets of the kernel's dynamic shared memory:
-//   grid [D][nb+1] (and in double-float, mixed precision) | histograms | value buffer |
+//   grid [D][nb+1] (FP64, or double-float for the mixed kinematics) | histograms | value buffer |
 //   bins buffer (heavy) | event queue and counts (heavy) | block-sum scratch |
 //   tensor-core colour-sum state (TC processes) | per-thread slots (heavy)
 // Light processes keep one histogram per warp (updated by bin leaders);
@@ -549,12 +549,13 @@ struct SmemLayout {
         else return 0;
     }
     static __host__ __device__ size_t grid_off() { return lh_bytes() + bg_bytes(); }
-    // the mixed-precision kinematics keep a double-float copy of the grid after the FP64 one,
-    // except for the 2 -> 3 processes, whose two CTAs per SM it would not leave room for
-    // (they convert the edges they read)
-    static constexpr bool GDF = sizeof(R) == 4 && P::NPDF > 0 && !P::STORE_KIN;
-    static __host__ __device__ size_t gdf_off(int nb) { return al(grid_off() + sizeof(double) * D * (nb + 1)); }
-    static __host__ __device__ size_t pdf_off(int nb) { return al(gdf_off(nb) + (GDF ? sizeof(Df) * D * (nb + 1) : 0)); }
+    // the mixed-precision kinematics keep the grid in double-float in the FP64 grid's place (8
+    // bytes an edge either way: the recycled kernel's shared memory stays below the 196 KB
+    // carveout step, which leaves L1 60 KB instead of 28); their per-event outputs read the FP64
+    // edges from global memory
+    static constexpr bool GDF = sizeof(R) == 4 && P::NPDF > 0;
+    static __host__ __device__ size_t gdf_off(int nb) { return grid_off(); }
+    static __host__ __device__ size_t pdf_off(int nb) { return al(grid_off() + sizeof(double) * D * (nb + 1)); }
     static __host__ __device__ size_t hist_off(int nb, int npv) { return al(pdf_off(nb)); }
     static __host__ __device__ size_t vbuf_off(int nb, int npv) { return al(hist_off(nb, npv) + sizeof(double) * NHIST * D * nb); }
     static __host__ __device__ size_t bbuf_off(int nb, int npv) { return al(vbuf_off(nb, npv) + sizeof(double) * TPB); }
@@ -668,20 +669,27 @@ __device__ __forceinline__ void write_momenta(const KParams& kp, long long e, co
 }
 
 // the VEGAS grid into shared memory (every thread of the CTA calls; the caller synchronises):
-// its FP64 edges, and for the mixed-precision kinematics their double-float copy
+// its FP64 edges, or for the mixed-precision kinematics their double-float values
 template <class L>
 __device__ __forceinline__ void stage_grid(const KParams& kp, unsigned char* smem_raw, double* sgrid)
 {
     const int n = L::D * (kp.nb + 1);
-    for (int i = threadIdx.x; i < n; i += blockDim.x) sgrid[i] = kp.grid[i];
     if constexpr (L::GDF) {
         Df* sgdf = reinterpret_cast<Df*>(smem_raw + L::gdf_off(kp.nb));
         for (int i = threadIdx.x; i < n; i += blockDim.x) sgdf[i] = Df(kp.grid[i]);
+    } else {
+        for (int i = threadIdx.x; i < n; i += blockDim.x) sgrid[i] = kp.grid[i];
     }
 }
 template <class L> __device__ __forceinline__ const Df* grid_df(const KParams& kp, const unsigned char* smem_raw)
 {
     return L::GDF ? reinterpret_cast<const Df*>(smem_raw + L::gdf_off(kp.nb)) : nullptr;
+}
+// the FP64 edges the kinematics read: shared memory, or global memory where the shared copy is
+// double-float (only the per-event outputs read them then)
+template <class L> __device__ __forceinline__ const double* grid_fp64(const KParams& kp, const double* sgrid)
+{
+    return L::GDF ? kp.grid : sgrid;
 }
 
 // queued events' momenta: FP64 words, or a double-float's two floats in one 8-byte word
@@ -750,7 +758,7 @@ __device__ __forceinline__ void integrand_light(const KParams& kp, unsigned char
                 event_ee<R>(kp, sgrid, ev, o, pm);
             } else {
                 double pref;
-                kinematics_path<P, R>(kp, sgrid, sgdf, ev, o, pm, pref, wr);
+                kinematics_path<P, R>(kp, grid_fp64<L>(kp, sgrid), sgdf, ev, o, pm, pref, wr);
                 // the per-event kinematics go out before the matrix element, so that the
                 // uniforms and mapped points need not stay live across it (the same kernel
                 // serves passes with and without outputs)
@@ -1010,7 +1018,8 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
             KM pm[P::NEXT][4];
             double pref = 0.0;
             if (tid < EPB && e < end) {
-                kinematics_path<P, R>(kp, sgrid, sgdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref, wr);
+                kinematics_path<P, R>(kp, grid_fp64<L>(kp, sgrid), sgdf, (unsigned long long)(kp.ev_offset + e), o, pm,
+                                      pref, wr);
                 pass = o.mask ? 1 : 0;
                 npass += pass;
                 if (wr) {
@@ -1064,7 +1073,8 @@ __device__ __forceinline__ void integrand_heavy(const KParams& kp, unsigned char
 #pragma unroll
                 for (int d = 0; d < D; ++d) o.bins[d] = kbins[d * CAP + pos];
             } else {
-                kinematics_path<P, R>(kp, sgrid, sgdf, (unsigned long long)(kp.ev_offset + e), o, pm, pref, false);
+                kinematics_path<P, R>(kp, grid_fp64<L>(kp, sgrid), sgdf, (unsigned long long)(kp.ev_offset + e), o, pm,
+                                      pref, false);
             }
             double me;
             if constexpr (P::BG) {
