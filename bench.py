@@ -40,7 +40,7 @@ FP64_PEAK_NOMINAL_TFLOPS = 1.25
 # the out-of-line double-float kinematics' results passed through the stack, partly evicted
 # from L2)
 DRAM_BYTES_PER_EVENT_P3 = 4235.4
-DRAM_BYTES_PER_EVENT_P4 = 111.3
+DRAM_BYTES_PER_EVENT_P4 = 109.9
 DEFAULT_SCHED = 4
 
 
