@@ -175,7 +175,7 @@ def run_batch(ctx, phys, IN, n_iter):
     # the chosen schedule, and one representative schedule per mode
     t_batch, (tot, chans) = timed(choice)
     per_mode = {0: timed((0, 1, 4096, 4096, 0, 1)), 1: timed((1, 1, 4096, 4096, 0, 1)),
-                2: timed((2, 3, 4096, 4096, 0, 1))}
+                2: timed((2, 3, 4096, 4096, 0, 1)), 3: timed((3, 4, 4096, 2048, 0, 1))}
     ctx.set_batch_schedule(*choice)
     ctx.integrate_batch(procs, ns, phys.sqrt_s, n_iter)               # grids of the chosen schedule
     g = ctx.batch_grad(procs, ns, phys.sqrt_s, 1000)
@@ -191,13 +191,15 @@ def run_batch(ctx, phys, IN, n_iter):
             "events_per_s": ev / t_batch, "s_per_call": t_batch,
             "sequential_events_per_s": ev / t_seq, "speedup_vs_sequential": t_seq / t_batch,
             "sequential_s_by_channel": {names[p]: t for p, t in zip(procs, t_ch)},
-            "schedule": {"mode": ["one launch", "split", "per-channel kernels"][choice[0]],
+            "schedule": {"mode": ["one launch", "split", "per-channel kernels",
+                                  "per-channel kernels in turn"][choice[0]],
                          "integrand_schedule": choice[1],
                          "tile_heavy": choice[2], "tile_light": choice[3], "ctas_per_sm": choice[4],
                          "helicity_split": choice[5]},
             "events_per_s_by_mode": {"one launch (0, 1, 4096, 4096)": ev / per_mode[0][0],
                                      "split (1, 1, 4096, 4096)": ev / per_mode[1][0],
-                                     "per-channel kernels (2, 3, -, 4096)": ev / per_mode[2][0]},
+                                     "per-channel kernels (2, 3, -, 4096)": ev / per_mode[2][0],
+                                     "per-channel kernels in turn (3, 4, -, 2048)": ev / per_mode[3][0]},
             "sigma_pb": tot["sigma"], "error_pb": tot["error"],
             "channels": {names[p]: {"sigma_pb": c["sigma"], "error_pb": c["error"], "chi2dof": c["chi2dof"],
                                     "sequential_sigma_pb": q["sigma"]} for p, c, q in zip(procs, chans, seq)},

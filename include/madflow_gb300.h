@@ -392,10 +392,12 @@ int mf_helicity_profile(struct mf_ctx *ctx, int process, const double *momenta_d
  * their own integrand kernels at low priority, which fill the SMs as the
  * expensive work runs out; 2 = every channel as
  * its own integrand kernel, the g g -> t tbar g(g) ones at high priority (in
- * mode 2 these run a single-process pass's kernel, not persistent tiles).
- * Every channel that runs as its own kernel has its own stream, forked from
- * the iteration's start and joined before its reductions, so that the
- * channels overlap on the GPU.  All iterations
+ * mode 2 these run a single-process pass's kernel, not persistent tiles);
+ * 3 = the kernels of mode 2 one after another on the iteration's stream,
+ * each filling the GPU.  In modes 1 and 2 every channel that runs as its own
+ * kernel has its own stream, forked from the iteration's start and joined
+ * before its reductions, so that the channels overlap on the GPU.  All
+ * iterations
  * (launches, reductions, refinements) are captured once as a CUDA graph on a
  * private stream and replayed while the channel list, sizes, sqrt_s, n_iter,
  * couplings and schedule stay the same.  The schedule changes how sums are
@@ -446,14 +448,14 @@ int mf_batch_grad(struct mf_ctx *ctx, int n_ch, const int *processes, const long
                   const mf_cuts *cuts, unsigned int iteration, double *out_host);
 
 /* Sets the mf_integrate_batch schedule explicitly (no counterpart in the
- * paper): mode 0/1/2 (one launch / split / per-channel kernels, see
- * mf_integrate_batch), sched 0/1 (helicity barrier off/on in the
- * g g -> t tbar g(g) matrix elements; in mode 2 also 2, the integrand
+ * paper): mode 0/1/2/3 (one launch / split / per-channel kernels / the same
+ * in turn, see mf_integrate_batch), sched 0/1 (helicity barrier off/on in the
+ * g g -> t tbar g(g) matrix elements; in modes 2 and 3 also 2, the integrand
  * schedule with the tensor-core colour sum, 3, the warp-per-event
  * schedule, and 4, the helicity-recycled recursion, as mf_set_schedule),
  * tile_heavy and tile_light in [32, 2^26] events per work item for the
  * g g -> t tbar g(g) channels and for the others (in modes 1 and 2 the cheaper
- * channels' kernels get one CTA per tile_light events; in mode 2 the
+ * channels' kernels get one CTA per tile_light events; in modes 2 and 3 the
  * g g -> t tbar g(g) kernels at most one CTA per tile_heavy events, up to as
  * many as fit), ctas_per_sm in
  * [0, 16] (0 = as many as fit; values above that are clamped), hsplit 1 or 2
@@ -467,8 +469,9 @@ int mf_set_batch_schedule(struct mf_ctx *ctx, int mode, int sched, long long til
  * paper).  Times one iteration of the given channels and sizes at uniform
  * grids for every mode {0, 1} x (helicity barrier, helicity split) {(0, 1),
  * (1, 1), (1, 2)} x tile_heavy {1024, 2048, 4096} x tile_light {2048, 4096},
- * and mode 2 x sched {1, 2, 3} x tile_heavy {512, 4096} x tile_light
- * {256, 2048, 4096} (CTAs per SM as fit; 54 candidates; each run once
+ * mode 2 x sched {1, 2, 3, 4} x tile_heavy {512, 4096} x tile_light
+ * {256, 2048, 4096}, and mode 3 x sched 4 x tile_heavy {512, 4096} x
+ * tile_light {256, 2048} (CTAs per SM as fit; 64 candidates; each run once
  * untimed first, so that no candidate pays for its kernels' first launch)
  * and keeps the fastest for later
  * mf_integrate_batch calls on this context.  choice_host [6] (nullable)

@@ -263,7 +263,9 @@ int make_plan(mf_ctx* c, int n_ch, const int* procs, const long long* n_events, 
             MF_BCUDA(c, ops->occupancy(MF_MIXED, sm, &per_sm));
             if (per_sm < 1) return mf_fail(c, MF_ERR_CUDA, "integrand kernel does not fit on an SM");
             const long long want = (n_events[i] + sch.tile_light - 1) / sch.tile_light;
-            pl.rows[i] = std::max(1LL, std::min(want, (long long)c->max_blocks));
+            // mode 3 runs one kernel at a time: at most one wave of CTAs, as a single-process pass
+            const long long cap = sch.mode == 3 ? (long long)per_sm * c->n_sm : (long long)c->max_blocks;
+            pl.rows[i] = std::max(1LL, std::min({ want, cap, (long long)c->max_blocks }));
         }
         tile_doubles += (size_t)pl.rows[i] * (2 + ops->D * nb);
     }
@@ -347,13 +349,14 @@ int reset_batch(mf_ctx* c, const Plan& pl, cudaStream_t s)
 }
 
 // one iteration: the persistent launch on s and the side kernels, each channel's on its own
-// stream forked from s and joined back, then per channel the row reduction and refinement
+// stream forked from s and joined back (mode 3: one after another on s), then per channel the
+// row reduction and refinement
 int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s, long long philox_it = -1)
 {
     // Philox iteration of the pass: the iteration index unless given apart
     const unsigned pit = philox_it >= 0 ? (unsigned)philox_it : (unsigned)it;
     const int nb = c->cfg.n_bins;
-    const bool fork = !pl.side.empty();
+    const bool fork = !pl.side.empty() && pl.sch.mode != 3;
     if (fork) MF_BCUDA(c, cudaEventRecord(c->ev_cap, s));
     if (pl.bp.n_slot > 0) {
         MF_BCUDA(c, cudaMemsetAsync(pl.bp.tile_counter, 0, sizeof(unsigned long long), s));
@@ -365,13 +368,18 @@ int enqueue_iteration(mf_ctx* c, Plan& pl, int it, int n_iter, cudaStream_t s, l
     }
     for (size_t k = 0; k < pl.side.size(); ++k) {
         SideLaunch& sl = pl.side[k];
-        cudaStream_t ss = c->cap_side[k];
         sl.kp.iteration = pit;
+        if (!fork) {
+            MF_BCUDA(c, sl.ops->integrand(MF_MIXED, false, sl.sched, 1, sl.kp, sl.nblk, sl.sm, s));
+            continue;
+        }
+        cudaStream_t ss = c->cap_side[k];
         MF_BCUDA(c, cudaStreamWaitEvent(ss, c->ev_cap, 0));
         MF_BCUDA(c, sl.ops->integrand(MF_MIXED, false, sl.sched, 1, sl.kp, sl.nblk, sl.sm, ss));
         MF_BCUDA(c, cudaEventRecord(c->ev_side[k], ss));
     }
-    for (size_t k = 0; k < pl.side.size(); ++k) MF_BCUDA(c, cudaStreamWaitEvent(s, c->ev_side[k], 0));
+    if (fork)
+        for (size_t k = 0; k < pl.side.size(); ++k) MF_BCUDA(c, cudaStreamWaitEvent(s, c->ev_side[k], 0));
     for (int i = 0; i < pl.n_ch; ++i) {
         const int ncol = 2 + pl.dim[i] * nb;
         finish_pass_kernel<<<1, 1024, ncol * sizeof(double), s>>>(
@@ -653,9 +661,9 @@ int mf_set_batch_schedule(mf_ctx* c, int mode, int sched, long long tile_heavy, 
                           int hsplit)
 {
     if (!c) return MF_ERR_ARG;
-    if (mode < 0 || mode > 2 || sched < 0 || sched > 4 || (sched >= 2 && mode != 2) || tile_heavy < 32 ||
+    if (mode < 0 || mode > 3 || sched < 0 || sched > 4 || (sched >= 2 && mode < 2) || tile_heavy < 32 ||
         tile_heavy > (1LL << 26) || tile_light < 32 || tile_light > (1LL << 26) || ctas_per_sm < 0 ||
-        ctas_per_sm > 16 || (hsplit != 1 && hsplit != 2) || (hsplit == 2 && (sched != 1 || mode == 2)))
+        ctas_per_sm > 16 || (hsplit != 1 && hsplit != 2) || (hsplit == 2 && (sched != 1 || mode >= 2)))
         return mf_fail(c, MF_ERR_ARG, "mf_set_batch_schedule: bad argument");
     c->b_hsplit = hsplit;
     c->b_mode = mode;
@@ -686,6 +694,10 @@ int mf_autotune_batch(mf_ctx* c, int n_ch, const int* processes, const long long
     for (int sched = 1; sched <= 4; ++sched)
         for (long long th : { 512LL, 4096LL })
             for (long long tl : { 256LL, 2048LL, 4096LL }) cand.push_back(Schedule{ 2, sched, 0, th, tl, 1 });
+    // the same kernels one after another, each filling the GPU (concurrent channels can starve the
+    // expensive one, whose CTAs take a whole SM's shared memory)
+    for (long long th : { 512LL, 4096LL })
+        for (long long tl : { 256LL, 2048LL }) cand.push_back(Schedule{ 3, 4, 0, th, tl, 1 });
     float best = 1e30f;
     Schedule pick = current_schedule(c);
     cudaEvent_t e0 = nullptr, e1 = nullptr;

@@ -39,7 +39,7 @@ def ctx(pdf_grid):
     c.close()
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_batch_one_iteration_matches_oracle(ctx, opdf, mode):
     """One iteration at the uniform grid: channel i is the oracle pass of that
     process with channel id PHYS.channel + i (mixed precision: 1e-5)."""
@@ -65,7 +65,7 @@ def test_batch_one_iteration_matches_oracle(ctx, opdf, mode):
 # (mode, barrier schedule, helicity split): the persistent kernel with and without the barrier and
 # the split, the split mode (heavy channels persistent, the others as their own kernels), and the
 # per-channel kernels with the warp-per-event schedules (diagrams, helicity-recycled recursion)
-@pytest.mark.parametrize("mode,sched,hsplit", [(0, 0, 1), (0, 1, 2), (1, 1, 1), (2, 3, 1), (2, 4, 1)])
+@pytest.mark.parametrize("mode,sched,hsplit", [(0, 0, 1), (0, 1, 2), (1, 1, 1), (2, 3, 1), (2, 4, 1), (3, 4, 1)])
 def test_batch_pass_events_match_oracle(ctx, opdf, mode, sched, hsplit):
     """One batch pass at non-uniform caller grids with per-event outputs,
     written by the batch's own kernels (the persistent kernel in modes 0 and
@@ -94,7 +94,7 @@ def test_batch_pass_events_match_oracle(ctx, opdf, mode, sched, hsplit):
                                     what=f"batch mode {mode} sched {sched} split {hsplit} process {p}")
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_batch_iterations_match_single_process(ctx, pdf_grid, mode):
     """Three iterations with refinement: each channel equals mf_integrate of
     that process alone (same channel id); only the grouping of the sums
@@ -124,7 +124,7 @@ def test_batch_light_channels_match_oracle_integrate(ctx, opdf):
         assert chans[i]["error"] == pytest.approx(ref["error"], rel=1e-4), p
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_batch_schedule_independent(ctx, mode):
     """At fixed mode and tile sizes the result is bit-identical for every
     barrier schedule and CTA count, and on repeated (graph-replayed) calls."""
@@ -197,11 +197,13 @@ def test_batch_graph_cache_invalidation(ctx):
 def test_batch_autotune(ctx):
     choice = ctx.autotune_batch(CHANNELS, [40000, 10000, 10000, 8000, 4000], PHYS.sqrt_s)
     # the candidates: modes 0/1 with heavy tiles 1024/2048/4096 and light tiles 2048/4096; mode 2
-    # with heavy tiles 512/4096 and light tiles 256/2048/4096
-    assert choice[0] in (0, 1, 2) and choice[1] in (0, 1, 2, 3, 4)
-    assert choice[2] in ((512, 4096) if choice[0] == 2 else (1024, 2048, 4096))
-    assert choice[1] < 2 or choice[0] == 2
-    assert choice[3] in ((256, 2048, 4096) if choice[0] == 2 else (2048, 4096))
+    # with heavy tiles 512/4096 and light tiles 256/2048/4096; mode 3 (schedule 4) with heavy tiles
+    # 512/4096 and light tiles 256/2048
+    assert choice[0] in (0, 1, 2, 3) and choice[1] in (0, 1, 2, 3, 4)
+    assert choice[2] in ((512, 4096) if choice[0] >= 2 else (1024, 2048, 4096))
+    assert choice[1] < 2 or choice[0] >= 2
+    assert choice[0] != 3 or choice[1] == 4
+    assert choice[3] in ({2: (256, 2048, 4096), 3: (256, 2048)}.get(choice[0], (2048, 4096)))
     assert choice[4] == 0 and choice[5] in (1, 2)
     assert choice[5] == 1 or choice[1] == 1
     tot, chans = ctx.integrate_batch(CHANNELS, N_EV, PHYS.sqrt_s, 1)
@@ -221,7 +223,8 @@ def test_batch_bad_arguments(ctx, pdf_grid):
         ctx.integrate_batch([IN.GG_TT], [100], PHYS.sqrt_s, 0)
     assert e.value.code == 1
     for bad in [(1, 2, 1024, 4096, 0), (1, 1, 16, 4096, 0), (1, 1, 1024, 16, 0),
-                (1, 1, 1024, 4096, -1), (1, 1, 1024, 4096, 0, 3), (1, 0, 1024, 4096, 0, 2), (3, 1, 1024, 4096, 0),
+                (1, 1, 1024, 4096, -1), (1, 1, 1024, 4096, 0, 3), (1, 0, 1024, 4096, 0, 2), (4, 1, 1024, 4096, 0),
+                (3, 1, 1024, 4096, 0, 2),
                 (0, 2, 1024, 4096, 0), (2, 1, 1024, 4096, 0, 2), (1, 3, 1024, 4096, 0), (2, 5, 1024, 4096, 0)]:
         with pytest.raises(MfError):
             ctx.set_batch_schedule(*bad)
