@@ -50,10 +50,15 @@ extern "C" {
 enum mf_process { MF_EE_MUMU = 0, MF_GG_TT = 1, MF_UU_TT = 2, MF_GG_TTG = 3, MF_UG_TTU = 4, MF_GG_TTGG = 5,
                   MF_GG_TTGGG = 6 };
 
-/* Arithmetic of the matrix element: MF_FP64 everywhere in FP64; MF_MIXED
- * evaluates wavefunctions, vertices and the colour sum in FP32 and keeps
- * FP64 for phase space, Jacobians, propagator denominators, the heavy-quark
- * spinor normalisation, PDFs, event weights and all accumulations. */
+/* Arithmetic of the integrand: MF_FP64 everywhere in FP64; MF_MIXED
+ * evaluates wavefunctions, vertices and the colour sum in FP32, computes the
+ * phase space, Jacobians, PDFs, propagator denominators and the spinor and
+ * polarisation bases in double-float arithmetic (a value as the sum of two
+ * floats, about 48 bits, on the FP32 pipes; the VEGAS bins and cut decisions
+ * are those of the FP64 path), and keeps FP64 for event weights and all
+ * accumulations.  mf_evaluate and the derivative calls take FP64 momenta and
+ * form the per-event pieces in FP64, except the g g -> t tbar g g record of
+ * the recycled recursion, formed in double-float. */
 enum mf_precision { MF_FP64 = 0, MF_MIXED = 1 };
 
 enum mf_status {
